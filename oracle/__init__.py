@@ -1,0 +1,297 @@
+"""FP64 CPU oracle of the photometric bundle-adjustment step (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package entry's smoke
+check and by the benchmark's CPU-baseline leg, never by the product path.
+The arithmetic lives in `pba_oracle.c` (plain C, double precision, one point at
+a time, following the paper's equations); this module compiles it with gcc and
+marshals numpy arrays.  It shares no code with the CUDA library.
+
+The Levenberg-Marquardt driver (`lm_iteration`) is written out here in Python:
+linearise, damp and solve (Sec. IV-C), apply X [+] dx (Supp.), re-evaluate the
+cost, accept when it decreased (lambda / 10) or reject (lambda x 10).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pba_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+PINHOLE = 0
+SPHERICAL = 1
+
+
+class OSensor(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("Xo", ctypes.c_double * 12)]
+
+
+class OParams(ctypes.Structure):
+    _fields_ = [("w_int", ctypes.c_double), ("w_depth", ctypes.c_double), ("w_normal", ctypes.c_double),
+                ("huber_delta", ctypes.c_double), ("occ_abs", ctypes.c_double), ("occ_rel", ctypes.c_double),
+                ("z_min", ctypes.c_double), ("range_min", ctypes.c_double), ("range_max", ctypes.c_double),
+                ("margin_px", ctypes.c_double), ("margin_rel", ctypes.c_double),
+                ("grad_mode", ctypes.c_int), ("pad_", ctypes.c_int)]
+
+
+def build(force: bool = False, src: Optional[str] = None, out: Optional[str] = None) -> str:
+    """Compile pba_oracle.c into a shared library (gcc, -ffp-contract=off so
+    x86 and Arm builds round identically).  `src` / `out` compile another copy
+    of the source (tests plant a mistake in a private copy this way)."""
+    src = src or _SRC
+    out = out or _LIB_PATH
+    if not force and src == _SRC and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-Wall", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """The oracle library; `path` loads another build (a planted-mistake copy)."""
+    return _load(path)
+
+
+def _load(path: Optional[str] = None):
+    global _lib
+    if path is not None:
+        return _declare(ctypes.CDLL(path))
+    if _lib is None:
+        _lib = _declare(ctypes.CDLL(build()))
+    return _lib
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    d, i32, i64, u32 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    S, Pr = P(OSensor), P(OParams)
+    lib.o_project.argtypes = [S, P(d), P(d)]
+    lib.o_unproject.argtypes = [S, d, d, d, P(d)]
+    lib.o_proj_jacobian.argtypes = [S, P(d), P(d)]
+    lib.o_boxplus.argtypes = [P(d), P(d), P(d)]
+    lib.o_frame_points.argtypes = [S, Pr, P(ctypes.c_float), P(d), P(i32), ctypes.c_int]
+    lib.o_frame_points.restype = ctypes.c_int
+    lib.o_point_residual.argtypes = [S, Pr, P(ctypes.c_float), P(d), P(d), P(d), P(d), P(d), P(d),
+                                     P(d), P(d), P(ctypes.c_int)]
+    lib.o_point_residual.restype = ctypes.c_int
+    lib.o_linearize_pair.argtypes = [S, Pr, P(ctypes.c_float), P(ctypes.c_float), P(d), P(d), P(d), P(d),
+                                     P(d), P(i64), P(u32), P(u32)]
+    lib.o_linearize_pair.restype = ctypes.c_int
+    lib.o_linearize.argtypes = [ctypes.c_int, S, P(i32), P(P(ctypes.c_float)), P(d), ctypes.c_int, P(i32), Pr,
+                                P(d), P(d), P(d), P(i64), P(d), P(d), P(d), P(i64)]
+    lib.o_linearize.restype = ctypes.c_int
+    lib.o_cholesky_solve.argtypes = [ctypes.c_int, P(d), P(d), P(d)]
+    lib.o_cholesky_solve.restype = ctypes.c_int
+    lib.o_solve_step.argtypes = [ctypes.c_int, P(d), P(d), d, P(d)]
+    lib.o_solve_step.restype = ctypes.c_int
+    lib.o_apply_update.argtypes = [ctypes.c_int, P(d), P(d), P(d)]
+    return lib
+
+
+def _ptr(a: Optional[np.ndarray], ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _sensor(s) -> OSensor:
+    """Accepts a synth.Sensor-like object or a dict with the same fields."""
+    g = (lambda k: s[k]) if isinstance(s, dict) else (lambda k: getattr(s, k))
+    o = OSensor()
+    o.model, o.width, o.height = int(g("model")), int(g("width")), int(g("height"))
+    o.fx, o.fy, o.cx, o.cy = float(g("fx")), float(g("fy")), float(g("cx")), float(g("cy"))
+    xo = np.asarray(g("extrinsic"), dtype=np.float64).reshape(12)
+    for k in range(12):
+        o.Xo[k] = xo[k]
+    return o
+
+
+def _params(p: Dict, margin_px: float = 1e-3, margin_rel: float = 1e-4) -> OParams:
+    o = OParams()
+    for k in ("w_int", "w_depth", "w_normal", "huber_delta", "occ_abs", "occ_rel", "z_min",
+              "range_min", "range_max"):
+        setattr(o, k, float(p[k]))
+    o.margin_px = float(p.get("margin_px", margin_px))
+    o.margin_rel = float(p.get("margin_rel", margin_rel))
+    o.grad_mode = int(p.get("grad_mode", 0))
+    return o
+
+
+# ---------------------------------------------------------------- primitives
+
+def project(sensor, p, lib=None) -> np.ndarray:
+    lib, p = lib or _load(), _f64(p)
+    uv = np.zeros(2)
+    lib.o_project(ctypes.byref(_sensor(sensor)), _ptr(p, ctypes.c_double), _ptr(uv, ctypes.c_double))
+    return uv
+
+
+def unproject(sensor, u: float, v: float, d: float, lib=None) -> np.ndarray:
+    lib = lib or _load()
+    p = np.zeros(3)
+    lib.o_unproject(ctypes.byref(_sensor(sensor)), u, v, d, _ptr(p, ctypes.c_double))
+    return p
+
+
+def proj_jacobian(sensor, p, lib=None) -> np.ndarray:
+    lib, p = lib or _load(), _f64(p)
+    J = np.zeros(6)
+    lib.o_proj_jacobian(ctypes.byref(_sensor(sensor)), _ptr(p, ctypes.c_double), _ptr(J, ctypes.c_double))
+    return J.reshape(2, 3)
+
+
+def boxplus(X, dx, lib=None) -> np.ndarray:
+    lib, X, dx = lib or _load(), _f64(X).reshape(12), _f64(dx).reshape(6)
+    out = np.zeros(12)
+    lib.o_boxplus(_ptr(X, ctypes.c_double), _ptr(dx, ctypes.c_double), _ptr(out, ctypes.c_double))
+    return out.reshape(3, 4)
+
+
+def frame_points(sensor, params: Dict, channels: np.ndarray, lib=None):
+    """(points (P, 7) = p_u, g_u, n_u^o ; pixel indices (P,)) in raster order."""
+    lib = lib or _load()
+    ch = np.ascontiguousarray(channels, dtype=np.float32)
+    s = _sensor(sensor)
+    cap = s.width * s.height
+    out = np.zeros((cap, 7))
+    pix = np.zeros(cap, dtype=np.int32)
+    n = lib.o_frame_points(ctypes.byref(s), ctypes.byref(_params(params)), _ptr(ch, ctypes.c_float),
+                           _ptr(out, ctypes.c_double), _ptr(pix, ctypes.c_int32), cap)
+    return out[:n].copy(), pix[:n].copy()
+
+
+def point_residual(sensor, params: Dict, tgt_channels: np.ndarray, Xi, Xj, pt, lib=None) -> Dict:
+    lib = lib or _load()
+    tgt = np.ascontiguousarray(tgt_channels, dtype=np.float32)
+    Xi, Xj, pt = _f64(Xi).reshape(12), _f64(Xj).reshape(12), _f64(pt).reshape(7)
+    e, Ji, Jj = np.zeros(5), np.zeros(30), np.zeros(30)
+    rho, w, flag = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    ok = lib.o_point_residual(ctypes.byref(_sensor(sensor)), ctypes.byref(_params(params)),
+                              _ptr(tgt, ctypes.c_float), _ptr(Xi, ctypes.c_double), _ptr(Xj, ctypes.c_double),
+                              _ptr(pt, ctypes.c_double), _ptr(e, ctypes.c_double), _ptr(Ji, ctypes.c_double),
+                              _ptr(Jj, ctypes.c_double), ctypes.byref(rho), ctypes.byref(w), ctypes.byref(flag))
+    return dict(valid=bool(ok), e=e, Ji=Ji.reshape(5, 6), Jj=Jj.reshape(5, 6), rho=rho.value, w=w.value,
+                flag=bool(flag.value))
+
+
+def linearize_pair(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, Xj, lib=None) -> Dict:
+    """H12 (12x12), b12, cost, count, mask and margin-flag bit words of one pair."""
+    lib = lib or _load()
+    src = np.ascontiguousarray(src, dtype=np.float32)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+    Xi, Xj = _f64(Xi).reshape(12), _f64(Xj).reshape(12)
+    s = _sensor(sensor)
+    cap_words = (s.width * s.height + 31) // 32 + 1
+    H, b = np.zeros(144), np.zeros(12)
+    cost, count = ctypes.c_double(0.0), ctypes.c_int64(0)
+    mask = np.zeros(cap_words, dtype=np.uint32)
+    flags = np.zeros(cap_words, dtype=np.uint32)
+    n = lib.o_linearize_pair(ctypes.byref(s), ctypes.byref(_params(params)), _ptr(src, ctypes.c_float),
+                             _ptr(tgt, ctypes.c_float), _ptr(Xi, ctypes.c_double), _ptr(Xj, ctypes.c_double),
+                             _ptr(H, ctypes.c_double), _ptr(b, ctypes.c_double), ctypes.byref(cost),
+                             ctypes.byref(count), _ptr(mask, ctypes.c_uint32), _ptr(flags, ctypes.c_uint32))
+    if n < 0:
+        raise MemoryError("oracle: allocation failed")
+    nw = (n + 31) // 32
+    return dict(H=H.reshape(12, 12), b=b, cost=cost.value, count=count.value, n_points=n,
+                mask=mask[:nw].copy(), flags=flags[:nw].copy())
+
+
+def linearize(sensors: Sequence, frame_sensor, channels: Sequence[np.ndarray], poses, pairs, params: Dict,
+              want_system: bool = True, want_pairs: bool = False, lib=None) -> Dict:
+    """Dense H (6N x 6N, gauge not fixed), b, total cost F (Eq. 6), count."""
+    lib = lib or _load()
+    n = len(channels)
+    chans = [np.ascontiguousarray(c, dtype=np.float32) for c in channels]
+    cptrs = (ctypes.POINTER(ctypes.c_float) * n)(*[_ptr(c, ctypes.c_float) for c in chans])
+    sarr = (OSensor * len(sensors))(*[_sensor(s) for s in sensors])
+    fs = np.ascontiguousarray(frame_sensor, dtype=np.int32)
+    poses = _f64(poses).reshape(n, 12)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    m = pairs.shape[0]
+    H = np.zeros((6 * n, 6 * n)) if want_system else None
+    b = np.zeros(6 * n) if want_system else None
+    pH = np.zeros((m, 12, 12)) if want_pairs else None
+    pb = np.zeros((m, 12)) if want_pairs else None
+    pc = np.zeros(m)
+    pn = np.zeros(m, dtype=np.int64)
+    cost, count = ctypes.c_double(0.0), ctypes.c_int64(0)
+    st = lib.o_linearize(n, sarr, _ptr(fs, ctypes.c_int32), cptrs, _ptr(poses, ctypes.c_double), m,
+                         _ptr(pairs, ctypes.c_int32), ctypes.byref(_params(params)), _ptr(H, ctypes.c_double),
+                         _ptr(b, ctypes.c_double), ctypes.byref(cost), ctypes.byref(count),
+                         _ptr(pH, ctypes.c_double), _ptr(pb, ctypes.c_double), _ptr(pc, ctypes.c_double),
+                         _ptr(pn, ctypes.c_int64))
+    if st != 0:
+        raise ValueError(f"oracle: malformed pair list (status {st})")
+    return dict(H=H, b=b, cost=cost.value, count=count.value, pair_H=pH, pair_b=pb, pair_cost=pc,
+                pair_count=pn)
+
+
+def cholesky_solve(A, rhs, lib=None) -> np.ndarray:
+    lib, A, rhs = lib or _load(), _f64(A), _f64(rhs)
+    x = np.zeros(rhs.shape[0])
+    st = lib.o_cholesky_solve(rhs.shape[0], _ptr(A, ctypes.c_double), _ptr(rhs, ctypes.c_double),
+                              _ptr(x, ctypes.c_double))
+    if st != 0:
+        raise np.linalg.LinAlgError("oracle: matrix not positive definite")
+    return x
+
+
+def solve_step(H, b, lam: float, lib=None):
+    """dx (6N) with dx_0 = 0; returns (dx, ok)."""
+    lib, H, b = lib or _load(), _f64(H), _f64(b)
+    n = b.shape[0] // 6
+    dx = np.zeros(6 * n)
+    st = lib.o_solve_step(n, _ptr(H, ctypes.c_double), _ptr(b, ctypes.c_double), float(lam),
+                          _ptr(dx, ctypes.c_double))
+    return dx, st == 0
+
+
+def apply_update(poses, dx, lib=None) -> np.ndarray:
+    lib, poses, dx = lib or _load(), _f64(poses), _f64(dx)
+    n = poses.reshape(-1, 12).shape[0]
+    out = np.zeros((n, 12))
+    lib.o_apply_update(n, _ptr(poses.reshape(n, 12), ctypes.c_double), _ptr(dx, ctypes.c_double),
+                       _ptr(out, ctypes.c_double))
+    return out.reshape(n, 3, 4)
+
+
+def initial_lambda(H) -> float:
+    """lambda_0 = 1e-4 * max diag(H_ff) (frame 0 excluded)."""
+    d = np.diag(np.asarray(H))[6:]
+    return 1e-4 * float(d.max()) if d.size else 0.0
+
+
+def lm_iteration(w, poses, lam: Optional[float], lib=None) -> Dict:
+    """One Levenberg-Marquardt iteration on workload-like `w` (sensors,
+    frame_sensor, channels, pairs, params) at `poses`.  lam=None takes
+    initial_lambda.  Returns the accepted poses, the new lambda, both costs."""
+    lin = linearize(w.sensors, w.frame_sensor, w.channels, poses, w.pairs, w.params, lib=lib)
+    if lam is None:
+        lam = initial_lambda(lin["H"])
+    dx, ok = solve_step(lin["H"], lin["b"], lam, lib=lib)
+    cand = apply_update(poses, dx, lib=lib)
+    new = linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False, lib=lib)
+    accepted = ok and new["cost"] < lin["cost"]
+    return dict(poses=cand if accepted else np.asarray(poses).copy(), accepted=accepted,
+                lam=lam / 10.0 if accepted else lam * 10.0, lam_used=lam, cost=lin["cost"],
+                new_cost=new["cost"], count=lin["count"], H=lin["H"], b=lin["b"], dx=dx,
+                candidate=cand, solve_ok=ok)

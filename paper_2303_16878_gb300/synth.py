@@ -1,0 +1,561 @@
+"""Seeded synthetic scenes, sensor renders, trajectories and pair lists.
+
+This module produces the inputs of the photometric bundle-adjustment path
+(Sec. IV, Eq. 3-6 and the supplementary error terms): per-frame five-channel
+cue images (intensity g, depth or range d, normal n_x n_y n_z, Sec. IV-A),
+ground-truth and perturbed sensor poses, and a directed pair list (Sec. IV-B).
+
+It ray-casts analytic scenes (axis-aligned boxes seen from outside, rooms seen
+from inside) along each pixel's viewing ray, as any renderer must.  It contains
+none of the bundle-adjustment arithmetic: no residuals, no Jacobians, no robust
+weights, no normal equations and no pose updates.  Both the CPU oracle and the
+CUDA path consume what it returns, and neither imports the other.
+
+Everything is a pure function of the integer seeds, so every test and benchmark
+input can be regenerated bit for bit on any machine.
+
+Pose convention: a pose is a 3x4 row-major matrix [R | t] mapping points of the
+sensor (platform) frame into the world frame, p_w = R p + t (Eq. 1).
+Pinhole sensor frame: x right, y down, z forward; depth is the z coordinate.
+Spherical (LiDAR) sensor frame: x forward, y left, z up; d is the range.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+PINHOLE = 0
+SPHERICAL = 1
+
+IDENTITY_3x4 = np.array([[1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, 1.0, 0]])
+
+
+# --------------------------------------------------------------------------
+# sensors
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Sensor:
+    """Intrinsics of one sensor (Eq. 2 pinhole K, Eq. 3 spherical K_[1,2])."""
+
+    model: int
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    extrinsic: np.ndarray = dataclasses.field(default_factory=lambda: IDENTITY_3x4.copy())
+
+    def as_dict(self) -> Dict:
+        return dict(model=self.model, width=self.width, height=self.height,
+                    fx=self.fx, fy=self.fy, cx=self.cx, cy=self.cy,
+                    extrinsic=np.asarray(self.extrinsic, dtype=np.float64).reshape(12))
+
+
+def pinhole_sensor(width: int, height: int, f: float, cx: float, cy: float) -> Sensor:
+    return Sensor(PINHOLE, width, height, f, f, cx, cy)
+
+
+def spherical_sensor(width: int, height: int, vfov_up_deg: float, vfov_down_deg: float) -> Sensor:
+    """Spherical sensor with azimuth decreasing left to right over 360 degrees
+    and row 0 at the top elevation (the reading of the spherical K taken for
+    the paper's "resolution and offset" wording of Eq. 3)."""
+    up = math.radians(vfov_up_deg)
+    down = math.radians(vfov_down_deg)
+    vfov = up - down
+    fx = -width / (2.0 * math.pi)
+    cx = width / 2.0
+    fy = -(height - 1) / vfov
+    cy = (height - 1) * up / vfov
+    return Sensor(SPHERICAL, width, height, fx, fy, cx, cy)
+
+
+def _pixel_rays(s: Sensor) -> Tuple[np.ndarray, bool]:
+    """Viewing ray of every pixel centre in the sensor frame, shape (H, W, 3).
+
+    Pinhole rays have unit z so the hit distance along them is the depth;
+    spherical rays have unit length so the hit distance is the range.
+    """
+    cols = np.arange(s.width, dtype=np.float64)[None, :]
+    rows = np.arange(s.height, dtype=np.float64)[:, None]
+    if s.model == PINHOLE:
+        x = np.broadcast_to((cols - s.cx) / s.fx, (s.height, s.width))
+        y = np.broadcast_to((rows - s.cy) / s.fy, (s.height, s.width))
+        return np.stack([x, y, np.ones_like(x)], axis=-1), True
+    az = np.broadcast_to((cols - s.cx) / s.fx, (s.height, s.width))
+    el = np.broadcast_to((rows - s.cy) / s.fy, (s.height, s.width))
+    ce = np.cos(el)
+    return np.stack([ce * np.cos(az), ce * np.sin(az), np.sin(el)], axis=-1), False
+
+
+# --------------------------------------------------------------------------
+# rotations (for building trajectories; plain matrix algebra)
+# --------------------------------------------------------------------------
+
+def rot_axis_angle(axis: Sequence[float], angle: float) -> np.ndarray:
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    k = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * k + (1 - math.cos(angle)) * (k @ k)
+
+
+def rot_vec(v: np.ndarray) -> np.ndarray:
+    th = float(np.linalg.norm(v))
+    if th < 1e-15:
+        return np.eye(3)
+    return rot_axis_angle(v / th, th)
+
+
+def look_at(eye, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """3x4 pose of a pinhole camera (x right, y down, z forward) at `eye`."""
+    eye = np.asarray(eye, dtype=np.float64)
+    z = np.asarray(target, dtype=np.float64) - eye
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, dtype=np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    out = np.zeros((3, 4))
+    out[:, 0], out[:, 1], out[:, 2], out[:, 3] = x, y, z, eye
+    return out
+
+
+def compose(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """a * b for 3x4 rigid transforms."""
+    out = np.zeros((3, 4))
+    out[:, :3] = a[:, :3] @ b[:, :3]
+    out[:, 3] = a[:, :3] @ b[:, 3] + a[:, 3]
+    return out
+
+
+def perturb_poses(poses: np.ndarray, sigma_t: float, sigma_r: float, seed: int,
+                  keep_first: bool = True) -> np.ndarray:
+    """Right-multiply each pose by a random rigid motion: translation
+    N(0, sigma_t) per axis, rotation vector N(0, sigma_r) per axis [rad]."""
+    rng = np.random.default_rng(seed)
+    out = poses.copy()
+    for k in range(poses.shape[0]):
+        dt = rng.normal(0.0, sigma_t, 3)
+        dr = rng.normal(0.0, sigma_r, 3)
+        if keep_first and k == 0:
+            continue
+        d = np.zeros((3, 4))
+        d[:, :3] = rot_vec(dr)
+        d[:, 3] = dt
+        out[k] = compose(poses[k], d)
+    return out
+
+
+# --------------------------------------------------------------------------
+# procedural texture
+# --------------------------------------------------------------------------
+
+def _hash2(i: np.ndarray, j: np.ndarray, seed: int) -> np.ndarray:
+    """Lattice hash to [0, 1) (integer mixing, 32-bit)."""
+    m = np.uint64(0xFFFFFFFF)
+    x = (i.astype(np.int64).astype(np.uint64) * np.uint64(0x8DA6B343)) & m
+    x ^= (j.astype(np.int64).astype(np.uint64) * np.uint64(0xD8163841)) & m
+    x ^= np.uint64((seed * 0xCB1AB31F) & 0xFFFFFFFF)
+    x = (x ^ (x >> np.uint64(16))) * np.uint64(0x7FEB352D) & m
+    x = (x ^ (x >> np.uint64(15))) * np.uint64(0x846CA68B) & m
+    x = x ^ (x >> np.uint64(16))
+    return x.astype(np.float64) / 4294967296.0
+
+
+def value_noise(s: np.ndarray, t: np.ndarray, seed: int, octaves: int = 4) -> np.ndarray:
+    """Fractal value noise in [0, 1] with C1 (smoothstep) interpolation."""
+    total = np.zeros_like(s)
+    amp, freq, norm = 0.5, 1.0, 0.0
+    for o in range(octaves):
+        ss, tt = s * freq, t * freq
+        i0, j0 = np.floor(ss), np.floor(tt)
+        fs, ft = ss - i0, tt - j0
+        fs = fs * fs * (3 - 2 * fs)
+        ft = ft * ft * (3 - 2 * ft)
+        sd = seed * 7919 + o * 104729
+        h00 = _hash2(i0, j0, sd)
+        h10 = _hash2(i0 + 1, j0, sd)
+        h01 = _hash2(i0, j0 + 1, sd)
+        h11 = _hash2(i0 + 1, j0 + 1, sd)
+        v = (h00 * (1 - fs) + h10 * fs) * (1 - ft) + (h01 * (1 - fs) + h11 * fs) * ft
+        total += amp * v
+        norm += amp
+        amp *= 0.5
+        freq *= 2.0
+    return total / norm
+
+
+# --------------------------------------------------------------------------
+# scenes and ray casting
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Box:
+    lo: np.ndarray
+    hi: np.ndarray
+    inside: bool = False        # True: viewed from inside (a room), hit the exit face
+    albedo: float = 0.8
+    tex_freq: float = 2.0       # texture base frequency [cycles / m]
+    tex_seed: int = 0
+    tex_contrast: float = 0.8   # intensity = albedo * (1 - c + c * noise)
+
+
+@dataclasses.dataclass
+class Scene:
+    boxes: List[Box]
+    lambertian: bool = False    # intensity *= |n . ray| (LiDAR reflectance)
+
+
+def _cast(scene: Scene, origin: np.ndarray, dirs: np.ndarray, d_max: float = np.inf):
+    """Nearest hit of rays origin + t * dirs (dirs: (K, 3)) against the scene.
+    Returns (t, normal_world, intensity); t = inf where nothing is hit.
+    Boxes farther than d_max from the origin are skipped."""
+    k = dirs.shape[0]
+    best_t = np.full(k, np.inf)
+    best_axis = np.zeros(k, dtype=np.int64)
+    best_box = np.full(k, -1, dtype=np.int64)
+    d = [np.ascontiguousarray(dirs[:, a]) for a in range(3)]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = [1.0 / d[a] for a in range(3)]
+    for bi, b in enumerate(scene.boxes):
+        if not b.inside:
+            nearest = np.clip(origin, b.lo, b.hi)
+            if np.linalg.norm(nearest - origin) > d_max * 1.01:
+                continue
+        tmin, tmax = [], []
+        with np.errstate(invalid="ignore"):
+            for a in range(3):
+                t1 = (b.lo[a] - origin[a]) * inv[a]
+                t2 = (b.hi[a] - origin[a]) * inv[a]
+                if origin[a] == b.lo[a] or origin[a] == b.hi[a]:  # 0 * inf on the slab plane
+                    t1 = np.where(np.isnan(t1), -np.inf, t1)
+                    t2 = np.where(np.isnan(t2), np.inf, t2)
+                tmin.append(np.minimum(t1, t2))
+                tmax.append(np.maximum(t1, t2))
+        if b.inside:
+            t_hit = np.minimum(np.minimum(tmax[0], tmax[1]), tmax[2])
+            axis = np.where(tmax[0] == t_hit, 0, np.where(tmax[1] == t_hit, 1, 2))
+            ok = t_hit > 1e-9
+        else:
+            t_near = np.maximum(np.maximum(tmin[0], tmin[1]), tmin[2])
+            t_far = np.minimum(np.minimum(tmax[0], tmax[1]), tmax[2])
+            axis = np.where(tmin[0] == t_near, 0, np.where(tmin[1] == t_near, 1, 2))
+            ok = (t_near <= t_far) & (t_near > 1e-9)
+            t_hit = t_near
+        upd = ok & (t_hit < best_t)
+        best_t = np.where(upd, t_hit, best_t)
+        best_axis = np.where(upd, axis, best_axis)
+        best_box = np.where(upd, bi, best_box)
+    hit = np.isfinite(best_t)
+    rows_all = np.arange(k)
+    # the face normal points against the ray (outside boxes: outward normal of
+    # the entry face; rooms: inward normal of the exit face)
+    sign = -np.sign(dirs[rows_all, best_axis])
+    normal = np.zeros((k, 3))
+    normal[rows_all, best_axis] = np.where(hit, sign, 0.0)
+    point = origin[None, :] + np.where(hit, best_t, 0.0)[:, None] * dirs
+    inten = np.zeros(k)
+    for bi, b in enumerate(scene.boxes):
+        sel = hit & (best_box == bi)
+        if not np.any(sel):
+            continue
+        ax = best_axis[sel]
+        p = point[sel]
+        # texture coordinates: the two world axes spanning the face
+        s_idx = np.where(ax == 0, 1, 0)
+        t_idx = np.where(ax == 2, 1, 2)
+        rows = np.arange(p.shape[0])
+        s = p[rows, s_idx] * b.tex_freq
+        t = p[rows, t_idx] * b.tex_freq
+        nz = value_noise(s, t, b.tex_seed * 31 + ax)
+        inten[sel] = b.albedo * (1.0 - b.tex_contrast + b.tex_contrast * nz)
+    if scene.lambertian:
+        dn = np.linalg.norm(dirs, axis=1)
+        cosang = np.abs(np.sum(normal * dirs, axis=1)) / np.maximum(dn, 1e-30)
+        inten = inten * cosang
+    return best_t, normal, inten
+
+
+def render(scene: Scene, sensor: Sensor, sensor_pose: np.ndarray,
+           d_min: float, d_max: float) -> np.ndarray:
+    """Five-channel image (H, W, 5) float32: g, d, n_x, n_y, n_z (Sec. IV-A).
+
+    d is the depth (pinhole) or range (spherical) of the nearest surface, 0
+    where no surface lies within [d_min, d_max] (an invalid pixel).  Normals
+    are the analytic surface normals in the sensor frame, oriented towards the
+    sensor, and zero at invalid pixels.
+    """
+    rays, _ = _pixel_rays(sensor)
+    r = sensor_pose[:, :3]
+    o = sensor_pose[:, 3]
+    d_world = rays.reshape(-1, 3) @ r.T
+    t, n_world, inten = _cast(scene, o, d_world, d_max)
+    valid = np.isfinite(t) & (t >= d_min) & (t <= d_max)
+    n_sensor = n_world @ r  # R^T n for each row
+    out = np.zeros((sensor.height * sensor.width, 5), dtype=np.float64)
+    out[:, 0] = np.where(valid, inten, 0.0)
+    out[:, 1] = np.where(valid, t, 0.0)
+    out[:, 2:5] = np.where(valid[:, None], n_sensor, 0.0)
+    return out.reshape(sensor.height, sensor.width, 5).astype(np.float32)
+
+
+def quantize_fp16(channels: np.ndarray) -> np.ndarray:
+    """Round the intensity and normal channels to the nearest binary16 value
+    (like a sensor with a 10-bit mantissa), leaving depth in float32."""
+    out = channels.copy()
+    for c in (0, 2, 3, 4):
+        out[..., c] = out[..., c].astype(np.float16).astype(np.float32)
+    return out
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    """One bundle-adjustment problem instance."""
+
+    name: str
+    sensors: List[Sensor]
+    frame_sensor: np.ndarray     # (N,) int32
+    channels: List[np.ndarray]   # N arrays (H, W, 5) float32
+    poses_gt: np.ndarray         # (N, 3, 4) float64
+    poses_init: np.ndarray       # (N, 3, 4) float64
+    pairs: np.ndarray            # (M, 2) int32, directed (source i, target j)
+    params: Dict                 # method configuration (weights, Huber delta, thresholds)
+
+    @property
+    def n_frames(self) -> int:
+        return len(self.channels)
+
+    def channels_array(self) -> np.ndarray:
+        """All frames stacked (N, H, W, 5); valid only when sizes agree."""
+        return np.stack(self.channels, axis=0)
+
+    def subset(self, frames: Sequence[int]) -> "Workload":
+        frames = list(frames)
+        remap = {f: k for k, f in enumerate(frames)}
+        keep = [p for p in self.pairs.tolist() if p[0] in remap and p[1] in remap]
+        pairs = np.array([[remap[a], remap[b]] for a, b in keep], dtype=np.int32).reshape(-1, 2)
+        return Workload(self.name + "-subset", self.sensors, self.frame_sensor[frames].copy(),
+                        [self.channels[f] for f in frames], self.poses_gt[frames].copy(),
+                        self.poses_init[frames].copy(), pairs, dict(self.params))
+
+
+def default_params(**over) -> Dict:
+    """Method configuration; values the paper leaves open take these defaults."""
+    p = dict(w_int=1.0, w_depth=1.0, w_normal=1.0, huber_delta=0.1,
+             occ_abs=0.1, occ_rel=0.05, z_min=0.05, range_min=0.0, range_max=1e30,
+             grad_mode=0)
+    p.update(over)
+    return p
+
+
+def _room_scene(seed: int) -> Scene:
+    rng = np.random.default_rng(seed)
+    room = Box(np.array([-2.5, -2.5, 0.0]), np.array([2.5, 2.5, 3.0]), inside=True,
+               albedo=1.0, tex_freq=float(rng.uniform(2.5, 3.5)), tex_seed=int(rng.integers(1, 1 << 20)),
+               tex_contrast=0.85)
+    return Scene([room])
+
+
+def make_rgbd_room(n_frames: int = 8, width: int = 160, height: int = 120, f: float = 120.0,
+                   cx: Optional[float] = None, cy: Optional[float] = None,
+                   seed: int = 1, sigma_t: float = 0.02, sigma_r_deg: float = 1.0,
+                   pair_window: int = 3, fp16_exact: bool = True,
+                   depth_noise: float = 0.0, intensity_noise: float = 0.0,
+                   params: Optional[Dict] = None) -> Workload:
+    """RGB-D pinhole sequence in a 5 x 5 x 3 m room of six textured planes.
+
+    Cameras sit on a 1 m circle at 1.5 m height and look at a common point on
+    the +y wall, so all pairs within `pair_window` frames overlap.  Depth is
+    clipped to 0.5-5 m.  Seeds: scene 1000+seed, trajectory 2000+seed,
+    perturbation 3000+seed.
+    """
+    cx = width / 2.0 if cx is None else cx
+    cy = height / 2.0 if cy is None else cy
+    scene = _room_scene(1000 + seed)
+    sensor = pinhole_sensor(width, height, f, cx, cy)
+    rng = np.random.default_rng(2000 + seed)
+    poses = np.zeros((n_frames, 3, 4))
+    for k in range(n_frames):
+        th = 2 * math.pi * k / n_frames + rng.uniform(-0.05, 0.05)
+        eye = np.array([math.cos(th), math.sin(th), 1.5 + rng.uniform(-0.05, 0.05)])
+        target = np.array([rng.uniform(-0.3, 0.3), 2.5, 1.3 + rng.uniform(-0.2, 0.2)])
+        poses[k] = look_at(eye, target)
+    chans = []
+    for k in range(n_frames):
+        c = render(scene, sensor, poses[k], 0.5, 5.0)
+        if depth_noise > 0 or intensity_noise > 0:
+            nrng = np.random.default_rng(5000 + seed * 977 + k)
+            valid = c[..., 1] > 0
+            z = c[..., 1].astype(np.float64)
+            c[..., 1] = np.where(valid, z + nrng.normal(0, 1, z.shape) * depth_noise * z * z, 0).astype(np.float32)
+            c[..., 0] = np.where(valid, c[..., 0] + nrng.normal(0, intensity_noise, z.shape), 0).astype(np.float32)
+        if fp16_exact:
+            c = quantize_fp16(c)
+        chans.append(c)
+    init = perturb_poses(poses, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    pairs = [(i, j) for i in range(n_frames) for j in range(i + 1, n_frames) if j - i <= pair_window]
+    prm = default_params()
+    if params:
+        prm.update(params)
+    return Workload(f"rgbd-room-{n_frames}x{width}x{height}", [sensor],
+                    np.zeros(n_frames, dtype=np.int32), chans, poses, init,
+                    np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)
+
+
+def _street_scene(seed: int, x_lo: float, x_hi: float) -> Scene:
+    rng = np.random.default_rng(seed)
+    boxes = [Box(np.array([x_lo - 150, -150.0, -1.0]), np.array([x_hi + 150, 150.0, 0.0]),
+                 albedo=0.35, tex_freq=1.5, tex_seed=int(rng.integers(1, 1 << 20)), tex_contrast=0.7)]
+    for side in (+1, -1):
+        x = x_lo - 60.0
+        while x < x_hi + 60.0:
+            length = rng.uniform(8, 20)
+            depth = rng.uniform(6, 15)
+            height = rng.uniform(4, 15)
+            y0 = 7.0 + rng.uniform(0, 1.5)
+            lo = np.array([x, y0 if side > 0 else -y0 - depth, 0.0])
+            hi = np.array([x + length, y0 + depth if side > 0 else -y0, height])
+            boxes.append(Box(lo, hi, albedo=float(rng.uniform(0.3, 0.95)),
+                             tex_freq=float(rng.uniform(0.8, 2.0)),
+                             tex_seed=int(rng.integers(1, 1 << 20)), tex_contrast=0.75))
+            x += length + rng.uniform(0.0, 4.0)
+        x = x_lo - 40.0 + rng.uniform(0, 4)
+        while x < x_hi + 40.0:
+            y = side * rng.uniform(4.5, 5.5)
+            boxes.append(Box(np.array([x - 0.15, y - 0.15, 0.0]), np.array([x + 0.15, y + 0.15, 5.0]),
+                             albedo=0.9, tex_freq=3.0, tex_seed=int(rng.integers(1, 1 << 20)),
+                             tex_contrast=0.3))
+            x += rng.uniform(6, 10)
+        x = x_lo - 30.0 + rng.uniform(0, 10)
+        while x < x_hi + 30.0:
+            y = side * rng.uniform(2.8, 3.6)
+            boxes.append(Box(np.array([x, y - 0.9, 0.0]), np.array([x + 4.2, y + 0.9, 1.5]),
+                             albedo=float(rng.uniform(0.2, 0.9)), tex_freq=2.5,
+                             tex_seed=int(rng.integers(1, 1 << 20)), tex_contrast=0.6))
+            x += rng.uniform(7, 16)
+    return Scene(boxes, lambertian=True)
+
+
+def _street_trajectory(n_frames: int, spacing: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    phase = rng.uniform(0, 2 * math.pi)
+    poses = np.zeros((n_frames, 3, 4))
+    for k in range(n_frames):
+        x = k * spacing
+        y = 0.6 * math.sin(x / 9.0 + phase)
+        dy = 0.6 / 9.0 * math.cos(x / 9.0 + phase)
+        yaw = math.atan2(dy, 1.0) + rng.uniform(-0.02, 0.02)
+        r = rot_axis_angle((0, 0, 1), yaw) @ rot_axis_angle((0, 1, 0), rng.uniform(-0.01, 0.01))
+        poses[k, :, :3] = r
+        poses[k, :, 3] = (x, y, 1.8 + rng.uniform(-0.03, 0.03))
+    return poses
+
+
+def overlap_ratio(src: np.ndarray, tgt: np.ndarray, sensor: Sensor, pose_src: np.ndarray,
+                  pose_tgt: np.ndarray, rel_tol: float = 0.05, stride: int = 1) -> float:
+    """Fraction of frame src's valid pixels that are seen by frame tgt at the
+    same distance (visibility test for building the pair list, Sec. IV-B
+    criterion 3).  Uses the renderer's own ray geometry and nearest pixels;
+    `stride` > 1 estimates the ratio on every stride-th pixel (raster order)."""
+    rays, is_pin = _pixel_rays(sensor)
+    d = src[..., 1].astype(np.float64)
+    valid = d > 0
+    if stride > 1:
+        sub = np.zeros(valid.size, dtype=bool)
+        sub[::stride] = True
+        valid &= sub.reshape(valid.shape)
+    if not np.any(valid):
+        return 0.0
+    pts = rays[valid] * d[valid][:, None]
+    pw = pts @ pose_src[:, :3].T + pose_src[:, 3]
+    pt = (pw - pose_tgt[:, 3]) @ pose_tgt[:, :3]
+    if is_pin:
+        z = pt[:, 2]
+        ok = z > 1e-3
+        zz = np.where(ok, z, 1.0)
+        col = np.rint(sensor.fx * pt[:, 0] / zz + sensor.cx)
+        row = np.rint(sensor.fy * pt[:, 1] / zz + sensor.cy)
+        dist = z
+    else:
+        rxy = np.hypot(pt[:, 0], pt[:, 1])
+        col = np.rint(sensor.fx * np.arctan2(pt[:, 1], pt[:, 0]) + sensor.cx) % sensor.width
+        row = np.rint(sensor.fy * np.arctan2(pt[:, 2], rxy) + sensor.cy)
+        dist = np.linalg.norm(pt, axis=1)
+        ok = np.ones(pt.shape[0], dtype=bool)
+    ok &= (col >= 0) & (col < sensor.width) & (row >= 0) & (row < sensor.height)
+    ci = np.where(ok, col, 0).astype(np.int64)
+    ri = np.where(ok, row, 0).astype(np.int64)
+    dt = tgt[..., 1].astype(np.float64)[ri, ci]
+    ok &= (dt > 0) & (np.abs(dt - dist) <= rel_tol * dist + 0.05)
+    return float(np.count_nonzero(ok)) / float(pts.shape[0])
+
+
+def make_lidar_street(n_frames: int = 50, width: int = 1024, height: int = 64,
+                      vfov_up_deg: float = 16.6, vfov_down_deg: float = -16.6,
+                      spacing: float = 1.0, seed: int = 2, sigma_t: float = 0.10,
+                      sigma_r_deg: float = 0.5, drop: float = 0.05, min_overlap: float = 0.3,
+                      max_pair_distance: float = 40.0, fp16_exact: bool = True,
+                      params: Optional[Dict] = None) -> Workload:
+    """LiDAR spherical-projection sequence along a synthetic street.
+
+    Ground plane, two rows of textured box buildings, poles and parked cars;
+    range 1-80 m; intensity = Lambertian |n . ray| x textured albedo; a
+    fraction `drop` of returns is removed (Bernoulli); 50 poses along a 50 m
+    path.  Pairs (i < j) are kept when the overlap ratio exceeds `min_overlap`.
+    Seeds: scene 1000+seed, trajectory 2000+seed, perturbation 3000+seed,
+    dropped returns 4000+seed.
+    """
+    poses = _street_trajectory(n_frames, spacing, 2000 + seed)
+    scene = _street_scene(1000 + seed, 0.0, (n_frames - 1) * spacing)
+    sensor = spherical_sensor(width, height, vfov_up_deg, vfov_down_deg)
+    drng = np.random.default_rng(4000 + seed)
+    chans = []
+    for k in range(n_frames):
+        c = render(scene, sensor, poses[k], 1.0, 80.0)
+        keep = drng.random((height, width)) >= drop
+        c = np.where(keep[..., None], c, 0.0).astype(np.float32)
+        if fp16_exact:
+            c = quantize_fp16(c)
+        chans.append(c)
+    pairs = []
+    for i in range(n_frames):
+        for j in range(i + 1, n_frames):
+            if np.linalg.norm(poses[i, :, 3] - poses[j, :, 3]) > max_pair_distance:
+                continue
+            if overlap_ratio(chans[i], chans[j], sensor, poses[i], poses[j], stride=7) > min_overlap:
+                pairs.append((i, j))
+    init = perturb_poses(poses, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    prm = default_params(w_depth=0.1, huber_delta=0.2, occ_abs=0.3, occ_rel=0.05, z_min=0.5,
+                         range_min=1.0, range_max=80.0)
+    if params:
+        prm.update(params)
+    return Workload(f"lidar-street-{n_frames}x{height}x{width}", [sensor],
+                    np.zeros(n_frames, dtype=np.int32), chans, poses, init,
+                    np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)
+
+
+def make_plane_shift(width: int = 48, height: int = 40, f: float = 40.0, depth: float = 2.0,
+                     shift_px: Tuple[int, int] = (3, 2), seed: int = 7) -> Workload:
+    """Two pinhole frames facing a fronto-parallel textured plane at constant
+    depth, the second translated so that the image moves by an integer number
+    of pixels: every pixel of frame 0 lands exactly on a pixel centre of
+    frame 1 with the same intensity, depth and normal."""
+    sensor = pinhole_sensor(width, height, f, width / 2.0, height / 2.0)
+    wall = Box(np.array([-50.0, -50.0, depth]), np.array([50.0, 50.0, depth + 1.0]),
+               albedo=1.0, tex_freq=4.0, tex_seed=seed, tex_contrast=0.9)
+    scene = Scene([wall])
+    poses = np.zeros((2, 3, 4))
+    poses[0] = IDENTITY_3x4
+    poses[1] = IDENTITY_3x4
+    poses[1, 0, 3] = shift_px[0] * depth / f
+    poses[1, 1, 3] = shift_px[1] * depth / f
+    chans = [quantize_fp16(render(scene, sensor, poses[k], 0.1, 100.0)) for k in range(2)]
+    return Workload("plane-shift", [sensor], np.zeros(2, dtype=np.int32), chans, poses,
+                    poses.copy(), np.array([[0, 1]], dtype=np.int32), default_params())

@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each pin returns an error measure; `PIN_TOL` holds the bar.  The pins are used
+twice: by test_oracle_pins.py on the oracle as committed, and by
+test_oracle_mutations.py on copies with a planted mistake, where at least one
+pin must fail.  Sources of truth:
+  - hand-derived closed forms of Eq. 2 / Eq. 3 (tests/golden/projection_closed_form.json);
+  - scipy's rotation and bilinear-interpolation routines and numpy's linear solver;
+  - central finite differences of the oracle's own residual and cost;
+  - invariants of the formulation: the 6-dim gauge null space of H (the
+    residual depends on X_i, X_j only through X_j^-1 X_i, Eq. 4), exact zero
+    error for integer-pixel shifts of a fronto-parallel plane.
+"""
+import json
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+PIN_TOL = {
+    "projection_golden": 1e-9,
+    "roundtrip": 1e-9,
+    "proj_jacobian_fd": 1e-6,
+    "boxplus": 1e-12,
+    "jacobian_fd_pinhole": 1e-6,
+    "jacobian_fd_spherical": 1e-6,
+    "ramp_grad_mode0": 1e-6,
+    "gauge": 1e-10,
+    "cost_gradient": 1e-5,
+    "plane_shift": 1e-9,
+    "single_channel": 1e-9,
+    "cholesky": 1e-10,
+}
+
+
+def _sensor_from(d):
+    from paper_2303_16878_gb300 import synth
+    if d["model"] == 0:
+        return synth.Sensor(0, d["width"], d["height"], d["fx"], d["fy"], d["cx"], d["cy"])
+    return synth.spherical_sensor(d["width"], d["height"], d["vfov_up_deg"], d["vfov_down_deg"])
+
+
+def pin_projection_golden(O, lib):
+    g = json.load(open(os.path.join(HERE, "golden", "projection_closed_form.json")))
+    err = 0.0
+    for key in ("pinhole", "spherical"):
+        s = _sensor_from(g[key]["sensor"])
+        for c in g[key]["cases"]:
+            uv = O.project(s, c["p"], lib=lib)
+            err = max(err, float(np.abs(uv - np.array(c["uv"])).max()))
+    return err
+
+
+def pin_roundtrip(O, lib):
+    """pi(pi^-1(u, d)) = u and the depth / range of pi^-1(u, d) is d."""
+    from paper_2303_16878_gb300 import synth
+    rng = np.random.default_rng(11)
+    err = 0.0
+    for s in (synth.pinhole_sensor(160, 120, 120.0, 80.0, 60.0), synth.spherical_sensor(1024, 64, 16.6, -16.6)):
+        for _ in range(200):
+            u = rng.uniform(0, s.width - 1)
+            v = rng.uniform(0, s.height - 1)
+            d = rng.uniform(0.5, 80.0)
+            p = O.unproject(s, u, v, d, lib=lib)
+            uv = O.project(s, p, lib=lib)
+            du = abs(uv[0] - u)
+            if s.model == 1:
+                du = min(du, abs(du - s.width))
+            dist = p[2] if s.model == 0 else float(np.linalg.norm(p))
+            err = max(err, du, abs(uv[1] - v), abs(dist - d) / d)
+    return err
+
+
+def pin_proj_jacobian_fd(O, lib):
+    from paper_2303_16878_gb300 import synth
+    rng = np.random.default_rng(12)
+    err = 0.0
+    for s in (synth.pinhole_sensor(160, 120, 120.0, 80.0, 60.0), synth.spherical_sensor(1024, 64, 16.6, -16.6)):
+        for _ in range(50):
+            p = rng.normal(0, 3, 3)
+            p[2] = abs(p[2]) + 1.0 if s.model == 0 else p[2] * 0.2
+            J = O.proj_jacobian(s, p, lib=lib)
+            h = 1e-6
+            Jf = np.zeros((2, 3))
+            for a in range(3):
+                d = np.zeros(3)
+                d[a] = h
+                Jf[:, a] = (O.project(s, p + d, lib=lib) - O.project(s, p - d, lib=lib)) / (2 * h)
+            err = max(err, float(np.abs(J - Jf).max() / np.abs(Jf).max()))
+    return err
+
+
+def pin_boxplus(O, lib):
+    """X [+] dx = X exp(dx): the 4x4 product of X with [R(dq) dt; 0 1], R(dq)
+    the rotation of the unit quaternion with imaginary part dq (scipy)."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(13)
+    err = 0.0
+    for _ in range(50):
+        X = np.zeros((3, 4))
+        X[:, :3] = Rotation.from_rotvec(rng.normal(0, 1, 3)).as_matrix()
+        X[:, 3] = rng.normal(0, 2, 3)
+        dx = np.concatenate([rng.normal(0, 0.5, 3), rng.normal(0, 0.2, 3)])
+        q = dx[3:]
+        qw = math.sqrt(1.0 - float(q @ q))
+        dR = Rotation.from_quat([q[0], q[1], q[2], qw]).as_matrix()
+        E = np.eye(4)
+        E[:3, :3] = dR
+        E[:3, 3] = dx[:3]
+        X4 = np.eye(4)
+        X4[:3] = X
+        ref = (X4 @ E)[:3]
+        err = max(err, float(np.abs(O.boxplus(X, dx, lib=lib) - ref).max()))
+    # X [+] 0 = X
+    err = max(err, float(np.abs(O.boxplus(X, np.zeros(6), lib=lib) - X).max()))
+    return err
+
+
+def _fd_point_jacobians(O, lib, w, params, n_points=300, h=1e-6, seed=0, pairs=((0, 1), (1, 2))):
+    rng = np.random.default_rng(seed)
+    s = w.sensors[0]
+    worst, used = 0.0, 0
+    for i, j in pairs:
+        pts, _ = O.frame_points(s, params, w.channels[i], lib=lib)
+        Xi, Xj = w.poses_init[i], w.poses_init[j]
+        for k in rng.permutation(len(pts))[:n_points]:
+            r = O.point_residual(s, params, w.channels[j], Xi, Xj, pts[k], lib=lib)
+            if not r["valid"] or r["flag"]:
+                continue
+            Jfi, Jfj, ok = np.zeros((5, 6)), np.zeros((5, 6)), True
+            for a in range(6):
+                d = np.zeros(6)
+                d[a] = h
+                ev = [O.point_residual(s, params, w.channels[j], O.boxplus(Xi, sg * d, lib=lib), Xj, pts[k], lib=lib)
+                      for sg in (1, -1)]
+                ev += [O.point_residual(s, params, w.channels[j], Xi, O.boxplus(Xj, sg * d, lib=lib), pts[k], lib=lib)
+                       for sg in (1, -1)]
+                if not all(e["valid"] for e in ev):
+                    ok = False
+                    break
+                Jfi[:, a] = (ev[0]["e"] - ev[1]["e"]) / (2 * h)
+                Jfj[:, a] = (ev[2]["e"] - ev[3]["e"]) / (2 * h)
+            if not ok:
+                continue
+            used += 1
+            scale = max(np.abs(Jfi).max(), np.abs(Jfj).max(), 1e-12)
+            worst = max(worst, float(np.abs(Jfi - r["Ji"]).max() / scale),
+                        float(np.abs(Jfj - r["Jj"]).max() / scale))
+    assert used >= 20, "too few usable points for the finite-difference check"
+    return worst
+
+
+def pin_jacobian_fd(O, lib, w):
+    """J_i, J_j (Supp.) against central differences of e under X [+] dx,
+    with the exact derivative of the bilinear interpolant (grad_mode 1)."""
+    params = dict(w.params, grad_mode=1)
+    return _fd_point_jacobians(O, lib, w, params)
+
+
+def ramp_workload(model=0):
+    """Two frames whose target channels are affine in the pixel coordinates
+    (intensity and depth ramps, constant unit normal): central differences
+    equal the exact gradient and bilinear interpolation is exact, so the
+    paper's image Jacobians (grad_mode 0) are the true derivatives."""
+    from paper_2303_16878_gb300 import synth
+    if model == 0:
+        s = synth.pinhole_sensor(64, 48, 50.0, 32.0, 24.0)
+    else:
+        s = synth.spherical_sensor(256, 32, 15.0, -15.0)
+    H, W = s.height, s.width
+    cols = np.arange(W)[None, :].astype(np.float64)
+    rows = np.arange(H)[:, None].astype(np.float64)
+    def img(g0, gc, gr, d0, dc, dr, n):
+        c = np.zeros((H, W, 5), dtype=np.float32)
+        c[..., 0] = g0 + gc * cols + gr * rows
+        c[..., 1] = d0 + dc * cols + dr * rows
+        c[..., 2:] = np.asarray(n, dtype=np.float32)
+        return c
+    # dyadic slopes and offsets keep every texel exactly affine in float32
+    if model == 0:
+        src = img(0.25, 2.0 ** -8, -2.0 ** -9, 2.0, 0.0, 0.0, (0.0, 0.0, -1.0))
+        tgt = img(0.3125, 2.0 ** -7, 2.0 ** -8, 2.125, 2.0 ** -9, 2.0 ** -10, (0.0, 0.0, -1.0))
+    else:
+        # columns wrap at the seam, where no ramp is affine: keep only the
+        # middle half of the azimuth range valid, far from the seam
+        src = img(0.25, 2.0 ** -10, 2.0 ** -7, 10.0, 2.0 ** -9, 2.0 ** -5, (-1.0, 0.0, 0.0))
+        tgt = img(0.3125, 2.0 ** -9, 2.0 ** -6, 10.25, 2.0 ** -8, 2.0 ** -4, (-1.0, 0.0, 0.0))
+        for c in (src, tgt):
+            c[:, : W // 4] = 0.0
+            c[:, 3 * W // 4:] = 0.0
+    X0 = synth.IDENTITY_3x4.copy()
+    X1 = synth.IDENTITY_3x4.copy()
+    X1[:, :3] = synth.rot_vec(np.array([0.01, -0.02, 0.015]))
+    X1[:, 3] = (0.03, -0.02, 0.04)
+    poses = np.stack([X0, X1])
+    params = synth.default_params(occ_abs=10.0, occ_rel=1.0, huber_delta=1e9, grad_mode=0)
+    return synth.Workload("ramp", [s], np.zeros(2, dtype=np.int32), [src, tgt], poses, poses.copy(),
+                          np.array([[0, 1]], dtype=np.int32), params)
+
+
+def pin_ramp_grad_mode0(O, lib):
+    worst = 0.0
+    for model in (0, 1):
+        w = ramp_workload(model)
+        worst = max(worst, _fd_point_jacobians(O, lib, w, w.params, n_points=200, pairs=((0, 1),)))
+    return worst
+
+
+def gauge_directions(poses):
+    """The six infinitesimal global motions G = exp(eps xi) applied as
+    X_k -> G X_k, written in each frame's [dt, dq] coordinates:
+    dt_k = R_k^T (rho + phi x t_k), dq_k = R_k^T phi / 2 (R(dq) ~ I + 2 [dq]x)."""
+    V = []
+    for xi in np.eye(6):
+        rho, phi = xi[:3], xi[3:]
+        v = []
+        for X in poses:
+            R, t = X[:, :3], X[:, 3]
+            v.append(np.concatenate([R.T @ (rho + np.cross(phi, t)), 0.5 * R.T @ phi]))
+        V.append(np.concatenate(v))
+    return np.stack(V, axis=1)
+
+
+def pin_gauge(O, lib, w):
+    """H V = 0 and b^T V = 0 for the gauge directions V (either grad mode)."""
+    worst = 0.0
+    for gm in (0, 1):
+        params = dict(w.params, grad_mode=gm)
+        r = O.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, params, lib=lib)
+        V = gauge_directions(w.poses_init)
+        H, b = r["H"], r["b"]
+        worst = max(worst, float(np.linalg.norm(H @ V) / (np.linalg.norm(H) * np.linalg.norm(V))),
+                    float(np.linalg.norm(b @ V) / (np.linalg.norm(b) * np.linalg.norm(V))))
+    return worst
+
+
+def pin_cost_gradient(O, lib, w):
+    """dF / d dx_k (central differences of Eq. 6 under X_k [+] dx) equals 2 b_k
+    (grad_mode 1, non-unit Omega, a Huber delta that some residuals exceed)."""
+    params = dict(w.params, grad_mode=1, w_depth=0.5, w_normal=0.3, huber_delta=0.05)
+    s = w.sensors[0]
+    r = O.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, params, lib=lib)
+    b = r["b"]
+    worst = 0.0
+    for k in range(1, w.n_frames):
+        for a in range(6):
+            done = False
+            # small steps: the bilinear interpolant has kinks at cell edges, and
+            # a point crossing one within +-h biases the difference by O(h)
+            for h in (2e-8, 1e-8, 5e-9):
+                Fs, masks = [], []
+                for sg in (1, -1):
+                    d = np.zeros(6)
+                    d[a] = sg * h
+                    poses = w.poses_init.copy()
+                    poses[k] = O.boxplus(poses[k], d, lib=lib)
+                    F, mk = 0.0, []
+                    for (i, j) in w.pairs.tolist():
+                        if k not in (i, j):
+                            continue
+                        pr = O.linearize_pair(s, params, w.channels[i], w.channels[j], poses[i], poses[j], lib=lib)
+                        F += pr["cost"]
+                        mk.append(pr["mask"])
+                    Fs.append(F)
+                    masks.append(mk)
+                if all(np.array_equal(x, y) for x, y in zip(masks[0], masks[1])):
+                    g = (Fs[0] - Fs[1]) / (2 * h)
+                    worst = max(worst, abs(g - 2 * b[6 * k + a]) / (np.abs(2 * b[6 * k:6 * k + 6]).max() + 1e-30))
+                    done = True
+                    break
+            assert done, "mask changed under every finite-difference step"
+    return worst
+
+
+def pin_plane_shift(O, lib):
+    """Integer-pixel shift of a fronto-parallel plane: every residual is 0."""
+    from paper_2303_16878_gb300 import synth
+    w = synth.make_plane_shift()
+    s = w.sensors[0]
+    pts, _ = O.frame_points(s, w.params, w.channels[0], lib=lib)
+    worst, used = 0.0, 0
+    for k in range(0, len(pts), 3):
+        r = O.point_residual(s, w.params, w.channels[1], w.poses_gt[0], w.poses_gt[1], pts[k], lib=lib)
+        if r["valid"]:
+            used += 1
+            worst = max(worst, float(np.abs(r["e"]).max()))
+    assert used > 100
+    return worst
+
+
+def pin_single_channel(O, lib):
+    """With Omega = diag(1, 0, 0, 0, 0), rho = identity and no occlusion test,
+    F equals the classic photometric error of Eq. 5 summed by brute force:
+    u' from Eq. 4 composed as X_j^-1 X_i, I_j^g(u') by scipy's order-1 spline
+    (bilinear), over the source pixels whose samples are usable."""
+    from scipy.ndimage import map_coordinates
+    from paper_2303_16878_gb300 import synth
+    w = synth.make_plane_shift(shift_px=(0, 0))
+    X1 = synth.IDENTITY_3x4.copy()
+    X1[:, :3] = synth.rot_vec(np.array([0.004, -0.006, 0.01]))
+    X1[:, 3] = (0.0731, -0.0417, 0.05)
+    poses = np.stack([synth.IDENTITY_3x4, X1])
+    s = w.sensors[0]
+    params = dict(w.params, w_depth=0.0, w_normal=0.0, huber_delta=1e12, occ_abs=1e6, occ_rel=0.0)
+    r = O.linearize(w.sensors, w.frame_sensor, w.channels, poses, w.pairs, params, want_system=False, lib=lib)
+    src, tgt = w.channels[0].astype(np.float64), w.channels[1].astype(np.float64)
+    A = np.eye(4)
+    A[:3] = poses[1]
+    Bm = np.eye(4)
+    Bm[:3] = poses[0]
+    Xji = np.linalg.inv(A) @ Bm
+    total, n = 0.0, 0
+    for row in range(s.height):
+        for col in range(s.width):
+            d = src[row, col, 1]
+            if d <= 0:
+                continue
+            p = np.array([(col - s.cx) / s.fx * d, (row - s.cy) / s.fy * d, d, 1.0])
+            q = Xji @ p
+            u, v = s.fx * q[0] / q[2] + s.cx, s.fy * q[1] / q[2] + s.cy
+            if not (1 <= u < s.width - 2 and 1 <= v < s.height - 2):
+                continue
+            gj = map_coordinates(tgt[..., 0], [[v], [u]], order=1)[0]
+            total += (src[row, col, 0] - gj) ** 2
+            n += 1
+    assert n == r["count"], (n, r["count"])
+    return abs(total - r["cost"]) / max(total, 1e-30)
+
+
+def pin_cholesky(O, lib):
+    rng = np.random.default_rng(14)
+    worst = 0.0
+    for n in (1, 5, 42, 120):
+        B = rng.normal(size=(n, n))
+        A = B @ B.T + n * np.eye(n)
+        rhs = rng.normal(size=n)
+        x = O.cholesky_solve(A, rhs, lib=lib)
+        ref = np.linalg.solve(A, rhs)
+        worst = max(worst, float(np.abs(x - ref).max() / np.abs(ref).max()))
+    return worst
+
+
+def all_pins(O, lib, room, street):
+    """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
+    return {
+        "projection_golden": pin_projection_golden(O, lib),
+        "roundtrip": pin_roundtrip(O, lib),
+        "proj_jacobian_fd": pin_proj_jacobian_fd(O, lib),
+        "boxplus": pin_boxplus(O, lib),
+        "jacobian_fd_pinhole": pin_jacobian_fd(O, lib, room),
+        "jacobian_fd_spherical": pin_jacobian_fd(O, lib, street),
+        "ramp_grad_mode0": pin_ramp_grad_mode0(O, lib),
+        "gauge": max(pin_gauge(O, lib, room), pin_gauge(O, lib, street)),
+        "cost_gradient": pin_cost_gradient(O, lib, room),
+        "plane_shift": pin_plane_shift(O, lib),
+        "single_channel": pin_single_channel(O, lib),
+        "cholesky": pin_cholesky(O, lib),
+    }

@@ -1,0 +1,64 @@
+"""Plant one plausible mistake at a time in a private copy of the oracle
+source, compile it, and check that at least one pin catches it (CPU only)."""
+import os
+
+import pytest
+
+import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "pba_oracle.c")
+
+MUTATIONS = {
+    "rotation_jacobian_skew_sign": ("acc += M[3 * r + k] * (-2.0 * Spu[3 * k + c]);",
+                                    "acc += M[3 * r + k] * (2.0 * Spu[3 * k + c]);"),
+    "target_translation_jacobian_sign": ("dPj[6 * r + c] = -RoT[3 * r + c];", "dPj[6 * r + c] = RoT[3 * r + c];"),
+    "normal_cue_uses_Rj_not_RjT": ("mat3_vec(RjT, Rn, RjTRn);", "mat3_vec(Rj, Rn, RjTRn);"),
+    "image_gradient_axes_swapped": ("gu[ci] += w[t] * 0.5 * ((double)Ir[ci] - (double)Il[ci]);",
+                                    "gu[ci] += w[t] * 0.5 * ((double)Id[ci] - (double)Iu[ci]);"),
+    "huber_weight_dropped": ("*w = prm->huber_delta / chi;", "*w = 1.0;"),
+    "omega_dropped_from_b": ("s_b += J[r][a] * om[r] * e[r];", "s_b += J[r][a] * e[r];"),
+    "depth_cue_jacobian_dropped": ("map_i += dz[k] * dPi[6 * k + col];", "map_i += 0.0 * dPi[6 * k + col];"),
+    "cholesky_off_by_one": ("for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];",
+                            "for (int k = 1; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];"),
+    "spherical_jacobian_transposed": ("for (int k = 0; k < 3; ++k) acc += K12[3 * r + k] * D[3 * k + c];",
+                                      "for (int k = 0; k < 3; ++k) acc += K12[3 * r + k] * D[3 * c + k];"),
+    "boxplus_translation_not_rotated": ("mat3_vec(R, dx, Rdt);", "Rdt[0] = dx[0]; Rdt[1] = dx[1]; Rdt[2] = dx[2];"),
+    "pinhole_principal_point_swapped": ("double vy = s->fy * p[1] + s->cy * p[2];\n        double vz = p[2];\n        uv[0]",
+                                        "double vy = s->fy * p[1] + s->cx * p[2];\n        double vz = p[2];\n        uv[0]"),
+    "assembly_block_transposed": ("+= H12[12 * (6 * ba + a) + 6 * bb + c];", "+= H12[12 * (6 * bb + a) + 6 * ba + c];"),
+    "bilinear_weight_swapped": ("const double w[4] = {(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b};",
+                                "const double w[4] = {(1 - a) * (1 - b), (1 - a) * b, a * (1 - b), a * b};"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
+    before, after = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / "pba_oracle_mutated.c"
+    mutated.write_text(src.replace(before, after))
+    lib = oracle_lib.load(oracle_lib.build(force=True, src=str(mutated), out=str(tmp_path / "libmut.so")))
+    failed = []
+    for pin, fn in [("projection_golden", lambda: P.pin_projection_golden(oracle_lib, lib)),
+                    ("roundtrip", lambda: P.pin_roundtrip(oracle_lib, lib)),
+                    ("proj_jacobian_fd", lambda: P.pin_proj_jacobian_fd(oracle_lib, lib)),
+                    ("boxplus", lambda: P.pin_boxplus(oracle_lib, lib)),
+                    ("jacobian_fd_pinhole", lambda: P.pin_jacobian_fd(oracle_lib, lib, room3)),
+                    ("jacobian_fd_spherical", lambda: P.pin_jacobian_fd(oracle_lib, lib, street3)),
+                    ("ramp_grad_mode0", lambda: P.pin_ramp_grad_mode0(oracle_lib, lib)),
+                    ("gauge", lambda: max(P.pin_gauge(oracle_lib, lib, room3), P.pin_gauge(oracle_lib, lib, street3))),
+                    ("cost_gradient", lambda: P.pin_cost_gradient(oracle_lib, lib, room3)),
+                    ("plane_shift", lambda: P.pin_plane_shift(oracle_lib, lib)),
+                    ("single_channel", lambda: P.pin_single_channel(oracle_lib, lib)),
+                    ("cholesky", lambda: P.pin_cholesky(oracle_lib, lib))]:
+        try:
+            err = fn()
+        except (AssertionError, ValueError, ArithmeticError, Exception):
+            failed.append(pin)
+            continue
+        if not err < P.PIN_TOL[pin]:
+            failed.append(pin)
+        if failed:
+            break
+    assert failed, f"no pin caught the planted mistake {name}"

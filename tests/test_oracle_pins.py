@@ -1,0 +1,111 @@
+"""The FP64 oracle against closed forms, library routines, finite differences
+and invariants of the formulation (CPU only)."""
+import numpy as np
+import pytest
+
+import oracle_pins as P
+
+
+def test_projection_closed_form(oracle_lib):
+    assert P.pin_projection_golden(oracle_lib, oracle_lib.load()) < P.PIN_TOL["projection_golden"]
+
+
+def test_unproject_project_roundtrip(oracle_lib):
+    assert P.pin_roundtrip(oracle_lib, oracle_lib.load()) < P.PIN_TOL["roundtrip"]
+
+
+def test_projection_jacobian_fd(oracle_lib):
+    assert P.pin_proj_jacobian_fd(oracle_lib, oracle_lib.load()) < P.PIN_TOL["proj_jacobian_fd"]
+
+
+def test_boxplus_is_right_multiplication_by_exp(oracle_lib):
+    assert P.pin_boxplus(oracle_lib, oracle_lib.load()) < P.PIN_TOL["boxplus"]
+
+
+def test_point_jacobians_fd_pinhole(oracle_lib, room3):
+    assert P.pin_jacobian_fd(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["jacobian_fd_pinhole"]
+
+
+def test_point_jacobians_fd_spherical(oracle_lib, street3):
+    assert P.pin_jacobian_fd(oracle_lib, oracle_lib.load(), street3) < P.PIN_TOL["jacobian_fd_spherical"]
+
+
+def test_paper_image_jacobians_exact_on_ramps(oracle_lib):
+    assert P.pin_ramp_grad_mode0(oracle_lib, oracle_lib.load()) < P.PIN_TOL["ramp_grad_mode0"]
+
+
+@pytest.mark.parametrize("which", ["room3", "street3"])
+def test_gauge_null_space(oracle_lib, which, request):
+    w = request.getfixturevalue(which)
+    assert P.pin_gauge(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["gauge"]
+
+
+def test_cost_gradient_is_twice_b(oracle_lib, room3):
+    assert P.pin_cost_gradient(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["cost_gradient"]
+
+
+def test_integer_shift_of_plane_gives_zero_error(oracle_lib):
+    assert P.pin_plane_shift(oracle_lib, oracle_lib.load()) < P.PIN_TOL["plane_shift"]
+
+
+def test_single_channel_reduces_to_classic_photometric_error(oracle_lib):
+    assert P.pin_single_channel(oracle_lib, oracle_lib.load()) < P.PIN_TOL["single_channel"]
+
+
+def test_cholesky_matches_numpy_solve(oracle_lib):
+    assert P.pin_cholesky(oracle_lib, oracle_lib.load()) < P.PIN_TOL["cholesky"]
+
+
+def test_system_symmetric_psd_rank(oracle_lib, room8):
+    r = oracle_lib.linearize(room8.sensors, room8.frame_sensor, room8.channels, room8.poses_init,
+                             room8.pairs, room8.params)
+    H = r["H"]
+    assert np.array_equal(H, H.T)
+    ev = np.linalg.eigvalsh(H)
+    assert ev[0] >= -1e-12 * ev[-1]
+    assert np.count_nonzero(ev > 1e-9 * ev[-1]) == H.shape[0] - 6
+
+
+def test_self_pair_has_zero_error(oracle_lib, room3):
+    """Frame i against itself at the same pose: pbar = p_u and u' = u."""
+    s = room3.sensors[0]
+    pr = oracle_lib.linearize_pair(s, room3.params, room3.channels[0], room3.channels[0],
+                                   room3.poses_gt[0], room3.poses_gt[0])
+    assert pr["count"] > 0.9 * pr["n_points"]
+    assert pr["cost"] < 1e-18
+    assert np.abs(pr["b"]).max() < 1e-9
+
+
+def test_solve_step_fixes_gauge_and_solves_damped_system(oracle_lib, room8):
+    r = oracle_lib.linearize(room8.sensors, room8.frame_sensor, room8.channels, room8.poses_init,
+                             room8.pairs, room8.params)
+    lam = oracle_lib.initial_lambda(r["H"])
+    dx, ok = oracle_lib.solve_step(r["H"], r["b"], lam)
+    assert ok
+    assert np.all(dx[:6] == 0)
+    A = r["H"][6:, 6:] + lam * np.eye(r["H"].shape[0] - 6)
+    np.testing.assert_allclose(A @ dx[6:], -r["b"][6:], rtol=0, atol=1e-9 * np.abs(r["b"]).max())
+
+
+def test_lm_converges_towards_ground_truth(oracle_lib):
+    """RGB-D room at 80x60, 4 frames, 2 cm / 1 deg init noise: every accepted
+    step lowers F, and the poses approach ground truth to the accuracy that
+    bilinear interpolation of the renders allows."""
+    from conftest import workload
+    w = workload("room", n_frames=4, width=80, height=60, f=60.0)
+    poses, lam = w.poses_init.copy(), None
+    costs = []
+    for _ in range(12):
+        o = oracle_lib.lm_iteration(w, poses, lam)
+        if o["accepted"]:
+            assert o["new_cost"] < o["cost"]
+        poses, lam = o["poses"], o["lam"]
+        costs.append(o["cost"])
+    t_err0 = max(np.linalg.norm(w.poses_init[k][:, 3] - w.poses_gt[k][:, 3]) for k in range(4))
+    r_err0 = max(np.linalg.norm(w.poses_init[k][:, :3].T @ w.poses_gt[k][:, :3] - np.eye(3)) for k in range(4))
+    t_err = max(np.linalg.norm(poses[k][:, 3] - w.poses_gt[k][:, 3]) for k in range(4))
+    r_err = max(np.linalg.norm(poses[k][:, :3].T @ w.poses_gt[k][:, :3] - np.eye(3)) for k in range(4))
+    assert costs[-1] < 0.1 * costs[0]
+    # at 80x60 (1 deg pixels) interpolation bias keeps the minimum ~1 cm / ~0.3 deg off ground truth
+    assert t_err < 0.25 * t_err0 and t_err < 0.012
+    assert r_err < 0.15 * r_err0
