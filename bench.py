@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of one Levenberg-Marquardt iteration of photometric bundle
+adjustment (linearise every pair, reduce, assemble, damped FP64 Cholesky
+solve, box-plus update, cost re-evaluation, accept/reject) on one GB300.
+
+Default workload: LiDAR spherical-projection BA, 50 frames of 64 x 1024
+(vertical FOV -16.6..+16.6 deg) along a synthetic street, every pair with more
+than 30% overlap, FP16 texels / FP32 residuals / FP64 solve.
+
+Metric: residuals per second (valid pixel-point residuals linearised per
+iteration / device time of the iteration) and ms per iteration.  Every timed
+step restarts from the same initial poses, so all steps do identical work;
+L2 is flushed (256 MiB write) before each step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the problem
+on its own GPU (the path has no exchange step); value = all ranks' residuals /
+the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
+host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "residuals/sec and ms per GN iteration, batched vs plain GPU path at stated error"
+UNIT = "residuals/s"
+WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, "
+            "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64 solve")
+
+# Algorithmic FP32 work of the linearisation kernel (derivation in the design doc):
+# per processed point (transform + spherical projection + bounds) and per
+# valid residual (sampling, residual, Huber, 5 x 6 Jacobian, 6 x 6 accumulation).
+FLOP_PER_POINT_SPHERICAL = 76
+FLOP_PER_RESIDUAL_FULL = 720
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["street", "room"], default="street")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-pair path")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2303_16878_gb300 import synth
+    if name == "room":
+        return synth.make_rgbd_room()
+    return synth.make_lidar_street()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]) if f[3] not in ("[N/A]", "") else 0.0,
+                                 hw=f[5], hw_th=f[6], sw_th=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hw_th", "hw_thermal_slowdown"),
+                              ("sw_th", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [r["sm"] for r in rows if r["power"] > 0.25 * max(x["power"] for x in rows)] or [r["sm"] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, device):
+    import torch
+    import paper_2303_16878_gb300 as pba
+
+    w = make_workload(args.workload)
+    # a dedicated stream: the library enqueues on it and the events below are recorded on it
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    prob = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream)
+    init = np.ascontiguousarray(w.poses_init.reshape(-1, 12))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    n_points_total = sum(prob.frame_points(int(i)) for i, _ in w.pairs)
+
+    def one_step(p):
+        p.set_poses(init)
+        p.set_lambda(None)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.iterate_async(1)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), p.get_stats()
+
+    for _ in range(args.warmup):
+        one_step(prob)
+    launches = prob.iteration_launches()
+
+    # timed region: K identical iterations
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device.index if device.index is not None else 0)
+    wall0 = time.perf_counter()
+    ms, nvalid, stats = [], [], None
+    for _ in range(args.steps):
+        t, stats = one_step(prob)
+        ms.append(t)
+        nvalid.append(stats["n_valid"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = float(sum(ms))
+    res_local = float(sum(nvalid))
+    if world > 1:
+        t = torch.tensor([total_ms, res_local], dtype=torch.float64, device=device)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, res_all = float(tmax[0]), float(t[1])
+    else:
+        res_all = res_local
+    value = res_all / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # per-phase device times (same stream, same flush), for the roofline
+    phases = {}
+    for _ in range(args.steps):
+        prob.set_poses(init)
+        prob.set_lambda(None)
+        flush.zero_()
+        _, ph = prob.iterate_timed()
+        for k, v in ph.items():
+            phases.setdefault(k, []).append(v)
+    phase_ms = {k: float(np.mean(v)) for k, v in phases.items()}
+
+    out = dict(value=value, ms_per_step=ms_per_step, n_valid=int(nvalid[-1]), launches=launches, clocks=clk,
+               phase_ms=phase_ms, wall_s=wall, n_points=int(n_points_total), n_pairs=int(len(w.pairs)),
+               stats=stats)
+
+    # plain per-pair path on the same workload
+    if not args.no_plain:
+        plain = pba.problem_from_workload(w, path=pba.PBA_PATH_PLAIN, texel=pba.PBA_TEXEL_F32, stream=stream)
+        for _ in range(max(1, args.warmup)):
+            one_step(plain)
+        pms = []
+        for _ in range(max(3, args.steps // 2)):
+            t, _ = one_step(plain)
+            pms.append(t)
+        plain.close()
+        out["plain_ms_per_step"] = float(np.mean(pms))
+
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        chans = torch.from_numpy(w.channels_array()).pin_memory()
+        poses_h = torch.from_numpy(init.copy()).pin_memory()
+        out_h = torch.empty_like(poses_h).pin_memory()
+        h2d = chans.numel() * 4 + poses_h.numel() * 8
+        d2h = out_h.numel() * 8 + 48
+        walls, ev = [], 0
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            prob.upload_frames(0, chans)
+            prob.set_poses(poses_h)
+            prob.set_lambda(None)
+            prob.iterate_async(1)
+            st = prob.get_stats()
+            prob._check(prob._lib.pba_get_poses(prob._h, out_h.data_ptr()), "get_poses")
+            t1 = time.perf_counter()
+            if k >= args.warmup:
+                walls.append(t1 - t0)
+                ev += st["n_valid"]
+        e2e_local = ev / sum(walls)
+        if world > 1:
+            t = torch.tensor([sum(walls), float(ev)], dtype=torch.float64, device=device)
+            tmax = t.clone()
+            torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+            e2e_local = float(t[1]) / float(tmax[0])
+        out["e2e"] = {"value": e2e_local, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": 1e3 * sum(walls) / len(walls)}
+    prob.close()
+    return out, w
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, seconds, seed=0):
+    """Time the FP64 oracle's LM iteration work (full linearisation + cost
+    re-evaluation) on a seeded sample of pairs of the same workload, one core."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(w.pairs))
+    s = w.sensors[0]
+    done_res, elapsed, used = 0, 0.0, 0
+    for q in order:
+        i, j = w.pairs[q]
+        t0 = time.perf_counter()
+        r = oracle.linearize_pair(s, w.params, w.channels[i], w.channels[j], w.poses_init[i], w.poses_init[j])
+        oracle.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs[q:q + 1], w.params,
+                         want_system=False)
+        elapsed += time.perf_counter() - t0
+        done_res += r["count"]
+        used += 1
+        if elapsed >= seconds:
+            break
+    return dict(value=done_res / elapsed, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{used} of {len(w.pairs)} pairs (seeded), full linearisation + cost re-evaluation, "
+                       f"{done_res} residuals in {elapsed:.1f} s, single-threaded FP64 C",
+                seconds=elapsed, pairs=used)
+
+
+def run_reference(args):
+    w = make_workload(args.workload)
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(w, per_step, seed=k)
+        if k >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: seeded pairs of the workload until {per_step:.0f} s of "
+                                       f"single-threaded FP64 oracle work (full + cost linearisation)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the GPU path has no CPU fallback)")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+    out, w = run_ours(args, rank, world, device)
+    if rank == 0:
+        ph = out["phase_ms"]
+        lin_ms = ph["linearize"]
+        n_valid = out["n_valid"]
+        flops = n_valid * FLOP_PER_RESIDUAL_FULL + out["n_points"] * FLOP_PER_POINT_SPHERICAL
+        import torch
+        props = torch.cuda.get_device_properties(device)
+        sm_max = (out["clocks"] or {}).get("sm_max_mhz") or 2070.0
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (lin_ms / 1e3) / 1e12
+        line = {
+            "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames": w.n_frames, "pairs": out["n_pairs"],
+                       "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
+                       "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_linearize<f16, full>",
+                         "kernel_ms": lin_ms},
+            "phase_ms": ph,
+            "gpu_launches": out["launches"] * args.steps,
+            "clocks": out["clocks"],
+        }
+        if "plain_ms_per_step" in out:
+            line["plain_ms_per_step"] = out["plain_ms_per_step"]
+            line["speedup_vs_plain"] = out["plain_ms_per_step"] / out["ms_per_step"]
+        if "e2e" in out:
+            line["e2e"] = out["e2e"]
+        if not args.no_cpu:
+            cb = oracle_sample(w, args.cpu_seconds)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * pba.h -- C ABI of the GB300 photometric bundle-adjustment library (libpba.so).
+ *
+ * The library linearises the multi-cue photometric error of Di Giammarino et
+ * al., "Photometric LiDAR and RGB-D Bundle Adjustment" (Eq. 6 with the offset
+ * form of the supplementary material), assembles the Gauss-Newton system
+ * H dx = -b over all sensor poses, and takes damped (Levenberg-Marquardt)
+ * steps X_k <- X_k [+] dx_k, all on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - Status: every int-returning call returns PBA_OK (0) or a negative
+ *     PBA_E* code and never throws; pba_last_error() gives a message.
+ *   - Ownership: input buffers are borrowed for the duration of the call
+ *     only (the library copies what it keeps); outputs are caller-allocated.
+ *     The problem object owns all device memory it allocates.
+ *   - Host / device pointers: arguments documented "host or device" take an
+ *     `is_device` flag; 1 means a pointer into the current CUDA device's
+ *     global memory (e.g. a torch tensor's data_ptr()).
+ *   - Streams: all device work is ordered on the stream given at creation
+ *     (or pba_set_stream); calls that return results synchronise that stream.
+ *   - Poses are 3x4 row-major [R | t] (Eq. 1) mapping the platform frame into
+ *     the world frame, in double precision, frame k at offset 12 k.
+ *   - Pose perturbations dx_k = [dt, dq] (Supp.): dt a translation, dq the
+ *     imaginary part of a unit quaternion; X [+] dx = X exp(dx).
+ *   - Not thread-safe per problem; distinct problems may be used from
+ *     distinct threads.
+ */
+#ifndef PBA_H
+#define PBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PBA_OK 0
+#define PBA_EINVAL (-1)     /* bad argument (null pointer, size, index, sensor mismatch) */
+#define PBA_ENOMEM (-2)     /* device or host allocation failed */
+#define PBA_ECUDA (-3)      /* a CUDA call failed; the message names it */
+#define PBA_ENOTPD (-4)     /* damped system not positive definite; the step was rejected */
+#define PBA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define PBA_ENOTREADY (-6)  /* a required input (frames, poses, pairs) was not set */
+
+/* projection models, Sec. III */
+#define PBA_PINHOLE 0       /* pi_p(p) = phi(K p), Eq. 2; d is the depth */
+#define PBA_SPHERICAL 1     /* pi_s(p) = K_[1,2] psi(p), Eq. 3; d is the range */
+
+/* linearisation paths */
+#define PBA_PATH_BATCHED 0  /* all pairs in one persistent launch, 6x6 reduced accumulation */
+#define PBA_PATH_PLAIN 1    /* one launch per pair, full 12x12 accumulation, FP32 atomics */
+
+/* storage of the target-image channels used for sampling (depth always FP32) */
+#define PBA_TEXEL_F32 0
+#define PBA_TEXEL_F16 1     /* intensity and normal in binary16 (round to nearest even) */
+
+/* image-gradient modes (Supp., image Jacobians) */
+#define PBA_GRAD_CENTRAL 0  /* central differences at pixels, bilinearly interpolated (paper) */
+#define PBA_GRAD_BILINEAR 1 /* exact derivative of the bilinear interpolant */
+
+typedef struct pba_problem pba_problem;
+
+/* One sensor: intrinsics K (Eq. 2; for the spherical model f_x, f_y are the
+ * azimuth / elevation resolutions in pixels per radian and c_x, c_y their
+ * offsets, Eq. 3) and the extrinsic offset X_o = [R_o | t_o] (row-major 3x4)
+ * placing the sensor on the platform (Supp., p_u = R_o pi^-1(u, d) + t_o). */
+typedef struct {
+    int32_t model;              /* PBA_PINHOLE or PBA_SPHERICAL */
+    int32_t width, height;      /* image size in pixels; >= 4 each */
+    int32_t reserved;           /* 0 */
+    double fx, fy, cx, cy;
+    double extrinsic[12];
+} pba_sensor;
+
+/* Problem configuration.  A pixel is valid iff range_min <= d <= range_max,
+ * d > 0 and |n| > 0.5.  The residual of a pixel-point is the stacked
+ * five-channel error e = (g, d, n_x, n_y, n_z) of the Supp. error term with
+ * Omega = diag(w_int, w_depth, w_normal, w_normal, w_normal); the Huber
+ * function acts on chi = sqrt(e^T Omega e) with threshold huber_delta.
+ * A sample is rejected (occlusion suppression, Sec. IV-C) when
+ * |zeta^d - I^d(u')| > occ_abs + occ_rel * zeta^d or the sampled normal has
+ * norm < 0.5, and when pbar_z (pinhole) or |pbar| (spherical) <= z_min. */
+typedef struct {
+    int32_t n_frames;           /* N >= 1 */
+    int32_t n_sensors;          /* >= 1 */
+    const pba_sensor* sensors;  /* n_sensors entries, host memory */
+    const int32_t* frame_sensor;/* n_frames entries (host) or NULL: every frame uses sensor 0 */
+    double w_int, w_depth, w_normal;
+    double huber_delta;         /* > 0 */
+    double occ_abs, occ_rel;
+    double z_min;
+    double range_min, range_max;
+    int32_t grad_mode;          /* PBA_GRAD_CENTRAL or PBA_GRAD_BILINEAR */
+    int32_t texel_precision;    /* PBA_TEXEL_F32 or PBA_TEXEL_F16 (batched path only) */
+    int32_t path;               /* PBA_PATH_BATCHED or PBA_PATH_PLAIN */
+    int32_t reserved;           /* 0 */
+} pba_config;
+
+/* Outcome of one Levenberg-Marquardt iteration. */
+typedef struct {
+    double cost;        /* F (Eq. 6) at the poses the iteration started from */
+    double new_cost;    /* F at the candidate poses X [+] dx */
+    double lambda_used; /* damping of the solved system (H_ff + lambda I) */
+    double lambda_next; /* lambda / 10 after an accepted step, lambda * 10 otherwise */
+    int64_t n_valid;    /* residuals (valid pixel-points over all pairs) linearised */
+    int32_t accepted;   /* 1 when new_cost < cost and the poses were updated */
+    int32_t status;     /* PBA_OK, or PBA_ENOTPD when the Cholesky met a non-positive pivot */
+} pba_iter_stats;
+
+/* Create a problem on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates its own non-blocking stream).
+ * Allocates every device buffer whose size the configuration fixes.
+ * Errors: PBA_EINVAL (bad config), PBA_ENOMEM, PBA_ECUDA. */
+int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out);
+
+/* Free the problem and its device memory (synchronises its stream). NULL is a no-op. */
+void pba_destroy(pba_problem* p);
+
+/* Message of the last failed call on p (static text when p is NULL). */
+const char* pba_last_error(const pba_problem* p);
+
+/* Order all further device work on cuda_stream (NULL: the problem's own stream). */
+int pba_set_stream(pba_problem* p, void* cuda_stream);
+
+/* Upload the five-channel cue images (Sec. IV-A) of frames first..first+count-1
+ * and build their pixel-point clouds and sampling texels.  channels holds
+ * count images back to back, each height x width x 5 float32 (row-major,
+ * channel fastest: g, d, n_x, n_y, n_z; normals in the sensor frame), with the
+ * frame's sensor size; host or device memory.  All frames of one call must
+ * use sensors of the same size.  Errors: PBA_EINVAL, PBA_ECUDA. */
+int pba_upload_frames(pba_problem* p, int first, int count, const float* channels, int is_device);
+
+/* Number of valid pixel-points of a frame (after its upload). */
+int pba_frame_points(pba_problem* p, int frame, int32_t* n_points);
+
+/* Set all N poses (N x 12 doubles, host or device). */
+int pba_set_poses(pba_problem* p, const double* poses, int is_device);
+
+/* Read all N poses into host memory (N x 12 doubles); synchronises. */
+int pba_get_poses(pba_problem* p, double* poses);
+
+/* Set the directed pairs (source i, target j), m x 2 int32 in host memory,
+ * Sec. IV-B.  Both frames must use the same sensor; i == j is allowed.
+ * Requires every frame named to have been uploaded. */
+int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m);
+
+/* Linearise all pairs at the current poses: builds H (6N x 6N, gauge not
+ * fixed) and b (6N) on the device and returns the total cost F (Eq. 6) and
+ * the number of valid residuals; synchronises.  Either output may be NULL. */
+int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
+
+/* Copy the last linearisation's H (6N x 6N row-major) and b (6N) to host
+ * memory; either may be NULL.  Frame k owns rows and columns 6k..6k+5. */
+int pba_get_system(pba_problem* p, double* H, double* b);
+
+/* Copy the last linearisation's per-pair results to host memory: pair_H
+ * (m x 12 x 12: rows/cols 0-5 frame i, 6-11 frame j), pair_b (m x 12),
+ * pair_cost (m), pair_count (m).  Any may be NULL. */
+int pba_get_pair_system(pba_problem* p, double* pair_H, double* pair_b, double* pair_cost,
+                        int64_t* pair_count);
+
+/* Enable (1) or disable (0) export of the valid-residual mask by later
+ * linearisations (batched path only). */
+int pba_set_mask_export(pba_problem* p, int enable);
+
+/* Copy the valid-residual mask of one pair from the last linearisation with
+ * mask export on: bit k % 32 of word k / 32 is set when the k-th pixel-point
+ * (raster order) of the source frame gave a valid residual.  n_words must be
+ * >= ceil(P_i / 32).  Errors: PBA_EINVAL, PBA_ENOTREADY (no mask exported). */
+int pba_get_mask(pba_problem* p, int pair, uint32_t* bits, int n_words);
+
+/* One damped step from the last linearisation with the given lambda >= 0:
+ * solve (H_ff + lambda I) dx_f = -b_f with frame 0 held fixed (gauge),
+ * evaluate F at X [+] dx, keep the candidate when F decreased.  Fills stats
+ * (may be NULL); synchronises.  Returns PBA_OK even when the step is
+ * rejected; stats->status reports PBA_ENOTPD. */
+int pba_solve_step(pba_problem* p, double lambda, pba_iter_stats* stats);
+
+/* Damping used by pba_iterate: lambda >= 0 sets it, lambda < 0 resets it to
+ * automatic (1e-4 times the largest diagonal entry of H_ff on the next
+ * iteration).  The schedule then divides by 10 on acceptance and multiplies
+ * by 10 on rejection, on the device. */
+int pba_set_lambda(pba_problem* p, double lambda);
+
+/* One full Levenberg-Marquardt iteration (linearise, damp, solve, update,
+ * re-evaluate, accept or reject) with the device-side lambda schedule;
+ * fills stats (may be NULL) and synchronises. */
+int pba_iterate(pba_problem* p, pba_iter_stats* stats);
+
+/* Enqueue n iterations as replays of one captured CUDA graph without
+ * synchronising; pba_get_stats() then reads the last iteration's outcome. */
+int pba_iterate_async(pba_problem* p, int n);
+
+/* Synchronise and read the outcome of the last iteration. */
+int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
+
+/* Number of kernel launches one pba_iterate performs (for accounting). */
+int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
+
+/* Instrumentation: one iteration like pba_iterate, enqueued launch by launch
+ * (not as a graph) with CUDA events recorded on the problem's stream between
+ * its phases; writes min(n_phases, PBA_N_PHASES) device times in
+ * milliseconds: [0] pair transforms, [1] the linearisation kernel,
+ * [2] per-pair reduction + assembly + total cost, [3] damping + Cholesky +
+ * triangular solves + box-plus + candidate transforms, [4] the cost-only
+ * linearisation kernel at the candidate, [5] its reduction + accept.
+ * Fills stats (may be NULL); synchronises. */
+#define PBA_N_PHASES 6
+int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBA_H */

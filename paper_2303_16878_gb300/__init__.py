@@ -1,0 +1,242 @@
+"""GB300-native photometric LiDAR and RGB-D bundle adjustment.
+
+The compute path is libpba (CUDA for sm_103a, C ABI in include/pba.h); this
+package is a thin binding over it.  `Problem` mirrors the C calls one to one:
+it converts numpy arrays and torch tensors into pointers and sizes and raises
+`PbaError` on a non-zero status.  PyTorch is used only for device memory and
+streams.  `synth` generates seeded synthetic workloads.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PBA_PATH_BATCHED, PBA_PATH_PLAIN, PBA_PINHOLE, PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32,
+                   PbaError)
+
+__all__ = ["Problem", "PbaError", "PBA_PATH_BATCHED", "PBA_PATH_PLAIN", "PBA_TEXEL_F16", "PBA_TEXEL_F32",
+           "PBA_PINHOLE", "PBA_SPHERICAL", "problem_from_workload"]
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stats(s: _lib.PbaIterStats) -> Dict:
+    return dict(cost=s.cost, new_cost=s.new_cost, lambda_used=s.lambda_used, lambda_next=s.lambda_next,
+                n_valid=int(s.n_valid), accepted=bool(s.accepted), status=int(s.status))
+
+
+class Problem:
+    """One bundle-adjustment problem on the current CUDA device (C: pba_problem)."""
+
+    def __init__(self, sensors: Sequence, n_frames: int, params: Dict, frame_sensor=None,
+                 path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXEL_F16, stream=None):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        self.n_frames = int(n_frames)
+        sens = (_lib.PbaSensor * len(sensors))()
+        self._sizes = []
+        for k, s in enumerate(sensors):
+            g = (lambda key: s[key]) if isinstance(s, dict) else (lambda key: getattr(s, key))
+            sens[k].model, sens[k].width, sens[k].height = int(g("model")), int(g("width")), int(g("height"))
+            sens[k].fx, sens[k].fy, sens[k].cx, sens[k].cy = (float(g("fx")), float(g("fy")), float(g("cx")),
+                                                              float(g("cy")))
+            xo = np.asarray(g("extrinsic"), dtype=np.float64).reshape(12)
+            for e in range(12):
+                sens[k].extrinsic[e] = xo[e]
+            self._sizes.append((sens[k].height, sens[k].width))
+        self._sens = sens
+        fs = None
+        if frame_sensor is not None:
+            self._fs = np.ascontiguousarray(frame_sensor, dtype=np.int32)
+            fs = self._fs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        else:
+            self._fs = np.zeros(self.n_frames, dtype=np.int32)
+        cfg = _lib.PbaConfig()
+        cfg.n_frames, cfg.n_sensors = self.n_frames, len(sensors)
+        cfg.sensors = ctypes.cast(sens, ctypes.POINTER(_lib.PbaSensor))
+        cfg.frame_sensor = fs
+        for key in ("w_int", "w_depth", "w_normal", "huber_delta", "occ_abs", "occ_rel", "z_min", "range_min",
+                    "range_max"):
+            setattr(cfg, key, float(params[key]))
+        cfg.grad_mode = int(params.get("grad_mode", 0))
+        cfg.texel_precision = int(texel)
+        cfg.path = int(path)
+        self.path, self.texel = int(path), int(texel)
+        st = self._lib.pba_create(ctypes.byref(cfg), ctypes.c_void_p(self._stream_handle(stream)),
+                                  ctypes.byref(self._h))
+        if st != 0:
+            raise PbaError(st, "pba_create failed")
+
+    @staticmethod
+    def _stream_handle(stream) -> int:
+        if stream is None:
+            return 0
+        if isinstance(stream, int):
+            return stream
+        return int(stream.cuda_stream)
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self._lib.pba_last_error(self._h)
+            raise PbaError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if self._h:
+            self._lib.pba_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        self._check(self._lib.pba_set_stream(self._h, ctypes.c_void_p(self._stream_handle(stream))), "set_stream")
+
+    # -------------------------------------------------------------- inputs
+    def _check_shape(self, first: int, shape):
+        shape = tuple(shape)
+        if len(shape) == 3:
+            shape = (1,) + shape
+        count = shape[0]
+        if len(shape) != 4 or shape[3] != 5 or count < 1 or first < 0 or first + count > self.n_frames:
+            raise ValueError(f"channels must be (count, H, W, 5) within the frame range, got {shape}")
+        for k in range(first, first + count):
+            if shape[1:3] != self._sizes[int(self._fs[k])]:
+                raise ValueError(f"frame {k}: image {shape[1:3]} does not match its sensor {self._sizes[int(self._fs[k])]}")
+        return count
+
+    def upload_frames(self, first: int, channels):
+        """channels: (count, H, W, 5) float32 numpy array or CUDA torch tensor."""
+        if _is_torch(channels):
+            if str(channels.dtype) != "torch.float32" or not channels.is_contiguous():
+                raise ValueError("channels must be a contiguous float32 tensor")
+            count = self._check_shape(first, channels.shape)
+            self._check(self._lib.pba_upload_frames(self._h, first, count, ctypes.c_void_p(channels.data_ptr()),
+                                                    1 if channels.is_cuda else 0), "upload_frames")
+            return
+        arr = np.ascontiguousarray(channels, dtype=np.float32)
+        if arr.ndim == 3:
+            arr = arr[None]
+        self._check_shape(first, arr.shape)
+        self._check(self._lib.pba_upload_frames(self._h, first, arr.shape[0], arr.ctypes.data_as(ctypes.c_void_p), 0),
+                    "upload_frames")
+
+    def frame_points(self, frame: int) -> int:
+        n = ctypes.c_int32()
+        self._check(self._lib.pba_frame_points(self._h, frame, ctypes.byref(n)), "frame_points")
+        return n.value
+
+    def set_poses(self, poses):
+        if _is_torch(poses):
+            self._check(self._lib.pba_set_poses(self._h, ctypes.c_void_p(poses.data_ptr()), 1 if poses.is_cuda else 0),
+                        "set_poses")
+            return
+        arr = np.ascontiguousarray(poses, dtype=np.float64).reshape(self.n_frames, 12)
+        self._check(self._lib.pba_set_poses(self._h, arr.ctypes.data_as(ctypes.c_void_p), 0), "set_poses")
+
+    def get_poses(self) -> np.ndarray:
+        out = np.zeros((self.n_frames, 12))
+        self._check(self._lib.pba_get_poses(self._h, out.ctypes.data_as(ctypes.c_void_p)), "get_poses")
+        return out.reshape(self.n_frames, 3, 4)
+
+    def set_pairs(self, pairs):
+        arr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        self.n_pairs = arr.shape[0]
+        self._check(self._lib.pba_set_pairs(self._h, arr.ctypes.data_as(ctypes.c_void_p), arr.shape[0]), "set_pairs")
+
+    # -------------------------------------------------------------- linearise / solve
+    def linearize(self):
+        cost, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self._lib.pba_linearize(self._h, ctypes.byref(cost), ctypes.byref(n)), "linearize")
+        return cost.value, n.value
+
+    def get_system(self):
+        n6 = 6 * self.n_frames
+        H, b = np.zeros((n6, n6)), np.zeros(n6)
+        self._check(self._lib.pba_get_system(self._h, H.ctypes.data_as(ctypes.c_void_p),
+                                             b.ctypes.data_as(ctypes.c_void_p)), "get_system")
+        return H, b
+
+    def get_pair_system(self):
+        m = self.n_pairs
+        H, b, c, n = np.zeros((m, 12, 12)), np.zeros((m, 12)), np.zeros(m), np.zeros(m, dtype=np.int64)
+        self._check(self._lib.pba_get_pair_system(self._h, *(x.ctypes.data_as(ctypes.c_void_p) for x in (H, b, c, n))),
+                    "get_pair_system")
+        return dict(H=H, b=b, cost=c, count=n)
+
+    def set_mask_export(self, enable: bool):
+        self._check(self._lib.pba_set_mask_export(self._h, 1 if enable else 0), "set_mask_export")
+
+    def get_mask(self, pair: int, n_points: int) -> np.ndarray:
+        nw = max(1, (n_points + 31) // 32)
+        out = np.zeros(nw, dtype=np.uint32)
+        self._check(self._lib.pba_get_mask(self._h, pair, out.ctypes.data_as(ctypes.c_void_p), nw), "get_mask")
+        return out[: (n_points + 31) // 32]
+
+    def solve_step(self, lam: float) -> Dict:
+        s = _lib.PbaIterStats()
+        self._check(self._lib.pba_solve_step(self._h, float(lam), ctypes.byref(s)), "solve_step")
+        return _stats(s)
+
+    def set_lambda(self, lam: Optional[float]):
+        self._check(self._lib.pba_set_lambda(self._h, -1.0 if lam is None else float(lam)), "set_lambda")
+
+    def iterate(self) -> Dict:
+        s = _lib.PbaIterStats()
+        self._check(self._lib.pba_iterate(self._h, ctypes.byref(s)), "iterate")
+        return _stats(s)
+
+    def iterate_async(self, n: int = 1):
+        self._check(self._lib.pba_iterate_async(self._h, int(n)), "iterate_async")
+
+    def get_stats(self) -> Dict:
+        s = _lib.PbaIterStats()
+        self._check(self._lib.pba_get_stats(self._h, ctypes.byref(s)), "get_stats")
+        return _stats(s)
+
+    def iterate_timed(self):
+        """One iteration launched kernel by kernel with CUDA events between its
+        phases; returns (stats, {phase name: device ms})."""
+        ms = (ctypes.c_float * _lib.PBA_N_PHASES)()
+        s = _lib.PbaIterStats()
+        self._check(self._lib.pba_iterate_timed(self._h, ms, _lib.PBA_N_PHASES, ctypes.byref(s)), "iterate_timed")
+        return _stats(s), dict(zip(_lib.PHASE_NAMES, list(ms)))
+
+    def iteration_launches(self) -> int:
+        n = ctypes.c_int32()
+        self._check(self._lib.pba_iteration_launches(self._h, ctypes.byref(n)), "iteration_launches")
+        return n.value
+
+
+def problem_from_workload(w, path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXEL_F16, params: Optional[Dict] = None,
+                          poses=None, stream=None) -> Problem:
+    """Create a Problem from a synth.Workload: upload every frame (grouped by
+    image size), set the initial poses and the pair list."""
+    prm = dict(w.params)
+    if params:
+        prm.update(params)
+    p = Problem(w.sensors, w.n_frames, prm, frame_sensor=w.frame_sensor, path=path, texel=texel, stream=stream)
+    k = 0
+    while k < w.n_frames:
+        j = k
+        while j + 1 < w.n_frames and w.channels[j + 1].shape == w.channels[k].shape:
+            j += 1
+        p.upload_frames(k, np.stack(w.channels[k:j + 1]))
+        k = j + 1
+    p.set_poses(w.poses_init if poses is None else poses)
+    p.set_pairs(w.pairs)
+    return p

@@ -1,0 +1,784 @@
+// pba_api.cu -- the C ABI of libpba (declared in include/pba.h): problem
+// lifecycle, uploads, the host-side plan of one Gauss-Newton iteration (chunk
+// queue, per-pair chunk ranges, assembly tasks) and the enqueueing of the
+// kernels, directly or as a captured CUDA graph.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pba.h"
+#include "pba_internal.cuh"
+
+using namespace pba;
+
+namespace {
+
+constexpr int kChunk = 2048;  // points per work item of the persistent launch
+
+}  // namespace
+
+struct pba_problem {
+    pba_config cfg{};
+    std::vector<pba_sensor> sensors;
+    std::vector<int> frame_sensor;
+    int N = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    std::string err;
+
+    // frames
+    std::vector<long long> px_off;
+    long long total_px = 0;
+    std::vector<int> n_points;
+    std::vector<char> uploaded;
+    bool points_known = false;
+
+    // device buffers (problem lifetime)
+    float* raw = nullptr;
+    void* tex = nullptr;
+    float4* pts_pg = nullptr;
+    float4* pts_n = nullptr;
+    int* d_npoints = nullptr;
+    FrameInfo* d_frames = nullptr;
+    SensorDev* d_sensors = nullptr;
+    int* d_frame_ids = nullptr;
+    double* d_poses = nullptr;
+    double* d_cand = nullptr;
+    LmState* d_state = nullptr;
+    double* d_H = nullptr;
+    double* d_b = nullptr;
+    double* d_A = nullptr;
+    double* d_rhs = nullptr;
+    int n_pad = 0;
+    int* d_queue = nullptr;  // two counters: full pass, cost pass
+
+    // pair-dependent buffers
+    int M = 0;
+    std::vector<int32_t> pairs;
+    PairStatic* d_ps = nullptr;
+    PairPose* d_pp = nullptr;
+    int2* d_pf = nullptr;
+    double* d_pair_Xo = nullptr;
+    int4* d_chunks = nullptr;
+    int n_chunks = 0;
+    float* d_partials = nullptr;
+    double* d_blocks = nullptr;
+    double* d_blocks_cand = nullptr;
+    AsmTask* d_tasks = nullptr;
+    int n_tasks = 0;
+    AsmContrib* d_contrib = nullptr;
+    uint32_t* d_mask = nullptr;
+    std::vector<long long> mask_off;
+    std::vector<int> pair_src_points;
+    float* d_plain_acc = nullptr;
+
+    bool poses_set = false;
+    bool mask_export = false;
+    bool mask_valid = false;
+    bool linearized = false;
+    int grid_full = 0, grid_cost = 0;
+    LinParams prm{};
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int launches_last = 0;
+};
+
+namespace {
+
+int fail(pba_problem* p, int code, const std::string& msg) {
+    if (p) p->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(p, call)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail((p), e_ == cudaErrorMemoryAllocation ? PBA_ENOMEM : PBA_ECUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+template <typename T>
+void dfree(T*& ptr) {
+    if (ptr) cudaFree((void*)ptr);
+    ptr = nullptr;
+}
+
+void free_pair_buffers(pba_problem* p) {
+    dfree(p->d_ps);
+    dfree(p->d_pp);
+    dfree(p->d_pf);
+    dfree(p->d_pair_Xo);
+    dfree(p->d_chunks);
+    dfree(p->d_partials);
+    dfree(p->d_blocks);
+    dfree(p->d_blocks_cand);
+    dfree(p->d_tasks);
+    dfree(p->d_contrib);
+    dfree(p->d_mask);
+    dfree(p->d_plain_acc);
+    p->M = 0;
+    p->n_chunks = 0;
+    p->n_tasks = 0;
+}
+
+void drop_graph(pba_problem* p) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+}
+
+int ensure_points(pba_problem* p) {
+    if (p->points_known) return PBA_OK;
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    CUDA_TRY(p, cudaMemcpy(p->n_points.data(), p->d_npoints, sizeof(int) * p->N, cudaMemcpyDeviceToHost));
+    p->points_known = true;
+    return PBA_OK;
+}
+
+// Full linearisation at the current poses: pair pose table, persistent
+// linearise, per-pair FP64 reduction, assembly of H and b, total cost.
+int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr) {
+    CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
+    ++*nl;
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
+    if (p->cfg.path == PBA_PATH_PLAIN) {
+        CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
+        for (int q = 0; q < p->M; ++q) {
+            const int src = p->pairs[2 * q];
+            const pba_sensor& S = p->sensors[p->frame_sensor[src]];
+            CUDA_TRY(p, launch_plain(true, q, p->d_ps, p->d_pp, p->raw, p->d_sensors, p->frame_sensor[src], p->prm,
+                                     p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width, S.height, s));
+            ++*nl;
+        }
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
+        CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, true, p->d_blocks, s));
+        ++*nl;
+    } else {
+        CUDA_TRY(p, cudaMemsetAsync(p->d_queue, 0, sizeof(int), s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
+        const bool mask = p->mask_export;
+        CUDA_TRY(p, launch_linearize(true, mask, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue,
+                                     p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials,
+                                     p->d_mask, p->grid_full, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
+        CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M, true,
+                                       p->d_blocks, s));
+        *nl += 2;
+    }
+    CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, p->d_blocks, p->N, p->d_H, p->d_b, s));
+    CUDA_TRY(p, launch_total_cost(p->d_blocks, p->M, p->d_state, false, s));
+    *nl += 2;
+    return PBA_OK;
+}
+
+// Damped solve, candidate poses, cost at the candidate, accept / reject.
+int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr) {
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[3], s));
+    CUDA_TRY(p, launch_lm_prepare(p->d_H, p->N, p->d_state, lambda, s));
+    CUDA_TRY(p, launch_damp(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->d_A, p->d_rhs, s));
+    int nc = 0;
+    CUDA_TRY(p, launch_cholesky(p->d_A, p->n_pad, p->d_state, s, &nc));
+    CUDA_TRY(p, launch_trsv(p->d_A, p->n_pad, p->d_rhs, p->d_state, s));
+    CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->d_state, p->d_cand, s));
+    CUDA_TRY(p, launch_pair_pose(p->d_cand, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
+    *nl += 5 + nc;
+    if (p->cfg.path == PBA_PATH_PLAIN) {
+        CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
+        for (int q = 0; q < p->M; ++q) {
+            const int src = p->pairs[2 * q];
+            const pba_sensor& S = p->sensors[p->frame_sensor[src]];
+            CUDA_TRY(p, launch_plain(false, q, p->d_ps, p->d_pp, p->raw, p->d_sensors, p->frame_sensor[src], p->prm,
+                                     p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width, S.height, s));
+            ++*nl;
+        }
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
+        CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, false, p->d_blocks_cand, s));
+        ++*nl;
+    } else {
+        CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
+        CUDA_TRY(p, launch_linearize(false, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue + 1,
+                                     p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials, nullptr,
+                                     p->grid_cost, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
+        CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_cand, p->d_pair_Xo, p->M, false,
+                                       p->d_blocks_cand, s));
+        *nl += 2;
+    }
+    CUDA_TRY(p, launch_total_cost(p->d_blocks_cand, p->M, p->d_state, true, s));
+    CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, s));
+    *nl += 2;
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[6], s));
+    return PBA_OK;
+}
+
+int read_stats(pba_problem* p, pba_iter_stats* stats) {
+    LmState st;
+    CUDA_TRY(p, cudaMemcpyAsync(&st, p->d_state, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    if (stats) {
+        stats->cost = st.cost;
+        stats->new_cost = st.new_cost;
+        stats->lambda_used = st.lambda_used;
+        stats->lambda_next = st.lambda;
+        stats->n_valid = st.n_valid;
+        stats->accepted = st.accepted;
+        stats->status = st.status;
+    }
+    return PBA_OK;
+}
+
+int ready(pba_problem* p) {
+    if (!p) return PBA_EINVAL;
+    if (!p->poses_set) return fail(p, PBA_ENOTREADY, "poses not set");
+    if (p->M <= 0) return fail(p, PBA_ENOTREADY, "pairs not set");
+    cudaSetDevice(p->device);
+    return PBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pba_last_error(const pba_problem* p) {
+    if (!p) return "null problem";
+    return p->err.c_str();
+}
+
+int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
+    if (!cfg || !out) return PBA_EINVAL;
+    *out = nullptr;
+    if (cfg->n_frames < 1 || cfg->n_sensors < 1 || !cfg->sensors) return PBA_EINVAL;
+    if (!(cfg->huber_delta > 0.0)) return PBA_EINVAL;
+    if (cfg->grad_mode != 0 && cfg->grad_mode != 1) return PBA_EINVAL;
+    if (cfg->texel_precision != 0 && cfg->texel_precision != 1) return PBA_EINVAL;
+    if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return PBA_EINVAL;
+    for (int s = 0; s < cfg->n_sensors; ++s) {
+        const pba_sensor& S = cfg->sensors[s];
+        if ((S.model != PBA_PINHOLE && S.model != PBA_SPHERICAL) || S.width < 4 || S.height < 4) return PBA_EINVAL;
+        if (S.fx == 0.0 || S.fy == 0.0) return PBA_EINVAL;
+        if ((long long)S.width * S.height > (1LL << 30)) return PBA_EINVAL;
+    }
+    pba_problem* p = new pba_problem();
+    p->cfg = *cfg;
+    p->N = cfg->n_frames;
+    p->sensors.assign(cfg->sensors, cfg->sensors + cfg->n_sensors);
+    p->cfg.sensors = nullptr;
+    p->frame_sensor.assign(p->N, 0);
+    if (cfg->frame_sensor) {
+        for (int k = 0; k < p->N; ++k) {
+            if (cfg->frame_sensor[k] < 0 || cfg->frame_sensor[k] >= cfg->n_sensors) {
+                delete p;
+                return PBA_EINVAL;
+            }
+            p->frame_sensor[k] = cfg->frame_sensor[k];
+        }
+    }
+    p->cfg.frame_sensor = nullptr;
+    cudaGetDevice(&p->device);
+    auto bail = [&](int code) {
+        pba_destroy(p);
+        return code;
+    };
+    if (cuda_stream) {
+        p->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PBA_ECUDA);
+        p->stream = p->own_stream;
+    }
+    if (cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PBA_ECUDA);
+
+    p->px_off.resize(p->N);
+    long long off = 0;
+    for (int k = 0; k < p->N; ++k) {
+        const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+        p->px_off[k] = off;
+        off += (long long)S.width * S.height;
+    }
+    p->total_px = off;
+    p->n_points.assign(p->N, 0);
+    p->uploaded.assign(p->N, 0);
+
+    const size_t texel_bytes = cfg->texel_precision == PBA_TEXEL_F16 ? sizeof(Tex16) : sizeof(Tex32);
+    const int n6 = 6 * p->N;
+    const int n = n6 - 6;
+    p->n_pad = ((n + kTile - 1) / kTile) * kTile;
+    if (p->n_pad == 0) p->n_pad = kTile;
+    auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
+    bool ok = alloc((void**)&p->raw, sizeof(float) * 5 * (size_t)p->total_px) &&
+              alloc(&p->tex, texel_bytes * (size_t)p->total_px) &&
+              alloc((void**)&p->pts_pg, sizeof(float4) * (size_t)p->total_px) &&
+              alloc((void**)&p->pts_n, sizeof(float4) * (size_t)p->total_px) &&
+              alloc((void**)&p->d_npoints, sizeof(int) * p->N) &&
+              alloc((void**)&p->d_frames, sizeof(FrameInfo) * p->N) &&
+              alloc((void**)&p->d_sensors, sizeof(SensorDev) * p->sensors.size()) &&
+              alloc((void**)&p->d_frame_ids, sizeof(int) * p->N) &&
+              alloc((void**)&p->d_poses, sizeof(double) * 12 * p->N) &&
+              alloc((void**)&p->d_cand, sizeof(double) * 12 * p->N) &&
+              alloc((void**)&p->d_state, sizeof(LmState)) &&
+              alloc((void**)&p->d_H, sizeof(double) * (size_t)n6 * n6) &&
+              alloc((void**)&p->d_b, sizeof(double) * n6) &&
+              alloc((void**)&p->d_A, sizeof(double) * (size_t)p->n_pad * p->n_pad) &&
+              alloc((void**)&p->d_rhs, sizeof(double) * p->n_pad) &&
+              alloc((void**)&p->d_queue, sizeof(int) * 2);
+    if (!ok) return bail(PBA_ENOMEM);
+
+    std::vector<FrameInfo> fi(p->N);
+    for (int k = 0; k < p->N; ++k) {
+        const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+        fi[k].width = S.width;
+        fi[k].height = S.height;
+        fi[k].sensor = p->frame_sensor[k];
+        fi[k].model = S.model;
+        fi[k].fx = (float)S.fx;
+        fi[k].fy = (float)S.fy;
+        fi[k].cx = (float)S.cx;
+        fi[k].cy = (float)S.cy;
+        fi[k].px_offset = p->px_off[k];
+        fi[k].pt_offset = p->px_off[k];
+    }
+    std::vector<SensorDev> sd(p->sensors.size());
+    for (size_t s = 0; s < p->sensors.size(); ++s) {
+        const pba_sensor& S = p->sensors[s];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) sd[s].R[3 * r + c] = (float)S.extrinsic[4 * r + c];
+            sd[s].t[r] = (float)S.extrinsic[4 * r + 3];
+        }
+        sd[s].model = S.model;
+        sd[s].width = S.width;
+        sd[s].height = S.height;
+        sd[s].fx = (float)S.fx;
+        sd[s].fy = (float)S.fy;
+        sd[s].cx = (float)S.cx;
+        sd[s].cy = (float)S.cy;
+    }
+    LmState st{};
+    st.lambda = -1.0;
+    if (cudaMemcpy(p->d_frames, fi.data(), sizeof(FrameInfo) * p->N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_sensors, sd.data(), sizeof(SensorDev) * sd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_state, &st, sizeof st, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->d_npoints, 0, sizeof(int) * p->N) != cudaSuccess ||
+        cudaMemset(p->d_H, 0, sizeof(double) * (size_t)n6 * n6) != cudaSuccess ||
+        cudaMemset(p->d_b, 0, sizeof(double) * n6) != cudaSuccess)
+        return bail(PBA_ECUDA);
+
+    p->prm.w_int = (float)cfg->w_int;
+    p->prm.w_depth = (float)cfg->w_depth;
+    p->prm.w_normal = (float)cfg->w_normal;
+    p->prm.huber_delta = (float)cfg->huber_delta;
+    p->prm.huber_delta2 = (float)(cfg->huber_delta * cfg->huber_delta);
+    p->prm.occ_abs = (float)cfg->occ_abs;
+    p->prm.occ_rel = (float)cfg->occ_rel;
+    p->prm.z_min = (float)cfg->z_min;
+    p->prm.grad_mode = cfg->grad_mode;
+    p->grid_full = linearize_grid(cfg->texel_precision, true);
+    p->grid_cost = linearize_grid(cfg->texel_precision, false);
+    *out = p;
+    return PBA_OK;
+}
+
+void pba_destroy(pba_problem* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    drop_graph(p);
+    free_pair_buffers(p);
+    dfree(p->raw);
+    dfree(p->tex);
+    dfree(p->pts_pg);
+    dfree(p->pts_n);
+    dfree(p->d_npoints);
+    dfree(p->d_frames);
+    dfree(p->d_sensors);
+    dfree(p->d_frame_ids);
+    dfree(p->d_poses);
+    dfree(p->d_cand);
+    dfree(p->d_state);
+    dfree(p->d_H);
+    dfree(p->d_b);
+    dfree(p->d_A);
+    dfree(p->d_rhs);
+    dfree(p->d_queue);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    if (p->own_stream) cudaStreamDestroy(p->own_stream);
+    delete p;
+}
+
+int pba_set_stream(pba_problem* p, void* cuda_stream) {
+    if (!p) return PBA_EINVAL;
+    p->stream = cuda_stream ? (cudaStream_t)cuda_stream : p->own_stream;
+    if (!p->stream) {
+        CUDA_TRY(p, cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking));
+        p->stream = p->own_stream;
+    }
+    return PBA_OK;
+}
+
+int pba_upload_frames(pba_problem* p, int first, int count, const float* channels, int is_device) {
+    if (!p) return PBA_EINVAL;
+    if (!channels || count < 1 || first < 0 || first + count > p->N)
+        return fail(p, PBA_EINVAL, "upload: bad frame range or null channels");
+    cudaSetDevice(p->device);
+    const pba_sensor& S0 = p->sensors[p->frame_sensor[first]];
+    for (int k = first; k < first + count; ++k) {
+        const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+        if (S.width != S0.width || S.height != S0.height)
+            return fail(p, PBA_EINVAL, "upload: frames of one call must share the image size");
+    }
+    const size_t bytes = sizeof(float) * 5 * (size_t)S0.width * S0.height * count;
+    CUDA_TRY(p, cudaMemcpyAsync(p->raw + 5 * p->px_off[first], channels, bytes,
+                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    std::vector<int> ids(count);
+    for (int k = 0; k < count; ++k) ids[k] = first + k;
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
+                            p->pts_pg, p->pts_n, p->d_npoints, p->cfg.range_min, p->cfg.range_max, p->stream));
+    // the id list is pageable host memory: the synchronisation also makes sure
+    // the copy has consumed it
+    std::vector<int> before = p->n_points;
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    CUDA_TRY(p, cudaMemcpy(p->n_points.data(), p->d_npoints, sizeof(int) * p->N, cudaMemcpyDeviceToHost));
+    p->points_known = true;
+    for (int k = first; k < first + count; ++k) p->uploaded[k] = 1;
+    p->linearized = false;
+    p->mask_valid = false;
+    if (p->M > 0 && before != p->n_points) {
+        // the chunk queue depends on the point counts: rebuild the pair plan
+        std::vector<int32_t> keep = p->pairs;
+        return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
+    }
+    return PBA_OK;
+}
+
+int pba_frame_points(pba_problem* p, int frame, int32_t* n_points) {
+    if (!p || !n_points || frame < 0 || frame >= p->N) return fail(p, PBA_EINVAL, "frame_points: bad argument");
+    if (!p->uploaded[frame]) return fail(p, PBA_ENOTREADY, "frame not uploaded");
+    cudaSetDevice(p->device);
+    int st = ensure_points(p);
+    if (st) return st;
+    *n_points = p->n_points[frame];
+    return PBA_OK;
+}
+
+int pba_set_poses(pba_problem* p, const double* poses, int is_device) {
+    if (!p || !poses) return fail(p, PBA_EINVAL, "set_poses: null");
+    cudaSetDevice(p->device);
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_poses, poses, sizeof(double) * 12 * p->N,
+                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    if (!is_device) CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    p->poses_set = true;
+    p->linearized = false;
+    return PBA_OK;
+}
+
+int pba_get_poses(pba_problem* p, double* poses) {
+    if (!p || !poses) return fail(p, PBA_EINVAL, "get_poses: null");
+    cudaSetDevice(p->device);
+    CUDA_TRY(p, cudaMemcpyAsync(poses, p->d_poses, sizeof(double) * 12 * p->N, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return PBA_OK;
+}
+
+int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
+    if (!p || (!pairs && m > 0) || m < 0) return fail(p, PBA_EINVAL, "set_pairs: bad argument");
+    cudaSetDevice(p->device);
+    for (int q = 0; q < m; ++q) {
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        if (i < 0 || j < 0 || i >= p->N || j >= p->N) return fail(p, PBA_EINVAL, "set_pairs: frame out of range");
+        if (p->frame_sensor[i] != p->frame_sensor[j])
+            return fail(p, PBA_EINVAL, "set_pairs: pair frames use different sensors");
+        if (!p->uploaded[i] || !p->uploaded[j]) return fail(p, PBA_ENOTREADY, "set_pairs: frame not uploaded");
+    }
+    int st = ensure_points(p);
+    if (st) return st;
+    drop_graph(p);
+    free_pair_buffers(p);
+    p->pairs.assign(pairs, pairs + 2 * (size_t)m);
+    p->M = m;
+    p->linearized = false;
+    p->mask_valid = false;
+    if (m == 0) return PBA_OK;
+
+    // processing order: by target frame (its texels stay in L2), then source
+    std::vector<int> order(m);
+    for (int q = 0; q < m; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (pairs[2 * a + 1] != pairs[2 * b + 1]) return pairs[2 * a + 1] < pairs[2 * b + 1];
+        return pairs[2 * a] < pairs[2 * b];
+    });
+    std::vector<PairStatic> ps(m);
+    std::vector<int2> pf(m);
+    std::vector<double> pxo(12 * (size_t)m);
+    std::vector<int4> chunks;
+    p->mask_off.assign(m, 0);
+    p->pair_src_points.assign(m, 0);
+    long long mask_words = 0;
+    for (int q = 0; q < m; ++q) {
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        const pba_sensor& S = p->sensors[p->frame_sensor[i]];
+        PairStatic& P = ps[q];
+        P.src = i;
+        P.tgt = j;
+        P.model = S.model;
+        P.width = S.width;
+        P.height = S.height;
+        P.n_points = p->n_points[i];
+        P.fx = (float)S.fx;
+        P.fy = (float)S.fy;
+        P.cx = (float)S.cx;
+        P.cy = (float)S.cy;
+        P.src_pt_offset = p->px_off[i];
+        P.tgt_px_offset = p->px_off[j];
+        P.src_px_offset = p->px_off[i];
+        P.src_width = S.width;
+        P.src_height = S.height;
+        P.mask_offset = mask_words;
+        p->mask_off[q] = mask_words;
+        p->pair_src_points[q] = P.n_points;
+        mask_words += (P.n_points + 31) / 32;
+        pf[q] = make_int2(i, j);
+        for (int e = 0; e < 12; ++e) pxo[12 * q + e] = S.extrinsic[e];
+    }
+    for (int oi = 0; oi < m; ++oi) {
+        const int q = order[oi];
+        ps[q].chunk_begin = (int)chunks.size();
+        for (int s = 0; s < ps[q].n_points; s += kChunk)
+            chunks.push_back(make_int4(q, s, std::min(kChunk, ps[q].n_points - s), 0));
+        ps[q].chunk_end = (int)chunks.size();
+    }
+    p->n_chunks = (int)chunks.size();
+
+    // assembly tasks: one per diagonal block and per unordered frame pair
+    std::map<std::pair<int, int>, std::vector<AsmContrib>> tasks;
+    for (int q = 0; q < m; ++q) {
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        // roles: 0 = i (rows/cols 0-5 of the pair block), 1 = j
+        const int fr[2] = {i, j};
+        for (int rr = 0; rr < 2; ++rr)
+            for (int cc = 0; cc < 2; ++cc) {
+                const int a = fr[rr], b = fr[cc];
+                if (a > b) continue;  // the transpose is written by the (b, a) contribution's task
+                tasks[{a, b}].push_back(AsmContrib{q, rr, cc, rr == cc ? 1 : 0});
+            }
+    }
+    std::vector<AsmTask> tv;
+    std::vector<AsmContrib> cv;
+    for (auto& kv : tasks) {
+        AsmTask T;
+        T.a = kv.first.first;
+        T.b = kv.first.second;
+        T.contrib_begin = (int)cv.size();
+        for (auto& c : kv.second) cv.push_back(c);
+        T.contrib_end = (int)cv.size();
+        tv.push_back(T);
+    }
+    p->n_tasks = (int)tv.size();
+
+    auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
+    bool ok = alloc((void**)&p->d_ps, sizeof(PairStatic) * m) && alloc((void**)&p->d_pp, sizeof(PairPose) * m) &&
+              alloc((void**)&p->d_pf, sizeof(int2) * m) && alloc((void**)&p->d_pair_Xo, sizeof(double) * 12 * m) &&
+              alloc((void**)&p->d_chunks, sizeof(int4) * chunks.size()) &&
+              alloc((void**)&p->d_partials, sizeof(float) * kPartialStride * chunks.size()) &&
+              alloc((void**)&p->d_blocks, sizeof(double) * kBlockStride * m) &&
+              alloc((void**)&p->d_blocks_cand, sizeof(double) * kBlockStride * m) &&
+              alloc((void**)&p->d_tasks, sizeof(AsmTask) * tv.size()) &&
+              alloc((void**)&p->d_contrib, sizeof(AsmContrib) * cv.size()) &&
+              alloc((void**)&p->d_mask, sizeof(uint32_t) * (size_t)mask_words) &&
+              alloc((void**)&p->d_plain_acc, sizeof(float) * 96 * m);
+    if (!ok) {
+        free_pair_buffers(p);
+        return fail(p, PBA_ENOMEM, "set_pairs: device allocation failed");
+    }
+    CUDA_TRY(p, cudaMemcpy(p->d_ps, ps.data(), sizeof(PairStatic) * m, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_pf, pf.data(), sizeof(int2) * m, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_pair_Xo, pxo.data(), sizeof(double) * 12 * m, cudaMemcpyHostToDevice));
+    if (!chunks.empty())
+        CUDA_TRY(p, cudaMemcpy(p->d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_tasks, tv.data(), sizeof(AsmTask) * tv.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_contrib, cv.data(), sizeof(AsmContrib) * cv.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemset(p->d_blocks, 0, sizeof(double) * kBlockStride * m));
+    CUDA_TRY(p, cudaMemset(p->d_blocks_cand, 0, sizeof(double) * kBlockStride * m));
+    const int n6 = 6 * p->N;
+    CUDA_TRY(p, cudaMemset(p->d_H, 0, sizeof(double) * (size_t)n6 * n6));
+    CUDA_TRY(p, cudaMemset(p->d_b, 0, sizeof(double) * n6));
+    return PBA_OK;
+}
+
+int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid) {
+    int st = ready(p);
+    if (st) return st;
+    int nl = 0;
+    st = enqueue_linearize(p, p->stream, &nl);
+    if (st) return st;
+    pba_iter_stats s{};
+    st = read_stats(p, &s);
+    if (st) return st;
+    p->linearized = true;
+    p->mask_valid = p->mask_export && p->cfg.path == PBA_PATH_BATCHED;
+    if (cost) *cost = s.cost;
+    if (n_valid) *n_valid = s.n_valid;
+    return PBA_OK;
+}
+
+int pba_get_system(pba_problem* p, double* H, double* b) {
+    if (!p) return PBA_EINVAL;
+    if (!p->linearized) return fail(p, PBA_ENOTREADY, "get_system: no linearisation");
+    cudaSetDevice(p->device);
+    const int n6 = 6 * p->N;
+    if (H) CUDA_TRY(p, cudaMemcpyAsync(H, p->d_H, sizeof(double) * (size_t)n6 * n6, cudaMemcpyDeviceToHost, p->stream));
+    if (b) CUDA_TRY(p, cudaMemcpyAsync(b, p->d_b, sizeof(double) * n6, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return PBA_OK;
+}
+
+int pba_get_pair_system(pba_problem* p, double* pair_H, double* pair_b, double* pair_cost, int64_t* pair_count) {
+    if (!p) return PBA_EINVAL;
+    if (!p->linearized) return fail(p, PBA_ENOTREADY, "get_pair_system: no linearisation");
+    cudaSetDevice(p->device);
+    std::vector<double> blk((size_t)kBlockStride * p->M);
+    CUDA_TRY(p, cudaMemcpyAsync(blk.data(), p->d_blocks, sizeof(double) * blk.size(), cudaMemcpyDeviceToHost,
+                                p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    for (int q = 0; q < p->M; ++q) {
+        const double* B = blk.data() + (size_t)kBlockStride * q;
+        if (pair_H) memcpy(pair_H + 144 * (size_t)q, B, sizeof(double) * 144);
+        if (pair_b) memcpy(pair_b + 12 * (size_t)q, B + 144, sizeof(double) * 12);
+        if (pair_cost) pair_cost[q] = B[156];
+        if (pair_count) pair_count[q] = (int64_t)B[157];
+    }
+    return PBA_OK;
+}
+
+int pba_set_mask_export(pba_problem* p, int enable) {
+    if (!p) return PBA_EINVAL;
+    if (p->cfg.path != PBA_PATH_BATCHED && enable) return fail(p, PBA_EINVAL, "mask export needs the batched path");
+    if ((p->mask_export ? 1 : 0) != (enable ? 1 : 0)) drop_graph(p);
+    p->mask_export = enable != 0;
+    return PBA_OK;
+}
+
+int pba_get_mask(pba_problem* p, int pair, uint32_t* bits, int n_words) {
+    if (!p || !bits || pair < 0 || pair >= p->M) return fail(p, PBA_EINVAL, "get_mask: bad argument");
+    if (!p->mask_valid) return fail(p, PBA_ENOTREADY, "get_mask: no mask exported");
+    const int need = (p->pair_src_points[pair] + 31) / 32;
+    if (n_words < need) return fail(p, PBA_EINVAL, "get_mask: buffer too small");
+    cudaSetDevice(p->device);
+    if (need > 0)
+        CUDA_TRY(p, cudaMemcpyAsync(bits, p->d_mask + p->mask_off[pair], sizeof(uint32_t) * need,
+                                    cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return PBA_OK;
+}
+
+int pba_solve_step(pba_problem* p, double lambda, pba_iter_stats* stats) {
+    int st = ready(p);
+    if (st) return st;
+    if (!p->linearized) return fail(p, PBA_ENOTREADY, "solve_step: no linearisation");
+    if (!(lambda >= 0.0)) return fail(p, PBA_EINVAL, "solve_step: lambda must be >= 0");
+    int nl = 0;
+    st = enqueue_step(p, lambda, p->stream, &nl);
+    if (st) return st;
+    p->linearized = false;
+    return read_stats(p, stats);
+}
+
+int pba_set_lambda(pba_problem* p, double lambda) {
+    if (!p) return PBA_EINVAL;
+    cudaSetDevice(p->device);
+    const double v = lambda >= 0.0 ? lambda : -1.0;
+    CUDA_TRY(p, cudaMemcpyAsync(&p->d_state->lambda, &v, sizeof v, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return PBA_OK;
+}
+
+int pba_iterate(pba_problem* p, pba_iter_stats* stats) {
+    int st = pba_iterate_async(p, 1);
+    if (st) return st;
+    p->linearized = false;
+    return read_stats(p, stats);
+}
+
+int pba_iterate_async(pba_problem* p, int n) {
+    int st = ready(p);
+    if (st) return st;
+    if (n < 0) return fail(p, PBA_EINVAL, "iterate_async: n < 0");
+    if (!p->graph_exec) {
+        int nl = 0;
+        CUDA_TRY(p, cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_linearize(p, p->capture_stream, &nl);
+        if (!st) st = enqueue_step(p, -1.0, p->capture_stream, &nl);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->capture_stream, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(p, PBA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        p->graph = g;
+        CUDA_TRY(p, cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+        p->launches_last = nl;
+    }
+    for (int k = 0; k < n; ++k) CUDA_TRY(p, cudaGraphLaunch(p->graph_exec, p->stream));
+    p->linearized = false;
+    p->mask_valid = false;
+    return PBA_OK;
+}
+
+int pba_get_stats(pba_problem* p, pba_iter_stats* stats) {
+    if (!p) return PBA_EINVAL;
+    cudaSetDevice(p->device);
+    return read_stats(p, stats);
+}
+
+int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_stats* stats) {
+    int st = ready(p);
+    if (st) return st;
+    cudaEvent_t ev[PBA_N_PHASES + 1] = {};
+    for (auto& e : ev) CUDA_TRY(p, cudaEventCreate(&e));
+    int nl = 0;
+    CUDA_TRY(p, cudaEventRecord(ev[0], p->stream));
+    st = enqueue_linearize(p, p->stream, &nl, ev);
+    if (!st) st = enqueue_step(p, -1.0, p->stream, &nl, ev);
+    if (!st) st = read_stats(p, stats);
+    if (!st && phase_ms)
+        for (int k = 0; k < n_phases && k < PBA_N_PHASES; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            phase_ms[k] = ms;
+        }
+    for (auto& e : ev) cudaEventDestroy(e);
+    p->linearized = false;
+    return st;
+}
+
+int pba_iteration_launches(pba_problem* p, int32_t* n_launches) {
+    if (!p || !n_launches) return PBA_EINVAL;
+    if (p->M <= 0) return fail(p, PBA_ENOTREADY, "pairs not set");
+    if (!p->graph_exec) {
+        // count without running: the same enqueue logic, on a capture that is discarded
+        int nl = 0;
+        CUDA_TRY(p, cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal));
+        int st = enqueue_linearize(p, p->capture_stream, &nl);
+        if (!st) st = enqueue_step(p, -1.0, p->capture_stream, &nl);
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(p->capture_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        if (st) return st;
+        *n_launches = nl;
+        return PBA_OK;
+    }
+    *n_launches = p->launches_last;
+    return PBA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// pba_internal.cuh -- device-side data layout shared by the kernels of libpba.
+//
+// Layout in HBM (one problem):
+//   raw       FP32 H x W x 5 per frame (the uploaded cue images, kept for the plain path)
+//   texels    per frame H x W sampling texels: Tex16 {float d; half g, nx, ny, nz; pad}
+//             or Tex32 {float d, g, nx, ny, nz, pad x 3}; d = 0 marks an invalid pixel
+//   points    per frame, compacted valid pixels in raster order:
+//             pg = float4(p_u, g_u), pn = float4(n_u^o, 0)   (Supp., p_u = R_o pi^-1(u, d) + t_o)
+//   pair pose table (FP32, per iteration): pbar = M p_u + a with M = R_o^T R_j^T R_i,
+//             a = R_o^T (R_j^T (t_i - t_j) - t_o)   (Supp., pbar_u)
+//   chunk list int4 {pair, first point, count, 0}: the persistent launch's work queue
+//   partials  FP32 per chunk: 21 (H6 upper) + 6 (b6) + cost + count (+3 pad) = 32 floats
+//   pair blocks FP64 per pair: H12 (144) + b12 (12) + cost + count (+2 pad) = 160 doubles
+//   H (6N x 6N) and b (6N) FP64 dense; A = H_ff + lambda I padded to a multiple of 32
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pba {
+
+constexpr int kPartialStride = 32;   // floats per chunk partial
+constexpr int kNumAcc = 29;          // 21 + 6 + cost + count
+constexpr int kBlockStride = 160;    // doubles per pair block
+constexpr int kTile = 32;            // Cholesky tile
+
+struct FrameInfo {
+    int width, height, sensor, model;
+    float fx, fy, cx, cy;
+    long long px_offset;     // pixel offset of the frame in raw / texel buffers
+    long long pt_offset;     // point offset of the frame in the point buffers
+};
+
+struct SensorDev {
+    float R[9];              // R_o row-major (FP32 copy)
+    float t[3];              // t_o
+    int model, width, height, pad;
+    float fx, fy, cx, cy;
+};
+
+// Static per-pair data, built on the host by pba_set_pairs.
+struct PairStatic {
+    int src, tgt, model, width, height;
+    int n_points;            // points of the source frame
+    int chunk_begin, chunk_end;
+    float fx, fy, cx, cy;
+    long long src_pt_offset; // into point buffers
+    long long tgt_px_offset; // into texel / raw buffers
+    long long mask_offset;   // in 32-bit words
+    long long src_px_offset; // raw buffer of the source (plain path)
+    int src_width, src_height;
+};
+
+// Pose-dependent per-pair constants (FP32), rebuilt on the device each iteration.
+struct PairPose {
+    float M[9];
+    float a[3];
+};
+
+struct Tex16 {
+    float d;
+    __half2 g_nx;
+    __half2 ny_nz;
+    float pad;
+};
+
+struct Tex32 {
+    float d, g, nx, ny, nz, p0, p1, p2;
+};
+
+struct LinParams {
+    float w_int, w_depth, w_normal;
+    float huber_delta, huber_delta2;
+    float occ_abs, occ_rel;
+    float z_min;
+    int grad_mode;
+};
+
+// Device-side Levenberg-Marquardt state of one problem.
+struct LmState {
+    double lambda;          // next damping (< 0: automatic on the next iteration)
+    double lambda_used;
+    double cost;
+    double new_cost;
+    long long n_valid;
+    long long n_valid_new;
+    int accepted;
+    int status;             // 0 or PBA_ENOTPD
+    int chol_fail;          // set by the factorisation
+    int pad;
+};
+
+// Assembly task: one 6x6 block of H (diagonal when a == b).
+struct AsmTask {
+    int a, b;               // frames (a <= b)
+    int contrib_begin, contrib_end;
+};
+
+// Contribution to an assembly task: pair index and the two roles (0 = i, 1 = j)
+// selecting the 6x6 sub-block (row role, column role) of the pair's H12.
+struct AsmContrib {
+    int pair;
+    int row_role, col_role;
+    int add_b;              // 1: also add the pair's b sub-vector of row_role (diagonal tasks)
+};
+
+}  // namespace pba
+
+// ---------------------------------------------------------------- launchers
+// (host-callable, defined in the .cu files; all asynchronous on `s`)
+
+namespace pba {
+
+cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors,
+                        const int* frame_ids, int n, int texel_precision, void* texels,
+                        float4* pts_pg, float4* pts_n, int* n_points, double range_min,
+                        double range_max, cudaStream_t s);
+
+cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
+                             PairPose* out, cudaStream_t s);
+
+cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const int4* chunks, int n_chunks,
+                             int* queue, const PairStatic* ps, const PairPose* pp, const float4* pts_pg,
+                             const float4* pts_n, const void* texels, const LinParams& prm,
+                             float* partials, uint32_t* mask_bits, int grid, cudaStream_t s);
+
+int linearize_grid(int texel_precision, bool full);
+
+cudaError_t launch_pair_reduce(const float* partials, const PairStatic* ps, const int2* pair_frames,
+                               const double* poses, const double* pair_Xo, int m, bool full,
+                               double* blocks, cudaStream_t s);
+
+cudaError_t launch_plain(bool full, int pair, const PairStatic* ps, const PairPose* pp, const float* raw,
+                         const SensorDev* sensors, int src_sensor, const LinParams& prm, double range_min,
+                         double range_max, float* acc, int width, int height, cudaStream_t s);
+
+cudaError_t launch_plain_expand(const float* acc, int m, bool full, double* blocks, cudaStream_t s);
+
+cudaError_t launch_assemble(const AsmTask* tasks, int n_tasks, const AsmContrib* contrib,
+                            const double* blocks, int n_frames, double* H, double* b, cudaStream_t s);
+
+cudaError_t launch_total_cost(const double* blocks, int m, LmState* st, bool candidate, cudaStream_t s);
+
+cudaError_t launch_lm_prepare(const double* H, int n_frames, LmState* st, double explicit_lambda,
+                              cudaStream_t s);
+
+cudaError_t launch_damp(const double* H, const double* b, int n_frames, int n_pad, const LmState* st,
+                        double* A, double* rhs, cudaStream_t s);
+
+cudaError_t launch_cholesky(double* A, int n_pad, LmState* st, cudaStream_t s, int* n_launches);
+
+cudaError_t launch_trsv(const double* A, int n_pad, double* rhs, const LmState* st, cudaStream_t s);
+
+cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const LmState* st,
+                           double* cand, cudaStream_t s);
+
+cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, cudaStream_t s);
+
+}  // namespace pba

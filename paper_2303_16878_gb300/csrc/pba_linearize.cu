@@ -1,0 +1,593 @@
+// pba_linearize.cu -- the batched photometric linearisation (hot path).
+//
+// k_pair_pose     FP64 poses -> FP32 per-pair transform pbar = M p_u + a with
+//                 M = R_o^T R_j^T R_i, a = R_o^T (R_j^T (t_i - t_j) - t_o)  (Supp., pbar_u; Eq. 4)
+// k_linearize     one persistent launch over a queue of chunks (pair, points);
+//                 per pixel-point: transform, project (Eq. 2 / Eq. 3), sample the
+//                 five target channels and their image gradients bilinearly from
+//                 the 12-texel central-difference stencil (Supp., image Jacobians),
+//                 residual e = zeta(pbar) - I_j(u') (Supp., Eq. error-jacobian),
+//                 Huber weight, Jacobian J_i, and accumulation of the 6x6
+//                 H6 = sum w J_i^T Omega J_i, b6 = sum w J_i^T Omega e, cost, count
+//                 in FP32 registers; warp shuffles + shared memory give one FP32
+//                 partial per chunk (no global atomics on residuals).
+// k_pair_reduce   FP64 sum of a pair's chunk partials in a fixed order, then the
+//                 pair's full 12x12 block from J_j = J_i T (see below).
+//
+// J_j from J_i.  With q = R_j^T (R_i p_u + t_i - t_j), R = R_j^T R_i and
+// t = R_j^T (t_i - t_j), the Supp. derivatives are
+//   d pbar / d dx_i = R_o^T R [I | -2 [p_u]x],   d pbar / d dx_j = R_o^T [-I | 2 [q]x],
+//   d nbar / d dq_i = R_o^T R (-2 [n^o]x),       d nbar / d dq_j = R_o^T 2 [R n^o]x,
+// and every one of them satisfies (d/d dx_j) = (d/d dx_i) T with the
+// point-independent 6x6 map
+//   T = [[-R^T, 2 R^T [t]x], [0, -R^T]]
+// (use [R p]x = R [p]x R^T).  Hence J_j = J_i T for every row, H_ij = H6 T,
+// H_jj = T^T H6 T and b_j = T^T b6: the kernel accumulates 21 + 6 sums instead
+// of 78 + 12, and the parity tests compare against the oracle's independently
+// computed J_j.
+//
+// In the i-frame form used below, J_c = [h_c, 2 p_u x h_c] with
+// h_c = M^T (d zeta_c / d pbar - grad I_c d pi / d pbar), plus, for the normal
+// rows c = 2 + k, 2 n^o x m_k in the rotation part (m_k = row k of M).
+#include "pba_internal.cuh"
+
+namespace pba {
+
+namespace {
+
+constexpr int kLinThreads = 256;
+constexpr int kLinWarps = kLinThreads / 32;
+
+// ------------------------------------------------------------ pair poses
+
+__global__ void k_pair_pose(const double* __restrict__ poses, const int2* __restrict__ pf,
+                            const double* __restrict__ pair_Xo, int m, PairPose* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const int2 ij = pf[p];
+    const double* Xi = poses + 12 * ij.x;
+    const double* Xj = poses + 12 * ij.y;
+    const double* Xo = pair_Xo + 12 * p;
+    double R[9], t[3];
+    // R = R_j^T R_i ; t = R_j^T (t_i - t_j)
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)
+            R[3 * r + c] = Xj[r] * Xi[c] + Xj[4 + r] * Xi[4 + c] + Xj[8 + r] * Xi[8 + c];
+        t[r] = Xj[r] * (Xi[3] - Xj[3]) + Xj[4 + r] * (Xi[7] - Xj[7]) + Xj[8 + r] * (Xi[11] - Xj[11]);
+    }
+    PairPose o;
+    // M = R_o^T R ; a = R_o^T (t - t_o)
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)
+            o.M[3 * r + c] = (float)(Xo[r] * R[c] + Xo[4 + r] * R[3 + c] + Xo[8 + r] * R[6 + c]);
+        o.a[r] = (float)(Xo[r] * (t[0] - Xo[3]) + Xo[4 + r] * (t[1] - Xo[7]) + Xo[8 + r] * (t[2] - Xo[11]));
+    }
+    out[p] = o;
+}
+
+// ------------------------------------------------------------ texel access
+
+struct Texel {
+    float d, g, nx, ny, nz;
+};
+
+template <int TEXEL>
+__device__ __forceinline__ Texel load_texel(const void* __restrict__ base, long long idx) {
+    Texel t;
+    if (TEXEL == 1) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + idx);
+        t.d = __uint_as_float(v.x);
+        __half2 a = *reinterpret_cast<const __half2*>(&v.y);
+        __half2 b = *reinterpret_cast<const __half2*>(&v.z);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        t.g = fa.x;
+        t.nx = fa.y;
+        t.ny = fb.x;
+        t.nz = fb.y;
+    } else {
+        const float4* p = reinterpret_cast<const float4*>(base) + 2 * idx;
+        const float4 v0 = __ldg(p);
+        const float v1 = __ldg(reinterpret_cast<const float*>(p + 1));
+        t.d = v0.x;
+        t.g = v0.y;
+        t.nx = v0.z;
+        t.ny = v0.w;
+        t.nz = v1;
+    }
+    return t;
+}
+
+// Channel sums: value, d/du, d/dv for the five channels (g, d, nx, ny, nz).
+struct Sample {
+    float v[5], gu[5], gv[5];
+};
+
+__device__ __forceinline__ void add_texel(Sample& s, const Texel& t, float cv, float cu, float cg) {
+    const float x[5] = {t.g, t.d, t.nx, t.ny, t.nz};
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        s.v[c] = fmaf(cv, x[c], s.v[c]);
+        s.gu[c] = fmaf(cu, x[c], s.gu[c]);
+        s.gv[c] = fmaf(cg, x[c], s.gv[c]);
+    }
+}
+
+// Bilinear sample at (u, v) of value and image gradient from the 4 x 4 stencil
+// minus corners.  Taps A (r0,c0), B (r0,c0+1), C (r0+1,c0), D (r0+1,c0+1).
+// grad_mode 0: the central differences of the Supp. at each tap, interpolated;
+// grad_mode 1: the exact derivative of the bilinear interpolant.
+// Returns false when any of the 12 stencil texels is invalid (d == 0).
+template <int TEXEL>
+__device__ __forceinline__ bool sample_stencil(const void* __restrict__ tex, long long base, int W, bool wrap,
+                                               int r0, int c0, float a, float b, int grad_mode, Sample& s) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) s.v[c] = s.gu[c] = s.gv[c] = 0.f;
+    int cm1 = c0 - 1, cp1 = c0 + 1, cp2 = c0 + 2, cc = c0;
+    if (wrap) {
+        cc = c0 % W;
+        if (cc < 0) cc += W;
+        cm1 = cc == 0 ? W - 1 : cc - 1;
+        cp1 = cc == W - 1 ? 0 : cc + 1;
+        cp2 = cp1 == W - 1 ? 0 : cp1 + 1;
+    }
+    const long long rm1 = base + (long long)(r0 - 1) * W, rr0 = base + (long long)r0 * W;
+    const long long rp1 = rr0 + W, rp2 = rp1 + W;
+    const float wA = (1.f - a) * (1.f - b), wB = a * (1.f - b), wC = (1.f - a) * b, wD = a * b;
+    const float hA = 0.5f * wA, hB = 0.5f * wB, hC = 0.5f * wC, hD = 0.5f * wD;
+    bool ok = true;
+    Texel t;
+    if (grad_mode == 0) {
+        // row r0 - 1
+        t = load_texel<TEXEL>(tex, rm1 + cc);   ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, -hA);
+        t = load_texel<TEXEL>(tex, rm1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, -hB);
+        // row r0
+        t = load_texel<TEXEL>(tex, rr0 + cm1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, -hA, 0.f);
+        t = load_texel<TEXEL>(tex, rr0 + cc);   ok &= t.d > 0.f; add_texel(s, t, wA, -hB, -hC);
+        t = load_texel<TEXEL>(tex, rr0 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wB, hA, -hD);
+        t = load_texel<TEXEL>(tex, rr0 + cp2);  ok &= t.d > 0.f; add_texel(s, t, 0.f, hB, 0.f);
+        // row r0 + 1
+        t = load_texel<TEXEL>(tex, rp1 + cm1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, -hC, 0.f);
+        t = load_texel<TEXEL>(tex, rp1 + cc);   ok &= t.d > 0.f; add_texel(s, t, wC, -hD, hA);
+        t = load_texel<TEXEL>(tex, rp1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wD, hC, hB);
+        t = load_texel<TEXEL>(tex, rp1 + cp2);  ok &= t.d > 0.f; add_texel(s, t, 0.f, hD, 0.f);
+        // row r0 + 2
+        t = load_texel<TEXEL>(tex, rp2 + cc);   ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, hC);
+        t = load_texel<TEXEL>(tex, rp2 + cp1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, hD);
+    } else {
+        // exact derivative of the bilinear interpolant: only the taps carry weight,
+        // but the stencil texels still decide usability
+        t = load_texel<TEXEL>(tex, rm1 + cc);   ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rm1 + cp1);  ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rr0 + cm1);  ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rr0 + cc);   ok &= t.d > 0.f; add_texel(s, t, wA, -(1.f - b), -(1.f - a));
+        t = load_texel<TEXEL>(tex, rr0 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wB, (1.f - b), -a);
+        t = load_texel<TEXEL>(tex, rr0 + cp2);  ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rp1 + cm1);  ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rp1 + cc);   ok &= t.d > 0.f; add_texel(s, t, wC, -b, (1.f - a));
+        t = load_texel<TEXEL>(tex, rp1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wD, b, a);
+        t = load_texel<TEXEL>(tex, rp1 + cp2);  ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rp2 + cc);   ok &= t.d > 0.f;
+        t = load_texel<TEXEL>(tex, rp2 + cp1);  ok &= t.d > 0.f;
+    }
+    return ok;
+}
+
+// H6 (upper triangle, row-major 21) += s * J J^T ; b6 += s * J e
+__device__ __forceinline__ void accum_row(float (&H)[21], float (&bb)[6], const float (&J)[6], float sw, float e) {
+    float t[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) t[a] = sw * J[a];
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+#pragma unroll
+        for (int c = a; c < 6; ++c) {
+            H[k] = fmaf(t[a], J[c], H[k]);
+            ++k;
+        }
+        bb[a] = fmaf(t[a], e, bb[a]);
+    }
+}
+
+// J = [h, 2 p x h] (+ [0, extra] for the normal rows)
+__device__ __forceinline__ void make_row(float (&J)[6], const float (&h)[3], const float4& p) {
+    J[0] = h[0];
+    J[1] = h[1];
+    J[2] = h[2];
+    J[3] = 2.f * (p.y * h[2] - p.z * h[1]);
+    J[4] = 2.f * (p.z * h[0] - p.x * h[2]);
+    J[5] = 2.f * (p.x * h[1] - p.y * h[0]);
+}
+
+constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two >= 63)
+constexpr int kQItems = 20;  // floats per queued residual: e[5], dI/du[5], dI/dv[5], w, pbar[3], point index
+
+// a6 + a7 for one queued residual: d pi / d pbar, the 5 x 6 Jacobian J_i and its
+// Huber-weighted accumulation into H6 (upper triangle) and b6.
+__device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int model, float fx, float fy,
+                                               const float (&M)[9], const float (&om)[5],
+                                               const float4* __restrict__ pg, const float4* __restrict__ pn,
+                                               float (&Hacc)[21], float (&bacc)[6]) {
+    float e[5], gu[5], gv[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        e[c] = Q[c][slot];
+        gu[c] = Q[5 + c][slot];
+        gv[c] = Q[10 + c][slot];
+    }
+    const float w = Q[15][slot];
+    const float qx = Q[16][slot], qy = Q[17][slot], qz = Q[18][slot];
+    const int k = __float_as_int(Q[19][slot]);
+    const float4 p = __ldg(pg + k);
+    const float4 n = __ldg(pn + k);
+    // d pi / d pbar (2 x 3) and d zeta^d / d pbar
+    float P0[3], P1[3], dz[3];
+    if (model == 0) {
+        const float iz = 1.f / qz;
+        P0[0] = fx * iz; P0[1] = 0.f; P0[2] = -fx * qx * iz * iz;
+        P1[0] = 0.f; P1[1] = fy * iz; P1[2] = -fy * qy * iz * iz;
+        dz[0] = 0.f; dz[1] = 0.f; dz[2] = 1.f;
+    } else {
+        const float rxy2 = fmaf(qx, qx, qy * qy);
+        const float irxy2 = 1.f / rxy2;
+        const float rxy = sqrtf(rxy2);
+        const float inv_r = rsqrtf(fmaf(qz, qz, rxy2));
+        const float ir2 = inv_r * inv_r;
+        P0[0] = -fx * qy * irxy2; P0[1] = fx * qx * irxy2; P0[2] = 0.f;
+        const float k1 = -fy * qz * ir2 / rxy;
+        P1[0] = k1 * qx; P1[1] = k1 * qy; P1[2] = fy * rxy * ir2;
+        dz[0] = qx * inv_r; dz[1] = qy * inv_r; dz[2] = qz * inv_r;
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        // g_c = d zeta_c / d pbar - grad I_c d pi / d pbar
+        float g[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a] = -fmaf(gu[c], P0[a], gv[c] * P1[a]);
+            if (c == 1) g[a] += dz[a];
+        }
+        // h_c = M^T g_c
+        float h[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a] = fmaf(M[a], g[0], fmaf(M[3 + a], g[1], M[6 + a] * g[2]));
+        float J[6];
+        make_row(J, h, p);
+        if (c >= 2) {
+            // + 2 n^o x m_k, m_k = row k of M
+            const int r = c - 2;
+            const float mx = M[3 * r], my = M[3 * r + 1], mz = M[3 * r + 2];
+            J[3] += 2.f * (n.y * mz - n.z * my);
+            J[4] += 2.f * (n.z * mx - n.x * mz);
+            J[5] += 2.f * (n.x * my - n.y * mx);
+        }
+        accum_row(Hacc, bacc, J, w * om[c], e[c]);
+    }
+}
+
+template <int TEXEL, bool FULL, bool MASK>
+__global__ void __launch_bounds__(kLinThreads, 2)
+    k_linearize(const int4* __restrict__ chunks, int n_chunks, int* __restrict__ queue,
+                const PairStatic* __restrict__ ps, const PairPose* __restrict__ pp,
+                const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
+                const void* __restrict__ tex, const LinParams prm, float* __restrict__ partials,
+                uint32_t* __restrict__ mask_bits) {
+    __shared__ int s_chunk;
+    __shared__ float s_red[kLinWarps][kNumAcc];
+    __shared__ float s_q[kLinWarps][kQItems][kQueue];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float om[5] = {prm.w_int, prm.w_depth, prm.w_normal, prm.w_normal, prm.w_normal};
+
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(queue, 1);
+        __syncthreads();
+        const int ci = s_chunk;
+        __syncthreads();
+        if (ci >= n_chunks) break;
+        const int4 ch = __ldg(chunks + ci);
+        const int pair = ch.x, first = ch.y, count = ch.z;
+        const PairStatic& P = ps[pair];
+        const int W = P.width, Hh = P.height, model = P.model;
+        const float fx = P.fx, fy = P.fy, cx = P.cx, cy = P.cy;
+        const long long pt_off = P.src_pt_offset, tex_off = P.tgt_px_offset;
+        float M[9], av[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) M[k] = pp[pair].M[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) av[k] = pp[pair].a[k];
+        const bool wrap = model == 1;
+        const float umax = wrap ? 3.4e38f : (float)(W - 2);
+        const float vmax = (float)(Hh - 2);
+
+        float Hacc[21], bacc[6], cost = 0.f, cnt = 0.f;
+        if (FULL) {
+#pragma unroll
+            for (int k = 0; k < 21; ++k) Hacc[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) bacc[k] = 0.f;
+        }
+
+        // Residuals that pass every test wait in this warp's queue until 32 of
+        // them are ready; the Jacobian stage then runs on full warps only.
+        float(*Q)[kQueue] = s_q[warp];
+        int head = 0, tail = 0;  // warp-uniform ring-buffer counters
+        const int end = first + count;
+        for (int base = first + warp * 32; base < end; base += kLinThreads) {
+            const int k = base + lane;
+            bool valid = false;
+            float e[5], gu[5], gv[5], w = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
+            if (k < end) {
+                const float4 p = __ldg(pts_pg + pt_off + k);
+                // a2: pbar = M p_u + a
+                qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
+                qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));
+                qz = fmaf(M[6], p.x, fmaf(M[7], p.y, fmaf(M[8], p.z, av[2])));
+                // a3: projection and validity
+                float u, v, zeta_d;
+                bool ok;
+                if (model == 0) {
+                    ok = qz > prm.z_min;
+                    const float iz = 1.f / qz;
+                    u = fmaf(fx * qx, iz, cx);
+                    v = fmaf(fy * qy, iz, cy);
+                    zeta_d = qz;
+                } else {
+                    const float rxy2 = fmaf(qx, qx, qy * qy);
+                    zeta_d = sqrtf(fmaf(qz, qz, rxy2));
+                    ok = zeta_d > prm.z_min;
+                    u = fmaf(fx, atan2f(qy, qx), cx);
+                    v = fmaf(fy, atan2f(qz, sqrtf(rxy2)), cy);
+                }
+                ok = ok && v >= 1.f && v < vmax && u >= (wrap ? -3.4e38f : 1.f) && u < umax;
+                if (ok) {
+                    const float fu = floorf(u), fv = floorf(v);
+                    const int c0 = (int)fu, r0 = (int)fv;
+                    Sample s;
+                    // a4: bilinear sample of value and gradient
+                    ok = sample_stencil<TEXEL>(tex, tex_off, W, wrap, r0, c0, u - fu, v - fv, prm.grad_mode, s);
+                    // a5: residual, occlusion test, Huber
+                    const float e_d = zeta_d - s.v[1];
+                    ok = ok && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
+                    const float nt2 = fmaf(s.v[2], s.v[2], fmaf(s.v[3], s.v[3], s.v[4] * s.v[4]));
+                    ok = ok && nt2 >= 0.25f;
+                    if (ok) {
+                        valid = true;
+                        const float4 n = __ldg(pts_n + pt_off + k);
+                        const float nbx = fmaf(M[0], n.x, fmaf(M[1], n.y, M[2] * n.z));
+                        const float nby = fmaf(M[3], n.x, fmaf(M[4], n.y, M[5] * n.z));
+                        const float nbz = fmaf(M[6], n.x, fmaf(M[7], n.y, M[8] * n.z));
+                        e[0] = p.w - s.v[0];
+                        e[1] = e_d;
+                        e[2] = nbx - s.v[2];
+                        e[3] = nby - s.v[3];
+                        e[4] = nbz - s.v[4];
+                        float chi2 = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
+                        float rho;
+                        if (chi2 <= prm.huber_delta2) {
+                            w = 1.f;
+                            rho = chi2;
+                        } else {
+                            const float chi = sqrtf(chi2);
+                            w = prm.huber_delta / chi;
+                            rho = fmaf(2.f * prm.huber_delta, chi, -prm.huber_delta2);
+                        }
+                        cost += rho;
+                        cnt += 1.f;
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) {
+                            gu[c] = s.gu[c];
+                            gv[c] = s.gv[c];
+                        }
+                    }
+                }
+            }
+            if (MASK) {
+                const unsigned bits = __ballot_sync(0xffffffffu, valid);
+                if (lane == 0) mask_bits[P.mask_offset + (base >> 5)] = bits;
+            }
+            if (FULL) {
+                const unsigned bal = __ballot_sync(0xffffffffu, valid);
+                if (valid) {
+                    const int slot = (tail + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        Q[c][slot] = e[c];
+                        Q[5 + c][slot] = gu[c];
+                        Q[10 + c][slot] = gv[c];
+                    }
+                    Q[15][slot] = w;
+                    Q[16][slot] = qx;
+                    Q[17][slot] = qy;
+                    Q[18][slot] = qz;
+                    Q[19][slot] = __int_as_float(k);
+                }
+                tail += __popc(bal);
+                __syncwarp();
+                if (tail - head >= 32) {
+                    jacobian_stage(Q, (head + lane) & (kQueue - 1), model, fx, fy, M, om, pts_pg + pt_off,
+                                   pts_n + pt_off, Hacc, bacc);
+                    head += 32;
+                    __syncwarp();
+                }
+            }
+        }
+        if (FULL && tail > head) {
+            if (lane < tail - head)
+                jacobian_stage(Q, (head + lane) & (kQueue - 1), model, fx, fy, M, om, pts_pg + pt_off,
+                               pts_n + pt_off, Hacc, bacc);
+            __syncwarp();
+        }
+
+        // a7: chunk reduction (warp shuffle, then shared memory), one FP32 partial per chunk
+        float acc[kNumAcc];
+        if (FULL) {
+#pragma unroll
+            for (int k = 0; k < 21; ++k) acc[k] = Hacc[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[21 + k] = bacc[k];
+        }
+        acc[27] = cost;
+        acc[28] = cnt;
+        const int k0 = FULL ? 0 : 27;
+#pragma unroll
+        for (int k = k0; k < kNumAcc; ++k) {
+            float x = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) s_red[warp][k] = x;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x >= k0 && threadIdx.x < kNumAcc) {
+            float x = 0.f;
+#pragma unroll
+            for (int w8 = 0; w8 < kLinWarps; ++w8) x += s_red[w8][threadIdx.x];
+            partials[(long long)ci * kPartialStride + threadIdx.x] = x;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ pair reduction
+
+__global__ void k_pair_reduce(const float* __restrict__ partials, const PairStatic* __restrict__ ps,
+                              const int2* __restrict__ pf, const double* __restrict__ poses, bool full,
+                              double* __restrict__ blocks) {
+    const int p = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ double acc[kNumAcc + 3];
+    __shared__ double H6[36], T[36], HT[36];
+    const PairStatic P = ps[p];
+    const int k0 = full ? 0 : 27;
+    if (t >= k0 && t < kNumAcc) {
+        double s = 0.0;
+        for (int c = P.chunk_begin; c < P.chunk_end; ++c) s += (double)partials[(long long)c * kPartialStride + t];
+        acc[t] = s;
+    }
+    __syncthreads();
+    double* out = blocks + (long long)p * kBlockStride;
+    if (!full) {
+        if (t == 0) {
+            out[156] = acc[27];
+            out[157] = acc[28];
+        }
+        return;
+    }
+    if (t < 36) {
+        const int r = t / 6, c = t % 6;
+        const int a = r < c ? r : c, bb = r < c ? c : r;
+        // index of (a, bb) in the row-major upper triangle
+        const int idx = a * 6 - a * (a - 1) / 2 + (bb - a);
+        H6[t] = acc[idx];
+        // T = [[-R^T, 2 R^T [t]x], [0, -R^T]],  R = R_j^T R_i, t = R_j^T (t_i - t_j)
+        const int2 ij = pf[p];
+        const double* Xi = poses + 12 * ij.x;
+        const double* Xj = poses + 12 * ij.y;
+        double R[9], tv[3];
+        for (int rr = 0; rr < 3; ++rr) {
+            for (int cc = 0; cc < 3; ++cc)
+                R[3 * rr + cc] = Xj[rr] * Xi[cc] + Xj[4 + rr] * Xi[4 + cc] + Xj[8 + rr] * Xi[8 + cc];
+            tv[rr] = Xj[rr] * (Xi[3] - Xj[3]) + Xj[4 + rr] * (Xi[7] - Xj[7]) + Xj[8 + rr] * (Xi[11] - Xj[11]);
+        }
+        double val = 0.0;
+        if (r < 3 && c < 3) {
+            val = -R[3 * c + r];
+        } else if (r < 3 && c >= 3) {
+            // (2 R^T [t]x)[r][c-3] = 2 sum_k R[k][r] [t]x[k][c-3]
+            const double S[9] = {0.0, -tv[2], tv[1], tv[2], 0.0, -tv[0], -tv[1], tv[0], 0.0};
+            for (int k = 0; k < 3; ++k) val += 2.0 * R[3 * k + r] * S[3 * k + (c - 3)];
+        } else if (r >= 3 && c >= 3) {
+            val = -R[3 * (c - 3) + (r - 3)];
+        }
+        T[t] = val;
+    }
+    __syncthreads();
+    if (t < 36) {
+        const int r = t / 6, c = t % 6;
+        double s = 0.0;
+        for (int k = 0; k < 6; ++k) s += H6[6 * r + k] * T[6 * k + c];
+        HT[t] = s;  // H_ij = H6 T
+    }
+    __syncthreads();
+    if (t < 36) {
+        const int r = t / 6, c = t % 6;
+        out[12 * r + c] = H6[t];                 // H_ii
+        out[12 * r + 6 + c] = HT[t];             // H_ij
+        out[12 * (6 + c) + r] = HT[t];           // H_ji = H_ij^T
+        if (r <= c) {
+            // H_jj = T^T H6 T, computed once per unordered entry so it is exactly symmetric
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += T[6 * k + r] * HT[6 * k + c];
+            out[12 * (6 + r) + 6 + c] = s;
+            out[12 * (6 + c) + 6 + r] = s;
+        }
+    }
+    if (t < 6) {
+        out[144 + t] = acc[21 + t];              // b_i = b6
+        double s = 0.0;
+        for (int k = 0; k < 6; ++k) s += T[6 * k + t] * acc[21 + k];
+        out[150 + t] = s;                        // b_j = T^T b6
+    }
+    if (t == 0) {
+        out[156] = acc[27];
+        out[157] = acc[28];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
+                             PairPose* out, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    k_pair_pose<<<(m + 127) / 128, 128, 0, s>>>(poses, pair_frames, pair_Xo, m, out);
+    return cudaGetLastError();
+}
+
+template <int TEXEL, bool FULL, bool MASK>
+static void* lin_kernel() {
+    return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK>);
+}
+
+static void* pick(int texel_precision, bool full, bool mask) {
+    if (texel_precision == 1) {
+        if (full) return mask ? lin_kernel<1, true, true>() : lin_kernel<1, true, false>();
+        return mask ? lin_kernel<1, false, true>() : lin_kernel<1, false, false>();
+    }
+    if (full) return mask ? lin_kernel<0, true, true>() : lin_kernel<0, true, false>();
+    return mask ? lin_kernel<0, false, true>() : lin_kernel<0, false, false>();
+}
+
+int linearize_grid(int texel_precision, bool full) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pick(texel_precision, full, false),
+                                                  kLinThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const int4* chunks, int n_chunks, int* queue,
+                             const PairStatic* ps, const PairPose* pp, const float4* pts_pg, const float4* pts_n,
+                             const void* texels, const LinParams& prm, float* partials, uint32_t* mask_bits,
+                             int grid, cudaStream_t s) {
+    if (n_chunks <= 0) return cudaSuccess;
+    if (grid > n_chunks) grid = n_chunks;
+    void* fn = pick(texel_precision, full, mask);
+    LinParams prm_copy = prm;
+    void* args[] = {(void*)&chunks, (void*)&n_chunks, (void*)&queue, (void*)&ps, (void*)&pp, (void*)&pts_pg,
+                    (void*)&pts_n, (void*)&texels, (void*)&prm_copy, (void*)&partials, (void*)&mask_bits};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kLinThreads), args, 0, s);
+}
+
+cudaError_t launch_pair_reduce(const float* partials, const PairStatic* ps, const int2* pair_frames,
+                               const double* poses, const double* pair_Xo, int m, bool full, double* blocks,
+                               cudaStream_t s) {
+    (void)pair_Xo;
+    if (m <= 0) return cudaSuccess;
+    k_pair_reduce<<<m, 64, 0, s>>>(partials, ps, pair_frames, poses, full, blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace pba

@@ -1,0 +1,273 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars (relative Frobenius norms unless stated): H and b <= 1e-4, total cost
+<= 1e-5, converged poses <= 1e-4 m and <= 1e-5 rad; valid-residual masks
+bit-exact on every point whose validity decisions are not within the oracle's
+float32 decision margin (flagged points), with at most 1e-5 of the residuals
+(+2) disagreeing at all.
+"""
+import numpy as np
+import pytest
+
+from conftest import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_H = 1e-4
+TOL_B = 1e-4
+TOL_COST = 1e-5
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def make(w, path, texel, params=None, poses=None):
+    import paper_2303_16878_gb300 as pba
+    gpu()
+    return pba.problem_from_workload(w, path=path, texel=texel, params=params, poses=poses)
+
+
+CASES = [
+    ("batched", 1, 0), ("batched", 0, 0), ("batched", 1, 1), ("batched", 0, 1),
+    ("plain", 0, 0), ("plain", 0, 1),
+]
+
+
+def _path(name):
+    import paper_2303_16878_gb300 as pba
+    return pba.PBA_PATH_BATCHED if name == "batched" else pba.PBA_PATH_PLAIN
+
+
+@pytest.mark.parametrize("path,texel,grad_mode", CASES)
+@pytest.mark.parametrize("which", ["room8", "street3"])
+def test_system_matches_oracle(oracle_lib, which, path, texel, grad_mode, request):
+    w = request.getfixturevalue(which)
+    params = dict(w.params, grad_mode=grad_mode)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, params,
+                               want_pairs=True)
+    p = make(w, _path(path), texel, params={"grad_mode": grad_mode})
+    cost, count = p.linearize()
+    H, b = p.get_system()
+    ps = p.get_pair_system()
+    assert abs(count - ref["count"]) <= 1e-5 * ref["count"] + 2
+    assert abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+    assert rel(H, ref["H"]) <= TOL_H
+    assert rel(b, ref["b"]) <= TOL_B
+    assert rel(ps["H"], ref["pair_H"]) <= TOL_H
+    assert rel(ps["b"], ref["pair_b"]) <= TOL_B
+    assert np.abs(ps["count"] - ref["pair_count"]).max() <= 2
+    p.close()
+
+
+@pytest.mark.parametrize("texel", [0, 1])
+@pytest.mark.parametrize("which", ["room8", "street3"])
+def test_valid_mask_bit_exact_outside_decision_margin(oracle_lib, which, texel, request):
+    import paper_2303_16878_gb300 as pba
+    w = request.getfixturevalue(which)
+    p = make(w, pba.PBA_PATH_BATCHED, texel)
+    p.set_mask_export(True)
+    p.linearize()
+    total, disagree = 0, 0
+    for q, (i, j) in enumerate(w.pairs.tolist()):
+        r = oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], w.poses_init[i],
+                                      w.poses_init[j])
+        assert p.frame_points(i) == r["n_points"]
+        m = p.get_mask(q, r["n_points"])
+        diff = m ^ r["mask"]
+        assert not np.any(diff & ~r["flags"]), f"pair {q}: mask differs on unflagged points"
+        disagree += int(sum(bin(int(x)).count("1") for x in diff))
+        total += r["count"]
+    assert disagree <= 1e-5 * total + 2
+    p.close()
+
+
+def test_full_size_lidar_street_sampled_pairs(oracle_lib):
+    """50 frames of 64 x 1024 with every overlapping pair in one persistent
+    launch (the benchmark's configuration); the oracle recomputes a seeded
+    sample of pairs one by one, and the whole system is checked for the
+    properties that hold at any size."""
+    import paper_2303_16878_gb300 as pba
+    import oracle_pins
+    w = workload("street")
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    cost, count = p.linearize()
+    H, b = p.get_system()
+    ps = p.get_pair_system()
+    rng = np.random.default_rng(5)
+    sample = rng.choice(len(w.pairs), size=8, replace=False)
+    for q in sample:
+        i, j = w.pairs[q]
+        r = oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], w.poses_init[i],
+                                      w.poses_init[j])
+        assert abs(ps["count"][q] - r["count"]) <= 2
+        assert abs(ps["cost"][q] - r["cost"]) <= 1e-4 * r["cost"] + 1e-9
+        assert rel(ps["H"][q], r["H"]) <= TOL_H
+        assert rel(ps["b"][q], r["b"]) <= TOL_B
+    assert count == int(ps["count"].sum())
+    assert abs(cost - ps["cost"].sum()) <= 1e-9 * cost
+    np.testing.assert_array_equal(H, H.T)
+    V = oracle_pins.gauge_directions(w.poses_init)
+    assert np.linalg.norm(H @ V) <= 1e-6 * np.linalg.norm(H) * np.linalg.norm(V)
+    p.close()
+
+
+def test_damped_step_matches_oracle(oracle_lib, room8):
+    """A strongly damped step is well conditioned, so its dx is fixed to the
+    accuracy of H and b; compare the updated poses."""
+    import paper_2303_16878_gb300 as pba
+    w = room8
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
+    lam = 10.0 * float(np.diag(ref["H"])[6:].max())
+    dx, ok = oracle_lib.solve_step(ref["H"], ref["b"], lam)
+    cand = oracle_lib.apply_update(w.poses_init, dx)
+    new = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False)
+    assert ok and new["cost"] < ref["cost"]
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    p.linearize()
+    st = p.solve_step(lam)
+    assert st["accepted"] and st["status"] == 0
+    assert abs(st["new_cost"] - new["cost"]) <= TOL_COST * new["cost"]
+    got = p.get_poses()
+    step_ref = np.abs(cand - w.poses_init).max()
+    assert np.abs(got - cand).max() <= 1e-4 * step_ref + 1e-12
+    p.close()
+
+
+def test_lm_converges_to_oracle_poses(oracle_lib):
+    """Ten LM iterations from the same start: GPU (device-side lambda schedule,
+    captured graph) and oracle reach the same poses within 1e-4 m / 1e-5 rad."""
+    import paper_2303_16878_gb300 as pba
+    w = workload("room", n_frames=4, width=80, height=60, f=60.0)
+    poses, lam = w.poses_init.copy(), None
+    for _ in range(10):
+        o = oracle_lib.lm_iteration(w, poses, lam)
+        poses, lam = o["poses"], o["lam"]
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    for _ in range(10):
+        p.iterate()
+    got = p.get_poses()
+    for k in range(w.n_frames):
+        assert np.linalg.norm(got[k][:, 3] - poses[k][:, 3]) <= 1e-4
+        R = got[k][:, :3].T @ poses[k][:, :3]
+        ang = np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1))
+        assert ang <= 1e-5
+    p.close()
+
+
+def test_graph_iteration_equals_explicit_calls(room8):
+    """pba_iterate (captured graph, device lambda) and pba_linearize +
+    pba_solve_step with the same lambda give bitwise identical results."""
+    import paper_2303_16878_gb300 as pba
+    a = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    b = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    sa = a.iterate()
+    cost, _ = b.linearize()
+    sb = b.solve_step(sa["lambda_used"])
+    assert sa["cost"] == cost and sa["new_cost"] == sb["new_cost"] and sa["accepted"] == sb["accepted"]
+    np.testing.assert_array_equal(a.get_poses(), b.get_poses())
+    a.close()
+    b.close()
+
+
+def test_linearize_is_deterministic(room8):
+    import paper_2303_16878_gb300 as pba
+    p = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    p.linearize()
+    H1, b1 = p.get_system()
+    p.linearize()
+    H2, b2 = p.get_system()
+    np.testing.assert_array_equal(H1, H2)
+    np.testing.assert_array_equal(b1, b2)
+    p.close()
+
+
+def test_plain_and_batched_agree(room8):
+    import paper_2303_16878_gb300 as pba
+    a = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    b = make(room8, pba.PBA_PATH_PLAIN, pba.PBA_TEXEL_F32)
+    ca, na = a.linearize()
+    cb, nb = b.linearize()
+    Ha, ba = a.get_system()
+    Hb, bb = b.get_system()
+    assert abs(na - nb) <= 2
+    assert rel(Ha, Hb) <= TOL_H and rel(ba, bb) <= TOL_B
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_self_pair_and_empty_frames(oracle_lib):
+    """A self pair (i, i) at equal poses gives zero error; a frame without a
+    single valid pixel yields no residuals and zero blocks; a pair that sees
+    nothing of its target contributes nothing."""
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import synth
+    base = workload("room", n_frames=3)
+    chans = [c.copy() for c in base.channels]
+    chans[2][..., 1] = 0.0  # frame 2: no valid pixel
+    far = base.poses_init.copy()
+    far[1][:, 3] += np.array([0.0, 0.0, -50.0])  # frame 1 far away: nothing projects into frame 0
+    pairs = np.array([[0, 0], [2, 0], [0, 2], [1, 0]], dtype=np.int32)
+    w = synth.Workload("edge", base.sensors, base.frame_sensor, chans, base.poses_gt, far, pairs, base.params)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params,
+                               want_pairs=True)
+    for texel in (0, 1):
+        p = make(w, pba.PBA_PATH_BATCHED, texel)
+        assert p.frame_points(2) == 0
+        cost, count = p.linearize()
+        H, b = p.get_system()
+        ps = p.get_pair_system()
+        assert ps["count"][0] > 0.9 * p.frame_points(0) and ps["cost"][0] < 1e-9
+        assert ps["count"][1] == 0 and ps["count"][2] == 0 and np.all(ps["H"][1] == 0) and np.all(ps["H"][2] == 0)
+        assert ps["count"][3] == ref["pair_count"][3]
+        assert count == ref["count"]
+        assert rel(H, ref["H"]) <= TOL_H
+        p.close()
+
+
+def test_single_frame_problem():
+    """N = 1: the gauge-fixed system is empty; the step keeps the pose."""
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import synth
+    base = workload("room", n_frames=3)
+    w = synth.Workload("one", base.sensors, base.frame_sensor[:1], base.channels[:1], base.poses_gt[:1],
+                       base.poses_init[:1], np.array([[0, 0]], dtype=np.int32), base.params)
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    st = p.iterate()
+    assert st["status"] == 0
+    np.testing.assert_array_equal(p.get_poses(), w.poses_init)
+    p.close()
+
+
+def test_invalid_arguments_fail_loudly():
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import synth
+    gpu()
+    base = workload("room", n_frames=3)
+    s2 = synth.pinhole_sensor(80, 60, 60.0, 40.0, 30.0)
+    p = pba.Problem([base.sensors[0], s2], 3, base.params, frame_sensor=[0, 0, 1])
+    with pytest.raises(pba.PbaError) as e:
+        p.linearize()
+    assert e.value.code == pba._lib.PBA_ENOTREADY
+    p.upload_frames(0, np.stack(base.channels[:2]))
+    with pytest.raises(ValueError):
+        p.upload_frames(2, base.channels[2])  # 160 x 120 image for an 80 x 60 sensor
+    p.upload_frames(2, np.zeros((60, 80, 5), dtype=np.float32))
+    p.set_poses(base.poses_init)
+    with pytest.raises(pba.PbaError) as e:
+        p.set_pairs([[0, 2]])  # different sensors
+    assert e.value.code == pba._lib.PBA_EINVAL
+    with pytest.raises(pba.PbaError) as e:
+        p.set_pairs([[0, 7]])
+    assert e.value.code == pba._lib.PBA_EINVAL
+    p.close()
