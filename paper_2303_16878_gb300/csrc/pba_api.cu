@@ -17,7 +17,7 @@ using namespace pba;
 
 namespace {
 
-constexpr int kChunk = 2048;  // points per work item of the persistent launch
+constexpr int kChunk = 1024;  // points per work item (one warp) of the persistent launch
 
 }  // namespace
 

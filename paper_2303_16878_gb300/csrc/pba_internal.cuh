@@ -2,14 +2,16 @@
 //
 // Layout in HBM (one problem):
 //   raw       FP32 H x W x 5 per frame (the uploaded cue images, kept for the plain path)
-//   texels    per frame H x W sampling texels: Tex16 {float d; half g, nx, ny, nz; pad}
-//             or Tex32 {float d, g, nx, ny, nz, pad x 3}; d = 0 marks an invalid pixel
+//   texels    per frame H x W sampling texels: Tex16 {float d; half g, nx, ny, nz; usable}
+//             or Tex32 {float d, g, nx, ny, nz, usable, pad x 2}; d = 0 marks an invalid
+//             pixel, usable = pixel and its 4 neighbours valid
 //   points    per frame, compacted valid pixels in raster order:
 //             pg = float4(p_u, g_u), pn = float4(n_u^o, 0)   (Supp., p_u = R_o pi^-1(u, d) + t_o)
 //   pair pose table (FP32, per iteration): pbar = M p_u + a with M = R_o^T R_j^T R_i,
 //             a = R_o^T (R_j^T (t_i - t_j) - t_o)   (Supp., pbar_u)
 //   chunk list int4 {pair, first point, count, 0}: the persistent launch's work queue
-//   partials  FP32 per chunk: 21 (H6 upper) + 6 (b6) + cost + count (+3 pad) = 32 floats
+//   partials  FP32 per chunk (one warp's work item): 21 (H6 upper) + 6 (b6) + cost + count
+//             (+3 pad) = 32 floats
 //   pair blocks FP64 per pair: H12 (144) + b12 (12) + cost + count (+2 pad) = 160 doubles
 //   H (6N x 6N) and b (6N) FP64 dense; A = H_ff + lambda I padded to a multiple of 32
 #pragma once
@@ -58,15 +60,18 @@ struct PairPose {
     float a[3];
 };
 
+// usable = the pixel and its 4 neighbours are valid (central differences defined)
 struct Tex16 {
     float d;
     __half2 g_nx;
     __half2 ny_nz;
-    float pad;
+    unsigned usable;
 };
 
 struct Tex32 {
-    float d, g, nx, ny, nz, p0, p1, p2;
+    float d, g, nx, ny, nz;
+    unsigned usable;
+    float p1, p2;
 };
 
 struct LinParams {

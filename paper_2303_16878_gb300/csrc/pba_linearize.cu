@@ -9,8 +9,8 @@
 //                 residual e = zeta(pbar) - I_j(u') (Supp., Eq. error-jacobian),
 //                 Huber weight, Jacobian J_i, and accumulation of the 6x6
 //                 H6 = sum w J_i^T Omega J_i, b6 = sum w J_i^T Omega e, cost, count
-//                 in FP32 registers; warp shuffles + shared memory give one FP32
-//                 partial per chunk (no global atomics on residuals).
+//                 in FP32 registers; warp shuffles give one FP32 partial per
+//                 work item (no global atomics on residuals).
 // k_pair_reduce   FP64 sum of a pair's chunk partials in a fixed order, then the
 //                 pair's full 12x12 block from J_j = J_i T (see below).
 //
@@ -69,6 +69,7 @@ __global__ void k_pair_pose(const double* __restrict__ poses, const int2* __rest
 
 struct Texel {
     float d, g, nx, ny, nz;
+    bool usable;
 };
 
 template <int TEXEL>
@@ -84,92 +85,45 @@ __device__ __forceinline__ Texel load_texel(const void* __restrict__ base, long 
         t.nx = fa.y;
         t.ny = fb.x;
         t.nz = fb.y;
+        t.usable = v.w != 0u;
     } else {
         const float4* p = reinterpret_cast<const float4*>(base) + 2 * idx;
         const float4 v0 = __ldg(p);
-        const float v1 = __ldg(reinterpret_cast<const float*>(p + 1));
+        const float2 v1 = __ldg(reinterpret_cast<const float2*>(p + 1));
         t.d = v0.x;
         t.g = v0.y;
         t.nx = v0.z;
         t.ny = v0.w;
-        t.nz = v1;
+        t.nz = v1.x;
+        t.usable = __float_as_uint(v1.y) != 0u;
     }
     return t;
 }
 
-// Channel sums: value, d/du, d/dv for the five channels (g, d, nx, ny, nz).
-struct Sample {
-    float v[5], gu[5], gv[5];
-};
-
-__device__ __forceinline__ void add_texel(Sample& s, const Texel& t, float cv, float cu, float cg) {
-    const float x[5] = {t.g, t.d, t.nx, t.ny, t.nz};
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        s.v[c] = fmaf(cv, x[c], s.v[c]);
-        s.gu[c] = fmaf(cu, x[c], s.gu[c]);
-        s.gv[c] = fmaf(cg, x[c], s.gv[c]);
-    }
+__device__ __forceinline__ void channels(const Texel& t, float (&x)[5]) {
+    x[0] = t.g;
+    x[1] = t.d;
+    x[2] = t.nx;
+    x[3] = t.ny;
+    x[4] = t.nz;
 }
 
-// Bilinear sample at (u, v) of value and image gradient from the 4 x 4 stencil
-// minus corners.  Taps A (r0,c0), B (r0,c0+1), C (r0+1,c0), D (r0+1,c0+1).
-// grad_mode 0: the central differences of the Supp. at each tap, interpolated;
-// grad_mode 1: the exact derivative of the bilinear interpolant.
-// Returns false when any of the 12 stencil texels is invalid (d == 0).
-template <int TEXEL>
-__device__ __forceinline__ bool sample_stencil(const void* __restrict__ tex, long long base, int W, bool wrap,
-                                               int r0, int c0, float a, float b, int grad_mode, Sample& s) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) s.v[c] = s.gu[c] = s.gv[c] = 0.f;
-    int cm1 = c0 - 1, cp1 = c0 + 1, cp2 = c0 + 2, cc = c0;
+// Column indices c0 - 1, c0, c0 + 1, c0 + 2 (wrapped modulo W for the spherical model).
+__device__ __forceinline__ void stencil_cols(int c0, int W, bool wrap, int& cm1, int& cc, int& cp1, int& cp2) {
+    cc = c0;
     if (wrap) {
-        cc = c0 % W;
-        if (cc < 0) cc += W;
+        if (cc < 0 || cc >= W) {
+            cc %= W;
+            if (cc < 0) cc += W;
+        }
         cm1 = cc == 0 ? W - 1 : cc - 1;
         cp1 = cc == W - 1 ? 0 : cc + 1;
         cp2 = cp1 == W - 1 ? 0 : cp1 + 1;
-    }
-    const long long rm1 = base + (long long)(r0 - 1) * W, rr0 = base + (long long)r0 * W;
-    const long long rp1 = rr0 + W, rp2 = rp1 + W;
-    const float wA = (1.f - a) * (1.f - b), wB = a * (1.f - b), wC = (1.f - a) * b, wD = a * b;
-    const float hA = 0.5f * wA, hB = 0.5f * wB, hC = 0.5f * wC, hD = 0.5f * wD;
-    bool ok = true;
-    Texel t;
-    if (grad_mode == 0) {
-        // row r0 - 1
-        t = load_texel<TEXEL>(tex, rm1 + cc);   ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, -hA);
-        t = load_texel<TEXEL>(tex, rm1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, -hB);
-        // row r0
-        t = load_texel<TEXEL>(tex, rr0 + cm1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, -hA, 0.f);
-        t = load_texel<TEXEL>(tex, rr0 + cc);   ok &= t.d > 0.f; add_texel(s, t, wA, -hB, -hC);
-        t = load_texel<TEXEL>(tex, rr0 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wB, hA, -hD);
-        t = load_texel<TEXEL>(tex, rr0 + cp2);  ok &= t.d > 0.f; add_texel(s, t, 0.f, hB, 0.f);
-        // row r0 + 1
-        t = load_texel<TEXEL>(tex, rp1 + cm1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, -hC, 0.f);
-        t = load_texel<TEXEL>(tex, rp1 + cc);   ok &= t.d > 0.f; add_texel(s, t, wC, -hD, hA);
-        t = load_texel<TEXEL>(tex, rp1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wD, hC, hB);
-        t = load_texel<TEXEL>(tex, rp1 + cp2);  ok &= t.d > 0.f; add_texel(s, t, 0.f, hD, 0.f);
-        // row r0 + 2
-        t = load_texel<TEXEL>(tex, rp2 + cc);   ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, hC);
-        t = load_texel<TEXEL>(tex, rp2 + cp1);  ok &= t.d > 0.f; add_texel(s, t, 0.f, 0.f, hD);
     } else {
-        // exact derivative of the bilinear interpolant: only the taps carry weight,
-        // but the stencil texels still decide usability
-        t = load_texel<TEXEL>(tex, rm1 + cc);   ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rm1 + cp1);  ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rr0 + cm1);  ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rr0 + cc);   ok &= t.d > 0.f; add_texel(s, t, wA, -(1.f - b), -(1.f - a));
-        t = load_texel<TEXEL>(tex, rr0 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wB, (1.f - b), -a);
-        t = load_texel<TEXEL>(tex, rr0 + cp2);  ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rp1 + cm1);  ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rp1 + cc);   ok &= t.d > 0.f; add_texel(s, t, wC, -b, (1.f - a));
-        t = load_texel<TEXEL>(tex, rp1 + cp1);  ok &= t.d > 0.f; add_texel(s, t, wD, b, a);
-        t = load_texel<TEXEL>(tex, rp1 + cp2);  ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rp2 + cc);   ok &= t.d > 0.f;
-        t = load_texel<TEXEL>(tex, rp2 + cp1);  ok &= t.d > 0.f;
+        cm1 = cc - 1;
+        cp1 = cc + 1;
+        cp2 = cc + 2;
     }
-    return ok;
 }
 
 // H6 (upper triangle, row-major 21) += s * J J^T ; b6 += s * J e
@@ -200,24 +154,65 @@ __device__ __forceinline__ void make_row(float (&J)[6], const float (&h)[3], con
 }
 
 constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two >= 63)
-constexpr int kQItems = 20;  // floats per queued residual: e[5], dI/du[5], dI/dv[5], w, pbar[3], point index
+constexpr int kQItems = 14;  // floats per queued residual: e[5], w, pbar[3], point, r0, c0, a, b
 
-// a6 + a7 for one queued residual: d pi / d pbar, the 5 x 6 Jacobian J_i and its
-// Huber-weighted accumulation into H6 (upper triangle) and b6.
-__device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int model, float fx, float fy,
-                                               const float (&M)[9], const float (&om)[5],
+// Stage 2 (a4 gradients + a6 + a7) for one queued residual: the image
+// gradients of the five channels at u' from the 12-texel stencil (central
+// differences of the Supp. interpolated bilinearly, grad_mode 0, or the exact
+// bilinear derivative, grad_mode 1), d pi / d pbar, the 5 x 6 Jacobian J_i and
+// its Huber-weighted accumulation into H6 (upper triangle) and b6.
+template <int TEXEL>
+__device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int model, float fx, float fy, int W,
+                                               bool wrap, const float (&M)[9], const float (&om)[5],
                                                const float4* __restrict__ pg, const float4* __restrict__ pn,
+                                               const void* __restrict__ tex, long long tex_off, int grad_mode,
                                                float (&Hacc)[21], float (&bacc)[6]) {
-    float e[5], gu[5], gv[5];
+    float e[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        e[c] = Q[c][slot];
-        gu[c] = Q[5 + c][slot];
-        gv[c] = Q[10 + c][slot];
+    for (int c = 0; c < 5; ++c) e[c] = Q[c][slot];
+    const float w = Q[5][slot];
+    const float qx = Q[6][slot], qy = Q[7][slot], qz = Q[8][slot];
+    const int k = __float_as_int(Q[9][slot]);
+    const int r0 = __float_as_int(Q[10][slot]);
+    const int c0 = __float_as_int(Q[11][slot]);
+    const float a = Q[12][slot], b = Q[13][slot];
+
+    int cm1, cc, cp1, cp2;
+    stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
+    const long long rr0 = tex_off + (long long)r0 * W, rm1 = rr0 - W, rp1 = rr0 + W, rp2 = rp1 + W;
+    float gu[5], gv[5];
+    {
+        float A[5], B[5], C[5], D[5];
+        channels(load_texel<TEXEL>(tex, rr0 + cc), A);
+        channels(load_texel<TEXEL>(tex, rr0 + cp1), B);
+        channels(load_texel<TEXEL>(tex, rp1 + cc), C);
+        channels(load_texel<TEXEL>(tex, rp1 + cp1), D);
+        if (grad_mode == 0) {
+            float T01[5], T02[5], T10[5], T13[5], T20[5], T23[5], T31[5], T32[5];
+            channels(load_texel<TEXEL>(tex, rm1 + cc), T01);
+            channels(load_texel<TEXEL>(tex, rm1 + cp1), T02);
+            channels(load_texel<TEXEL>(tex, rr0 + cm1), T10);
+            channels(load_texel<TEXEL>(tex, rr0 + cp2), T13);
+            channels(load_texel<TEXEL>(tex, rp1 + cm1), T20);
+            channels(load_texel<TEXEL>(tex, rp1 + cp2), T23);
+            channels(load_texel<TEXEL>(tex, rp2 + cc), T31);
+            channels(load_texel<TEXEL>(tex, rp2 + cp1), T32);
+            const float hA = 0.5f * (1.f - a) * (1.f - b), hB = 0.5f * a * (1.f - b);
+            const float hC = 0.5f * (1.f - a) * b, hD = 0.5f * a * b;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                // central differences at the taps A, B, C, D, interpolated
+                gu[c] = fmaf(hA, B[c] - T10[c], fmaf(hB, T13[c] - A[c], fmaf(hC, D[c] - T20[c], hD * (T23[c] - C[c]))));
+                gv[c] = fmaf(hA, C[c] - T01[c], fmaf(hB, D[c] - T02[c], fmaf(hC, T31[c] - A[c], hD * (T32[c] - B[c]))));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                gu[c] = fmaf(1.f - b, B[c] - A[c], b * (D[c] - C[c]));
+                gv[c] = fmaf(1.f - a, C[c] - A[c], a * (D[c] - B[c]));
+            }
+        }
     }
-    const float w = Q[15][slot];
-    const float qx = Q[16][slot], qy = Q[17][slot], qz = Q[18][slot];
-    const int k = __float_as_int(Q[19][slot]);
     const float4 p = __ldg(pg + k);
     const float4 n = __ldg(pn + k);
     // d pi / d pbar (2 x 3) and d zeta^d / d pbar
@@ -243,14 +238,14 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
         // g_c = d zeta_c / d pbar - grad I_c d pi / d pbar
         float g[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            g[a] = -fmaf(gu[c], P0[a], gv[c] * P1[a]);
-            if (c == 1) g[a] += dz[a];
+        for (int j = 0; j < 3; ++j) {
+            g[j] = -fmaf(gu[c], P0[j], gv[c] * P1[j]);
+            if (c == 1) g[j] += dz[j];
         }
         // h_c = M^T g_c
         float h[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) h[a] = fmaf(M[a], g[0], fmaf(M[3 + a], g[1], M[6 + a] * g[2]));
+        for (int j = 0; j < 3; ++j) h[j] = fmaf(M[j], g[0], fmaf(M[3 + j], g[1], M[6 + j] * g[2]));
         float J[6];
         make_row(J, h, p);
         if (c >= 2) {
@@ -265,6 +260,12 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
     }
 }
 
+// One warp per work item (a chunk of up to kWarpChunk points of one pair); no
+// block-wide synchronisation.  Stage 1 runs on every point: transform,
+// projection, bounds, the 4 bilinear taps (whose usable flags decide the
+// 12-texel stencil), sampled values, residual, occlusion test, Huber weight and
+// cost.  Valid residuals are compacted into the warp's queue; stage 2 runs on
+// full warps of them.
 template <int TEXEL, bool FULL, bool MASK>
 __global__ void __launch_bounds__(kLinThreads, 2)
     k_linearize(const int4* __restrict__ chunks, int n_chunks, int* __restrict__ queue,
@@ -272,17 +273,15 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                 const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
                 const void* __restrict__ tex, const LinParams prm, float* __restrict__ partials,
                 uint32_t* __restrict__ mask_bits) {
-    __shared__ int s_chunk;
-    __shared__ float s_red[kLinWarps][kNumAcc];
-    __shared__ float s_q[kLinWarps][kQItems][kQueue];
+    __shared__ float s_q[FULL ? kLinWarps : 1][kQItems][kQueue];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float om[5] = {prm.w_int, prm.w_depth, prm.w_normal, prm.w_normal, prm.w_normal};
+    float(*Q)[kQueue] = s_q[FULL ? warp : 0];
 
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(queue, 1);
-        __syncthreads();
-        const int ci = s_chunk;
-        __syncthreads();
+        int ci = 0;
+        if (lane == 0) ci = atomicAdd(queue, 1);
+        ci = __shfl_sync(0xffffffffu, ci, 0);
         if (ci >= n_chunks) break;
         const int4 ch = __ldg(chunks + ci);
         const int pair = ch.x, first = ch.y, count = ch.z;
@@ -297,6 +296,7 @@ __global__ void __launch_bounds__(kLinThreads, 2)
         for (int k = 0; k < 3; ++k) av[k] = pp[pair].a[k];
         const bool wrap = model == 1;
         const float umax = wrap ? 3.4e38f : (float)(W - 2);
+        const float umin = wrap ? -3.4e38f : 1.f;
         const float vmax = (float)(Hh - 2);
 
         float Hacc[21], bacc[6], cost = 0.f, cnt = 0.f;
@@ -306,23 +306,20 @@ __global__ void __launch_bounds__(kLinThreads, 2)
 #pragma unroll
             for (int k = 0; k < 6; ++k) bacc[k] = 0.f;
         }
-
-        // Residuals that pass every test wait in this warp's queue until 32 of
-        // them are ready; the Jacobian stage then runs on full warps only.
-        float(*Q)[kQueue] = s_q[warp];
-        int head = 0, tail = 0;  // warp-uniform ring-buffer counters
+        int head = 0, tail = 0;  // warp-uniform queue counters
         const int end = first + count;
-        for (int base = first + warp * 32; base < end; base += kLinThreads) {
+        for (int base = first; base < end; base += 32) {
             const int k = base + lane;
             bool valid = false;
-            float e[5], gu[5], gv[5], w = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
+            float e[5], w = 0.f, qx = 0.f, qy = 0.f, qz = 0.f, fa = 0.f, fb = 0.f;
+            int r0 = 0, c0 = 0;
             if (k < end) {
                 const float4 p = __ldg(pts_pg + pt_off + k);
                 // a2: pbar = M p_u + a
                 qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
                 qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));
                 qz = fmaf(M[6], p.x, fmaf(M[7], p.y, fmaf(M[8], p.z, av[2])));
-                // a3: projection and validity
+                // a3: projection and bounds
                 float u, v, zeta_d;
                 bool ok;
                 if (model == 0) {
@@ -338,17 +335,33 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                     u = fmaf(fx, atan2f(qy, qx), cx);
                     v = fmaf(fy, atan2f(qz, sqrtf(rxy2)), cy);
                 }
-                ok = ok && v >= 1.f && v < vmax && u >= (wrap ? -3.4e38f : 1.f) && u < umax;
+                ok = ok && v >= 1.f && v < vmax && u >= umin && u < umax;
                 if (ok) {
                     const float fu = floorf(u), fv = floorf(v);
-                    const int c0 = (int)fu, r0 = (int)fv;
-                    Sample s;
-                    // a4: bilinear sample of value and gradient
-                    ok = sample_stencil<TEXEL>(tex, tex_off, W, wrap, r0, c0, u - fu, v - fv, prm.grad_mode, s);
+                    c0 = (int)fu;
+                    r0 = (int)fv;
+                    fa = u - fu;
+                    fb = v - fv;
+                    int cm1, cc, cp1, cp2;
+                    stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
+                    c0 = cc;
+                    // a4: the four bilinear taps; their usable flags decide the 12-texel stencil
+                    const long long rr0 = tex_off + (long long)r0 * W, rp1 = rr0 + W;
+                    const Texel A = load_texel<TEXEL>(tex, rr0 + cc), B = load_texel<TEXEL>(tex, rr0 + cp1);
+                    const Texel C = load_texel<TEXEL>(tex, rp1 + cc), D = load_texel<TEXEL>(tex, rp1 + cp1);
+                    ok = A.usable && B.usable && C.usable && D.usable;
+                    const float wA = (1.f - fa) * (1.f - fb), wB = fa * (1.f - fb), wC = (1.f - fa) * fb, wD = fa * fb;
+                    float xa[5], xb[5], xc[5], xd[5], s[5];
+                    channels(A, xa);
+                    channels(B, xb);
+                    channels(C, xc);
+                    channels(D, xd);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) s[c] = fmaf(wA, xa[c], fmaf(wB, xb[c], fmaf(wC, xc[c], wD * xd[c])));
                     // a5: residual, occlusion test, Huber
-                    const float e_d = zeta_d - s.v[1];
+                    const float e_d = zeta_d - s[1];
                     ok = ok && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
-                    const float nt2 = fmaf(s.v[2], s.v[2], fmaf(s.v[3], s.v[3], s.v[4] * s.v[4]));
+                    const float nt2 = fmaf(s[2], s[2], fmaf(s[3], s[3], s[4] * s[4]));
                     ok = ok && nt2 >= 0.25f;
                     if (ok) {
                         valid = true;
@@ -356,11 +369,11 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                         const float nbx = fmaf(M[0], n.x, fmaf(M[1], n.y, M[2] * n.z));
                         const float nby = fmaf(M[3], n.x, fmaf(M[4], n.y, M[5] * n.z));
                         const float nbz = fmaf(M[6], n.x, fmaf(M[7], n.y, M[8] * n.z));
-                        e[0] = p.w - s.v[0];
+                        e[0] = p.w - s[0];
                         e[1] = e_d;
-                        e[2] = nbx - s.v[2];
-                        e[3] = nby - s.v[3];
-                        e[4] = nbz - s.v[4];
+                        e[2] = nbx - s[2];
+                        e[3] = nby - s[3];
+                        e[4] = nbz - s[4];
                         float chi2 = 0.f;
 #pragma unroll
                         for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
@@ -375,11 +388,6 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                         }
                         cost += rho;
                         cnt += 1.f;
-#pragma unroll
-                        for (int c = 0; c < 5; ++c) {
-                            gu[c] = s.gu[c];
-                            gv[c] = s.gv[c];
-                        }
                     }
                 }
             }
@@ -392,22 +400,22 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                 if (valid) {
                     const int slot = (tail + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) {
-                        Q[c][slot] = e[c];
-                        Q[5 + c][slot] = gu[c];
-                        Q[10 + c][slot] = gv[c];
-                    }
-                    Q[15][slot] = w;
-                    Q[16][slot] = qx;
-                    Q[17][slot] = qy;
-                    Q[18][slot] = qz;
-                    Q[19][slot] = __int_as_float(k);
+                    for (int c = 0; c < 5; ++c) Q[c][slot] = e[c];
+                    Q[5][slot] = w;
+                    Q[6][slot] = qx;
+                    Q[7][slot] = qy;
+                    Q[8][slot] = qz;
+                    Q[9][slot] = __int_as_float(k);
+                    Q[10][slot] = __int_as_float(r0);
+                    Q[11][slot] = __int_as_float(c0);
+                    Q[12][slot] = fa;
+                    Q[13][slot] = fb;
                 }
                 tail += __popc(bal);
                 __syncwarp();
                 if (tail - head >= 32) {
-                    jacobian_stage(Q, (head + lane) & (kQueue - 1), model, fx, fy, M, om, pts_pg + pt_off,
-                                   pts_n + pt_off, Hacc, bacc);
+                    jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
+                                          pts_pg + pt_off, pts_n + pt_off, tex, tex_off, prm.grad_mode, Hacc, bacc);
                     head += 32;
                     __syncwarp();
                 }
@@ -415,37 +423,30 @@ __global__ void __launch_bounds__(kLinThreads, 2)
         }
         if (FULL && tail > head) {
             if (lane < tail - head)
-                jacobian_stage(Q, (head + lane) & (kQueue - 1), model, fx, fy, M, om, pts_pg + pt_off,
-                               pts_n + pt_off, Hacc, bacc);
+                jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
+                                      pts_pg + pt_off, pts_n + pt_off, tex, tex_off, prm.grad_mode, Hacc, bacc);
             __syncwarp();
         }
 
-        // a7: chunk reduction (warp shuffle, then shared memory), one FP32 partial per chunk
-        float acc[kNumAcc];
+        // a7: warp reduction, one FP32 partial per work item (lane t writes sum t)
+        float mine = 0.f;
         if (FULL) {
 #pragma unroll
-            for (int k = 0; k < 21; ++k) acc[k] = Hacc[k];
+            for (int j = 0; j < 27; ++j) {
+                float x = j < 21 ? Hacc[j] : bacc[j - 21];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[21 + k] = bacc[k];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == j) mine = x;
+            }
         }
-        acc[27] = cost;
-        acc[28] = cnt;
-        const int k0 = FULL ? 0 : 27;
 #pragma unroll
-        for (int k = k0; k < kNumAcc; ++k) {
-            float x = acc[k];
+        for (int j = 27; j < kNumAcc; ++j) {
+            float x = j == 27 ? cost : cnt;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) s_red[warp][k] = x;
+            if (lane == j) mine = x;
         }
-        __syncthreads();
-        if ((int)threadIdx.x >= k0 && threadIdx.x < kNumAcc) {
-            float x = 0.f;
-#pragma unroll
-            for (int w8 = 0; w8 < kLinWarps; ++w8) x += s_red[w8][threadIdx.x];
-            partials[(long long)ci * kPartialStride + threadIdx.x] = x;
-        }
-        __syncthreads();
+        if (lane < kNumAcc && (FULL || lane >= 27)) partials[(long long)ci * kPartialStride + lane] = mine;
     }
 }
 

@@ -49,18 +49,35 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
             const float* src = raw + (fr.px_offset + px) * 5;
             for (int k = 0; k < 5; ++k) c[k] = src[k];
             valid = pixel_valid(c, rmin, rmax);
+            // usable: the pixel and its four neighbours are valid, i.e. the
+            // central differences of the Supp. are defined at this pixel
+            bool usable = valid;
+            {
+                const int col = px % fr.width, row = px / fr.width;
+                const bool wrap = fr.model == 1;
+                const int nb[4][2] = {{row - 1, col}, {row + 1, col}, {row, col - 1}, {row, col + 1}};
+                for (int q = 0; q < 4 && usable; ++q) {
+                    int r = nb[q][0], cc = nb[q][1];
+                    if (r < 0 || r >= fr.height) { usable = false; break; }
+                    if (cc < 0 || cc >= fr.width) {
+                        if (!wrap) { usable = false; break; }
+                        cc = cc < 0 ? cc + fr.width : cc - fr.width;
+                    }
+                    usable = pixel_valid(raw + (fr.px_offset + (long long)r * fr.width + cc) * 5, rmin, rmax);
+                }
+            }
             const long long t = fr.px_offset + px;
             if (TEXEL == 1) {
                 Tex16 tx;
                 tx.d = valid ? c[1] : 0.f;
                 tx.g_nx = __halves2half2(__float2half_rn(c[0]), __float2half_rn(c[2]));
                 tx.ny_nz = __halves2half2(__float2half_rn(c[3]), __float2half_rn(c[4]));
-                tx.pad = 0.f;
+                tx.usable = usable ? 1u : 0u;
                 reinterpret_cast<Tex16*>(texels)[t] = tx;
             } else {
                 float4* t4 = reinterpret_cast<float4*>(texels) + 2 * t;
                 t4[0] = make_float4(valid ? c[1] : 0.f, c[0], c[2], c[3]);
-                t4[1] = make_float4(c[4], 0.f, 0.f, 0.f);
+                t4[1] = make_float4(c[4], __uint_as_float(usable ? 1u : 0u), 0.f, 0.f);
             }
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, valid);
