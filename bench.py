@@ -46,8 +46,8 @@ WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs w
 # Algorithmic FP32 work of the linearisation kernel (derivation in the design doc):
 # per processed point (transform + spherical projection + bounds) and per
 # valid residual (sampling, residual, Huber, 5 x 6 Jacobian, 6 x 6 accumulation).
-FLOP_PER_POINT_SPHERICAL = 76
-FLOP_PER_RESIDUAL_FULL = 720
+FLOP_PER_POINT_SPHERICAL = 31
+FLOP_PER_RESIDUAL_FULL = 765
 FP32_LANES_PER_SM = 128
 
 

@@ -2,7 +2,7 @@
  * pba.h -- C ABI of the GB300 photometric bundle-adjustment library (libpba.so).
  *
  * The library linearises the multi-cue photometric error of Di Giammarino et
- * al., "Photometric LiDAR and RGB-D Bundle Adjustment" (Eq. 6 with the offset
+ * al., "Photometric LiDAR and RGB-D Bundle Adjustment" (Eq. total-error-multicue with the offset
  * form of the supplementary material), assembles the Gauss-Newton system
  * H dx = -b over all sensor poses, and takes damped (Levenberg-Marquardt)
  * steps X_k <- X_k [+] dx_k, all on one GPU.
@@ -44,8 +44,8 @@ extern "C" {
 #define PBA_ENOTREADY (-6)  /* a required input (frames, poses, pairs) was not set */
 
 /* projection models, Sec. III */
-#define PBA_PINHOLE 0       /* pi_p(p) = phi(K p), Eq. 2; d is the depth */
-#define PBA_SPHERICAL 1     /* pi_s(p) = K_[1,2] psi(p), Eq. 3; d is the range */
+#define PBA_PINHOLE 0       /* pi_p(p) = phi(K p), Eq. pinhole-projection; d is the depth */
+#define PBA_SPHERICAL 1     /* pi_s(p) = K_[1,2] psi(p), Eq. spherical-projection; d is the range */
 
 /* linearisation paths */
 #define PBA_PATH_BATCHED 0  /* all pairs in one persistent launch, 6x6 reduced accumulation */
@@ -61,9 +61,9 @@ extern "C" {
 
 typedef struct pba_problem pba_problem;
 
-/* One sensor: intrinsics K (Eq. 2; for the spherical model f_x, f_y are the
+/* One sensor: intrinsics K (Eq. camera-matrix-p; for the spherical model f_x, f_y are the
  * azimuth / elevation resolutions in pixels per radian and c_x, c_y their
- * offsets, Eq. 3) and the extrinsic offset X_o = [R_o | t_o] (row-major 3x4)
+ * offsets, Eq. spherical-projection) and the extrinsic offset X_o = [R_o | t_o] (row-major 3x4)
  * placing the sensor on the platform (Supp., p_u = R_o pi^-1(u, d) + t_o). */
 typedef struct {
     int32_t model;              /* PBA_PINHOLE or PBA_SPHERICAL */
@@ -99,7 +99,7 @@ typedef struct {
 
 /* Outcome of one Levenberg-Marquardt iteration. */
 typedef struct {
-    double cost;        /* F (Eq. 6) at the poses the iteration started from */
+    double cost;        /* F (Eq. total-error-multicue) at the poses the iteration started from */
     double new_cost;    /* F at the candidate poses X [+] dx */
     double lambda_used; /* damping of the solved system (H_ff + lambda I) */
     double lambda_next; /* lambda / 10 after an accepted step, lambda * 10 otherwise */
@@ -146,7 +146,7 @@ int pba_get_poses(pba_problem* p, double* poses);
 int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m);
 
 /* Linearise all pairs at the current poses: builds H (6N x 6N, gauge not
- * fixed) and b (6N) on the device and returns the total cost F (Eq. 6) and
+ * fixed) and b (6N) on the device and returns the total cost F (Eq. total-error-multicue) and
  * the number of valid residuals; synchronises.  Either output may be NULL. */
 int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
 

@@ -217,7 +217,7 @@ def linearize_pair(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, X
 
 def linearize(sensors: Sequence, frame_sensor, channels: Sequence[np.ndarray], poses, pairs, params: Dict,
               want_system: bool = True, want_pairs: bool = False, lib=None) -> Dict:
-    """Dense H (6N x 6N, gauge not fixed), b, total cost F (Eq. 6), count."""
+    """Dense H (6N x 6N, gauge not fixed), b, total cost F (Eq. total-error-multicue), count."""
     lib = lib or _load()
     n = len(channels)
     chans = [np.ascontiguousarray(c, dtype=np.float32) for c in channels]

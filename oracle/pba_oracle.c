@@ -10,12 +10,12 @@
  * Every function follows the paper's definitions literally, one point at a
  * time, in double precision, with no blocking, fusion or reordering:
  *   - rigid transforms and their inverse ............... Eq. 1
- *   - pinhole projection pi_p = phi(K p) ............... Eq. 2 (pinhole-projection)
- *   - spherical projection pi_s = K_[1,2] psi(p) ....... Eq. 3 (spherical-projection)
+ *   - pinhole projection pi_p = phi(K p) ............... Eq. pinhole-projection
+ *   - spherical projection pi_s = K_[1,2] psi(p) ....... Eq. spherical-projection
  *   - unprojection pi^-1(u, d) (depth / range) ......... Sec. III
  *   - five-channel cue image (g, d, n) ................. Sec. IV-A
- *   - u' and the relative transform .................... Eq. 4 (uprime)
- *   - multi-cue robust error F ......................... Eq. 6 (total-error-multicue)
+ *   - u' and the relative transform .................... Eq. uprime
+ *   - multi-cue robust error F ......................... Eq. total-error-multicue
  *   - offset points p_u, pbar_u and the error e ........ Supp., Eq. error-jacobian
  *   - perturbed points and their Jacobians ............. Supp., dpbar/dDx_i, dpbar/dDx_j
  *   - projection Jacobians (pinhole, spherical) ........ Supp.
@@ -32,7 +32,7 @@
  * design notes of the repository):
  *   R1  the Huber rho acts on chi = sqrt(e^T Omega e); w = 1 if chi <= delta,
  *       else delta / chi; rho = chi^2 or 2 delta chi - delta^2.
- *   R2  the channel norm of Eq. 6 is the stacked weighted norm
+ *   R2  the channel norm of Eq. total-error-multicue is the stacked weighted norm
  *       sum_c Omega^c (e^c)^2 with Omega = diag(w_g, w_d, w_n, w_n, w_n).
  *   R3  R(Dq) ~ I + 2 [Dq]x, so d(R(Dq) p)/dDq = -2 [p]x with [a]x b = a x b;
  *       the Supp. "2 [p]x" is read with the opposite skew convention.
@@ -120,7 +120,7 @@ static void skew(const double a[3], double S[9]) {
 
 /* ------------------------------------------------------- Sec. III models */
 
-/* Eq. 2 (pinhole) and Eq. 3 (spherical): image coordinates of p. */
+/* Eq. pinhole-projection and Eq. spherical-projection: image coordinates of p. */
 void o_project(const o_sensor* s, const double p[3], double uv[2]) {
     if (s->model == O_PINHOLE) {
         /* v = K p ; phi(v) = (v_x / v_z, v_y / v_z) */
@@ -366,7 +366,7 @@ int o_point_residual(const o_sensor* s, const o_params* prm, const float* tgt,
     if (fabs(zd - prm->z_min) < prm->margin_rel * (1.0 + fabs(zd))) *flag = 1;
     if (!(zd > prm->z_min)) return 0;
 
-    /* u' = pi(pbar)  (Eq. 4) and the sample of I_j at u' */
+    /* u' = pi(pbar)  (Eq. uprime) and the sample of I_j at u' */
     double uv[2];
     o_project(s, pb, uv);
     double Iv[5], Igu[5], Igv[5];
@@ -551,7 +551,7 @@ int o_linearize_pair(const o_sensor* s, const o_params* prm, const float* src, c
 /*
  * Linearise every directed pair and assemble the dense system (gauge not
  * fixed): H (6N x 6N row-major) and b (6N), frame k owning rows 6k..6k+5,
- * plus the total cost F (Eq. 6) and the number of valid residuals.
+ * plus the total cost F (Eq. total-error-multicue) and the number of valid residuals.
  * channels[k] is frame k's H x W x 5 float image; poses is N x 12.
  * H and b may be NULL (cost only).  Pair k's 12x12 block and 12-vector are
  * also returned in pair_H (M x 144) / pair_b (M x 12) when those are non-NULL,

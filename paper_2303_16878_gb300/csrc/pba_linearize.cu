@@ -1,9 +1,9 @@
 // pba_linearize.cu -- the batched photometric linearisation (hot path).
 //
 // k_pair_pose     FP64 poses -> FP32 per-pair transform pbar = M p_u + a with
-//                 M = R_o^T R_j^T R_i, a = R_o^T (R_j^T (t_i - t_j) - t_o)  (Supp., pbar_u; Eq. 4)
+//                 M = R_o^T R_j^T R_i, a = R_o^T (R_j^T (t_i - t_j) - t_o)  (Supp., pbar_u; Eq. uprime)
 // k_linearize     one persistent launch over a queue of chunks (pair, points);
-//                 per pixel-point: transform, project (Eq. 2 / Eq. 3), sample the
+//                 per pixel-point: transform, project (Eq. pinhole-projection / spherical-projection), sample the
 //                 five target channels and their image gradients bilinearly from
 //                 the 12-texel central-difference stencil (Supp., image Jacobians),
 //                 residual e = zeta(pbar) - I_j(u') (Supp., Eq. error-jacobian),

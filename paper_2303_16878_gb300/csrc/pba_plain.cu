@@ -7,7 +7,7 @@
 // Supp. derivatives of both frames, and the 78 + 12 entries of
 // w J^T Omega J, w J^T Omega e (plus cost and count) reduced per block and
 // added to the pair's FP32 accumulator with global atomics.  The same
-// definitions as the batched path (Eq. 2-4, Eq. 6, Supp.): only the
+// definitions as the batched path (Eq. pinhole-projection, spherical-projection, uprime, total-error-multicue, Supp.): only the
 // organisation of the work differs.
 #include "pba_internal.cuh"
 

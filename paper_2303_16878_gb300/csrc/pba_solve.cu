@@ -1,7 +1,7 @@
 // pba_solve.cu -- FP64 assembly, damped gauge-fixed Cholesky solve, box-plus
 // update and the Levenberg-Marquardt accept / reject, all on the device.
 //
-// The paper minimises Eq. 6 with Levenberg-Marquardt (Sec. IV-C, srrg2_solver);
+// The paper minimises Eq. total-error-multicue with Levenberg-Marquardt (Sec. IV-C, srrg2_solver);
 // the normal equations are H = sum w J^T Omega J, b = sum w J^T Omega e over all
 // residuals.  Each step solves (H_ff + lambda I) dx_f = -b_f, where _f drops
 // frame 0 (gauge freedom), and applies X_k <- X_k [+] dx_k (Supp.):

@@ -1,7 +1,7 @@
 """Seeded synthetic scenes, sensor renders, trajectories and pair lists.
 
 This module produces the inputs of the photometric bundle-adjustment path
-(Sec. IV, Eq. 3-6 and the supplementary error terms): per-frame five-channel
+(Sec. IV, Eq. uprime to Eq. total-error-multicue and the supplementary error terms): per-frame five-channel
 cue images (intensity g, depth or range d, normal n_x n_y n_z, Sec. IV-A),
 ground-truth and perturbed sensor poses, and a directed pair list (Sec. IV-B).
 
@@ -39,7 +39,7 @@ IDENTITY_3x4 = np.array([[1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, 1.0, 0]])
 
 @dataclasses.dataclass
 class Sensor:
-    """Intrinsics of one sensor (Eq. 2 pinhole K, Eq. 3 spherical K_[1,2])."""
+    """Intrinsics of one sensor (Eq. camera-matrix-p pinhole K, Eq. spherical-projection K_[1,2])."""
 
     model: int
     width: int
@@ -63,7 +63,7 @@ def pinhole_sensor(width: int, height: int, f: float, cx: float, cy: float) -> S
 def spherical_sensor(width: int, height: int, vfov_up_deg: float, vfov_down_deg: float) -> Sensor:
     """Spherical sensor with azimuth decreasing left to right over 360 degrees
     and row 0 at the top elevation (the reading of the spherical K taken for
-    the paper's "resolution and offset" wording of Eq. 3)."""
+    the paper's "resolution and offset" wording of Eq. spherical-projection)."""
     up = math.radians(vfov_up_deg)
     down = math.radians(vfov_down_deg)
     vfov = up - down
@@ -539,6 +539,32 @@ def make_lidar_street(n_frames: int = 50, width: int = 1024, height: int = 64,
     return Workload(f"lidar-street-{n_frames}x{height}x{width}", [sensor],
                     np.zeros(n_frames, dtype=np.int32), chans, poses, init,
                     np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)
+
+
+def with_extrinsic(w: Workload, Xo: np.ndarray) -> Workload:
+    """The same renders described with a sensor mounted at offset Xo on the
+    platform: every sensor gets extrinsic Xo and the platform poses become
+    X_sensor Xo^-1, so that platform pose times offset is the render pose."""
+    Xo = np.asarray(Xo, dtype=np.float64).reshape(3, 4)
+    inv = np.zeros((3, 4))
+    inv[:, :3] = Xo[:, :3].T
+    inv[:, 3] = -Xo[:, :3].T @ Xo[:, 3]
+    sensors = [dataclasses.replace(s, extrinsic=Xo.copy()) for s in w.sensors]
+    gt = np.stack([compose(X, inv) for X in w.poses_gt])
+    init = np.stack([compose(X, inv) for X in w.poses_init])
+    return Workload(w.name + "-offset", sensors, w.frame_sensor.copy(), w.channels, gt, init, w.pairs.copy(),
+                    dict(w.params))
+
+
+def offset_transform(t_m: float = 0.02, r_deg: float = 0.5, seed: int = 5) -> np.ndarray:
+    """A seeded sensor offset: translation of norm t_m, rotation of r_deg degrees."""
+    rng = np.random.default_rng(seed)
+    t = rng.normal(size=3)
+    a = rng.normal(size=3)
+    X = np.zeros((3, 4))
+    X[:, :3] = rot_vec(a / np.linalg.norm(a) * math.radians(r_deg))
+    X[:, 3] = t / np.linalg.norm(t) * t_m
+    return X
 
 
 def make_plane_shift(width: int = 48, height: int = 40, f: float = 40.0, depth: float = 2.0,

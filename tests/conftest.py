@@ -46,5 +46,12 @@ def room8():
 
 
 @pytest.fixture(scope="session")
+def room8x(room8):
+    """The RGB-D room with the camera mounted at a 2 cm / 0.5 deg offset."""
+    from paper_2303_16878_gb300 import synth
+    return synth.with_extrinsic(room8, synth.offset_transform(0.02, 0.5, seed=3005))
+
+
+@pytest.fixture(scope="session")
 def street3():
     return workload("street", n_frames=3, width=256, height=32)

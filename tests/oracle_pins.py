@@ -4,11 +4,11 @@ Each pin returns an error measure; `PIN_TOL` holds the bar.  The pins are used
 twice: by test_oracle_pins.py on the oracle as committed, and by
 test_oracle_mutations.py on copies with a planted mistake, where at least one
 pin must fail.  Sources of truth:
-  - hand-derived closed forms of Eq. 2 / Eq. 3 (tests/golden/projection_closed_form.json);
+  - hand-derived closed forms of Eq. pinhole-projection / Eq. spherical-projection (tests/golden/projection_closed_form.json);
   - scipy's rotation and bilinear-interpolation routines and numpy's linear solver;
   - central finite differences of the oracle's own residual and cost;
   - invariants of the formulation: the 6-dim gauge null space of H (the
-    residual depends on X_i, X_j only through X_j^-1 X_i, Eq. 4), exact zero
+    residual depends on X_i, X_j only through X_j^-1 X_i, Eq. uprime), exact zero
     error for integer-pixel shifts of a fronto-parallel plane.
 """
 import json
@@ -32,6 +32,8 @@ PIN_TOL = {
     "plane_shift": 1e-9,
     "single_channel": 1e-9,
     "cholesky": 1e-10,
+    "extrinsic_equivalence": 1e-9,
+    "jacobian_fd_extrinsic": 1e-6,
 }
 
 
@@ -237,7 +239,7 @@ def pin_gauge(O, lib, w):
 
 
 def pin_cost_gradient(O, lib, w):
-    """dF / d dx_k (central differences of Eq. 6 under X_k [+] dx) equals 2 b_k
+    """dF / d dx_k (central differences of Eq. total-error-multicue under X_k [+] dx) equals 2 b_k
     (grad_mode 1, non-unit Omega, a Huber delta that some residuals exceed)."""
     params = dict(w.params, grad_mode=1, w_depth=0.5, w_normal=0.3, huber_delta=0.05)
     s = w.sensors[0]
@@ -292,8 +294,8 @@ def pin_plane_shift(O, lib):
 
 def pin_single_channel(O, lib):
     """With Omega = diag(1, 0, 0, 0, 0), rho = identity and no occlusion test,
-    F equals the classic photometric error of Eq. 5 summed by brute force:
-    u' from Eq. 4 composed as X_j^-1 X_i, I_j^g(u') by scipy's order-1 spline
+    F equals the classic photometric error of Eq. total-error summed by brute force:
+    u' from Eq. uprime composed as X_j^-1 X_i, I_j^g(u') by scipy's order-1 spline
     (bilinear), over the source pixels whose samples are usable."""
     from scipy.ndimage import map_coordinates
     from paper_2303_16878_gb300 import synth
@@ -329,6 +331,31 @@ def pin_single_channel(O, lib):
     return abs(total - r["cost"]) / max(total, 1e-30)
 
 
+def pin_extrinsic_equivalence(O, lib, w):
+    """Supp. offset form: with extrinsic X_o and platform poses X_k the error
+    equals the error with no offset and sensor poses X_k X_o (composed here
+    with numpy), point by point; compare cost and count of every pair."""
+    from paper_2303_16878_gb300 import synth
+    Xo = synth.offset_transform(0.3, 20.0, seed=9)  # a large offset, so mistakes are visible
+    wx = synth.with_extrinsic(w, Xo)
+    a = O.linearize(wx.sensors, wx.frame_sensor, wx.channels, wx.poses_init, wx.pairs, wx.params,
+                    want_system=False, want_pairs=True, lib=lib)
+    sensor_poses = np.stack([synth.compose(X, Xo) for X in wx.poses_init])
+    b = O.linearize(w.sensors, w.frame_sensor, w.channels, sensor_poses, w.pairs, w.params,
+                    want_system=False, want_pairs=True, lib=lib)
+    assert b["count"] > 0
+    if not np.array_equal(a["pair_count"], b["pair_count"]):
+        return float(np.abs(a["pair_count"] - b["pair_count"]).max())
+    return float(np.abs(a["pair_cost"] - b["pair_cost"]).max() / max(np.abs(b["pair_cost"]).max(), 1e-30))
+
+
+def pin_jacobian_fd_extrinsic(O, lib, w):
+    """J_i, J_j against central differences with a non-identity offset X_o."""
+    from paper_2303_16878_gb300 import synth
+    wx = synth.with_extrinsic(w, synth.offset_transform(0.3, 20.0, seed=9))
+    return _fd_point_jacobians(O, lib, wx, dict(wx.params, grad_mode=1))
+
+
 def pin_cholesky(O, lib):
     rng = np.random.default_rng(14)
     worst = 0.0
@@ -357,4 +384,6 @@ def all_pins(O, lib, room, street):
         "plane_shift": pin_plane_shift(O, lib),
         "single_channel": pin_single_channel(O, lib),
         "cholesky": pin_cholesky(O, lib),
+        "extrinsic_equivalence": pin_extrinsic_equivalence(O, lib, room),
+        "jacobian_fd_extrinsic": pin_jacobian_fd_extrinsic(O, lib, room),
     }

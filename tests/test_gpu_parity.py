@@ -48,7 +48,7 @@ def _path(name):
 
 
 @pytest.mark.parametrize("path,texel,grad_mode", CASES)
-@pytest.mark.parametrize("which", ["room8", "street3"])
+@pytest.mark.parametrize("which", ["room8", "street3", "room8x"])
 def test_system_matches_oracle(oracle_lib, which, path, texel, grad_mode, request):
     w = request.getfixturevalue(which)
     params = dict(w.params, grad_mode=grad_mode)

@@ -26,6 +26,9 @@ MUTATIONS = {
     "pinhole_principal_point_swapped": ("double vy = s->fy * p[1] + s->cy * p[2];\n        double vz = p[2];\n        uv[0]",
                                         "double vy = s->fy * p[1] + s->cx * p[2];\n        double vz = p[2];\n        uv[0]"),
     "assembly_block_transposed": ("+= H12[12 * (6 * ba + a) + 6 * bb + c];", "+= H12[12 * (6 * bb + a) + 6 * ba + c];"),
+    "offset_rotation_not_transposed": ("mat3_vec(RoT, tmp, pb);", "mat3_vec(Ro, tmp, pb);"),
+    "offset_translation_sign": ("for (int a = 0; a < 3; ++a) tmp[a] = q[a] - to[a];",
+                                "for (int a = 0; a < 3; ++a) tmp[a] = q[a] + to[a];"),
     "bilinear_weight_swapped": ("const double w[4] = {(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b};",
                                 "const double w[4] = {(1 - a) * (1 - b), (1 - a) * b, a * (1 - b), a * b};"),
 }
@@ -51,7 +54,9 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("cost_gradient", lambda: P.pin_cost_gradient(oracle_lib, lib, room3)),
                     ("plane_shift", lambda: P.pin_plane_shift(oracle_lib, lib)),
                     ("single_channel", lambda: P.pin_single_channel(oracle_lib, lib)),
-                    ("cholesky", lambda: P.pin_cholesky(oracle_lib, lib))]:
+                    ("cholesky", lambda: P.pin_cholesky(oracle_lib, lib)),
+                    ("extrinsic_equivalence", lambda: P.pin_extrinsic_equivalence(oracle_lib, lib, room3)),
+                    ("jacobian_fd_extrinsic", lambda: P.pin_jacobian_fd_extrinsic(oracle_lib, lib, room3))]:
         try:
             err = fn()
         except (AssertionError, ValueError, ArithmeticError, Exception):

@@ -52,6 +52,20 @@ def test_single_channel_reduces_to_classic_photometric_error(oracle_lib):
     assert P.pin_single_channel(oracle_lib, oracle_lib.load()) < P.PIN_TOL["single_channel"]
 
 
+def test_extrinsic_offset_equals_composed_sensor_poses(oracle_lib, room3):
+    assert P.pin_extrinsic_equivalence(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["extrinsic_equivalence"]
+
+
+def test_point_jacobians_fd_with_extrinsic_offset(oracle_lib, room3):
+    assert P.pin_jacobian_fd_extrinsic(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["jacobian_fd_extrinsic"]
+
+
+def test_gauge_null_space_with_extrinsic_offset(oracle_lib, room3):
+    from paper_2303_16878_gb300 import synth
+    wx = synth.with_extrinsic(room3, synth.offset_transform(0.3, 20.0, seed=9))
+    assert P.pin_gauge(oracle_lib, oracle_lib.load(), wx) < P.PIN_TOL["gauge"]
+
+
 def test_cholesky_matches_numpy_solve(oracle_lib):
     assert P.pin_cholesky(oracle_lib, oracle_lib.load()) < P.PIN_TOL["cholesky"]
 
