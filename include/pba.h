@@ -42,6 +42,7 @@ extern "C" {
 #define PBA_ENOTPD (-4)     /* damped system not positive definite; the step was rejected */
 #define PBA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define PBA_ENOTREADY (-6)  /* a required input (frames, poses, pairs) was not set */
+#define PBA_ETOOBIG (-7)    /* a size exceeds the fixed maximum of pba_linearize_pairs_noalloc */
 
 /* projection models, Sec. III */
 #define PBA_PINHOLE 0       /* pi_p(p) = phi(K p), Eq. pinhole-projection; d is the depth */
@@ -208,6 +209,48 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
  * Fills stats (may be NULL); synchronises. */
 #define PBA_N_PHASES 6
 int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_stats* stats);
+
+/* ------------------------------------------------------------------------
+ * Linearisation without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code that is
+ * handed its device buffers by a host framework which owns the memory pool,
+ * or a loop whose memory budget is fixed at start-up, where a cudaMalloc could
+ * fail or stall the device mid-run.  It performs no cudaMalloc, cudaFree or
+ * other allocation: its working memory is a static device array of
+ * PBA_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *
+ * It linearises m directed pairs (i, j) of frames that share one sensor,
+ * exactly as pba_linearize does on the plain path (same residual, Jacobians,
+ * robust weights and validity rules as set by cfg; cfg->texel_precision,
+ * cfg->path and cfg->n_frames / sensors / frame_sensor are ignored), and
+ * writes per pair PBA_NOALLOC_PAIR_STRIDE doubles to pair_out: H12 (144,
+ * rows/cols 0-5 frame i, 6-11 frame j), b12 (12), cost, count, 2 zeros --
+ * the layout of pba_get_pair_system.
+ *
+ * Arguments: sensor, cfg in host memory; channels (n_frames x H x W x 5
+ * float32, layout of pba_upload_frames), poses (n_frames x 12 doubles), pairs
+ * (m x 2 int32) and pair_out in device memory of the current device, all
+ * owned by the caller; cuda_stream orders the work (NULL: legacy stream); the
+ * call does not synchronise.  A pair naming a frame outside [0, n_frames)
+ * yields an all-zero block.
+ *
+ * Limits and errors: PBA_ETOOBIG when m > PBA_NOALLOC_MAX_PAIRS or the image
+ * has more than 2^30 pixels; PBA_EINVAL for null pointers or a bad sensor /
+ * configuration; PBA_ECUDA when a launch fails.
+ *
+ * Sharing: the first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Every call reuses the same array and clears the accumulators it uses, so
+ * the array keeps the previous call's contents until then; calls whose device
+ * work overlaps (other streams or threads) race on it and must be serialised
+ * by the caller. */
+#define PBA_NOALLOC_MAX_PAIRS 4096
+#define PBA_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+#define PBA_NOALLOC_PAIR_STRIDE 160
+int pba_linearize_pairs_noalloc(const pba_sensor* sensor, const pba_config* cfg, const float* channels, int n_frames,
+                                const double* poses, const int32_t* pairs, int m, double* pair_out,
+                                void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,9 @@ PBA_ECUDA = -3
 PBA_ENOTPD = -4
 PBA_ETIMEOUT = -5
 PBA_ENOTREADY = -6
+PBA_ETOOBIG = -7
+PBA_NOALLOC_MAX_PAIRS = 4096
+PBA_NOALLOC_PAIR_STRIDE = 160
 
 PBA_PINHOLE = 0
 PBA_SPHERICAL = 1
@@ -28,14 +31,15 @@ PBA_TEXEL_F32 = 0
 PBA_TEXEL_F16 = 1
 
 ERROR_NAMES = {PBA_EINVAL: "PBA_EINVAL", PBA_ENOMEM: "PBA_ENOMEM", PBA_ECUDA: "PBA_ECUDA",
-               PBA_ENOTPD: "PBA_ENOTPD", PBA_ETIMEOUT: "PBA_ETIMEOUT", PBA_ENOTREADY: "PBA_ENOTREADY"}
+               PBA_ENOTPD: "PBA_ENOTPD", PBA_ETIMEOUT: "PBA_ETIMEOUT", PBA_ENOTREADY: "PBA_ENOTREADY",
+               PBA_ETOOBIG: "PBA_ETOOBIG"}
 
 # every exported symbol of include/pba.h
 EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba_upload_frames",
            "pba_frame_points", "pba_set_poses", "pba_get_poses", "pba_set_pairs", "pba_linearize",
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
-           "pba_iterate_timed"]
+           "pba_iterate_timed", "pba_linearize_pairs_noalloc"]
 PBA_N_PHASES = 6
 PHASE_NAMES = ["pair_pose", "linearize", "reduce_assemble", "solve_update", "cost_linearize", "cost_accept"]
 
@@ -106,6 +110,8 @@ def load(build_if_missing: bool = True):
             "pba_get_stats": ([vp, P(PbaIterStats)], ctypes.c_int),
             "pba_iteration_launches": ([vp, P(i32)], ctypes.c_int),
             "pba_iterate_timed": ([vp, P(ctypes.c_float), ctypes.c_int, P(PbaIterStats)], ctypes.c_int),
+            "pba_linearize_pairs_noalloc": ([P(PbaSensor), P(PbaConfig), vp, ctypes.c_int, vp, vp, ctypes.c_int, vp,
+                                             vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
