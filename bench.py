@@ -41,7 +41,7 @@ if ROOT not in sys.path:
 METRIC = "residuals/sec and ms per GN iteration, batched vs plain GPU path at stated error"
 UNIT = "residuals/s"
 WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, "
-            "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64 solve")
+            "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64-refined solve")
 
 # Algorithmic FP32 work of the linearisation kernel (derivation in the design doc):
 # per processed point (transform + spherical projection + bounds) and per
@@ -124,6 +124,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def reduce_over_ranks(seconds_or_ms: float, units: float, world: int, device=None):
+    """Whole-job aggregation across ranks: the slowest rank's time and the sum
+    of every rank's units (residuals).  With world == 1 the inputs pass through."""
+    if world <= 1:
+        return float(seconds_or_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args, rank, world, device):
@@ -134,7 +150,8 @@ def run_ours(args, rank, world, device):
     # a dedicated stream: the library enqueues on it and the events below are recorded on it
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
-    prob = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream)
+    prob = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
+                                     solver=pba.PBA_SOLVE_MIXED)
     init = np.ascontiguousarray(w.poses_init.reshape(-1, 12))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     n_points_total = sum(prob.frame_points(int(i)) for i, _ in w.pairs)
@@ -150,6 +167,7 @@ def run_ours(args, rank, world, device):
         e1.synchronize()
         return e0.elapsed_time(e1), p.get_stats()
 
+    variants = prob.autotune(2)
     for _ in range(args.warmup):
         one_step(prob)
     launches = prob.iteration_launches()
@@ -170,16 +188,7 @@ def run_ours(args, rank, world, device):
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = float(sum(ms))
-    res_local = float(sum(nvalid))
-    if world > 1:
-        t = torch.tensor([total_ms, res_local], dtype=torch.float64, device=device)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, res_all = float(tmax[0]), float(t[1])
-    else:
-        res_all = res_local
+    total_ms, res_all = reduce_over_ranks(float(sum(ms)), float(sum(nvalid)), world, device)
     value = res_all / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
@@ -196,7 +205,21 @@ def run_ours(args, rank, world, device):
 
     out = dict(value=value, ms_per_step=ms_per_step, n_valid=int(nvalid[-1]), launches=launches, clocks=clk,
                phase_ms=phase_ms, wall_s=wall, n_points=int(n_points_total), n_pairs=int(len(w.pairs)),
-               stats=stats)
+               stats=stats, variants=variants)
+
+    # the same iteration with the FP64 Cholesky solver (phase times only)
+    f64 = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
+                                    solver=pba.PBA_SOLVE_CHOLESKY_F64)
+    f64.autotune(1)
+    f64_solve = []
+    for _ in range(max(3, args.steps // 2)):
+        f64.set_poses(init)
+        f64.set_lambda(None)
+        flush.zero_()
+        _, ph = f64.iterate_timed()
+        f64_solve.append(ph["solve_update"])
+    f64.close()
+    out["solve_update_f64_ms"] = float(np.mean(f64_solve))
 
     # plain per-pair path on the same workload
     if not args.no_plain:
@@ -231,13 +254,8 @@ def run_ours(args, rank, world, device):
             if k >= args.warmup:
                 walls.append(t1 - t0)
                 ev += st["n_valid"]
-        e2e_local = ev / sum(walls)
-        if world > 1:
-            t = torch.tensor([sum(walls), float(ev)], dtype=torch.float64, device=device)
-            tmax = t.clone()
-            torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-            e2e_local = float(t[1]) / float(tmax[0])
+        wall_max, ev_all = reduce_over_ranks(sum(walls), float(ev), world, device)
+        e2e_local = ev_all / wall_max
         out["e2e"] = {"value": e2e_local, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                       "ms_per_step": 1e3 * sum(walls) / len(walls)}
     prob.close()
@@ -328,11 +346,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames": w.n_frames, "pairs": out["n_pairs"],
                        "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
-                       "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "autotuned_variants": list(out["variants"])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_linearize<f16, full>",
                          "kernel_ms": lin_ms},
             "phase_ms": ph,
+            "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|)",
+            "solve_update_f64_cholesky_ms": out["solve_update_f64_ms"],
             "gpu_launches": out["launches"] * args.steps,
             "clocks": out["clocks"],
         }

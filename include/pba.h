@@ -56,6 +56,14 @@ extern "C" {
 #define PBA_TEXEL_F32 0
 #define PBA_TEXEL_F16 1     /* intensity and normal in binary16 (round to nearest even) */
 
+/* damped solve (Sec. IV-C, LM): both deliver the FP64 solution of
+ * (H_ff + lambda I) dx_f = -b_f.  CHOLESKY_F64 factorises in FP64;
+ * MIXED factorises the Jacobi-scaled system in FP32 and refines the solution
+ * with FP64 residuals until |r| <= 1e-10 |b| (else the step is rejected and
+ * lambda grows), which suits GB300's FP64 rate of ~1/64 of FP32. */
+#define PBA_SOLVE_CHOLESKY_F64 0
+#define PBA_SOLVE_MIXED 1
+
 /* image-gradient modes (Supp., image Jacobians) */
 #define PBA_GRAD_CENTRAL 0  /* central differences at pixels, bilinearly interpolated (paper) */
 #define PBA_GRAD_BILINEAR 1 /* exact derivative of the bilinear interpolant */
@@ -95,7 +103,7 @@ typedef struct {
     int32_t grad_mode;          /* PBA_GRAD_CENTRAL or PBA_GRAD_BILINEAR */
     int32_t texel_precision;    /* PBA_TEXEL_F32 or PBA_TEXEL_F16 (batched path only) */
     int32_t path;               /* PBA_PATH_BATCHED or PBA_PATH_PLAIN */
-    int32_t reserved;           /* 0 */
+    int32_t solver;             /* PBA_SOLVE_CHOLESKY_F64 or PBA_SOLVE_MIXED */
 } pba_config;
 
 /* Outcome of one Levenberg-Marquardt iteration. */
@@ -198,6 +206,13 @@ int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
 
 /* Number of kernel launches one pba_iterate performs (for accounting). */
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
+
+/* Pick, by timing them on this problem, the fastest occupancy variant of the
+ * batched linearisation kernel for the full pass and for the cost-only pass
+ * (each launched repeats + 1 times, the first as warm-up); later iterations
+ * use the choice.  Reports the choice (0 or 1) in the optional outputs.
+ * Needs frames, poses and pairs; synchronises.  A no-op on the plain path. */
+int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost);
 
 /* Instrumentation: one iteration like pba_iterate, enqueued launch by launch
  * (not as a graph) with CUDA events recorded on the problem's stream between

@@ -14,11 +14,11 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (PBA_PATH_BATCHED, PBA_PATH_PLAIN, PBA_PINHOLE, PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32,
-                   PbaError)
+from ._lib import (PBA_PATH_BATCHED, PBA_PATH_PLAIN, PBA_PINHOLE, PBA_SOLVE_CHOLESKY_F64, PBA_SOLVE_MIXED,
+                   PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32, PbaError)
 
 __all__ = ["Problem", "PbaError", "PBA_PATH_BATCHED", "PBA_PATH_PLAIN", "PBA_TEXEL_F16", "PBA_TEXEL_F32",
-           "PBA_PINHOLE", "PBA_SPHERICAL", "problem_from_workload"]
+           "PBA_PINHOLE", "PBA_SPHERICAL", "PBA_SOLVE_CHOLESKY_F64", "PBA_SOLVE_MIXED", "problem_from_workload"]
 
 
 def _is_torch(x) -> bool:
@@ -34,7 +34,8 @@ class Problem:
     """One bundle-adjustment problem on the current CUDA device (C: pba_problem)."""
 
     def __init__(self, sensors: Sequence, n_frames: int, params: Dict, frame_sensor=None,
-                 path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXEL_F16, stream=None):
+                 path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXEL_F16, stream=None,
+                 solver: int = PBA_SOLVE_CHOLESKY_F64):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.n_frames = int(n_frames)
@@ -66,7 +67,8 @@ class Problem:
         cfg.grad_mode = int(params.get("grad_mode", 0))
         cfg.texel_precision = int(texel)
         cfg.path = int(path)
-        self.path, self.texel = int(path), int(texel)
+        cfg.solver = int(solver)
+        self.path, self.texel, self.solver = int(path), int(texel), int(solver)
         st = self._lib.pba_create(ctypes.byref(cfg), ctypes.c_void_p(self._stream_handle(stream)),
                                   ctypes.byref(self._h))
         if st != 0:
@@ -216,6 +218,13 @@ class Problem:
         self._check(self._lib.pba_iterate_timed(self._h, ms, _lib.PBA_N_PHASES, ctypes.byref(s)), "iterate_timed")
         return _stats(s), dict(zip(_lib.PHASE_NAMES, list(ms)))
 
+    def autotune(self, repeats: int = 2):
+        """Time the occupancy variants of the linearisation kernel on this
+        problem and keep the fastest; returns (variant_full, variant_cost)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.pba_autotune(self._h, int(repeats), ctypes.byref(a), ctypes.byref(b)), "autotune")
+        return a.value, b.value
+
     def iteration_launches(self) -> int:
         n = ctypes.c_int32()
         self._check(self._lib.pba_iteration_launches(self._h, ctypes.byref(n)), "iteration_launches")
@@ -223,13 +232,14 @@ class Problem:
 
 
 def problem_from_workload(w, path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXEL_F16, params: Optional[Dict] = None,
-                          poses=None, stream=None) -> Problem:
+                          poses=None, stream=None, solver: int = PBA_SOLVE_CHOLESKY_F64) -> Problem:
     """Create a Problem from a synth.Workload: upload every frame (grouped by
     image size), set the initial poses and the pair list."""
     prm = dict(w.params)
     if params:
         prm.update(params)
-    p = Problem(w.sensors, w.n_frames, prm, frame_sensor=w.frame_sensor, path=path, texel=texel, stream=stream)
+    p = Problem(w.sensors, w.n_frames, prm, frame_sensor=w.frame_sensor, path=path, texel=texel, stream=stream,
+                solver=solver)
     k = 0
     while k < w.n_frames:
         j = k

@@ -29,6 +29,8 @@ PBA_PATH_BATCHED = 0
 PBA_PATH_PLAIN = 1
 PBA_TEXEL_F32 = 0
 PBA_TEXEL_F16 = 1
+PBA_SOLVE_CHOLESKY_F64 = 0
+PBA_SOLVE_MIXED = 1
 
 ERROR_NAMES = {PBA_EINVAL: "PBA_EINVAL", PBA_ENOMEM: "PBA_ENOMEM", PBA_ECUDA: "PBA_ECUDA",
                PBA_ENOTPD: "PBA_ENOTPD", PBA_ETIMEOUT: "PBA_ETIMEOUT", PBA_ENOTREADY: "PBA_ENOTREADY",
@@ -39,7 +41,7 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_frame_points", "pba_set_poses", "pba_get_poses", "pba_set_pairs", "pba_linearize",
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
-           "pba_iterate_timed", "pba_linearize_pairs_noalloc"]
+           "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune"]
 PBA_N_PHASES = 6
 PHASE_NAMES = ["pair_pose", "linearize", "reduce_assemble", "solve_update", "cost_linearize", "cost_accept"]
 
@@ -57,7 +59,7 @@ class PbaConfig(ctypes.Structure):
                 ("huber_delta", ctypes.c_double), ("occ_abs", ctypes.c_double), ("occ_rel", ctypes.c_double),
                 ("z_min", ctypes.c_double), ("range_min", ctypes.c_double), ("range_max", ctypes.c_double),
                 ("grad_mode", ctypes.c_int32), ("texel_precision", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("solver", ctypes.c_int32)]
 
 
 class PbaIterStats(ctypes.Structure):
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True):
             "pba_get_stats": ([vp, P(PbaIterStats)], ctypes.c_int),
             "pba_iteration_launches": ([vp, P(i32)], ctypes.c_int),
             "pba_iterate_timed": ([vp, P(ctypes.c_float), ctypes.c_int, P(PbaIterStats)], ctypes.c_int),
+            "pba_autotune": ([vp, ctypes.c_int, P(i32), P(i32)], ctypes.c_int),
             "pba_linearize_pairs_noalloc": ([P(PbaSensor), P(PbaConfig), vp, ctypes.c_int, vp, vp, ctypes.c_int, vp,
                                              vp], ctypes.c_int),
         }

@@ -55,7 +55,9 @@ struct pba_problem {
     double* d_b = nullptr;
     double* d_A = nullptr;
     double* d_rhs = nullptr;
+    double* d_Dinv = nullptr;  // inverses of the Cholesky diagonal tiles
     int n_pad = 0;
+    MixedWork mixed{};  // buffers of the mixed-precision solve
     int* d_queue = nullptr;  // two counters: full pass, cost pass
 
     // pair-dependent buffers
@@ -83,6 +85,7 @@ struct pba_problem {
     bool mask_valid = false;
     bool linearized = false;
     int grid_full = 0, grid_cost = 0;
+    int variant_full = 0, variant_cost = 0;  // occupancy variants chosen by pba_autotune
     LinParams prm{};
 
     cudaGraph_t graph = nullptr;
@@ -168,7 +171,7 @@ int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev =
         const bool mask = p->mask_export;
         CUDA_TRY(p, launch_linearize(true, mask, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue,
                                      p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials,
-                                     p->d_mask, p->grid_full, s));
+                                     p->d_mask, p->grid_full, p->variant_full, s));
         if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
         CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M, true,
                                        p->d_blocks, s));
@@ -184,13 +187,19 @@ int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev =
 int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr) {
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[3], s));
     CUDA_TRY(p, launch_lm_prepare(p->d_H, p->N, p->d_state, lambda, s));
-    CUDA_TRY(p, launch_damp(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->d_A, p->d_rhs, s));
     int nc = 0;
-    CUDA_TRY(p, launch_cholesky(p->d_A, p->n_pad, p->d_state, s, &nc));
-    CUDA_TRY(p, launch_trsv(p->d_A, p->n_pad, p->d_rhs, p->d_state, s));
+    if (p->cfg.solver == PBA_SOLVE_MIXED) {
+        CUDA_TRY(p, launch_solve_mixed(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->mixed, 3, p->d_rhs, s, &nc));
+        *nl += 1 + nc;
+    } else {
+        CUDA_TRY(p, launch_damp(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->d_A, p->d_rhs, s));
+        CUDA_TRY(p, launch_cholesky(p->d_A, p->d_Dinv, p->n_pad, p->d_state, s, &nc));
+        CUDA_TRY(p, launch_trsv(p->d_A, p->d_Dinv, p->n_pad, p->d_rhs, p->d_state, s));
+        *nl += 3 + nc;
+    }
     CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->d_state, p->d_cand, s));
     CUDA_TRY(p, launch_pair_pose(p->d_cand, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
-    *nl += 5 + nc;
+    *nl += 2;
     if (p->cfg.path == PBA_PATH_PLAIN) {
         CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
         if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
@@ -209,7 +218,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
         if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
         CUDA_TRY(p, launch_linearize(false, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue + 1,
                                      p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials, nullptr,
-                                     p->grid_cost, s));
+                                     p->grid_cost, p->variant_cost, s));
         if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
         CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_cand, p->d_pair_Xo, p->M, false,
                                        p->d_blocks_cand, s));
@@ -263,6 +272,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     if (cfg->grad_mode != 0 && cfg->grad_mode != 1) return PBA_EINVAL;
     if (cfg->texel_precision != 0 && cfg->texel_precision != 1) return PBA_EINVAL;
     if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return PBA_EINVAL;
+    if (cfg->solver != PBA_SOLVE_CHOLESKY_F64 && cfg->solver != PBA_SOLVE_MIXED) return PBA_EINVAL;
     for (int s = 0; s < cfg->n_sensors; ++s) {
         const pba_sensor& S = cfg->sensors[s];
         if ((S.model != PBA_PINHOLE && S.model != PBA_SPHERICAL) || S.width < 4 || S.height < 4) return PBA_EINVAL;
@@ -330,7 +340,16 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
               alloc((void**)&p->d_b, sizeof(double) * n6) &&
               alloc((void**)&p->d_A, sizeof(double) * (size_t)p->n_pad * p->n_pad) &&
               alloc((void**)&p->d_rhs, sizeof(double) * p->n_pad) &&
-              alloc((void**)&p->d_queue, sizeof(int) * 2);
+              alloc((void**)&p->d_Dinv, sizeof(double) * (size_t)p->n_pad * kTile) &&
+              alloc((void**)&p->d_queue, sizeof(int) * 2) &&
+              (cfg->solver != PBA_SOLVE_MIXED ||
+               (alloc((void**)&p->mixed.A32, sizeof(float) * (size_t)p->n_pad * p->n_pad) &&
+                alloc((void**)&p->mixed.D32, sizeof(float) * (size_t)p->n_pad * kTile) &&
+                alloc((void**)&p->mixed.r32, sizeof(float) * p->n_pad) &&
+                alloc((void**)&p->mixed.bs, sizeof(double) * p->n_pad) &&
+                alloc((void**)&p->mixed.x, sizeof(double) * p->n_pad) &&
+                alloc((void**)&p->mixed.dscale, sizeof(double) * p->n_pad) &&
+                alloc((void**)&p->mixed.norms, sizeof(double) * 2)));
     if (!ok) return bail(PBA_ENOMEM);
 
     std::vector<FrameInfo> fi(p->N);
@@ -381,8 +400,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->prm.occ_rel = (float)cfg->occ_rel;
     p->prm.z_min = (float)cfg->z_min;
     p->prm.grad_mode = cfg->grad_mode;
-    p->grid_full = linearize_grid(cfg->texel_precision, true);
-    p->grid_cost = linearize_grid(cfg->texel_precision, false);
+    p->grid_full = linearize_grid(cfg->texel_precision, true, 0);
+    p->grid_cost = linearize_grid(cfg->texel_precision, false, 0);
     *out = p;
     return PBA_OK;
 }
@@ -408,7 +427,15 @@ void pba_destroy(pba_problem* p) {
     dfree(p->d_b);
     dfree(p->d_A);
     dfree(p->d_rhs);
+    dfree(p->d_Dinv);
     dfree(p->d_queue);
+    dfree(p->mixed.A32);
+    dfree(p->mixed.D32);
+    dfree(p->mixed.r32);
+    dfree(p->mixed.bs);
+    dfree(p->mixed.x);
+    dfree(p->mixed.dscale);
+    dfree(p->mixed.norms);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     if (p->own_stream) cudaStreamDestroy(p->own_stream);
     delete p;
@@ -759,6 +786,56 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
     for (auto& e : ev) cudaEventDestroy(e);
     p->linearized = false;
     return st;
+}
+
+int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost) {
+    int st = ready(p);
+    if (st) return st;
+    if (repeats < 1) repeats = 1;
+    if (p->cfg.path != PBA_PATH_BATCHED) {
+        if (variant_full) *variant_full = 0;
+        if (variant_cost) *variant_cost = 0;
+        return PBA_OK;
+    }
+    cudaEvent_t e0, e1;
+    CUDA_TRY(p, cudaEventCreate(&e0));
+    CUDA_TRY(p, cudaEventCreate(&e1));
+    CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
+    int best[2] = {0, 0};
+    for (int full = 1; full >= 0; --full) {
+        float best_ms = 3.4e38f;
+        for (int v = 0; v < 2; ++v) {
+            const int grid = linearize_grid(p->cfg.texel_precision, full != 0, v);
+            float total = 0.f;
+            for (int r = 0; r <= repeats; ++r) {  // r = 0 is a warm-up
+                CUDA_TRY(p, cudaMemsetAsync(p->d_queue, 0, sizeof(int), p->stream));
+                CUDA_TRY(p, cudaEventRecord(e0, p->stream));
+                CUDA_TRY(p, launch_linearize(full != 0, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks,
+                                             p->d_queue, p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm,
+                                             p->d_partials, nullptr, grid, v, p->stream));
+                CUDA_TRY(p, cudaEventRecord(e1, p->stream));
+                CUDA_TRY(p, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(p, cudaEventElapsedTime(&ms, e0, e1));
+                if (r > 0) total += ms;
+            }
+            if (total < best_ms) {
+                best_ms = total;
+                best[full] = v;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->variant_full = best[1];
+    p->variant_cost = best[0];
+    p->grid_full = linearize_grid(p->cfg.texel_precision, true, p->variant_full);
+    p->grid_cost = linearize_grid(p->cfg.texel_precision, false, p->variant_cost);
+    drop_graph(p);
+    p->linearized = false;
+    if (variant_full) *variant_full = p->variant_full;
+    if (variant_cost) *variant_cost = p->variant_cost;
+    return PBA_OK;
 }
 
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches) {

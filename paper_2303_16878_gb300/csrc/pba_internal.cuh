@@ -128,9 +128,10 @@ cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const
 cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const int4* chunks, int n_chunks,
                              int* queue, const PairStatic* ps, const PairPose* pp, const float4* pts_pg,
                              const float4* pts_n, const void* texels, const LinParams& prm,
-                             float* partials, uint32_t* mask_bits, int grid, cudaStream_t s);
+                             float* partials, uint32_t* mask_bits, int grid, int variant, cudaStream_t s);
 
-int linearize_grid(int texel_precision, bool full);
+// Persistent grid (SMs x resident blocks) of a linearisation variant (0 or 1, see launch_linearize).
+int linearize_grid(int texel_precision, bool full, int variant);
 
 cudaError_t launch_pair_reduce(const float* partials, const PairStatic* ps, const int2* pair_frames,
                                const double* poses, const double* pair_Xo, int m, bool full,
@@ -153,9 +154,28 @@ cudaError_t launch_lm_prepare(const double* H, int n_frames, LmState* st, double
 cudaError_t launch_damp(const double* H, const double* b, int n_frames, int n_pad, const LmState* st,
                         double* A, double* rhs, cudaStream_t s);
 
-cudaError_t launch_cholesky(double* A, int n_pad, LmState* st, cudaStream_t s, int* n_launches);
+// Tiled Cholesky A = L L^T in place (L in the lower triangle, L^T copied to the
+// upper one); Dinv receives the inverses of the diagonal tiles (n_pad / 32 tiles of 32 x 32).
+cudaError_t launch_cholesky(double* A, double* Dinv, int n_pad, LmState* st, cudaStream_t s, int* n_launches);
 
-cudaError_t launch_trsv(const double* A, int n_pad, double* rhs, const LmState* st, cudaStream_t s);
+cudaError_t launch_trsv(const double* A, const double* Dinv, int n_pad, double* rhs, const LmState* st,
+                        cudaStream_t s);
+
+// Working buffers of the mixed-precision solve (all n_pad long except A32, n_pad^2).
+struct MixedWork {
+    float* A32;
+    float* D32;     // inverses of the diagonal tiles (n_pad * 32)
+    float* r32;
+    double* bs;
+    double* x;
+    double* dscale;
+    double* norms;  // 2
+};
+
+// Jacobi-scaled FP32 Cholesky + FP64 iterative refinement; writes dx_f (n_pad) = rhs layout
+// of launch_trsv.  Sets st->chol_fail when a pivot fails or the refinement misses its tolerance.
+cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, int n_pad, LmState* st,
+                               MixedWork& w, int refinements, double* dx, cudaStream_t s, int* n_launches);
 
 cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const LmState* st,
                            double* cand, cudaStream_t s);

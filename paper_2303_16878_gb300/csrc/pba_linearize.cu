@@ -65,6 +65,33 @@ __global__ void k_pair_pose(const double* __restrict__ poses, const int2* __rest
     out[p] = o;
 }
 
+// ------------------------------------------------------------ arctangent
+
+// atan2(y, x) for the spherical projection: reduce to t = min(|x|,|y|) /
+// max(|x|,|y|) in [0, 1], approximate atan(t) = t P(t^2) with a degree-8
+// polynomial fitted by least squares (gen_atan_poly.py prints the
+// coefficients and its float32 error, max 3e-7 rad), then reflect into the
+// octant.  atan2(0, 0) = 0.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    const float s = t * t;
+    float p = 0.002932762f;
+    p = fmaf(p, s, -0.01641319f);
+    p = fmaf(p, s, 0.043278243f);
+    p = fmaf(p, s, -0.075569004f);
+    p = fmaf(p, s, 0.10667487f);
+    p = fmaf(p, s, -0.14211106f);
+    p = fmaf(p, s, 0.19993694f);
+    p = fmaf(p, s, -0.33333138f);
+    p = fmaf(p, s, 1.0f);
+    float r = t * p;
+    if (ay > ax) r = 1.57079637f - r;
+    if (x < 0.f) r = 3.14159274f - r;
+    return y < 0.f ? -r : r;
+}
+
 // ------------------------------------------------------------ texel access
 
 struct Texel {
@@ -73,7 +100,7 @@ struct Texel {
 };
 
 template <int TEXEL>
-__device__ __forceinline__ Texel load_texel(const void* __restrict__ base, long long idx) {
+__device__ __forceinline__ Texel load_texel(const void* __restrict__ base, int idx) {
     Texel t;
     if (TEXEL == 1) {
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + idx);
@@ -179,7 +206,9 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
 
     int cm1, cc, cp1, cp2;
     stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
-    const long long rr0 = tex_off + (long long)r0 * W, rm1 = rr0 - W, rp1 = rr0 + W, rp2 = rp1 + W;
+    tex = TEXEL == 1 ? (const void*)(reinterpret_cast<const Tex16*>(tex) + tex_off)
+                     : (const void*)(reinterpret_cast<const Tex32*>(tex) + tex_off);
+    const int rr0 = r0 * W, rm1 = rr0 - W, rp1 = rr0 + W, rp2 = rp1 + W;
     float gu[5], gv[5];
     {
         float A[5], B[5], C[5], D[5];
@@ -266,8 +295,8 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
 // 12-texel stencil), sampled values, residual, occlusion test, Huber weight and
 // cost.  Valid residuals are compacted into the warp's queue; stage 2 runs on
 // full warps of them.
-template <int TEXEL, bool FULL, bool MASK>
-__global__ void __launch_bounds__(kLinThreads, 2)
+template <int TEXEL, bool FULL, bool MASK, int MINB>
+__global__ void __launch_bounds__(kLinThreads, MINB)
     k_linearize(const int4* __restrict__ chunks, int n_chunks, int* __restrict__ queue,
                 const PairStatic* __restrict__ ps, const PairPose* __restrict__ pp,
                 const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
@@ -295,6 +324,8 @@ __global__ void __launch_bounds__(kLinThreads, 2)
 #pragma unroll
         for (int k = 0; k < 3; ++k) av[k] = pp[pair].a[k];
         const bool wrap = model == 1;
+        const void* tex_j = TEXEL == 1 ? (const void*)(reinterpret_cast<const Tex16*>(tex) + tex_off)
+                                       : (const void*)(reinterpret_cast<const Tex32*>(tex) + tex_off);
         const float umax = wrap ? 3.4e38f : (float)(W - 2);
         const float umin = wrap ? -3.4e38f : 1.f;
         const float vmax = (float)(Hh - 2);
@@ -332,8 +363,8 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                     const float rxy2 = fmaf(qx, qx, qy * qy);
                     zeta_d = sqrtf(fmaf(qz, qz, rxy2));
                     ok = zeta_d > prm.z_min;
-                    u = fmaf(fx, atan2f(qy, qx), cx);
-                    v = fmaf(fy, atan2f(qz, sqrtf(rxy2)), cy);
+                    u = fmaf(fx, atan2_poly(qy, qx), cx);
+                    v = fmaf(fy, atan2_poly(qz, sqrtf(rxy2)), cy);
                 }
                 ok = ok && v >= 1.f && v < vmax && u >= umin && u < umax;
                 if (ok) {
@@ -346,9 +377,9 @@ __global__ void __launch_bounds__(kLinThreads, 2)
                     stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
                     c0 = cc;
                     // a4: the four bilinear taps; their usable flags decide the 12-texel stencil
-                    const long long rr0 = tex_off + (long long)r0 * W, rp1 = rr0 + W;
-                    const Texel A = load_texel<TEXEL>(tex, rr0 + cc), B = load_texel<TEXEL>(tex, rr0 + cp1);
-                    const Texel C = load_texel<TEXEL>(tex, rp1 + cc), D = load_texel<TEXEL>(tex, rp1 + cp1);
+                    const int rr0 = r0 * W, rp1 = rr0 + W;
+                    const Texel A = load_texel<TEXEL>(tex_j, rr0 + cc), B = load_texel<TEXEL>(tex_j, rr0 + cp1);
+                    const Texel C = load_texel<TEXEL>(tex_j, rp1 + cc), D = load_texel<TEXEL>(tex_j, rp1 + cp1);
                     ok = A.usable && B.usable && C.usable && D.usable;
                     const float wA = (1.f - fa) * (1.f - fb), wB = fa * (1.f - fb), wC = (1.f - fa) * fb, wD = fa * fb;
                     float xa[5], xb[5], xc[5], xd[5], s[5];
@@ -545,25 +576,33 @@ cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const
     return cudaGetLastError();
 }
 
-template <int TEXEL, bool FULL, bool MASK>
+template <int TEXEL, bool FULL, bool MASK, int MINB>
 static void* lin_kernel() {
-    return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK>);
+    return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK, MINB>);
 }
 
-static void* pick(int texel_precision, bool full, bool mask) {
+// Occupancy variants (blocks of 256 threads per SM the register budget aims
+// at): full pass 2 or 3, cost-only pass 3 or 4.  variant 0 = the lower one.
+template <int TEXEL, bool FULL, bool MASK>
+static void* pick_minb(int variant) {
+    if (FULL) return variant ? lin_kernel<TEXEL, FULL, MASK, 3>() : lin_kernel<TEXEL, FULL, MASK, 2>();
+    return variant ? lin_kernel<TEXEL, FULL, MASK, 4>() : lin_kernel<TEXEL, FULL, MASK, 3>();
+}
+
+static void* pick(int texel_precision, bool full, bool mask, int variant) {
     if (texel_precision == 1) {
-        if (full) return mask ? lin_kernel<1, true, true>() : lin_kernel<1, true, false>();
-        return mask ? lin_kernel<1, false, true>() : lin_kernel<1, false, false>();
+        if (full) return mask ? pick_minb<1, true, true>(variant) : pick_minb<1, true, false>(variant);
+        return mask ? pick_minb<1, false, true>(variant) : pick_minb<1, false, false>(variant);
     }
-    if (full) return mask ? lin_kernel<0, true, true>() : lin_kernel<0, true, false>();
-    return mask ? lin_kernel<0, false, true>() : lin_kernel<0, false, false>();
+    if (full) return mask ? pick_minb<0, true, true>(variant) : pick_minb<0, true, false>(variant);
+    return mask ? pick_minb<0, false, true>(variant) : pick_minb<0, false, false>(variant);
 }
 
-int linearize_grid(int texel_precision, bool full) {
+int linearize_grid(int texel_precision, bool full, int variant) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pick(texel_precision, full, false),
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pick(texel_precision, full, false, variant),
                                                   kLinThreads, 0);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
@@ -572,10 +611,11 @@ int linearize_grid(int texel_precision, bool full) {
 cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const int4* chunks, int n_chunks, int* queue,
                              const PairStatic* ps, const PairPose* pp, const float4* pts_pg, const float4* pts_n,
                              const void* texels, const LinParams& prm, float* partials, uint32_t* mask_bits,
-                             int grid, cudaStream_t s) {
+                             int grid, int variant, cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    if (grid > n_chunks) grid = n_chunks;
-    void* fn = pick(texel_precision, full, mask);
+    const int warps = (n_chunks + 0);
+    if (grid * (kLinThreads / 32) > warps) grid = (warps + kLinThreads / 32 - 1) / (kLinThreads / 32);
+    void* fn = pick(texel_precision, full, mask, variant);
     LinParams prm_copy = prm;
     void* args[] = {(void*)&chunks, (void*)&n_chunks, (void*)&queue, (void*)&ps, (void*)&pp, (void*)&pts_pg,
                     (void*)&pts_n, (void*)&texels, (void*)&prm_copy, (void*)&partials, (void*)&mask_bits};

@@ -128,70 +128,116 @@ __global__ void k_damp(const double* __restrict__ H, const double* __restrict__ 
 // tiles of 32 x 32: factor the diagonal tile, solve the panel below it,
 // update the trailing lower triangle.
 
-__global__ void __launch_bounds__(1024) k_potrf(double* __restrict__ A, int n_pad, int k, LmState* st) {
+// Diagonal tile, 256 threads (thread (c, g) owns column c, rows g, g+8, g+16,
+// g+24).  The trailing update of pivot j uses the unscaled column:
+// T[r][c] -= T[r][j] T[c][j] / T[j][j], so each step needs one barrier and one
+// reciprocal, computed by the owner of the next pivot right after its own
+// update.  The same row operations applied to an identity block R give
+// R = Lh^-1 for the unit-lower factor of T = Lh diag(d) Lh^T, so the tile
+// inverse L^-1 = diag(d)^-1/2 R comes out of the same 31 steps (columns c <= j
+// update R while columns c > j update T).  The columns are scaled by
+// 1 / sqrt(pivot) once at the end.
+template <typename F>
+__global__ void __launch_bounds__(256) k_potrf(F* __restrict__ A, int n_pad, int k, LmState* st, F* __restrict__ Dinv) {
     if (st->chol_fail) return;
-    __shared__ double T[kTile][kTile + 1];
-    __shared__ double inv_d;
+    __shared__ F T[kTile][kTile + 1];
+    __shared__ F R[kTile][kTile + 1];
+    __shared__ F inv_piv[kTile];
     __shared__ int fail;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = threadIdx.x, g = threadIdx.y;  // 32 x 8
     const long long base = (long long)(k * kTile) * n_pad + k * kTile;
-    T[ty][tx] = A[base + (long long)ty * n_pad + tx];
-    if (tx == 0 && ty == 0) fail = 0;
+    for (int r = g; r < kTile; r += 8) {
+        T[r][c] = A[base + (long long)r * n_pad + c];
+        R[r][c] = r == c ? F(1) : F(0);
+    }
+    if (c == 0 && g == 0) fail = 0;
     __syncthreads();
-    for (int j = 0; j < kTile; ++j) {
-        if (tx == j && ty == j) {
-            const double v = T[j][j];
-            if (!(v > 0.0)) {
-                fail = 1;
-            } else {
-                const double d = sqrt(v);
-                T[j][j] = d;
-                inv_d = 1.0 / d;
-            }
-        }
-        __syncthreads();
+    if (c == 0 && g == 0) {
+        const F p0 = T[0][0];
+        if (!(p0 > F(0))) fail = 1;
+        else inv_piv[0] = F(1) / p0;
+    }
+    __syncthreads();
+    for (int j = 0; j < kTile - 1; ++j) {
         if (fail) break;
-        if (tx == j && ty > j) T[ty][j] *= inv_d;
-        __syncthreads();
-        if (ty > j && tx > j && tx <= ty) T[ty][tx] -= T[ty][j] * T[tx][j];
+        const F ip = inv_piv[j];
+        if (c > j) {
+            const F tcj = T[c][j] * ip;
+            for (int r = g; r < kTile; r += 8)
+                if (r >= c) T[r][c] -= T[r][j] * tcj;
+        } else {
+            // row operation on the identity block: R[r] -= (T[r][j] / T[j][j]) R[j], r > j
+            const F rjc = R[j][c] * ip;
+            for (int r = g; r < kTile; r += 8)
+                if (r > j) R[r][c] -= T[r][j] * rjc;
+        }
+        // the owner of the next pivot (row j+1, column j+1) computes its reciprocal
+        if (c == j + 1 && ((j + 1) & 7) == g) {
+            const F pn = T[j + 1][j + 1];
+            if (!(pn > F(0))) fail = 1;
+            else inv_piv[j + 1] = F(1) / pn;
+        }
         __syncthreads();
     }
     if (fail) {
-        if (tx == 0 && ty == 0) st->chol_fail = 1;
+        if (c == 0 && g == 0) st->chol_fail = 1;
         return;
     }
-    if (tx <= ty) A[base + (long long)ty * n_pad + tx] = T[ty][tx];
+    // L[r][c] = T[r][c] / sqrt(T[c][c]) for r >= c, L^T into the upper triangle;
+    // L^-1[r][c] = R[r][c] / sqrt(T[r][r]) for r >= c
+    const F s = sqrt(inv_piv[c]);
+    F* Dk = Dinv ? Dinv + (long long)k * kTile * kTile : nullptr;
+    for (int r = g; r < kTile; r += 8) {
+        if (r >= c) {
+            const F l = T[r][c] * s;
+            A[base + (long long)r * n_pad + c] = l;
+            A[base + (long long)c * n_pad + r] = l;
+        }
+        if (Dk) Dk[r * kTile + c] = r >= c ? R[r][c] * sqrt(inv_piv[r]) : F(0);
+    }
 }
 
-// L_ik = A_ik L_kk^{-T} for tiles i > k (one block per tile).
-__global__ void __launch_bounds__(1024) k_trsm(double* __restrict__ A, int n_pad, int k, const LmState* st) {
+// L_ik = A_ik L_kk^{-T} for tiles i > k (one block per tile, 256 threads).
+// Row r: x[m] = (a[m] - sum_{c<m} x[c] L[m][c]) / L[m][m].  With the
+// column-normalised factor U[c][m] = L[c][m] / L[m][m] the recurrence runs on
+// y[m] = x[m] L[m][m]: y[c] -= y[m] U[c][m], one barrier per column.
+template <typename F>
+__global__ void __launch_bounds__(256) k_trsm(F* __restrict__ A, int n_pad, int k, const LmState* st) {
     if (st->chol_fail) return;
-    __shared__ double L[kTile][kTile + 1];
-    __shared__ double X[kTile][kTile + 1];
-    __shared__ double inv[kTile];
+    __shared__ F U[kTile][kTile + 1];
+    __shared__ F Y[kTile][kTile + 1];
+    __shared__ F inv[kTile];
     const int i = k + 1 + blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = threadIdx.x, g = threadIdx.y;
     const long long lk = (long long)(k * kTile) * n_pad + k * kTile;
     const long long ak = (long long)(i * kTile) * n_pad + k * kTile;
-    L[ty][tx] = A[lk + (long long)ty * n_pad + tx];
-    X[ty][tx] = A[ak + (long long)ty * n_pad + tx];
-    if (ty == 0) inv[tx] = 1.0 / A[lk + (long long)tx * n_pad + tx];
+    if (g == 0) inv[c] = F(1) / A[lk + (long long)c * n_pad + c];
+    for (int r = g; r < kTile; r += 8) Y[r][c] = A[ak + (long long)r * n_pad + c];
     __syncthreads();
-    // row ty: x L^T = a  <=>  x[m] = (a[m] - sum_{c<m} x[c] L[m][c]) / L[m][m]
-    for (int m = 0; m < kTile; ++m) {
-        if (tx == m) X[ty][m] *= inv[m];
-        __syncthreads();
-        if (tx > m) X[ty][tx] -= X[ty][m] * L[tx][m];
+    for (int r = g; r < kTile; r += 8) U[r][c] = r > c ? A[lk + (long long)r * n_pad + c] * inv[c] : F(0);
+    __syncthreads();
+    for (int m = 0; m < kTile - 1; ++m) {
+        if (c > m) {
+            const F u = U[c][m];
+            for (int r = g; r < kTile; r += 8) Y[r][c] -= Y[r][m] * u;
+        }
         __syncthreads();
     }
-    A[ak + (long long)ty * n_pad + tx] = X[ty][tx];
+    // L_ik, and L_ik^T into the upper tile (k, i)
+    const long long at = (long long)(k * kTile) * n_pad + i * kTile;
+    for (int r = g; r < kTile; r += 8) {
+        const F l = Y[r][c] * inv[c];
+        A[ak + (long long)r * n_pad + c] = l;
+        A[at + (long long)c * n_pad + r] = l;
+    }
 }
 
 // A_ij -= L_ik L_jk^T for k < j <= i (one block per tile of the trailing lower triangle).
-__global__ void __launch_bounds__(1024) k_syrk(double* __restrict__ A, int n_pad, int k, int nt, const LmState* st) {
+template <typename F>
+__global__ void __launch_bounds__(1024) k_syrk(F* __restrict__ A, int n_pad, int k, int nt, const LmState* st) {
     if (st->chol_fail) return;
-    __shared__ double Li[kTile][kTile + 1];
-    __shared__ double Lj[kTile][kTile + 1];
+    __shared__ F Li[kTile][kTile + 1];
+    __shared__ F Lj[kTile][kTile + 1];
     // decode blockIdx.x -> (i, j), k < j <= i < nt, column-major over j
     int idx = blockIdx.x, j = k + 1;
     while (idx >= nt - j) {
@@ -203,59 +249,157 @@ __global__ void __launch_bounds__(1024) k_syrk(double* __restrict__ A, int n_pad
     Li[ty][tx] = A[(long long)(i * kTile + ty) * n_pad + k * kTile + tx];
     Lj[ty][tx] = A[(long long)(j * kTile + ty) * n_pad + k * kTile + tx];
     __syncthreads();
-    double s = 0.0;
+    F s = F(0);
 #pragma unroll 8
     for (int m = 0; m < kTile; ++m) s += Li[ty][m] * Lj[tx][m];
     A[(long long)(i * kTile + ty) * n_pad + j * kTile + tx] -= s;
 }
 
 // ------------------------------------------------------------------ triangular solves
-// One block: L y = rhs, then L^T x = y, tile by tile; x overwrites rhs.
-__global__ void __launch_bounds__(1024) k_trsv(const double* __restrict__ A, int n_pad, double* __restrict__ x,
-                                               const LmState* st) {
+// One block of 1024 threads: L y = rhs, then L^T x = y, tile by tile, with the
+// inverses Dinv_k of the diagonal tiles (from k_potrf): y_k = Dinv_k (r_k -
+// sum_{j<k} L_kj y_j), x_k = Dinv_k^T (y_k - sum_{j>k} (L^T)_kj x_j).  Warp w
+// handles row w of the tile; rows of L (lower part) and of L^T (upper part)
+// are read with coalesced loads and reduced with warp shuffles.  x overwrites rhs.
+template <typename F>
+__global__ void __launch_bounds__(1024) k_trsv(const F* __restrict__ A, const F* __restrict__ Dinv, int n_pad,
+                                               F* __restrict__ x, const LmState* st) {
     if (st->chol_fail) return;
+    __shared__ F t[kTile];
+    __shared__ F D[kTile][kTile + 1];
     const int nt = n_pad / kTile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // forward
     for (int k = 0; k < nt; ++k) {
-        if (warp == 0) {
-            double r = x[k * kTile + lane];
-            const double dinv = 1.0 / A[(long long)(k * kTile + lane) * n_pad + k * kTile + lane];
-            for (int m = 0; m < kTile; ++m) {
-                const double ym = __shfl_sync(0xffffffffu, r, m) * __shfl_sync(0xffffffffu, dinv, m);
-                if (lane == m) r = ym;
-                if (lane > m) r -= A[(long long)(k * kTile + lane) * n_pad + k * kTile + m] * ym;
-            }
-            x[k * kTile + lane] = r;
-        }
+        const int row = k * kTile + w;
+        const F* Lr = A + (long long)row * n_pad;
+        F s = F(0);
+        for (int c = lane; c < k * kTile; c += 32) s += Lr[c] * x[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        D[w][lane] = Dinv[(long long)k * kTile * kTile + w * kTile + lane];
+        if (lane == 0) t[w] = x[row] - s;
         __syncthreads();
-        for (int row = (k + 1) * kTile + threadIdx.x; row < n_pad; row += blockDim.x) {
-            double s = 0.0;
-            for (int m = 0; m < kTile; ++m) s += A[(long long)row * n_pad + k * kTile + m] * x[k * kTile + m];
-            x[row] -= s;
-        }
+        F y = D[w][lane] * t[lane];
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        __syncthreads();
+        if (lane == 0) x[row] = y;
         __syncthreads();
     }
-    // backward: L^T x = y
+    // backward
     for (int k = nt - 1; k >= 0; --k) {
-        if (warp == 0) {
-            double r = x[k * kTile + lane];
-            const double dinv = 1.0 / A[(long long)(k * kTile + lane) * n_pad + k * kTile + lane];
-            for (int m = kTile - 1; m >= 0; --m) {
-                const double xm = __shfl_sync(0xffffffffu, r, m) * __shfl_sync(0xffffffffu, dinv, m);
-                if (lane == m) r = xm;
-                if (lane < m) r -= A[(long long)(k * kTile + m) * n_pad + k * kTile + lane] * xm;
-            }
-            x[k * kTile + lane] = r;
-        }
+        const int row = k * kTile + w;
+        const F* Ur = A + (long long)row * n_pad;  // row of L^T (upper part)
+        F s = F(0);
+        for (int c = (k + 1) * kTile + lane; c < n_pad; c += 32) s += Ur[c] * x[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        D[w][lane] = Dinv[(long long)k * kTile * kTile + w * kTile + lane];
+        if (lane == 0) t[w] = x[row] - s;
         __syncthreads();
-        for (int row = threadIdx.x; row < k * kTile; row += blockDim.x) {
-            double s = 0.0;
-            for (int m = 0; m < kTile; ++m) s += A[(long long)(k * kTile + m) * n_pad + row] * x[k * kTile + m];
-            x[row] -= s;
-        }
+        F xv = D[lane][w] * t[lane];  // (Dinv^T)[w][lane]
+        for (int o = 16; o > 0; o >>= 1) xv += __shfl_xor_sync(0xffffffffu, xv, o);
+        __syncthreads();
+        if (lane == 0) x[row] = xv;
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------------ mixed-precision solve
+// GB300 runs FP32 at ~64x its FP64 rate, so the damped system is factorised in
+// FP32 after Jacobi scaling and the solution is refined in FP64 (iterative
+// refinement, as in LAPACK's dsposv):
+//   D = diag(H_ff + lambda I)^-1/2,  A' = D (H_ff + lambda I) D (unit diagonal),
+//   b' = -D b_f;  L L^T = fl32(A');  x = 0, r = b';
+//   repeat: z = (L L^T)^-1 r (FP32), x += z (FP64), r = b' - A' x (FP64);
+//   dx_f = D x.
+// The step is declared failed (chol_fail, then rejected with lambda x 10) when
+// the final FP64 residual exceeds kRefineTol |b'|.
+
+constexpr double kRefineTol = 1e-10;
+
+// A32 = fl32(D (H_ff + lambda I) D) padded with identity; bs = -D b_f (FP64); x = 0; dscale = D.
+__global__ void k_damp_mixed(const double* __restrict__ H, const double* __restrict__ b, int n_frames, int n_pad,
+                             const LmState* __restrict__ st, float* __restrict__ A32, double* __restrict__ bs,
+                             double* __restrict__ x, double* __restrict__ dscale) {
+    const int n6 = 6 * n_frames, n = n6 - 6;
+    const long long total = (long long)n_pad * n_pad;
+    const double lam = st->lambda_used;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n_pad), j = (int)(idx % n_pad);
+        float v;
+        if (i < n && j < n) {
+            const double hii = H[(long long)(i + 6) * n6 + (i + 6)] + lam;
+            const double hjj = H[(long long)(j + 6) * n6 + (j + 6)] + lam;
+            const double hij = H[(long long)(i + 6) * n6 + (j + 6)] + (i == j ? lam : 0.0);
+            v = (float)(hij / sqrt(hii * hjj));
+        } else {
+            v = (i == j) ? 1.f : 0.f;
+        }
+        A32[idx] = v;
+        if (j == 0) {
+            double d = 1.0;
+            if (i < n) {
+                const double hii = H[(long long)(i + 6) * n6 + (i + 6)] + lam;
+                d = hii > 0.0 ? 1.0 / sqrt(hii) : 0.0;
+            }
+            dscale[i] = d;
+            bs[i] = i < n ? -b[i + 6] * d : 0.0;
+            x[i] = 0.0;
+        }
+    }
+}
+
+// r = b' - A' x in FP64 (one warp per row, A' = D (H_ff + lambda I) D evaluated
+// from H), r32 = fl32(r); the last call also records |r|^2 and |b'|^2.
+__global__ void k_refine_residual(const double* __restrict__ H, int n_frames, int n_pad, const LmState* st,
+                                  const double* __restrict__ dscale, const double* __restrict__ bs,
+                                  const double* __restrict__ x, float* __restrict__ r32, double* __restrict__ norms,
+                                  int first) {
+    if (st->chol_fail) return;
+    const int n6 = 6 * n_frames, n = n6 - 6;
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n_pad) return;
+    double r;
+    if (first) {
+        r = bs[row];
+    } else {
+        double s = 0.0;
+        if (row < n) {
+            const double lam = st->lambda_used;
+            const double* Hr = H + (long long)(row + 6) * n6 + 6;
+            for (int j = lane; j < n; j += 32) s += (Hr[j] + (j == row ? lam : 0.0)) * dscale[j] * x[j];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s *= dscale[row];
+        } else {
+            s = x[row];  // identity padding
+        }
+        r = bs[row] - s;
+    }
+    if (lane == 0) {
+        r32[row] = (float)r;
+        if (norms) {
+            atomicAdd(norms, r * r);
+            atomicAdd(norms + 1, bs[row] * bs[row]);
+        }
+    }
+}
+
+// x += z (FP64)
+__global__ void k_refine_update(const LmState* st, const float* __restrict__ z, double* __restrict__ x, int n_pad) {
+    if (st->chol_fail) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pad) x[i] += (double)z[i];
+}
+
+// dx_f = D x; mark the step failed when the refinement did not converge.
+__global__ void k_refine_finish(LmState* st, const double* __restrict__ dscale, const double* __restrict__ x,
+                                double* __restrict__ dx, const double* __restrict__ norms, int n_pad) {
+    if (st->chol_fail) return;
+    const bool ok = norms[0] <= kRefineTol * kRefineTol * norms[1] || norms[1] == 0.0;
+    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) dx[i] = dscale[i] * x[i];
+    __syncthreads();
+    if (threadIdx.x == 0 && !ok) st->chol_fail = 1;
 }
 
 // ------------------------------------------------------------------ update
@@ -336,17 +480,18 @@ cudaError_t launch_damp(const double* H, const double* b, int n_frames, int n_pa
     return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky(double* A, int n_pad, LmState* st, cudaStream_t s, int* n_launches) {
+cudaError_t launch_cholesky(double* A, double* Dinv, int n_pad, LmState* st, cudaStream_t s, int* n_launches) {
     const int nt = n_pad / kTile;
     const dim3 blk(kTile, kTile);
+    const dim3 blk8(kTile, 8);
     int nl = 0;
     for (int k = 0; k < nt; ++k) {
-        k_potrf<<<1, blk, 0, s>>>(A, n_pad, k, st);
+        k_potrf<double><<<1, blk8, 0, s>>>(A, n_pad, k, st, Dinv);
         ++nl;
         const int rest = nt - k - 1;
         if (rest > 0) {
-            k_trsm<<<rest, blk, 0, s>>>(A, n_pad, k, st);
-            k_syrk<<<rest * (rest + 1) / 2, blk, 0, s>>>(A, n_pad, k, nt, st);
+            k_trsm<double><<<rest, blk8, 0, s>>>(A, n_pad, k, st);
+            k_syrk<double><<<rest * (rest + 1) / 2, blk, 0, s>>>(A, n_pad, k, nt, st);
             nl += 2;
         }
     }
@@ -354,8 +499,45 @@ cudaError_t launch_cholesky(double* A, int n_pad, LmState* st, cudaStream_t s, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_trsv(const double* A, int n_pad, double* rhs, const LmState* st, cudaStream_t s) {
-    k_trsv<<<1, 1024, 0, s>>>(A, n_pad, rhs, st);
+cudaError_t launch_trsv(const double* A, const double* Dinv, int n_pad, double* rhs, const LmState* st,
+                        cudaStream_t s) {
+    k_trsv<double><<<1, 1024, 0, s>>>(A, Dinv, n_pad, rhs, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, int n_pad, LmState* st,
+                               MixedWork& w, int refinements, double* dx, cudaStream_t s, int* n_launches) {
+    const long long total = (long long)n_pad * n_pad;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    int nl = 0;
+    k_damp_mixed<<<grid, 256, 0, s>>>(H, b, n_frames, n_pad, st, w.A32, w.bs, w.x, w.dscale);
+    ++nl;
+    const int nt = n_pad / kTile;
+    const dim3 blk(kTile, kTile), blk8(kTile, 8);
+    for (int k = 0; k < nt; ++k) {
+        k_potrf<float><<<1, blk8, 0, s>>>(w.A32, n_pad, k, st, w.D32);
+        ++nl;
+        const int rest = nt - k - 1;
+        if (rest > 0) {
+            k_trsm<float><<<rest, blk8, 0, s>>>(w.A32, n_pad, k, st);
+            k_syrk<float><<<rest * (rest + 1) / 2, blk, 0, s>>>(w.A32, n_pad, k, nt, st);
+            nl += 2;
+        }
+    }
+    cudaMemsetAsync(w.norms, 0, 2 * sizeof(double), s);
+    const int rgrid = (n_pad + 7) / 8;  // 8 warps per block, one row per warp
+    for (int it = 0; it < refinements; ++it) {
+        k_refine_residual<<<rgrid, 256, 0, s>>>(H, n_frames, n_pad, st, w.dscale, w.bs, w.x, w.r32, nullptr,
+                                                it == 0 ? 1 : 0);
+        k_trsv<float><<<1, 1024, 0, s>>>(w.A32, w.D32, n_pad, w.r32, st);
+        k_refine_update<<<(n_pad + 255) / 256, 256, 0, s>>>(st, w.r32, w.x, n_pad);
+        nl += 3;
+    }
+    k_refine_residual<<<rgrid, 256, 0, s>>>(H, n_frames, n_pad, st, w.dscale, w.bs, w.x, w.r32, w.norms, 0);
+    k_refine_finish<<<1, 256, 0, s>>>(st, w.dscale, w.x, dx, w.norms, n_pad);
+    nl += 2;
+    if (n_launches) *n_launches = nl;
     return cudaGetLastError();
 }
 

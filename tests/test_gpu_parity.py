@@ -30,10 +30,10 @@ def gpu():
     return torch
 
 
-def make(w, path, texel, params=None, poses=None):
+def make(w, path, texel, params=None, poses=None, solver=0):
     import paper_2303_16878_gb300 as pba
     gpu()
-    return pba.problem_from_workload(w, path=path, texel=texel, params=params, poses=poses)
+    return pba.problem_from_workload(w, path=path, texel=texel, params=params, poses=poses, solver=solver)
 
 
 CASES = [
@@ -120,9 +120,11 @@ def test_full_size_lidar_street_sampled_pairs(oracle_lib):
     p.close()
 
 
-def test_damped_step_matches_oracle(oracle_lib, room8):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_damped_step_matches_oracle(oracle_lib, room8, solver):
     """A strongly damped step is well conditioned, so its dx is fixed to the
-    accuracy of H and b; compare the updated poses."""
+    accuracy of H and b; compare the updated poses (FP64 Cholesky and the
+    FP32-factorisation + FP64-refinement solver)."""
     import paper_2303_16878_gb300 as pba
     w = room8
     ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
@@ -131,7 +133,7 @@ def test_damped_step_matches_oracle(oracle_lib, room8):
     cand = oracle_lib.apply_update(w.poses_init, dx)
     new = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False)
     assert ok and new["cost"] < ref["cost"]
-    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16, solver=solver)
     p.linearize()
     st = p.solve_step(lam)
     assert st["accepted"] and st["status"] == 0
@@ -142,7 +144,8 @@ def test_damped_step_matches_oracle(oracle_lib, room8):
     p.close()
 
 
-def test_lm_converges_to_oracle_poses(oracle_lib):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_lm_converges_to_oracle_poses(oracle_lib, solver):
     """Ten LM iterations from the same start: GPU (device-side lambda schedule,
     captured graph) and oracle reach the same poses within 1e-4 m / 1e-5 rad."""
     import paper_2303_16878_gb300 as pba
@@ -151,7 +154,7 @@ def test_lm_converges_to_oracle_poses(oracle_lib):
     for _ in range(10):
         o = oracle_lib.lm_iteration(w, poses, lam)
         poses, lam = o["poses"], o["lam"]
-    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32, solver=solver)
     for _ in range(10):
         p.iterate()
     got = p.get_poses()
@@ -174,6 +177,43 @@ def test_graph_iteration_equals_explicit_calls(room8):
     sb = b.solve_step(sa["lambda_used"])
     assert sa["cost"] == cost and sa["new_cost"] == sb["new_cost"] and sa["accepted"] == sb["accepted"]
     np.testing.assert_array_equal(a.get_poses(), b.get_poses())
+    a.close()
+    b.close()
+
+
+def test_autotuned_variants_agree(oracle_lib, street3):
+    """Whatever occupancy variant the autotuner keeps, the system is the same
+    (within float32 reordering) and matches the oracle."""
+    import paper_2303_16878_gb300 as pba
+    w = street3
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    p.linearize()
+    H0, b0 = p.get_system()
+    vf, vc = p.autotune(1)
+    assert vf in (0, 1) and vc in (0, 1)
+    cost, _ = p.linearize()
+    H1, b1 = p.get_system()
+    assert rel(H1, H0) <= 1e-6 and rel(b1, b0) <= 1e-6
+    assert rel(H1, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+    p.close()
+
+
+def test_mixed_and_f64_solvers_agree_on_the_lidar_street():
+    """One LM iteration on the full 50-frame street: the mixed solver's step
+    equals the FP64 Cholesky step to the refinement tolerance."""
+    import paper_2303_16878_gb300 as pba
+    w = workload("street")
+    a = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16, solver=pba.PBA_SOLVE_CHOLESKY_F64)
+    b = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16, solver=pba.PBA_SOLVE_MIXED)
+    for lam in (None, 1e-3):
+        for p in (a, b):
+            p.set_poses(w.poses_init)
+            p.set_lambda(lam)
+        sa, sb = a.iterate(), b.iterate()
+        assert sa["status"] == 0 and sb["status"] == 0 and sa["accepted"] == sb["accepted"]
+        step = np.abs(a.get_poses() - w.poses_init).max()
+        assert np.abs(a.get_poses() - b.get_poses()).max() <= 1e-8 * max(step, 1e-3)
     a.close()
     b.close()
 
