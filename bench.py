@@ -156,9 +156,14 @@ def run_ours(args, rank, world, device):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     n_points_total = sum(prob.frame_points(int(i)) for i, _ in w.pairs)
 
-    def one_step(p):
+    def start(p):
+        # every run starts from the initial poses with automatic damping; the
+        # first linearisation is not part of any timed iteration
         p.set_poses(init)
         p.set_lambda(None)
+        p.linearize()
+
+    def one_step(p):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -168,6 +173,7 @@ def run_ours(args, rank, world, device):
         return e0.elapsed_time(e1), p.get_stats()
 
     variants = prob.autotune(2)
+    start(prob)
     for _ in range(args.warmup):
         one_step(prob)
     launches = prob.iteration_launches()
@@ -194,9 +200,8 @@ def run_ours(args, rank, world, device):
 
     # per-phase device times (same stream, same flush), for the roofline
     phases = {}
+    start(prob)
     for _ in range(args.steps):
-        prob.set_poses(init)
-        prob.set_lambda(None)
         flush.zero_()
         _, ph = prob.iterate_timed()
         for k, v in ph.items():
@@ -212,18 +217,19 @@ def run_ours(args, rank, world, device):
                                     solver=pba.PBA_SOLVE_CHOLESKY_F64)
     f64.autotune(1)
     f64_solve = []
+    start(f64)
     for _ in range(max(3, args.steps // 2)):
-        f64.set_poses(init)
-        f64.set_lambda(None)
         flush.zero_()
         _, ph = f64.iterate_timed()
-        f64_solve.append(ph["solve_update"])
+        f64_solve.append(ph["solve"])
     f64.close()
     out["solve_update_f64_ms"] = float(np.mean(f64_solve))
 
     # plain per-pair path on the same workload
     if not args.no_plain:
-        plain = pba.problem_from_workload(w, path=pba.PBA_PATH_PLAIN, texel=pba.PBA_TEXEL_F32, stream=stream)
+        plain = pba.problem_from_workload(w, path=pba.PBA_PATH_PLAIN, texel=pba.PBA_TEXEL_F32, stream=stream,
+                                          solver=pba.PBA_SOLVE_MIXED)
+        start(plain)
         for _ in range(max(1, args.warmup)):
             one_step(plain)
         pms = []
@@ -346,14 +352,16 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames": w.n_frames, "pairs": out["n_pairs"],
                        "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
-                       "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)", "parallelism": f"replicas x{world}",
                        "autotuned_variants": list(out["variants"])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_linearize<f16, full>",
                          "kernel_ms": lin_ms},
             "phase_ms": ph,
             "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|)",
-            "solve_update_f64_cholesky_ms": out["solve_update_f64_ms"],
+            "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
+            "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
             "gpu_launches": out["launches"] * args.steps,
             "clocks": out["clocks"],
         }

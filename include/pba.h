@@ -192,9 +192,14 @@ int pba_solve_step(pba_problem* p, double lambda, pba_iter_stats* stats);
  * by 10 on rejection, on the device. */
 int pba_set_lambda(pba_problem* p, double lambda);
 
-/* One full Levenberg-Marquardt iteration (linearise, damp, solve, update,
- * re-evaluate, accept or reject) with the device-side lambda schedule;
- * fills stats (may be NULL) and synchronises. */
+/* One full Levenberg-Marquardt iteration with the device-side lambda
+ * schedule: damp and solve the current system, form the candidate poses,
+ * linearise fully at the candidate, and accept (the candidate's poses and
+ * system become current) or reject (nothing changes).  The first iteration
+ * after new poses, frames or pairs first linearises at the current poses.
+ * stats->cost is F at the start, stats->new_cost F at the candidate,
+ * stats->n_valid the residuals of the candidate's linearisation.  Fills stats
+ * (may be NULL) and synchronises. */
 int pba_iterate(pba_problem* p, pba_iter_stats* stats);
 
 /* Enqueue n iterations as replays of one captured CUDA graph without
@@ -217,12 +222,11 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
 /* Instrumentation: one iteration like pba_iterate, enqueued launch by launch
  * (not as a graph) with CUDA events recorded on the problem's stream between
  * its phases; writes min(n_phases, PBA_N_PHASES) device times in
- * milliseconds: [0] pair transforms, [1] the linearisation kernel,
- * [2] per-pair reduction + assembly + total cost, [3] damping + Cholesky +
- * triangular solves + box-plus + candidate transforms, [4] the cost-only
- * linearisation kernel at the candidate, [5] its reduction + accept.
- * Fills stats (may be NULL); synchronises. */
-#define PBA_N_PHASES 6
+ * milliseconds: [0] damping + solve, [1] box-plus + candidate transforms,
+ * [2] the linearisation kernel at the candidate, [3] per-pair reduction +
+ * assembly + cost, [4] accept / reject (and the swap of the system).  Fills
+ * stats (may be NULL); synchronises. */
+#define PBA_N_PHASES 5
 int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_stats* stats);
 
 /* ------------------------------------------------------------------------

@@ -42,8 +42,8 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune"]
-PBA_N_PHASES = 6
-PHASE_NAMES = ["pair_pose", "linearize", "reduce_assemble", "solve_update", "cost_linearize", "cost_accept"]
+PBA_N_PHASES = 5
+PHASE_NAMES = ["solve", "update", "linearize", "reduce_assemble", "accept"]
 
 
 class PbaSensor(ctypes.Structure):

@@ -53,6 +53,8 @@ struct pba_problem {
     LmState* d_state = nullptr;
     double* d_H = nullptr;
     double* d_b = nullptr;
+    double* d_H_cand = nullptr;  // system linearised at the candidate (speculative LM step)
+    double* d_b_cand = nullptr;
     double* d_A = nullptr;
     double* d_rhs = nullptr;
     double* d_Dinv = nullptr;  // inverses of the Cholesky diagonal tiles
@@ -147,14 +149,20 @@ int ensure_points(pba_problem* p) {
     return PBA_OK;
 }
 
-// Full linearisation at the current poses: pair pose table, persistent
-// linearise, per-pair FP64 reduction, assembly of H and b, total cost.
-int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr) {
-    CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
+// Full linearisation at the current poses (or, at_cand, at the candidate
+// poses into the candidate buffers): pair pose table, persistent linearise,
+// per-pair FP64 reduction, assembly of H and b, total cost.
+int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr, bool at_cand = false) {
+    const double* poses = at_cand ? p->d_cand : p->d_poses;
+    double* blocks = at_cand ? p->d_blocks_cand : p->d_blocks;
+    double* H = at_cand ? p->d_H_cand : p->d_H;
+    double* b = at_cand ? p->d_b_cand : p->d_b;
+    // timing events (speculative timed iteration): [2] before the kernel, [3] after it, [4] after the cost
+    CUDA_TRY(p, launch_pair_pose(poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
     ++*nl;
-    if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
     if (p->cfg.path == PBA_PATH_PLAIN) {
         CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
         for (int q = 0; q < p->M; ++q) {
             const int src = p->pairs[2 * q];
             const pba_sensor& S = p->sensors[p->frame_sensor[src]];
@@ -162,30 +170,34 @@ int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev =
                                      p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width, S.height, s));
             ++*nl;
         }
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
-        CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, true, p->d_blocks, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[3], s));
+        CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, true, blocks, s));
         ++*nl;
     } else {
         CUDA_TRY(p, cudaMemsetAsync(p->d_queue, 0, sizeof(int), s));
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
-        const bool mask = p->mask_export;
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
+        const bool mask = p->mask_export && !at_cand;
         CUDA_TRY(p, launch_linearize(true, mask, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue,
                                      p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials,
                                      p->d_mask, p->grid_full, p->variant_full, s));
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[2], s));
-        CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M, true,
-                                       p->d_blocks, s));
+        if (ev) CUDA_TRY(p, cudaEventRecord(ev[3], s));
+        CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, poses, p->d_pair_Xo, p->M, true, blocks, s));
         *nl += 2;
     }
-    CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, p->d_blocks, p->N, p->d_H, p->d_b, s));
-    CUDA_TRY(p, launch_total_cost(p->d_blocks, p->M, p->d_state, false, s));
+    CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, blocks, p->N, H, b, s));
+    CUDA_TRY(p, launch_total_cost(blocks, p->M, p->d_state, at_cand, s));
     *nl += 2;
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
     return PBA_OK;
 }
 
-// Damped solve, candidate poses, cost at the candidate, accept / reject.
-int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr) {
-    if (ev) CUDA_TRY(p, cudaEventRecord(ev[3], s));
+// Damped solve, candidate poses, then either (speculative) a full
+// linearisation at the candidate, whose system becomes current on
+// acceptance, or only the cost at the candidate; accept / reject.
+int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEvent_t* ev = nullptr,
+                 bool speculative = false) {
+    // timing events (speculative timed iteration only): [1] after the solve, [5] after the accept
+    if (!speculative) ev = nullptr;
     CUDA_TRY(p, launch_lm_prepare(p->d_H, p->N, p->d_state, lambda, s));
     int nc = 0;
     if (p->cfg.solver == PBA_SOLVE_MIXED) {
@@ -197,37 +209,43 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
         CUDA_TRY(p, launch_trsv(p->d_A, p->d_Dinv, p->n_pad, p->d_rhs, p->d_state, s));
         *nl += 3 + nc;
     }
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
     CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->d_state, p->d_cand, s));
-    CUDA_TRY(p, launch_pair_pose(p->d_cand, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
-    *nl += 2;
-    if (p->cfg.path == PBA_PATH_PLAIN) {
-        CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
-        for (int q = 0; q < p->M; ++q) {
-            const int src = p->pairs[2 * q];
-            const pba_sensor& S = p->sensors[p->frame_sensor[src]];
-            CUDA_TRY(p, launch_plain(false, q, p->d_ps, p->d_pp, p->raw, p->d_sensors, p->frame_sensor[src], p->prm,
-                                     p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width, S.height, s));
-            ++*nl;
-        }
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
-        CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, false, p->d_blocks_cand, s));
-        ++*nl;
+    ++*nl;
+    if (speculative) {
+        int st = enqueue_linearize(p, s, nl, ev, true);
+        if (st) return st;
     } else {
-        CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s));
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
-        CUDA_TRY(p, launch_linearize(false, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue + 1,
-                                     p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials, nullptr,
-                                     p->grid_cost, p->variant_cost, s));
-        if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
-        CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_cand, p->d_pair_Xo, p->M, false,
-                                       p->d_blocks_cand, s));
-        *nl += 2;
+        CUDA_TRY(p, launch_pair_pose(p->d_cand, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
+        ++*nl;
+        if (p->cfg.path == PBA_PATH_PLAIN) {
+            CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, s));
+            for (int q = 0; q < p->M; ++q) {
+                const int src = p->pairs[2 * q];
+                const pba_sensor& S = p->sensors[p->frame_sensor[src]];
+                CUDA_TRY(p, launch_plain(false, q, p->d_ps, p->d_pp, p->raw, p->d_sensors, p->frame_sensor[src],
+                                         p->prm, p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width,
+                                         S.height, s));
+                ++*nl;
+            }
+            CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, false, p->d_blocks_cand, s));
+            ++*nl;
+        } else {
+            CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s));
+            CUDA_TRY(p, launch_linearize(false, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks,
+                                         p->d_queue + 1, p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm,
+                                         p->d_partials, nullptr, p->grid_cost, p->variant_cost, s));
+            CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_cand, p->d_pair_Xo, p->M, false,
+                                           p->d_blocks_cand, s));
+            *nl += 2;
+        }
+        CUDA_TRY(p, launch_total_cost(p->d_blocks_cand, p->M, p->d_state, true, s));
+        ++*nl;
     }
-    CUDA_TRY(p, launch_total_cost(p->d_blocks_cand, p->M, p->d_state, true, s));
-    CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, s));
-    *nl += 2;
-    if (ev) CUDA_TRY(p, cudaEventRecord(ev[6], s));
+    CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, speculative, p->d_H, p->d_H_cand, p->d_b,
+                              p->d_b_cand, p->d_blocks, p->d_blocks_cand, p->M, s));
+    *nl += speculative ? 2 : 1;
+    if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
     return PBA_OK;
 }
 
@@ -236,11 +254,11 @@ int read_stats(pba_problem* p, pba_iter_stats* stats) {
     CUDA_TRY(p, cudaMemcpyAsync(&st, p->d_state, sizeof st, cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     if (stats) {
-        stats->cost = st.cost;
+        stats->cost = st.iter_cost;
         stats->new_cost = st.new_cost;
         stats->lambda_used = st.lambda_used;
         stats->lambda_next = st.lambda;
-        stats->n_valid = st.n_valid;
+        stats->n_valid = st.iter_n_valid;
         stats->accepted = st.accepted;
         stats->status = st.status;
     }
@@ -338,6 +356,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
               alloc((void**)&p->d_state, sizeof(LmState)) &&
               alloc((void**)&p->d_H, sizeof(double) * (size_t)n6 * n6) &&
               alloc((void**)&p->d_b, sizeof(double) * n6) &&
+              alloc((void**)&p->d_H_cand, sizeof(double) * (size_t)n6 * n6) &&
+              alloc((void**)&p->d_b_cand, sizeof(double) * n6) &&
               alloc((void**)&p->d_A, sizeof(double) * (size_t)p->n_pad * p->n_pad) &&
               alloc((void**)&p->d_rhs, sizeof(double) * p->n_pad) &&
               alloc((void**)&p->d_Dinv, sizeof(double) * (size_t)p->n_pad * kTile) &&
@@ -425,6 +445,8 @@ void pba_destroy(pba_problem* p) {
     dfree(p->d_state);
     dfree(p->d_H);
     dfree(p->d_b);
+    dfree(p->d_H_cand);
+    dfree(p->d_b_cand);
     dfree(p->d_A);
     dfree(p->d_rhs);
     dfree(p->d_Dinv);
@@ -638,6 +660,8 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     const int n6 = 6 * p->N;
     CUDA_TRY(p, cudaMemset(p->d_H, 0, sizeof(double) * (size_t)n6 * n6));
     CUDA_TRY(p, cudaMemset(p->d_b, 0, sizeof(double) * n6));
+    CUDA_TRY(p, cudaMemset(p->d_H_cand, 0, sizeof(double) * (size_t)n6 * n6));
+    CUDA_TRY(p, cudaMemset(p->d_b_cand, 0, sizeof(double) * n6));
     return PBA_OK;
 }
 
@@ -647,13 +671,13 @@ int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid) {
     int nl = 0;
     st = enqueue_linearize(p, p->stream, &nl);
     if (st) return st;
-    pba_iter_stats s{};
-    st = read_stats(p, &s);
-    if (st) return st;
+    LmState ls;
+    CUDA_TRY(p, cudaMemcpyAsync(&ls, p->d_state, sizeof ls, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     p->linearized = true;
     p->mask_valid = p->mask_export && p->cfg.path == PBA_PATH_BATCHED;
-    if (cost) *cost = s.cost;
-    if (n_valid) *n_valid = s.n_valid;
+    if (cost) *cost = ls.cost;
+    if (n_valid) *n_valid = ls.n_valid;
     return PBA_OK;
 }
 
@@ -731,7 +755,6 @@ int pba_set_lambda(pba_problem* p, double lambda) {
 int pba_iterate(pba_problem* p, pba_iter_stats* stats) {
     int st = pba_iterate_async(p, 1);
     if (st) return st;
-    p->linearized = false;
     return read_stats(p, stats);
 }
 
@@ -742,8 +765,7 @@ int pba_iterate_async(pba_problem* p, int n) {
     if (!p->graph_exec) {
         int nl = 0;
         CUDA_TRY(p, cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal));
-        st = enqueue_linearize(p, p->capture_stream, &nl);
-        if (!st) st = enqueue_step(p, -1.0, p->capture_stream, &nl);
+        st = enqueue_step(p, -1.0, p->capture_stream, &nl, nullptr, true);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(p->capture_stream, &g);
         if (st) {
@@ -755,8 +777,14 @@ int pba_iterate_async(pba_problem* p, int n) {
         CUDA_TRY(p, cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
         p->launches_last = nl;
     }
+    if (n > 0 && !p->linearized) {
+        // the step needs the system at the current poses; every iteration then keeps it current
+        int nl = 0;
+        st = enqueue_linearize(p, p->stream, &nl);
+        if (st) return st;
+    }
     for (int k = 0; k < n; ++k) CUDA_TRY(p, cudaGraphLaunch(p->graph_exec, p->stream));
-    p->linearized = false;
+    if (n > 0) p->linearized = true;
     p->mask_valid = false;
     return PBA_OK;
 }
@@ -773,9 +801,12 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
     cudaEvent_t ev[PBA_N_PHASES + 1] = {};
     for (auto& e : ev) CUDA_TRY(p, cudaEventCreate(&e));
     int nl = 0;
+    if (!p->linearized) {
+        st = enqueue_linearize(p, p->stream, &nl);
+        if (st) return st;
+    }
     CUDA_TRY(p, cudaEventRecord(ev[0], p->stream));
-    st = enqueue_linearize(p, p->stream, &nl, ev);
-    if (!st) st = enqueue_step(p, -1.0, p->stream, &nl, ev);
+    st = enqueue_step(p, -1.0, p->stream, &nl, ev, true);
     if (!st) st = read_stats(p, stats);
     if (!st && phase_ms)
         for (int k = 0; k < n_phases && k < PBA_N_PHASES; ++k) {
@@ -784,7 +815,7 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
             phase_ms[k] = ms;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    p->linearized = false;
+    p->linearized = st == PBA_OK;
     return st;
 }
 

@@ -94,6 +94,8 @@ struct LmState {
     int status;             // 0 or PBA_ENOTPD
     int chol_fail;          // set by the factorisation
     int pad;
+    double iter_cost;       // F at the poses the last iteration started from
+    long long iter_n_valid; // residuals linearised by the last iteration
 };
 
 // Assembly task: one 6x6 block of H (diagonal when a == b).
@@ -180,6 +182,11 @@ cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, i
 cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const LmState* st,
                            double* cand, cudaStream_t s);
 
-cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, cudaStream_t s);
+// Keep the candidate when the cost decreased.  speculative: the candidate was
+// linearised in full, so on acceptance its system (H_cand, b_cand, blocks_cand,
+// cost, count) replaces the current one as well as the poses.
+cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, bool speculative,
+                          double* H, const double* H_cand, double* b, const double* b_cand, double* blocks,
+                          const double* blocks_cand, int m, cudaStream_t s);
 
 }  // namespace pba

@@ -438,7 +438,8 @@ __global__ void k_boxplus(const double* __restrict__ poses, const double* __rest
 }
 
 // Keep the candidate when the cost decreased (and the factorisation succeeded).
-__global__ void k_accept(LmState* st, double* __restrict__ poses, const double* __restrict__ cand, int n_frames) {
+__global__ void k_accept(LmState* st, double* __restrict__ poses, const double* __restrict__ cand, int n_frames,
+                         bool speculative) {
     __shared__ int acc;
     if (threadIdx.x == 0) {
         const bool ok = !st->chol_fail && st->new_cost < st->cost;
@@ -446,10 +447,28 @@ __global__ void k_accept(LmState* st, double* __restrict__ poses, const double* 
         st->accepted = acc;
         st->status = st->chol_fail ? PBA_ENOTPD : PBA_OK;
         st->lambda = ok ? st->lambda_used * 0.1 : st->lambda_used * 10.0;
+        st->iter_cost = st->cost;
+        st->iter_n_valid = speculative ? st->n_valid_new : st->n_valid;
+        if (ok && speculative) {
+            st->cost = st->new_cost;
+            st->n_valid = st->n_valid_new;
+        }
     }
     __syncthreads();
     if (acc)
         for (int e = threadIdx.x; e < 12 * n_frames; e += blockDim.x) poses[e] = cand[e];
+}
+
+// After an accepted speculative step: the candidate's linearisation becomes current.
+__global__ void k_accept_copy(const LmState* st, double* __restrict__ H, const double* __restrict__ H_cand,
+                              long long nH, double* __restrict__ b, const double* __restrict__ b_cand, int nb,
+                              double* __restrict__ blocks, const double* __restrict__ blocks_cand, long long nblk) {
+    if (!st->accepted) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long i = i0; i < nH; i += stride) H[i] = H_cand[i];
+    for (long long i = i0; i < nb; i += stride) b[i] = b_cand[i];
+    for (long long i = i0; i < nblk; i += stride) blocks[i] = blocks_cand[i];
 }
 
 }  // namespace
@@ -547,8 +566,18 @@ cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frame
     return cudaGetLastError();
 }
 
-cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, cudaStream_t s) {
-    k_accept<<<1, 256, 0, s>>>(st, poses, cand, n_frames);
+cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, bool speculative,
+                          double* H, const double* H_cand, double* b, const double* b_cand, double* blocks,
+                          const double* blocks_cand, int m, cudaStream_t s) {
+    k_accept<<<1, 256, 0, s>>>(st, poses, cand, n_frames, speculative);
+    if (speculative) {
+        const long long n6 = 6LL * n_frames;
+        const long long nblk = (long long)kBlockStride * m;
+        long long most = n6 * n6 > nblk ? n6 * n6 : nblk;
+        int grid = (int)((most + 255) / 256);
+        if (grid > 1024) grid = 1024;
+        k_accept_copy<<<grid, 256, 0, s>>>(st, H, H_cand, n6 * n6, b, b_cand, (int)n6, blocks, blocks_cand, nblk);
+    }
     return cudaGetLastError();
 }
 

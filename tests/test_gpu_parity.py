@@ -167,16 +167,23 @@ def test_lm_converges_to_oracle_poses(oracle_lib, solver):
 
 
 def test_graph_iteration_equals_explicit_calls(room8):
-    """pba_iterate (captured graph, device lambda) and pba_linearize +
-    pba_solve_step with the same lambda give bitwise identical results."""
+    """pba_iterate (captured graph, device lambda, full linearisation at the
+    candidate) and pba_linearize + pba_solve_step (cost-only pass at the
+    candidate) with the same lambda take the same step; after an accepted
+    iteration the current system equals a fresh linearisation at the new poses."""
     import paper_2303_16878_gb300 as pba
     a = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
     b = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
     sa = a.iterate()
     cost, _ = b.linearize()
     sb = b.solve_step(sa["lambda_used"])
-    assert sa["cost"] == cost and sa["new_cost"] == sb["new_cost"] and sa["accepted"] == sb["accepted"]
+    assert sa["cost"] == cost and sa["accepted"] == sb["accepted"]
+    assert abs(sa["new_cost"] - sb["new_cost"]) <= 1e-12 * sb["new_cost"]
     np.testing.assert_array_equal(a.get_poses(), b.get_poses())
+    Ha, ba = a.get_system()
+    b.linearize()
+    Hb, bb = b.get_system()
+    assert rel(Ha, Hb) <= 1e-12 and rel(ba, bb) <= 1e-12
     a.close()
     b.close()
 
