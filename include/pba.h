@@ -140,6 +140,11 @@ int pba_set_stream(pba_problem* p, void* cuda_stream);
  * use sensors of the same size.  Errors: PBA_EINVAL, PBA_ECUDA. */
 int pba_upload_frames(pba_problem* p, int first, int count, const float* channels, int is_device);
 
+/* Replace the extrinsic offset X_o (row-major 3x4, host memory) of one
+ * sensor (Supp., p_u = R_o pi^-1(u, d) + t_o): the pixel-points of that
+ * sensor's uploaded frames are rebuilt; the next iteration relinearises. */
+int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic);
+
 /* Number of valid pixel-points of a frame (after its upload). */
 int pba_frame_points(pba_problem* p, int frame, int32_t* n_points);
 
@@ -154,10 +159,45 @@ int pba_get_poses(pba_problem* p, double* poses);
  * Requires every frame named to have been uploaded. */
 int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m);
 
+/* Graph construction (Sec. IV-B): directed candidate pairs (i, j), i < j,
+ * frames of the same sensor, whose poses differ by a rotation angle below
+ * max_angle [rad] and a translation below max_dist [m] are tested in one
+ * persistent launch of the cost-only linearisation at the current poses; a
+ * pair is kept when the ratio of frame i's pixel-points that give a valid
+ * residual against frame j (same validity rules as the residuals) exceeds
+ * min_ratio.  With sequential != 0, every (i, i + 1) of the same sensor is
+ * kept as well (odometry-like edges).  Writes up to cap pairs (m x 2 int32,
+ * ascending i then j) to pairs_out and their ratios to ratio_out (either may
+ * be NULL), and the number found to *m_out.  The problem's own pair list is
+ * unchanged; pass the result to pba_set_pairs.  Needs poses and every frame
+ * uploaded; synchronises.  PBA_EINVAL when cap is too small (*m_out then
+ * holds the size needed). */
+int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double min_ratio, int sequential,
+                    int32_t* pairs_out, float* ratio_out, int cap, int32_t* m_out);
+
 /* Linearise all pairs at the current poses: builds H (6N x 6N, gauge not
  * fixed) and b (6N) on the device and returns the total cost F (Eq. total-error-multicue) and
  * the number of valid residuals; synchronises.  Either output may be NULL. */
 int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
+
+/* Adjoint of the total cost F (Eq. total-error-multicue) at the current
+ * poses.  One launch recomputes every residual (no Jacobian is stored) and
+ * accumulates the gradient of F, the validity decisions (bounds, stencil,
+ * occlusion, Huber branch) held fixed:
+ *   d_poses     N x 12 doubles: dF/dX_k, the derivative with respect to the
+ *               entries of each 3x4 pose [R_k | t_k] (F evaluated with the
+ *               paper's formulas for any 3x4 matrices; the se(3) gradient in
+ *               the box-plus chart is [R^T g_t, 2 vex-type pairs of R^T G_R]);
+ *   d_extrinsic S x 12 doubles: dF/dX_o per sensor, likewise;
+ *   d_channels  one float per channel of every uploaded pixel (the layout of
+ *               pba_upload_frames, frames back to back): dF/d(g, d, n) through
+ *               the bilinear samples of the targets and the source pixels.
+ * Image derivatives use the exact derivative of the bilinear interpolant.
+ * All three are caller-allocated device buffers of the current device (any
+ * may be NULL); cost and n_valid (host, may be NULL) receive F and the number
+ * of valid residuals.  Batched path only; synchronises. */
+int pba_cost_gradient(pba_problem* p, double* cost, int64_t* n_valid, double* d_poses, double* d_extrinsic,
+                      float* d_channels);
 
 /* Copy the last linearisation's H (6N x 6N row-major) and b (6N) to host
  * memory; either may be NULL.  Frame k owns rows and columns 6k..6k+5. */

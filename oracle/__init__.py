@@ -295,3 +295,41 @@ def lm_iteration(w, poses, lam: Optional[float], lib=None) -> Dict:
                 lam=lam / 10.0 if accepted else lam * 10.0, lam_used=lam, cost=lin["cost"],
                 new_cost=new["cost"], count=lin["count"], H=lin["H"], b=lin["b"], dx=dx,
                 candidate=cand, solve_ok=ok)
+
+
+def pose_angle(Xi, Xj) -> float:
+    """Rotation angle between two poses: acos((trace(R_i^T R_j) - 1) / 2)."""
+    Ri, Rj = np.asarray(Xi)[:, :3], np.asarray(Xj)[:, :3]
+    return float(np.arccos(np.clip(0.5 * (np.trace(Ri.T @ Rj) - 1.0), -1.0, 1.0)))
+
+
+def build_pairs(sensors, frame_sensor, channels, poses, params: Dict, max_angle: float, max_dist: float,
+                min_ratio: float, sequential: bool = False, lib=None) -> Dict:
+    """Graph construction (Sec. IV-B): directed pairs (i, j), i < j, same
+    sensor, with rotation angle < max_angle and translation < max_dist,
+    kept when (valid residuals of i against j) / (points of i) > min_ratio;
+    with `sequential`, (i, i + 1) is always kept.  Also returns each
+    candidate's ratio and how many of its points lie within the float32
+    decision margin (their validity may differ in a float32 implementation)."""
+    lib = lib or _load()
+    poses = np.asarray(poses, dtype=np.float64).reshape(-1, 3, 4)
+    n = poses.shape[0]
+    out, info = [], {}
+    for i in range(n):
+        for j in range(i + 1, n):
+            if frame_sensor[i] != frame_sensor[j]:
+                continue
+            ang = pose_angle(poses[i], poses[j])
+            dist = float(np.linalg.norm(poses[i][:, 3] - poses[j][:, 3]))
+            is_seq = sequential and j == i + 1
+            if not ((ang < max_angle and dist < max_dist) or is_seq):
+                continue
+            r = linearize_pair(sensors[frame_sensor[i]], params, channels[i], channels[j], poses[i], poses[j],
+                               lib=lib)
+            ratio = r["count"] / r["n_points"] if r["n_points"] else 0.0
+            flagged = int(sum(bin(int(x)).count("1") for x in r["flags"]))
+            info[(i, j)] = dict(ratio=ratio, n_points=r["n_points"], count=r["count"], flagged=flagged,
+                                sequential=is_seq)
+            if ratio > min_ratio or is_seq:
+                out.append((i, j))
+    return dict(pairs=np.array(out, dtype=np.int32).reshape(-1, 2), candidates=info)

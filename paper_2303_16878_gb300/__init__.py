@@ -160,6 +160,18 @@ class Problem:
         self.n_pairs = arr.shape[0]
         self._check(self._lib.pba_set_pairs(self._h, arr.ctypes.data_as(ctypes.c_void_p), arr.shape[0]), "set_pairs")
 
+    def build_pairs(self, max_angle: float, max_dist: float, min_ratio: float, sequential: bool = False):
+        """Graph construction (Sec. IV-B) at the current poses: (pairs (m, 2) int32, ratios (m,))."""
+        n = ctypes.c_int32()
+        cap = self.n_frames * (self.n_frames - 1) // 2 + 1
+        pairs = np.zeros((cap, 2), dtype=np.int32)
+        ratios = np.zeros(cap, dtype=np.float32)
+        self._check(self._lib.pba_build_pairs(self._h, float(max_angle), float(max_dist), float(min_ratio),
+                                              1 if sequential else 0, pairs.ctypes.data_as(ctypes.c_void_p),
+                                              ratios.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)),
+                    "build_pairs")
+        return pairs[: n.value].copy(), ratios[: n.value].copy()
+
     # -------------------------------------------------------------- linearise / solve
     def linearize(self):
         cost, n = ctypes.c_double(), ctypes.c_int64()

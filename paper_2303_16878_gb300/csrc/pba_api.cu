@@ -3,6 +3,7 @@
 // queue, per-pair chunk ranges, assembly tasks) and the enqueueing of the
 // kernels, directly or as a captured CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -44,6 +45,8 @@ struct pba_problem {
     void* tex = nullptr;
     float4* pts_pg = nullptr;
     float4* pts_n = nullptr;
+    int* pts_pix = nullptr;
+    int* d_frame_sensor = nullptr;
     int* d_npoints = nullptr;
     FrameInfo* d_frames = nullptr;
     SensorDev* d_sensors = nullptr;
@@ -81,6 +84,9 @@ struct pba_problem {
     std::vector<long long> mask_off;
     std::vector<int> pair_src_points;
     float* d_plain_acc = nullptr;
+    float* d_adj_partials = nullptr;  // adjoint: per work item
+    double* d_adj_pair = nullptr;     // adjoint: per pair
+    double* d_adj_totals = nullptr;   // adjoint: cost, count
 
     bool poses_set = false;
     bool mask_export = false;
@@ -129,6 +135,9 @@ void free_pair_buffers(pba_problem* p) {
     dfree(p->d_contrib);
     dfree(p->d_mask);
     dfree(p->d_plain_acc);
+    dfree(p->d_adj_partials);
+    dfree(p->d_adj_pair);
+    dfree(p->d_adj_totals);
     p->M = 0;
     p->n_chunks = 0;
     p->n_tasks = 0;
@@ -347,6 +356,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
               alloc(&p->tex, texel_bytes * (size_t)p->total_px) &&
               alloc((void**)&p->pts_pg, sizeof(float4) * (size_t)p->total_px) &&
               alloc((void**)&p->pts_n, sizeof(float4) * (size_t)p->total_px) &&
+              alloc((void**)&p->pts_pix, sizeof(int) * (size_t)p->total_px) &&
+              alloc((void**)&p->d_frame_sensor, sizeof(int) * p->N) &&
               alloc((void**)&p->d_npoints, sizeof(int) * p->N) &&
               alloc((void**)&p->d_frames, sizeof(FrameInfo) * p->N) &&
               alloc((void**)&p->d_sensors, sizeof(SensorDev) * p->sensors.size()) &&
@@ -405,6 +416,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     st.lambda = -1.0;
     if (cudaMemcpy(p->d_frames, fi.data(), sizeof(FrameInfo) * p->N, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_sensors, sd.data(), sizeof(SensorDev) * sd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_frame_sensor, p->frame_sensor.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
         cudaMemcpy(p->d_state, &st, sizeof st, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->d_npoints, 0, sizeof(int) * p->N) != cudaSuccess ||
         cudaMemset(p->d_H, 0, sizeof(double) * (size_t)n6 * n6) != cudaSuccess ||
@@ -436,6 +449,8 @@ void pba_destroy(pba_problem* p) {
     dfree(p->tex);
     dfree(p->pts_pg);
     dfree(p->pts_n);
+    dfree(p->pts_pix);
+    dfree(p->d_frame_sensor);
     dfree(p->d_npoints);
     dfree(p->d_frames);
     dfree(p->d_sensors);
@@ -491,7 +506,8 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
     for (int k = 0; k < count; ++k) ids[k] = first + k;
     CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
-                            p->pts_pg, p->pts_n, p->d_npoints, p->cfg.range_min, p->cfg.range_max, p->stream));
+                            p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
+                            p->stream));
     // the id list is pageable host memory: the synchronisation also makes sure
     // the copy has consumed it
     std::vector<int> before = p->n_points;
@@ -506,6 +522,52 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
         std::vector<int32_t> keep = p->pairs;
         return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
     }
+    return PBA_OK;
+}
+
+int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
+    if (!p || !extrinsic || sensor < 0 || sensor >= (int)p->sensors.size())
+        return fail(p, PBA_EINVAL, "set_extrinsic: bad argument");
+    cudaSetDevice(p->device);
+    pba_sensor& S = p->sensors[sensor];
+    for (int e = 0; e < 12; ++e) S.extrinsic[e] = extrinsic[e];
+    SensorDev sd{};
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) sd.R[3 * r + c] = (float)S.extrinsic[4 * r + c];
+        sd.t[r] = (float)S.extrinsic[4 * r + 3];
+    }
+    sd.model = S.model;
+    sd.width = S.width;
+    sd.height = S.height;
+    sd.fx = (float)S.fx;
+    sd.fy = (float)S.fy;
+    sd.cx = (float)S.cx;
+    sd.cy = (float)S.cy;
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_sensors + sensor, &sd, sizeof sd, cudaMemcpyHostToDevice, p->stream));
+    // the points p_u = R_o pi^-1(u, d) + t_o of this sensor's uploaded frames are rebuilt
+    std::vector<int> ids;
+    for (int k = 0; k < p->N; ++k)
+        if (p->frame_sensor[k] == sensor && p->uploaded[k]) ids.push_back(k);
+    if (!ids.empty()) {
+        CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice,
+                                    p->stream));
+        CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, (int)ids.size(),
+                                p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
+                                p->cfg.range_min, p->cfg.range_max, p->stream));
+    }
+    // per-pair copies of the extrinsic
+    if (p->M > 0) {
+        std::vector<double> pxo(12 * (size_t)p->M);
+        for (int q = 0; q < p->M; ++q) {
+            const pba_sensor& Sq = p->sensors[p->frame_sensor[p->pairs[2 * q]]];
+            for (int e = 0; e < 12; ++e) pxo[12 * q + e] = Sq.extrinsic[e];
+        }
+        CUDA_TRY(p, cudaMemcpyAsync(p->d_pair_Xo, pxo.data(), sizeof(double) * pxo.size(), cudaMemcpyHostToDevice,
+                                    p->stream));
+    }
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // host vectors above are pageable
+    p->linearized = false;
+    p->mask_valid = false;
     return PBA_OK;
 }
 
@@ -643,7 +705,10 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
               alloc((void**)&p->d_tasks, sizeof(AsmTask) * tv.size()) &&
               alloc((void**)&p->d_contrib, sizeof(AsmContrib) * cv.size()) &&
               alloc((void**)&p->d_mask, sizeof(uint32_t) * (size_t)mask_words) &&
-              alloc((void**)&p->d_plain_acc, sizeof(float) * 96 * m);
+              alloc((void**)&p->d_plain_acc, sizeof(float) * 96 * m) &&
+              alloc((void**)&p->d_adj_partials, sizeof(float) * adjoint_partial_stride() * chunks.size()) &&
+              alloc((void**)&p->d_adj_pair, sizeof(double) * adjoint_pair_stride() * m) &&
+              alloc((void**)&p->d_adj_totals, sizeof(double) * 2);
     if (!ok) {
         free_pair_buffers(p);
         return fail(p, PBA_ENOMEM, "set_pairs: device allocation failed");
@@ -662,6 +727,127 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     CUDA_TRY(p, cudaMemset(p->d_b, 0, sizeof(double) * n6));
     CUDA_TRY(p, cudaMemset(p->d_H_cand, 0, sizeof(double) * (size_t)n6 * n6));
     CUDA_TRY(p, cudaMemset(p->d_b_cand, 0, sizeof(double) * n6));
+    return PBA_OK;
+}
+
+int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double min_ratio, int sequential,
+                    int32_t* pairs_out, float* ratio_out, int cap, int32_t* m_out) {
+    if (!p || !m_out || cap < 0) return fail(p, PBA_EINVAL, "build_pairs: bad argument");
+    if (!p->poses_set) return fail(p, PBA_ENOTREADY, "build_pairs: poses not set");
+    for (int k = 0; k < p->N; ++k)
+        if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "build_pairs: frame not uploaded");
+    cudaSetDevice(p->device);
+    std::vector<double> X(12 * (size_t)p->N);
+    CUDA_TRY(p, cudaMemcpyAsync(X.data(), p->d_poses, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    // candidates: rotation angle of R_i^T R_j and |t_i - t_j| (FP64)
+    std::vector<int32_t> cand;
+    std::vector<char> seq;
+    for (int i = 0; i < p->N; ++i)
+        for (int j = i + 1; j < p->N; ++j) {
+            if (p->frame_sensor[i] != p->frame_sensor[j]) continue;
+            const double* A = X.data() + 12 * (size_t)i;
+            const double* B = X.data() + 12 * (size_t)j;
+            double tr = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) tr += A[4 * r + c] * B[4 * r + c];  // trace(R_i^T R_j)
+            const double ca = std::max(-1.0, std::min(1.0, 0.5 * (tr - 1.0)));
+            const double ang = std::acos(ca);
+            const double dx = A[3] - B[3], dy = A[7] - B[7], dz = A[11] - B[11];
+            const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+            const bool is_seq = sequential && j == i + 1;
+            if ((ang < max_angle && dist < max_dist) || is_seq) {
+                cand.push_back(i);
+                cand.push_back(j);
+                seq.push_back(is_seq ? 1 : 0);
+            }
+        }
+    const int mc = (int)(cand.size() / 2);
+    std::vector<double> cost_c(mc), count_c(mc);
+    if (mc > 0) {
+        // count valid residuals of the candidates with the problem's own machinery, then restore its pairs
+        std::vector<int32_t> keep = p->pairs;
+        int st = pba_set_pairs(p, cand.data(), mc);
+        if (st) return st;
+        int nl = 0;
+        CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
+        if (p->cfg.path == PBA_PATH_BATCHED) {
+            CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), p->stream));
+            CUDA_TRY(p, launch_linearize(false, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks,
+                                         p->d_queue + 1, p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm,
+                                         p->d_partials, nullptr, p->grid_cost, p->variant_cost, p->stream));
+            CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M, false,
+                                           p->d_blocks_cand, p->stream));
+        } else {
+            CUDA_TRY(p, cudaMemsetAsync(p->d_plain_acc, 0, sizeof(float) * 96 * (size_t)p->M, p->stream));
+            for (int q = 0; q < p->M; ++q) {
+                const int src = p->pairs[2 * q];
+                const pba_sensor& S = p->sensors[p->frame_sensor[src]];
+                CUDA_TRY(p, launch_plain(false, q, p->d_ps, p->d_pp, p->raw, p->d_sensors, p->frame_sensor[src],
+                                         p->prm, p->cfg.range_min, p->cfg.range_max, p->d_plain_acc, S.width,
+                                         S.height, p->stream));
+            }
+            CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, false, p->d_blocks_cand, p->stream));
+        }
+        (void)nl;
+        std::vector<double> blk((size_t)kBlockStride * mc);
+        CUDA_TRY(p, cudaMemcpyAsync(blk.data(), p->d_blocks_cand, sizeof(double) * blk.size(),
+                                    cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+        for (int q = 0; q < mc; ++q) count_c[q] = blk[(size_t)kBlockStride * q + 157];
+        st = keep.empty() ? PBA_OK : pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
+        if (keep.empty()) {
+            drop_graph(p);
+            free_pair_buffers(p);
+            p->pairs.clear();
+            p->linearized = false;
+        }
+        if (st) return st;
+    }
+    int m = 0;
+    for (int q = 0; q < mc; ++q) {
+        const int i = cand[2 * q];
+        const double np = (double)p->n_points[i];
+        const double ratio = np > 0 ? count_c[q] / np : 0.0;
+        if (ratio > min_ratio || seq[q]) {
+            if (m < cap) {
+                if (pairs_out) {
+                    pairs_out[2 * m] = i;
+                    pairs_out[2 * m + 1] = cand[2 * q + 1];
+                }
+                if (ratio_out) ratio_out[m] = (float)ratio;
+            }
+            ++m;
+        }
+    }
+    *m_out = m;
+    if (m > cap) return fail(p, PBA_EINVAL, "build_pairs: output capacity too small");
+    return PBA_OK;
+}
+
+int pba_cost_gradient(pba_problem* p, double* cost, int64_t* n_valid, double* d_poses, double* d_extrinsic,
+                      float* d_channels) {
+    int st = ready(p);
+    if (st) return st;
+    if (p->cfg.path != PBA_PATH_BATCHED) return fail(p, PBA_EINVAL, "cost_gradient needs the batched path");
+    for (int k = 0; k < p->N; ++k)
+        if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "cost_gradient: frame not uploaded");
+    cudaStream_t s = p->stream;
+    CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, s));
+    if (d_poses) CUDA_TRY(p, cudaMemsetAsync(d_poses, 0, sizeof(double) * 12 * p->N, s));
+    if (d_channels) CUDA_TRY(p, cudaMemsetAsync(d_channels, 0, sizeof(float) * 5 * (size_t)p->total_px, s));
+    CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s));
+    CUDA_TRY(p, launch_adjoint(p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue + 1, p->d_ps, p->d_pp,
+                               p->pts_pg, p->pts_n, p->pts_pix, p->tex, p->d_sensors, p->d_frame_sensor, p->prm,
+                               p->d_adj_partials, d_channels, adjoint_grid(p->cfg.texel_precision), s));
+    CUDA_TRY(p, launch_adjoint_reduce(p->d_adj_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M,
+                                      p->d_adj_pair, p->d_tasks, p->n_tasks, p->d_contrib, p->d_frame_sensor,
+                                      (int)p->sensors.size(), d_poses, d_extrinsic, p->d_adj_totals, s));
+    double tot[2];
+    CUDA_TRY(p, cudaMemcpyAsync(tot, p->d_adj_totals, sizeof tot, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(p, cudaStreamSynchronize(s));
+    if (cost) *cost = tot[0];
+    if (n_valid) *n_valid = (int64_t)tot[1];
     return PBA_OK;
 }
 

@@ -66,6 +66,31 @@ def test_gauge_null_space_with_extrinsic_offset(oracle_lib, room3):
     assert P.pin_gauge(oracle_lib, oracle_lib.load(), wx) < P.PIN_TOL["gauge"]
 
 
+def test_pose_angle_is_the_rotation_magnitude(oracle_lib):
+    """Graph construction's first criterion (Sec. IV-B): the angle between two
+    poses, against scipy's rotation-vector magnitude of R_i^T R_j."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        Xi, Xj = np.zeros((3, 4)), np.zeros((3, 4))
+        Xi[:, :3] = Rotation.from_rotvec(rng.normal(0, 1, 3)).as_matrix()
+        Xj[:, :3] = Rotation.from_rotvec(rng.normal(0, 1, 3)).as_matrix()
+        ref = Rotation.from_matrix(Xi[:, :3].T @ Xj[:, :3]).magnitude()
+        assert abs(oracle_lib.pose_angle(Xi, Xj) - ref) < 1e-7
+
+
+def test_build_pairs_keeps_ratio_above_threshold(oracle_lib, room8):
+    """The pair criterion uses the count of valid residuals (pinned above)
+    over the source's points; sequential edges are kept regardless."""
+    r = oracle_lib.build_pairs(room8.sensors, room8.frame_sensor, room8.channels, room8.poses_init, room8.params,
+                               np.radians(60), 2.0, 0.5, sequential=True)
+    kept = {tuple(p) for p in r["pairs"].tolist()}
+    for (i, j), c in r["candidates"].items():
+        assert ((i, j) in kept) == (c["ratio"] > 0.5 or c["sequential"])
+        assert c["count"] <= c["n_points"]
+    assert all((i, i + 1) in kept for i in range(room8.n_frames - 1))
+
+
 def test_cholesky_matches_numpy_solve(oracle_lib):
     assert P.pin_cholesky(oracle_lib, oracle_lib.load()) < P.PIN_TOL["cholesky"]
 
