@@ -6,7 +6,8 @@
 //             or Tex32 {float d, g, nx, ny, nz, usable, pad x 2}; d = 0 marks an invalid
 //             pixel, usable = pixel and its 4 neighbours valid
 //   points    per frame, compacted valid pixels in raster order:
-//             pg = float4(p_u, g_u), pn = float4(n_u^o, 0)   (Supp., p_u = R_o pi^-1(u, d) + t_o)
+//             pg = float4(p_u, g_u), pn = float4(n_u^o, 0)   (Supp., p_u = R_o pi^-1(u, d) + t_o),
+//             pix = pixel index (row * W + column) of the point
 //   pair pose table (FP32, per iteration): pbar = M p_u + a with M = R_o^T R_j^T R_i,
 //             a = R_o^T (R_j^T (t_i - t_j) - t_o)   (Supp., pbar_u)
 //   chunk list int4 {pair, first point, count, 0}: the persistent launch's work queue
@@ -121,7 +122,7 @@ namespace pba {
 
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors,
                         const int* frame_ids, int n, int texel_precision, void* texels,
-                        float4* pts_pg, float4* pts_n, int* n_points, double range_min,
+                        float4* pts_pg, float4* pts_n, int* pts_pix, int* n_points, double range_min,
                         double range_max, cudaStream_t s);
 
 cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
@@ -188,5 +189,18 @@ cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frame
 cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, bool speculative,
                           double* H, const double* H_cand, double* b, const double* b_cand, double* blocks,
                           const double* blocks_cand, int m, cudaStream_t s);
+
+// Adjoint of the total cost (pba_adjoint.cu).
+int adjoint_partial_stride();  // floats per work-item partial
+int adjoint_pair_stride();     // doubles per pair result
+int adjoint_grid(int texel_precision);
+cudaError_t launch_adjoint(int texel_precision, const int4* chunks, int n_chunks, int* queue, const PairStatic* ps,
+                           const PairPose* pp, const float4* pts_pg, const float4* pts_n, const int* pts_pix,
+                           const void* texels, const SensorDev* sensors, const int* frame_sensor,
+                           const LinParams& prm, float* partials, float* d_img, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_reduce(const float* partials, const PairStatic* ps, const int2* pf, const double* poses,
+                                  const double* pair_Xo, int m, double* pair_out, const AsmTask* tasks, int n_tasks,
+                                  const AsmContrib* contrib, const int* frame_sensor, int n_sensors,
+                                  double* d_poses, double* d_ext, double* totals, cudaStream_t s);
 
 }  // namespace pba

@@ -4,8 +4,8 @@
 //   - a sampling texel: d (FP32, 0 when the pixel is not valid) and g, n in
 //     FP16 or FP32, so one bilinear tap is one 16- or 32-byte load;
 //   - when the pixel is valid, a pixel-point p_u = R_o pi^-1(u, d) + t_o with
-//     its intensity g_u and normal n_u^o = R_o n_u (Supp., p_u), written in
-//     raster order to a compacted array (block-wide ballot scan).
+//     its intensity g_u, normal n_u^o = R_o n_u (Supp., p_u) and pixel index,
+//     written in raster order to a compacted array (block-wide ballot scan).
 // Unprojection pi^-1 (Sec. III): pinhole p = d K^-1 (u, v, 1)^T; spherical
 // p = d (cos el cos az, cos el sin az, sin el) with az = (u - c_x) / f_x,
 // el = (v - c_y) / f_y.  Validity: range_min <= d <= range_max, d > 0 and
@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
                                                        const SensorDev* __restrict__ sensors,
                                                        const int* __restrict__ frame_ids, void* texels,
                                                        float4* __restrict__ pts_pg, float4* __restrict__ pts_n,
-                                                       int* __restrict__ n_points, double rmin, double rmax) {
+                                                       int* __restrict__ pts_pix, int* __restrict__ n_points,
+                                                       double rmin, double rmax) {
     __shared__ int s_warp[kPackThreads / 32];
     __shared__ int s_base, s_total;
     const int f = frame_ids[blockIdx.x];
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
             }
             pts_pg[fr.pt_offset + idx] = make_float4(pu[0], pu[1], pu[2], c[0]);
             pts_n[fr.pt_offset + idx] = make_float4(no[0], no[1], no[2], 0.f);
+            pts_pix[fr.pt_offset + idx] = px;
         }
         __syncthreads();
         if (threadIdx.x == 0) s_base += s_total;
@@ -131,15 +133,15 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
 }  // namespace
 
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors, const int* frame_ids,
-                        int n, int texel_precision, void* texels, float4* pts_pg, float4* pts_n, int* n_points,
-                        double range_min, double range_max, cudaStream_t s) {
+                        int n, int texel_precision, void* texels, float4* pts_pg, float4* pts_n, int* pts_pix,
+                        int* n_points, double range_min, double range_max, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (texel_precision == 1)
-        k_pack<1><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, n_points,
-                                             range_min, range_max);
+        k_pack<1><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
+                                             n_points, range_min, range_max);
     else
-        k_pack<0><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, n_points,
-                                             range_min, range_max);
+        k_pack<0><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
+                                             n_points, range_min, range_max);
     return cudaGetLastError();
 }
 
