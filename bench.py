@@ -212,6 +212,22 @@ def run_ours(args, rank, world, device):
                phase_ms=phase_ms, wall_s=wall, n_points=int(n_points_total), n_pairs=int(len(w.pairs)),
                stats=stats, variants=variants)
 
+    # adjoint of the total cost (pose / extrinsic / image gradients), events on the same stream
+    start(prob)
+    adj = {}
+    for images in (False, True):
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            prob.cost_gradient(poses=True, extrinsics=True, images=images, device=device)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        adj["with_image_gradient_ms" if images else "poses_extrinsic_ms"] = float(np.median(ts))
+    out["adjoint"] = adj
+
     # graph construction (Sec. IV-B) over every same-sensor candidate within 30 deg / 40 m
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -373,6 +389,7 @@ def main():
             "clocks": out["clocks"],
         }
         line["build_pairs"] = out["build_pairs"]
+        line["adjoint"] = out["adjoint"]
         if "plain_ms_per_step" in out:
             line["plain_ms_per_step"] = out["plain_ms_per_step"]
             line["speedup_vs_plain"] = out["plain_ms_per_step"] / out["ms_per_step"]

@@ -137,6 +137,14 @@ class Problem:
         self._check(self._lib.pba_upload_frames(self._h, first, arr.shape[0], arr.ctypes.data_as(ctypes.c_void_p), 0),
                     "upload_frames")
 
+    def set_extrinsic(self, sensor: int, X):
+        """Replace a sensor's offset X_o (3x4); its frames' points are rebuilt."""
+        if _is_torch(X):
+            X = X.detach().cpu().numpy()
+        arr = np.ascontiguousarray(X, dtype=np.float64).reshape(12)
+        self._check(self._lib.pba_set_extrinsic(self._h, int(sensor), arr.ctypes.data_as(ctypes.c_void_p)),
+                    "set_extrinsic")
+
     def frame_points(self, frame: int) -> int:
         n = ctypes.c_int32()
         self._check(self._lib.pba_frame_points(self._h, frame, ctypes.byref(n)), "frame_points")
@@ -177,6 +185,23 @@ class Problem:
         cost, n = ctypes.c_double(), ctypes.c_int64()
         self._check(self._lib.pba_linearize(self._h, ctypes.byref(cost), ctypes.byref(n)), "linearize")
         return cost.value, n.value
+
+    def cost_gradient(self, poses: bool = True, extrinsics: bool = True, images: bool = False, device=None):
+        """Total cost F and its gradient (pba_cost_gradient): returns
+        (cost, n_valid, dF/dposes (N, 3, 4) or None, dF/dX_o (S, 3, 4) or None,
+        dF/dchannels (total pixels * 5,) float32 or None) as CUDA tensors."""
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        n_s = len(self._sizes)
+        total_px = int(sum(self._sizes[int(k)][0] * self._sizes[int(k)][1] for k in self._fs))
+        dP = torch.zeros((self.n_frames, 3, 4), dtype=torch.float64, device=dev) if poses else None
+        dE = torch.zeros((n_s, 3, 4), dtype=torch.float64, device=dev) if extrinsics else None
+        dI = torch.zeros(total_px * 5, dtype=torch.float32, device=dev) if images else None
+        cost, n = ctypes.c_double(), ctypes.c_int64()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._lib.pba_cost_gradient(self._h, ctypes.byref(cost), ctypes.byref(n), ptr(dP), ptr(dE),
+                                                ptr(dI)), "cost_gradient")
+        return cost.value, n.value, dP, dE, dI
 
     def get_system(self):
         n6 = 6 * self.n_frames
