@@ -48,6 +48,9 @@ WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs w
 # valid residual (sampling, residual, Huber, 5 x 6 Jacobian, 6 x 6 accumulation).
 FLOP_PER_POINT_SPHERICAL = 31
 FLOP_PER_RESIDUAL_FULL = 765
+# normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
+NORMAL_SCALE = 8.0
+NORMAL_MAX_RADIUS = 5
 FP32_LANES_PER_SM = 128
 
 
@@ -235,6 +238,24 @@ def run_ours(args, rank, world, device):
     out["build_pairs"] = {"ms": 1e3 * (time.perf_counter() - t0), "pairs_kept": int(len(gp)),
                           "criteria": "angle < 30 deg, translation < 40 m, valid ratio > 0.3, sequential edges"}
 
+    # normal estimation (Sec. IV-A) of every frame from its depth, then the rebuild of
+    # texels and pixel-points; the problem's later use (e2e) uploads the frames again
+    nts, nwall = [], []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        prob.estimate_normals(0, w.n_frames, scale=NORMAL_SCALE, max_radius=NORMAL_MAX_RADIUS)
+        e1.record(stream)
+        e1.synchronize()
+        nwall.append(1e3 * (time.perf_counter() - t0))
+        nts.append(e0.elapsed_time(e1))
+    out["normals"] = {"device_ms": float(np.median(nts)), "call_ms": float(np.median(nwall)),
+                      "frames": int(w.n_frames), "scale": NORMAL_SCALE, "max_radius": NORMAL_MAX_RADIUS,
+                      "points_after": int(sum(prob.frame_points(k) for k in range(w.n_frames)))}
+
     # the same iteration with the FP64 Cholesky solver (phase times only)
     f64 = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
                                     solver=pba.PBA_SOLVE_CHOLESKY_F64)
@@ -389,6 +410,7 @@ def main():
             "clocks": out["clocks"],
         }
         line["build_pairs"] = out["build_pairs"]
+        line["normals"] = out["normals"]
         line["adjoint"] = out["adjoint"]
         if "plain_ms_per_step" in out:
             line["plain_ms_per_step"] = out["plain_ms_per_step"]

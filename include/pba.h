@@ -145,6 +145,31 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
  * sensor's uploaded frames are rebuilt; the next iteration relinearises. */
 int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic);
 
+/* Normal estimation (Sec. IV-A) for the uploaded frames first..first+count-1,
+ * computed from their depth channel and written over their normal channels
+ * on the device; their texels and pixel-points are then rebuilt (and the
+ * pair plan when a point count changed), as after pba_upload_frames.
+ * For every pixel u with valid depth d (d > 0, range_min <= d <= range_max):
+ * the valid pixels u' with |u - u'| < r(u) (pixel distance, columns wrapping
+ * for the spherical model), r(u) = clamp(scale / d, 1.5, max_radius), are
+ * unprojected; n_u is the normal of their least-squares plane (eigenvector
+ * of the smallest eigenvalue of their covariance) oriented towards the
+ * observer (n_u . p < 0).  A pixel with fewer than 5 such points, or whose
+ * points are collinear (middle eigenvalue <= 1e-6 x largest), gets a zero
+ * normal and so no pixel-point.  Arithmetic is float32.
+ * Errors: PBA_EINVAL (bad range, scale not finite or < 0, max_radius outside
+ * [2, PBA_NORMALS_MAX_RADIUS], a spherical image narrower than
+ * 2 max_radius + 1 columns), PBA_ENOTREADY (a frame not uploaded),
+ * PBA_ECUDA.  Synchronises. */
+#define PBA_NORMALS_MAX_RADIUS 32
+int pba_estimate_normals(pba_problem* p, int first, int count, float scale, int max_radius);
+
+/* Copy the five-channel images of the uploaded frames first..first+count-1
+ * (the layout of pba_upload_frames, frames back to back) to channels (host
+ * memory, or device memory with is_device != 0).  Synchronises.
+ * Errors: PBA_EINVAL, PBA_ENOTREADY (a frame not uploaded), PBA_ECUDA. */
+int pba_get_channels(pba_problem* p, int first, int count, float* channels, int is_device);
+
 /* Number of valid pixel-points of a frame (after its upload). */
 int pba_frame_points(pba_problem* p, int frame, int32_t* n_points);
 

@@ -333,3 +333,74 @@ def build_pairs(sensors, frame_sensor, channels, poses, params: Dict, max_angle:
             if ratio > min_ratio or is_seq:
                 out.append((i, j))
     return dict(pairs=np.array(out, dtype=np.int32).reshape(-1, 2), candidates=info)
+
+
+# ------------------------------------------------------------------ Sec. IV-A: normals
+
+def estimate_normals(sensor, channels: np.ndarray, scale: float, max_radius: int, params: Dict = None,
+                     min_count: int = 5, collinear: float = 1e-6, lib=None) -> Dict:
+    """Normal image of one frame (Sec. IV-A): for every pixel u with valid
+    depth, unproject the valid pixels u' with |u - u'| < r(u) (pixel
+    distance; columns wrap for the spherical model), r(u) = clamp(scale /
+    d(u), 1.5, max_radius) (a radius inversely proportional to the range, at
+    least the 3 x 3 block), fit the least-squares plane (normal = eigenvector
+    of the smallest eigenvalue of the points' covariance, numpy.linalg.eigh)
+    and orient it towards the observer (n . p_u < 0).  A pixel gets a normal
+    when at least min_count points are used and the points are not collinear
+    (middle eigenvalue > collinear * largest); other pixels get 0.
+    Returns normals (H, W, 3), eig (H, W, 3, ascending), count (H, W),
+    radius (H, W), depth_valid (H, W), dmax (H, W: the largest depth among
+    the points used) and margin (H, W): pixels where a
+    decision lies close to its threshold (an integer squared offset within
+    1e-4 relative of r^2, the collinearity ratio within 1e-4 of its bound, or
+    |n . p| < 1e-4 |p|), so that float32 arithmetic may decide otherwise."""
+    s = sensor
+    g = (lambda k: s[k]) if isinstance(s, dict) else (lambda k: getattr(s, k))
+    H, W, model = int(g("height")), int(g("width")), int(g("model"))
+    d = np.asarray(channels)[..., 1].astype(np.float64)
+    rmin = (params or {}).get("range_min", 0.0)
+    rmax = (params or {}).get("range_max", 1e30)
+    valid = (d > 0) & (d >= rmin) & (d <= rmax)
+    # unprojected points of every pixel, through the oracle's own pi^-1
+    P = np.zeros((H, W, 3))
+    for r in range(H):
+        for c in range(W):
+            if valid[r, c]:
+                P[r, c] = unproject(s, float(c), float(r), d[r, c], lib=lib)
+    rad = np.where(valid, np.clip(scale / np.where(valid, d, 1.0), 1.5, float(max_radius)), 0.0)
+    S1 = np.zeros((H, W, 3))
+    S2 = np.zeros((H, W, 3, 3))
+    N = np.zeros((H, W), dtype=np.int64)
+    dmax = np.where(valid, d, 0.0)
+    near = np.zeros((H, W), dtype=bool)
+    for dr in range(-max_radius, max_radius + 1):
+        for dc in range(-max_radius, max_radius + 1):
+            dd2 = dr * dr + dc * dc
+            near |= valid & (np.abs(dd2 - rad * rad) <= 1e-4 * rad * rad) & (rad > 1.5) & (rad < max_radius)
+            rows = np.arange(H)[:, None] + dr
+            cols = np.arange(W)[None, :] + dc
+            if model == 1:
+                cols = cols % W
+            inside = (rows >= 0) & (rows < H) & (cols >= 0) & (cols < W)
+            rr = np.clip(rows, 0, H - 1)
+            cc = np.clip(cols, 0, W - 1)
+            take = inside & valid & (dd2 < rad * rad) & valid[rr, cc]
+            q = P[rr, cc] - P  # relative to the centre pixel's point
+            q = np.where(take[..., None], q, 0.0)
+            S1 += q
+            S2 += q[..., :, None] * q[..., None, :]
+            N += take
+            dmax = np.maximum(dmax, np.where(take, d[rr, cc], 0.0))
+    Nn = np.maximum(N, 1)[..., None]
+    mean = S1 / Nn
+    cov = S2 / Nn[..., None] - mean[..., :, None] * mean[..., None, :]
+    ev, evec = np.linalg.eigh(cov.reshape(-1, 3, 3))
+    ev = ev.reshape(H, W, 3)
+    n = evec[:, :, 0].reshape(H, W, 3)
+    nP = np.sum(n * P, axis=-1)
+    n = np.where((nP > 0)[..., None], -n, n)
+    ok = valid & (N >= min_count) & (ev[..., 1] > collinear * ev[..., 2])
+    near |= valid & (N >= min_count) & (np.abs(ev[..., 1] - collinear * ev[..., 2]) <= 1e-4 * ev[..., 2])
+    near |= ok & (np.abs(nP) < 1e-4 * np.linalg.norm(P, axis=-1))
+    n = np.where(ok[..., None], n, 0.0)
+    return dict(normals=n, eig=ev, count=N, radius=rad, depth_valid=valid, margin=near, dmax=dmax)

@@ -145,6 +145,33 @@ class Problem:
         self._check(self._lib.pba_set_extrinsic(self._h, int(sensor), arr.ctypes.data_as(ctypes.c_void_p)),
                     "set_extrinsic")
 
+    def estimate_normals(self, first: int = 0, count: Optional[int] = None, scale: float = 10.0,
+                         max_radius: int = 5):
+        """Sec. IV-A: recompute the normal channels of uploaded frames from their
+        depth (plane fit over a radius clamp(scale / d, 1.5, max_radius) pixels,
+        oriented towards the observer) and rebuild their pixel-points."""
+        count = self.n_frames - first if count is None else int(count)
+        self._check(self._lib.pba_estimate_normals(self._h, int(first), count, float(scale), int(max_radius)),
+                    "estimate_normals")
+
+    def get_channels(self, first: int = 0, count: int = 1, out=None):
+        """The (count, H, W, 5) float32 cue images of uploaded frames as stored on
+        the device (after estimate_normals: with the estimated normals)."""
+        H, W = self._sizes[int(self._fs[first])]
+        for k in range(first, first + count):
+            if self._sizes[int(self._fs[k])] != (H, W):
+                raise ValueError("get_channels: frames of one call must share the image size")
+        if out is not None and _is_torch(out) and out.is_cuda:
+            if not out.is_contiguous() or out.numel() != count * H * W * 5 or str(out.dtype) != "torch.float32":
+                raise ValueError(f"get_channels: out must be a contiguous float32 tensor of {count * H * W * 5} values")
+            self._check(self._lib.pba_get_channels(self._h, int(first), int(count), ctypes.c_void_p(out.data_ptr()), 1),
+                        "get_channels")
+            return out
+        arr = np.empty((count, H, W, 5), dtype=np.float32)
+        self._check(self._lib.pba_get_channels(self._h, int(first), int(count),
+                                               arr.ctypes.data_as(ctypes.c_void_p), 0), "get_channels")
+        return arr
+
     def frame_points(self, frame: int) -> int:
         n = ctypes.c_int32()
         self._check(self._lib.pba_frame_points(self._h, frame, ctypes.byref(n)), "frame_points")

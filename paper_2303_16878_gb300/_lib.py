@@ -42,7 +42,8 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
-           "pba_set_extrinsic", "pba_cost_gradient"]
+           "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels"]
+PBA_NORMALS_MAX_RADIUS = 32
 PBA_N_PHASES = 5
 PHASE_NAMES = ["solve", "update", "linearize", "reduce_assemble", "accept"]
 
@@ -116,6 +117,8 @@ def load(build_if_missing: bool = True):
             "pba_autotune": ([vp, ctypes.c_int, P(i32), P(i32)], ctypes.c_int),
             "pba_build_pairs": ([vp, d, d, d, ctypes.c_int, vp, vp, ctypes.c_int, P(i32)], ctypes.c_int),
             "pba_set_extrinsic": ([vp, ctypes.c_int, vp], ctypes.c_int),
+            "pba_estimate_normals": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int], ctypes.c_int),
+            "pba_get_channels": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
             "pba_cost_gradient": ([vp, P(d), P(i64), vp, vp, vp], ctypes.c_int),
             "pba_linearize_pairs_noalloc": ([P(PbaSensor), P(PbaConfig), vp, ctypes.c_int, vp, vp, ctypes.c_int, vp,
                                              vp], ctypes.c_int),

@@ -282,6 +282,40 @@ int ready(pba_problem* p) {
     return PBA_OK;
 }
 
+// Optionally re-estimates the normals of frames first..first+count-1 (max_radius > 0),
+// then rebuilds their texels and pixel-points and, when a point count changed, the
+// pair plan.  Synchronises.
+int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
+    std::vector<int> ids(count);
+    int max_px = 0;
+    for (int k = 0; k < count; ++k) {
+        ids[k] = first + k;
+        const pba_sensor& S = p->sensors[p->frame_sensor[first + k]];
+        max_px = std::max(max_px, S.width * S.height);
+    }
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice, p->stream));
+    if (max_radius > 0)
+        CUDA_TRY(p, launch_normals(p->raw, p->d_frames, p->d_frame_ids, count, max_px, scale, max_radius,
+                                   p->cfg.range_min, p->cfg.range_max, p->stream));
+    CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
+                            p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
+                            p->stream));
+    // the id list is pageable host memory: the synchronisation also makes sure
+    // the copy has consumed it
+    std::vector<int> before = p->n_points;
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    CUDA_TRY(p, cudaMemcpy(p->n_points.data(), p->d_npoints, sizeof(int) * p->N, cudaMemcpyDeviceToHost));
+    p->points_known = true;
+    p->linearized = false;
+    p->mask_valid = false;
+    if (p->M > 0 && before != p->n_points) {
+        // the chunk queue depends on the point counts: rebuild the pair plan
+        std::vector<int32_t> keep = p->pairs;
+        return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
+    }
+    return PBA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -502,26 +536,38 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
     const size_t bytes = sizeof(float) * 5 * (size_t)S0.width * S0.height * count;
     CUDA_TRY(p, cudaMemcpyAsync(p->raw + 5 * p->px_off[first], channels, bytes,
                                 is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-    std::vector<int> ids(count);
-    for (int k = 0; k < count; ++k) ids[k] = first + k;
-    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice, p->stream));
-    CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
-                            p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
-                            p->stream));
-    // the id list is pageable host memory: the synchronisation also makes sure
-    // the copy has consumed it
-    std::vector<int> before = p->n_points;
-    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
-    CUDA_TRY(p, cudaMemcpy(p->n_points.data(), p->d_npoints, sizeof(int) * p->N, cudaMemcpyDeviceToHost));
-    p->points_known = true;
     for (int k = first; k < first + count; ++k) p->uploaded[k] = 1;
-    p->linearized = false;
-    p->mask_valid = false;
-    if (p->M > 0 && before != p->n_points) {
-        // the chunk queue depends on the point counts: rebuild the pair plan
-        std::vector<int32_t> keep = p->pairs;
-        return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
+    return repack(p, first, count, 0.f, 0);
+}
+
+int pba_estimate_normals(pba_problem* p, int first, int count, float scale, int max_radius) {
+    if (!p) return PBA_EINVAL;
+    if (count < 1 || first < 0 || first + count > p->N)
+        return fail(p, PBA_EINVAL, "estimate_normals: bad frame range");
+    if (!(scale >= 0.f) || !(scale < 1e30f) || max_radius < 2 || max_radius > PBA_NORMALS_MAX_RADIUS)
+        return fail(p, PBA_EINVAL, "estimate_normals: scale must be finite and >= 0, max_radius in [2, 32]");
+    for (int k = first; k < first + count; ++k) {
+        const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+        if (S.model == PBA_SPHERICAL && 2 * max_radius + 1 > S.width)
+            return fail(p, PBA_EINVAL, "estimate_normals: spherical image narrower than the neighbourhood");
+        if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "estimate_normals: frame not uploaded");
     }
+    cudaSetDevice(p->device);
+    return repack(p, first, count, scale, max_radius);
+}
+
+int pba_get_channels(pba_problem* p, int first, int count, float* channels, int is_device) {
+    if (!p) return PBA_EINVAL;
+    if (!channels || count < 1 || first < 0 || first + count > p->N)
+        return fail(p, PBA_EINVAL, "get_channels: bad frame range or null output");
+    for (int k = first; k < first + count; ++k)
+        if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "get_channels: frame not uploaded");
+    cudaSetDevice(p->device);
+    const long long end = first + count < p->N ? p->px_off[first + count] : p->total_px;
+    const size_t bytes = sizeof(float) * 5 * (size_t)(end - p->px_off[first]);
+    CUDA_TRY(p, cudaMemcpyAsync(channels, p->raw + 5 * p->px_off[first], bytes,
+                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     return PBA_OK;
 }
 

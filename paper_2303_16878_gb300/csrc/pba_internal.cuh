@@ -120,6 +120,10 @@ struct AsmContrib {
 
 namespace pba {
 
+// Normal estimation (Sec. IV-A), in place on the normal channels of raw.
+cudaError_t launch_normals(float* raw, const FrameInfo* frames, const int* frame_ids, int n, int max_px, float scale,
+                           int max_radius, double range_min, double range_max, cudaStream_t s);
+
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors,
                         const int* frame_ids, int n, int texel_precision, void* texels,
                         float4* pts_pg, float4* pts_n, int* pts_pix, int* n_points, double range_min,

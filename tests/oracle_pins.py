@@ -34,6 +34,10 @@ PIN_TOL = {
     "cholesky": 1e-10,
     "extrinsic_equivalence": 1e-9,
     "jacobian_fd_extrinsic": 1e-6,
+    "normals_plane": 1e-9,
+    "normals_counts": 0.5,
+    "normals_brute_force": 1e-8,
+    "normals_degenerate": 0.5,
 }
 
 
@@ -369,6 +373,149 @@ def pin_cholesky(O, lib):
     return worst
 
 
+# ---------------------------------------------------------------- normals (Sec. IV-A)
+
+def _plane_depth(s, n, c):
+    """Depth image of the plane n . p = c seen by sensor s (closed form: the
+    ray p = z r (pinhole, r = K^-1 [u v 1]) or p = rho r (spherical, r the unit
+    ray), so z = c / (n . r)); 0 where the plane lies behind."""
+    H, W = s.height, s.width
+    v, u = np.mgrid[0:H, 0:W].astype(np.float64)
+    if s.model == 0:
+        r = np.stack([(u - s.cx) / s.fx, (v - s.cy) / s.fy, np.ones_like(u)], -1)
+    else:
+        az, el = (u - s.cx) / s.fx, (v - s.cy) / s.fy
+        r = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], -1)
+    den = r @ np.asarray(n, dtype=np.float64)
+    z = np.where(np.abs(den) > 1e-9, c / np.where(np.abs(den) > 1e-9, den, 1.0), -1.0)
+    ch = np.zeros((H, W, 5))
+    ch[..., 1] = np.where((z > 0) & (z < 50.0), z, 0.0)
+    return ch
+
+
+def pin_normals_plane(O, lib=None):
+    """Points of one plane: every pixel gets exactly the plane's normal, turned
+    towards the sensor (n . p < 0), for a pinhole and a spherical sensor and
+    radii varying with the depth.  Returns the largest |n - n_true| (inf if a
+    valid pixel with at least 5 neighbours got no normal, or another one did)."""
+    from paper_2303_16878_gb300 import synth
+    cases = [(synth.pinhole_sensor(48, 40, 40.0, 23.5, 19.5), np.array([0.3, -0.2, 0.93]), 2.5, 6.0, 4),
+             (synth.spherical_sensor(96, 16, 10.0, -25.0), np.array([0.1, 0.05, 1.0]), -1.7, 12.0, 5)]
+    worst = 0.0
+    for s, n, c, scale, rmax in cases:
+        n = n / np.linalg.norm(n)
+        ch = _plane_depth(s, n, c * np.linalg.norm(n))
+        out = O.estimate_normals(s, ch, scale, rmax, lib=lib)
+        valid = (ch[..., 1] > 0) & (out["count"] >= 5)
+        has = np.linalg.norm(out["normals"], axis=-1) > 0
+        if not np.array_equal(valid, has) or valid.sum() < 100:
+            return float("inf")
+        toward = -n if c > 0 else n  # the sensor sits on the side n . p < c
+        worst = max(worst, float(np.abs(out["normals"][valid] - toward).max()))
+    return worst
+
+
+# Lattice points (a, b) with a^2 + b^2 < r^2, counted by hand: 9 for r = 1.5
+# (the 3 x 3 block), 21 for r = 2.5, 69 for r = 5 (81 points with a^2 + b^2 <= 25
+# minus the 12 on the circle).  The half disc b >= 0 holds 6, 13 and 39 of
+# them (rows b = 0..4 of r = 5: 9 + 9 + 9 + 7 + 5); the quarter disc a, b >= 0
+# of r = 2.5 holds 8.
+LATTICE_DISC = {1.5: 9, 2.5: 21, 5.0: 69}
+LATTICE_HALF = {1.5: 6, 2.5: 13, 5.0: 39}
+LATTICE_QUARTER_2_5 = 8
+
+
+def pin_normals_counts(O, lib=None):
+    """Neighbourhood sizes |U| on constant-depth images: interior pixels use the
+    full disc of radius clamp(scale / d, 1.5, max_radius); a pinhole corner
+    uses a quarter disc; a spherical image wraps its columns, so column 0 of
+    an interior row uses the full disc.  Returns the number of mismatches."""
+    from paper_2303_16878_gb300 import synth
+    bad = 0
+    for model in (0, 1):
+        s = (synth.pinhole_sensor(24, 20, 20.0, 11.5, 9.5) if model == 0
+             else synth.spherical_sensor(64, 20, 15.0, -15.0))
+        for d, scale, rmax, r in ((4.0, 4.0, 4, 1.5), (2.0, 5.0, 4, 2.5), (1.0, 10.0, 5, 5.0), (0.5, 10.0, 5, 5.0)):
+            ch = np.zeros((s.height, s.width, 5))
+            ch[..., 1] = d
+            N = O.estimate_normals(s, ch, scale, rmax, lib=lib)["count"]
+            bad += int(N[10, 12] != LATTICE_DISC[r])
+            edge = LATTICE_DISC[r] if model == 1 else LATTICE_HALF[r]
+            bad += int(N[10, 0] != edge) + int(N[10, s.width - 1] != edge)
+            if r == 2.5 and model == 0:
+                bad += int(N[0, 0] != LATTICE_QUARTER_2_5)
+    return float(bad)
+
+
+def pin_normals_brute_force(O, lib, w, stride=5):
+    """Every stride-th pixel of frame 0 of w: the neighbour set enumerated pixel
+    by pixel, the points unprojected with the closed forms of Sec. III, and the
+    best-fitting plane taken from numpy's SVD of the centred points (the
+    singular vector of the smallest singular value).  Compared where the two
+    smallest singular values are well apart; returns the largest |n - n_bf|."""
+    s = w.sensors[0]
+    ch = w.channels[0]
+    scale, rmax = (6.0, 4) if s.model == 0 else (8.0, 4)
+    out = O.estimate_normals(s, ch, scale, rmax, params=w.params, lib=lib)
+    H, W = s.height, s.width
+    d = ch[..., 1].astype(np.float64)
+    valid = (d > 0) & (d >= w.params["range_min"]) & (d <= w.params["range_max"])
+
+    def point(r, c):
+        if s.model == 0:
+            return d[r, c] * np.array([(c - s.cx) / s.fx, (r - s.cy) / s.fy, 1.0])
+        az, el = (c - s.cx) / s.fx, (r - s.cy) / s.fy
+        return d[r, c] * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+
+    worst, used = 0.0, 0
+    for k in range(0, H * W, stride):
+        r0, c0 = divmod(k, W)
+        if not valid[r0, c0]:
+            continue
+        rad = min(max(scale / d[r0, c0], 1.5), float(rmax))
+        pts = []
+        for r in range(max(0, r0 - rmax), min(H, r0 + rmax + 1)):
+            for c in (range(W) if s.model == 1 else range(max(0, c0 - rmax), min(W, c0 + rmax + 1))):
+                dc = c - c0
+                if s.model == 1:
+                    dc = min(abs(dc), W - abs(dc))
+                if (r - r0) ** 2 + dc ** 2 < rad * rad and valid[r, c]:
+                    pts.append(point(r, c))
+        if len(pts) != out["count"][r0, c0]:
+            return float("inf")
+        if len(pts) < 5:
+            continue
+        X = np.array(pts)
+        X -= X.mean(axis=0)
+        _, sv, vt = np.linalg.svd(X)
+        if sv[1] - sv[2] < 1e-3 * sv[0]:
+            continue
+        nb = vt[2] if np.dot(vt[2], point(r0, c0)) <= 0 else -vt[2]
+        worst = max(worst, float(np.abs(out["normals"][r0, c0] - nb).max()))
+        used += 1
+    return worst if used > 200 else float("inf")
+
+
+def pin_normals_degenerate(O, lib=None):
+    """No normal where the plane is undetermined: a single valid row of a
+    pinhole image (collinear points), and valid pixels isolated on a grid of
+    pitch 3 (a neighbourhood of radius below 3 holds only the pixel itself).  Returns
+    the number of pixels that got a normal."""
+    from paper_2303_16878_gb300 import synth
+    s = synth.pinhole_sensor(32, 24, 30.0, 15.5, 11.5)
+    n_bad = 0
+    ch = _plane_depth(s, np.array([0.0, 0.0, 1.0]), 2.0)
+    ch[np.arange(24) != 12, :, 1] = 0.0
+    n_bad += int(np.count_nonzero(np.linalg.norm(O.estimate_normals(s, ch, 5.0, 4, lib=lib)["normals"], axis=-1)))
+    ch = _plane_depth(s, np.array([0.2, 0.1, 1.0]) / np.linalg.norm([0.2, 0.1, 1.0]), 2.0)
+    keep = np.zeros((24, 32), dtype=bool)
+    keep[::3, ::3] = True
+    ch[~keep, 1] = 0.0
+    out = O.estimate_normals(s, ch, 5.0, 4, lib=lib)  # r = clamp(5 / d, ...) is about 2.5
+    n_bad += int(np.count_nonzero(np.linalg.norm(out["normals"], axis=-1)))
+    return float(n_bad)
+
+
 def all_pins(O, lib, room, street):
     """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
     return {
@@ -386,4 +533,8 @@ def all_pins(O, lib, room, street):
         "cholesky": pin_cholesky(O, lib),
         "extrinsic_equivalence": pin_extrinsic_equivalence(O, lib, room),
         "jacobian_fd_extrinsic": pin_jacobian_fd_extrinsic(O, lib, room),
+        "normals_plane": pin_normals_plane(O, lib),
+        "normals_counts": pin_normals_counts(O, lib),
+        "normals_brute_force": max(pin_normals_brute_force(O, lib, room), pin_normals_brute_force(O, lib, street)),
+        "normals_degenerate": pin_normals_degenerate(O, lib),
     }

@@ -67,3 +67,48 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
         if failed:
             break
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+# Planted mistakes in the oracle's normal estimation (Python, Sec. IV-A).
+PY_SRC = os.path.join(os.path.dirname(SRC), "__init__.py")
+
+NORMAL_MUTATIONS = {
+    "mean_not_subtracted": ("cov = S2 / Nn[..., None] - mean[..., :, None] * mean[..., None, :]",
+                            "cov = S2 / Nn[..., None]"),
+    "largest_eigenvector": ("n = evec[:, :, 0].reshape(H, W, 3)", "n = evec[:, :, 2].reshape(H, W, 3)"),
+    "oriented_away_from_observer": ("n = np.where((nP > 0)[..., None], -n, n)",
+                                    "n = np.where((nP < 0)[..., None], -n, n)"),
+    "columns_not_wrapped": ("cols = cols % W", "cols = cols"),
+    "radius_grows_with_range": ("np.clip(scale / np.where(valid, d, 1.0)", "np.clip(scale * np.where(valid, d, 1.0)"),
+    "radius_inclusive": ("(dd2 < rad * rad) & valid[rr, cc]", "(dd2 <= rad * rad) & valid[rr, cc]"),
+    "invalid_neighbours_used": ("(dd2 < rad * rad) & valid[rr, cc]", "(dd2 < rad * rad)"),
+    "collinear_points_kept": ("(ev[..., 1] > collinear * ev[..., 2])", "(ev[..., 2] > 0)"),
+    "min_count_ignored": ("ok = valid & (N >= min_count)", "ok = valid & (N >= 1)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(NORMAL_MUTATIONS))
+def test_planted_normal_mistake_is_caught(name, oracle_lib, room3, street3):
+    import types
+    before, after = NORMAL_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle_mutated")
+    mod.__file__ = PY_SRC
+    exec(compile(src.replace(before, after), PY_SRC, "exec"), mod.__dict__)
+    lib = oracle_lib.load()
+    failed = []
+    for pin, fn in [("normals_plane", lambda: P.pin_normals_plane(mod, lib)),
+                    ("normals_counts", lambda: P.pin_normals_counts(mod, lib)),
+                    ("normals_degenerate", lambda: P.pin_normals_degenerate(mod, lib)),
+                    ("normals_brute_force", lambda: max(P.pin_normals_brute_force(mod, lib, room3),
+                                                        P.pin_normals_brute_force(mod, lib, street3)))]:
+        try:
+            err = fn()
+        except Exception:
+            failed.append(pin)
+            break
+        if not err < P.PIN_TOL[pin]:
+            failed.append(pin)
+            break
+    assert failed, f"no pin caught the planted mistake {name}"

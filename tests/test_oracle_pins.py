@@ -148,3 +148,21 @@ def test_lm_converges_towards_ground_truth(oracle_lib):
     # at 80x60 (1 deg pixels) interpolation bias keeps the minimum ~1 cm / ~0.3 deg off ground truth
     assert t_err < 0.25 * t_err0 and t_err < 0.012
     assert r_err < 0.15 * r_err0
+
+
+def test_normals_of_a_plane_are_its_normal(oracle_lib):
+    assert P.pin_normals_plane(oracle_lib, oracle_lib.load()) < P.PIN_TOL["normals_plane"]
+
+
+def test_normal_neighbourhood_sizes_match_lattice_counts(oracle_lib):
+    assert P.pin_normals_counts(oracle_lib, oracle_lib.load()) < P.PIN_TOL["normals_counts"]
+
+
+@pytest.mark.parametrize("which", ["room3", "street3"])
+def test_normals_match_brute_force_plane_fit(oracle_lib, which, request):
+    w = request.getfixturevalue(which)
+    assert P.pin_normals_brute_force(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["normals_brute_force"]
+
+
+def test_no_normal_where_the_plane_is_undetermined(oracle_lib):
+    assert P.pin_normals_degenerate(oracle_lib, oracle_lib.load()) < P.PIN_TOL["normals_degenerate"]
