@@ -78,24 +78,32 @@ def make_workload(name):
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Started before the
+    warm-up so that short timed regions still see samples: mark() brackets the
+    timed region, and stop() keeps the samples taken inside it (widened by
+    `slack` seconds on both sides when it holds fewer than three)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
         self.proc = None
         self.path = None
         self.gpu = gpu_index
+        self.window = None
         if shutil.which("nvidia-smi"):
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
 
-    def stop(self):
+    def mark(self, t0: float, t1: float):
+        """The timed region, as time.time() values."""
+        self.window = (t0, t1)
+
+    def stop(self, slack: float = 0.5):
         if not self.proc:
             return None
         self.proc.terminate()
@@ -103,28 +111,55 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]) if f[3] not in ("[N/A]", "") else 0.0,
-                                 hw=f[5], hw_th=f[6], sw_th=f[7], pcap=f[8]))
-            except ValueError:
-                continue
+        with open(self.path) as fh:
+            rows = parse_clock_lines(fh)
         os.unlink(self.path)
-        if not rows:
-            return None
-        reasons = set()
-        for r in rows:
-            for key, name in (("hw", "hw_slowdown"), ("hw_th", "hw_thermal_slowdown"),
-                              ("sw_th", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
-                if r[key].lower().startswith("active"):
-                    reasons.add(name)
-        loaded = [r["sm"] for r in rows if r["power"] > 0.25 * max(x["power"] for x in rows)] or [r["sm"] for r in rows]
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["max"] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows)}
+        return summarise_clocks(rows, self.window, slack)
+
+
+def parse_clock_lines(lines):
+    """Rows of the ClockSampler query (nvidia-smi csv, noheader, nounits)."""
+    from datetime import datetime
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            ts = datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            rows.append(dict(ts=ts, sm=float(f[2]), max=float(f[3]),
+                             power=float(f[4]) if f[4] not in ("[N/A]", "") else 0.0,
+                             hw=f[6], hw_th=f[7], sw_th=f[8], pcap=f[9]))
+        except ValueError:
+            continue
+    return rows
+
+
+def summarise_clocks(rows, window=None, slack: float = 0.5):
+    """Median SM clock under load, the max clock and the throttle reasons seen
+    within the window (t0, t1) (widened by slack seconds when it holds fewer
+    than three samples)."""
+    in_region = rows
+    widened = False
+    if window is not None:
+        t0, t1 = window
+        in_region = [r for r in rows if t0 <= r["ts"] <= t1]
+        if len(in_region) < 3:
+            in_region = [r for r in rows if t0 - slack <= r["ts"] <= t1 + slack]
+            widened = True
+    if not in_region:
+        return None
+    reasons = set()
+    for r in in_region:
+        for key, name in (("hw", "hw_slowdown"), ("hw_th", "hw_thermal_slowdown"),
+                          ("sw_th", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+            if r[key].lower().startswith("active"):
+                reasons.add(name)
+    top = max(x["power"] for x in in_region)
+    loaded = [r["sm"] for r in in_region if r["power"] > 0.25 * top] or [r["sm"] for r in in_region]
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["max"] for r in in_region),
+            "reasons": sorted(reasons), "samples": len(in_region),
+            "window": "timed region +- %.1f s" % slack if widened else "timed region"}
 
 
 # ----------------------------------------------------------------------------- ranks
@@ -176,6 +211,7 @@ def run_ours(args, rank, world, device):
         return e0.elapsed_time(e1), p.get_stats()
 
     variants = prob.autotune(2)
+    clocks = ClockSampler(device.index if device.index is not None else 0)
     start(prob)
     for _ in range(args.warmup):
         one_step(prob)
@@ -185,7 +221,7 @@ def run_ours(args, rank, world, device):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(device.index if device.index is not None else 0)
+    epoch0 = time.time()
     wall0 = time.perf_counter()
     ms, nvalid, stats = [], [], None
     for _ in range(args.steps):
@@ -194,6 +230,7 @@ def run_ours(args, rank, world, device):
         nvalid.append(stats["n_valid"])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.mark(epoch0, time.time())
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
