@@ -274,6 +274,54 @@ int pba_iterate_async(pba_problem* p, int n);
 /* Synchronise and read the outcome of the last iteration. */
 int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
 
+/* ---- Pyramid and coarse-to-fine optimisation (Sec. IV-A, Sec. IV-C) ----
+ *
+ * Level 0 is the problem itself; level l + 1 halves the resolution of level
+ * l (sizes rounded down; each level at least 4 x 4).  A coarse pixel
+ * summarises a 2 x 2 block: valid when all four fine pixels are valid, then
+ * g and d are the block means and n the normalised sum of the four normals
+ * (float64 sums of the float32 inputs, rounded once to float32).  Its
+ * intrinsics are f' = f / 2, c' = (c + 1/2) / 2 - 1/2 (the coarse pixel k is
+ * centred on fine coordinate 2k + 1/2), for both models; extrinsics,
+ * weights, thresholds, path, texels and solver are those of the problem. */
+#define PBA_MAX_LEVELS 8
+
+/* Build levels 1..n_levels-1 from the uploaded frames (downsampled on the
+ * device), with the problem's poses and pairs.  Each level is a problem of
+ * its own, owned by p and on p's stream.  Uploading frames, estimating
+ * normals, setting pairs or an extrinsic afterwards makes the pyramid stale
+ * (PBA_ENOTREADY from the calls below until it is rebuilt).  Allocates;
+ * synchronises.  Errors: PBA_EINVAL (n_levels outside [1, PBA_MAX_LEVELS],
+ * a level below 4 x 4), PBA_ENOTREADY (a frame not uploaded), PBA_ENOMEM,
+ * PBA_ECUDA. */
+int pba_build_pyramid(pba_problem* p, int n_levels);
+
+/* The problem of one level (borrowed: owned by p, valid until the pyramid is
+ * rebuilt or p destroyed; level 0 returns p).  Every entry point applies to
+ * it, e.g. to linearise at a coarse level. */
+int pba_pyramid_level(pba_problem* p, int level, pba_problem** level_out);
+
+/* Outcome of one level of pba_optimize. */
+typedef struct {
+    int32_t level;       /* 0 = finest */
+    int32_t iterations;  /* LM iterations run (accepted or not) */
+    int32_t accepted;
+    int32_t status;      /* PBA_OK, or PBA_ENOTPD when some step met a non-positive pivot */
+    double cost_first;   /* F at the level's starting poses */
+    double cost_last;    /* F at the level's final poses */
+} pba_level_stats;
+
+/* Hierarchical optimisation (Sec. IV-C): Levenberg-Marquardt on level
+ * n_levels-1 (coarsest) first, then on each finer level from the poses
+ * reached so far, ending on level 0, whose poses are the problem's.  Each
+ * level starts with automatic damping and runs at most max_iters[k]
+ * iterations (k = 0 the coarsest), ending early at the first accepted step
+ * whose relative decrease (F - F_new) / F is below rel_tol (the paper's
+ * error-variation criterion).  stats (n_levels entries, coarsest first) may
+ * be NULL.  Synchronises after every iteration.  Errors: PBA_EINVAL,
+ * PBA_ENOTREADY (stale pyramid, poses or pairs not set), PBA_ECUDA. */
+int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double rel_tol, pba_level_stats* stats);
+
 /* Number of kernel launches one pba_iterate performs (for accounting). */
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 

@@ -404,3 +404,95 @@ def estimate_normals(sensor, channels: np.ndarray, scale: float, max_radius: int
     near |= ok & (np.abs(nP) < 1e-4 * np.linalg.norm(P, axis=-1))
     n = np.where(ok[..., None], n, 0.0)
     return dict(normals=n, eig=ev, count=N, radius=rad, depth_valid=valid, margin=near, dmax=dmax)
+
+
+# ------------------------------------------------------------------ Sec. IV-A: pyramids, Sec. IV-C: coarse to fine
+
+def downsample_sensor(sensor):
+    """Intrinsics of the level with half the resolution (Sec. IV-A, each level
+    half the previous one).  Coarse pixel k covers fine pixels 2k and 2k + 1,
+    so its centre is fine coordinate 2k + 1/2: u_coarse = (u_fine + 1/2) / 2 -
+    1/2 for every projected point, i.e. f' = f / 2 and c' = (c + 1/2) / 2 - 1/2
+    for both models (Eq. pinhole-projection, Eq. spherical-projection are
+    affine in K).  Sizes are halved (rounded down)."""
+    s = sensor
+    g = (lambda k: s[k]) if isinstance(s, dict) else (lambda k: getattr(s, k))
+    out = dict(model=int(g("model")), width=int(g("width")) // 2, height=int(g("height")) // 2,
+               fx=float(g("fx")) / 2.0, fy=float(g("fy")) / 2.0,
+               cx=(float(g("cx")) + 0.5) / 2.0 - 0.5, cy=(float(g("cy")) + 0.5) / 2.0 - 0.5)
+    ext = g("extrinsic") if (isinstance(s, dict) and "extrinsic" in s) or hasattr(s, "extrinsic") else None
+    out["extrinsic"] = np.asarray(ext if ext is not None else np.eye(3, 4), dtype=np.float64).reshape(12)
+    return out
+
+
+def downsample(channels: np.ndarray, params: Dict) -> np.ndarray:
+    """Five-channel image of the next pyramid level (Sec. IV-A): coarse pixel
+    (r, c) summarises the 2 x 2 block of fine pixels (2r..2r+1, 2c..2c+1).  It
+    is valid when all four are valid pixels (d > 0, range_min <= d <=
+    range_max, |n| > 0.5); then g and d are the block means and n the
+    normalised sum of the four normals, each computed in float64 from the
+    float32 inputs ((a + b) + (c + d) summed exactly, one rounding to float32
+    at the end; |s| = sqrt((s_x^2 + s_y^2) + s_z^2)).  Invalid coarse pixels are
+    all zero."""
+    x = np.asarray(channels, dtype=np.float32)
+    H, W = x.shape[0] // 2, x.shape[1] // 2
+    x = x[:2 * H, :2 * W].astype(np.float64)
+    d = x[..., 1]
+    n2 = x[..., 2] * x[..., 2] + x[..., 3] * x[..., 3] + x[..., 4] * x[..., 4]
+    valid = (d > 0) & (d >= params["range_min"]) & (d <= params["range_max"]) & (n2 > 0.25)
+    blocks = x.reshape(H, 2, W, 2, 5)
+    vb = valid.reshape(H, 2, W, 2).all(axis=(1, 3))
+    s = (blocks[:, 0, :, 0] + blocks[:, 0, :, 1]) + (blocks[:, 1, :, 0] + blocks[:, 1, :, 1])
+    out = np.zeros((H, W, 5))
+    out[..., 0] = s[..., 0] * 0.25
+    out[..., 1] = s[..., 1] * 0.25
+    norm = np.sqrt((s[..., 2] * s[..., 2] + s[..., 3] * s[..., 3]) + s[..., 4] * s[..., 4])
+    for k in range(3):
+        out[..., 2 + k] = s[..., 2 + k] / np.where(norm > 0, norm, 1.0)
+    out = np.where((vb & (norm > 0))[..., None], out, 0.0)
+    return out.astype(np.float32)
+
+
+def pyramid(w, n_levels: int):
+    """Levels 0 (the input) .. n_levels - 1 of a workload-like `w`: a list of
+    (sensors, channels) with every frame downsampled level by level."""
+    levels = [([s.as_dict() if hasattr(s, "as_dict") else dict(s) for s in w.sensors], list(w.channels))]
+    for _ in range(1, n_levels):
+        sens, chans = levels[-1]
+        levels.append(([downsample_sensor(s) for s in sens], [downsample(c, w.params) for c in chans]))
+    return levels
+
+
+class _Level:
+    def __init__(self, w, sensors, channels):
+        self.sensors, self.channels = sensors, channels
+        self.frame_sensor, self.pairs, self.params = w.frame_sensor, w.pairs, w.params
+
+
+def coarse_to_fine(w, poses, n_levels: int, max_iters: Sequence[int], rel_tol: float, lib=None) -> Dict:
+    """The hierarchical optimisation of Sec. IV-C: Levenberg-Marquardt from
+    the coarsest level to the finest, each level starting from the poses of
+    the previous one with a fresh damping (initial_lambda).  A level ends
+    after max_iters[level] iterations (coarsest first) or at the first
+    accepted step whose relative decrease of F, (F - F_new) / F, is below
+    rel_tol (the error-variation criterion); rejected steps count as
+    iterations.  Returns the final poses and one log entry per level."""
+    levels = pyramid(w, n_levels)
+    poses = np.asarray(poses, dtype=np.float64).reshape(-1, 3, 4).copy()
+    log = []
+    for li in range(n_levels - 1, -1, -1):
+        lw = _Level(w, *levels[li])
+        lam, its, acc, first, last = None, 0, 0, None, None
+        for _ in range(int(max_iters[n_levels - 1 - li])):
+            r = lm_iteration(lw, poses, lam, lib=lib)
+            its += 1
+            first = r["cost"] if first is None else first
+            lam = r["lam"]
+            poses = r["poses"]
+            last = r["new_cost"] if r["accepted"] else r["cost"]
+            if r["accepted"]:
+                acc += 1
+                if (r["cost"] - r["new_cost"]) < rel_tol * r["cost"]:
+                    break
+        log.append(dict(level=li, iterations=its, accepted=acc, cost_first=first, cost_last=last))
+    return dict(poses=poses, log=log)

@@ -89,9 +89,9 @@ class Problem:
 
     # -------------------------------------------------------------- lifecycle
     def close(self):
-        if self._h:
+        if self._h and not getattr(self, "_owner", None):
             self._lib.pba_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -171,6 +171,39 @@ class Problem:
         self._check(self._lib.pba_get_channels(self._h, int(first), int(count),
                                                arr.ctypes.data_as(ctypes.c_void_p), 0), "get_channels")
         return arr
+
+    # -------------------------------------------------------------- pyramid (Sec. IV-A, IV-C)
+    def build_pyramid(self, n_levels: int = 3):
+        """Levels 1..n_levels-1, each half the resolution of the previous one,
+        downsampled on the device from the uploaded frames."""
+        self._check(self._lib.pba_build_pyramid(self._h, int(n_levels)), "build_pyramid")
+        self._n_levels = int(n_levels)
+
+    def level(self, level: int) -> "Problem":
+        """The problem of one pyramid level (borrowed from this one; level 0 is self)."""
+        if level == 0:
+            return self
+        h = ctypes.c_void_p()
+        self._check(self._lib.pba_pyramid_level(self._h, int(level), ctypes.byref(h)), "pyramid_level")
+        q = Problem.__new__(Problem)
+        q._lib, q._h, q._owner = self._lib, h, self
+        q.n_frames, q._fs = self.n_frames, self._fs
+        q._sizes = list(self._sizes)
+        for _ in range(int(level)):
+            q._sizes = [(hh // 2, ww // 2) for hh, ww in q._sizes]
+        q.path, q.texel, q.solver = self.path, self.texel, self.solver
+        q.n_pairs = getattr(self, "n_pairs", 0)
+        return q
+
+    def optimize(self, max_iters=(10, 5, 2), rel_tol: float = 1e-4):
+        """Coarse-to-fine Levenberg-Marquardt over the first len(max_iters)
+        levels (max_iters coarsest first); returns one dict per level."""
+        n = len(max_iters)
+        its = (ctypes.c_int32 * n)(*[int(x) for x in max_iters])
+        st = (_lib.PbaLevelStats * n)()
+        self._check(self._lib.pba_optimize(self._h, n, its, float(rel_tol), st), "optimize")
+        return [dict(level=s.level, iterations=s.iterations, accepted=s.accepted, status=s.status,
+                     cost_first=s.cost_first, cost_last=s.cost_last) for s in st]
 
     def frame_points(self, frame: int) -> int:
         n = ctypes.c_int32()

@@ -42,7 +42,9 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
-           "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels"]
+           "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels",
+           "pba_build_pyramid", "pba_pyramid_level", "pba_optimize"]
+PBA_MAX_LEVELS = 8
 PBA_NORMALS_MAX_RADIUS = 32
 PBA_N_PHASES = 5
 PHASE_NAMES = ["solve", "update", "linearize", "reduce_assemble", "accept"]
@@ -68,6 +70,11 @@ class PbaIterStats(ctypes.Structure):
     _fields_ = [("cost", ctypes.c_double), ("new_cost", ctypes.c_double), ("lambda_used", ctypes.c_double),
                 ("lambda_next", ctypes.c_double), ("n_valid", ctypes.c_int64), ("accepted", ctypes.c_int32),
                 ("status", ctypes.c_int32)]
+
+
+class PbaLevelStats(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("iterations", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("cost_first", ctypes.c_double), ("cost_last", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -119,6 +126,9 @@ def load(build_if_missing: bool = True):
             "pba_set_extrinsic": ([vp, ctypes.c_int, vp], ctypes.c_int),
             "pba_estimate_normals": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int], ctypes.c_int),
             "pba_get_channels": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+            "pba_build_pyramid": ([vp, ctypes.c_int], ctypes.c_int),
+            "pba_pyramid_level": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
+            "pba_optimize": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_double, P(PbaLevelStats)], ctypes.c_int),
             "pba_cost_gradient": ([vp, P(d), P(i64), vp, vp, vp], ctypes.c_int),
             "pba_linearize_pairs_noalloc": ([P(PbaSensor), P(PbaConfig), vp, ctypes.c_int, vp, vp, ctypes.c_int, vp,
                                              vp], ctypes.c_int),

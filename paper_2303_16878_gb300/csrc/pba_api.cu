@@ -99,6 +99,10 @@ struct pba_problem {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int launches_last = 0;
+
+    // coarser pyramid levels 1.. (Sec. IV-A), each a problem of its own on the same stream
+    std::vector<pba_problem*> levels;
+    bool pyramid_stale = true;
 };
 
 namespace {
@@ -477,6 +481,8 @@ void pba_destroy(pba_problem* p) {
     if (!p) return;
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (pba_problem* q : p->levels) pba_destroy(q);
+    p->levels.clear();
     drop_graph(p);
     free_pair_buffers(p);
     dfree(p->raw);
@@ -537,6 +543,7 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
     CUDA_TRY(p, cudaMemcpyAsync(p->raw + 5 * p->px_off[first], channels, bytes,
                                 is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
     for (int k = first; k < first + count; ++k) p->uploaded[k] = 1;
+    p->pyramid_stale = true;
     return repack(p, first, count, 0.f, 0);
 }
 
@@ -553,6 +560,7 @@ int pba_estimate_normals(pba_problem* p, int first, int count, float scale, int 
         if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "estimate_normals: frame not uploaded");
     }
     cudaSetDevice(p->device);
+    p->pyramid_stale = true;
     return repack(p, first, count, scale, max_radius);
 }
 
@@ -614,6 +622,7 @@ int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // host vectors above are pageable
     p->linearized = false;
     p->mask_valid = false;
+    p->pyramid_stale = true;
     return PBA_OK;
 }
 
@@ -659,6 +668,7 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     int st = ensure_points(p);
     if (st) return st;
     drop_graph(p);
+    p->pyramid_stale = true;
     free_pair_buffers(p);
     p->pairs.assign(pairs, pairs + 2 * (size_t)m);
     p->M = m;
@@ -1098,6 +1108,144 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     p->linearized = false;
     if (variant_full) *variant_full = p->variant_full;
     if (variant_cost) *variant_cost = p->variant_cost;
+    return PBA_OK;
+}
+
+int pba_build_pyramid(pba_problem* p, int n_levels) {
+    if (!p) return PBA_EINVAL;
+    if (n_levels < 1 || n_levels > PBA_MAX_LEVELS) return fail(p, PBA_EINVAL, "build_pyramid: n_levels outside [1, 8]");
+    for (int k = 0; k < p->N; ++k)
+        if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "build_pyramid: frame not uploaded");
+    cudaSetDevice(p->device);
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    for (pba_problem* q : p->levels) pba_destroy(q);
+    p->levels.clear();
+    p->pyramid_stale = true;
+    pba_problem* prev = p;
+    for (int l = 1; l < n_levels; ++l) {
+        // intrinsics of the half-resolution level: coarse pixel k is centred on
+        // fine coordinate 2k + 1/2, so f' = f / 2 and c' = (c + 1/2) / 2 - 1/2
+        std::vector<pba_sensor> cs = prev->sensors;
+        for (pba_sensor& S : cs) {
+            S.width /= 2;
+            S.height /= 2;
+            S.fx /= 2.0;
+            S.fy /= 2.0;
+            S.cx = (S.cx + 0.5) / 2.0 - 0.5;
+            S.cy = (S.cy + 0.5) / 2.0 - 0.5;
+            if (S.width < 4 || S.height < 4) {
+                for (pba_problem* q : p->levels) pba_destroy(q);
+                p->levels.clear();
+                return fail(p, PBA_EINVAL, "build_pyramid: a level would be smaller than 4 x 4 pixels");
+            }
+        }
+        pba_config cfg = prev->cfg;
+        cfg.n_sensors = (int)cs.size();
+        cfg.sensors = cs.data();
+        cfg.frame_sensor = prev->frame_sensor.data();
+        pba_problem* q = nullptr;
+        int st = pba_create(&cfg, prev->stream, &q);
+        if (st) {
+            for (pba_problem* r : p->levels) pba_destroy(r);
+            p->levels.clear();
+            return fail(p, st, "build_pyramid: creating a level failed");
+        }
+        p->levels.push_back(q);
+        auto bail = [&](int code, const std::string& msg) {
+            for (pba_problem* r : p->levels) pba_destroy(r);
+            p->levels.clear();
+            return fail(p, code, msg);
+        };
+        float* tmp = nullptr;
+        long long* d_off = nullptr;
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 5 * (size_t)std::max(q->total_px, 1LL)) != cudaSuccess ||
+            cudaMalloc((void**)&d_off, sizeof(long long) * q->N) != cudaSuccess) {
+            cudaFree(tmp);
+            return bail(PBA_ENOMEM, "build_pyramid: out of device memory");
+        }
+        std::vector<int> ids(q->N);
+        int max_px = 0;
+        for (int k = 0; k < q->N; ++k) {
+            ids[k] = k;
+            const pba_sensor& S = cs[q->frame_sensor[k]];
+            max_px = std::max(max_px, S.width * S.height);
+        }
+        cudaError_t ce = cudaMemcpyAsync(prev->d_frame_ids, ids.data(), sizeof(int) * q->N, cudaMemcpyHostToDevice,
+                                         prev->stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(d_off, q->px_off.data(), sizeof(long long) * q->N, cudaMemcpyHostToDevice,
+                                 prev->stream);
+        if (ce == cudaSuccess)
+            ce = launch_downsample(prev->raw, prev->d_frames, prev->d_frame_ids, d_off, q->N, max_px, tmp,
+                                   prev->cfg.range_min, prev->cfg.range_max, prev->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(prev->stream);
+        // upload runs of consecutive frames of one image size
+        for (int k0 = 0; ce == cudaSuccess && k0 < q->N;) {
+            const pba_sensor& S0 = cs[q->frame_sensor[k0]];
+            int k1 = k0 + 1;
+            while (k1 < q->N && cs[q->frame_sensor[k1]].width == S0.width &&
+                   cs[q->frame_sensor[k1]].height == S0.height)
+                ++k1;
+            st = pba_upload_frames(q, k0, k1 - k0, tmp + 5 * q->px_off[k0], 1);
+            if (st) {
+                cudaFree(tmp);
+                cudaFree(d_off);
+                return bail(st, std::string("build_pyramid: ") + q->err);
+            }
+            k0 = k1;
+        }
+        cudaFree(tmp);
+        cudaFree(d_off);
+        if (ce != cudaSuccess) return bail(PBA_ECUDA, std::string("build_pyramid: ") + cudaGetErrorString(ce));
+        if (p->poses_set && (st = pba_set_poses(q, p->d_poses, 1))) return bail(st, "build_pyramid: poses");
+        if (p->M > 0 && (st = pba_set_pairs(q, p->pairs.data(), p->M))) return bail(st, "build_pyramid: pairs");
+        prev = q;
+    }
+    p->pyramid_stale = false;
+    return PBA_OK;
+}
+
+int pba_pyramid_level(pba_problem* p, int level, pba_problem** level_out) {
+    if (!p || !level_out) return PBA_EINVAL;
+    if (level < 0 || level > (int)p->levels.size()) return fail(p, PBA_EINVAL, "pyramid_level: no such level");
+    if (level > 0 && p->pyramid_stale)
+        return fail(p, PBA_ENOTREADY, "pyramid_level: frames, pairs or extrinsics changed since build_pyramid");
+    *level_out = level == 0 ? p : p->levels[level - 1];
+    return PBA_OK;
+}
+
+int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double rel_tol, pba_level_stats* stats) {
+    int st = ready(p);
+    if (st) return st;
+    if (!max_iters || n_levels < 1 || n_levels > (int)p->levels.size() + 1)
+        return fail(p, PBA_EINVAL, "optimize: n_levels exceeds the built pyramid, or max_iters is NULL");
+    if (n_levels > 1 && p->pyramid_stale)
+        return fail(p, PBA_ENOTREADY, "optimize: frames, pairs or extrinsics changed since build_pyramid");
+    for (int l = 0; l < n_levels; ++l)
+        if (max_iters[l] < 0) return fail(p, PBA_EINVAL, "optimize: negative iteration count");
+    for (int l = n_levels - 1; l >= 0; --l) {
+        pba_problem* q = l == 0 ? p : p->levels[l - 1];
+        if (q != p && (st = pba_set_poses(q, p->d_poses, 1))) return fail(p, st, "optimize: " + q->err);
+        if ((st = pba_set_lambda(q, -1.0))) return fail(p, st, "optimize: " + q->err);
+        pba_level_stats ls{};
+        ls.level = l;
+        ls.status = PBA_OK;
+        for (int it = 0; it < max_iters[n_levels - 1 - l]; ++it) {
+            pba_iter_stats s{};
+            if ((st = pba_iterate(q, &s))) return fail(p, st, "optimize: " + q->err);
+            if (it == 0) ls.cost_first = s.cost;
+            ++ls.iterations;
+            ls.cost_last = s.accepted ? s.new_cost : s.cost;
+            if (s.status) ls.status = s.status;
+            if (s.accepted) {
+                ++ls.accepted;
+                if (s.cost - s.new_cost < rel_tol * s.cost) break;  // error variation below the threshold
+            }
+        }
+        if (q != p && (st = pba_set_poses(p, q->d_poses, 1))) return fail(p, st, "optimize: poses");
+        if (stats) stats[n_levels - 1 - l] = ls;
+    }
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     return PBA_OK;
 }
 

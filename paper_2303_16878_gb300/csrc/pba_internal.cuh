@@ -120,6 +120,12 @@ struct AsmContrib {
 
 namespace pba {
 
+// One pyramid level down (Sec. IV-A): frames frame_ids[0..n) of raw into out at
+// out_offsets (coarse pixels), 2 x 2 blocks.
+cudaError_t launch_downsample(const float* raw, const FrameInfo* frames, const int* frame_ids,
+                              const long long* out_offsets, int n, int max_coarse_px, float* out, double range_min,
+                              double range_max, cudaStream_t s);
+
 // Normal estimation (Sec. IV-A), in place on the normal channels of raw.
 cudaError_t launch_normals(float* raw, const FrameInfo* frames, const int* frame_ids, int n, int max_px, float scale,
                            int max_radius, double range_min, double range_max, cudaStream_t s);

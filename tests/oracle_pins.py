@@ -38,6 +38,9 @@ PIN_TOL = {
     "normals_counts": 0.5,
     "normals_brute_force": 1e-8,
     "normals_degenerate": 0.5,
+    "pyramid_projection": 1e-9,
+    "downsample_closed_forms": 1e-12,
+    "coarse_to_fine": 0.5,
 }
 
 
@@ -516,6 +519,98 @@ def pin_normals_degenerate(O, lib=None):
     return float(n_bad)
 
 
+# ---------------------------------------------------------------- pyramid (Sec. IV-A) and coarse to fine (Sec. IV-C)
+
+def pin_pyramid_projection(O, lib=None):
+    """Coarse pixel k covers fine pixels 2k, 2k + 1 and is centred on fine
+    coordinate 2k + 1/2, so any point projects to u_c = (u_f + 1/2) / 2 - 1/2
+    (and v alike) at the next level, for both models.  Returns the largest
+    deviation in coarse pixels over seeded points."""
+    from paper_2303_16878_gb300 import synth
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for s in (synth.pinhole_sensor(160, 120, 120.0, 80.0, 60.0), synth.spherical_sensor(1024, 64, 16.6, -16.6)):
+        c = O.downsample_sensor(s)
+        if (c["width"], c["height"]) != (s.width // 2, s.height // 2):
+            return float("inf")
+        for _ in range(200):
+            p = rng.normal(size=3) * 3.0
+            p[2] = abs(p[2]) + 0.5 if s.model == 0 else p[2]
+            uf = O.project(s, p, lib=lib)
+            uc = O.project(c, p, lib=lib)
+            du = abs(uc[0] - ((uf[0] + 0.5) / 2 - 0.5))
+            if s.model == 1:  # the azimuth wraps with period W / 2 at the coarse level
+                du = min(du, abs(du - c["width"]))
+            worst = max(worst, du, abs(uc[1] - ((uf[1] + 0.5) / 2 - 0.5)))
+    return worst
+
+
+def pin_downsample_closed_forms(O, lib=None):
+    """Closed forms of the 2 x 2 summary: a constant image stays constant; an
+    affine intensity ramp g = a + b c + e r (dyadic, exact in float32) gives
+    the ramp at the block centre (2r + 1/2, 2c + 1/2); four normals placed
+    symmetrically about -z average to exactly -z; one invalid fine pixel
+    invalidates its block only; odd sizes drop the last row and column.
+    Returns the largest error (inf on a validity mismatch)."""
+    prm = dict(range_min=0.0, range_max=100.0)
+    H, W = 7, 9
+    x = np.zeros((H, W, 5), dtype=np.float32)
+    r, c = np.mgrid[0:H, 0:W]
+    x[..., 0] = 0.25 + 0.0625 * c + 0.03125 * r
+    x[..., 1] = 2.5
+    x[..., 4] = -1.0
+    y = O.downsample(x, prm)
+    if y.shape != (3, 4, 5):
+        return float("inf")
+    rc, cc = np.mgrid[0:3, 0:4]
+    err = float(np.abs(y[..., 0] - (0.25 + 0.0625 * (2 * cc + 0.5) + 0.03125 * (2 * rc + 0.5))).max())
+    err = max(err, float(np.abs(y[..., 1] - 2.5).max()), float(np.abs(y[..., 2:] - [0, 0, -1]).max()))
+    a = 0.6
+    b = math.sqrt(1 - a * a)
+    x[0:2, 0:2, 2:5] = np.array([[[a, 0, -b], [-a, 0, -b]], [[0, a, -b], [0, -a, -b]]], dtype=np.float32)
+    x[3, 5, 1] = 0.0  # block (1, 2) loses one pixel
+    y = O.downsample(x, prm)
+    err = max(err, float(np.abs(y[0, 0, 2:] - [0, 0, -1]).max()))
+    valid = y[..., 1] > 0
+    expect = np.ones((3, 4), dtype=bool)
+    expect[1, 2] = False
+    if not np.array_equal(valid, expect) or np.any(y[1, 2] != 0):
+        return float("inf")
+    return err
+
+
+def _pose_error(P, G):
+    """Largest translation [m] and rotation [rad] error of the poses relative
+    to frame 0 (the gauge) against ground truth."""
+    P = np.asarray(P).reshape(-1, 3, 4)
+    G = np.asarray(G).reshape(-1, 3, 4)
+
+    def h(X):
+        return np.vstack([X, [0, 0, 0, 1]])
+    et = er = 0.0
+    for k in range(1, len(P)):
+        D = np.linalg.inv(np.linalg.inv(h(G[0])) @ h(G[k])) @ (np.linalg.inv(h(P[0])) @ h(P[k]))
+        et = max(et, float(np.linalg.norm(D[:3, 3])))
+        er = max(er, float(np.arccos(np.clip((np.trace(D[:3, :3]) - 1) / 2, -1, 1))))
+    return et, er
+
+
+def pin_coarse_to_fine(O, lib=None):
+    """Brute-force convergence on a tiny problem: from 4.7 cm / 2.9 deg
+    initial errors, three levels of 10 / 5 / 2 iterations reach the ground
+    truth within 1 cm and 0.3 deg (the interpolation-limited optimum of
+    rendered images), and F never increases within a level.  Returns the
+    number of violated conditions."""
+    from paper_2303_16878_gb300 import synth
+    w = synth.make_rgbd_room(n_frames=4, width=160, height=120, f=120.0)
+    r = O.coarse_to_fine(w, w.poses_init, 3, [10, 5, 2], 1e-4, lib=lib)
+    et, er = _pose_error(r["poses"], w.poses_gt)
+    bad = int(et > 0.01) + int(er > math.radians(0.3))
+    bad += sum(int(lv["cost_last"] > lv["cost_first"]) for lv in r["log"])
+    bad += int([lv["level"] for lv in r["log"]] != [2, 1, 0])
+    return float(bad)
+
+
 def all_pins(O, lib, room, street):
     """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
     return {
@@ -537,4 +632,7 @@ def all_pins(O, lib, room, street):
         "normals_counts": pin_normals_counts(O, lib),
         "normals_brute_force": max(pin_normals_brute_force(O, lib, room), pin_normals_brute_force(O, lib, street)),
         "normals_degenerate": pin_normals_degenerate(O, lib),
+        "pyramid_projection": pin_pyramid_projection(O, lib),
+        "downsample_closed_forms": pin_downsample_closed_forms(O, lib),
+        "coarse_to_fine": pin_coarse_to_fine(O, lib),
     }

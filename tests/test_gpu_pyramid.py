@@ -1,0 +1,140 @@
+"""Pyramid (Sec. IV-A) and coarse-to-fine optimisation (Sec. IV-C) on the GPU
+against the FP64 oracle.
+
+Bars: downsampled images bit-exact (both sides sum four float32 values
+exactly in float64 and round once); coarse-level systems to the same bars as
+level 0 (relative Frobenius 1e-4 on H and b, 1e-5 on the cost); the
+coarse-to-fine result within 1e-4 m and 1e-5 rad of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import workload
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_problem(w, **kw):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2303_16878_gb300 as pba
+    return pba.problem_from_workload(w, **kw)
+
+
+@pytest.mark.parametrize("which", ["room3", "street3"])
+def test_levels_are_bit_exact(oracle_lib, which, request):
+    w = request.getfixturevalue(which)
+    p = gpu_problem(w)
+    p.build_pyramid(3)
+    ref = oracle_lib.pyramid(w, 3)
+    for lv in (1, 2):
+        q = p.level(lv)
+        got = q.get_channels(0, w.n_frames)
+        for k in range(w.n_frames):
+            assert np.array_equal(got[k], ref[lv][1][k]), f"level {lv} frame {k} differs"
+        n_ref = [int(oracle_lib.frame_points(ref[lv][0][0], w.params, ref[lv][1][k])[0].shape[0])
+                 for k in range(w.n_frames)]
+        assert [q.frame_points(k) for k in range(w.n_frames)] == n_ref
+
+
+@pytest.mark.parametrize("which", ["room8", "street3"])
+def test_coarse_level_system_matches_oracle(oracle_lib, which, request):
+    """H and b of the whole level to 1e-4; per pair, the valid masks agree on
+    every point outside the oracle's decision margin, and pairs whose masks
+    agree fully match the oracle's cost to 1e-5 and its count exactly (a
+    point decided the other way inside the margin changes its pair's cost by
+    that point's rho: such pairs are left out of the cost comparison).
+    FP32 texels: the coarse images are block means, not binary16 values, so
+    FP16 texels would round them (level 0 inputs are binary16-exact)."""
+    w = request.getfixturevalue(which)
+    p = gpu_problem(w, texel=0)
+    p.build_pyramid(3)
+    ref_levels = oracle_lib.pyramid(w, 3)
+    for lv in (1, 2):
+        sens, chans = ref_levels[lv]
+        ref = oracle_lib.linearize(sens, w.frame_sensor, chans, w.poses_init, w.pairs, w.params)
+        q = p.level(lv)
+        q.set_mask_export(True)
+        cost, count = q.linearize()
+        H, b = q.get_system()
+        assert rel(H, ref["H"]) <= 1e-4 and rel(b, ref["b"]) <= 1e-4
+        ps = q.get_pair_system()
+        total, disagree, compared = 0, 0, 0
+        for k, (i, j) in enumerate(w.pairs.tolist()):
+            s = sens[int(w.frame_sensor[i])]
+            r = oracle_lib.linearize_pair(s, w.params, chans[i], chans[j], w.poses_init[i], w.poses_init[j])
+            diff = q.get_mask(k, r["n_points"]) ^ r["mask"]
+            assert not np.any(diff & ~r["flags"]), f"level {lv} pair {k}: mask differs on unflagged points"
+            nd = int(sum(bin(int(x)).count("1") for x in diff))
+            disagree += nd
+            total += r["count"]
+            if nd == 0:
+                compared += 1
+                assert ps["count"][k] == r["count"]
+                assert abs(ps["cost"][k] - r["cost"]) <= 1e-5 * abs(r["cost"]) + 1e-12
+        assert disagree <= 1e-5 * total + 2
+        assert compared >= len(w.pairs) - 2
+        assert abs(count - ref["count"]) <= disagree
+
+
+def _pose_diff(A, B):
+    A = np.asarray(A).reshape(-1, 3, 4)
+    B = np.asarray(B).reshape(-1, 3, 4)
+    dt = float(np.abs(A[:, :, 3] - B[:, :, 3]).max())
+    dr = 0.0
+    for a, b in zip(A, B):
+        c = np.clip((np.trace(a[:, :3].T @ b[:, :3]) - 1) / 2, -1, 1)
+        dr = max(dr, float(np.arccos(c)))
+    return dt, dr
+
+
+@pytest.mark.parametrize("solver,texel", [(0, 0), (1, 1)])
+def test_coarse_to_fine_matches_oracle(oracle_lib, solver, texel):
+    """Final poses within 1e-4 m / 1e-5 rad of the oracle's; with FP32 texels
+    the first cost of the coarsest level (same initial poses) also to 1e-5.
+    The levels' accept / reject sequences may differ where a step's decrease
+    is within float32 rounding, so only the converged finest level is
+    compared."""
+    w = workload("room", n_frames=4, width=160, height=120, f=120.0)
+    iters = [10, 5, 10]
+    ref = oracle_lib.coarse_to_fine(w, w.poses_init, 3, iters, 1e-7)
+    p = gpu_problem(w, solver=solver, texel=texel)
+    p.build_pyramid(3)
+    log = p.optimize(iters, rel_tol=1e-7)
+    assert [lv["level"] for lv in log] == [2, 1, 0]
+    for lv in log:
+        assert lv["iterations"] <= iters[2 - lv["level"]] and lv["cost_last"] <= lv["cost_first"]
+    if texel == 0:
+        assert abs(log[0]["cost_first"] - ref["log"][0]["cost_first"]) <= 1e-5 * ref["log"][0]["cost_first"]
+    dt, dr = _pose_diff(p.get_poses(), ref["poses"])
+    assert dt <= 1e-4 and dr <= 1e-5, (dt, dr)
+
+
+def test_stale_pyramid_and_bad_arguments(room3):
+    import paper_2303_16878_gb300 as pba
+    p = gpu_problem(room3)
+    with pytest.raises(pba.PbaError):
+        p.build_pyramid(0)
+    with pytest.raises(pba.PbaError):
+        p.build_pyramid(pba._lib.PBA_MAX_LEVELS + 1)
+    with pytest.raises(pba.PbaError):
+        p.build_pyramid(6)  # 160 x 120 -> ... -> 5 x 3 is below 4 x 4
+    p.build_pyramid(2)
+    with pytest.raises(pba.PbaError):
+        p.optimize([3, 3, 3])  # three levels requested, two built
+    p.set_pairs(room3.pairs)
+    with pytest.raises(pba.PbaError) as e:
+        p.optimize([2, 2])
+    assert e.value.code == pba._lib.PBA_ENOTREADY
+    log = p.optimize([2])  # the finest level alone needs no pyramid
+    assert len(log) == 1 and log[0]["level"] == 0
+    p.build_pyramid(2)
+    assert len(p.optimize([2, 1])) == 2

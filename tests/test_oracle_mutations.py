@@ -112,3 +112,40 @@ def test_planted_normal_mistake_is_caught(name, oracle_lib, room3, street3):
             failed.append(pin)
             break
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+PYRAMID_MUTATIONS = {
+    "principal_point_halved": ("cx=(float(g(\"cx\")) + 0.5) / 2.0 - 0.5", "cx=float(g(\"cx\")) / 2.0"),
+    "block_sum_not_averaged": ("out[..., 0] = s[..., 0] * 0.25", "out[..., 0] = s[..., 0] * 0.5"),
+    "depth_sum_not_averaged": ("out[..., 1] = s[..., 1] * 0.25", "out[..., 1] = s[..., 1] * 0.3"),
+    "normals_not_normalised": ("out[..., 2 + k] = s[..., 2 + k] / np.where(norm > 0, norm, 1.0)",
+                               "out[..., 2 + k] = s[..., 2 + k] * 0.25"),
+    "any_valid_instead_of_all": ("vb = valid.reshape(H, 2, W, 2).all(axis=(1, 3))",
+                                 "vb = valid.reshape(H, 2, W, 2).any(axis=(1, 3))"),
+    "fine_to_coarse_order": ("for li in range(n_levels - 1, -1, -1):", "for li in range(n_levels):"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PYRAMID_MUTATIONS))
+def test_planted_pyramid_mistake_is_caught(name, oracle_lib):
+    import types
+    before, after = PYRAMID_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle_mutated")
+    mod.__file__ = PY_SRC
+    exec(compile(src.replace(before, after), PY_SRC, "exec"), mod.__dict__)
+    lib = oracle_lib.load()
+    failed = []
+    for pin, fn in [("pyramid_projection", lambda: P.pin_pyramid_projection(mod, lib)),
+                    ("downsample_closed_forms", lambda: P.pin_downsample_closed_forms(mod, lib)),
+                    ("coarse_to_fine", lambda: P.pin_coarse_to_fine(mod, lib))]:
+        try:
+            err = fn()
+        except Exception:
+            failed.append(pin)
+            break
+        if not err < P.PIN_TOL[pin]:
+            failed.append(pin)
+            break
+    assert failed, f"no pin caught the planted mistake {name}"

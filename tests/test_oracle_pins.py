@@ -166,3 +166,15 @@ def test_normals_match_brute_force_plane_fit(oracle_lib, which, request):
 
 def test_no_normal_where_the_plane_is_undetermined(oracle_lib):
     assert P.pin_normals_degenerate(oracle_lib, oracle_lib.load()) < P.PIN_TOL["normals_degenerate"]
+
+
+def test_coarse_level_projection_is_the_halved_pixel_grid(oracle_lib):
+    assert P.pin_pyramid_projection(oracle_lib, oracle_lib.load()) < P.PIN_TOL["pyramid_projection"]
+
+
+def test_downsample_closed_forms(oracle_lib):
+    assert P.pin_downsample_closed_forms(oracle_lib, oracle_lib.load()) < P.PIN_TOL["downsample_closed_forms"]
+
+
+def test_coarse_to_fine_converges_on_a_tiny_room(oracle_lib):
+    assert P.pin_coarse_to_fine(oracle_lib, oracle_lib.load()) < P.PIN_TOL["coarse_to_fine"]
