@@ -274,6 +274,23 @@ int pba_iterate_async(pba_problem* p, int n);
 /* Synchronise and read the outcome of the last iteration. */
 int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
 
+/* Pose variables of the damped solve.  By default frame 0 is held fixed (the
+ * gauge) and every other frame k moves with its own variable.  frame_var
+ * (n_frames entries, host memory) instead maps frame k to variable
+ * frame_var[k] in [0, n_vars), or to -1 to hold it fixed: frames sharing a
+ * variable move together, e.g. the frames of several sensors rigidly mounted
+ * on one platform and captured at one platform pose (the coupled multi-sensor
+ * problem of Sec. V, fusion), or a fixed frame per independent sub-problem.
+ * The step solves (S^T H S + lambda I) dx_v = -S^T b, S the 0/1 selection
+ * (frame k's perturbation is dx_v[frame_var[k]]), and applies dx_v to every
+ * frame of each variable; the initial lambda is 1e-4 max diag(S^T H S).
+ * Frames tied to one variable should carry equal poses (their common
+ * perturbation keeps them equal).  frame_var = NULL restores the default.
+ * pba_get_system still returns the per-frame H and b.  Errors: PBA_EINVAL
+ * (n_vars outside [1, n_frames - 1], an entry outside [-1, n_vars), no frame
+ * held fixed, a variable without frames), PBA_ENOMEM, PBA_ECUDA. */
+int pba_set_variables(pba_problem* p, const int32_t* frame_var, int n_vars);
+
 /* ---- Pyramid and coarse-to-fine optimisation (Sec. IV-A, Sec. IV-C) ----
  *
  * Level 0 is the problem itself; level l + 1 halves the resolution of level

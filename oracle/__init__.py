@@ -280,14 +280,56 @@ def initial_lambda(H) -> float:
     return 1e-4 * float(d.max()) if d.size else 0.0
 
 
+def selection(frame_var, n_vars: int) -> np.ndarray:
+    """S (6N x 6 n_vars) with S[6k + a, 6 v + a] = 1 when frame k's pose moves
+    with variable v (frame_var[k] = v); rows of frames with frame_var[k] = -1
+    (held fixed) are zero.  The pose perturbations are dx_frames = S dx_vars."""
+    fv = np.asarray(frame_var, dtype=np.int64)
+    S = np.zeros((6 * fv.size, 6 * n_vars))
+    for k, v in enumerate(fv):
+        if v >= 0:
+            S[6 * k:6 * k + 6, 6 * v:6 * v + 6] = np.eye(6)
+    return S
+
+
+def solve_step_vars(H, b, lam: float, frame_var, n_vars: int, lib=None):
+    """Damped Gauss-Newton step when frames share pose variables or are held
+    fixed: F(X [+] S dx_v) has gradient S^T b and Gauss-Newton matrix S^T H S,
+    so dx_v = -(S^T H S + lam I)^-1 S^T b (the oracle's Cholesky) and the
+    frames move by S dx_v.  Returns (dx_frames (6N), ok)."""
+    S = selection(frame_var, n_vars)
+    Hr = S.T @ np.asarray(H, dtype=np.float64) @ S
+    br = S.T @ np.asarray(b, dtype=np.float64)
+    try:
+        x = cholesky_solve(Hr + lam * np.eye(Hr.shape[0]), -br, lib=lib)
+    except np.linalg.LinAlgError:
+        return np.zeros(S.shape[0]), False
+    return S @ x, True
+
+
+def initial_lambda_vars(H, frame_var, n_vars: int) -> float:
+    """lambda_0 = 1e-4 * max diag(S^T H S)."""
+    S = selection(frame_var, n_vars)
+    d = np.diag(S.T @ np.asarray(H, dtype=np.float64) @ S)
+    return 1e-4 * float(d.max()) if d.size else 0.0
+
+
 def lm_iteration(w, poses, lam: Optional[float], lib=None) -> Dict:
     """One Levenberg-Marquardt iteration on workload-like `w` (sensors,
-    frame_sensor, channels, pairs, params) at `poses`.  lam=None takes
-    initial_lambda.  Returns the accepted poses, the new lambda, both costs."""
+    frame_sensor, channels, pairs, params; optionally frame_var / n_vars, the
+    pose variables of the frames, else frame 0 fixed and every other frame
+    free) at `poses`.  lam=None takes the initial damping.  Returns the
+    accepted poses, the new lambda, both costs."""
     lin = linearize(w.sensors, w.frame_sensor, w.channels, poses, w.pairs, w.params, lib=lib)
-    if lam is None:
-        lam = initial_lambda(lin["H"])
-    dx, ok = solve_step(lin["H"], lin["b"], lam, lib=lib)
+    fv = getattr(w, "frame_var", None)
+    if fv is not None:
+        if lam is None:
+            lam = initial_lambda_vars(lin["H"], fv, w.n_vars)
+        dx, ok = solve_step_vars(lin["H"], lin["b"], lam, fv, w.n_vars, lib=lib)
+    else:
+        if lam is None:
+            lam = initial_lambda(lin["H"])
+        dx, ok = solve_step(lin["H"], lin["b"], lam, lib=lib)
     cand = apply_update(poses, dx, lib=lib)
     new = linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False, lib=lib)
     accepted = ok and new["cost"] < lin["cost"]
@@ -467,6 +509,7 @@ class _Level:
     def __init__(self, w, sensors, channels):
         self.sensors, self.channels = sensors, channels
         self.frame_sensor, self.pairs, self.params = w.frame_sensor, w.pairs, w.params
+        self.frame_var, self.n_vars = getattr(w, "frame_var", None), getattr(w, "n_vars", 0)
 
 
 def coarse_to_fine(w, poses, n_levels: int, max_iters: Sequence[int], rel_tol: float, lib=None) -> Dict:

@@ -172,6 +172,18 @@ class Problem:
                                                arr.ctypes.data_as(ctypes.c_void_p), 0), "get_channels")
         return arr
 
+    def set_variables(self, frame_var=None, n_vars: int = 0):
+        """Pose variables of the solve: frame k moves with variable frame_var[k]
+        (-1: held fixed); None restores frame 0 fixed, every other frame free."""
+        if frame_var is None:
+            self._check(self._lib.pba_set_variables(self._h, None, 0), "set_variables")
+            return
+        fv = np.ascontiguousarray(frame_var, dtype=np.int32).reshape(-1)
+        if fv.size != self.n_frames:
+            raise ValueError(f"frame_var needs {self.n_frames} entries, got {fv.size}")
+        self._check(self._lib.pba_set_variables(self._h, fv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                int(n_vars)), "set_variables")
+
     # -------------------------------------------------------------- pyramid (Sec. IV-A, IV-C)
     def build_pyramid(self, n_levels: int = 3):
         """Levels 1..n_levels-1, each half the resolution of the previous one,
@@ -346,4 +358,6 @@ def problem_from_workload(w, path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXE
         k = j + 1
     p.set_poses(w.poses_init if poses is None else poses)
     p.set_pairs(w.pairs)
+    if getattr(w, "frame_var", None) is not None:
+        p.set_variables(w.frame_var, w.n_vars)
     return p

@@ -100,6 +100,16 @@ struct pba_problem {
     cudaGraphExec_t graph_exec = nullptr;
     int launches_last = 0;
 
+    // pose variables (pba_set_variables); n_vars < 0: frame 0 fixed, frame k -> variable k - 1
+    int n_vars = -1;
+    std::vector<int32_t> frame_var;
+    int* d_frame_var = nullptr;
+    int* d_var_start = nullptr;
+    int* d_var_frames = nullptr;
+    double* d_Hr = nullptr;
+    double* d_br = nullptr;
+    int n_pad_vars = 0;
+
     // coarser pyramid levels 1.. (Sec. IV-A), each a problem of its own on the same stream
     std::vector<pba_problem*> levels;
     bool pyramid_stale = true;
@@ -211,19 +221,34 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                  bool speculative = false) {
     // timing events (speculative timed iteration only): [1] after the solve, [5] after the accept
     if (!speculative) ev = nullptr;
-    CUDA_TRY(p, launch_lm_prepare(p->d_H, p->N, p->d_state, lambda, s));
+    // the system in pose variables: H itself by default (the solve drops frame 0),
+    // else S^T H S with a leading fixed dummy block
+    const double* Hs = p->d_H;
+    const double* bs = p->d_b;
+    int nf = p->N, npad = p->n_pad;
+    if (p->n_vars >= 0) {
+        CUDA_TRY(p, launch_reduce_vars(p->d_H, p->d_b, p->N, p->d_var_start, p->d_var_frames, p->n_vars, p->d_Hr,
+                                       p->d_br, s));
+        ++*nl;
+        Hs = p->d_Hr;
+        bs = p->d_br;
+        nf = p->n_vars + 1;
+        npad = p->n_pad_vars;
+    }
+    CUDA_TRY(p, launch_lm_prepare(Hs, nf, p->d_state, lambda, s));
     int nc = 0;
     if (p->cfg.solver == PBA_SOLVE_MIXED) {
-        CUDA_TRY(p, launch_solve_mixed(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->mixed, 3, p->d_rhs, s, &nc));
+        CUDA_TRY(p, launch_solve_mixed(Hs, bs, nf, npad, p->d_state, p->mixed, 3, p->d_rhs, s, &nc));
         *nl += 1 + nc;
     } else {
-        CUDA_TRY(p, launch_damp(p->d_H, p->d_b, p->N, p->n_pad, p->d_state, p->d_A, p->d_rhs, s));
-        CUDA_TRY(p, launch_cholesky(p->d_A, p->d_Dinv, p->n_pad, p->d_state, s, &nc));
-        CUDA_TRY(p, launch_trsv(p->d_A, p->d_Dinv, p->n_pad, p->d_rhs, p->d_state, s));
+        CUDA_TRY(p, launch_damp(Hs, bs, nf, npad, p->d_state, p->d_A, p->d_rhs, s));
+        CUDA_TRY(p, launch_cholesky(p->d_A, p->d_Dinv, npad, p->d_state, s, &nc));
+        CUDA_TRY(p, launch_trsv(p->d_A, p->d_Dinv, npad, p->d_rhs, p->d_state, s));
         *nl += 3 + nc;
     }
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[1], s));
-    CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->d_state, p->d_cand, s));
+    CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->n_vars >= 0 ? p->d_frame_var : nullptr, p->d_state,
+                               p->d_cand, s));
     ++*nl;
     if (speculative) {
         int st = enqueue_linearize(p, s, nl, ev, true);
@@ -484,6 +509,11 @@ void pba_destroy(pba_problem* p) {
     for (pba_problem* q : p->levels) pba_destroy(q);
     p->levels.clear();
     drop_graph(p);
+    dfree(p->d_frame_var);
+    dfree(p->d_var_start);
+    dfree(p->d_var_frames);
+    dfree(p->d_Hr);
+    dfree(p->d_br);
     free_pair_buffers(p);
     dfree(p->raw);
     dfree(p->tex);
@@ -1111,6 +1141,63 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     return PBA_OK;
 }
 
+int pba_set_variables(pba_problem* p, const int32_t* frame_var, int n_vars) {
+    if (!p) return PBA_EINVAL;
+    cudaSetDevice(p->device);
+    if (!frame_var) {  // back to the default: frame 0 fixed, every other frame free
+        drop_graph(p);
+        p->n_vars = -1;
+        p->frame_var.clear();
+        p->pyramid_stale = true;
+        return PBA_OK;
+    }
+    if (n_vars < 1 || n_vars > p->N - 1)
+        return fail(p, PBA_EINVAL, "set_variables: n_vars must lie in [1, n_frames - 1]");
+    std::vector<int> count(n_vars, 0);
+    int fixed = 0;
+    for (int k = 0; k < p->N; ++k) {
+        if (frame_var[k] < -1 || frame_var[k] >= n_vars)
+            return fail(p, PBA_EINVAL, "set_variables: frame_var entry outside [-1, n_vars)");
+        if (frame_var[k] < 0) ++fixed;
+        else ++count[frame_var[k]];
+    }
+    if (!fixed) return fail(p, PBA_EINVAL, "set_variables: no frame is held fixed (the gauge would be free)");
+    for (int v = 0; v < n_vars; ++v)
+        if (!count[v]) return fail(p, PBA_EINVAL, "set_variables: a variable moves no frame");
+    std::vector<int> start(n_vars + 1, 0), frames(p->N - fixed);
+    for (int v = 0; v < n_vars; ++v) start[v + 1] = start[v] + count[v];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int k = 0; k < p->N; ++k)
+        if (frame_var[k] >= 0) frames[fill[frame_var[k]]++] = k;
+    drop_graph(p);
+    dfree(p->d_frame_var);
+    dfree(p->d_var_start);
+    dfree(p->d_var_frames);
+    dfree(p->d_Hr);
+    dfree(p->d_br);
+    p->d_frame_var = p->d_var_start = p->d_var_frames = nullptr;
+    p->d_Hr = p->d_br = nullptr;
+    p->n_vars = -1;
+    const size_t nr = 6 * (size_t)(n_vars + 1);
+    if (cudaMalloc((void**)&p->d_frame_var, sizeof(int) * p->N) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_var_start, sizeof(int) * (n_vars + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_var_frames, sizeof(int) * std::max<size_t>(frames.size(), 1)) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_Hr, sizeof(double) * nr * nr) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_br, sizeof(double) * nr) != cudaSuccess)
+        return fail(p, PBA_ENOMEM, "set_variables: out of device memory");
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_var, frame_var, sizeof(int) * p->N, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_var_start, start.data(), sizeof(int) * (n_vars + 1), cudaMemcpyHostToDevice,
+                                p->stream));
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_var_frames, frames.data(), sizeof(int) * frames.size(), cudaMemcpyHostToDevice,
+                                p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // the host vectors are pageable
+    p->frame_var.assign(frame_var, frame_var + p->N);
+    p->n_vars = n_vars;
+    p->n_pad_vars = ((6 * n_vars + kTile - 1) / kTile) * kTile;
+    p->pyramid_stale = true;
+    return PBA_OK;
+}
+
 int pba_build_pyramid(pba_problem* p, int n_levels) {
     if (!p) return PBA_EINVAL;
     if (n_levels < 1 || n_levels > PBA_MAX_LEVELS) return fail(p, PBA_EINVAL, "build_pyramid: n_levels outside [1, 8]");
@@ -1199,6 +1286,8 @@ int pba_build_pyramid(pba_problem* p, int n_levels) {
         if (ce != cudaSuccess) return bail(PBA_ECUDA, std::string("build_pyramid: ") + cudaGetErrorString(ce));
         if (p->poses_set && (st = pba_set_poses(q, p->d_poses, 1))) return bail(st, "build_pyramid: poses");
         if (p->M > 0 && (st = pba_set_pairs(q, p->pairs.data(), p->M))) return bail(st, "build_pyramid: pairs");
+        if (p->n_vars >= 0 && (st = pba_set_variables(q, p->frame_var.data(), p->n_vars)))
+            return bail(st, "build_pyramid: variables");
         prev = q;
     }
     p->pyramid_stale = false;

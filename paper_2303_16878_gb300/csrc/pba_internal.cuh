@@ -190,8 +190,11 @@ struct MixedWork {
 cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, int n_pad, LmState* st,
                                MixedWork& w, int refinements, double* dx, cudaStream_t s, int* n_launches);
 
-cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const LmState* st,
-                           double* cand, cudaStream_t s);
+cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const int* frame_var,
+                           const LmState* st, double* cand, cudaStream_t s);
+// Hr = S^T H S, br = S^T b in pose variables (leading fixed dummy block).
+cudaError_t launch_reduce_vars(const double* H, const double* b, int n_frames, const int* var_start,
+                               const int* var_frames, int n_vars, double* Hr, double* br, cudaStream_t s);
 
 // Keep the candidate when the cost decreased.  speculative: the candidate was
 // linearised in full, so on acceptance its system (H_cand, b_cand, blocks_cand,

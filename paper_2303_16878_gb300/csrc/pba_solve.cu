@@ -1,3 +1,4 @@
+#include <algorithm>
 // pba_solve.cu -- FP64 assembly, damped gauge-fixed Cholesky solve, box-plus
 // update and the Levenberg-Marquardt accept / reject, all on the device.
 //
@@ -404,17 +405,57 @@ __global__ void k_refine_finish(LmState* st, const double* __restrict__ dscale, 
 
 // ------------------------------------------------------------------ update
 // cand_k = X_k [+] dx_k (dx_0 = 0); on a failed factorisation cand = poses.
+// Gauss-Newton system in pose variables when frames share variables or are
+// held fixed: Hr = S^T H S, br = S^T b, S the 0/1 selection of 6 x 6 identity
+// blocks (frame f moves with variable v).  Hr gets a leading 6 x 6 zero block
+// (a fixed dummy variable) so that the gauge-fixed solve, which drops the
+// first block, applies unchanged.  Both triangles sum the same terms in the
+// same order (outer loop over the lower index's frames), so Hr is exactly
+// symmetric like H.
+__global__ void k_reduce_vars(const double* __restrict__ H, const double* __restrict__ b, int n_frames,
+                              const int* __restrict__ var_start, const int* __restrict__ var_frames, int n_vars,
+                              double* __restrict__ Hr, double* __restrict__ br) {
+    const long long n6 = 6LL * n_frames;
+    const int nr = 6 * (n_vars + 1);
+    const long long total = (long long)nr * nr;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / nr), j = (int)(idx % nr);
+        double v = 0.0;
+        if (i >= 6 && j >= 6) {
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            const int va = (lo - 6) / 6, x = (lo - 6) % 6, vb = (hi - 6) / 6, y = (hi - 6) % 6;
+            for (int fa = var_start[va]; fa < var_start[va + 1]; ++fa) {
+                const long long row = 6LL * var_frames[fa] + x;
+                for (int gb = var_start[vb]; gb < var_start[vb + 1]; ++gb)
+                    v += H[row * n6 + 6LL * var_frames[gb] + y];
+            }
+        }
+        Hr[idx] = v;
+        if (j == 0) {
+            double s = 0.0;
+            if (i >= 6) {
+                const int va = (i - 6) / 6, x = (i - 6) % 6;
+                for (int fa = var_start[va]; fa < var_start[va + 1]; ++fa) s += b[6LL * var_frames[fa] + x];
+            }
+            br[i] = s;
+        }
+    }
+}
+
 __global__ void k_boxplus(const double* __restrict__ poses, const double* __restrict__ dx_ff, int n_frames,
-                          const LmState* st, double* __restrict__ cand) {
+                          const int* __restrict__ frame_var, const LmState* st, double* __restrict__ cand) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_frames) return;
     const double* X = poses + 12 * k;
     double* out = cand + 12 * k;
-    if (k == 0 || st->chol_fail) {
+    // pose variable of frame k: frame 0 fixed and frame k -> k - 1 by default; -1 = held fixed
+    const int v = frame_var ? frame_var[k] : k - 1;
+    if (v < 0 || st->chol_fail) {
         for (int e = 0; e < 12; ++e) out[e] = X[e];
         return;
     }
-    const double* dx = dx_ff + 6 * (k - 1);
+    const double* dx = dx_ff + 6 * v;
     double qx = dx[3], qy = dx[4], qz = dx[5];
     const double n2 = qx * qx + qy * qy + qz * qz;
     double qw;
@@ -560,9 +601,17 @@ cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const LmState* st, double* cand,
-                           cudaStream_t s) {
-    k_boxplus<<<(n_frames + 127) / 128, 128, 0, s>>>(poses, dx_ff, n_frames, st, cand);
+cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const int* frame_var,
+                           const LmState* st, double* cand, cudaStream_t s) {
+    k_boxplus<<<(n_frames + 127) / 128, 128, 0, s>>>(poses, dx_ff, n_frames, frame_var, st, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_vars(const double* H, const double* b, int n_frames, const int* var_start,
+                               const int* var_frames, int n_vars, double* Hr, double* br, cudaStream_t s) {
+    const long long nr = 6LL * (n_vars + 1);
+    const int blocks = (int)std::min<long long>((nr * nr + 255) / 256, 4096);
+    k_reduce_vars<<<blocks, 256, 0, s>>>(H, b, n_frames, var_start, var_frames, n_vars, Hr, br);
     return cudaGetLastError();
 }
 

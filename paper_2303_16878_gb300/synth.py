@@ -327,6 +327,8 @@ class Workload:
     poses_init: np.ndarray       # (N, 3, 4) float64
     pairs: np.ndarray            # (M, 2) int32, directed (source i, target j)
     params: Dict                 # method configuration (weights, Huber delta, thresholds)
+    frame_var: Optional[np.ndarray] = None  # pose variable per frame (-1 fixed); None: frame 0 fixed
+    n_vars: int = 0
 
     @property
     def n_frames(self) -> int:
@@ -585,3 +587,70 @@ def make_plane_shift(width: int = 48, height: int = 40, f: float = 40.0, depth: 
     chans = [quantize_fp16(render(scene, sensor, poses[k], 0.1, 100.0)) for k in range(2)]
     return Workload("plane-shift", [sensor], np.zeros(2, dtype=np.int32), chans, poses,
                     poses.copy(), np.array([[0, 1]], dtype=np.int32), default_params())
+
+
+def rot_z(a: float) -> np.ndarray:
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def rot_y(a: float) -> np.ndarray:
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+# camera axes (x right, y down, z forward) in the platform frame (x forward, y left, z up)
+CAMERA_ON_PLATFORM = np.array([[0.0, 0.0, 1.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0]])
+
+
+def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 120, f: float = 120.0,
+                     lidar_width: int = 512, lidar_height: int = 32, vfov_up_deg: float = 16.6,
+                     vfov_down_deg: float = -16.6, cam_offset=(0.10, 0.0, 0.10), seed: int = 7,
+                     sigma_t: float = 0.02, sigma_r_deg: float = 1.0, coupled: bool = True,
+                     params: Optional[Dict] = None) -> Workload:
+    """A platform carrying an RGB-D camera and a 3D LiDAR (Sec. V, fusion) in
+    the textured room of make_rgbd_room.
+
+    Platform frame: x forward, y left, z up.  The LiDAR sits at the platform
+    origin (identity offset); the camera `cam_offset` from it, looking along
+    the platform x axis.  Platform poses: n_poses points near the room centre
+    at 1.2-1.3 m height, heading towards the +y wall +- 15 deg.  Frames 0..n-1
+    are the camera's, n..2n-1 the LiDAR's; frames k and n + k were captured at
+    platform pose k.  Pairs: camera (i, j), j - i <= 3; LiDAR (n + i, n + j)
+    for all i < j.  With `coupled`, frame_var ties frames k and n + k to one
+    variable and holds platform pose 0 fixed.  Seeds: scene 1000 + seed,
+    trajectory 2000 + seed, perturbation 3000 + seed (the same perturbation
+    for the two frames of a platform pose)."""
+    scene = _room_scene(1000 + seed)
+    cam = pinhole_sensor(cam_width, cam_height, f, cam_width / 2.0, cam_height / 2.0)
+    Xc = np.zeros((3, 4))
+    Xc[:, :3] = CAMERA_ON_PLATFORM
+    Xc[:, 3] = cam_offset
+    cam.extrinsic = Xc
+    lidar = spherical_sensor(lidar_width, lidar_height, vfov_up_deg, vfov_down_deg)
+    rng = np.random.default_rng(2000 + seed)
+    plat = np.zeros((n_poses, 3, 4))
+    for k in range(n_poses):
+        th = 2 * math.pi * k / max(n_poses, 1)
+        yaw = math.pi / 2 + rng.uniform(-0.26, 0.26)
+        plat[k, :, :3] = rot_z(yaw) @ rot_y(rng.uniform(-0.05, 0.05))
+        plat[k, :, 3] = [0.4 * math.cos(th), 0.4 * math.sin(th) - 0.3, 1.2 + rng.uniform(0.0, 0.1)]
+    chans = []
+    for k in range(n_poses):
+        chans.append(quantize_fp16(render(scene, cam, compose(plat[k], Xc), 0.5, 5.0)))
+    for k in range(n_poses):
+        chans.append(quantize_fp16(render(scene, lidar, plat[k], 0.5, 8.0)))
+    init_plat = perturb_poses(plat, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    poses = np.concatenate([plat, plat])
+    init = np.concatenate([init_plat, init_plat])
+    pairs = [(i, j) for i in range(n_poses) for j in range(i + 1, n_poses) if j - i <= 3]
+    pairs += [(n_poses + i, n_poses + j) for i in range(n_poses) for j in range(i + 1, n_poses)]
+    prm = default_params(range_min=0.5, range_max=8.0)
+    if params:
+        prm.update(params)
+    fv = None
+    if coupled:
+        fv = np.array([k - 1 for k in range(n_poses)] * 2, dtype=np.int32)
+    return Workload(f"fusion-room-{n_poses}", [cam, lidar],
+                    np.array([0] * n_poses + [1] * n_poses, dtype=np.int32), chans, poses, init,
+                    np.array(pairs, dtype=np.int32).reshape(-1, 2), prm, fv, n_poses - 1 if coupled else 0)

@@ -23,7 +23,7 @@ def workload(name, **kw):
     key = (name, tuple(sorted(kw.items())))
     if key not in _CACHE:
         fn = {"room": synth.make_rgbd_room, "street": synth.make_lidar_street,
-              "plane": synth.make_plane_shift}[name]
+              "plane": synth.make_plane_shift, "fusion": synth.make_fusion_room}[name]
         _CACHE[key] = fn(**kw)
     return _CACHE[key]
 
@@ -55,3 +55,9 @@ def room8x(room8):
 @pytest.fixture(scope="session")
 def street3():
     return workload("street", n_frames=3, width=256, height=32)
+
+
+@pytest.fixture(scope="session")
+def fusion():
+    """RGB-D camera + LiDAR on one platform in the room, 4 platform poses, coupled."""
+    return workload("fusion")

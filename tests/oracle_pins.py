@@ -41,6 +41,8 @@ PIN_TOL = {
     "pyramid_projection": 1e-9,
     "downsample_closed_forms": 1e-12,
     "coarse_to_fine": 0.5,
+    "tied_gradient": 1e-4,  # central differences of F ~ 900 at h = 2e-8: roundoff eps F / h ~ 1e-5 absolute
+    "variables_reduce_to_gauge": 1e-12,
 }
 
 
@@ -609,6 +611,65 @@ def pin_coarse_to_fine(O, lib=None):
     bad += sum(int(lv["cost_last"] > lv["cost_first"]) for lv in r["log"])
     bad += int([lv["level"] for lv in r["log"]] != [2, 1, 0])
     return float(bad)
+
+
+# ---------------------------------------------------------------- pose variables (frames sharing a pose)
+
+def pin_tied_gradient(O, lib, w):
+    """Frames of several sensors captured at one platform pose move together
+    (w.frame_var): the derivative of F under the common perturbation
+    X_f [+] dx for every frame f of variable v (central differences) equals
+    2 (S^T b)_v.  Returns the largest relative deviation."""
+    params = dict(w.params, grad_mode=1)
+    r = O.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, params, lib=lib)
+    S = O.selection(w.frame_var, w.n_vars)
+    br = S.T @ r["b"]
+    worst = 0.0
+    for v in range(w.n_vars):
+        frames = [k for k in range(w.n_frames) if w.frame_var[k] == v]
+        for a in range(6):
+            done = False
+            for h in (2e-8, 1e-8, 5e-9):
+                Fs, masks = [], []
+                for sg in (1, -1):
+                    d = np.zeros(6)
+                    d[a] = sg * h
+                    poses = w.poses_init.copy()
+                    for k in frames:
+                        poses[k] = O.boxplus(poses[k], d, lib=lib)
+                    F, mk = 0.0, []
+                    for (i, j) in w.pairs.tolist():
+                        if i not in frames and j not in frames:
+                            continue
+                        s = w.sensors[int(w.frame_sensor[i])]
+                        pr = O.linearize_pair(s, params, w.channels[i], w.channels[j], poses[i], poses[j], lib=lib)
+                        F += pr["cost"]
+                        mk.append(pr["mask"])
+                    Fs.append(F)
+                    masks.append(mk)
+                if all(np.array_equal(x, y) for x, y in zip(masks[0], masks[1])):
+                    g = (Fs[0] - Fs[1]) / (2 * h)
+                    worst = max(worst, abs(g - 2 * br[6 * v + a]) / (np.abs(2 * br[6 * v:6 * v + 6]).max() + 1e-30))
+                    done = True
+                    break
+            assert done, "mask changed under every finite-difference step"
+    return worst
+
+
+def pin_variables_reduce_to_gauge(O, lib, w):
+    """With frame_var = (-1, 0, 1, ..., N - 2) the variable-space step is the
+    gauge-fixed step (frame 0 removed from H, Sec. IV-C).  Returns the
+    largest difference of the two dx."""
+    r = O.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params, lib=lib)
+    lam = O.initial_lambda(r["H"])
+    fv = np.arange(-1, w.n_frames - 1)
+    if abs(O.initial_lambda_vars(r["H"], fv, w.n_frames - 1) - lam) > 1e-15 * lam:
+        return float("inf")
+    a, ok_a = O.solve_step(r["H"], r["b"], lam, lib=lib)
+    b, ok_b = O.solve_step_vars(r["H"], r["b"], lam, fv, w.n_frames - 1, lib=lib)
+    if not (ok_a and ok_b):
+        return float("inf")
+    return float(np.abs(a - b).max() / np.abs(a).max())
 
 
 def all_pins(O, lib, room, street):

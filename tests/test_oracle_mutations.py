@@ -149,3 +149,35 @@ def test_planted_pyramid_mistake_is_caught(name, oracle_lib):
             failed.append(pin)
             break
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+VARIABLE_MUTATIONS = {
+    "first_variable_dropped": ("        if v >= 0:\n            S[6 * k", "        if v > 0:\n            S[6 * k"),
+    "reduced_gradient_halved": ("    br = S.T @ np.asarray(b, dtype=np.float64)\n", "    br = 0.5 * S.T @ np.asarray(b, dtype=np.float64)\n"),
+    "reduced_matrix_not_projected": ("    Hr = S.T @ np.asarray(H, dtype=np.float64) @ S\n    br",
+                                     "    Hr = S.T @ np.asarray(H, dtype=np.float64) @ S * 2.0\n    br"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(VARIABLE_MUTATIONS))
+def test_planted_variable_mistake_is_caught(name, oracle_lib, room3, fusion):
+    import types
+    before, after = VARIABLE_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle_mutated")
+    mod.__file__ = PY_SRC
+    exec(compile(src.replace(before, after), PY_SRC, "exec"), mod.__dict__)
+    lib = oracle_lib.load()
+    failed = []
+    for pin, fn in [("variables_reduce_to_gauge", lambda: P.pin_variables_reduce_to_gauge(mod, lib, room3)),
+                    ("tied_gradient", lambda: P.pin_tied_gradient(mod, lib, fusion))]:
+        try:
+            err = fn()
+        except Exception:
+            failed.append(pin)
+            break
+        if not err < P.PIN_TOL[pin]:
+            failed.append(pin)
+            break
+    assert failed, f"no pin caught the planted mistake {name}"

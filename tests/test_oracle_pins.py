@@ -178,3 +178,11 @@ def test_downsample_closed_forms(oracle_lib):
 
 def test_coarse_to_fine_converges_on_a_tiny_room(oracle_lib):
     assert P.pin_coarse_to_fine(oracle_lib, oracle_lib.load()) < P.PIN_TOL["coarse_to_fine"]
+
+
+def test_tied_frames_gradient_matches_finite_differences(oracle_lib, fusion):
+    assert P.pin_tied_gradient(oracle_lib, oracle_lib.load(), fusion) < P.PIN_TOL["tied_gradient"]
+
+
+def test_default_variables_reduce_to_the_gauge_fixed_step(oracle_lib, room3):
+    assert P.pin_variables_reduce_to_gauge(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["variables_reduce_to_gauge"]
