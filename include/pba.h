@@ -342,12 +342,23 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
 /* Number of kernel launches one pba_iterate performs (for accounting). */
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
+/* Occupancy variants of the batched linearisation kernel: register budgets
+ * for 2, 3 or 4 (full pass) and 3, 4 or 5 (cost-only pass) blocks of 256
+ * threads per SM, variants 0, 1, 2.  The results agree up to float32
+ * summation order. */
+#define PBA_N_VARIANTS 3
+
 /* Pick, by timing them on this problem, the fastest occupancy variant of the
  * batched linearisation kernel for the full pass and for the cost-only pass
  * (each launched repeats + 1 times, the first as warm-up); later iterations
- * use the choice.  Reports the choice (0 or 1) in the optional outputs.
- * Needs frames, poses and pairs; synchronises.  A no-op on the plain path. */
+ * use the choice.  Reports the choice (0 .. PBA_N_VARIANTS - 1) in the
+ * optional outputs.  Needs frames, poses and pairs; synchronises.  A no-op on
+ * the plain path. */
 int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost);
+
+/* Set the variants explicitly (e.g. to reproduce a tuned configuration).
+ * Errors: PBA_EINVAL (a variant outside [0, PBA_N_VARIANTS)). */
+int pba_set_variants(pba_problem* p, int variant_full, int variant_cost);
 
 /* Instrumentation: one iteration like pba_iterate, enqueued launch by launch
  * (not as a graph) with CUDA events recorded on the problem's stream between

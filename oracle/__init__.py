@@ -39,7 +39,7 @@ class OParams(ctypes.Structure):
                 ("huber_delta", ctypes.c_double), ("occ_abs", ctypes.c_double), ("occ_rel", ctypes.c_double),
                 ("z_min", ctypes.c_double), ("range_min", ctypes.c_double), ("range_max", ctypes.c_double),
                 ("margin_px", ctypes.c_double), ("margin_rel", ctypes.c_double),
-                ("grad_mode", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("grad_mode", ctypes.c_int), ("other_branch", ctypes.c_int)]
 
 
 def build(force: bool = False, src: Optional[str] = None, out: Optional[str] = None) -> str:
@@ -132,6 +132,7 @@ def _params(p: Dict, margin_px: float = 1e-3, margin_rel: float = 1e-4) -> OPara
     o.margin_px = float(p.get("margin_px", margin_px))
     o.margin_rel = float(p.get("margin_rel", margin_rel))
     o.grad_mode = int(p.get("grad_mode", 0))
+    o.other_branch = int(p.get("other_branch", 0))
     return o
 
 
@@ -178,8 +179,14 @@ def frame_points(sensor, params: Dict, channels: np.ndarray, lib=None):
     return out[:n].copy(), pix[:n].copy()
 
 
-def point_residual(sensor, params: Dict, tgt_channels: np.ndarray, Xi, Xj, pt, lib=None) -> Dict:
+def point_residual(sensor, params: Dict, tgt_channels: np.ndarray, Xi, Xj, pt, lib=None,
+                   other_branch: bool = False) -> Dict:
+    """One pixel-point's residual, Jacobians, rho, weight and margin flag.
+    other_branch: overrule rejections whose decision lies within its margin
+    (the contribution a float32 implementation may count)."""
     lib = lib or _load()
+    if other_branch:
+        params = dict(params, other_branch=1)
     tgt = np.ascontiguousarray(tgt_channels, dtype=np.float32)
     Xi, Xj, pt = _f64(Xi).reshape(12), _f64(Xj).reshape(12), _f64(pt).reshape(7)
     e, Ji, Jj = np.zeros(5), np.zeros(30), np.zeros(30)
@@ -190,6 +197,18 @@ def point_residual(sensor, params: Dict, tgt_channels: np.ndarray, Xi, Xj, pt, l
                               _ptr(Jj, ctypes.c_double), ctypes.byref(rho), ctypes.byref(w), ctypes.byref(flag))
     return dict(valid=bool(ok), e=e, Ji=Ji.reshape(5, 6), Jj=Jj.reshape(5, 6), rho=rho.value, w=w.value,
                 flag=bool(flag.value))
+
+
+def point_contribution(sensor, params: Dict, tgt_channels: np.ndarray, Xi, Xj, pt, lib=None,
+                       other_branch: bool = False):
+    """(H12, b12, rho) of one pixel-point, w J^T Omega J and w J^T Omega e with
+    J = [J_i J_j] (the terms o_linearize_pair sums), or None when rejected."""
+    r = point_residual(sensor, params, tgt_channels, Xi, Xj, pt, lib=lib, other_branch=other_branch)
+    if not r["valid"]:
+        return None
+    J = np.hstack([r["Ji"], r["Jj"]])
+    om = np.array([params["w_int"], params["w_depth"]] + [params["w_normal"]] * 3)
+    return r["w"] * (J.T * om) @ J, r["w"] * (J.T * om) @ r["e"], r["rho"]
 
 
 def linearize_pair(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, Xj, lib=None) -> Dict:

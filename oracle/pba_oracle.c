@@ -57,7 +57,18 @@
  * Decision margins: the oracle flags a point when a validity decision lies
  * within `margin_px` pixels (projections against integers) or `margin_rel`
  * (relative, depth and norm tests) of its threshold, because a float32
- * implementation may take the other branch there.
+ * implementation may take the other branch there.  A sample position off by
+ * up to margin_px moves an interpolated value by its bilinear slope times
+ * margin_px, so the occlusion and normal-norm tests, which compare
+ * interpolated values, widen their margins by that amount (large at depth or
+ * normal discontinuities).
+ *
+ * With other_branch set, o_point_residual takes the other branch of every
+ * rejection whose decision lies within its margin (z_min, occlusion, normal
+ * norm; a sample that is not usable at u' is taken at u' moved by 2
+ * margin_px towards the neighbouring cell), so that a test can evaluate the
+ * contribution of a point that a float32 implementation counted and the
+ * oracle did not.
  */
 #include <math.h>
 #include <stdint.h>
@@ -83,7 +94,7 @@ typedef struct {
     double range_min, range_max;     /* R6 */
     double margin_px, margin_rel;    /* decision margins */
     int grad_mode;                   /* R5 */
-    int pad_;
+    int other_branch;                /* 1: a rejection whose decision lies within its margin is overruled */
 } o_params;
 
 /* ---------------------------------------------------------------- algebra */
@@ -277,7 +288,7 @@ static double near_int_dist(double x) {
  * usability test, may differ in another precision).
  */
 static int sample(const o_sensor* s, const o_params* prm, const float* ch, double u, double v,
-                  double val[5], double gu[5], double gv[5], int* flag) {
+                  double val[5], double gu[5], double gv[5], double slope[5], int* flag) {
     if (!(v >= 1.0 && v < (double)(s->height - 2))) {
         if (near_int_dist(v) < prm->margin_px) *flag = 1;
         return 0;
@@ -314,12 +325,16 @@ static int sample(const o_sensor* s, const o_params* prm, const float* ch, doubl
             }
         }
     }
-    if (prm->grad_mode == 1) {
-        for (int ci = 0; ci < 5; ++ci) {
-            double I00 = texel(s, ch, r0, c0)[ci], I01 = texel(s, ch, r0, c0 + 1)[ci];
-            double I10 = texel(s, ch, r0 + 1, c0)[ci], I11 = texel(s, ch, r0 + 1, c0 + 1)[ci];
-            gu[ci] = (1 - b) * (I01 - I00) + b * (I11 - I10);
-            gv[ci] = (1 - a) * (I10 - I00) + a * (I11 - I01);
+    for (int ci = 0; ci < 5; ++ci) {
+        /* slopes of the bilinear interpolant in u and v: |d val / du| + |d val / dv| */
+        double I00 = texel(s, ch, r0, c0)[ci], I01 = texel(s, ch, r0, c0 + 1)[ci];
+        double I10 = texel(s, ch, r0 + 1, c0)[ci], I11 = texel(s, ch, r0 + 1, c0 + 1)[ci];
+        double su = (1 - b) * (I01 - I00) + b * (I11 - I10);
+        double sv = (1 - a) * (I10 - I00) + a * (I11 - I01);
+        slope[ci] = fabs(su) + fabs(sv);
+        if (prm->grad_mode == 1) {
+            gu[ci] = su;
+            gv[ci] = sv;
         }
     }
     return 1;
@@ -363,16 +378,25 @@ int o_point_residual(const o_sensor* s, const o_params* prm, const float* tgt,
     } else {
         zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1] + pb[2] * pb[2]);
     }
-    if (fabs(zd - prm->z_min) < prm->margin_rel * (1.0 + fabs(zd))) *flag = 1;
-    if (!(zd > prm->z_min)) return 0;
+    int near_zmin = fabs(zd - prm->z_min) < prm->margin_rel * (1.0 + fabs(zd));
+    if (near_zmin) *flag = 1;
+    if (!(zd > prm->z_min) && !(prm->other_branch && near_zmin && zd > 0.0)) return 0;
 
     /* u' = pi(pbar)  (Eq. uprime) and the sample of I_j at u' */
     double uv[2];
     o_project(s, pb, uv);
-    double Iv[5], Igu[5], Igv[5];
+    double Iv[5], Igu[5], Igv[5], Islope[5];
     int sflag = 0;
-    int ok = sample(s, prm, tgt, uv[0], uv[1], Iv, Igu, Igv, &sflag);
+    int ok = sample(s, prm, tgt, uv[0], uv[1], Iv, Igu, Igv, Islope, &sflag);
     if (sflag) *flag = 1;
+    if (!ok && prm->other_branch && sflag) {
+        const double m2 = 2.0 * prm->margin_px;
+        const double du[8] = {-m2, m2, 0.0, 0.0, -m2, -m2, m2, m2}, dv[8] = {0.0, 0.0, -m2, m2, -m2, m2, -m2, m2};
+        for (int t = 0; t < 8 && !ok; ++t) {
+            int f2 = 0;
+            ok = sample(s, prm, tgt, uv[0] + du[t], uv[1] + dv[t], Iv, Igu, Igv, Islope, &f2);
+        }
+    }
     if (!ok) return 0;
 
     /* normal cue: nbar = R_o^T R_j^T R_i n_u^o  (Eq. normal-error-jacobian) */
@@ -384,11 +408,13 @@ int o_point_residual(const o_sensor* s, const o_params* prm, const float* tgt,
     /* occlusion suppression (R7) */
     double thr = prm->occ_abs + prm->occ_rel * zd;
     double dd = fabs(zd - Iv[1]);
-    if (fabs(dd - thr) < prm->margin_rel * (1.0 + fabs(zd))) *flag = 1;
-    if (dd > thr) return 0;
+    int near_occ = fabs(dd - thr) < prm->margin_rel * (1.0 + fabs(zd)) + prm->margin_px * Islope[1];
+    if (near_occ) *flag = 1;
+    if (dd > thr && !(prm->other_branch && near_occ)) return 0;
     double nt = sqrt(Iv[2] * Iv[2] + Iv[3] * Iv[3] + Iv[4] * Iv[4]);
-    if (fabs(nt - 0.5) < prm->margin_rel) *flag = 1;
-    if (nt < 0.5) return 0;
+    int near_nt = fabs(nt - 0.5) < prm->margin_rel + prm->margin_px * (Islope[2] + Islope[3] + Islope[4]);
+    if (near_nt) *flag = 1;
+    if (nt < 0.5 && !(prm->other_branch && near_nt)) return 0;
 
     /* e = zeta(pbar) - I_j(u')  (Supp., Eq. error-jacobian) */
     e[0] = gu_src - Iv[0];

@@ -334,6 +334,10 @@ class Problem:
         self._check(self._lib.pba_autotune(self._h, int(repeats), ctypes.byref(a), ctypes.byref(b)), "autotune")
         return a.value, b.value
 
+    def set_variants(self, variant_full: int, variant_cost: int):
+        """Occupancy variants of the linearisation kernel (0 .. PBA_N_VARIANTS - 1)."""
+        self._check(self._lib.pba_set_variants(self._h, int(variant_full), int(variant_cost)), "set_variants")
+
     def iteration_launches(self) -> int:
         n = ctypes.c_int32()
         self._check(self._lib.pba_iteration_launches(self._h, ctypes.byref(n)), "iteration_launches")
@@ -354,7 +358,13 @@ def problem_from_workload(w, path: int = PBA_PATH_BATCHED, texel: int = PBA_TEXE
         j = k
         while j + 1 < w.n_frames and w.channels[j + 1].shape == w.channels[k].shape:
             j += 1
-        p.upload_frames(k, np.stack(w.channels[k:j + 1]))
+        if _is_torch(w.channels[k]):  # device tensors (the large generators): upload from the device
+            import torch
+            block = torch.stack(w.channels[k:j + 1]).contiguous()
+            torch.cuda.synchronize()  # the library copies on its own stream
+            p.upload_frames(k, block)
+        else:
+            p.upload_frames(k, np.stack(w.channels[k:j + 1]))
         k = j + 1
     p.set_poses(w.poses_init if poses is None else poses)
     p.set_pairs(w.pairs)

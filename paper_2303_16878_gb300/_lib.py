@@ -43,7 +43,9 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
            "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels",
-           "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables"]
+           "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
+           "pba_set_variants"]
+PBA_N_VARIANTS = 3
 PBA_MAX_LEVELS = 8
 PBA_NORMALS_MAX_RADIUS = 32
 PBA_N_PHASES = 5
@@ -128,6 +130,7 @@ def load(build_if_missing: bool = True):
             "pba_get_channels": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
             "pba_build_pyramid": ([vp, ctypes.c_int], ctypes.c_int),
             "pba_set_variables": ([vp, P(ctypes.c_int32), ctypes.c_int], ctypes.c_int),
+            "pba_set_variants": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "pba_pyramid_level": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
             "pba_optimize": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_double, P(PbaLevelStats)], ctypes.c_int),
             "pba_cost_gradient": ([vp, P(d), P(i64), vp, vp, vp], ctypes.c_int),

@@ -1107,7 +1107,7 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     int best[2] = {0, 0};
     for (int full = 1; full >= 0; --full) {
         float best_ms = 3.4e38f;
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < PBA_N_VARIANTS; ++v) {
             const int grid = linearize_grid(p->cfg.texel_precision, full != 0, v);
             float total = 0.f;
             for (int r = 0; r <= repeats; ++r) {  // r = 0 is a warm-up
@@ -1335,6 +1335,19 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
         if (stats) stats[n_levels - 1 - l] = ls;
     }
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return PBA_OK;
+}
+
+int pba_set_variants(pba_problem* p, int variant_full, int variant_cost) {
+    if (!p) return PBA_EINVAL;
+    if (variant_full < 0 || variant_full >= PBA_N_VARIANTS || variant_cost < 0 || variant_cost >= PBA_N_VARIANTS)
+        return fail(p, PBA_EINVAL, "set_variants: variant outside [0, PBA_N_VARIANTS)");
+    cudaSetDevice(p->device);
+    p->variant_full = variant_full;
+    p->variant_cost = variant_cost;
+    p->grid_full = linearize_grid(p->cfg.texel_precision, true, variant_full);
+    p->grid_cost = linearize_grid(p->cfg.texel_precision, false, variant_cost);
+    drop_graph(p);
     return PBA_OK;
 }
 

@@ -495,10 +495,15 @@ static void* lin_kernel() {
 }
 
 // Occupancy variants (blocks of 256 threads per SM the register budget aims
-// at): full pass 2 or 3, cost-only pass 3 or 4.  variant 0 = the lower one.
+// at): full pass 2, 3 or 4, cost-only pass 3, 4 or 5 for variants 0, 1, 2.
+// Fewer registers per thread trade spills for warps to hide gather latency.
 template <int TEXEL, bool FULL, bool MASK>
 static void* pick_minb(int variant) {
-    if (FULL) return variant ? lin_kernel<TEXEL, FULL, MASK, 3>() : lin_kernel<TEXEL, FULL, MASK, 2>();
+    if (FULL) {
+        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 4>();
+        return variant ? lin_kernel<TEXEL, FULL, MASK, 3>() : lin_kernel<TEXEL, FULL, MASK, 2>();
+    }
+    if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 5>();
     return variant ? lin_kernel<TEXEL, FULL, MASK, 4>() : lin_kernel<TEXEL, FULL, MASK, 3>();
 }
 

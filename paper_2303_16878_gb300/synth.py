@@ -654,3 +654,382 @@ def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 1
     return Workload(f"fusion-room-{n_poses}", [cam, lidar],
                     np.array([0] * n_poses + [1] * n_poses, dtype=np.int32), chans, poses, init,
                     np.array(pairs, dtype=np.int32).reshape(-1, 2), prm, fv, n_poses - 1 if coupled else 0)
+
+
+# --------------------------------------------------------------------------
+# the same renderer on torch tensors (CPU or CUDA), for the large workloads
+# --------------------------------------------------------------------------
+
+def _mulmod32_t(a, c: int):
+    """(a * c) mod 2^32 for int64 tensors 0 <= a < 2^32 without overflowing int64."""
+    lo = a & 0xFFFF
+    hi = a >> 16
+    return ((lo * c) + (((hi * c) & 0xFFFF) << 16)) & 0xFFFFFFFF
+
+
+def _hash2_t(i, j, seed: int):
+    """_hash2 on int64 tensors, bit for bit."""
+    m = 0xFFFFFFFF
+    x = _mulmod32_t(i & m, 0x8DA6B343)
+    x = x ^ _mulmod32_t(j & m, 0xD8163841)
+    x = x ^ ((seed * 0xCB1AB31F) & m)
+    x = _mulmod32_t(x ^ (x >> 16), 0x7FEB352D)
+    x = _mulmod32_t(x ^ (x >> 15), 0x846CA68B)
+    x = x ^ (x >> 16)
+    return x.double() / 4294967296.0
+
+
+def value_noise_t(s, t, seed, octaves: int = 4):
+    """value_noise on float64 tensors; `seed` an int or an int64 tensor of
+    per-element seeds (the same integer arithmetic, so the same values)."""
+    import torch
+    total = torch.zeros_like(s)
+    amp, freq, norm = 0.5, 1.0, 0.0
+    for o in range(octaves):
+        ss, tt = s * freq, t * freq
+        i0, j0 = torch.floor(ss), torch.floor(tt)
+        fs, ft = ss - i0, tt - j0
+        fs = fs * fs * (3 - 2 * fs)
+        ft = ft * ft * (3 - 2 * ft)
+        sd = seed * 7919 + o * 104729
+        ii, jj = i0.long(), j0.long()
+        h00 = _hash2_t(ii, jj, sd)
+        h10 = _hash2_t(ii + 1, jj, sd)
+        h01 = _hash2_t(ii, jj + 1, sd)
+        h11 = _hash2_t(ii + 1, jj + 1, sd)
+        v = (h00 * (1 - fs) + h10 * fs) * (1 - ft) + (h01 * (1 - fs) + h11 * fs) * ft
+        total = total + amp * v
+        norm += amp
+        amp *= 0.5
+        freq *= 2.0
+    return total / norm
+
+
+def _scene_tensors(scene: Scene, device):
+    import torch
+    lo = torch.as_tensor(np.array([b.lo for b in scene.boxes], dtype=np.float64), device=device)
+    hi = torch.as_tensor(np.array([b.hi for b in scene.boxes], dtype=np.float64), device=device)
+    inside = torch.as_tensor([b.inside for b in scene.boxes], device=device)
+    albedo = torch.as_tensor([b.albedo for b in scene.boxes], dtype=torch.float64, device=device)
+    freq = torch.as_tensor([b.tex_freq for b in scene.boxes], dtype=torch.float64, device=device)
+    seed = torch.as_tensor([b.tex_seed for b in scene.boxes], dtype=torch.int64, device=device)
+    contrast = torch.as_tensor([b.tex_contrast for b in scene.boxes], dtype=torch.float64, device=device)
+    return dict(lo=lo, hi=hi, inside=inside, albedo=albedo, freq=freq, seed=seed, contrast=contrast)
+
+
+def _cast_t(scene: Scene, origin: np.ndarray, dirs, d_max: float = math.inf, st=None):
+    """_cast on a (K, 3) float64 tensor of ray directions, all boxes at once
+    (the first box of the smallest hit distance wins, as in the loop of _cast;
+    boxes that _cast skips lie beyond d_max and change no valid pixel)."""
+    import torch
+    dev = dirs.device
+    st = st or _scene_tensors(scene, dev)
+    k = dirs.shape[0]
+    keep = [bi for bi, b in enumerate(scene.boxes)
+            if b.inside or np.linalg.norm(np.clip(origin, b.lo, b.hi) - origin) <= d_max * 1.01]
+    sel = torch.as_tensor(keep, dtype=torch.long, device=dev)
+    lo, hi, inside = st["lo"][sel], st["hi"][sel], st["inside"][sel]
+    o = torch.as_tensor(origin, dtype=torch.float64, device=dev)
+    inv = 1.0 / dirs                                   # (K, 3)
+    t1 = (lo[None, :, :] - o) * inv[:, None, :]        # (K, B, 3)
+    t2 = (hi[None, :, :] - o) * inv[:, None, :]
+    on_lo = (lo == o)[None, :, :]
+    on_hi = (hi == o)[None, :, :]
+    on = on_lo | on_hi                                 # the 0 * inf case on a slab plane
+    t1 = torch.where(on & torch.isnan(t1), torch.full_like(t1, -math.inf), t1)
+    t2 = torch.where(on & torch.isnan(t2), torch.full_like(t2, math.inf), t2)
+    tmin = torch.minimum(t1, t2)
+    tmax = torch.maximum(t1, t2)
+    t_exit = torch.minimum(torch.minimum(tmax[..., 0], tmax[..., 1]), tmax[..., 2])
+    t_near = torch.maximum(torch.maximum(tmin[..., 0], tmin[..., 1]), tmin[..., 2])
+    ax_in = torch.where(tmax[..., 0] == t_exit, 0, torch.where(tmax[..., 1] == t_exit, 1, 2))
+    ax_out = torch.where(tmin[..., 0] == t_near, 0, torch.where(tmin[..., 1] == t_near, 1, 2))
+    t_hit = torch.where(inside[None, :], t_exit, t_near)
+    axis = torch.where(inside[None, :], ax_in, ax_out)
+    ok = torch.where(inside[None, :], t_exit > 1e-9, (t_near <= t_exit) & (t_near > 1e-9))
+    t_hit = torch.where(ok, t_hit, torch.full_like(t_hit, math.inf))
+    best_t, arg = torch.min(t_hit, dim=1)              # first minimum: the lowest box index
+    hit = torch.isfinite(best_t)
+    best_axis = torch.gather(axis, 1, arg[:, None])[:, 0]
+    best_box = sel[arg]
+    rows_all = torch.arange(k, device=dev)
+    sign = -torch.sign(dirs[rows_all, best_axis])
+    normal = torch.zeros((k, 3), dtype=torch.float64, device=dev)
+    normal[rows_all, best_axis] = torch.where(hit, sign, torch.zeros_like(sign))
+    point = o[None, :] + torch.where(hit, best_t, torch.zeros_like(best_t))[:, None] * dirs
+    s_idx = torch.where(best_axis == 0, 1, 0)
+    t_idx = torch.where(best_axis == 2, 1, 2)
+    fq = st["freq"][best_box]
+    s = point[rows_all, s_idx] * fq
+    t = point[rows_all, t_idx] * fq
+    nz = value_noise_t(s, t, st["seed"][best_box] * 31 + best_axis)
+    inten = st["albedo"][best_box] * (1.0 - st["contrast"][best_box] + st["contrast"][best_box] * nz)
+    inten = torch.where(hit, inten, torch.zeros_like(inten))
+    if scene.lambertian:
+        dn = torch.linalg.norm(dirs, dim=1)
+        cosang = torch.abs(torch.sum(normal * dirs, dim=1)) / torch.clamp(dn, min=1e-30)
+        inten = inten * cosang
+    return best_t, normal, inten
+
+
+def render_t(scene: Scene, sensor: Sensor, sensor_pose: np.ndarray, d_min: float, d_max: float, device="cpu",
+             rays=None, st=None):
+    """render() on torch: a (H, W, 5) float32 tensor on `device`."""
+    import torch
+    if rays is None:
+        rays = torch.as_tensor(_pixel_rays(sensor)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    r = torch.as_tensor(sensor_pose[:, :3], dtype=torch.float64, device=device)
+    o = np.asarray(sensor_pose[:, 3], dtype=np.float64)
+    d_world = rays @ r.T
+    t, n_world, inten = _cast_t(scene, o, d_world, d_max, st)
+    valid = torch.isfinite(t) & (t >= d_min) & (t <= d_max)
+    n_sensor = n_world @ r
+    out = torch.zeros((sensor.height * sensor.width, 5), dtype=torch.float64, device=device)
+    zero = torch.zeros_like(t)
+    out[:, 0] = torch.where(valid, inten, zero)
+    out[:, 1] = torch.where(valid, t, zero)
+    out[:, 2:5] = torch.where(valid[:, None], n_sensor, torch.zeros_like(n_sensor))
+    return out.reshape(sensor.height, sensor.width, 5).float()
+
+
+def quantize_fp16_t(ch):
+    out = ch.clone()
+    for c in (0, 2, 3, 4):
+        out[..., c] = out[..., c].half().float()
+    return out
+
+
+def _hall_scene(seed: int) -> Scene:
+    """Multi-room indoor scene: a 20 x 12 x 3 m hall seen from inside, split
+    into four rooms by 0.12 m partition walls with 1.2 m doorways, plus
+    furniture boxes along the outer walls.  Every surface is textured."""
+    rng = np.random.default_rng(seed)
+
+    def tex():
+        return dict(albedo=float(rng.uniform(0.5, 1.0)), tex_freq=float(rng.uniform(2.0, 4.0)),
+                    tex_seed=int(rng.integers(1, 1 << 20)), tex_contrast=0.8)
+    boxes = [Box(np.array([-10.0, -6.0, 0.0]), np.array([10.0, 6.0, 3.0]), inside=True, **tex())]
+    th = 0.06
+
+    def wall_x(y, x0, x1):  # a partition along x at height 0..3
+        boxes.append(Box(np.array([x0, y - th, 0.0]), np.array([x1, y + th, 3.0]), **tex()))
+
+    def wall_y(x, y0, y1):
+        boxes.append(Box(np.array([x - th, y0, 0.0]), np.array([x + th, y1, 3.0]), **tex()))
+    # y = 0 partition with doorways at x in [-6.0, -4.8], [6.0, 7.2]
+    wall_x(0.0, -10.0, -6.0)
+    wall_x(0.0, -4.8, 6.0)
+    wall_x(0.0, 7.2, 10.0)
+    # x = -3 (south half) doorway y in [-3.5, -2.3]; x = 4 (north half) doorway y in [2.0, 3.2]
+    wall_y(-3.0, -6.0, -3.5)
+    wall_y(-3.0, -2.3, 0.0)
+    wall_y(4.0, 0.0, 2.0)
+    wall_y(4.0, 3.2, 6.0)
+    # furniture along the outer walls (the path stays at least 1.5 m away from them)
+    for _ in range(18):
+        side = int(rng.integers(0, 4))
+        w, d, h = rng.uniform(0.6, 1.8), rng.uniform(0.4, 0.8), rng.uniform(0.5, 2.0)
+        if side < 2:
+            x = rng.uniform(-9.5, 9.5 - w)
+            y0 = -6.0 if side == 0 else 6.0 - d
+            lo, hi = [x, y0, 0.0], [x + w, y0 + d, h]
+        else:
+            y = rng.uniform(-5.5, 5.5 - w)
+            x0 = -10.0 if side == 2 else 10.0 - d
+            lo, hi = [x0, y, 0.0], [x0 + d, y + w, h]
+        boxes.append(Box(np.array(lo), np.array(hi), **tex()))
+    return Scene(boxes)
+
+
+def _hall_path(n: int, seed: int, height: float = 1.4) -> np.ndarray:
+    """Platform poses (x forward, y left, z up) along a closed Catmull-Rom
+    spline through the hall's four rooms and its doorways, resampled to n
+    poses equally spaced in arc length; heading along the path with smooth
+    yaw (+-15 deg) and pitch (-8..+4 deg) wobble, height +- 0.1 m."""
+    rng = np.random.default_rng(seed)
+    way = np.array([[-7.0, -3.0], [-5.4, -1.2], [-5.4, 1.5], [-4.0, 3.2], [0.5, 3.5], [3.0, 2.6], [5.0, 2.6],
+                    [6.6, 1.5], [6.6, -1.3], [5.0, -3.0], [0.0, -3.2], [-2.0, -2.9], [-4.5, -2.9]])
+    way = way + rng.uniform(-0.15, 0.15, way.shape)
+    m = len(way)
+    dense = []
+    for i in range(m):
+        p0, p1, p2, p3 = way[(i - 1) % m], way[i], way[(i + 1) % m], way[(i + 2) % m]
+        for u in np.linspace(0.0, 1.0, 200, endpoint=False):
+            u2, u3 = u * u, u * u * u
+            dense.append(0.5 * ((2 * p1) + (-p0 + p2) * u + (2 * p0 - 5 * p1 + 4 * p2 - p3) * u2 +
+                                (-p0 + 3 * p1 - 3 * p2 + p3) * u3))
+    dense = np.array(dense)
+    seg = np.linalg.norm(np.diff(np.vstack([dense, dense[:1]]), axis=0), axis=1)
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    targets = np.linspace(0.0, s[-1], n, endpoint=False)
+    loop = np.vstack([dense, dense[:1]])
+    xy = np.stack([np.interp(targets, s, loop[:, 0]), np.interp(targets, s, loop[:, 1])], axis=1)
+    tang = np.roll(xy, -1, axis=0) - np.roll(xy, 1, axis=0)
+    ph = rng.uniform(0, 2 * math.pi, 3)
+    poses = np.zeros((n, 3, 4))
+    for k in range(n):
+        a = 2 * math.pi * k / n
+        yaw = math.atan2(tang[k, 1], tang[k, 0]) + math.radians(15.0) * math.sin(3 * a + ph[0])
+        pitch = math.radians(-2.0 + 6.0 * math.sin(5 * a + ph[1]))
+        poses[k, :, :3] = rot_z(yaw) @ rot_y(-pitch)
+        poses[k, :, 3] = [xy[k, 0], xy[k, 1], height + 0.1 * math.sin(4 * a + ph[2])]
+    return poses
+
+
+def _pose_angle_deg(A: np.ndarray, B: np.ndarray) -> float:
+    c = (np.trace(A[:, :3].T @ B[:, :3]) - 1.0) / 2.0
+    return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+
+
+def overlap_ratios_t(src, tgts, sensor: Sensor, pose_src: np.ndarray, poses_tgt: np.ndarray, rays,
+                     rel_tol: float = 0.05, stride: int = 7) -> np.ndarray:
+    """overlap_ratio of frame src against each of the frames tgts (a list of
+    (H, W, 5) tensors on src's device; poses_tgt (C, 3, 4)), on torch, all
+    candidates at once; rays: the sensor's (H * W, 3) float64 pixel rays."""
+    import torch
+    dev = src.device
+    C = len(tgts)
+    if C == 0:
+        return np.zeros(0)
+    d = src[..., 1].reshape(-1).double()
+    idx = torch.arange(0, d.numel(), stride, device=dev)
+    dv = d[idx]
+    keep = dv > 0
+    n = int(keep.sum())
+    if n == 0:
+        return np.zeros(C)
+    pts = rays[idx][keep] * dv[keep][:, None]
+    Rs = torch.as_tensor(pose_src[:, :3], dtype=torch.float64, device=dev)
+    ts = torch.as_tensor(pose_src[:, 3], dtype=torch.float64, device=dev)
+    pw = pts @ Rs.T + ts                                                  # (P, 3)
+    Rt = torch.as_tensor(np.asarray(poses_tgt)[:, :, :3], dtype=torch.float64, device=dev)   # (C, 3, 3)
+    tt = torch.as_tensor(np.asarray(poses_tgt)[:, :, 3], dtype=torch.float64, device=dev)    # (C, 3)
+    pt = torch.einsum("cpi,cij->cpj", pw[None, :, :] - tt[:, None, :], Rt)                   # (C, P, 3)
+    if sensor.model == PINHOLE:
+        z = pt[..., 2]
+        ok = z > 1e-3
+        zz = torch.where(ok, z, torch.ones_like(z))
+        col = torch.round(sensor.fx * pt[..., 0] / zz + sensor.cx)
+        row = torch.round(sensor.fy * pt[..., 1] / zz + sensor.cy)
+        dist = z
+    else:
+        rxy = torch.hypot(pt[..., 0], pt[..., 1])
+        col = torch.remainder(torch.round(sensor.fx * torch.atan2(pt[..., 1], pt[..., 0]) + sensor.cx), sensor.width)
+        row = torch.round(sensor.fy * torch.atan2(pt[..., 2], rxy) + sensor.cy)
+        dist = torch.linalg.norm(pt, dim=-1)
+        ok = torch.ones_like(dist, dtype=torch.bool)
+    ok = ok & (col >= 0) & (col < sensor.width) & (row >= 0) & (row < sensor.height)
+    ci = torch.where(ok, col, torch.zeros_like(col)).long()
+    ri = torch.where(ok, row, torch.zeros_like(row)).long()
+    dep = torch.stack([t[..., 1] for t in tgts]).double()                 # (C, H, W)
+    cidx = torch.arange(C, device=dev)[:, None].expand_as(ci)
+    dt = dep[cidx, ri, ci]
+    ok = ok & (dt > 0) & (torch.abs(dt - dist) <= rel_tol * dist + 0.05)
+    return (ok.sum(dim=1).double() / float(n)).cpu().numpy()
+
+
+def _noisy(ch, seed: int, depth_noise: float, intensity_noise: float):
+    """Depth noise sigma = depth_noise * z^2 and intensity noise (seeded, on the channels' device)."""
+    import torch
+    g = torch.Generator(device=ch.device)
+    g.manual_seed(seed)
+    valid = ch[..., 1] > 0
+    z = ch[..., 1].double()
+    nz = torch.randn(z.shape, generator=g, device=ch.device, dtype=torch.float64)
+    ni = torch.randn(z.shape, generator=g, device=ch.device, dtype=torch.float64)
+    out = ch.clone()
+    out[..., 1] = torch.where(valid, z + nz * depth_noise * z * z, torch.zeros_like(z)).float()
+    out[..., 0] = torch.where(valid, ch[..., 0].double() + ni * intensity_noise, torch.zeros_like(z)).float()
+    return out
+
+
+def make_rgbd_hall(n_frames: int = 200, width: int = 640, height: int = 480, f: float = 525.0, seed: int = 3,
+                   sigma_t: float = 0.02, sigma_r_deg: float = 1.0, depth_noise: float = 1e-3,
+                   intensity_noise: float = 0.01, max_angle_deg: float = 30.0, max_dist: float = 1.0,
+                   min_ratio: float = 1.0 / 3.0, device="cuda", params: Optional[Dict] = None) -> Workload:
+    """RGB-D 640 x 480 sequence of n_frames along a smooth closed spline
+    through the four rooms of _hall_scene; depth noise sigma = 1 mm z^2,
+    intensity noise sigma = 0.01, then intensity and normals rounded to
+    binary16.  Pairs by the Sec. IV-B rule on the initial poses: rotation
+    angle < 30 deg, translation < 1 m, overlap ratio (renderer geometry) >
+    1/3, plus consecutive frames (a sequential acquisition, closing the
+    loop).  Channels are torch tensors on `device`.  Seeds: scene 1000 + seed,
+    trajectory 2000 + seed, perturbation 3000 + seed, noise 5000 + seed."""
+    import torch
+    scene = _hall_scene(1000 + seed)
+    cam = pinhole_sensor(width, height, f, (width - 1) / 2.0, (height - 1) / 2.0)
+    Xc = np.zeros((3, 4))
+    Xc[:, :3] = CAMERA_ON_PLATFORM
+    cam.extrinsic = Xc
+    plat = _hall_path(n_frames, 2000 + seed)
+    rays = torch.as_tensor(_pixel_rays(cam)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    st = _scene_tensors(scene, device)
+    chans = []
+    for k in range(n_frames):
+        c = render_t(scene, cam, compose(plat[k], Xc), 0.5, 5.0, device=device, rays=rays, st=st)
+        c = _noisy(c, 5000 + seed * 977 + k, depth_noise, intensity_noise)
+        chans.append(quantize_fp16_t(c))
+    init = perturb_poses(plat, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    pairs = []
+    for i in range(n_frames):
+        cand = [j for j in range(i + 1, n_frames) if np.linalg.norm(init[i, :, 3] - init[j, :, 3]) < max_dist and
+                _pose_angle_deg(init[i], init[j]) < max_angle_deg]
+        ratios = overlap_ratios_t(chans[i], [chans[j] for j in cand], cam, compose(plat[i], Xc),
+                                  np.array([compose(plat[j], Xc) for j in cand]).reshape(-1, 3, 4), rays)
+        pairs += [(i, j) for j, r in zip(cand, ratios) if r > min_ratio]
+    # a sequential acquisition: consecutive frames are paired as well (Sec. IV-B)
+    have = set(pairs)
+    for i in range(n_frames):
+        j = (i + 1) % n_frames
+        if (min(i, j), max(i, j)) not in have:
+            pairs.append((min(i, j), max(i, j)))
+    pairs.sort()
+    prm = default_params(range_min=0.5, range_max=5.0)
+    if params:
+        prm.update(params)
+    return Workload(f"rgbd-hall-{n_frames}x{width}x{height}", [cam], np.zeros(n_frames, dtype=np.int32), chans,
+                    plat, init, np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)
+
+
+def make_lidar_street_graph(n_frames: int = 500, width: int = 2048, height: int = 128, vfov_up_deg: float = 22.5,
+                            vfov_down_deg: float = -22.5, spacing: float = 1.0, seed: int = 4,
+                            sigma_t: float = 0.10, sigma_r_deg: float = 0.5, drop: float = 0.05,
+                            degree=(2, 20), window: int = 40, min_overlap: float = 0.3, device="cuda",
+                            params: Optional[Dict] = None) -> Workload:
+    """LiDAR 128 x 2048 sequence of n_frames along the synthetic street with an
+    uneven overlap graph: frame i is the source of d_i pairs, d_i uniform in
+    [2, 20], towards frames j != i within `window` frames whose overlap ratio
+    exceeds `min_overlap`, drawn at random (seeded) among them.  Channels are
+    torch tensors on `device`.  Seeds: scene 1000 + seed, trajectory 2000 +
+    seed, perturbation 3000 + seed, dropped returns 4000 + seed, graph
+    6000 + seed."""
+    import torch
+    poses = _street_trajectory(n_frames, spacing, 2000 + seed)
+    scene = _street_scene(1000 + seed, 0.0, (n_frames - 1) * spacing)
+    sensor = spherical_sensor(width, height, vfov_up_deg, vfov_down_deg)
+    rays = torch.as_tensor(_pixel_rays(sensor)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(4000 + seed)
+    st = _scene_tensors(scene, device)
+    chans = []
+    for k in range(n_frames):
+        c = render_t(scene, sensor, poses[k], 1.0, 80.0, device=device, rays=rays, st=st)
+        keep = torch.rand((height, width), generator=g, device=device) >= drop
+        chans.append(quantize_fp16_t(torch.where(keep[..., None], c, torch.zeros_like(c))))
+    rng = np.random.default_rng(6000 + seed)
+    pairs = []
+    for i in range(n_frames):
+        near = [j for j in range(max(0, i - window), min(n_frames, i + window + 1)) if j != i]
+        ratios = overlap_ratios_t(chans[i], [chans[j] for j in near], sensor, poses[i], poses[near], rays)
+        cand = [j for j, r in zip(near, ratios) if r > min_overlap]
+        d = int(rng.integers(degree[0], degree[1] + 1))
+        for j in sorted(rng.permutation(cand)[:d].tolist()):
+            pairs.append((i, j))
+    init = perturb_poses(poses, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    prm = default_params(w_depth=0.1, huber_delta=0.2, occ_abs=0.3, occ_rel=0.05, z_min=0.5,
+                         range_min=1.0, range_max=80.0)
+    if params:
+        prm.update(params)
+    return Workload(f"lidar-street-graph-{n_frames}x{height}x{width}", [sensor],
+                    np.zeros(n_frames, dtype=np.int32), chans, poses, init,
+                    np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)

@@ -1,0 +1,135 @@
+"""The large configurations at full size, in the benchmark's launch
+configuration (batched path, FP16 texels, autotuned variants, graph
+iteration), against the FP64 oracle on seeded samples of pairs:
+
+  - RGB-D 640 x 480, 200 frames along a spline through a multi-room hall,
+    depth noise 1 mm z^2, intensity noise 0.01, pairs by the Sec. IV-B rule;
+  - LiDAR 128 x 2048, 500 frames along the street, an uneven overlap graph
+    (each frame the source of 2-20 pairs with more than 30 % overlap).
+
+Bars per sampled pair: the valid masks agree outside the oracle's decision
+margin; relative Frobenius error <= 1e-4 on H12 and b12 and <= 1e-5 on the
+cost against the oracle's sums with the points decided the other way inside
+the margin accounted for; for the whole system: exact symmetry and the gauge
+null space; one LM iteration runs.  The generators render on the GPU (torch), so these
+tests need one; the inputs are the same seeded scenes on any device.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def big(name):
+    gpu()
+    from paper_2303_16878_gb300 import synth
+    if name not in _CACHE:
+        _CACHE[name] = synth.make_rgbd_hall() if name == "hall" else synth.make_lidar_street_graph()
+    return _CACHE[name]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _host(ch):
+    return ch.detach().cpu().numpy()
+
+
+def accounted_pair(oracle_lib, s, params, src, tgt, Xi, Xj, gpu_mask, r):
+    """The oracle's sums of one pair with every flagged point that the GPU
+    decided the other way moved to the GPU's side: its contribution (from the
+    oracle, or from the oracle's other-branch evaluation when the oracle
+    rejected it) is removed or added.  Returns (H, b, cost, count, n_flipped,
+    n_unexplained)."""
+    H, b, cost, count = r["H"].copy(), r["b"].copy(), r["cost"], r["count"]
+    n = r["n_points"]
+    diff = np.unpackbits((gpu_mask ^ r["mask"]).view(np.uint8), bitorder="little")[:n]
+    ok_o = np.unpackbits(r["mask"].view(np.uint8), bitorder="little")[:n]
+    idx = np.nonzero(diff)[0]
+    unexplained = 0
+    if idx.size:
+        pts, _ = oracle_lib.frame_points(s, params, src)
+        for k in idx.tolist():
+            c = oracle_lib.point_contribution(s, params, tgt, Xi, Xj, pts[k], other_branch=not ok_o[k])
+            if c is None:
+                unexplained += 1
+                continue
+            sign = -1.0 if ok_o[k] else 1.0
+            H += sign * c[0]
+            b += sign * c[1]
+            cost += sign * c[2]
+            count += int(sign)
+    return H, b, cost, count, int(idx.size), unexplained
+
+
+@pytest.mark.parametrize("name", ["hall", "street_graph"])
+def test_large_config_sampled_pairs_match_oracle(oracle_lib, name):
+    """Per sampled pair: the valid masks agree on every point outside the
+    oracle's decision margin, and the GPU's H12, b12, cost and count meet the
+    bars against the oracle's sums with the points decided the other way
+    (inside the margin) accounted for by their own contributions."""
+    import paper_2303_16878_gb300 as pba
+    w = big(name)
+    p = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, solver=pba.PBA_SOLVE_MIXED)
+    p.autotune(1)
+    p.set_mask_export(True)
+    cost, count = p.linearize()
+    H, b = p.get_system()
+    assert np.array_equal(H, H.T)
+    ps = p.get_pair_system()
+    rng = np.random.default_rng(8)
+    sample = rng.choice(len(w.pairs), size=min(10, len(w.pairs)), replace=False)
+    for q in sample.tolist():
+        i, j = w.pairs[q].tolist()
+        s = w.sensors[int(w.frame_sensor[i])]
+        src, tgt = _host(w.channels[i]), _host(w.channels[j])
+        r = oracle_lib.linearize_pair(s, w.params, src, tgt, w.poses_init[i], w.poses_init[j])
+        assert p.frame_points(i) == r["n_points"]
+        m = p.get_mask(q, r["n_points"])
+        assert not np.any((m ^ r["mask"]) & ~r["flags"]), f"pair {q}: masks differ outside the decision margin"
+        Ho, bo, co, no, nf, nu = accounted_pair(oracle_lib, s, w.params, src, tgt, w.poses_init[i], w.poses_init[j],
+                                                m, r)
+        assert nu == 0, f"pair {q}: {nu} flipped points without an other-branch evaluation"
+        assert int(ps["count"][q]) == no, q
+        assert rel(ps["H"][q], Ho) <= 1e-4, (q, nf, rel(ps["H"][q], Ho))
+        assert rel(ps["b"][q], bo) <= 1e-4, (q, nf, rel(ps["b"][q], bo))
+        assert abs(ps["cost"][q] - co) <= 1e-5 * co + 1e-12, q
+    # gauge: H annihilates a common motion of all frames (6 directions of the global frame)
+    from oracle_pins import gauge_directions
+    V = gauge_directions(w.poses_init)
+    assert np.linalg.norm(H @ V) <= 1e-4 * np.linalg.norm(H) * np.linalg.norm(V)
+    p.set_mask_export(False)
+    st = p.iterate()
+    assert st["status"] == 0
+    p.close()
+
+
+def test_hall_adjoint_on_a_four_frame_subset(oracle_lib):
+    """The adjoint's tangent pose gradient on four consecutive full-size frames
+    equals twice the oracle's b with exact Jacobians (grad_mode 1: the
+    derivative of the bilinear interpolant, which the adjoint differentiates;
+    Eq. total-error-multicue, Huber with the decisions held fixed)."""
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import autograd
+    torch = gpu()
+    w = big("hall").subset(range(4))
+    host = [_host(c) for c in w.channels]
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, host, w.poses_init, w.pairs, dict(w.params, grad_mode=1))
+    p = pba.problem_from_workload(w)
+    cost, _, dposes, _, _ = p.cost_gradient(poses=True, extrinsics=False, images=False, device="cuda")
+    X = torch.as_tensor(w.poses_init, dtype=torch.float64, device="cuda")
+    gt = autograd.tangent_gradient(X, dposes.reshape(-1, 3, 4)).reshape(-1).cpu().numpy()
+    assert rel(gt, 2.0 * ref["b"]) <= 1e-4
+    assert abs(cost - ref["cost"]) <= 1e-5 * ref["cost"]
+    p.close()

@@ -198,11 +198,18 @@ def test_autotuned_variants_agree(oracle_lib, street3):
     p.linearize()
     H0, b0 = p.get_system()
     vf, vc = p.autotune(1)
-    assert vf in (0, 1) and vc in (0, 1)
-    cost, _ = p.linearize()
-    H1, b1 = p.get_system()
-    assert rel(H1, H0) <= 1e-6 and rel(b1, b0) <= 1e-6
-    assert rel(H1, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+    assert vf in range(pba._lib.PBA_N_VARIANTS) and vc in range(pba._lib.PBA_N_VARIANTS)
+    for v in [None] + list(range(pba._lib.PBA_N_VARIANTS)):
+        if v is not None:
+            p.set_variants(v, v)
+        cost, _ = p.linearize()
+        H1, b1 = p.get_system()
+        assert rel(H1, H0) <= 1e-6 and rel(b1, b0) <= 1e-6
+        assert rel(H1, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+        p.iterate()  # the graph is rebuilt for the variant
+        p.set_poses(w.poses_init)
+    with pytest.raises(pba.PbaError):
+        p.set_variants(pba._lib.PBA_N_VARIANTS, 0)
     p.close()
 
 

@@ -186,3 +186,26 @@ def test_tied_frames_gradient_matches_finite_differences(oracle_lib, fusion):
 
 def test_default_variables_reduce_to_the_gauge_fixed_step(oracle_lib, room3):
     assert P.pin_variables_reduce_to_gauge(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["variables_reduce_to_gauge"]
+
+
+def test_other_branch_only_touches_flagged_rejections(oracle_lib, street3):
+    """The other-branch evaluation (used to account for points a float32
+    implementation decides the other way) leaves every valid point unchanged
+    and validates only points whose decision lies within its margin."""
+    w = street3
+    s = w.sensors[0]
+    lib = oracle_lib.load()
+    forced = 0
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        pts, _ = oracle_lib.frame_points(s, w.params, w.channels[i], lib=lib)
+        for k in range(len(pts)):
+            a = oracle_lib.point_residual(s, w.params, w.channels[j], w.poses_init[i], w.poses_init[j], pts[k],
+                                          lib=lib)
+            b = oracle_lib.point_residual(s, w.params, w.channels[j], w.poses_init[i], w.poses_init[j], pts[k],
+                                          lib=lib, other_branch=True)
+            if a["valid"]:
+                assert b["valid"] and np.array_equal(a["e"], b["e"]) and np.array_equal(a["Ji"], b["Ji"])
+            elif b["valid"]:
+                assert a["flag"]
+                forced += 1
+    assert forced > 0
