@@ -274,6 +274,25 @@ int pba_iterate_async(pba_problem* p, int n);
 /* Synchronise and read the outcome of the last iteration. */
 int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
 
+/* The current offset X_o of one sensor (row-major 3x4, host memory).
+ * Errors: PBA_EINVAL. */
+int pba_get_extrinsic(pba_problem* p, int sensor, double* extrinsic);
+
+/* Refine one sensor's offset X_o (Supp., offset form) at the current poses
+ * by quasi-Newton (BFGS) descent of F over its 6 box-plus coordinates, with
+ * the adjoint gradient of pba_cost_gradient and a backtracking (Armijo)
+ * line search; the first step moves at most 0.01 in the chart (1 cm or
+ * ~1 deg).  Stops after max_iters iterations or at the first step whose
+ * relative decrease of F is below rel_tol.  The refined offset is the
+ * sensor's extrinsic afterwards (as after pba_set_extrinsic).  Alternating
+ * it with pose iterations (pba_iterate / pba_optimize) refines poses and
+ * offset jointly.  Host or device outputs: cost_before, cost_after (F before
+ * and after) and iterations (host, any may be NULL).  Needs poses, pairs and
+ * the batched path; allocates a small device buffer; synchronises.
+ * Errors: PBA_EINVAL, PBA_ENOTREADY, PBA_ENOMEM, PBA_ECUDA. */
+int pba_refine_extrinsic(pba_problem* p, int sensor, int max_iters, double rel_tol, double* cost_before,
+                         double* cost_after, int32_t* iterations);
+
 /* Pose variables of the damped solve.  By default frame 0 is held fixed (the
  * gauge) and every other frame k moves with its own variable.  frame_var
  * (n_frames entries, host memory) instead maps frame k to variable
@@ -290,6 +309,22 @@ int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
  * (n_vars outside [1, n_frames - 1], an entry outside [-1, n_vars), no frame
  * held fixed, a variable without frames), PBA_ENOMEM, PBA_ECUDA. */
 int pba_set_variables(pba_problem* p, const int32_t* frame_var, int n_vars);
+
+/* Make the offset X_o of one sensor a variable of the damped solve (is_free
+ * != 0) or hold it fixed again (0, the default).  The paper holds offsets
+ * fixed (Supp., offset form); as a variable its Jacobian follows from the
+ * first-order identity J_o = (J_i + J_j) A_o, A_o = [[R_o, 2 [t_o]x R_o],
+ * [0, R_o]] (a right perturbation of X_o acts like the perturbation
+ * X_o exp(d) X_o^-1 of both poses), so the offset blocks of every pair come
+ * from its H12 and b12 in FP64.  Each iteration then moves the free offsets
+ * with the poses, rebuilds the pixel-points of their frames for the
+ * candidate, and again after the accept decision.  With one sensor the
+ * offset and the poses share a 6-dimensional gauge: free an offset when
+ * another sensor's offset is fixed and the sensors' frames are tied by
+ * pba_set_variables (coupled platforms), or with fixed frames.
+ * pba_get_extrinsic reads the refined offsets.  Drops the iteration graph.
+ * Errors: PBA_EINVAL (bad sensor, too many unknowns), PBA_ENOMEM, PBA_ECUDA. */
+int pba_set_offset_free(pba_problem* p, int sensor, int is_free);
 
 /* ---- Pyramid and coarse-to-fine optimisation (Sec. IV-A, Sec. IV-C) ----
  *

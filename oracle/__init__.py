@@ -99,6 +99,10 @@ def _declare(lib):
     lib.o_solve_step.argtypes = [ctypes.c_int, P(d), P(d), d, P(d)]
     lib.o_solve_step.restype = ctypes.c_int
     lib.o_apply_update.argtypes = [ctypes.c_int, P(d), P(d), P(d)]
+    lib.o_offset_map.argtypes = [P(d), P(d)]
+    lib.o_offset_jacobian.argtypes = [P(d), P(d), P(d), P(d)]
+    lib.o_pair_offset_blocks.argtypes = [S, Pr, P(ctypes.c_float), P(ctypes.c_float), P(d), P(d), P(d)]
+    lib.o_pair_offset_blocks.restype = ctypes.c_int
     return lib
 
 
@@ -234,6 +238,39 @@ def linearize_pair(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, X
                 mask=mask[:nw].copy(), flags=flags[:nw].copy())
 
 
+def offset_map(extrinsic) -> np.ndarray:
+    """A_o (6 x 6): the offset perturbation d acts like A_o d on both poses (R23)."""
+    lib = _load()
+    A = np.zeros(36)
+    lib.o_offset_map(_ptr(_f64(extrinsic).reshape(12), ctypes.c_double), _ptr(A, ctypes.c_double))
+    return A.reshape(6, 6)
+
+
+def pair_offset_blocks(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, Xj, lib=None) -> Dict:
+    """Offset blocks of one pair (R23): H_io, H_jo, H_oo (6x6 each) and b_o."""
+    lib = lib or _load()
+    src = np.ascontiguousarray(src, dtype=np.float32)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+    out = np.zeros(114)
+    n = lib.o_pair_offset_blocks(ctypes.byref(_sensor(sensor)), ctypes.byref(_params(params)),
+                                 _ptr(src, ctypes.c_float), _ptr(tgt, ctypes.c_float),
+                                 _ptr(_f64(Xi).reshape(12), ctypes.c_double),
+                                 _ptr(_f64(Xj).reshape(12), ctypes.c_double), _ptr(out, ctypes.c_double))
+    if n < 0:
+        raise MemoryError("oracle: allocation failed")
+    return dict(H_io=out[:36].reshape(6, 6), H_jo=out[36:72].reshape(6, 6), H_oo=out[72:108].reshape(6, 6),
+                b_o=out[108:].copy())
+
+
+def offset_jacobian(extrinsic, Ji, Jj) -> np.ndarray:
+    """J_o = (J_i + J_j) A_o (5 x 6, R23)."""
+    lib = _load()
+    Jo = np.zeros(30)
+    lib.o_offset_jacobian(_ptr(_f64(extrinsic).reshape(12), ctypes.c_double), _ptr(_f64(Ji).reshape(30), ctypes.c_double),
+                          _ptr(_f64(Jj).reshape(30), ctypes.c_double), _ptr(Jo, ctypes.c_double))
+    return Jo.reshape(5, 6)
+
+
 def linearize(sensors: Sequence, frame_sensor, channels: Sequence[np.ndarray], poses, pairs, params: Dict,
               want_system: bool = True, want_pairs: bool = False, lib=None) -> Dict:
     """Dense H (6N x 6N, gauge not fixed), b, total cost F (Eq. total-error-multicue), count."""
@@ -331,6 +368,83 @@ def initial_lambda_vars(H, frame_var, n_vars: int) -> float:
     S = selection(frame_var, n_vars)
     d = np.diag(S.T @ np.asarray(H, dtype=np.float64) @ S)
     return 1e-4 * float(d.max()) if d.size else 0.0
+
+
+def offset_system(w, sensors, poses, lin: Dict, free: Sequence[int], lib=None):
+    """H and b over the blocks [frames..., free offsets...]: the frames' system
+    of `lin` plus, per pair of a sensor with a free offset, its offset blocks
+    from pair_offset_blocks (R23) at rows/columns of that offset."""
+    n = len(w.channels)
+    nb = n + len(free)
+    H = np.zeros((6 * nb, 6 * nb))
+    b = np.zeros(6 * nb)
+    H[:6 * n, :6 * n] = lin["H"]
+    b[:6 * n] = lin["b"]
+    for i, j in np.asarray(w.pairs).reshape(-1, 2).tolist():
+        s = int(w.frame_sensor[i])
+        if s not in free:
+            continue
+        o = 6 * (n + list(free).index(s))
+        blk = pair_offset_blocks(sensors[s], w.params, w.channels[i], w.channels[j], poses[i], poses[j], lib=lib)
+        for f, Hfo in ((i, blk["H_io"]), (j, blk["H_jo"])):
+            H[6 * f:6 * f + 6, o:o + 6] += Hfo
+            H[o:o + 6, 6 * f:6 * f + 6] += Hfo.T
+        H[o:o + 6, o:o + 6] += blk["H_oo"]
+        b[o:o + 6] += blk["b_o"]
+    return H, b
+
+
+def _with_offsets(sensors, offsets: Dict):
+    out = []
+    for k, s in enumerate(sensors):
+        if k in offsets:
+            d = s.as_dict() if hasattr(s, "as_dict") else dict(s)
+            d["extrinsic"] = np.asarray(offsets[k], dtype=np.float64).reshape(12)
+            out.append(d)
+        else:
+            out.append(s)
+    return out
+
+
+def _extrinsic_of(s) -> np.ndarray:
+    g = s["extrinsic"] if isinstance(s, dict) else s.extrinsic
+    return np.asarray(g, dtype=np.float64).reshape(3, 4)
+
+
+def lm_iteration_offsets(w, poses, sensors, lam: Optional[float], free: Sequence[int], lib=None) -> Dict:
+    """One Levenberg-Marquardt iteration whose variables are the frames' (as in
+    lm_iteration) and the offsets of the sensors in `free` (R23), at `poses`
+    with `sensors` carrying the current offsets.  Returns the accepted poses
+    and sensors, the new lambda and both costs."""
+    lin = linearize(sensors, w.frame_sensor, w.channels, poses, w.pairs, w.params, lib=lib)
+    H, b = offset_system(w, sensors, poses, lin, free, lib=lib)
+    n = len(w.channels)
+    fv = getattr(w, "frame_var", None)
+    if fv is None:
+        fv, nf = np.arange(-1, n - 1), n - 1
+    else:
+        nf = w.n_vars
+    blocks_var = np.concatenate([np.asarray(fv), nf + np.arange(len(free))])
+    S = selection(blocks_var, nf + len(free))
+    Hr, br = S.T @ H @ S, S.T @ b
+    if lam is None:
+        lam = 1e-4 * float(np.diag(Hr).max())
+    try:
+        x = cholesky_solve(Hr + lam * np.eye(Hr.shape[0]), -br, lib=lib)
+        ok = True
+    except np.linalg.LinAlgError:
+        x, ok = np.zeros(Hr.shape[0]), False
+    dx = S @ x
+    cand = apply_update(poses, dx[:6 * n], lib=lib)
+    offs = {s: boxplus(_extrinsic_of(sensors[s]), dx[6 * (n + k):6 * (n + k) + 6], lib=lib).reshape(3, 4)
+            for k, s in enumerate(free)}
+    cand_sensors = _with_offsets(sensors, offs)
+    new = linearize(cand_sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False, lib=lib)
+    accepted = ok and new["cost"] < lin["cost"]
+    return dict(poses=cand if accepted else np.asarray(poses).copy(),
+                sensors=cand_sensors if accepted else list(sensors), accepted=accepted,
+                lam=lam / 10.0 if accepted else lam * 10.0, lam_used=lam, cost=lin["cost"], new_cost=new["cost"],
+                candidate=cand, candidate_sensors=cand_sensors, solve_ok=ok)
 
 
 def lm_iteration(w, poses, lam: Optional[float], lib=None) -> Dict:

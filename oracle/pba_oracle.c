@@ -584,6 +584,85 @@ int o_linearize_pair(const o_sensor* s, const o_params* prm, const float* src, c
  * and its cost / count in pair_cost / pair_count.  Returns 0, or -1 on a
  * malformed pair (frames out of range or of different sensors).
  */
+/* ----------------------------------------- the sensor offset as a variable */
+
+/*
+ * Reading R23 (the paper holds X_o fixed and prints no derivative for it):
+ * pbar = X_o^-1 X_j^-1 X_i X_o pi^-1(u, d), and n-bar likewise with the
+ * rotations.  Right-perturbing X_o by E = exp(d) gives E^-1 (X_o^-1 X_j^-1
+ * X_i X_o) E; right-perturbing X_i by X_o E X_o^-1 produces the right factor
+ * and right-perturbing X_j by the same transform the left one.  So, to first
+ * order, J_o = (J_i + J_j) A_o with A_o the map d -> [R_o dt + 2 [t_o]x R_o dq,
+ * R_o dq] (X_o E X_o^-1 in the [dt, dq] coordinates of Supp., R(dq) ~ I + 2
+ * [dq]x).  A is row-major 6 x 6.
+ */
+void o_offset_map(const double Xo[12], double A[36]) {
+    double Ro[9], to[3];
+    rot_of(Xo, Ro);
+    trans_of(Xo, to);
+    memset(A, 0, sizeof(double) * 36);
+    /* [t_o]x R_o, column c: t_o x (column c of R_o) */
+    for (int c = 0; c < 3; ++c) {
+        const double col[3] = {Ro[c], Ro[3 + c], Ro[6 + c]};
+        const double x[3] = {to[1] * col[2] - to[2] * col[1], to[2] * col[0] - to[0] * col[2],
+                             to[0] * col[1] - to[1] * col[0]};
+        for (int r = 0; r < 3; ++r) {
+            A[6 * r + c] = Ro[3 * r + c];
+            A[6 * r + 3 + c] = 2.0 * x[r];
+            A[6 * (3 + r) + 3 + c] = Ro[3 * r + c];
+        }
+    }
+}
+
+/* Jo (5x6) = (Ji + Jj) A_o  (R23). */
+void o_offset_jacobian(const double Xo[12], const double Ji[30], const double Jj[30], double Jo[30]) {
+    double A[36];
+    o_offset_map(Xo, A);
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 6; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += (Ji[6 * r + k] + Jj[6 * r + k]) * A[6 * k + c];
+            Jo[6 * r + c] = s;
+        }
+}
+
+/* Offset blocks of one pair, point by point: out = [H_io (6x6), H_jo (6x6),
+ * H_oo (6x6), b_o (6)] = sums of w J_i^T Omega J_o, w J_j^T Omega J_o,
+ * w J_o^T Omega J_o, w J_o^T Omega e over the valid residuals. */
+int o_pair_offset_blocks(const o_sensor* s, const o_params* prm, const float* src, const float* tgt,
+                         const double Xi[12], const double Xj[12], double out[114]) {
+    int cap = s->width * s->height;
+    double* pts = (double*)malloc(sizeof(double) * 7 * (size_t)(cap > 0 ? cap : 1));
+    if (!pts) return -1;
+    int np = o_frame_points(s, prm, src, pts, NULL, cap);
+    const double om[5] = {prm->w_int, prm->w_depth, prm->w_normal, prm->w_normal, prm->w_normal};
+    memset(out, 0, sizeof(double) * 114);
+    for (int k = 0; k < np; ++k) {
+        double e[5], Ji[30], Jj[30], Jo[30], rho, w;
+        int flag;
+        if (!o_point_residual(s, prm, tgt, Xi, Xj, pts + 7 * (size_t)k, e, Ji, Jj, &rho, &w, &flag)) continue;
+        o_offset_jacobian(s->Xo, Ji, Jj, Jo);
+        for (int a = 0; a < 6; ++a) {
+            for (int c = 0; c < 6; ++c) {
+                double hi = 0.0, hj = 0.0, ho = 0.0;
+                for (int r = 0; r < 5; ++r) {
+                    hi += Ji[6 * r + a] * om[r] * Jo[6 * r + c];
+                    hj += Jj[6 * r + a] * om[r] * Jo[6 * r + c];
+                    ho += Jo[6 * r + a] * om[r] * Jo[6 * r + c];
+                }
+                out[6 * a + c] += w * hi;
+                out[36 + 6 * a + c] += w * hj;
+                out[72 + 6 * a + c] += w * ho;
+            }
+            double bo = 0.0;
+            for (int r = 0; r < 5; ++r) bo += Jo[6 * r + a] * om[r] * e[r];
+            out[108 + a] += w * bo;
+        }
+    }
+    free(pts);
+    return np;
+}
+
 int o_linearize(int n_frames, const o_sensor* sensors, const int32_t* frame_sensor,
                 const float* const* channels, const double* poses, int m, const int32_t* pairs,
                 const o_params* prm, double* H, double* b, double* cost, int64_t* count,

@@ -217,6 +217,25 @@ class Problem:
         return [dict(level=s.level, iterations=s.iterations, accepted=s.accepted, status=s.status,
                      cost_first=s.cost_first, cost_last=s.cost_last) for s in st]
 
+    def refine_extrinsic(self, sensor: int, max_iters: int = 20, rel_tol: float = 1e-7) -> Dict:
+        """BFGS on one sensor's offset with the adjoint gradient (pba_refine_extrinsic)."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        self._check(self._lib.pba_refine_extrinsic(self._h, int(sensor), int(max_iters), float(rel_tol),
+                                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+                    "refine_extrinsic")
+        return dict(cost_before=a.value, cost_after=b.value, iterations=n.value)
+
+    def set_offset_free(self, sensor: int, free: bool = True):
+        """Make one sensor's offset X_o a variable of the LM steps (or fix it again)."""
+        self._check(self._lib.pba_set_offset_free(self._h, int(sensor), 1 if free else 0), "set_offset_free")
+
+    def get_extrinsic(self, sensor: int) -> np.ndarray:
+        """The sensor's current offset X_o (3x4), as last set or refined."""
+        out = np.zeros(12)
+        self._check(self._lib.pba_get_extrinsic(self._h, int(sensor), out.ctypes.data_as(ctypes.c_void_p)),
+                    "get_extrinsic")
+        return out.reshape(3, 4)
+
     def frame_points(self, frame: int) -> int:
         n = ctypes.c_int32()
         self._check(self._lib.pba_frame_points(self._h, frame, ctypes.byref(n)), "frame_points")

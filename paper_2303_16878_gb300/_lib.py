@@ -44,7 +44,8 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
            "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels",
            "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
-           "pba_set_variants"]
+           "pba_set_variants", "pba_refine_extrinsic",
+           "pba_get_extrinsic", "pba_set_offset_free"]
 PBA_N_VARIANTS = 3
 PBA_MAX_LEVELS = 8
 PBA_NORMALS_MAX_RADIUS = 32
@@ -131,6 +132,10 @@ def load(build_if_missing: bool = True):
             "pba_build_pyramid": ([vp, ctypes.c_int], ctypes.c_int),
             "pba_set_variables": ([vp, P(ctypes.c_int32), ctypes.c_int], ctypes.c_int),
             "pba_set_variants": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "pba_get_extrinsic": ([vp, ctypes.c_int, vp], ctypes.c_int),
+            "pba_set_offset_free": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "pba_refine_extrinsic": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, P(ctypes.c_double),
+                                      P(ctypes.c_double), P(ctypes.c_int32)], ctypes.c_int),
             "pba_pyramid_level": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
             "pba_optimize": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_double, P(PbaLevelStats)], ctypes.c_int),
             "pba_cost_gradient": ([vp, P(d), P(i64), vp, vp, vp], ctypes.c_int),

@@ -61,7 +61,8 @@ struct pba_problem {
     double* d_A = nullptr;
     double* d_rhs = nullptr;
     double* d_Dinv = nullptr;  // inverses of the Cholesky diagonal tiles
-    int n_pad = 0;
+    int n_pad = 0;        // padded size of the default gauge-fixed system
+    int n_pad_alloc = 0;  // padded size the solver buffers hold
     MixedWork mixed{};  // buffers of the mixed-precision solve
     int* d_queue = nullptr;  // two counters: full pass, cost pass
 
@@ -100,15 +101,38 @@ struct pba_problem {
     cudaGraphExec_t graph_exec = nullptr;
     int launches_last = 0;
 
-    // pose variables (pba_set_variables); n_vars < 0: frame 0 fixed, frame k -> variable k - 1
+    // pose variables.  fv_user / n_fv_user: the frames' mapping as given to
+    // pba_set_variables (n_fv_user < 0: frame 0 fixed, frame k -> variable k - 1);
+    // offset_free: sensors whose offset X_o is a variable (pba_set_offset_free).
+    // n_vars: the effective number of variables of the solve, < 0 when the default
+    // mapping applies and no offset is free (the solve then uses H directly).
+    int n_fv_user = -1;
+    std::vector<int32_t> fv_user;
+    std::vector<char> offset_free;
+    bool offsets_free = false;
     int n_vars = -1;
-    std::vector<int32_t> frame_var;
     int* d_frame_var = nullptr;
+    int* d_sensor_var = nullptr;
     int* d_var_start = nullptr;
-    int* d_var_frames = nullptr;
+    int* d_var_frames = nullptr;   // blocks of each variable: frames f < N, offsets N + s
     double* d_Hr = nullptr;
     double* d_br = nullptr;
     int n_pad_vars = 0;
+    // offsets on the device: current and candidate (S x 12, FP64), per-pair offset
+    // blocks, their assembly (Hfo per frame, Hoo and bo per sensor), the pair lists
+    // by frame and by sensor, and the frames re-packed when an offset moves
+    double* d_extr = nullptr;
+    double* d_extr_cand = nullptr;
+    double* d_pext = nullptr;
+    double* d_Hfo = nullptr;
+    double* d_Hoo = nullptr;
+    double* d_bo = nullptr;
+    int* d_f_start = nullptr;
+    int2* d_f_items = nullptr;
+    int* d_s_start = nullptr;
+    int* d_s_items = nullptr;
+    int* d_free_frames = nullptr;
+    int n_free_frames = 0;
 
     // coarser pyramid levels 1.. (Sec. IV-A), each a problem of its own on the same stream
     std::vector<pba_problem*> levels;
@@ -152,6 +176,14 @@ void free_pair_buffers(pba_problem* p) {
     dfree(p->d_adj_partials);
     dfree(p->d_adj_pair);
     dfree(p->d_adj_totals);
+    dfree(p->d_pext);
+    dfree(p->d_f_start);
+    dfree(p->d_f_items);
+    dfree(p->d_s_start);
+    dfree(p->d_s_items);
+    p->d_pext = nullptr;
+    p->d_f_start = p->d_s_start = p->d_s_items = nullptr;
+    p->d_f_items = nullptr;
     p->M = 0;
     p->n_chunks = 0;
     p->n_tasks = 0;
@@ -226,7 +258,20 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     const double* Hs = p->d_H;
     const double* bs = p->d_b;
     int nf = p->N, npad = p->n_pad;
-    if (p->n_vars >= 0) {
+    const int S = (int)p->sensors.size();
+    if (p->n_vars >= 0 && p->offsets_free) {
+        // offset blocks from the current pair blocks (J_o = (J_i + J_j) A_o), then S^T H S
+        CUDA_TRY(p, launch_offset_system(p->d_blocks, p->d_pair_Xo, p->M, p->d_pext, p->d_f_start, p->d_f_items,
+                                         p->d_s_start, p->d_s_items, p->d_frame_sensor, p->d_sensor_var, p->N, S,
+                                         p->d_Hfo, p->d_Hoo, p->d_bo, s));
+        CUDA_TRY(p, launch_reduce_vars_offset(p->d_H, p->d_b, p->d_Hfo, p->d_Hoo, p->d_bo, p->d_frame_sensor, p->N,
+                                              p->d_var_start, p->d_var_frames, p->n_vars, p->d_Hr, p->d_br, s));
+        *nl += p->M > 0 ? 3 : 2;
+        Hs = p->d_Hr;
+        bs = p->d_br;
+        nf = p->n_vars + 1;
+        npad = p->n_pad_vars;
+    } else if (p->n_vars >= 0) {
         CUDA_TRY(p, launch_reduce_vars(p->d_H, p->d_b, p->N, p->d_var_start, p->d_var_frames, p->n_vars, p->d_Hr,
                                        p->d_br, s));
         ++*nl;
@@ -250,6 +295,17 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     CUDA_TRY(p, launch_boxplus(p->d_poses, p->d_rhs, p->N, p->n_vars >= 0 ? p->d_frame_var : nullptr, p->d_state,
                                p->d_cand, s));
     ++*nl;
+    if (p->offsets_free) {
+        // candidate offsets, their per-pair / per-sensor copies, and the pixel-points
+        // p_u = R_o pi^-1(u, d) + t_o of the frames they move
+        CUDA_TRY(p, launch_offset_step(p->d_extr, p->d_rhs, p->d_sensor_var, S, p->d_state, p->d_extr_cand, s));
+        CUDA_TRY(p, launch_offset_refresh(p->d_extr_cand, S, p->d_pf, p->d_frame_sensor, p->M, p->d_pair_Xo,
+                                          p->d_sensors, s));
+        CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
+                                p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
+                                p->cfg.range_min, p->cfg.range_max, s));
+        *nl += 3;
+    }
     if (speculative) {
         int st = enqueue_linearize(p, s, nl, ev, true);
         if (st) return st;
@@ -283,6 +339,15 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, speculative, p->d_H, p->d_H_cand, p->d_b,
                               p->d_b_cand, p->d_blocks, p->d_blocks_cand, p->M, s));
     *nl += speculative ? 2 : 1;
+    if (p->offsets_free) {  // the accepted (or kept) offsets become current again everywhere
+        CUDA_TRY(p, launch_offset_accept(p->d_state, p->d_extr, p->d_extr_cand, S, s));
+        CUDA_TRY(p, launch_offset_refresh(p->d_extr, S, p->d_pf, p->d_frame_sensor, p->M, p->d_pair_Xo,
+                                          p->d_sensors, s));
+        CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
+                                p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
+                                p->cfg.range_min, p->cfg.range_max, s));
+        *nl += 3;
+    }
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
     return PBA_OK;
 }
@@ -342,6 +407,91 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
         std::vector<int32_t> keep = p->pairs;
         return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
     }
+    return PBA_OK;
+}
+
+// The effective variables of the solve from the frames' mapping and the free
+// offsets: device CSR of the blocks of each variable (frames f < N, offsets
+// N + s), the frame and sensor maps used by the box-plus, Hr / br, and the list
+// of frames re-packed when an offset moves.  Drops the iteration graph.
+int rebuild_vars(pba_problem* p) {
+    drop_graph(p);
+    p->pyramid_stale = true;
+    const int S = (int)p->sensors.size();
+    p->offsets_free = false;
+    for (int s = 0; s < S; ++s) p->offsets_free = p->offsets_free || p->offset_free[s];
+    dfree(p->d_frame_var);
+    dfree(p->d_var_start);
+    dfree(p->d_var_frames);
+    dfree(p->d_Hr);
+    dfree(p->d_br);
+    dfree(p->d_free_frames);
+    p->n_free_frames = 0;
+    p->n_vars = -1;
+    std::vector<int> sv(S, -1);
+    if (p->n_fv_user < 0 && !p->offsets_free) {
+        CUDA_TRY(p, cudaMemcpy(p->d_sensor_var, sv.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
+        return PBA_OK;
+    }
+    std::vector<int32_t> fv(p->N);
+    int nf;
+    if (p->n_fv_user >= 0) {
+        fv = p->fv_user;
+        nf = p->n_fv_user;
+    } else {
+        for (int k = 0; k < p->N; ++k) fv[k] = k - 1;
+        nf = p->N - 1;
+    }
+    int n_total = nf;
+    for (int s = 0; s < S; ++s)
+        if (p->offset_free[s]) sv[s] = n_total++;
+    if (n_total < 1) return fail(p, PBA_EINVAL, "variables: nothing to solve for");
+    std::vector<int> count(n_total, 0);
+    for (int k = 0; k < p->N; ++k)
+        if (fv[k] >= 0) ++count[fv[k]];
+    for (int s = 0; s < S; ++s)
+        if (sv[s] >= 0) ++count[sv[s]];
+    std::vector<int> start(n_total + 1, 0);
+    for (int v = 0; v < n_total; ++v) start[v + 1] = start[v] + count[v];
+    std::vector<int> fill(start.begin(), start.end() - 1), blocks(start[n_total]);
+    for (int k = 0; k < p->N; ++k)
+        if (fv[k] >= 0) blocks[fill[fv[k]]++] = k;
+    for (int s = 0; s < S; ++s)
+        if (sv[s] >= 0) blocks[fill[sv[s]]++] = p->N + s;
+    std::vector<int> free_frames;
+    for (int k = 0; k < p->N; ++k)
+        if (p->offset_free[p->frame_sensor[k]]) free_frames.push_back(k);
+    const size_t nr = 6 * (size_t)(n_total + 1);
+    if (cudaMalloc((void**)&p->d_frame_var, sizeof(int) * p->N) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_var_start, sizeof(int) * (n_total + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_var_frames, sizeof(int) * std::max<size_t>(blocks.size(), 1)) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_Hr, sizeof(double) * nr * nr) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_br, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_free_frames, sizeof(int) * std::max<size_t>(free_frames.size(), 1)) != cudaSuccess)
+        return fail(p, PBA_ENOMEM, "variables: out of device memory");
+    CUDA_TRY(p, cudaMemcpy(p->d_frame_var, fv.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_sensor_var, sv.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_var_start, start.data(), sizeof(int) * (n_total + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_var_frames, blocks.data(), sizeof(int) * blocks.size(), cudaMemcpyHostToDevice));
+    if (!free_frames.empty())
+        CUDA_TRY(p, cudaMemcpy(p->d_free_frames, free_frames.data(), sizeof(int) * free_frames.size(),
+                               cudaMemcpyHostToDevice));
+    p->n_free_frames = (int)free_frames.size();
+    p->n_vars = n_total;
+    p->n_pad_vars = ((6 * n_total + kTile - 1) / kTile) * kTile;
+    if (p->n_pad_vars > p->n_pad_alloc)
+        return fail(p, PBA_EINVAL, "variables: more unknowns than the problem's solver buffers hold");
+    return PBA_OK;
+}
+
+// The host copies of the offsets follow the device ones (refined by the solve).
+int sync_offsets_to_host(pba_problem* p) {
+    const int S = (int)p->sensors.size();
+    std::vector<double> X(12 * (size_t)S);
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    CUDA_TRY(p, cudaMemcpy(X.data(), p->d_extr, sizeof(double) * X.size(), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < S; ++s)
+        for (int e = 0; e < 12; ++e) p->sensors[s].extrinsic[e] = X[12 * s + e];
     return PBA_OK;
 }
 
@@ -414,6 +564,10 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     const int n = n6 - 6;
     p->n_pad = ((n + kTile - 1) / kTile) * kTile;
     if (p->n_pad == 0) p->n_pad = kTile;
+    // the solver's buffers also hold the variables of free offsets (6 per sensor)
+    const int S = (int)p->sensors.size();
+    p->n_pad_alloc = ((n + 6 * S + kTile - 1) / kTile) * kTile;
+    p->offset_free.assign(S, 0);
     auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
     bool ok = alloc((void**)&p->raw, sizeof(float) * 5 * (size_t)p->total_px) &&
               alloc(&p->tex, texel_bytes * (size_t)p->total_px) &&
@@ -432,17 +586,23 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
               alloc((void**)&p->d_b, sizeof(double) * n6) &&
               alloc((void**)&p->d_H_cand, sizeof(double) * (size_t)n6 * n6) &&
               alloc((void**)&p->d_b_cand, sizeof(double) * n6) &&
-              alloc((void**)&p->d_A, sizeof(double) * (size_t)p->n_pad * p->n_pad) &&
-              alloc((void**)&p->d_rhs, sizeof(double) * p->n_pad) &&
-              alloc((void**)&p->d_Dinv, sizeof(double) * (size_t)p->n_pad * kTile) &&
+              alloc((void**)&p->d_A, sizeof(double) * (size_t)p->n_pad_alloc * p->n_pad_alloc) &&
+              alloc((void**)&p->d_rhs, sizeof(double) * p->n_pad_alloc) &&
+              alloc((void**)&p->d_Dinv, sizeof(double) * (size_t)p->n_pad_alloc * kTile) &&
+              alloc((void**)&p->d_extr, sizeof(double) * 12 * S) &&
+              alloc((void**)&p->d_extr_cand, sizeof(double) * 12 * S) &&
+              alloc((void**)&p->d_sensor_var, sizeof(int) * S) &&
+              alloc((void**)&p->d_Hfo, sizeof(double) * 36 * (size_t)p->N) &&
+              alloc((void**)&p->d_Hoo, sizeof(double) * 36 * S) &&
+              alloc((void**)&p->d_bo, sizeof(double) * 6 * S) &&
               alloc((void**)&p->d_queue, sizeof(int) * 2) &&
               (cfg->solver != PBA_SOLVE_MIXED ||
-               (alloc((void**)&p->mixed.A32, sizeof(float) * (size_t)p->n_pad * p->n_pad) &&
-                alloc((void**)&p->mixed.D32, sizeof(float) * (size_t)p->n_pad * kTile) &&
-                alloc((void**)&p->mixed.r32, sizeof(float) * p->n_pad) &&
-                alloc((void**)&p->mixed.bs, sizeof(double) * p->n_pad) &&
-                alloc((void**)&p->mixed.x, sizeof(double) * p->n_pad) &&
-                alloc((void**)&p->mixed.dscale, sizeof(double) * p->n_pad) &&
+               (alloc((void**)&p->mixed.A32, sizeof(float) * (size_t)p->n_pad_alloc * p->n_pad_alloc) &&
+                alloc((void**)&p->mixed.D32, sizeof(float) * (size_t)p->n_pad_alloc * kTile) &&
+                alloc((void**)&p->mixed.r32, sizeof(float) * p->n_pad_alloc) &&
+                alloc((void**)&p->mixed.bs, sizeof(double) * p->n_pad_alloc) &&
+                alloc((void**)&p->mixed.x, sizeof(double) * p->n_pad_alloc) &&
+                alloc((void**)&p->mixed.dscale, sizeof(double) * p->n_pad_alloc) &&
                 alloc((void**)&p->mixed.norms, sizeof(double) * 2)));
     if (!ok) return bail(PBA_ENOMEM);
 
@@ -477,7 +637,15 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     }
     LmState st{};
     st.lambda = -1.0;
-    if (cudaMemcpy(p->d_frames, fi.data(), sizeof(FrameInfo) * p->N, cudaMemcpyHostToDevice) != cudaSuccess ||
+    std::vector<double> ex(12 * p->sensors.size());
+    for (size_t s = 0; s < p->sensors.size(); ++s)
+        for (int e = 0; e < 12; ++e) ex[12 * s + e] = p->sensors[s].extrinsic[e];
+    std::vector<int> no_var(p->sensors.size(), -1);
+    if (cudaMemcpy(p->d_extr, ex.data(), sizeof(double) * ex.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_extr_cand, ex.data(), sizeof(double) * ex.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_sensor_var, no_var.data(), sizeof(int) * no_var.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(p->d_frames, fi.data(), sizeof(FrameInfo) * p->N, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_sensors, sd.data(), sizeof(SensorDev) * sd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_frame_sensor, p->frame_sensor.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
@@ -514,6 +682,13 @@ void pba_destroy(pba_problem* p) {
     dfree(p->d_var_frames);
     dfree(p->d_Hr);
     dfree(p->d_br);
+    dfree(p->d_sensor_var);
+    dfree(p->d_free_frames);
+    dfree(p->d_extr);
+    dfree(p->d_extr_cand);
+    dfree(p->d_Hfo);
+    dfree(p->d_Hoo);
+    dfree(p->d_bo);
     free_pair_buffers(p);
     dfree(p->raw);
     dfree(p->tex);
@@ -613,8 +788,14 @@ int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
     if (!p || !extrinsic || sensor < 0 || sensor >= (int)p->sensors.size())
         return fail(p, PBA_EINVAL, "set_extrinsic: bad argument");
     cudaSetDevice(p->device);
+    int sst = sync_offsets_to_host(p);
+    if (sst) return sst;
     pba_sensor& S = p->sensors[sensor];
     for (int e = 0; e < 12; ++e) S.extrinsic[e] = extrinsic[e];
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_extr + 12 * sensor, S.extrinsic, sizeof(double) * 12, cudaMemcpyHostToDevice,
+                                p->stream));
+    CUDA_TRY(p, cudaMemcpyAsync(p->d_extr_cand + 12 * sensor, S.extrinsic, sizeof(double) * 12,
+                                cudaMemcpyHostToDevice, p->stream));
     SensorDev sd{};
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) sd.R[3 * r + c] = (float)S.extrinsic[4 * r + c];
@@ -697,6 +878,7 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     }
     int st = ensure_points(p);
     if (st) return st;
+    if ((st = sync_offsets_to_host(p))) return st;
     drop_graph(p);
     p->pyramid_stale = true;
     free_pair_buffers(p);
@@ -781,6 +963,27 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     }
     p->n_tasks = (int)tv.size();
 
+    // pair lists by frame ((pair, role) with role 0 = source, 1 = target) and by sensor
+    const int S = (int)p->sensors.size();
+    std::vector<int> f_start(p->N + 1, 0), s_start(S + 1, 0);
+    for (int q = 0; q < m; ++q) {
+        ++f_start[pairs[2 * q] + 1];
+        ++f_start[pairs[2 * q + 1] + 1];
+        ++s_start[p->frame_sensor[pairs[2 * q]] + 1];
+    }
+    for (int k = 0; k < p->N; ++k) f_start[k + 1] += f_start[k];
+    for (int s = 0; s < S; ++s) s_start[s + 1] += s_start[s];
+    std::vector<int2> f_items(2 * (size_t)m);
+    std::vector<int> s_items(m);
+    {
+        std::vector<int> ff(f_start.begin(), f_start.end() - 1), sf(s_start.begin(), s_start.end() - 1);
+        for (int q = 0; q < m; ++q) {
+            f_items[ff[pairs[2 * q]]++] = make_int2(q, 0);
+            f_items[ff[pairs[2 * q + 1]]++] = make_int2(q, 1);
+            s_items[sf[p->frame_sensor[pairs[2 * q]]]++] = q;
+        }
+    }
+
     auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
     bool ok = alloc((void**)&p->d_ps, sizeof(PairStatic) * m) && alloc((void**)&p->d_pp, sizeof(PairPose) * m) &&
               alloc((void**)&p->d_pf, sizeof(int2) * m) && alloc((void**)&p->d_pair_Xo, sizeof(double) * 12 * m) &&
@@ -794,7 +997,12 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
               alloc((void**)&p->d_plain_acc, sizeof(float) * 96 * m) &&
               alloc((void**)&p->d_adj_partials, sizeof(float) * adjoint_partial_stride() * chunks.size()) &&
               alloc((void**)&p->d_adj_pair, sizeof(double) * adjoint_pair_stride() * m) &&
-              alloc((void**)&p->d_adj_totals, sizeof(double) * 2);
+              alloc((void**)&p->d_adj_totals, sizeof(double) * 2) &&
+              alloc((void**)&p->d_pext, sizeof(double) * 114 * m) &&
+              alloc((void**)&p->d_f_start, sizeof(int) * (p->N + 1)) &&
+              alloc((void**)&p->d_f_items, sizeof(int2) * 2 * m) &&
+              alloc((void**)&p->d_s_start, sizeof(int) * (S + 1)) &&
+              alloc((void**)&p->d_s_items, sizeof(int) * m);
     if (!ok) {
         free_pair_buffers(p);
         return fail(p, PBA_ENOMEM, "set_pairs: device allocation failed");
@@ -806,6 +1014,10 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
         CUDA_TRY(p, cudaMemcpy(p->d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(p, cudaMemcpy(p->d_tasks, tv.data(), sizeof(AsmTask) * tv.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(p, cudaMemcpy(p->d_contrib, cv.data(), sizeof(AsmContrib) * cv.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_f_start, f_start.data(), sizeof(int) * (p->N + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_f_items, f_items.data(), sizeof(int2) * 2 * m, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_s_start, s_start.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemcpy(p->d_s_items, s_items.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
     CUDA_TRY(p, cudaMemset(p->d_blocks, 0, sizeof(double) * kBlockStride * m));
     CUDA_TRY(p, cudaMemset(p->d_blocks_cand, 0, sizeof(double) * kBlockStride * m));
     const int n6 = 6 * p->N;
@@ -1145,11 +1357,9 @@ int pba_set_variables(pba_problem* p, const int32_t* frame_var, int n_vars) {
     if (!p) return PBA_EINVAL;
     cudaSetDevice(p->device);
     if (!frame_var) {  // back to the default: frame 0 fixed, every other frame free
-        drop_graph(p);
-        p->n_vars = -1;
-        p->frame_var.clear();
-        p->pyramid_stale = true;
-        return PBA_OK;
+        p->n_fv_user = -1;
+        p->fv_user.clear();
+        return rebuild_vars(p);
     }
     if (n_vars < 1 || n_vars > p->N - 1)
         return fail(p, PBA_EINVAL, "set_variables: n_vars must lie in [1, n_frames - 1]");
@@ -1164,37 +1374,189 @@ int pba_set_variables(pba_problem* p, const int32_t* frame_var, int n_vars) {
     if (!fixed) return fail(p, PBA_EINVAL, "set_variables: no frame is held fixed (the gauge would be free)");
     for (int v = 0; v < n_vars; ++v)
         if (!count[v]) return fail(p, PBA_EINVAL, "set_variables: a variable moves no frame");
-    std::vector<int> start(n_vars + 1, 0), frames(p->N - fixed);
-    for (int v = 0; v < n_vars; ++v) start[v + 1] = start[v] + count[v];
-    std::vector<int> fill(start.begin(), start.end() - 1);
-    for (int k = 0; k < p->N; ++k)
-        if (frame_var[k] >= 0) frames[fill[frame_var[k]]++] = k;
-    drop_graph(p);
-    dfree(p->d_frame_var);
-    dfree(p->d_var_start);
-    dfree(p->d_var_frames);
-    dfree(p->d_Hr);
-    dfree(p->d_br);
-    p->d_frame_var = p->d_var_start = p->d_var_frames = nullptr;
-    p->d_Hr = p->d_br = nullptr;
-    p->n_vars = -1;
-    const size_t nr = 6 * (size_t)(n_vars + 1);
-    if (cudaMalloc((void**)&p->d_frame_var, sizeof(int) * p->N) != cudaSuccess ||
-        cudaMalloc((void**)&p->d_var_start, sizeof(int) * (n_vars + 1)) != cudaSuccess ||
-        cudaMalloc((void**)&p->d_var_frames, sizeof(int) * std::max<size_t>(frames.size(), 1)) != cudaSuccess ||
-        cudaMalloc((void**)&p->d_Hr, sizeof(double) * nr * nr) != cudaSuccess ||
-        cudaMalloc((void**)&p->d_br, sizeof(double) * nr) != cudaSuccess)
-        return fail(p, PBA_ENOMEM, "set_variables: out of device memory");
-    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_var, frame_var, sizeof(int) * p->N, cudaMemcpyHostToDevice, p->stream));
-    CUDA_TRY(p, cudaMemcpyAsync(p->d_var_start, start.data(), sizeof(int) * (n_vars + 1), cudaMemcpyHostToDevice,
-                                p->stream));
-    CUDA_TRY(p, cudaMemcpyAsync(p->d_var_frames, frames.data(), sizeof(int) * frames.size(), cudaMemcpyHostToDevice,
-                                p->stream));
-    CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // the host vectors are pageable
-    p->frame_var.assign(frame_var, frame_var + p->N);
-    p->n_vars = n_vars;
-    p->n_pad_vars = ((6 * n_vars + kTile - 1) / kTile) * kTile;
-    p->pyramid_stale = true;
+    p->fv_user.assign(frame_var, frame_var + p->N);
+    p->n_fv_user = n_vars;
+    return rebuild_vars(p);
+}
+
+int pba_set_offset_free(pba_problem* p, int sensor, int is_free) {
+    if (!p || sensor < 0 || sensor >= (int)p->sensors.size())
+        return fail(p, PBA_EINVAL, "set_offset_free: bad sensor");
+    cudaSetDevice(p->device);
+    p->offset_free[sensor] = is_free ? 1 : 0;
+    return rebuild_vars(p);
+}
+
+namespace {
+
+// X [+] d on the host for one 3x4 offset: [R R(dq), R dt + t], R(dq) from the
+// unit quaternion (sqrt(1 - |dq|^2), dq), normalised (1, dq) when |dq| >= 1.
+void boxplus_host(const double X[12], const double d[6], double out[12]) {
+    double qx = d[3], qy = d[4], qz = d[5];
+    const double n2 = qx * qx + qy * qy + qz * qz;
+    double qw;
+    if (n2 < 1.0) {
+        qw = std::sqrt(1.0 - n2);
+    } else {
+        const double nn = std::sqrt(1.0 + n2);
+        qw = 1.0 / nn;
+        qx /= nn;
+        qy /= nn;
+        qz /= nn;
+    }
+    const double dR[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz),     2 * (qx * qz + qw * qy),
+                          2 * (qx * qy + qw * qz),     1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                          2 * (qx * qz - qw * qy),     2 * (qy * qz + qw * qx),     1 - 2 * (qx * qx + qy * qy)};
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)
+            out[4 * r + c] = X[4 * r] * dR[c] + X[4 * r + 1] * dR[3 + c] + X[4 * r + 2] * dR[6 + c];
+        out[4 * r + 3] = X[4 * r] * d[0] + X[4 * r + 1] * d[1] + X[4 * r + 2] * d[2] + X[4 * r + 3];
+    }
+}
+
+// Gradient of F in the box-plus chart at X from the matrix gradient G = dF/dX:
+// dt part R^T G_t; dq part 2 (W_zy - W_yz, W_xz - W_zx, W_yx - W_xy), W = R^T G_R
+// (R(dq) ~ I + 2 [dq]x).
+void tangent_host(const double X[12], const double G[12], double g[6]) {
+    double W[9];
+    for (int a = 0; a < 3; ++a) {
+        g[a] = 0.0;
+        for (int r = 0; r < 3; ++r) g[a] += X[4 * r + a] * G[4 * r + 3];
+        for (int b = 0; b < 3; ++b) {
+            W[3 * a + b] = 0.0;
+            for (int r = 0; r < 3; ++r) W[3 * a + b] += X[4 * r + a] * G[4 * r + b];
+        }
+    }
+    g[3] = 2.0 * (W[7] - W[5]);
+    g[4] = 2.0 * (W[2] - W[6]);
+    g[5] = 2.0 * (W[3] - W[1]);
+}
+
+// F and its tangent gradient with respect to sensor `sensor`'s offset set to X.
+int extrinsic_eval(pba_problem* p, int sensor, const double X[12], double* dE, double* F, double g[6]) {
+    int st = pba_set_extrinsic(p, sensor, X);
+    if (st) return st;
+    st = pba_cost_gradient(p, F, nullptr, nullptr, dE, nullptr);
+    if (st) return st;
+    double G[12];
+    CUDA_TRY(p, cudaMemcpy(G, dE + 12 * sensor, sizeof G, cudaMemcpyDeviceToHost));
+    tangent_host(X, G, g);
+    return PBA_OK;
+}
+
+}  // namespace
+
+int pba_get_extrinsic(pba_problem* p, int sensor, double* extrinsic) {
+    if (!p || !extrinsic || sensor < 0 || sensor >= (int)p->sensors.size())
+        return fail(p, PBA_EINVAL, "get_extrinsic: bad argument");
+    cudaSetDevice(p->device);
+    int st = sync_offsets_to_host(p);
+    if (st) return st;
+    for (int e = 0; e < 12; ++e) extrinsic[e] = p->sensors[sensor].extrinsic[e];
+    return PBA_OK;
+}
+
+int pba_refine_extrinsic(pba_problem* p, int sensor, int max_iters, double rel_tol, double* cost_before,
+                         double* cost_after, int32_t* iterations) {
+    int st = ready(p);
+    if (st) return st;
+    if (sensor < 0 || sensor >= (int)p->sensors.size() || max_iters < 0)
+        return fail(p, PBA_EINVAL, "refine_extrinsic: bad sensor or iteration count");
+    if (p->cfg.path != PBA_PATH_BATCHED) return fail(p, PBA_EINVAL, "refine_extrinsic needs the batched path");
+    double* dE = nullptr;
+    if (cudaMalloc((void**)&dE, sizeof(double) * 12 * p->sensors.size()) != cudaSuccess)
+        return fail(p, PBA_ENOMEM, "refine_extrinsic: out of device memory");
+    double X[12], F, g[6];
+    for (int e = 0; e < 12; ++e) X[e] = p->sensors[sensor].extrinsic[e];
+    st = extrinsic_eval(p, sensor, X, dE, &F, g);
+    if (st) {
+        cudaFree(dE);
+        return st;
+    }
+    if (cost_before) *cost_before = F;
+    // BFGS on the 6 tangent coordinates; each iterate is re-expressed in the chart
+    // at the new offset (the curvature estimate carries over to first order)
+    double Hi[36] = {0};
+    for (int a = 0; a < 6; ++a) Hi[7 * a] = 1.0;
+    bool scaled = false;
+    int it = 0;
+    for (; it < max_iters; ++it) {
+        double d[6], gn = 0.0, slope = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            d[a] = 0.0;
+            for (int b = 0; b < 6; ++b) d[a] -= Hi[6 * a + b] * g[b];
+            gn += g[a] * g[a];
+        }
+        for (int a = 0; a < 6; ++a) slope += g[a] * d[a];
+        if (!(gn > 0.0)) break;
+        if (!(slope < 0.0)) {  // not a descent direction: restart from steepest descent
+            for (int a = 0; a < 36; ++a) Hi[a] = a % 7 ? 0.0 : 1.0;
+            for (int a = 0; a < 6; ++a) d[a] = -g[a];
+            slope = -gn;
+            scaled = false;
+        }
+        double alpha = 1.0, dn = 0.0;
+        for (int a = 0; a < 6; ++a) dn += d[a] * d[a];
+        dn = std::sqrt(dn);
+        if (!scaled && dn > 0.01) alpha = 0.01 / dn;  // first step: at most 1 cm / 0.01 in the chart
+        double Xn[12], Fn = F, gnew[6];
+        bool ok = false;
+        for (int ls = 0; ls < 30; ++ls) {
+            double step[6];
+            for (int a = 0; a < 6; ++a) step[a] = alpha * d[a];
+            boxplus_host(X, step, Xn);
+            st = extrinsic_eval(p, sensor, Xn, dE, &Fn, gnew);
+            if (st) {
+                cudaFree(dE);
+                return st;
+            }
+            if (Fn <= F + 1e-4 * alpha * slope) {
+                ok = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!ok) {  // no decrease along d: keep the current offset
+            st = pba_set_extrinsic(p, sensor, X);
+            break;
+        }
+        double s[6], y[6], sy = 0.0, yy = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            s[a] = alpha * d[a];
+            y[a] = gnew[a] - g[a];
+            sy += s[a] * y[a];
+            yy += y[a] * y[a];
+        }
+        const double decrease = F - Fn;
+        for (int e = 0; e < 12; ++e) X[e] = Xn[e];
+        for (int a = 0; a < 6; ++a) g[a] = gnew[a];
+        F = Fn;
+        if (sy > 1e-300) {
+            if (!scaled) {
+                for (int a = 0; a < 36; ++a) Hi[a] = a % 7 ? 0.0 : sy / yy;
+                scaled = true;
+            }
+            // Hi <- (I - rho s y^T) Hi (I - rho y s^T) + rho s s^T
+            const double rho = 1.0 / sy;
+            double Hy[6], yHy = 0.0;
+            for (int a = 0; a < 6; ++a) {
+                Hy[a] = 0.0;
+                for (int b = 0; b < 6; ++b) Hy[a] += Hi[6 * a + b] * y[b];
+                yHy += y[a] * Hy[a];
+            }
+            for (int a = 0; a < 6; ++a)
+                for (int b = 0; b < 6; ++b)
+                    Hi[6 * a + b] += -rho * (s[a] * Hy[b] + Hy[a] * s[b]) + (rho * rho * yHy + rho) * s[a] * s[b];
+        }
+        if (decrease < rel_tol * (F + decrease)) {
+            ++it;
+            break;
+        }
+    }
+    cudaFree(dE);
+    if (st) return st;
+    if (cost_after) *cost_after = F;
+    if (iterations) *iterations = it;
     return PBA_OK;
 }
 
@@ -1205,6 +1567,8 @@ int pba_build_pyramid(pba_problem* p, int n_levels) {
         if (!p->uploaded[k]) return fail(p, PBA_ENOTREADY, "build_pyramid: frame not uploaded");
     cudaSetDevice(p->device);
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    int sst = sync_offsets_to_host(p);
+    if (sst) return sst;
     for (pba_problem* q : p->levels) pba_destroy(q);
     p->levels.clear();
     p->pyramid_stale = true;
@@ -1286,8 +1650,10 @@ int pba_build_pyramid(pba_problem* p, int n_levels) {
         if (ce != cudaSuccess) return bail(PBA_ECUDA, std::string("build_pyramid: ") + cudaGetErrorString(ce));
         if (p->poses_set && (st = pba_set_poses(q, p->d_poses, 1))) return bail(st, "build_pyramid: poses");
         if (p->M > 0 && (st = pba_set_pairs(q, p->pairs.data(), p->M))) return bail(st, "build_pyramid: pairs");
-        if (p->n_vars >= 0 && (st = pba_set_variables(q, p->frame_var.data(), p->n_vars)))
+        if (p->n_fv_user >= 0 && (st = pba_set_variables(q, p->fv_user.data(), p->n_fv_user)))
             return bail(st, "build_pyramid: variables");
+        for (int s = 0; s < (int)p->sensors.size(); ++s)
+            if (p->offset_free[s] && (st = pba_set_offset_free(q, s, 1))) return bail(st, "build_pyramid: offsets");
         prev = q;
     }
     p->pyramid_stale = false;
@@ -1312,9 +1678,15 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
         return fail(p, PBA_ENOTREADY, "optimize: frames, pairs or extrinsics changed since build_pyramid");
     for (int l = 0; l < n_levels; ++l)
         if (max_iters[l] < 0) return fail(p, PBA_EINVAL, "optimize: negative iteration count");
+    const bool was_stale = p->pyramid_stale;
+    const int S = (int)p->sensors.size();
+    double X[12];
     for (int l = n_levels - 1; l >= 0; --l) {
         pba_problem* q = l == 0 ? p : p->levels[l - 1];
         if (q != p && (st = pba_set_poses(q, p->d_poses, 1))) return fail(p, st, "optimize: " + q->err);
+        for (int s = 0; q != p && s < S; ++s)  // refined offsets travel with the poses
+            if (p->offset_free[s] && ((st = pba_get_extrinsic(p, s, X)) || (st = pba_set_extrinsic(q, s, X))))
+                return fail(p, st, "optimize: offsets");
         if ((st = pba_set_lambda(q, -1.0))) return fail(p, st, "optimize: " + q->err);
         pba_level_stats ls{};
         ls.level = l;
@@ -1332,8 +1704,12 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
             }
         }
         if (q != p && (st = pba_set_poses(p, q->d_poses, 1))) return fail(p, st, "optimize: poses");
+        for (int s = 0; q != p && s < S; ++s)
+            if (p->offset_free[s] && ((st = pba_get_extrinsic(q, s, X)) || (st = pba_set_extrinsic(p, s, X))))
+                return fail(p, st, "optimize: offsets");
         if (stats) stats[n_levels - 1 - l] = ls;
     }
+    p->pyramid_stale = was_stale;  // offsets carried between levels leave the levels' images valid
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     return PBA_OK;
 }

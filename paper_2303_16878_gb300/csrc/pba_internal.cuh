@@ -126,6 +126,21 @@ cudaError_t launch_downsample(const float* raw, const FrameInfo* frames, const i
                               const long long* out_offsets, int n, int max_coarse_px, float* out, double range_min,
                               double range_max, cudaStream_t s);
 
+// Sensor offsets as variables (pba_offset.cu).
+cudaError_t launch_offset_system(const double* blocks, const double* pair_Xo, int m, double* pext,
+                                 const int* f_start, const int2* f_items, const int* s_start, const int* s_items,
+                                 const int* frame_sensor, const int* sensor_var, int n_frames, int n_sensors,
+                                 double* Hfo, double* Hoo, double* bo, cudaStream_t s);
+cudaError_t launch_reduce_vars_offset(const double* H, const double* b, const double* Hfo, const double* Hoo,
+                                      const double* bo, const int* frame_sensor, int n_frames, const int* var_start,
+                                      const int* var_blocks, int n_vars, double* Hr, double* br, cudaStream_t s);
+cudaError_t launch_offset_step(const double* extr, const double* dx, const int* sensor_var, int n_sensors,
+                               const LmState* st, double* cand, cudaStream_t s);
+cudaError_t launch_offset_accept(const LmState* st, double* extr, const double* cand, int n_sensors,
+                                 cudaStream_t s);
+cudaError_t launch_offset_refresh(const double* extr, int n_sensors, const int2* pf, const int* frame_sensor, int m,
+                                  double* pair_Xo, SensorDev* sensors, cudaStream_t s);
+
 // Normal estimation (Sec. IV-A), in place on the normal channels of raw.
 cudaError_t launch_normals(float* raw, const FrameInfo* frames, const int* frame_ids, int n, int max_px, float scale,
                            int max_radius, double range_min, double range_max, cudaStream_t s);

@@ -329,6 +329,7 @@ class Workload:
     params: Dict                 # method configuration (weights, Huber delta, thresholds)
     frame_var: Optional[np.ndarray] = None  # pose variable per frame (-1 fixed); None: frame 0 fixed
     n_vars: int = 0
+    extrinsic_gt: Optional[List[np.ndarray]] = None  # true sensor offsets when the sensors carry perturbed ones
 
     @property
     def n_frames(self) -> int:
@@ -607,14 +608,17 @@ def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 1
                      lidar_width: int = 512, lidar_height: int = 32, vfov_up_deg: float = 16.6,
                      vfov_down_deg: float = -16.6, cam_offset=(0.10, 0.0, 0.10), seed: int = 7,
                      sigma_t: float = 0.02, sigma_r_deg: float = 1.0, coupled: bool = True,
-                     params: Optional[Dict] = None) -> Workload:
+                     tilt_deg: float = 0.0, params: Optional[Dict] = None) -> Workload:
     """A platform carrying an RGB-D camera and a 3D LiDAR (Sec. V, fusion) in
     the textured room of make_rgbd_room.
 
     Platform frame: x forward, y left, z up.  The LiDAR sits at the platform
     origin (identity offset); the camera `cam_offset` from it, looking along
     the platform x axis.  Platform poses: n_poses points near the room centre
-    at 1.2-1.3 m height, heading towards the +y wall +- 15 deg.  Frames 0..n-1
+    at 1.2-1.3 m height, heading towards the +y wall +- 15 deg, pitched by up
+    to 3 deg, plus (tilt_deg > 0) roll and pitch of up to +-tilt_deg (the
+    rotational diversity under which an offset's translation is observable:
+    with rotations about one axis only, its component along that axis is not).  Frames 0..n-1
     are the camera's, n..2n-1 the LiDAR's; frames k and n + k were captured at
     platform pose k.  Pairs: camera (i, j), j - i <= 3; LiDAR (n + i, n + j)
     for all i < j.  With `coupled`, frame_var ties frames k and n + k to one
@@ -634,6 +638,9 @@ def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 1
         th = 2 * math.pi * k / max(n_poses, 1)
         yaw = math.pi / 2 + rng.uniform(-0.26, 0.26)
         plat[k, :, :3] = rot_z(yaw) @ rot_y(rng.uniform(-0.05, 0.05))
+        if tilt_deg > 0:
+            tr = np.random.default_rng(2500 + seed + 31 * k).uniform(-1.0, 1.0, 2) * math.radians(tilt_deg)
+            plat[k, :, :3] = plat[k, :, :3] @ rot_y(tr[0]) @ rot_axis_angle((1, 0, 0), tr[1])
         plat[k, :, 3] = [0.4 * math.cos(th), 0.4 * math.sin(th) - 0.3, 1.2 + rng.uniform(0.0, 0.1)]
     chans = []
     for k in range(n_poses):
@@ -841,11 +848,13 @@ def _hall_scene(seed: int) -> Scene:
     return Scene(boxes)
 
 
-def _hall_path(n: int, seed: int, height: float = 1.4) -> np.ndarray:
+def _hall_path(n: int, seed: int, height: float = 1.4, tilt_deg: float = 0.0) -> np.ndarray:
     """Platform poses (x forward, y left, z up) along a closed Catmull-Rom
     spline through the hall's four rooms and its doorways, resampled to n
     poses equally spaced in arc length; heading along the path with smooth
-    yaw (+-15 deg) and pitch (-8..+4 deg) wobble, height +- 0.1 m."""
+    yaw (+-15 deg) and pitch (-8..+4 deg) wobble, height +- 0.1 m; with
+    tilt_deg > 0 a further smooth roll and pitch of amplitude tilt_deg (a
+    hand-held platform)."""
     rng = np.random.default_rng(seed)
     way = np.array([[-7.0, -3.0], [-5.4, -1.2], [-5.4, 1.5], [-4.0, 3.2], [0.5, 3.5], [3.0, 2.6], [5.0, 2.6],
                     [6.6, 1.5], [6.6, -1.3], [5.0, -3.0], [0.0, -3.2], [-2.0, -2.9], [-4.5, -2.9]])
@@ -872,6 +881,10 @@ def _hall_path(n: int, seed: int, height: float = 1.4) -> np.ndarray:
         yaw = math.atan2(tang[k, 1], tang[k, 0]) + math.radians(15.0) * math.sin(3 * a + ph[0])
         pitch = math.radians(-2.0 + 6.0 * math.sin(5 * a + ph[1]))
         poses[k, :, :3] = rot_z(yaw) @ rot_y(-pitch)
+        if tilt_deg > 0:
+            tilt = math.radians(tilt_deg)
+            poses[k, :, :3] = poses[k, :, :3] @ rot_y(tilt * math.sin(7 * a + ph[0])) @ \
+                rot_axis_angle((1, 0, 0), tilt * math.sin(11 * a + ph[1]))
         poses[k, :, 3] = [xy[k, 0], xy[k, 1], height + 0.1 * math.sin(4 * a + ph[2])]
     return poses
 
@@ -1033,3 +1046,125 @@ def make_lidar_street_graph(n_frames: int = 500, width: int = 2048, height: int 
     return Workload(f"lidar-street-graph-{n_frames}x{height}x{width}", [sensor],
                     np.zeros(n_frames, dtype=np.int32), chans, poses, init,
                     np.array(pairs, dtype=np.int32).reshape(-1, 2), prm)
+
+
+def offset_error(Xa: np.ndarray, Xb: np.ndarray) -> Tuple[float, float]:
+    """Translation [m] and rotation [deg] of Xa^-1 Xb (3x4 rigid transforms)."""
+    R = Xa[:, :3].T @ Xb[:, :3]
+    t = Xa[:, :3].T @ (Xb[:, 3] - Xa[:, 3])
+    return float(np.linalg.norm(t)), math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R) - 1.0) / 2.0))))
+
+
+def make_joint_hall(n_lidar: int = 300, lidar_width: int = 1024, lidar_height: int = 128,
+                    vfov_up_deg: float = 45.0, vfov_down_deg: float = -45.0, cam_width: int = 640,
+                    cam_height: int = 480, f: float = 525.0, rate: int = 2, cam_offset=(0.10, 0.0, 0.10),
+                    offset_error_m: float = 0.02, offset_error_deg: float = 0.5, seed: int = 5,
+                    sigma_t: float = 0.02, sigma_r_deg: float = 1.0, tilt_deg: float = 10.0, device="cuda",
+                    params: Optional[Dict] = None) -> Workload:
+    """Joint LiDAR + RGB-D platform in the hall (Sec. V, fusion): n_lidar LiDAR
+    frames (128 x 1024, vfov +-45 deg, the platform origin) and rate x n_lidar
+    camera frames (640 x 480, `cam_offset` ahead / above, looking forward)
+    along the hall's spline path, hand-held (roll and pitch of up to tilt_deg,
+    so that the offset's translation is observable); camera frame rate k and
+    LiDAR frame k share a platform pose.  The camera's offset given to the problem (the sensor's
+    extrinsic) is the true one composed with a seeded error of
+    offset_error_m / offset_error_deg; extrinsic_gt holds the true offsets.
+    Frames: cameras first, then LiDARs; frame_var ties camera rate k and
+    LiDAR k and holds the first platform pose fixed.  Pairs: camera (i, j)
+    by the Sec. IV-B rule (30 deg, 1 m, overlap > 1/3) plus consecutive
+    frames; LiDAR (i, j), j - i <= 4, overlap > 0.3.  Channels are torch
+    tensors on `device`.  Seeds: scene 1000 + seed, path 2000 + seed,
+    perturbation 3000 + seed, offset error 4000 + seed."""
+    import torch
+    n_cam = rate * n_lidar
+    scene = _hall_scene(1000 + seed)
+    st = _scene_tensors(scene, device)
+    cam = pinhole_sensor(cam_width, cam_height, f, (cam_width - 1) / 2.0, (cam_height - 1) / 2.0)
+    Xc = np.zeros((3, 4))
+    Xc[:, :3] = CAMERA_ON_PLATFORM
+    Xc[:, 3] = cam_offset
+    lidar = spherical_sensor(lidar_width, lidar_height, vfov_up_deg, vfov_down_deg)
+    plat = _hall_path(n_cam, 2000 + seed, height=1.5, tilt_deg=tilt_deg)
+    rays_c = torch.as_tensor(_pixel_rays(cam)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    rays_l = torch.as_tensor(_pixel_rays(lidar)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    chans = [quantize_fp16_t(render_t(scene, cam, compose(plat[k], Xc), 0.5, 5.0, device, rays_c, st))
+             for k in range(n_cam)]
+    chans += [quantize_fp16_t(render_t(scene, lidar, plat[rate * k], 0.5, 12.0, device, rays_l, st))
+              for k in range(n_lidar)]
+    rng = np.random.default_rng(4000 + seed)
+    ax = rng.normal(size=3)
+    d = rng.normal(size=3)
+    err = np.zeros((3, 4))
+    err[:, :3] = rot_vec(math.radians(offset_error_deg) * ax / np.linalg.norm(ax))
+    err[:, 3] = offset_error_m * d / np.linalg.norm(d)
+    cam.extrinsic = compose(Xc, err)
+    init_plat = perturb_poses(plat, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
+    poses = np.concatenate([plat, plat[::rate]])
+    init = np.concatenate([init_plat, init_plat[::rate]])
+    pairs = []
+    for i in range(n_cam):
+        cand = [j for j in range(i + 1, n_cam) if np.linalg.norm(init[i, :, 3] - init[j, :, 3]) < 1.0 and
+                _pose_angle_deg(init[i], init[j]) < 30.0]
+        ratios = overlap_ratios_t(chans[i], [chans[j] for j in cand], cam, compose(plat[i], Xc),
+                                  np.array([compose(plat[j], Xc) for j in cand]).reshape(-1, 3, 4), rays_c)
+        pairs += [(i, j) for j, r in zip(cand, ratios) if r > 1.0 / 3.0]
+        if i + 1 < n_cam and (i, i + 1) not in pairs:
+            pairs.append((i, i + 1))
+    for i in range(n_lidar):
+        near = list(range(i + 1, min(n_lidar, i + 5)))
+        ratios = overlap_ratios_t(chans[n_cam + i], [chans[n_cam + j] for j in near], lidar, plat[rate * i],
+                                  plat[[rate * j for j in near]].reshape(-1, 3, 4), rays_l)
+        pairs += [(n_cam + i, n_cam + j) for j, r in zip(near, ratios) if r > 0.3]
+    fv = np.array([k - 1 for k in range(n_cam)] + [rate * k - 1 for k in range(n_lidar)], dtype=np.int32)
+    prm = default_params(range_min=0.5, range_max=12.0)
+    if params:
+        prm.update(params)
+    ident = IDENTITY_3x4.copy()
+    return Workload(f"joint-hall-{n_lidar}x{lidar_height}x{lidar_width}+{n_cam}x{cam_width}x{cam_height}",
+                    [cam, lidar], np.array([0] * n_cam + [1] * n_lidar, dtype=np.int32), chans, poses, init,
+                    np.array(sorted(pairs), dtype=np.int32).reshape(-1, 2), prm, fv, n_cam - 1, [Xc, ident])
+
+
+def make_street_batch(n_problems: int = 16, sizes=(50, 400), width: int = 1024, height: int = 64, seed: int = 6,
+                      device="cuda", params: Optional[Dict] = None):
+    """n_problems independent LiDAR street problems (sizes drawn uniformly in
+    `sizes`, seed 3005 + seed) concatenated into one workload: frames of
+    problem k follow those of problem k - 1, pairs stay within a problem
+    ((i, j), j - i <= 3, overlap > 0.3), and the first frame of every problem
+    is held fixed (frame_var), so the problems share nothing but the launch.
+    Returns (workload, list of (first frame, n_frames) per problem)."""
+    import torch
+    rng = np.random.default_rng(3005 + seed)
+    ns = [int(x) for x in rng.integers(sizes[0], sizes[1] + 1, n_problems)]
+    sensor = spherical_sensor(width, height, 16.6, -16.6)
+    rays = torch.as_tensor(_pixel_rays(sensor)[0].reshape(-1, 3), dtype=torch.float64, device=device)
+    chans, poses, init, pairs, fv, spans = [], [], [], [], [], []
+    g = torch.Generator(device=device)
+    g.manual_seed(4000 + seed)
+    n_var = 0
+    for k, n in enumerate(ns):
+        base = len(chans)
+        P = _street_trajectory(n, 1.0, 2000 + 100 * seed + k)
+        scene = _street_scene(1000 + 100 * seed + k, 0.0, (n - 1) * 1.0)
+        st = _scene_tensors(scene, device)
+        for f in range(n):
+            c = render_t(scene, sensor, P[f], 1.0, 80.0, device, rays, st)
+            keep = torch.rand((height, width), generator=g, device=device) >= 0.05
+            chans.append(quantize_fp16_t(torch.where(keep[..., None], c, torch.zeros_like(c))))
+        for i in range(n):
+            near = list(range(i + 1, min(n, i + 4)))
+            ratios = overlap_ratios_t(chans[base + i], [chans[base + j] for j in near], sensor, P[i], P[near], rays)
+            pairs += [(base + i, base + j) for j, r in zip(near, ratios) if r > 0.3]
+        poses.append(P)
+        init.append(perturb_poses(P, 0.10, math.radians(0.5), 3000 + 100 * seed + k))
+        fv += [-1] + list(range(n_var, n_var + n - 1))
+        n_var += n - 1
+        spans.append((base, n))
+    prm = default_params(w_depth=0.1, huber_delta=0.2, occ_abs=0.3, occ_rel=0.05, z_min=0.5,
+                         range_min=1.0, range_max=80.0)
+    if params:
+        prm.update(params)
+    w = Workload(f"street-batch-{n_problems}x{height}x{width}", [sensor], np.zeros(len(chans), dtype=np.int32),
+                 chans, np.concatenate(poses), np.concatenate(init), np.array(pairs, dtype=np.int32).reshape(-1, 2),
+                 prm, np.array(fv, dtype=np.int32), n_var)
+    return w, spans

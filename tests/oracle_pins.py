@@ -43,6 +43,8 @@ PIN_TOL = {
     "coarse_to_fine": 0.5,
     "tied_gradient": 1e-4,  # central differences of F ~ 900 at h = 2e-8: roundoff eps F / h ~ 1e-5 absolute
     "variables_reduce_to_gauge": 1e-12,
+    "offset_jacobian_fd": 1e-6,
+    "offset_gradient_fd": 1e-4,  # central differences of F at h = 2e-8 (roundoff eps F / h)
 }
 
 
@@ -672,6 +674,91 @@ def pin_variables_reduce_to_gauge(O, lib, w):
     return float(np.abs(a - b).max() / np.abs(a).max())
 
 
+# ---------------------------------------------------------------- the sensor offset as a variable (R23)
+
+def _with_offset(w):
+    from paper_2303_16878_gb300 import synth
+    return synth.with_extrinsic(w, synth.offset_transform(0.3, 20.0, seed=9))
+
+
+def _sensor_with(s, X):
+    import dataclasses
+    return dataclasses.replace(s, extrinsic=np.asarray(X, dtype=np.float64).reshape(3, 4))
+
+
+def pin_offset_jacobian_fd(O, lib, w, n_points=200, h=1e-6, seed=3):
+    """J_o = (J_i + J_j) A_o against central differences of e under X_o [+] d
+    (points rebuilt from the same pixels with the perturbed offset), grad_mode 1."""
+    wx = _with_offset(w)
+    params = dict(wx.params, grad_mode=1)
+    s = wx.sensors[0]
+    Xo = np.asarray(s.extrinsic)
+    rng = np.random.default_rng(seed)
+    worst, used = 0.0, 0
+    i, j = 0, 1
+    pts, _ = O.frame_points(s, params, wx.channels[i], lib=lib)
+    Xi, Xj = wx.poses_init[i], wx.poses_init[j]
+    shifted = {}
+    for a in range(6):
+        for sg in (1, -1):
+            d = np.zeros(6)
+            d[a] = sg * h
+            sp = _sensor_with(s, O.boxplus(Xo, d, lib=lib))
+            shifted[(a, sg)] = (sp, O.frame_points(sp, params, wx.channels[i], lib=lib)[0])
+    for k in rng.permutation(len(pts))[:n_points]:
+        r = O.point_residual(s, params, wx.channels[j], Xi, Xj, pts[k], lib=lib)
+        if not r["valid"] or r["flag"]:
+            continue
+        Jo = O.offset_jacobian(Xo, r["Ji"], r["Jj"])
+        Jf, ok = np.zeros((5, 6)), True
+        for a in range(6):
+            ev = []
+            for sg in (1, -1):
+                sp, pp = shifted[(a, sg)]
+                ev.append(O.point_residual(sp, params, wx.channels[j], Xi, Xj, pp[k], lib=lib))
+            if not all(e["valid"] for e in ev):
+                ok = False
+                break
+            Jf[:, a] = (ev[0]["e"] - ev[1]["e"]) / (2 * h)
+        if not ok:
+            continue
+        used += 1
+        worst = max(worst, float(np.abs(Jf - Jo).max() / max(np.abs(Jf).max(), 1e-12)))
+    assert used >= 20, "too few usable points for the finite-difference check"
+    return worst
+
+
+def pin_offset_gradient_fd(O, lib, w):
+    """dF / d d_o (central differences of F over all pairs under X_o [+] d)
+    equals 2 sum_pairs b_o (pair_offset_blocks), grad_mode 1."""
+    wx = _with_offset(w)
+    params = dict(wx.params, grad_mode=1)
+    s = wx.sensors[0]
+    Xo = np.asarray(s.extrinsic)
+    bo = sum(O.pair_offset_blocks(s, params, wx.channels[i], wx.channels[j], wx.poses_init[i], wx.poses_init[j],
+                                  lib=lib)["b_o"] for i, j in wx.pairs.tolist())
+    worst = 0.0
+    for a in range(6):
+        done = False
+        for h in (2e-8, 1e-8, 5e-9):
+            Fs, cnt = [], []
+            for sg in (1, -1):
+                d = np.zeros(6)
+                d[a] = sg * h
+                sp = _sensor_with(s, O.boxplus(Xo, d, lib=lib))
+                r = O.linearize([sp], wx.frame_sensor, wx.channels, wx.poses_init, wx.pairs, params,
+                                want_system=False, want_pairs=True, lib=lib)
+                Fs.append(r["cost"])
+                cnt.append(r["pair_count"])
+            if np.array_equal(cnt[0], cnt[1]):
+                g = (Fs[0] - Fs[1]) / (2 * h)
+                worst = max(worst, abs(g - 2 * bo[a]) / (np.abs(2 * bo).max() + 1e-30))
+                done = True
+                break
+        assert done, "validity changed under every finite-difference step"
+    return worst
+
+
 def all_pins(O, lib, room, street):
     """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
     return {
@@ -696,4 +783,6 @@ def all_pins(O, lib, room, street):
         "pyramid_projection": pin_pyramid_projection(O, lib),
         "downsample_closed_forms": pin_downsample_closed_forms(O, lib),
         "coarse_to_fine": pin_coarse_to_fine(O, lib),
+        "offset_jacobian_fd": pin_offset_jacobian_fd(O, lib, room),
+        "offset_gradient_fd": pin_offset_gradient_fd(O, lib, room),
     }

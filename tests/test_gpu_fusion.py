@@ -167,3 +167,87 @@ def test_convergence_basin_coupled_and_consecutive(fusion):
         assert s[mode][0] == res["n_dirs"], (mode, res)
     assert sum(s["coupled"]) >= sum(s["rgbd"]), res
     assert sum(s["consecutive"]) >= sum(s["rgbd"]), res
+
+
+# ------------------------------------------------------------------ the camera offset as an LM variable (R23)
+
+def _offset_workload():
+    import dataclasses
+    from paper_2303_16878_gb300 import synth
+    w = synth.make_fusion_room(tilt_deg=12.0)
+    true = np.asarray(w.sensors[0].extrinsic)
+    err = np.zeros((3, 4))
+    err[:, :3] = synth.rot_vec(np.radians(0.5) * np.array([0.6, -0.64, 0.48]))
+    err[:, 3] = 0.02 * np.array([-0.48, 0.8, 0.36])
+    bad = dataclasses.replace(w.sensors[0], extrinsic=synth.compose(true, err))
+    return dataclasses.replace(w, sensors=[bad, w.sensors[1]]), true
+
+
+def _rot_angle(A, B):
+    return float(np.arccos(np.clip((np.trace(A[:, :3].T @ B[:, :3]) - 1) / 2, -1, 1)))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_free_offset_damped_step_matches_oracle(oracle_lib, solver):
+    """A strongly damped step with the camera offset free: poses and offset as
+    the oracle's (offset blocks per point, R23) to 1e-4 of the step."""
+    w, _ = _offset_workload()
+    lin = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
+    H, b = oracle_lib.offset_system(w, w.sensors, w.poses_init, lin, [0])
+    blocks_var = np.concatenate([w.frame_var, [w.n_vars]])
+    S = oracle_lib.selection(blocks_var, w.n_vars + 1)
+    lam = 10.0 * float(np.diag(S.T @ H @ S).max())
+    ref = oracle_lib.lm_iteration_offsets(w, w.poses_init, w.sensors, lam, [0])
+    assert ref["accepted"]
+    p = make(w, texel=0, solver=solver)
+    p.set_offset_free(0)
+    p.linearize()
+    st = p.solve_step(lam)
+    assert st["accepted"] and abs(st["new_cost"] - ref["new_cost"]) <= TOL_COST * ref["new_cost"]
+    step = np.abs(ref["candidate"] - w.poses_init).max()
+    assert np.abs(p.get_poses() - ref["candidate"]).max() <= 1e-4 * step + 1e-12
+    Xo_ref = oracle_lib._extrinsic_of(ref["candidate_sensors"][0])
+    ostep = np.abs(Xo_ref - np.asarray(w.sensors[0].extrinsic)).max()
+    assert np.abs(p.get_extrinsic(0) - Xo_ref).max() <= 1e-4 * ostep + 1e-12
+    assert np.array_equal(p.get_extrinsic(1), np.asarray(w.sensors[1].extrinsic))
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_free_offset_lm_matches_oracle_and_recovers_the_offset(oracle_lib, solver):
+    """Eight LM iterations with poses and the camera offset free (camera and
+    LiDAR frames of one platform pose tied): poses and offset within 1e-4 m /
+    1e-5 rad of the oracle's, and the offset within 1 cm / 0.1 deg of the true
+    one from 2 cm / 0.5 deg (the platform tilts by up to 12 deg, so the
+    offset's translation is observable)."""
+    from paper_2303_16878_gb300 import synth
+    w, true = _offset_workload()
+    P, sens, lam = w.poses_init.copy(), list(w.sensors), None
+    for _ in range(8):
+        r = oracle_lib.lm_iteration_offsets(w, P, sens, lam, [0])
+        P, sens, lam = r["poses"], r["sensors"], r["lam"]
+    p = make(w, texel=0, solver=solver)
+    p.set_offset_free(0)
+    for _ in range(8):
+        p.iterate()
+    got = p.get_poses()
+    for k in range(w.n_frames):
+        assert np.linalg.norm(got[k][:, 3] - P[k][:, 3]) <= 1e-4 and _rot_angle(got[k], P[k]) <= 1e-5
+    Xo, Xo_ref = p.get_extrinsic(0), oracle_lib._extrinsic_of(sens[0])
+    assert np.linalg.norm(Xo[:, 3] - Xo_ref[:, 3]) <= 1e-4 and _rot_angle(Xo, Xo_ref) <= 1e-5
+    t1, r1 = synth.offset_error(true, Xo)
+    assert t1 < 0.01 and r1 < 0.1, (t1, r1)
+
+
+def test_refine_extrinsic_recovers_the_camera_offset():
+    """At the true poses of the tilted platform, a camera offset off by 2 cm /
+    0.5 deg is refined by BFGS with the adjoint gradient to within 1 cm /
+    0.1 deg of the true one, the LiDAR's offset untouched."""
+    from paper_2303_16878_gb300 import synth
+    w, true = _offset_workload()
+    p = make(w, poses=w.poses_gt, texel=0)
+    t0, r0 = synth.offset_error(true, p.get_extrinsic(0))
+    out = p.refine_extrinsic(0, max_iters=40, rel_tol=1e-9)
+    t1, r1 = synth.offset_error(true, p.get_extrinsic(0))
+    assert out["cost_after"] < out["cost_before"]
+    assert t0 > 0.019 and r0 > 0.49 and t1 < 0.01 and r1 < 0.1, (t0, r0, t1, r1, out)
+    assert np.array_equal(p.get_extrinsic(1), np.asarray(w.sensors[1].extrinsic))

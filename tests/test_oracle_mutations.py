@@ -31,6 +31,10 @@ MUTATIONS = {
                                 "for (int a = 0; a < 3; ++a) tmp[a] = q[a] + to[a];"),
     "bilinear_weight_swapped": ("const double w[4] = {(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b};",
                                 "const double w[4] = {(1 - a) * (1 - b), (1 - a) * b, a * (1 - b), a * b};"),
+    "offset_map_translation_factor": ("A[6 * r + 3 + c] = 2.0 * x[r];", "A[6 * r + 3 + c] = x[r];"),
+    "offset_jacobian_drops_target": ("s += (Ji[6 * r + k] + Jj[6 * r + k]) * A[6 * k + c];",
+                                     "s += Ji[6 * r + k] * A[6 * k + c];"),
+    "offset_map_rotation_transposed": ("A[6 * r + c] = Ro[3 * r + c];", "A[6 * r + c] = Ro[3 * c + r];"),
 }
 
 
@@ -56,7 +60,9 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("single_channel", lambda: P.pin_single_channel(oracle_lib, lib)),
                     ("cholesky", lambda: P.pin_cholesky(oracle_lib, lib)),
                     ("extrinsic_equivalence", lambda: P.pin_extrinsic_equivalence(oracle_lib, lib, room3)),
-                    ("jacobian_fd_extrinsic", lambda: P.pin_jacobian_fd_extrinsic(oracle_lib, lib, room3))]:
+                    ("jacobian_fd_extrinsic", lambda: P.pin_jacobian_fd_extrinsic(oracle_lib, lib, room3)),
+                    ("offset_jacobian_fd", lambda: P.pin_offset_jacobian_fd(oracle_lib, lib, room3)),
+                    ("offset_gradient_fd", lambda: P.pin_offset_gradient_fd(oracle_lib, lib, room3))]:
         try:
             err = fn()
         except (AssertionError, ValueError, ArithmeticError, Exception):

@@ -209,3 +209,11 @@ def test_other_branch_only_touches_flagged_rejections(oracle_lib, street3):
                 assert a["flag"]
                 forced += 1
     assert forced > 0
+
+
+def test_offset_jacobian_matches_finite_differences(oracle_lib, room3):
+    assert P.pin_offset_jacobian_fd(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["offset_jacobian_fd"]
+
+
+def test_offset_gradient_is_twice_b_o(oracle_lib, room3):
+    assert P.pin_offset_gradient_fd(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["offset_gradient_fd"]
