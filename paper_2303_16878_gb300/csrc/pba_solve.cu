@@ -129,7 +129,8 @@ __global__ void k_damp(const double* __restrict__ H, const double* __restrict__ 
 // tiles of 32 x 32: factor the diagonal tile, solve the panel below it,
 // update the trailing lower triangle.
 
-// Diagonal tile, 256 threads (thread (c, g) owns column c, rows g, g+8, g+16,
+// Diagonal tile (used for FP64, where one warp's long dependent FP64 chains
+// would serialise the tile), 256 threads (thread (c, g) owns column c, rows g, g+8, g+16,
 // g+24).  The trailing update of pivot j uses the unscaled column:
 // T[r][c] -= T[r][j] T[c][j] / T[j][j], so each step needs one barrier and one
 // reciprocal, computed by the owner of the next pivot right after its own
@@ -195,6 +196,68 @@ __global__ void __launch_bounds__(256) k_potrf(F* __restrict__ A, int n_pad, int
             A[base + (long long)c * n_pad + r] = l;
         }
         if (Dk) Dk[r * kTile + c] = r >= c ? R[r][c] * sqrt(inv_piv[r]) : F(0);
+    }
+}
+
+// Diagonal tile by one warp (FP32): lane i holds row i of the tile in registers.
+// Step j: L[j][j] = sqrt(T[j][j]); L[i][j] = T[i][j] / L[j][j] (i > j); the
+// rank-1 update T[i][k] -= L[i][j] L[k][j] (j < k <= i) takes L[k][j] from lane
+// k by a shuffle.  Then lane c forms column c of L^-1 by forward substitution
+// on e_c, reading L from shared memory (the same entry for every lane at each
+// step: broadcasts).  Loads and stores go through shared memory so that global
+// accesses are row-contiguous; L^T is written into the upper tile.
+template <typename F>
+__global__ void __launch_bounds__(32) k_potrf_warp(F* __restrict__ A, int n_pad, int k, LmState* st,
+                                                   F* __restrict__ Dinv) {
+    if (st->chol_fail) return;
+    __shared__ F S[kTile][kTile + 1];
+    const int lane = threadIdx.x;
+    const long long base = (long long)(k * kTile) * n_pad + k * kTile;
+    for (int r = 0; r < kTile; ++r) S[r][lane] = A[base + (long long)r * n_pad + lane];
+    __syncwarp();
+    F a[kTile];
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) a[c] = S[lane][c];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kTile; ++j) {
+        const F piv = __shfl_sync(0xffffffffu, a[j], j);
+        bad = bad || !(piv > F(0));
+        const F ljj = sqrt(piv);
+        const F lij = lane > j ? a[j] / ljj : (lane == j ? ljj : F(0));
+        a[j] = lij;
+#pragma unroll
+        for (int c = j + 1; c < kTile; ++c) {
+            const F lcj = __shfl_sync(0xffffffffu, lij, c);
+            if (c <= lane) a[c] -= lij * lcj;
+        }
+    }
+    if (bad) {
+        if (lane == 0) st->chol_fail = 1;
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) S[lane][c] = c <= lane ? a[c] : F(0);
+    __syncwarp();
+    // L into the lower tile and L^T into the upper tile, row-contiguous
+    for (int r = 0; r < kTile; ++r) A[base + (long long)r * n_pad + lane] = lane <= r ? S[r][lane] : S[lane][r];
+    if (Dinv) {
+        // column `lane` of L^-1: x_i = (delta_{i,lane} - sum_{lane <= m < i} L[i][m] x_m) / L[i][i]
+        F x[kTile];
+#pragma unroll
+        for (int i = 0; i < kTile; ++i) {
+            F s = i == lane ? F(1) : F(0);
+#pragma unroll
+            for (int m = 0; m < i; ++m) s -= S[i][m] * x[m];
+            x[i] = i >= lane ? s / S[i][i] : F(0);
+        }
+        __syncwarp();
+        // Dinv row-major: Dinv[i][lane] = x_i
+        F* Dk = Dinv + (long long)k * kTile * kTile;
+#pragma unroll
+        for (int i = 0; i < kTile; ++i) S[i][lane] = x[i];
+        __syncwarp();
+        for (int r = 0; r < kTile; ++r) Dk[r * kTile + lane] = S[r][lane];
     }
 }
 
@@ -576,7 +639,7 @@ cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, i
     const int nt = n_pad / kTile;
     const dim3 blk(kTile, kTile), blk8(kTile, 8);
     for (int k = 0; k < nt; ++k) {
-        k_potrf<float><<<1, blk8, 0, s>>>(w.A32, n_pad, k, st, w.D32);
+        k_potrf_warp<float><<<1, 32, 0, s>>>(w.A32, n_pad, k, st, w.D32);
         ++nl;
         const int rest = nt - k - 1;
         if (rest > 0) {
