@@ -43,6 +43,8 @@ struct pba_problem {
     // device buffers (problem lifetime)
     float* raw = nullptr;
     void* tex = nullptr;
+    float4* gtex = nullptr;  // central differences per pixel (LinParams::gtex)
+    int max_frame_px = 0;
     float4* pts_pg = nullptr;
     float4* pts_n = nullptr;
     int* pts_pix = nullptr;
@@ -303,7 +305,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px));
         *nl += 3;
     }
     if (speculative) {
@@ -345,7 +347,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px));
         *nl += 3;
     }
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
@@ -393,7 +395,7 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
                                    p->cfg.range_min, p->cfg.range_max, p->stream));
     CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
                             p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
-                            p->stream));
+                            p->stream, p->gtex, p->max_frame_px));
     // the id list is pageable host memory: the synchronisation also makes sure
     // the copy has consumed it
     std::vector<int> before = p->n_points;
@@ -571,6 +573,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
     bool ok = alloc((void**)&p->raw, sizeof(float) * 5 * (size_t)p->total_px) &&
               alloc(&p->tex, texel_bytes * (size_t)p->total_px) &&
+              alloc((void**)&p->gtex, sizeof(float4) * 3 * (size_t)p->total_px) &&
               alloc((void**)&p->pts_pg, sizeof(float4) * (size_t)p->total_px) &&
               alloc((void**)&p->pts_n, sizeof(float4) * (size_t)p->total_px) &&
               alloc((void**)&p->pts_pix, sizeof(int) * (size_t)p->total_px) &&
@@ -664,6 +667,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->prm.occ_rel = (float)cfg->occ_rel;
     p->prm.z_min = (float)cfg->z_min;
     p->prm.grad_mode = cfg->grad_mode;
+    p->prm.gtex = p->gtex;
+    for (const pba_sensor& S : p->sensors) p->max_frame_px = std::max(p->max_frame_px, S.width * S.height);
     p->grid_full = linearize_grid(cfg->texel_precision, true, 0);
     p->grid_cost = linearize_grid(cfg->texel_precision, false, 0);
     *out = p;
@@ -692,6 +697,7 @@ void pba_destroy(pba_problem* p) {
     free_pair_buffers(p);
     dfree(p->raw);
     dfree(p->tex);
+    dfree(p->gtex);
     dfree(p->pts_pg);
     dfree(p->pts_n);
     dfree(p->pts_pix);
@@ -818,7 +824,7 @@ int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
                                     p->stream));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, (int)ids.size(),
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, p->stream));
+                                p->cfg.range_min, p->cfg.range_max, p->stream, p->gtex, p->max_frame_px));
     }
     // per-pair copies of the extrinsic
     if (p->M > 0) {

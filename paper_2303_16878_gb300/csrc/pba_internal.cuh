@@ -81,6 +81,10 @@ struct LinParams {
     float occ_abs, occ_rel;
     float z_min;
     int grad_mode;
+    // per pixel of every frame: the central differences of the Supp. at the pixel,
+    // (d/du, d/dv) of (g, d, n_x, n_y, n_z), 12 floats (3 float4, the last two 0);
+    // zero where the pixel is not usable
+    const float4* gtex;
 };
 
 // Device-side Levenberg-Marquardt state of one problem.
@@ -148,7 +152,7 @@ cudaError_t launch_normals(float* raw, const FrameInfo* frames, const int* frame
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors,
                         const int* frame_ids, int n, int texel_precision, void* texels,
                         float4* pts_pg, float4* pts_n, int* pts_pix, int* n_points, double range_min,
-                        double range_max, cudaStream_t s);
+                        double range_max, cudaStream_t s, float4* gtex = nullptr, int max_px = 0);
 
 cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
                              PairPose* out, cudaStream_t s);

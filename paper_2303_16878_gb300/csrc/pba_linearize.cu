@@ -105,8 +105,9 @@ template <int TEXEL>
 __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int model, float fx, float fy, int W,
                                                bool wrap, const float (&M)[9], const float (&om)[5],
                                                const float4* __restrict__ pg, const float4* __restrict__ pn,
-                                               const void* __restrict__ tex, long long tex_off, int grad_mode,
-                                               float (&Hacc)[21], float (&bacc)[6]) {
+                                               const void* __restrict__ tex, const float4* __restrict__ gtex,
+                                               long long tex_off, int grad_mode, float (&Hacc)[21],
+                                               float (&bacc)[6]) {
     float e[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) e[c] = Q[c][slot];
@@ -119,40 +120,37 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
 
     int cm1, cc, cp1, cp2;
     stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
-    tex = TEXEL == 1 ? (const void*)(reinterpret_cast<const Tex16*>(tex) + tex_off)
-                     : (const void*)(reinterpret_cast<const Tex32*>(tex) + tex_off);
-    const int rr0 = r0 * W, rm1 = rr0 - W, rp1 = rr0 + W, rp2 = rp1 + W;
+    const int rr0 = r0 * W, rp1 = rr0 + W;
     float gu[5], gv[5];
-    {
+    if (grad_mode == 0) {
+        // central differences at the taps A, B, C, D (precomputed per pixel), interpolated
+        const float4* G = gtex + 3 * tex_off;
+        const int tap[4] = {rr0 + cc, rr0 + cp1, rp1 + cc, rp1 + cp1};
+        const float wt[4] = {(1.f - a) * (1.f - b), a * (1.f - b), (1.f - a) * b, a * b};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) gu[c] = gv[c] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float4 g0 = __ldg(G + 3 * tap[t]), g1 = __ldg(G + 3 * tap[t] + 1), g2 = __ldg(G + 3 * tap[t] + 2);
+            const float u[5] = {g0.x, g0.y, g0.z, g0.w, g1.x}, vv[5] = {g1.y, g1.z, g1.w, g2.x, g2.y};
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                gu[c] = fmaf(wt[t], u[c], gu[c]);
+                gv[c] = fmaf(wt[t], vv[c], gv[c]);
+            }
+        }
+    } else {
+        tex = TEXEL == 1 ? (const void*)(reinterpret_cast<const Tex16*>(tex) + tex_off)
+                         : (const void*)(reinterpret_cast<const Tex32*>(tex) + tex_off);
         float A[5], B[5], C[5], D[5];
         channels(load_texel<TEXEL>(tex, rr0 + cc), A);
         channels(load_texel<TEXEL>(tex, rr0 + cp1), B);
         channels(load_texel<TEXEL>(tex, rp1 + cc), C);
         channels(load_texel<TEXEL>(tex, rp1 + cp1), D);
-        if (grad_mode == 0) {
-            float T01[5], T02[5], T10[5], T13[5], T20[5], T23[5], T31[5], T32[5];
-            channels(load_texel<TEXEL>(tex, rm1 + cc), T01);
-            channels(load_texel<TEXEL>(tex, rm1 + cp1), T02);
-            channels(load_texel<TEXEL>(tex, rr0 + cm1), T10);
-            channels(load_texel<TEXEL>(tex, rr0 + cp2), T13);
-            channels(load_texel<TEXEL>(tex, rp1 + cm1), T20);
-            channels(load_texel<TEXEL>(tex, rp1 + cp2), T23);
-            channels(load_texel<TEXEL>(tex, rp2 + cc), T31);
-            channels(load_texel<TEXEL>(tex, rp2 + cp1), T32);
-            const float hA = 0.5f * (1.f - a) * (1.f - b), hB = 0.5f * a * (1.f - b);
-            const float hC = 0.5f * (1.f - a) * b, hD = 0.5f * a * b;
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                // central differences at the taps A, B, C, D, interpolated
-                gu[c] = fmaf(hA, B[c] - T10[c], fmaf(hB, T13[c] - A[c], fmaf(hC, D[c] - T20[c], hD * (T23[c] - C[c]))));
-                gv[c] = fmaf(hA, C[c] - T01[c], fmaf(hB, D[c] - T02[c], fmaf(hC, T31[c] - A[c], hD * (T32[c] - B[c]))));
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                gu[c] = fmaf(1.f - b, B[c] - A[c], b * (D[c] - C[c]));
-                gv[c] = fmaf(1.f - a, C[c] - A[c], a * (D[c] - B[c]));
-            }
+        for (int c = 0; c < 5; ++c) {
+            gu[c] = fmaf(1.f - b, B[c] - A[c], b * (D[c] - C[c]));
+            gv[c] = fmaf(1.f - a, C[c] - A[c], a * (D[c] - B[c]));
         }
     }
     const float4 p = __ldg(pg + k);
@@ -359,7 +357,8 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 __syncwarp();
                 if (tail - head >= 32) {
                     jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
-                                          pts_pg + pt_off, pts_n + pt_off, tex, tex_off, prm.grad_mode, Hacc, bacc);
+                                          pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, Hacc,
+                                          bacc);
                     head += 32;
                     __syncwarp();
                 }
@@ -368,7 +367,8 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         if (FULL && tail > head) {
             if (lane < tail - head)
                 jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
-                                      pts_pg + pt_off, pts_n + pt_off, tex, tex_off, prm.grad_mode, Hacc, bacc);
+                                      pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, Hacc,
+                                          bacc);
             __syncwarp();
         }
 

@@ -12,6 +12,7 @@
 // |n| > 0.5, evaluated in double so that the decision is exact for the
 // float32 inputs.
 #include "pba_internal.cuh"
+#include "pba_device.cuh"
 
 namespace pba {
 
@@ -132,9 +133,46 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
 
 }  // namespace
 
+// Central differences of the Supp. at every usable pixel of the frames
+// (d/du = (I(r, c + 1) - I(r, c - 1)) / 2, d/dv = (I(r + 1, c) - I(r - 1, c)) / 2,
+// columns wrapping for the spherical model), from the texels as sampled.
+template <int TEXEL>
+__global__ void k_grad(const void* __restrict__ texels, const FrameInfo* __restrict__ frames,
+                       const int* __restrict__ frame_ids, float4* __restrict__ gtex) {
+    const FrameInfo fr = frames[frame_ids[blockIdx.y]];
+    const int npx = fr.width * fr.height;
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= npx) return;
+    const void* tex = TEXEL == 1 ? (const void*)(reinterpret_cast<const Tex16*>(texels) + fr.px_offset)
+                                 : (const void*)(reinterpret_cast<const Tex32*>(texels) + fr.px_offset);
+    float4* out = gtex + 3 * (fr.px_offset + px);
+    const Texel me = load_texel<TEXEL>(tex, px);
+    if (!me.usable) {
+        out[0] = out[1] = out[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const int row = px / fr.width, col = px % fr.width;
+    const int cl = col == 0 ? fr.width - 1 : col - 1, cr = col == fr.width - 1 ? 0 : col + 1;  // usable: in range
+    float L[5], R[5], U[5], D[5];
+    channels(load_texel<TEXEL>(tex, row * fr.width + cl), L);
+    channels(load_texel<TEXEL>(tex, row * fr.width + cr), R);
+    channels(load_texel<TEXEL>(tex, (row - 1) * fr.width + col), U);
+    channels(load_texel<TEXEL>(tex, (row + 1) * fr.width + col), D);
+    float gu[5], gv[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        gu[c] = 0.5f * (R[c] - L[c]);
+        gv[c] = 0.5f * (D[c] - U[c]);
+    }
+    out[0] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+    out[1] = make_float4(gu[4], gv[0], gv[1], gv[2]);
+    out[2] = make_float4(gv[3], gv[4], 0.f, 0.f);
+}
+
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors, const int* frame_ids,
                         int n, int texel_precision, void* texels, float4* pts_pg, float4* pts_n, int* pts_pix,
-                        int* n_points, double range_min, double range_max, cudaStream_t s) {
+                        int* n_points, double range_min, double range_max, cudaStream_t s, float4* gtex,
+                        int max_px) {
     if (n <= 0) return cudaSuccess;
     if (texel_precision == 1)
         k_pack<1><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
@@ -142,6 +180,13 @@ cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorD
     else
         k_pack<0><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
                                              n_points, range_min, range_max);
+    if (gtex && max_px > 0) {
+        for (int f0 = 0; f0 < n; f0 += 65535) {  // grid.y limit
+            const dim3 grid((max_px + 255) / 256, n - f0 < 65535 ? n - f0 : 65535);
+            if (texel_precision == 1) k_grad<1><<<grid, 256, 0, s>>>(texels, frames, frame_ids + f0, gtex);
+            else k_grad<0><<<grid, 256, 0, s>>>(texels, frames, frame_ids + f0, gtex);
+        }
+    }
     return cudaGetLastError();
 }
 
