@@ -56,13 +56,18 @@ extern "C" {
 #define PBA_TEXEL_F32 0
 #define PBA_TEXEL_F16 1     /* intensity and normal in binary16 (round to nearest even) */
 
-/* damped solve (Sec. IV-C, LM): both deliver the FP64 solution of
+/* damped solve (Sec. IV-C, LM): all deliver the FP64 solution of
  * (H_ff + lambda I) dx_f = -b_f.  CHOLESKY_F64 factorises in FP64;
  * MIXED factorises the Jacobi-scaled system in FP32 and refines the solution
  * with FP64 residuals until |r| <= 1e-10 |b| (else the step is rejected and
- * lambda grows), which suits GB300's FP64 rate of ~1/64 of FP32. */
+ * lambda grows), which suits GB300's FP64 rate of ~1/64 of FP32.  MIXED runs
+ * as one launch of a thread-block cluster holding the FP32 factor in shared
+ * memory when the system fits (up to about 800 unknowns), else as one launch per
+ * tile step; MIXED_STEPS always takes the per-step launches (same arithmetic,
+ * kept for comparison). */
 #define PBA_SOLVE_CHOLESKY_F64 0
 #define PBA_SOLVE_MIXED 1
+#define PBA_SOLVE_MIXED_STEPS 2
 
 /* image-gradient modes (Supp., image Jacobians) */
 #define PBA_GRAD_CENTRAL 0  /* central differences at pixels, bilinearly interpolated (paper) */
@@ -103,7 +108,7 @@ typedef struct {
     int32_t grad_mode;          /* PBA_GRAD_CENTRAL or PBA_GRAD_BILINEAR */
     int32_t texel_precision;    /* PBA_TEXEL_F32 or PBA_TEXEL_F16 (batched path only) */
     int32_t path;               /* PBA_PATH_BATCHED or PBA_PATH_PLAIN */
-    int32_t solver;             /* PBA_SOLVE_CHOLESKY_F64 or PBA_SOLVE_MIXED */
+    int32_t solver;             /* PBA_SOLVE_CHOLESKY_F64, PBA_SOLVE_MIXED or PBA_SOLVE_MIXED_STEPS */
 } pba_config;
 
 /* Outcome of one Levenberg-Marquardt iteration. */

@@ -15,10 +15,11 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PBA_PATH_BATCHED, PBA_PATH_PLAIN, PBA_PINHOLE, PBA_SOLVE_CHOLESKY_F64, PBA_SOLVE_MIXED,
-                   PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32, PbaError)
+                   PBA_SOLVE_MIXED_STEPS, PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32, PbaError)
 
 __all__ = ["Problem", "PbaError", "PBA_PATH_BATCHED", "PBA_PATH_PLAIN", "PBA_TEXEL_F16", "PBA_TEXEL_F32",
-           "PBA_PINHOLE", "PBA_SPHERICAL", "PBA_SOLVE_CHOLESKY_F64", "PBA_SOLVE_MIXED", "problem_from_workload"]
+           "PBA_PINHOLE", "PBA_SPHERICAL", "PBA_SOLVE_CHOLESKY_F64", "PBA_SOLVE_MIXED", "PBA_SOLVE_MIXED_STEPS",
+           "problem_from_workload"]
 
 
 def _is_torch(x) -> bool:

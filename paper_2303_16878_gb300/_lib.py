@@ -31,6 +31,7 @@ PBA_TEXEL_F32 = 0
 PBA_TEXEL_F16 = 1
 PBA_SOLVE_CHOLESKY_F64 = 0
 PBA_SOLVE_MIXED = 1
+PBA_SOLVE_MIXED_STEPS = 2
 
 ERROR_NAMES = {PBA_EINVAL: "PBA_EINVAL", PBA_ENOMEM: "PBA_ENOMEM", PBA_ECUDA: "PBA_ECUDA",
                PBA_ENOTPD: "PBA_ENOTPD", PBA_ETIMEOUT: "PBA_ETIMEOUT", PBA_ENOTREADY: "PBA_ENOTREADY",

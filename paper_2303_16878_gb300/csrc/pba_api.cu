@@ -284,7 +284,11 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     }
     CUDA_TRY(p, launch_lm_prepare(Hs, nf, p->d_state, lambda, s));
     int nc = 0;
-    if (p->cfg.solver == PBA_SOLVE_MIXED) {
+    CsGeom cg{};
+    if (p->cfg.solver == PBA_SOLVE_MIXED && solve_cluster_plan(npad, &cg)) {
+        CUDA_TRY(p, launch_solve_cluster(Hs, bs, nf, cg, p->d_state, 3, p->d_rhs, s));
+        *nl += 2;
+    } else if (p->cfg.solver != PBA_SOLVE_CHOLESKY_F64) {
         CUDA_TRY(p, launch_solve_mixed(Hs, bs, nf, npad, p->d_state, p->mixed, 3, p->d_rhs, s, &nc));
         *nl += 1 + nc;
     } else {
@@ -514,7 +518,9 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     if (cfg->grad_mode != 0 && cfg->grad_mode != 1) return PBA_EINVAL;
     if (cfg->texel_precision != 0 && cfg->texel_precision != 1) return PBA_EINVAL;
     if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return PBA_EINVAL;
-    if (cfg->solver != PBA_SOLVE_CHOLESKY_F64 && cfg->solver != PBA_SOLVE_MIXED) return PBA_EINVAL;
+    if (cfg->solver != PBA_SOLVE_CHOLESKY_F64 && cfg->solver != PBA_SOLVE_MIXED &&
+        cfg->solver != PBA_SOLVE_MIXED_STEPS)
+        return PBA_EINVAL;
     for (int s = 0; s < cfg->n_sensors; ++s) {
         const pba_sensor& S = cfg->sensors[s];
         if ((S.model != PBA_PINHOLE && S.model != PBA_SPHERICAL) || S.width < 4 || S.height < 4) return PBA_EINVAL;
@@ -599,7 +605,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
               alloc((void**)&p->d_Hoo, sizeof(double) * 36 * S) &&
               alloc((void**)&p->d_bo, sizeof(double) * 6 * S) &&
               alloc((void**)&p->d_queue, sizeof(int) * 2) &&
-              (cfg->solver != PBA_SOLVE_MIXED ||
+              (cfg->solver == PBA_SOLVE_CHOLESKY_F64 ||
                (alloc((void**)&p->mixed.A32, sizeof(float) * (size_t)p->n_pad_alloc * p->n_pad_alloc) &&
                 alloc((void**)&p->mixed.D32, sizeof(float) * (size_t)p->n_pad_alloc * kTile) &&
                 alloc((void**)&p->mixed.r32, sizeof(float) * p->n_pad_alloc) &&
@@ -608,6 +614,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
                 alloc((void**)&p->mixed.dscale, sizeof(double) * p->n_pad_alloc) &&
                 alloc((void**)&p->mixed.norms, sizeof(double) * 2)));
     if (!ok) return bail(PBA_ENOMEM);
+    // cluster limits of the one-launch mixed solve, queried here (outside any stream capture)
+    if (cfg->solver == PBA_SOLVE_MIXED) solve_cluster_init();
 
     std::vector<FrameInfo> fi(p->N);
     for (int k = 0; k < p->N; ++k) {

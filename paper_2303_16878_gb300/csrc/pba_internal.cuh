@@ -27,6 +27,7 @@ constexpr int kPartialStride = 32;   // floats per chunk partial
 constexpr int kNumAcc = 29;          // 21 + 6 + cost + count
 constexpr int kBlockStride = 160;    // doubles per pair block
 constexpr int kTile = 32;            // Cholesky tile
+constexpr double kRefineTol = 1e-10; // |r| <= kRefineTol |b'| ends the mixed-precision refinement
 
 struct FrameInfo {
     int width, height, sensor, model;
@@ -208,6 +209,20 @@ struct MixedWork {
 // of launch_trsv.  Sets st->chol_fail when a pivot fails or the refinement misses its tolerance.
 cudaError_t launch_solve_mixed(const double* H, const double* b, int n_frames, int n_pad, LmState* st,
                                MixedWork& w, int refinements, double* dx, cudaStream_t s, int* n_launches);
+
+// The same solve as launch_solve_mixed in one launch of a thread-block cluster
+// whose shared memory holds the FP32 factor (pba_solve_cluster.cu).
+struct CsGeom {
+    int nt, C, n_pad, bytes;  // tile rows, CTAs in the cluster, padded size, shared memory per CTA
+    int o_x, o_dsc, o_xs, o_bs, o_rsq, o_nrm, o_flag, o_tiles, o_dinv, o_dk, o_stage, o_rv, o_yv, o_zv, o_cb, o_pv,
+        o_dsc32;
+};
+// Largest cluster the device schedules with the full opt-in shared memory (once; false: none).
+bool solve_cluster_init();
+// Layout for an n_pad system; false when it does not fit the cluster's shared memory.
+bool solve_cluster_plan(int n_pad, CsGeom* g);
+cudaError_t launch_solve_cluster(const double* H, const double* b, int n_frames, const CsGeom& g, LmState* st,
+                                 int refinements, double* dx, cudaStream_t s);
 
 cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const int* frame_var,
                            const LmState* st, double* cand, cudaStream_t s);

@@ -378,7 +378,6 @@ __global__ void __launch_bounds__(1024) k_trsv(const F* __restrict__ A, const F*
 // The step is declared failed (chol_fail, then rejected with lambda x 10) when
 // the final FP64 residual exceeds kRefineTol |b'|.
 
-constexpr double kRefineTol = 1e-10;
 
 // A32 = fl32(D (H_ff + lambda I) D) padded with identity; bs = -D b_f (FP64); x = 0; dscale = D.
 __global__ void k_damp_mixed(const double* __restrict__ H, const double* __restrict__ b, int n_frames, int n_pad,

@@ -1,0 +1,93 @@
+"""The damped solve of the LM step (Sec. IV-C) in its three forms on the same
+systems: the one-launch cluster solve (PBA_SOLVE_MIXED where the FP32 factor
+fits the cluster's shared memory), the per-tile-step launches of the same
+mixed-precision arithmetic (PBA_SOLVE_MIXED_STEPS) and the FP64 Cholesky.
+
+Bars: after one iteration the poses of the three agree to 1e-8 of the step
+(the refinement stops at |r| <= 1e-10 |b'|), accept/reject decisions are
+identical, and a singular damped system is rejected by all three.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _room(n_frames):
+    from paper_2303_16878_gb300 import synth
+    return synth.make_rgbd_room(n_frames=n_frames, width=48, height=36, f=36.0, seed=7)
+
+
+# systems whose FP32 factor fits the shared memory of a 16-CTA cluster (227 KB
+# per CTA, tile rows i -> CTA i mod 16): up to 130 frames (774 unknowns); 150
+# and 160 frames take the per-step launches
+CLUSTER_FRAMES = {3, 12, 40, 100, 130}
+
+
+@pytest.mark.parametrize("n_frames", [3, 12, 40, 100, 130, 150, 160])
+def test_cluster_solve_matches_per_step_and_f64(n_frames):
+    """Sizes from one tile (a single-CTA cluster) through 16 CTAs with two tile
+    rows each, to systems too large for the cluster (per-step launches)."""
+    gpu()
+    import paper_2303_16878_gb300 as pba
+    w = _room(n_frames)
+    solvers = (pba.PBA_SOLVE_MIXED, pba.PBA_SOLVE_MIXED_STEPS, pba.PBA_SOLVE_CHOLESKY_F64)
+    ps = [pba.problem_from_workload(w, texel=pba.PBA_TEXEL_F16, solver=s) for s in solvers]
+    try:
+        launches = [p.iteration_launches() for p in ps]
+        if n_frames in CLUSTER_FRAMES:
+            assert launches[0] < launches[1], launches
+        else:
+            assert launches[0] == launches[1], launches
+        for lam in (None, 1e-3, 1e-6):
+            stats = []
+            for p in ps:
+                p.set_poses(w.poses_init)
+                p.set_lambda(lam)
+                stats.append(p.iterate())
+            assert all(s["status"] == 0 for s in stats)
+            assert len({s["accepted"] for s in stats}) == 1
+            poses = [p.get_poses() for p in ps]
+            step = max(np.abs(poses[2] - w.poses_init).max(), 1e-6)
+            for q in poses[:2]:
+                assert np.abs(q - poses[2]).max() <= 1e-8 * max(step, 1e-3)
+            # the cost after the step is the same function of the same poses
+            for s in stats[:2]:
+                assert s["new_cost"] == pytest.approx(stats[2]["new_cost"], rel=1e-6)
+    finally:
+        for p in ps:
+            p.close()
+
+
+def test_singular_system_is_rejected_by_every_solver():
+    """A frame without pairs leaves a zero block in H_ff; with lambda = 0 the
+    first pivot of that block is 0, the factorisation fails (PBA_ENOTPD) and
+    the step is rejected with the poses kept."""
+    gpu()
+    import paper_2303_16878_gb300 as pba
+    w = _room(12)
+    last = w.poses_init.shape[0] - 1
+    pairs = np.array([pq for pq in np.asarray(w.pairs) if last not in pq])
+    w = dataclasses.replace(w, pairs=pairs)
+    for solver in (pba.PBA_SOLVE_MIXED, pba.PBA_SOLVE_MIXED_STEPS, pba.PBA_SOLVE_CHOLESKY_F64):
+        p = pba.problem_from_workload(w, texel=pba.PBA_TEXEL_F16, solver=solver)
+        try:
+            p.set_lambda(0.0)
+            s = p.iterate()
+            assert s["status"] == pba._lib.PBA_ENOTPD and s["accepted"] == 0
+            np.testing.assert_array_equal(p.get_poses(), w.poses_init)
+            # with damping the same system solves and the step is taken
+            p.set_lambda(1e-3)
+            s = p.iterate()
+            assert s["status"] == 0 and s["accepted"] == 1
+        finally:
+            p.close()
