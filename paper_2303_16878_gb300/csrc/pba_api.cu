@@ -286,7 +286,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     int nc = 0;
     CsGeom cg{};
     if (p->cfg.solver == PBA_SOLVE_MIXED && solve_cluster_plan(npad, &cg)) {
-        CUDA_TRY(p, launch_solve_cluster(Hs, bs, nf, cg, p->d_state, 3, p->d_rhs, s));
+        CUDA_TRY(p, launch_solve_cluster(Hs, bs, nf, cg, p->d_state, 3, p->d_rhs, p->mixed.A32, p->mixed.D32, s));
         *nl += 2;
     } else if (p->cfg.solver != PBA_SOLVE_CHOLESKY_F64) {
         CUDA_TRY(p, launch_solve_mixed(Hs, bs, nf, npad, p->d_state, p->mixed, 3, p->d_rhs, s, &nc));

@@ -221,8 +221,9 @@ struct CsGeom {
 bool solve_cluster_init();
 // Layout for an n_pad system; false when it does not fit the cluster's shared memory.
 bool solve_cluster_plan(int n_pad, CsGeom* g);
+// gL (n_pad x n_pad FP32) and gD (n_pad x 32 FP32): global scratch for the tiles the CTAs exchange.
 cudaError_t launch_solve_cluster(const double* H, const double* b, int n_frames, const CsGeom& g, LmState* st,
-                                 int refinements, double* dx, cudaStream_t s);
+                                 int refinements, double* dx, float* gL, float* gD, cudaStream_t s);
 
 cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const int* frame_var,
                            const LmState* st, double* cand, cudaStream_t s);

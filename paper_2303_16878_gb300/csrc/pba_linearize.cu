@@ -250,13 +250,17 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         }
         int head = 0, tail = 0;  // warp-uniform queue counters
         const int end = first + count;
+        // the point of the next iteration is loaded one iteration ahead (its
+        // latency, often a DRAM miss, overlaps this iteration's work)
+        float4 p_next = first + lane < end ? __ldg(pts_pg + pt_off + first + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int base = first; base < end; base += 32) {
             const int k = base + lane;
             bool valid = false;
             float e[5], w = 0.f, qx = 0.f, qy = 0.f, qz = 0.f, fa = 0.f, fb = 0.f;
             int r0 = 0, c0 = 0;
+            const float4 p = p_next;
+            if (k + 32 < end) p_next = __ldg(pts_pg + pt_off + k + 32);
             if (k < end) {
-                const float4 p = __ldg(pts_pg + pt_off + k);
                 // a2: pbar = M p_u + a
                 qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
                 qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));

@@ -8,11 +8,16 @@
 //   `refinements` times: z = (L L^T)^-1 r in FP32, x += z, r = b' - A' x in FP64;
 //   dx_f = D x, and the step fails (chol_fail) when a pivot is not positive or
 //   the last |r| exceeds kRefineTol |b'|.
-// What changes is where it runs.  The FP32 factor never leaves shared memory:
+// What changes is where it runs.  The FP32 factor is computed in shared memory:
 // tile row i (tiles (i, 0..i) of 32 x 32) lives on CTA i mod C of a cluster of
-// C <= 16 CTAs, the CTAs read each other's tiles through distributed shared
-// memory, and the steps are separated by cluster barriers instead of kernel
-// boundaries.  The FP64 residual rows are split over the CTAs the same way.
+// C <= 16 CTAs, and the steps are separated by cluster barriers instead of
+// kernel boundaries.  Finished tiles that other CTAs need (the columns of L
+// and the diagonal inverses) are also written to a global scratch copy and
+// read from L2, which moves 4 KB tiles several times faster than distributed
+// shared memory (measured on GB300: ~29 GB/s of remote shared-memory reads per
+// CTA); the short vectors of the triangular solves are pushed through
+// distributed shared memory.  The FP64 residual rows are split over the CTAs
+// like the tile rows.
 //
 // Factorisation, right-looking over tile columns with one cluster barrier per
 // step p (Dinv_k = L_kk^-1):
@@ -59,6 +64,31 @@ __host__ __device__ __forceinline__ int cs_slot(int rank, int C, int q, int j) {
     return q * (rank + 1) + C * q * (q - 1) / 2 + j;
 }
 
+// Distributed shared memory through explicit shared::cluster addresses (mapa):
+// the address of `p` (this CTA's shared memory) in the CTA of cluster rank `rank`.
+__device__ __forceinline__ unsigned dsm_addr(const void* p, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ int dsm_ld_s32(unsigned a) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void dsm_st(unsigned a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_st(unsigned a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// 16-byte load that bypasses L1 (data written by another CTA of the cluster
+// before a cluster barrier)
+__device__ __forceinline__ float4 ld_cg4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+
 __device__ __forceinline__ float dot4(const float4 a, const float4 b, float s) {
     s = fmaf(a.x, b.x, s);
     s = fmaf(a.y, b.y, s);
@@ -92,7 +122,7 @@ __device__ __forceinline__ void tile_rows_dot(const float* X, const float* Y, fl
 // the factor before scaling: L_rc = S_rc / sqrt(S_cc), and L^-1_rw = B_rw /
 // sqrt(S_rr) (right-looking forward substitution of L X = I).  Called by every
 // thread of the CTA.
-__device__ __forceinline__ void cs_diag(float* T, float* Dv, float* pv, int* fail) {
+__device__ __forceinline__ void cs_diag(float* T, float* Dv, float* pv, int* fail, float* gDv) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float a[kRpt], bm[kRpt], dr[kRpt], dc = 1.f;
 #pragma unroll
@@ -135,7 +165,9 @@ __device__ __forceinline__ void cs_diag(float* T, float* Dv, float* pv, int* fai
     for (int h = 0; h < kRpt; ++h) {
         const int r = warp + kCsWarps * h;
         T[r * kLd + lane] = r >= lane ? a[h] * rc : 0.f;
-        Dv[r * kLd + lane] = bm[h] * rsqrtf(dr[h]);
+        const float xr = bm[h] * rsqrtf(dr[h]);
+        Dv[r * kLd + lane] = xr;
+        gDv[r * kT + lane] = xr;  // the global copy the other CTAs read
     }
     if (bad && threadIdx.x == 0) *fail = 1;
     __syncthreads();
@@ -143,7 +175,8 @@ __device__ __forceinline__ void cs_diag(float* T, float* Dv, float* pv, int* fai
 
 __global__ void __launch_bounds__(kCsThreads, 1)
     k_solve_cluster(const double* __restrict__ H, const double* __restrict__ b, int n_frames, const CsGeom g,
-                    LmState* st, int refinements, double* __restrict__ dx) {
+                    LmState* st, int refinements, double* __restrict__ dx, float* __restrict__ gL,
+                    float* __restrict__ gD) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     const int rank = (int)cl.block_rank();
@@ -162,8 +195,8 @@ __global__ void __launch_bounds__(kCsThreads, 1)
     float* yfull = reinterpret_cast<float*>(smem + g.o_yv);   // y, each y_k pushed by its owner
     float* zfull = reinterpret_cast<float*>(smem + g.o_zv);   // z, each z_k pushed by its owner
     float* cbin = reinterpret_cast<float*>(smem + g.o_cb);    // [own row m][source row i][32]: L_im^T z_i, pushed
-    double* nrmall = reinterpret_cast<double*>(smem + g.o_nrm); // [2][C]: |r|^2 and |b'|^2 of every CTA, pushed
     float* pv = reinterpret_cast<float*>(smem + g.o_pv);      // pivot column / row exchange of cs_diag
+    double* nrmall = reinterpret_cast<double*>(smem + g.o_nrm); // [2][C]: |r|^2 and |b'|^2 of every CTA, pushed
     float* dsc32 = reinterpret_cast<float*>(smem + g.o_dsc32); // D in FP32 (scaling of the FP32 tiles)
     double* xs = reinterpret_cast<double*>(smem + g.o_xs);    // D x (FP64)
     int* conv = flag + 1;                                     // [1] refinement converged
@@ -224,7 +257,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
         }
     }
     __syncthreads();
-    if (rank == 0) cs_diag(own_tile(0, 0), dinv, pv, flag);
+    if (rank == 0) cs_diag(own_tile(0, 0), dinv, pv, flag, gD);
     cl.sync();
 
     // ---- factorisation
@@ -237,17 +270,15 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 const float* Li = own_tile(q, p - 1);
                 for (int j0 = p; j0 <= i; j0 += kStage) {
                     const int nj = min(kStage, i + 1 - j0);
-                    // stage the remote L_j,p-1 (kRpt elements per thread and tile)
-                    // thread tid moves the 16-byte piece (row tid / 8, columns 4 (tid % 8) ..) of each tile
-                    const int vo = (tid >> 3) * kLd + 4 * (tid & 7);
+                    // stage the other CTAs' L_j,p-1 from their global copies (L2): thread tid
+                    // moves the 16-byte piece (row tid / 8, columns 4 (tid % 8) ..) of each tile
+                    const int vr = tid >> 3, vc = 4 * (tid & 7), vo = vr * kLd + vc;
                     float4 v[kStage];
 #pragma unroll
                     for (int t = 0; t < kStage; ++t) {
                         const int j = j0 + t;
-                        if (t < nj && j % C != rank) {
-                            const float* src = cl.map_shared_rank(tiles, j % C) + cs_slot(j % C, C, j / C, p - 1) * kTF;
-                            v[t] = *reinterpret_cast<const float4*>(src + vo);
-                        }
+                        if (t < nj && j % C != rank)
+                            v[t] = ld_cg4(gL + (long long)(kT * j + vr) * n_pad + kT * (p - 1) + vc);
                     }
 #pragma unroll
                     for (int t = 0; t < kStage; ++t) {
@@ -255,15 +286,41 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                         if (t < nj && j % C != rank) *reinterpret_cast<float4*>(stage + t * kTF + vo) = v[t];
                     }
                     __syncthreads();
-                    // A_ij[r][c] -= sum_m Li[r][m] Lj[c][m]
-                    for (int t = 0; t < nj; ++t) {
-                        const int j = j0 + t;
-                        const float* Lj = j % C != rank ? stage + t * kTF : own_tile(j / C, p - 1);
-                        float* A = own_tile(q, j);
-                        float sv[kRpt];
-                        tile_rows_dot(Li, Lj, sv);
+                    // A_ij[r][c] -= sum_m Li[r][m] Lj[c][m] for the nj targets together: the Li
+                    // rows are loaded once per m for all of them (16 independent FMA chains)
+                    const float* Lj[kStage];
 #pragma unroll
-                        for (int h = 0; h < kRpt; ++h) A[(warp + kCsWarps * h) * kLd + lane] -= sv[h];
+                    for (int t = 0; t < kStage; ++t) {
+                        const int j = t < nj ? j0 + t : j0;
+                        Lj[t] = (j % C != rank ? stage + t * kTF : own_tile(j / C, p - 1)) + lane * kLd;
+                    }
+                    float sv[kStage][kRpt];
+#pragma unroll
+                    for (int t = 0; t < kStage; ++t)
+#pragma unroll
+                        for (int h = 0; h < kRpt; ++h) sv[t][h] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < kT; m += 4) {
+                        float4 xr[kRpt];
+#pragma unroll
+                        for (int h = 0; h < kRpt; ++h)
+                            xr[h] = *reinterpret_cast<const float4*>(Li + (warp + kCsWarps * h) * kLd + m);
+#pragma unroll
+                        for (int t = 0; t < kStage; ++t) {
+                            if (t < nj) {
+                                const float4 y = *reinterpret_cast<const float4*>(Lj[t] + m);
+#pragma unroll
+                                for (int h = 0; h < kRpt; ++h) sv[t][h] = dot4(xr[h], y, sv[t][h]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < kStage; ++t) {
+                        if (t < nj) {
+                            float* A = own_tile(q, j0 + t);
+#pragma unroll
+                            for (int h = 0; h < kRpt; ++h) A[(warp + kCsWarps * h) * kLd + lane] -= sv[t][h];
+                        }
                     }
                     __syncthreads();
                 }
@@ -277,9 +334,8 @@ __global__ void __launch_bounds__(kCsThreads, 1)
             if (p % C == rank) {
                 Dp = dinv + (p / C) * kTF;
             } else {
-                const float* src = cl.map_shared_rank(dinv, p % C) + (p / C) * kTF;
-                const int vo = (tid >> 3) * kLd + 4 * (tid & 7);
-                *reinterpret_cast<float4*>(dk + vo) = *reinterpret_cast<const float4*>(src + vo);
+                const int vr = tid >> 3, vc = 4 * (tid & 7);
+                *reinterpret_cast<float4*>(dk + vr * kLd + vc) = ld_cg4(gD + p * kT * kT + vr * kT + vc);
                 __syncthreads();
                 Dp = dk;
             }
@@ -289,8 +345,12 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 float sv[kRpt];
                 tile_rows_dot(A, Dp, sv);
                 __syncwarp();  // a warp reads and writes only its own rows of A
+                const int i = rank + C * q;
 #pragma unroll
-                for (int h = 0; h < kRpt; ++h) A[(warp + kCsWarps * h) * kLd + lane] = sv[h];
+                for (int h = 0; h < kRpt; ++h) {
+                    A[(warp + kCsWarps * h) * kLd + lane] = sv[h];
+                    gL[(long long)(kT * i + warp + kCsWarps * h) * n_pad + kT * p + lane] = sv[h];
+                }
                 __syncwarp();
             }
         }
@@ -305,7 +365,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
 #pragma unroll
             for (int h = 0; h < kRpt; ++h) A[(warp + kCsWarps * h) * kLd + lane] -= sv[h];
             __syncthreads();
-            cs_diag(A, dinv + q * kTF, pv, flag);
+            cs_diag(A, dinv + q * kTF, pv, flag, gD + (p + 1) * kT * kT);
         }
         cl.sync();
     }
@@ -316,7 +376,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
         double c = 0.0;
         for (int q = 0; q < rows; ++q)
             for (int rr = 0; rr < kT; ++rr) c += bsv[q * kT + rr] * bsv[q * kT + rr];
-        for (int k = 0; k < C; ++k) cl.map_shared_rank(nrmall, k)[C + rank] = c;
+        for (int k = 0; k < C; ++k) dsm_st(dsm_addr(nrmall + C + rank, k), c);
     }
     for (int it = 0; it <= refinements; ++it) {
         // r = b' - A' x (FP64) for the own rows, A' x = D ((H_ff + lambda I) (D x)); x = 0 on the first pass
@@ -362,7 +422,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 double a = 0.0;
                 for (int q = 0; q < rows; ++q)
                     for (int rr = 0; rr < kT; ++rr) a += rsq[q * kT + rr];
-                for (int k = 0; k < C; ++k) cl.map_shared_rank(nrmall, k)[rank] = a;
+                for (int k = 0; k < C; ++k) dsm_st(dsm_addr(nrmall + rank, k), a);
             }
             cl.sync();
             if (tid == 0) {
@@ -392,7 +452,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                               *reinterpret_cast<const float4*>(r + m + 4), s1);
                 }
                 const float y = s0 + s1;
-                for (int d = 0; d < C; ++d) cl.map_shared_rank(yfull, d)[k * kT + lane] = y;
+                for (int d = 0; d < C; ++d) dsm_st(dsm_addr(yfull + k * kT + lane, d), y);
             }
             cl.sync();
             if (warp < rows) {
@@ -429,7 +489,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                         z1 = fmaf(D[(m + 1) * kLd + lane], __shfl_sync(0xffffffffu, t, m + 1), z1);
                     }
                     const float z = z0 + z1;
-                    for (int d = 0; d < C; ++d) cl.map_shared_rank(zfull, d)[k * kT + lane] = z;
+                    for (int d = 0; d < C; ++d) dsm_st(dsm_addr(zfull + k * kT + lane, d), z);
                 }
                 __syncthreads();
                 // contributions L_km^T z_k to the rows m < k, pushed to their owners
@@ -442,7 +502,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                         s0 = fmaf(L[r * kLd + lane], z[r], s0);
                         s1 = fmaf(L[(r + 1) * kLd + lane], z[r + 1], s1);
                     }
-                    cl.map_shared_rank(cbin, m % C)[((m / C) * nt + k) * kT + lane] = s0 + s1;
+                    dsm_st(dsm_addr(cbin + ((m / C) * nt + k) * kT + lane, m % C), s0 + s1);
                 }
             }
             cl.sync();
@@ -463,7 +523,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
     cl.sync();
     if (rank == 0 && tid == 0) {
         int bad = 0;
-        for (int k = 0; k < C; ++k) bad |= cl.map_shared_rank(flag, k)[0];
+        for (int k = 0; k < C; ++k) bad |= dsm_ld_s32(dsm_addr(flag, k));
         if (bad || !conv[0]) st->chol_fail = 1;
     }
     cl.sync();
@@ -566,7 +626,7 @@ bool solve_cluster_plan(int n_pad, CsGeom* g) {
 }
 
 cudaError_t launch_solve_cluster(const double* H, const double* b, int n_frames, const CsGeom& g, LmState* st,
-                                 int refinements, double* dx, cudaStream_t s) {
+                                 int refinements, double* dx, float* gL, float* gD, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -579,7 +639,8 @@ cudaError_t launch_solve_cluster(const double* H, const double* b, int n_frames,
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_solve_cluster, H, b, n_frames, g, st, refinements < 1 ? 1 : refinements, dx);
+    return cudaLaunchKernelEx(&cfg, k_solve_cluster, H, b, n_frames, g, st, refinements < 1 ? 1 : refinements, dx, gL,
+                              gD);
 }
 
 }  // namespace pba
