@@ -83,16 +83,6 @@ __device__ __forceinline__ void accum_row(float (&H)[21], float (&bb)[6], const 
     }
 }
 
-// J = [h, 2 p x h] (+ [0, extra] for the normal rows)
-__device__ __forceinline__ void make_row(float (&J)[6], const float (&h)[3], const float4& p) {
-    J[0] = h[0];
-    J[1] = h[1];
-    J[2] = h[2];
-    J[3] = 2.f * (p.y * h[2] - p.z * h[1]);
-    J[4] = 2.f * (p.z * h[0] - p.x * h[2]);
-    J[5] = 2.f * (p.x * h[1] - p.y * h[0]);
-}
-
 constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two >= 63)
 constexpr int kQItems = 14;  // floats per queued residual: e[5], w, pbar[3], point, r0, c0, a, b
 
@@ -155,46 +145,59 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
     }
     const float4 p = __ldg(pg + k);
     const float4 n = __ldg(pn + k);
-    // d pi / d pbar (2 x 3) and d zeta^d / d pbar
+    // d pi / d pbar (2 x 3) and d zeta^d / d pbar (hardware reciprocal and
+    // reciprocal square root: ~1e-7 relative, far below the FP32 Jacobian's use)
     float P0[3], P1[3], dz[3];
     if (model == 0) {
-        const float iz = 1.f / qz;
+        const float iz = __fdividef(1.f, qz);
         P0[0] = fx * iz; P0[1] = 0.f; P0[2] = -fx * qx * iz * iz;
         P1[0] = 0.f; P1[1] = fy * iz; P1[2] = -fy * qy * iz * iz;
         dz[0] = 0.f; dz[1] = 0.f; dz[2] = 1.f;
     } else {
         const float rxy2 = fmaf(qx, qx, qy * qy);
-        const float irxy2 = 1.f / rxy2;
-        const float rxy = sqrtf(rxy2);
+        const float irxy = rsqrtf(rxy2);
+        const float irxy2 = irxy * irxy;
+        const float rxy = rxy2 * irxy;
         const float inv_r = rsqrtf(fmaf(qz, qz, rxy2));
         const float ir2 = inv_r * inv_r;
         P0[0] = -fx * qy * irxy2; P0[1] = fx * qx * irxy2; P0[2] = 0.f;
-        const float k1 = -fy * qz * ir2 / rxy;
+        const float k1 = -fy * qz * ir2 * irxy;
         P1[0] = k1 * qx; P1[1] = k1 * qy; P1[2] = fy * rxy * ir2;
         dz[0] = qx * inv_r; dz[1] = qy * inv_r; dz[2] = qz * inv_r;
     }
+    // h_c = M^T g_c with g_c = d zeta_c / d pbar - grad I_c d pi / d pbar is linear
+    // in the rows of d pi / d pbar: take them (and d zeta^d / d pbar) to the i-frame once
+    float A0[3], A1[3], Az[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        A0[j] = fmaf(M[j], P0[0], fmaf(M[3 + j], P0[1], M[6 + j] * P0[2]));
+        A1[j] = fmaf(M[j], P1[0], fmaf(M[3 + j], P1[1], M[6 + j] * P1[2]));
+        Az[j] = fmaf(M[j], dz[0], fmaf(M[3 + j], dz[1], M[6 + j] * dz[2]));
+    }
+    const float4 p2 = make_float4(2.f * p.x, 2.f * p.y, 2.f * p.z, 0.f);
+    const float n2x = 2.f * n.x, n2y = 2.f * n.y, n2z = 2.f * n.z;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-        // g_c = d zeta_c / d pbar - grad I_c d pi / d pbar
-        float g[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            g[j] = -fmaf(gu[c], P0[j], gv[c] * P1[j]);
-            if (c == 1) g[j] += dz[j];
-        }
-        // h_c = M^T g_c
         float h[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) h[j] = fmaf(M[j], g[0], fmaf(M[3 + j], g[1], M[6 + j] * g[2]));
+        for (int j = 0; j < 3; ++j) {
+            h[j] = -fmaf(gu[c], A0[j], gv[c] * A1[j]);
+            if (c == 1) h[j] += Az[j];
+        }
+        // J = [h, 2 p x h] (+ 2 n^o x m_k for the normal rows, m_k = row k of M)
         float J[6];
-        make_row(J, h, p);
+        J[0] = h[0];
+        J[1] = h[1];
+        J[2] = h[2];
+        J[3] = fmaf(p2.y, h[2], -p2.z * h[1]);
+        J[4] = fmaf(p2.z, h[0], -p2.x * h[2]);
+        J[5] = fmaf(p2.x, h[1], -p2.y * h[0]);
         if (c >= 2) {
-            // + 2 n^o x m_k, m_k = row k of M
             const int r = c - 2;
             const float mx = M[3 * r], my = M[3 * r + 1], mz = M[3 * r + 2];
-            J[3] += 2.f * (n.y * mz - n.z * my);
-            J[4] += 2.f * (n.z * mx - n.x * mz);
-            J[5] += 2.f * (n.x * my - n.y * mx);
+            J[3] += fmaf(n2y, mz, -n2z * my);
+            J[4] += fmaf(n2z, mx, -n2x * mz);
+            J[5] += fmaf(n2x, my, -n2y * mx);
         }
         accum_row(Hacc, bacc, J, w * om[c], e[c]);
     }
@@ -270,16 +273,19 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 bool ok;
                 if (model == 0) {
                     ok = qz > prm.z_min;
-                    const float iz = 1.f / qz;
+                    const float iz = __fdividef(1.f, qz);
                     u = fmaf(fx * qx, iz, cx);
                     v = fmaf(fy * qy, iz, cy);
                     zeta_d = qz;
                 } else {
+                    // square roots through the hardware reciprocal square root
+                    // (~1e-7 relative); a zero radius gives NaN and fails the tests
                     const float rxy2 = fmaf(qx, qx, qy * qy);
-                    zeta_d = sqrtf(fmaf(qz, qz, rxy2));
+                    const float r2 = fmaf(qz, qz, rxy2);
+                    zeta_d = r2 * rsqrtf(r2);
                     ok = zeta_d > prm.z_min;
                     u = fmaf(fx, atan2_poly(qy, qx), cx);
-                    v = fmaf(fy, atan2_poly(qz, sqrtf(rxy2)), cy);
+                    v = fmaf(fy, atan2_poly(qz, rxy2 * rsqrtf(rxy2)), cy);
                 }
                 ok = ok && v >= 1.f && v < vmax && u >= umin && u < umax;
                 if (ok) {

@@ -139,7 +139,9 @@ def test_autograd_function_matches_and_descends(room3):
     F.backward()
     _, _, dP, dE, dI = p.cost_gradient(poses=True, extrinsics=True, images=True)
     assert torch.allclose(poses.grad, dP) and torch.allclose(ext.grad, dE)
-    assert torch.allclose(chans.grad.reshape(-1), dI)
+    # the image gradient accumulates with FP32 atomics: two calls agree up to the summation order
+    gi = chans.grad.reshape(-1)
+    assert float(torch.linalg.norm(gi - dI)) <= 1e-5 * float(torch.linalg.norm(dI))
     # a small step against the se(3) gradient lowers F
     from paper_2303_16878_gb300.autograd import tangent_gradient
     import oracle
