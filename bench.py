@@ -440,7 +440,7 @@ def main():
                          "frac": achieved / peak, "traffic": None, "kernel": "k_linearize<f16, full>",
                          "kernel_ms": lin_ms},
             "phase_ms": ph,
-            "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|)",
+            "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
             "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
             "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
             "gpu_launches": out["launches"] * args.steps,
