@@ -45,6 +45,7 @@ struct pba_problem {
     void* tex = nullptr;
     float4* gtex = nullptr;  // central differences per pixel (LinParams::gtex)
     int max_frame_px = 0;
+    int* d_tile_counts = nullptr;  // scratch of the two-pass pack: valid pixels per 1024-pixel tile
     float4* pts_pg = nullptr;
     float4* pts_n = nullptr;
     int* pts_pix = nullptr;
@@ -309,7 +310,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts));
         *nl += 3;
     }
     if (speculative) {
@@ -351,7 +352,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts));
         *nl += 3;
     }
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
@@ -399,7 +400,7 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
                                    p->cfg.range_min, p->cfg.range_max, p->stream));
     CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
                             p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
-                            p->stream, p->gtex, p->max_frame_px));
+                            p->stream, p->gtex, p->max_frame_px, p->d_tile_counts));
     // the id list is pageable host memory: the synchronisation also makes sure
     // the copy has consumed it
     std::vector<int> before = p->n_points;
@@ -677,6 +678,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->prm.grad_mode = cfg->grad_mode;
     p->prm.gtex = p->gtex;
     for (const pba_sensor& S : p->sensors) p->max_frame_px = std::max(p->max_frame_px, S.width * S.height);
+    if (!alloc((void**)&p->d_tile_counts, sizeof(int) * (size_t)p->N * pack_tiles(p->max_frame_px)))
+        return bail(PBA_ENOMEM);
     p->grid_full = linearize_grid(cfg->texel_precision, true, 0);
     p->grid_cost = linearize_grid(cfg->texel_precision, false, 0);
     *out = p;
@@ -706,6 +709,7 @@ void pba_destroy(pba_problem* p) {
     dfree(p->raw);
     dfree(p->tex);
     dfree(p->gtex);
+    dfree(p->d_tile_counts);
     dfree(p->pts_pg);
     dfree(p->pts_n);
     dfree(p->pts_pix);
@@ -832,7 +836,7 @@ int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
                                     p->stream));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, (int)ids.size(),
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, p->stream, p->gtex, p->max_frame_px));
+                                p->cfg.range_min, p->cfg.range_max, p->stream, p->gtex, p->max_frame_px, p->d_tile_counts));
     }
     // per-pair copies of the extrinsic
     if (p->M > 0) {

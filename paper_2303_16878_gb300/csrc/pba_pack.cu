@@ -11,6 +11,8 @@
 // el = (v - c_y) / f_y.  Validity: range_min <= d <= range_max, d > 0 and
 // |n| > 0.5, evaluated in double so that the decision is exact for the
 // float32 inputs.
+#include <cfloat>
+
 #include "pba_internal.cuh"
 #include "pba_device.cuh"
 
@@ -18,54 +20,65 @@ namespace pba {
 
 namespace {
 
-constexpr int kPackThreads = 1024;
+constexpr int kPackThreads = 256;
+constexpr int kPackTile = 1024;  // pixels per CTA: 4 per thread, pixel tile * 1024 + 256 k + thread
 
-__device__ __forceinline__ bool pixel_valid(const float* px, double rmin, double rmax) {
-    double d = px[1];
-    double n2 = (double)px[2] * px[2] + (double)px[3] * px[3] + (double)px[4] * px[4];
-    return d > 0.0 && d >= rmin && d <= rmax && n2 > 0.25;
+// Validity of a raw pixel (Sec. IV-A): range_min <= d <= range_max, d > 0 and
+// |n|^2 > 0.25, decided exactly as the double evaluation of the float inputs
+// would: the range limits are their float images rounded inwards (so the float
+// comparisons agree with the double ones), and |n|^2 is summed in FP32 (error
+// below 2e-7 |n|^2) unless it lies within 1e-6 of the threshold, where the
+// double sum decides.
+__device__ __forceinline__ bool pixel_valid(const float* px, float rmin, float rmax) {
+    const float d = px[1];
+    if (!(d > 0.f && d >= rmin && d <= rmax)) return false;
+    const float nx = px[2], ny = px[3], nz = px[4];
+    const float s = fmaf(nz, nz, fmaf(ny, ny, nx * nx));
+    if (fabsf(s - 0.25f) > 1e-6f) return s > 0.25f;
+    const double n2 = (double)nx * nx + (double)ny * ny + (double)nz * nz;
+    return n2 > 0.25;
 }
 
+// Pass 1, one CTA per 1024 pixels of a frame: the sampling texel of every pixel
+// (with its usable flag: the pixel and its four neighbours are valid, i.e. the
+// central differences of the Supp. are defined) and the tile's count of valid
+// pixels.
 template <int TEXEL>
-__global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__ raw,
-                                                       const FrameInfo* __restrict__ frames,
-                                                       const SensorDev* __restrict__ sensors,
-                                                       const int* __restrict__ frame_ids, void* texels,
-                                                       float4* __restrict__ pts_pg, float4* __restrict__ pts_n,
-                                                       int* __restrict__ pts_pix, int* __restrict__ n_points,
-                                                       double rmin, double rmax) {
-    __shared__ int s_warp[kPackThreads / 32];
-    __shared__ int s_base, s_total;
-    const int f = frame_ids[blockIdx.x];
+__global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restrict__ raw,
+                                                           const FrameInfo* __restrict__ frames,
+                                                           const int* __restrict__ frame_ids, void* texels,
+                                                           int* __restrict__ tile_counts, int max_tiles, float rmin,
+                                                           float rmax) {
+    const int f = frame_ids[blockIdx.y];
     const FrameInfo fr = frames[f];
-    const SensorDev sd = sensors[fr.sensor];
     const int npx = fr.width * fr.height;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_base = 0;
-    __syncthreads();
-    for (int tile = 0; tile < npx; tile += kPackThreads) {
-        const int px = tile + threadIdx.x;
+    const int tile = blockIdx.x;
+    if (tile * kPackTile >= npx) return;
+    const bool wrap = fr.model == 1;
+    int count = 0;
+#pragma unroll
+    for (int k = 0; k < kPackTile / kPackThreads; ++k) {
+        const int px = tile * kPackTile + k * kPackThreads + threadIdx.x;
         bool valid = false;
-        float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (px < npx) {
             const float* src = raw + (fr.px_offset + px) * 5;
-            for (int k = 0; k < 5; ++k) c[k] = src[k];
+            float c[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) c[q] = src[q];
             valid = pixel_valid(c, rmin, rmax);
-            // usable: the pixel and its four neighbours are valid, i.e. the
-            // central differences of the Supp. are defined at this pixel
             bool usable = valid;
-            {
+            if (usable) {
                 const int col = px % fr.width, row = px / fr.width;
-                const bool wrap = fr.model == 1;
                 const int nb[4][2] = {{row - 1, col}, {row + 1, col}, {row, col - 1}, {row, col + 1}};
-                for (int q = 0; q < 4 && usable; ++q) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
                     int r = nb[q][0], cc = nb[q][1];
-                    if (r < 0 || r >= fr.height) { usable = false; break; }
+                    bool in = r >= 0 && r < fr.height;
                     if (cc < 0 || cc >= fr.width) {
-                        if (!wrap) { usable = false; break; }
+                        in = in && wrap;
                         cc = cc < 0 ? cc + fr.width : cc - fr.width;
                     }
-                    usable = pixel_valid(raw + (fr.px_offset + (long long)r * fr.width + cc) * 5, rmin, rmax);
+                    usable = usable && in && pixel_valid(raw + (fr.px_offset + (long long)r * fr.width + cc) * 5, rmin, rmax);
                 }
             }
             const long long t = fr.px_offset + px;
@@ -82,24 +95,73 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
                 t4[1] = make_float4(c[4], __uint_as_float(usable ? 1u : 0u), 0.f, 0.f);
             }
         }
+        count += __syncthreads_count(valid);
+    }
+    if (threadIdx.x == 0) tile_counts[(long long)f * max_tiles + tile] = count;
+}
+
+// Pass 2: the valid pixels of a tile as pixel-points p_u = R_o pi^-1(u, d) + t_o
+// with g_u, n_u^o = R_o n_u and the pixel index, written in raster order at the
+// tile's offset (the counts of the frame's earlier tiles); the CTA of tile 0
+// also writes the frame's point count.
+__global__ void __launch_bounds__(kPackThreads) k_pack_points(const float* __restrict__ raw,
+                                                              const FrameInfo* __restrict__ frames,
+                                                              const SensorDev* __restrict__ sensors,
+                                                              const int* __restrict__ frame_ids,
+                                                              const int* __restrict__ tile_counts, int max_tiles,
+                                                              float4* __restrict__ pts_pg, float4* __restrict__ pts_n,
+                                                              int* __restrict__ pts_pix, int* __restrict__ n_points,
+                                                              float rmin, float rmax) {
+    __shared__ int s_warp[kPackThreads / 32];
+    __shared__ int s_base;
+    const int f = frame_ids[blockIdx.y];
+    const FrameInfo fr = frames[f];
+    const int npx = fr.width * fr.height;
+    const int tile = blockIdx.x;
+    if (tile * kPackTile >= npx) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        const int n_tiles = (npx + kPackTile - 1) / kPackTile;
+        const int* tc = tile_counts + (long long)f * max_tiles;
+        int before = 0, all = 0;
+        for (int t = lane; t < n_tiles; t += 32) {
+            const int v = tc[t];
+            all += v;
+            if (t < tile) before += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) {
+            s_base = before;
+            if (tile == 0) n_points[f] = all;
+        }
+    }
+    const SensorDev sd = sensors[fr.sensor];
+    for (int k = 0; k < kPackTile / kPackThreads; ++k) {
+        const int px = tile * kPackTile + k * kPackThreads + threadIdx.x;
+        bool valid = false;
+        float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (px < npx) {
+            const float* src = raw + (fr.px_offset + px) * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) c[q] = src[q];
+            valid = pixel_valid(c, rmin, rmax);
+        }
         const unsigned ballot = __ballot_sync(0xffffffffu, valid);
         if (lane == 0) s_warp[warp] = __popc(ballot);
         __syncthreads();
-        if (warp == 0) {
-            // exclusive scan of the 32 warp counts; the inclusive total goes to s_total
-            const int v = s_warp[lane];
-            int incl = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            s_warp[lane] = incl - v;
-            if (lane == 31) s_total = incl;
+        int before_warp = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kPackThreads / 32; ++w) {
+            const int v = s_warp[w];
+            before_warp += w < warp ? v : 0;
+            total += v;
         }
-        __syncthreads();
         if (valid) {
-            const int within = __popc(ballot & ((1u << lane) - 1u));
-            const int idx = s_base + s_warp[warp] + within;
+            const int idx = s_base + before_warp + __popc(ballot & ((1u << lane) - 1u));
             const int col = px % fr.width, row = px / fr.width;
             const float d = c[1];
             float p[3];
@@ -116,6 +178,7 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
                 p[2] = d * sel;
             }
             float pu[3], no[3];
+#pragma unroll
             for (int r = 0; r < 3; ++r) {
                 pu[r] = sd.R[3 * r] * p[0] + sd.R[3 * r + 1] * p[1] + sd.R[3 * r + 2] * p[2] + sd.t[r];
                 no[r] = sd.R[3 * r] * c[2] + sd.R[3 * r + 1] * c[3] + sd.R[3 * r + 2] * c[4];
@@ -124,11 +187,10 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
             pts_n[fr.pt_offset + idx] = make_float4(no[0], no[1], no[2], 0.f);
             pts_pix[fr.pt_offset + idx] = px;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_base += s_total;
+        __syncthreads();  // s_warp is rewritten by the next round
+        if (threadIdx.x == 0) s_base += total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) n_points[f] = s_base;
 }
 
 }  // namespace
@@ -169,19 +231,31 @@ __global__ void k_grad(const void* __restrict__ texels, const FrameInfo* __restr
     out[2] = make_float4(gv[3], gv[4], 0.f, 0.f);
 }
 
+int pack_tiles(int max_px) { return (max_px + kPackTile - 1) / kPackTile; }
+
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors, const int* frame_ids,
                         int n, int texel_precision, void* texels, float4* pts_pg, float4* pts_n, int* pts_pix,
                         int* n_points, double range_min, double range_max, cudaStream_t s, float4* gtex,
-                        int max_px) {
+                        int max_px, int* tile_counts) {
     if (n <= 0) return cudaSuccess;
-    if (texel_precision == 1)
-        k_pack<1><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
-                                             n_points, range_min, range_max);
-    else
-        k_pack<0><<<n, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids, texels, pts_pg, pts_n, pts_pix,
-                                             n_points, range_min, range_max);
+    // float images of the double range limits, rounded inwards (exact decisions for float depths)
+    float rmin = (float)range_min, rmax = range_max > (double)FLT_MAX ? FLT_MAX : (float)range_max;
+    if ((double)rmin < range_min) rmin = nextafterf(rmin, FLT_MAX);
+    if ((double)rmax > range_max) rmax = nextafterf(rmax, -FLT_MAX);
+    const int max_tiles = pack_tiles(max_px);
+    for (int f0 = 0; f0 < n; f0 += 65535) {  // grid.y limit
+        const dim3 grid(max_tiles, n - f0 < 65535 ? n - f0 : 65535);
+        if (texel_precision == 1)
+            k_pack_tex<1><<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, texels, tile_counts, max_tiles,
+                                                        rmin, rmax);
+        else
+            k_pack_tex<0><<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, texels, tile_counts, max_tiles,
+                                                        rmin, rmax);
+        k_pack_points<<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, tile_counts, max_tiles,
+                                                    pts_pg, pts_n, pts_pix, n_points, rmin, rmax);
+    }
     if (gtex && max_px > 0) {
-        for (int f0 = 0; f0 < n; f0 += 65535) {  // grid.y limit
+        for (int f0 = 0; f0 < n; f0 += 65535) {
             const dim3 grid((max_px + 255) / 256, n - f0 < 65535 ? n - f0 : 65535);
             if (texel_precision == 1) k_grad<1><<<grid, 256, 0, s>>>(texels, frames, frame_ids + f0, gtex);
             else k_grad<0><<<grid, 256, 0, s>>>(texels, frames, frame_ids + f0, gtex);
