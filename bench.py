@@ -48,6 +48,20 @@ WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs w
 # valid residual (sampling, residual, Huber, 5 x 6 Jacobian, 6 x 6 accumulation).
 FLOP_PER_POINT_SPHERICAL = 31
 FLOP_PER_RESIDUAL_FULL = 765
+def measured_hbm_gbs() -> float:
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the
+    6.8 TB/s fallback of one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch on this
+# workload (ncu capture of k_linearize<1, 1, 0, 3>, profiles/k_linearize_lidar_street_50x64x1024.md);
+# to be retaken whenever the kernel changes
+LINEARIZE_DRAM_BYTES = (374.2272 + 11.571712) * 1e6
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
 NORMAL_MAX_RADIUS = 5
@@ -427,6 +441,7 @@ def main():
         sm_max = (out["clocks"] or {}).get("sm_max_mhz") or 2070.0
         peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         achieved = flops / (lin_ms / 1e3) / 1e12
+        hbm_peak = measured_hbm_gbs()
         line = {
             "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
@@ -437,8 +452,11 @@ def main():
                        "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)", "parallelism": f"replicas x{world}",
                        "autotuned_variants": list(out["variants"])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_linearize<f16, full>",
-                         "kernel_ms": lin_ms},
+                         "frac": achieved / peak, "traffic": LINEARIZE_DRAM_BYTES, "kernel": "k_linearize<f16, full>",
+                         "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
+                         "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak,
+                                 "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"}},
             "phase_ms": ph,
             "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
             "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
