@@ -416,8 +416,17 @@ __global__ void k_pair_reduce(const float* __restrict__ partials, const PairStat
     const PairStatic P = ps[p];
     const int k0 = full ? 0 : 27;
     if (t >= k0 && t < kNumAcc) {
+        // chunk order; 8 loads in flight, added in that order
         double s = 0.0;
-        for (int c = P.chunk_begin; c < P.chunk_end; ++c) s += (double)partials[(long long)c * kPartialStride + t];
+        for (int c0 = P.chunk_begin; c0 < P.chunk_end; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = c0 + u < P.chunk_end ? partials[(long long)(c0 + u) * kPartialStride + t] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < P.chunk_end) s += (double)v[u];
+        }
         acc[t] = s;
     }
     __syncthreads();

@@ -20,32 +20,53 @@ namespace {
 
 // One block per task: sums the 6x6 sub-blocks of the contributing pairs in a
 // fixed order (deterministic) and writes block (a, b) of H and its transpose;
-// diagonal tasks also write b_a.
-__global__ void k_assemble(const AsmTask* __restrict__ tasks, const AsmContrib* __restrict__ contrib,
-                           const double* __restrict__ blocks, int n6, double* __restrict__ H,
-                           double* __restrict__ b) {
+// diagonal tasks also write b_a.  The task's contribution list is staged in
+// shared memory and each thread keeps 8 block loads in flight (the sum order
+// is unchanged).
+constexpr int kAsmStage = 128;
+constexpr int kAsmUnroll = 8;
+
+__global__ void __launch_bounds__(64) k_assemble(const AsmTask* __restrict__ tasks,
+                                                 const AsmContrib* __restrict__ contrib,
+                                                 const double* __restrict__ blocks, int n6, double* __restrict__ H,
+                                                 double* __restrict__ b) {
+    __shared__ AsmContrib sc[kAsmStage];
     const AsmTask T = tasks[blockIdx.x];
     const int t = threadIdx.x;
-    if (t < 36) {
-        const int r = t / 6, c = t % 6;
-        const bool diag = T.a == T.b;
-        if (!diag || r <= c) {
-            double s = 0.0;
-            for (int k = T.contrib_begin; k < T.contrib_end; ++k) {
-                const AsmContrib C = contrib[k];
-                s += blocks[(long long)C.pair * kBlockStride + 12 * (6 * C.row_role + r) + 6 * C.col_role + c];
+    const bool diag = T.a == T.b;
+    // thread t < 36: H entry (r, c); 36 <= t < 42 on diagonal tasks: b entry t - 36
+    const int r = t < 36 ? t / 6 : t - 36, c = t < 36 ? t % 6 : 0;
+    const bool h_entry = t < 36 && (!diag || r <= c), b_entry = t >= 36 && t < 42 && diag;
+    double s = 0.0;
+    for (int k0 = T.contrib_begin; k0 < T.contrib_end; k0 += kAsmStage) {
+        const int nk = min(kAsmStage, T.contrib_end - k0);
+        __syncthreads();  // the previous round's reads of sc are done
+        for (int k = t; k < nk; k += blockDim.x) sc[k] = contrib[k0 + k];
+        __syncthreads();
+        if (h_entry || b_entry) {
+            for (int k = 0; k < nk; k += kAsmUnroll) {
+                double v[kAsmUnroll];
+#pragma unroll
+                for (int u = 0; u < kAsmUnroll; ++u) {
+                    v[u] = 0.0;
+                    if (k + u < nk) {
+                        const AsmContrib C = sc[k + u];
+                        const long long base = (long long)C.pair * kBlockStride;
+                        if (h_entry) v[u] = blocks[base + 12 * (6 * C.row_role + r) + 6 * C.col_role + c];
+                        else if (C.add_b) v[u] = blocks[base + 144 + 6 * C.row_role + r];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kAsmUnroll; ++u)
+                    if (k + u < nk && (h_entry || sc[k + u].add_b)) s += v[u];
             }
-            // diagonal blocks: one sum per unordered entry, mirrored, so H is exactly symmetric
-            H[(long long)(6 * T.a + r) * n6 + 6 * T.b + c] = s;
-            H[(long long)(6 * T.b + c) * n6 + 6 * T.a + r] = s;
         }
-    } else if (t < 42 && T.a == T.b) {
-        const int r = t - 36;
-        double s = 0.0;
-        for (int k = T.contrib_begin; k < T.contrib_end; ++k) {
-            const AsmContrib C = contrib[k];
-            if (C.add_b) s += blocks[(long long)C.pair * kBlockStride + 144 + 6 * C.row_role + r];
-        }
+    }
+    if (h_entry) {
+        // diagonal blocks: one sum per unordered entry, mirrored, so H is exactly symmetric
+        H[(long long)(6 * T.a + r) * n6 + 6 * T.b + c] = s;
+        H[(long long)(6 * T.b + c) * n6 + 6 * T.a + r] = s;
+    } else if (b_entry) {
         b[6 * T.a + r] = s;
     }
 }
@@ -55,9 +76,21 @@ __global__ void k_total_cost(const double* __restrict__ blocks, int m, LmState* 
     __shared__ double sc[256];
     __shared__ double sn[256];
     double c = 0.0, n = 0.0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        c += blocks[(long long)p * kBlockStride + 156];
-        n += blocks[(long long)p * kBlockStride + 157];
+    // strided per thread (loads 4 at a time, added in the same order), then a tree
+    for (int p0 = threadIdx.x; p0 < m; p0 += 4 * blockDim.x) {
+        double vc[4], vn[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * blockDim.x;
+            vc[u] = p < m ? blocks[(long long)p * kBlockStride + 156] : 0.0;
+            vn[u] = p < m ? blocks[(long long)p * kBlockStride + 157] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (p0 + u * blockDim.x < m) {
+                c += vc[u];
+                n += vn[u];
+            }
     }
     sc[threadIdx.x] = c;
     sn[threadIdx.x] = n;
