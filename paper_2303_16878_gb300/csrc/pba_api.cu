@@ -31,6 +31,11 @@ struct pba_problem {
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // host-to-device uploads are split over the problem's stream and these
+    // (one copy keeps one copy engine busy); the events join them back
+    static constexpr int kCopyLanes = 4;
+    cudaStream_t copy_streams[kCopyLanes - 1] = {};
+    cudaEvent_t copy_events[kCopyLanes] = {};
     std::string err;
 
     // frames
@@ -46,6 +51,7 @@ struct pba_problem {
     float4* gtex = nullptr;  // central differences per pixel (LinParams::gtex)
     int max_frame_px = 0;
     int* d_tile_counts = nullptr;  // scratch of the two-pass pack: valid pixels per 1024-pixel tile
+    unsigned char* d_valid_px = nullptr;  // scratch of the pack: validity of every pixel
     float4* pts_pg = nullptr;
     float4* pts_n = nullptr;
     int* pts_pix = nullptr;
@@ -310,7 +316,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts, p->d_valid_px));
         *nl += 3;
     }
     if (speculative) {
@@ -352,7 +358,7 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
                                           p->d_sensors, s));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_free_frames, p->n_free_frames,
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts));
+                                p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts, p->d_valid_px));
         *nl += 3;
     }
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[5], s));
@@ -400,7 +406,7 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
                                    p->cfg.range_min, p->cfg.range_max, p->stream));
     CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
                             p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
-                            p->stream, p->gtex, p->max_frame_px, p->d_tile_counts));
+                            p->stream, p->gtex, p->max_frame_px, p->d_tile_counts, p->d_valid_px));
     // the id list is pageable host memory: the synchronisation also makes sure
     // the copy has consumed it
     std::vector<int> before = p->n_points;
@@ -581,6 +587,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     bool ok = alloc((void**)&p->raw, sizeof(float) * 5 * (size_t)p->total_px) &&
               alloc(&p->tex, texel_bytes * (size_t)p->total_px) &&
               alloc((void**)&p->gtex, sizeof(float4) * 3 * (size_t)p->total_px) &&
+              alloc((void**)&p->d_valid_px, (size_t)p->total_px) &&
               alloc((void**)&p->pts_pg, sizeof(float4) * (size_t)p->total_px) &&
               alloc((void**)&p->pts_n, sizeof(float4) * (size_t)p->total_px) &&
               alloc((void**)&p->pts_pix, sizeof(int) * (size_t)p->total_px) &&
@@ -710,6 +717,7 @@ void pba_destroy(pba_problem* p) {
     dfree(p->tex);
     dfree(p->gtex);
     dfree(p->d_tile_counts);
+    dfree(p->d_valid_px);
     dfree(p->pts_pg);
     dfree(p->pts_n);
     dfree(p->pts_pix);
@@ -737,6 +745,10 @@ void pba_destroy(pba_problem* p) {
     dfree(p->mixed.dscale);
     dfree(p->mixed.norms);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    for (cudaStream_t& c : p->copy_streams)
+        if (c) cudaStreamDestroy(c);
+    for (cudaEvent_t& e : p->copy_events)
+        if (e) cudaEventDestroy(e);
     if (p->own_stream) cudaStreamDestroy(p->own_stream);
     delete p;
 }
@@ -763,8 +775,34 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
             return fail(p, PBA_EINVAL, "upload: frames of one call must share the image size");
     }
     const size_t bytes = sizeof(float) * 5 * (size_t)S0.width * S0.height * count;
-    CUDA_TRY(p, cudaMemcpyAsync(p->raw + 5 * p->px_off[first], channels, bytes,
-                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    float* dst = p->raw + 5 * p->px_off[first];
+    const int lanes = p->kCopyLanes;
+    if (is_device || bytes < ((size_t)16 << 20)) {
+        CUDA_TRY(p, cudaMemcpyAsync(dst, channels, bytes,
+                                    is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    } else {
+        // large host uploads: one copy per lane, in parallel, joined back into the stream
+        if (!p->copy_events[0]) {
+            for (cudaStream_t& c : p->copy_streams) CUDA_TRY(p, cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : p->copy_events) CUDA_TRY(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        CUDA_TRY(p, cudaEventRecord(p->copy_events[0], p->stream));
+        const size_t piece = (bytes / lanes + 4095) / 4096 * 4096;
+        for (int l = 0; l < lanes; ++l) {
+            const size_t off = piece * l;
+            if (off >= bytes) break;
+            const size_t len = bytes - off < piece ? bytes - off : piece;
+            cudaStream_t cs = l == 0 ? p->stream : p->copy_streams[l - 1];
+            if (l > 0) CUDA_TRY(p, cudaStreamWaitEvent(cs, p->copy_events[0], 0));
+            CUDA_TRY(p, cudaMemcpyAsync(reinterpret_cast<char*>(dst) + off,
+                                        reinterpret_cast<const char*>(channels) + off, len,
+                                        cudaMemcpyHostToDevice, cs));
+            if (l > 0) {
+                CUDA_TRY(p, cudaEventRecord(p->copy_events[l], cs));
+                CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->copy_events[l], 0));
+            }
+        }
+    }
     for (int k = first; k < first + count; ++k) p->uploaded[k] = 1;
     p->pyramid_stale = true;
     return repack(p, first, count, 0.f, 0);
@@ -836,7 +874,7 @@ int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic) {
                                     p->stream));
         CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, (int)ids.size(),
                                 p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
-                                p->cfg.range_min, p->cfg.range_max, p->stream, p->gtex, p->max_frame_px, p->d_tile_counts));
+                                p->cfg.range_min, p->cfg.range_max, p->stream, p->gtex, p->max_frame_px, p->d_tile_counts, p->d_valid_px));
     }
     // per-pair copies of the extrinsic
     if (p->M > 0) {

@@ -150,12 +150,14 @@ cudaError_t launch_offset_refresh(const double* extr, int n_sensors, const int2*
 cudaError_t launch_normals(float* raw, const FrameInfo* frames, const int* frame_ids, int n, int max_px, float scale,
                            int max_radius, double range_min, double range_max, cudaStream_t s);
 
-// max_px: the largest frame's pixel count; tile_counts: n_frames x pack_tiles(max_px) ints of scratch.
+// max_px: the largest frame's pixel count; tile_counts: n_frames x pack_tiles(max_px) ints of
+// scratch; valid_px: one byte per pixel of every frame (scratch, laid out like raw).
 int pack_tiles(int max_px);
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors,
                         const int* frame_ids, int n, int texel_precision, void* texels,
                         float4* pts_pg, float4* pts_n, int* pts_pix, int* n_points, double range_min,
-                        double range_max, cudaStream_t s, float4* gtex, int max_px, int* tile_counts);
+                        double range_max, cudaStream_t s, float4* gtex, int max_px, int* tile_counts,
+                        unsigned char* valid_px);
 
 cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
                              PairPose* out, cudaStream_t s);

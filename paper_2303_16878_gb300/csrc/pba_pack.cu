@@ -39,22 +39,19 @@ __device__ __forceinline__ bool pixel_valid(const float* px, float rmin, float r
     return n2 > 0.25;
 }
 
-// Pass 1, one CTA per 1024 pixels of a frame: the sampling texel of every pixel
-// (with its usable flag: the pixel and its four neighbours are valid, i.e. the
-// central differences of the Supp. are defined) and the tile's count of valid
-// pixels.
-template <int TEXEL>
-__global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restrict__ raw,
-                                                           const FrameInfo* __restrict__ frames,
-                                                           const int* __restrict__ frame_ids, void* texels,
-                                                           int* __restrict__ tile_counts, int max_tiles, float rmin,
-                                                           float rmax) {
+// Pass 1, one CTA per 1024 pixels of a frame: every pixel's validity as a
+// byte and the tile's count of valid pixels.
+__global__ void __launch_bounds__(kPackThreads) k_pack_valid(const float* __restrict__ raw,
+                                                             const FrameInfo* __restrict__ frames,
+                                                             const int* __restrict__ frame_ids,
+                                                             unsigned char* __restrict__ valid_px,
+                                                             int* __restrict__ tile_counts, int max_tiles, float rmin,
+                                                             float rmax) {
     const int f = frame_ids[blockIdx.y];
     const FrameInfo fr = frames[f];
     const int npx = fr.width * fr.height;
     const int tile = blockIdx.x;
     if (tile * kPackTile >= npx) return;
-    const bool wrap = fr.model == 1;
     int count = 0;
 #pragma unroll
     for (int k = 0; k < kPackTile / kPackThreads; ++k) {
@@ -66,38 +63,53 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restri
 #pragma unroll
             for (int q = 0; q < 5; ++q) c[q] = src[q];
             valid = pixel_valid(c, rmin, rmax);
-            bool usable = valid;
-            if (usable) {
-                const int col = px % fr.width, row = px / fr.width;
-                const int nb[4][2] = {{row - 1, col}, {row + 1, col}, {row, col - 1}, {row, col + 1}};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    int r = nb[q][0], cc = nb[q][1];
-                    bool in = r >= 0 && r < fr.height;
-                    if (cc < 0 || cc >= fr.width) {
-                        in = in && wrap;
-                        cc = cc < 0 ? cc + fr.width : cc - fr.width;
-                    }
-                    usable = usable && in && pixel_valid(raw + (fr.px_offset + (long long)r * fr.width + cc) * 5, rmin, rmax);
-                }
-            }
-            const long long t = fr.px_offset + px;
-            if (TEXEL == 1) {
-                Tex16 tx;
-                tx.d = valid ? c[1] : 0.f;
-                tx.g_nx = __halves2half2(__float2half_rn(c[0]), __float2half_rn(c[2]));
-                tx.ny_nz = __halves2half2(__float2half_rn(c[3]), __float2half_rn(c[4]));
-                tx.usable = usable ? 1u : 0u;
-                reinterpret_cast<Tex16*>(texels)[t] = tx;
-            } else {
-                float4* t4 = reinterpret_cast<float4*>(texels) + 2 * t;
-                t4[0] = make_float4(valid ? c[1] : 0.f, c[0], c[2], c[3]);
-                t4[1] = make_float4(c[4], __uint_as_float(usable ? 1u : 0u), 0.f, 0.f);
-            }
+            valid_px[fr.px_offset + px] = valid ? 1 : 0;
         }
         count += __syncthreads_count(valid);
     }
     if (threadIdx.x == 0) tile_counts[(long long)f * max_tiles + tile] = count;
+}
+
+// Pass 2: the sampling texel of every pixel, with its usable flag (the pixel
+// and its four neighbours are valid, i.e. the central differences of the Supp.
+// are defined there; columns wrap for the spherical model).
+template <int TEXEL>
+__global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restrict__ raw,
+                                                           const FrameInfo* __restrict__ frames,
+                                                           const int* __restrict__ frame_ids,
+                                                           const unsigned char* __restrict__ valid_px, void* texels) {
+    const FrameInfo fr = frames[frame_ids[blockIdx.y]];
+    const int npx = fr.width * fr.height;
+    const int px = blockIdx.x * kPackThreads + threadIdx.x;
+    if (px >= npx) return;
+    const unsigned char* vf = valid_px + fr.px_offset;
+    const bool valid = vf[px] != 0;
+    bool usable = valid;
+    if (usable) {
+        const int col = px % fr.width, row = px / fr.width;
+        const bool wrap = fr.model == 1;
+        const int cl = col > 0 ? col - 1 : (wrap ? fr.width - 1 : -1);
+        const int cr = col < fr.width - 1 ? col + 1 : (wrap ? 0 : -1);
+        usable = row > 0 && row < fr.height - 1 && cl >= 0 && cr >= 0 && vf[px - fr.width] && vf[px + fr.width] &&
+                 vf[row * fr.width + cl] && vf[row * fr.width + cr];
+    }
+    const float* src = raw + (fr.px_offset + px) * 5;
+    float c[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) c[q] = src[q];
+    const long long t = fr.px_offset + px;
+    if (TEXEL == 1) {
+        Tex16 tx;
+        tx.d = valid ? c[1] : 0.f;
+        tx.g_nx = __halves2half2(__float2half_rn(c[0]), __float2half_rn(c[2]));
+        tx.ny_nz = __halves2half2(__float2half_rn(c[3]), __float2half_rn(c[4]));
+        tx.usable = usable ? 1u : 0u;
+        reinterpret_cast<Tex16*>(texels)[t] = tx;
+    } else {
+        float4* t4 = reinterpret_cast<float4*>(texels) + 2 * t;
+        t4[0] = make_float4(valid ? c[1] : 0.f, c[0], c[2], c[3]);
+        t4[1] = make_float4(c[4], __uint_as_float(usable ? 1u : 0u), 0.f, 0.f);
+    }
 }
 
 // Pass 2: the valid pixels of a tile as pixel-points p_u = R_o pi^-1(u, d) + t_o
@@ -108,10 +120,10 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_points(const float* __res
                                                               const FrameInfo* __restrict__ frames,
                                                               const SensorDev* __restrict__ sensors,
                                                               const int* __restrict__ frame_ids,
+                                                              const unsigned char* __restrict__ valid_px,
                                                               const int* __restrict__ tile_counts, int max_tiles,
                                                               float4* __restrict__ pts_pg, float4* __restrict__ pts_n,
-                                                              int* __restrict__ pts_pix, int* __restrict__ n_points,
-                                                              float rmin, float rmax) {
+                                                              int* __restrict__ pts_pix, int* __restrict__ n_points) {
     __shared__ int s_warp[kPackThreads / 32];
     __shared__ int s_base;
     const int f = frame_ids[blockIdx.y];
@@ -142,13 +154,12 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_points(const float* __res
     const SensorDev sd = sensors[fr.sensor];
     for (int k = 0; k < kPackTile / kPackThreads; ++k) {
         const int px = tile * kPackTile + k * kPackThreads + threadIdx.x;
-        bool valid = false;
+        const bool valid = px < npx && valid_px[fr.px_offset + px] != 0;
         float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (px < npx) {
+        if (valid) {
             const float* src = raw + (fr.px_offset + px) * 5;
 #pragma unroll
             for (int q = 0; q < 5; ++q) c[q] = src[q];
-            valid = pixel_valid(c, rmin, rmax);
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, valid);
         if (lane == 0) s_warp[warp] = __popc(ballot);
@@ -236,7 +247,7 @@ int pack_tiles(int max_px) { return (max_px + kPackTile - 1) / kPackTile; }
 cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorDev* sensors, const int* frame_ids,
                         int n, int texel_precision, void* texels, float4* pts_pg, float4* pts_n, int* pts_pix,
                         int* n_points, double range_min, double range_max, cudaStream_t s, float4* gtex,
-                        int max_px, int* tile_counts) {
+                        int max_px, int* tile_counts, unsigned char* valid_px) {
     if (n <= 0) return cudaSuccess;
     // float images of the double range limits, rounded inwards (exact decisions for float depths)
     float rmin = (float)range_min, rmax = range_max > (double)FLT_MAX ? FLT_MAX : (float)range_max;
@@ -244,15 +255,16 @@ cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorD
     if ((double)rmax > range_max) rmax = nextafterf(rmax, -FLT_MAX);
     const int max_tiles = pack_tiles(max_px);
     for (int f0 = 0; f0 < n; f0 += 65535) {  // grid.y limit
-        const dim3 grid(max_tiles, n - f0 < 65535 ? n - f0 : 65535);
+        const int nf = n - f0 < 65535 ? n - f0 : 65535;
+        const dim3 grid(max_tiles, nf), grid_px((max_px + kPackThreads - 1) / kPackThreads, nf);
+        k_pack_valid<<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, tile_counts, max_tiles,
+                                                   rmin, rmax);
         if (texel_precision == 1)
-            k_pack_tex<1><<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, texels, tile_counts, max_tiles,
-                                                        rmin, rmax);
+            k_pack_tex<1><<<grid_px, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, texels);
         else
-            k_pack_tex<0><<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, texels, tile_counts, max_tiles,
-                                                        rmin, rmax);
-        k_pack_points<<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, tile_counts, max_tiles,
-                                                    pts_pg, pts_n, pts_pix, n_points, rmin, rmax);
+            k_pack_tex<0><<<grid_px, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, texels);
+        k_pack_points<<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, valid_px, tile_counts,
+                                                    max_tiles, pts_pg, pts_n, pts_pix, n_points);
     }
     if (gtex && max_px > 0) {
         for (int f0 = 0; f0 < n; f0 += 65535) {
