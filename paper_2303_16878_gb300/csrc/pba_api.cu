@@ -52,6 +52,7 @@ struct pba_problem {
     int max_frame_px = 0;
     int* d_tile_counts = nullptr;  // scratch of the two-pass pack: valid pixels per 1024-pixel tile
     unsigned char* d_valid_px = nullptr;  // scratch of the pack: validity of every pixel
+    int* d_frame_iota = nullptr;          // 0 .. N-1 (frame lists of contiguous ranges)
     float4* pts_pg = nullptr;
     float4* pts_n = nullptr;
     int* pts_pix = nullptr;
@@ -392,23 +393,18 @@ int ready(pba_problem* p) {
 // Optionally re-estimates the normals of frames first..first+count-1 (max_radius > 0),
 // then rebuilds their texels and pixel-points and, when a point count changed, the
 // pair plan.  Synchronises.
-int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
-    std::vector<int> ids(count);
-    int max_px = 0;
-    for (int k = 0; k < count; ++k) {
-        ids[k] = first + k;
-        const pba_sensor& S = p->sensors[p->frame_sensor[first + k]];
-        max_px = std::max(max_px, S.width * S.height);
-    }
-    CUDA_TRY(p, cudaMemcpyAsync(p->d_frame_ids, ids.data(), sizeof(int) * count, cudaMemcpyHostToDevice, p->stream));
-    if (max_radius > 0)
-        CUDA_TRY(p, launch_normals(p->raw, p->d_frames, p->d_frame_ids, count, max_px, scale, max_radius,
-                                   p->cfg.range_min, p->cfg.range_max, p->stream));
-    CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_ids, count, p->cfg.texel_precision, p->tex,
-                            p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints, p->cfg.range_min, p->cfg.range_max,
-                            p->stream, p->gtex, p->max_frame_px, p->d_tile_counts, p->d_valid_px));
-    // the id list is pageable host memory: the synchronisation also makes sure
-    // the copy has consumed it
+// Texels, pixel-points and central differences of frames first .. first+count-1 on stream s.
+int pack_frames(pba_problem* p, int first, int count, cudaStream_t s) {
+    CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_iota + first, count,
+                            p->cfg.texel_precision, p->tex, p->pts_pg, p->pts_n, p->pts_pix, p->d_npoints,
+                            p->cfg.range_min, p->cfg.range_max, s, p->gtex, p->max_frame_px, p->d_tile_counts,
+                            p->d_valid_px));
+    return PBA_OK;
+}
+
+// After packing: the frames' point counts on the host, and the pair plan rebuilt
+// when they changed.
+int finish_repack(pba_problem* p) {
     std::vector<int> before = p->n_points;
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     CUDA_TRY(p, cudaMemcpy(p->n_points.data(), p->d_npoints, sizeof(int) * p->N, cudaMemcpyDeviceToHost));
@@ -421,6 +417,21 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
         return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
     }
     return PBA_OK;
+}
+
+int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
+    if (max_radius > 0) {
+        int max_px = 0;
+        for (int k = 0; k < count; ++k) {
+            const pba_sensor& S = p->sensors[p->frame_sensor[first + k]];
+            max_px = std::max(max_px, S.width * S.height);
+        }
+        CUDA_TRY(p, launch_normals(p->raw, p->d_frames, p->d_frame_iota + first, count, max_px, scale, max_radius,
+                                   p->cfg.range_min, p->cfg.range_max, p->stream));
+    }
+    int st = pack_frames(p, first, count, p->stream);
+    if (st) return st;
+    return finish_repack(p);
 }
 
 // The effective variables of the solve from the frames' mapping and the free
@@ -685,8 +696,15 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->prm.grad_mode = cfg->grad_mode;
     p->prm.gtex = p->gtex;
     for (const pba_sensor& S : p->sensors) p->max_frame_px = std::max(p->max_frame_px, S.width * S.height);
-    if (!alloc((void**)&p->d_tile_counts, sizeof(int) * (size_t)p->N * pack_tiles(p->max_frame_px)))
+    if (!alloc((void**)&p->d_tile_counts, sizeof(int) * (size_t)p->N * pack_tiles(p->max_frame_px)) ||
+        !alloc((void**)&p->d_frame_iota, sizeof(int) * (size_t)p->N))
         return bail(PBA_ENOMEM);
+    {
+        std::vector<int> iota(p->N);
+        for (int k = 0; k < p->N; ++k) iota[k] = k;
+        if (cudaMemcpy(p->d_frame_iota, iota.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(PBA_ECUDA);
+    }
     p->grid_full = linearize_grid(cfg->texel_precision, true, 0);
     p->grid_cost = linearize_grid(cfg->texel_precision, false, 0);
     *out = p;
@@ -718,6 +736,7 @@ void pba_destroy(pba_problem* p) {
     dfree(p->gtex);
     dfree(p->d_tile_counts);
     dfree(p->d_valid_px);
+    dfree(p->d_frame_iota);
     dfree(p->pts_pg);
     dfree(p->pts_n);
     dfree(p->pts_pix);
@@ -774,38 +793,41 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
         if (S.width != S0.width || S.height != S0.height)
             return fail(p, PBA_EINVAL, "upload: frames of one call must share the image size");
     }
-    const size_t bytes = sizeof(float) * 5 * (size_t)S0.width * S0.height * count;
+    const size_t frame_bytes = sizeof(float) * 5 * (size_t)S0.width * S0.height;
+    const size_t bytes = frame_bytes * count;
     float* dst = p->raw + 5 * p->px_off[first];
-    const int lanes = p->kCopyLanes;
-    if (is_device || bytes < ((size_t)16 << 20)) {
-        CUDA_TRY(p, cudaMemcpyAsync(dst, channels, bytes,
-                                    is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-    } else {
-        // large host uploads: one copy per lane, in parallel, joined back into the stream
-        if (!p->copy_events[0]) {
-            for (cudaStream_t& c : p->copy_streams) CUDA_TRY(p, cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
-            for (cudaEvent_t& e : p->copy_events) CUDA_TRY(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
-        CUDA_TRY(p, cudaEventRecord(p->copy_events[0], p->stream));
-        const size_t piece = (bytes / lanes + 4095) / 4096 * 4096;
-        for (int l = 0; l < lanes; ++l) {
-            const size_t off = piece * l;
-            if (off >= bytes) break;
-            const size_t len = bytes - off < piece ? bytes - off : piece;
-            cudaStream_t cs = l == 0 ? p->stream : p->copy_streams[l - 1];
-            if (l > 0) CUDA_TRY(p, cudaStreamWaitEvent(cs, p->copy_events[0], 0));
-            CUDA_TRY(p, cudaMemcpyAsync(reinterpret_cast<char*>(dst) + off,
-                                        reinterpret_cast<const char*>(channels) + off, len,
-                                        cudaMemcpyHostToDevice, cs));
-            if (l > 0) {
-                CUDA_TRY(p, cudaEventRecord(p->copy_events[l], cs));
-                CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->copy_events[l], 0));
-            }
-        }
-    }
+    const int lanes = std::min(p->kCopyLanes, count);
     for (int k = first; k < first + count; ++k) p->uploaded[k] = 1;
     p->pyramid_stale = true;
-    return repack(p, first, count, 0.f, 0);
+    if (is_device || bytes < ((size_t)16 << 20) || lanes < 2) {
+        CUDA_TRY(p, cudaMemcpyAsync(dst, channels, bytes,
+                                    is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+        return repack(p, first, count, 0.f, 0);
+    }
+    // large host uploads: the frames are split into lanes of whole frames, each
+    // copied and packed on its own stream (one copy keeps one copy engine busy,
+    // and a lane's packing runs while the other lanes still copy), joined back
+    // into the problem's stream
+    if (!p->copy_events[0]) {
+        for (cudaStream_t& c : p->copy_streams) CUDA_TRY(p, cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : p->copy_events) CUDA_TRY(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    CUDA_TRY(p, cudaEventRecord(p->copy_events[0], p->stream));
+    for (int l = 0; l < lanes; ++l) {
+        const int f0 = first + (int)((long long)count * l / lanes), f1 = first + (int)((long long)count * (l + 1) / lanes);
+        cudaStream_t cs = l == 0 ? p->stream : p->copy_streams[l - 1];
+        if (l > 0) CUDA_TRY(p, cudaStreamWaitEvent(cs, p->copy_events[0], 0));
+        CUDA_TRY(p, cudaMemcpyAsync(reinterpret_cast<char*>(dst) + frame_bytes * (f0 - first),
+                                    reinterpret_cast<const char*>(channels) + frame_bytes * (f0 - first),
+                                    frame_bytes * (f1 - f0), cudaMemcpyHostToDevice, cs));
+        int st = pack_frames(p, f0, f1 - f0, cs);
+        if (st) return st;
+        if (l > 0) {
+            CUDA_TRY(p, cudaEventRecord(p->copy_events[l], cs));
+            CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->copy_events[l], 0));
+        }
+    }
+    return finish_repack(p);
 }
 
 int pba_estimate_normals(pba_problem* p, int first, int count, float scale, int max_radius) {
