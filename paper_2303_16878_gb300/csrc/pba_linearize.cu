@@ -412,7 +412,7 @@ __global__ void k_pair_reduce(const float* __restrict__ partials, const PairStat
     const int p = blockIdx.x;
     const int t = threadIdx.x;
     __shared__ double acc[kNumAcc + 3];
-    __shared__ double H6[36], T[36], HT[36];
+    __shared__ double H6[36], T[36], HT[36], R[9], tv[3];
     const PairStatic P = ps[p];
     const int k0 = full ? 0 : 27;
     if (t >= k0 && t < kNumAcc) {
@@ -438,22 +438,27 @@ __global__ void k_pair_reduce(const float* __restrict__ partials, const PairStat
         }
         return;
     }
+    // T = [[-R^T, 2 R^T [t]x], [0, -R^T]],  R = R_j^T R_i, t = R_j^T (t_i - t_j): once per pair
+    if (t >= 36 && t < 48) {
+        const int2 ij = pf[p];
+        const double* Xi = poses + 12 * ij.x;
+        const double* Xj = poses + 12 * ij.y;
+        const int e = t - 36;
+        if (e < 9) {
+            const int rr = e / 3, cc = e % 3;
+            R[e] = Xj[rr] * Xi[cc] + Xj[4 + rr] * Xi[4 + cc] + Xj[8 + rr] * Xi[8 + cc];
+        } else {
+            const int rr = e - 9;
+            tv[rr] = Xj[rr] * (Xi[3] - Xj[3]) + Xj[4 + rr] * (Xi[7] - Xj[7]) + Xj[8 + rr] * (Xi[11] - Xj[11]);
+        }
+    }
+    __syncthreads();
     if (t < 36) {
         const int r = t / 6, c = t % 6;
         const int a = r < c ? r : c, bb = r < c ? c : r;
         // index of (a, bb) in the row-major upper triangle
         const int idx = a * 6 - a * (a - 1) / 2 + (bb - a);
         H6[t] = acc[idx];
-        // T = [[-R^T, 2 R^T [t]x], [0, -R^T]],  R = R_j^T R_i, t = R_j^T (t_i - t_j)
-        const int2 ij = pf[p];
-        const double* Xi = poses + 12 * ij.x;
-        const double* Xj = poses + 12 * ij.y;
-        double R[9], tv[3];
-        for (int rr = 0; rr < 3; ++rr) {
-            for (int cc = 0; cc < 3; ++cc)
-                R[3 * rr + cc] = Xj[rr] * Xi[cc] + Xj[4 + rr] * Xi[4 + cc] + Xj[8 + rr] * Xi[8 + cc];
-            tv[rr] = Xj[rr] * (Xi[3] - Xj[3]) + Xj[4 + rr] * (Xi[7] - Xj[7]) + Xj[8 + rr] * (Xi[11] - Xj[11]);
-        }
         double val = 0.0;
         if (r < 3 && c < 3) {
             val = -R[3 * c + r];
