@@ -62,6 +62,9 @@ def measured_hbm_gbs() -> float:
 # workload (ncu capture of k_linearize<1, 1, 0, 3>, profiles/k_linearize_lidar_street_50x64x1024.md);
 # to be retaken whenever the kernel changes
 LINEARIZE_DRAM_BYTES = (374.2272 + 11.571712) * 1e6
+# the same capture's unit utilisations (fraction of each unit's peak over the launch):
+# SM issue, the L1 data pipe (the gathers), L2, DRAM
+LINEARIZE_NCU_UNITS = {"sm_issue": 0.729, "l1_data_pipe": 0.588, "l2": 0.213, "dram": 0.041}
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
 NORMAL_MAX_RADIUS = 5
@@ -456,7 +459,9 @@ def main():
                          "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
                          "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak,
                                  "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak,
-                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"}},
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                         "ncu_unit_fracs": LINEARIZE_NCU_UNITS,
+                         "binding": "SM instruction issue, then the L1 data pipe of the gathers"},
             "phase_ms": ph,
             "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
             "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
