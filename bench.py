@@ -43,13 +43,18 @@ UNIT = "residuals/s"
 WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, "
             "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64-refined solve")
 
-# Algorithmic FP32 work of the linearisation kernel (derivation in the design doc):
-# per processed point (transform + spherical projection + bounds) and per
-# valid residual (sampling, residual, Huber, 5 x 6 Jacobian, 6 x 6 accumulation).
+# Algorithmic FP32 work of the linearisation kernel, counted from the formulas as
+# implemented (FMA = 2 FLOP; square root, division and atan2 = 1):
+# per processed point, transform 18 + spherical projection 13 = 31;
+# per valid residual, taps and interpolation 51, residual / Huber / normal
+# rotation 40, image gradients 118, d pi / d pbar 23, five Jacobian rows and
+# their 6 x 6 accumulation 533 = 765.
 FLOP_PER_POINT_SPHERICAL = 31
 FLOP_PER_RESIDUAL_FULL = 765
+
+
 def measured_hbm_gbs() -> float:
-    """HBM copy bandwidth measured on this pool's GB300s (MEASURED_PEAKS.json), else the
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the
     6.8 TB/s fallback of one earlier GB300 measurement."""
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
