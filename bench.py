@@ -64,7 +64,7 @@ def measured_hbm_gbs() -> float:
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch on this
-# workload (ncu capture of k_linearize<1, 1, 0, 3>, profiles/k_linearize_lidar_street_50x64x1024.md);
+# workload (ncu --set full capture of k_linearize<1, 1, 0, 3>, one launch after the autotuner's);
 # to be retaken whenever the kernel changes
 LINEARIZE_DRAM_BYTES = (374.2272 + 11.571712) * 1e6
 # the same capture's unit utilisations (fraction of each unit's peak over the launch):
