@@ -480,15 +480,22 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 if (warp == 0) {
                     float s = 0.f;
                     for (int i = k + 1; i < nt; ++i) s += cbin[(q * nt + i) * kT + lane];
-                    const float t = yfull[k * kT + lane] - s;
+                    // t goes through shared memory (the row's residual slot is free
+                    // during the backward sweep) so that it is read back as broadcasts
+                    float* tt = rv + q * kT;
+                    tt[lane] = yfull[k * kT + lane] - s;
+                    __syncwarp();
                     const float* D = dinv + q * kTF;
-                    float z0 = 0.f, z1 = 0.f;
+                    float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-                    for (int m = 0; m < kT; m += 2) {
-                        z0 = fmaf(D[m * kLd + lane], __shfl_sync(0xffffffffu, t, m), z0);
-                        z1 = fmaf(D[(m + 1) * kLd + lane], __shfl_sync(0xffffffffu, t, m + 1), z1);
+                    for (int m = 0; m < kT; m += 4) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tt + m);
+                        z0 = fmaf(D[m * kLd + lane], t4.x, z0);
+                        z1 = fmaf(D[(m + 1) * kLd + lane], t4.y, z1);
+                        z2 = fmaf(D[(m + 2) * kLd + lane], t4.z, z2);
+                        z3 = fmaf(D[(m + 3) * kLd + lane], t4.w, z3);
                     }
-                    const float z = z0 + z1;
+                    const float z = (z0 + z1) + (z2 + z3);
                     for (int d = 0; d < C; ++d) dsm_st(dsm_addr(zfull + k * kT + lane, d), z);
                 }
                 __syncthreads();
@@ -496,13 +503,16 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 for (int m = warp; m < k; m += kCsWarps) {
                     const float* L = own_tile(q, m);
                     const float* z = zfull + k * kT;
-                    float s0 = 0.f, s1 = 0.f;
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-                    for (int r = 0; r < kT; r += 2) {
-                        s0 = fmaf(L[r * kLd + lane], z[r], s0);
-                        s1 = fmaf(L[(r + 1) * kLd + lane], z[r + 1], s1);
+                    for (int r = 0; r < kT; r += 4) {
+                        const float4 z4 = *reinterpret_cast<const float4*>(z + r);
+                        s0 = fmaf(L[r * kLd + lane], z4.x, s0);
+                        s1 = fmaf(L[(r + 1) * kLd + lane], z4.y, s1);
+                        s2 = fmaf(L[(r + 2) * kLd + lane], z4.z, s2);
+                        s3 = fmaf(L[(r + 3) * kLd + lane], z4.w, s3);
                     }
-                    dsm_st(dsm_addr(cbin + ((m / C) * nt + k) * kT + lane, m % C), s0 + s1);
+                    dsm_st(dsm_addr(cbin + ((m / C) * nt + k) * kT + lane, m % C), (s0 + s1) + (s2 + s3));
                 }
             }
             cl.sync();
