@@ -539,16 +539,25 @@ __global__ void __launch_bounds__(kCsThreads, 1)
     cl.sync();
 }
 
-int g_cs_cmax = -1;     // largest usable cluster size (0: none)
-int g_cs_smem_max = 0;  // opt-in shared memory per block
+// per device: largest usable cluster size (-1: not queried yet, 0: none) and
+// the opt-in shared memory per block
+constexpr int kCsMaxDevices = 64;
+int g_cs_cmax[kCsMaxDevices];
+int g_cs_smem_max[kCsMaxDevices];
+bool g_cs_init_done = false;
 
 }  // namespace
 
 bool solve_cluster_init() {
-    if (g_cs_cmax >= 0) return g_cs_cmax > 0;
-    g_cs_cmax = 0;
+    if (!g_cs_init_done) {
+        for (int d = 0; d < kCsMaxDevices; ++d) g_cs_cmax[d] = -1;
+        g_cs_init_done = true;
+    }
     int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCsMaxDevices) return false;
+    int& cmax = g_cs_cmax[dev];
+    if (cmax >= 0) return cmax > 0;
+    cmax = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
     if (cudaFuncSetAttribute(k_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
         cudaFuncSetAttribute(k_solve_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -569,19 +578,22 @@ bool solve_cluster_init() {
         cfg.numAttrs = 1;
         int clusters = 0;
         if (cudaOccupancyMaxActiveClusters(&clusters, k_solve_cluster, &cfg) == cudaSuccess && clusters > 0) {
-            g_cs_cmax = c;
+            cmax = c;
             break;
         }
         cudaGetLastError();
     }
-    g_cs_smem_max = optin;
-    return g_cs_cmax > 0;
+    g_cs_smem_max[dev] = optin;
+    return cmax > 0;
 }
 
 bool solve_cluster_plan(int n_pad, CsGeom* g) {
     if (!solve_cluster_init() || n_pad <= 0 || n_pad % kT) return false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int cmax = g_cs_cmax[dev];
     const int nt = n_pad / kT;
-    const int C = nt < g_cs_cmax ? nt : g_cs_cmax;
+    const int C = nt < cmax ? nt : cmax;
     const int R = cs_rows(0, nt, C);
     int slots = 0;
     for (int r = 0; r < C; ++r) {
@@ -629,7 +641,7 @@ bool solve_cluster_plan(int n_pad, CsGeom* g) {
     o = al(o + 4LL * 4 * kT);
     h.o_dsc32 = (int)o;
     o = al(o + 4LL * n_pad);
-    if (o > g_cs_smem_max) return false;
+    if (o > g_cs_smem_max[dev]) return false;
     h.bytes = (int)o;
     *g = h;
     return true;
