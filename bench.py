@@ -66,10 +66,10 @@ def measured_hbm_gbs() -> float:
 # dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch on this
 # workload (ncu --set full capture of k_linearize<1, 1, 0, 3>, one launch after the autotuner's);
 # to be retaken whenever the kernel changes
-LINEARIZE_DRAM_BYTES = (374.2272 + 11.571712) * 1e6
+LINEARIZE_DRAM_BYTES = (370.882048 + 11.2384) * 1e6
 # the same capture's unit utilisations (fraction of each unit's peak over the launch):
 # SM issue, the L1 data pipe (the gathers), L2, DRAM
-LINEARIZE_NCU_UNITS = {"sm_issue": 0.729, "l1_data_pipe": 0.588, "l2": 0.213, "dram": 0.041}
+LINEARIZE_NCU_UNITS = {"sm_issue": 0.727, "l1_data_pipe": 0.575, "l2": 0.216, "dram": 0.041}
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
 NORMAL_MAX_RADIUS = 5

@@ -9,8 +9,9 @@
 //                 residual e = zeta(pbar) - I_j(u') (Supp., Eq. error-jacobian),
 //                 Huber weight, Jacobian J_i, and accumulation of the 6x6
 //                 H6 = sum w J_i^T Omega J_i, b6 = sum w J_i^T Omega e, cost, count
-//                 in FP32 registers; warp shuffles give one FP32 partial per
-//                 work item (no global atomics on residuals).
+//                 in FP32 registers; a transposed table in the warp's shared
+//                 memory (and shuffles for cost and count) gives one FP32 partial
+//                 per work item (no global atomics on residuals).
 // k_pair_reduce   FP64 sum of a pair's chunk partials in a fixed order, then the
 //                 pair's full 12x12 block from J_j = J_i T (see below).
 //
@@ -216,7 +217,8 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
                 const void* __restrict__ tex, const LinParams prm, float* __restrict__ partials,
                 uint32_t* __restrict__ mask_bits) {
-    __shared__ float s_q[FULL ? kLinWarps : 1][kQItems][kQueue];
+    __shared__ __align__(16) float s_q[FULL ? kLinWarps : 1][kQItems][kQueue];
+    static_assert(27 * 32 <= kQItems * kQueue, "the reduction table must fit the queue region");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float om[5] = {prm.w_int, prm.w_depth, prm.w_normal, prm.w_normal, prm.w_normal};
     float(*Q)[kQueue] = s_q[FULL ? warp : 0];
@@ -382,16 +384,31 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
             __syncwarp();
         }
 
-        // a7: warp reduction, one FP32 partial per work item (lane t writes sum t)
+        // a7: warp reduction, one FP32 partial per work item (lane t writes sum t).
+        // H6 and b6 go through the warp's queue region, empty at this point: lane l
+        // writes its 27 sums as column l of a 27 x 32 table, lane j < 27 adds row j.
         float mine = 0.f;
         if (FULL) {
+            float* tab = &Q[0][0];  // 27 x 32 floats <= kQItems x kQueue
 #pragma unroll
-            for (int j = 0; j < 27; ++j) {
-                float x = j < 21 ? Hacc[j] : bacc[j - 21];
+            for (int j = 0; j < 27; ++j) tab[j * 32 + lane] = j < 21 ? Hacc[j] : bacc[j - 21];
+            __syncwarp();
+            if (lane < 27) {
+                // rows start on bank 0: lane j reads its row from float4 (q + j) mod 8 on,
+                // so that the 8 lanes of a quarter-warp hit 8 different bank quads
+                const float4* row = reinterpret_cast<const float4*>(tab + lane * 32);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == j) mine = x;
+                for (int q = 0; q < 8; ++q) {
+                    const float4 v = row[(q + lane) & 7];
+                    s0 += v.x;
+                    s1 += v.y;
+                    s2 += v.z;
+                    s3 += v.w;
+                }
+                mine = (s0 + s1) + (s2 + s3);
             }
+            __syncwarp();  // the next work item's queue writes come after these reads
         }
 #pragma unroll
         for (int j = 27; j < kNumAcc; ++j) {
