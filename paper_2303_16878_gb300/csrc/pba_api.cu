@@ -18,7 +18,8 @@ using namespace pba;
 
 namespace {
 
-constexpr int kChunk = 1024;  // points per work item (one warp) of the persistent launch
+constexpr int kChunk = 1024;     // points per work item (one warp) of the persistent launch
+constexpr int kChunkTail = 256;  // ... in the last stretch of the queue, so that the warps finish closer together
 
 }  // namespace
 
@@ -1006,11 +1007,24 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
         pf[q] = make_int2(i, j);
         for (int e = 0; e < 12; ++e) pxo[12 * q + e] = S.extrinsic[e];
     }
+    // the queue hands items out in order; about one item per resident warp at its
+    // end is cut into short ones, so that the last warps to finish are not left
+    // with a whole long item while the others idle
+    long long total_pts = 0;
+    for (int q = 0; q < m; ++q) total_pts += ps[q].n_points;
+    const long long resident = (long long)std::max(p->grid_full, 1) * 8;
+    const long long tail_start = total_pts - std::min(total_pts / 4, resident * kChunk);
+    long long done_pts = 0;
     for (int oi = 0; oi < m; ++oi) {
         const int q = order[oi];
         ps[q].chunk_begin = (int)chunks.size();
-        for (int s = 0; s < ps[q].n_points; s += kChunk)
-            chunks.push_back(make_int4(q, s, std::min(kChunk, ps[q].n_points - s), 0));
+        for (int s = 0; s < ps[q].n_points;) {
+            const int size = done_pts + s >= tail_start ? kChunkTail : kChunk;
+            const int n = std::min(size, ps[q].n_points - s);
+            chunks.push_back(make_int4(q, s, n, 0));
+            s += n;
+        }
+        done_pts += ps[q].n_points;
         ps[q].chunk_end = (int)chunks.size();
     }
     p->n_chunks = (int)chunks.size();

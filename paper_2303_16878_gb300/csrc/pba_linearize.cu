@@ -423,27 +423,42 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
 
 // ------------------------------------------------------------ pair reduction
 
-__global__ void k_pair_reduce(const float* __restrict__ partials, const PairStatic* __restrict__ ps,
+constexpr int kPairSlices = 8;  // threads summing one accumulator of a pair (one warp per slice)
+
+__global__ void __launch_bounds__(32 * kPairSlices) k_pair_reduce(const float* __restrict__ partials, const PairStatic* __restrict__ ps,
                               const int2* __restrict__ pf, const double* __restrict__ poses, bool full,
                               double* __restrict__ blocks) {
     const int p = blockIdx.x;
     const int t = threadIdx.x;
     __shared__ double acc[kNumAcc + 3];
+    __shared__ double part[kPairSlices][kNumAcc];
     __shared__ double H6[36], T[36], HT[36], R[9], tv[3];
     const PairStatic P = ps[p];
     const int k0 = full ? 0 : 27;
-    if (t >= k0 && t < kNumAcc) {
-        // chunk order; 8 loads in flight, added in that order
-        double s = 0.0;
-        for (int c0 = P.chunk_begin; c0 < P.chunk_end; c0 += 8) {
-            float v[8];
+    // thread (slice, j) sums accumulator j over its contiguous slice of the pair's
+    // chunks in chunk order (4 loads in flight), then the slices are added in order
+    {
+        const int j = t % 32, slice = t / 32;
+        const int n = P.chunk_end - P.chunk_begin;
+        const int c_lo = P.chunk_begin + (int)((long long)n * slice / kPairSlices);
+        const int c_hi = P.chunk_begin + (int)((long long)n * (slice + 1) / kPairSlices);
+        if (j >= k0 && j < kNumAcc) {
+            double s = 0.0;
+            for (int c0 = c_lo; c0 < c_hi; c0 += 4) {
+                float v[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = c0 + u < P.chunk_end ? partials[(long long)(c0 + u) * kPartialStride + t] : 0.f;
+                for (int u = 0; u < 4; ++u) v[u] = c0 + u < c_hi ? partials[(long long)(c0 + u) * kPartialStride + j] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < P.chunk_end) s += (double)v[u];
+                for (int u = 0; u < 4; ++u)
+                    if (c0 + u < c_hi) s += (double)v[u];
+            }
+            part[slice][j] = s;
         }
+    }
+    __syncthreads();
+    if (t >= k0 && t < kNumAcc) {
+        double s = 0.0;
+        for (int slice = 0; slice < kPairSlices; ++slice) s += part[slice][t];
         acc[t] = s;
     }
     __syncthreads();
@@ -586,7 +601,7 @@ cudaError_t launch_pair_reduce(const float* partials, const PairStatic* ps, cons
                                cudaStream_t s) {
     (void)pair_Xo;
     if (m <= 0) return cudaSuccess;
-    k_pair_reduce<<<m, 64, 0, s>>>(partials, ps, pair_frames, poses, full, blocks);
+    k_pair_reduce<<<m, 32 * kPairSlices, 0, s>>>(partials, ps, pair_frames, poses, full, blocks);
     return cudaGetLastError();
 }
 
