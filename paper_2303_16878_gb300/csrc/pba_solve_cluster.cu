@@ -38,6 +38,8 @@
 // until the others have finished reading it.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "pba_internal.cuh"
 
 namespace pba {
@@ -545,10 +547,12 @@ constexpr int kCsMaxDevices = 64;
 int g_cs_cmax[kCsMaxDevices];
 int g_cs_smem_max[kCsMaxDevices];
 bool g_cs_init_done = false;
+std::mutex g_cs_mutex;  // problems may be created from several host threads
 
 }  // namespace
 
 bool solve_cluster_init() {
+    std::lock_guard<std::mutex> lock(g_cs_mutex);
     if (!g_cs_init_done) {
         for (int d = 0; d < kCsMaxDevices; ++d) g_cs_cmax[d] = -1;
         g_cs_init_done = true;
@@ -591,7 +595,12 @@ bool solve_cluster_plan(int n_pad, CsGeom* g) {
     if (!solve_cluster_init() || n_pad <= 0 || n_pad % kT) return false;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int cmax = g_cs_cmax[dev];
+    int cmax, smem_max;
+    {
+        std::lock_guard<std::mutex> lock(g_cs_mutex);
+        cmax = g_cs_cmax[dev];
+        smem_max = g_cs_smem_max[dev];
+    }
     const int nt = n_pad / kT;
     const int C = nt < cmax ? nt : cmax;
     const int R = cs_rows(0, nt, C);
@@ -641,7 +650,7 @@ bool solve_cluster_plan(int n_pad, CsGeom* g) {
     o = al(o + 4LL * 4 * kT);
     h.o_dsc32 = (int)o;
     o = al(o + 4LL * n_pad);
-    if (o > g_cs_smem_max[dev]) return false;
+    if (o > smem_max) return false;
     h.bytes = (int)o;
     *g = h;
     return true;
