@@ -228,16 +228,40 @@ __global__ void __launch_bounds__(kAdjThreads)
 }
 
 // Per pair: FP64 sums of its work items, then the matrix gradients.
+constexpr int kAdjSlices = 8;  // slices of a pair's work items summed in parallel
+
 __global__ void k_adjoint_pairs(const float* __restrict__ partials, const PairStatic* __restrict__ ps,
                                 const int2* __restrict__ pf, const double* __restrict__ poses,
                                 const double* __restrict__ pair_Xo, int m, double* __restrict__ out) {
     const int q = blockIdx.x;
     if (q >= m) return;
     __shared__ double S[kAdjAcc];
+    __shared__ double part[kAdjSlices][kAdjAcc];
     const PairStatic P = ps[q];
+    // thread (slice, t) sums sum t over its contiguous slice of the pair's work
+    // items in order (4 loads in flight); the slices are then added in order
+    {
+        const int n = P.chunk_end - P.chunk_begin;
+        for (int e = threadIdx.x; e < kAdjSlices * kAdjAcc; e += blockDim.x) {
+            const int slice = e / kAdjAcc, t = e % kAdjAcc;
+            const int c_lo = P.chunk_begin + (int)((long long)n * slice / kAdjSlices);
+            const int c_hi = P.chunk_begin + (int)((long long)n * (slice + 1) / kAdjSlices);
+            double s = 0.0;
+            for (int c0 = c_lo; c0 < c_hi; c0 += 4) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = c0 + u < c_hi ? partials[(long long)(c0 + u) * kAdjStride + t] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (c0 + u < c_hi) s += (double)v[u];
+            }
+            part[slice][t] = s;
+        }
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < kAdjAcc; t += blockDim.x) {
         double s = 0.0;
-        for (int c = P.chunk_begin; c < P.chunk_end; ++c) s += (double)partials[(long long)c * kAdjStride + t];
+        for (int slice = 0; slice < kAdjSlices; ++slice) s += part[slice][t];
         S[t] = s;
     }
     __syncthreads();
@@ -406,7 +430,7 @@ cudaError_t launch_adjoint_reduce(const float* partials, const PairStatic* ps, c
                                   const AsmContrib* contrib, const int* frame_sensor, int n_sensors,
                                   double* d_poses, double* d_ext, double* totals, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    k_adjoint_pairs<<<m, 64, 0, s>>>(partials, ps, pf, poses, pair_Xo, m, pair_out);
+    k_adjoint_pairs<<<m, 256, 0, s>>>(partials, ps, pf, poses, pair_Xo, m, pair_out);
     if (d_poses) k_adjoint_frames<<<n_tasks, 32, 0, s>>>(tasks, n_tasks, contrib, pair_out, d_poses);
     k_adjoint_sensors<<<n_sensors, 32, 0, s>>>(ps, frame_sensor, m, pair_out, n_sensors, d_ext, totals);
     return cudaGetLastError();
