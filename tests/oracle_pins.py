@@ -45,6 +45,7 @@ PIN_TOL = {
     "variables_reduce_to_gauge": 1e-12,
     "offset_jacobian_fd": 1e-6,
     "offset_gradient_fd": 1e-4,  # central differences of F at h = 2e-8 (roundoff eps F / h)
+    "residual_brute_force": 1e-9,
 }
 
 
@@ -759,6 +760,146 @@ def pin_offset_gradient_fd(O, lib, w):
     return worst
 
 
+# ------------------------------------------------- the residual by brute force
+
+def _h44(X):
+    M = np.eye(4)
+    M[:3] = np.asarray(X, dtype=np.float64).reshape(3, 4)
+    return M
+
+
+def _bf_residuals(s, params, src, tgt, Xi, Xj, pix):
+    """Residuals of the source pixels `pix` (row * W + col) of image `src`
+    against `tgt`, evaluated from the definitions with homogeneous 4 x 4
+    matrices and scipy's order-1 spline, vectorised over the points:
+    p_u = X_o pi^-1(u, d) (Sec. III), pbar = X_o^-1 X_j^-1 X_i p_u (Eq. uprime),
+    u' = pi(pbar), a pixel valid iff range_min <= d <= range_max, d > 0 and
+    |n| > 0.5 (Sec. IV-A), a texel usable iff it and its four neighbours are
+    valid, the four bilinear taps usable (pinhole window 1 <= u' < W - 2, every
+    model 1 <= v' < H - 2, spherical columns wrapping), zeta = (g_u, depth or
+    range of pbar, rotated n_u) (Supp.), the occlusion and target-normal tests,
+    chi^2 = e^T Omega e and the Huber rho of Eq. total-error-multicue.
+    Returns (valid, e, rho, reason) with reason 0 valid, 1 depth limit,
+    2 window, 3 not usable, 4 occlusion, 5 target normal."""
+    from scipy.ndimage import map_coordinates
+    H, W = s.height, s.width
+    src = src.astype(np.float64)
+    tgt64 = tgt.astype(np.float64)
+    rows, cols = pix // W, pix % W
+    d = src[rows, cols, 1]
+    u0, v0 = cols.astype(np.float64), rows.astype(np.float64)
+    if s.model == 0:
+        p = np.stack([(u0 - s.cx) / s.fx * d, (v0 - s.cy) / s.fy * d, d], axis=1)
+    else:
+        az, el = (u0 - s.cx) / s.fx, (v0 - s.cy) / s.fy
+        p = d[:, None] * np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=1)
+    Xo = _h44(s.extrinsic)
+    A = np.linalg.inv(Xo) @ np.linalg.inv(_h44(Xj)) @ _h44(Xi) @ Xo
+    pb = p @ A[:3, :3].T + A[:3, 3]
+    nb = src[rows, cols, 2:5] @ A[:3, :3].T
+    if s.model == 0:
+        zeta_d = pb[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = s.fx * pb[:, 0] / pb[:, 2] + s.cx
+            v = s.fy * pb[:, 1] / pb[:, 2] + s.cy
+    else:
+        zeta_d = np.linalg.norm(pb, axis=1)
+        u = s.fx * np.arctan2(pb[:, 1], pb[:, 0]) + s.cx
+        v = s.fy * np.arctan2(pb[:, 2], np.hypot(pb[:, 0], pb[:, 1])) + s.cy
+    n2 = (tgt64[..., 2:5] ** 2).sum(-1)
+    dt = tgt64[..., 1]
+    valid_px = (dt > 0) & (dt >= params["range_min"]) & (dt <= params["range_max"]) & (n2 > 0.25)
+    img = tgt64
+    if s.model == 1:  # wrap columns: three copies side by side, u shifted into the middle one
+        valid_px = np.concatenate([valid_px] * 3, axis=1)
+        img = np.concatenate([tgt64] * 3, axis=1)
+    usable = np.zeros_like(valid_px)
+    usable[1:-1, 1:-1] = (valid_px[1:-1, 1:-1] & valid_px[:-2, 1:-1] & valid_px[2:, 1:-1]
+                          & valid_px[1:-1, :-2] & valid_px[1:-1, 2:])
+    reason = np.zeros(len(pix), dtype=np.int64)
+    reason[~(zeta_d > params["z_min"])] = 1
+    in_win = (v >= 1.0) & (v < H - 2)
+    if s.model == 0:
+        in_win &= (u >= 1.0) & (u < W - 2)
+    reason[(reason == 0) & ~in_win] = 2
+    live = reason == 0
+    uu = np.where(live, u + (W if s.model == 1 else 0), 1.0)
+    vv = np.where(live, v, 1.0)
+    c0, r0 = np.floor(uu).astype(np.int64), np.floor(vv).astype(np.int64)
+    taps_ok = usable[r0, c0] & usable[r0, c0 + 1] & usable[r0 + 1, c0] & usable[r0 + 1, c0 + 1]
+    reason[live & ~taps_ok] = 3
+    I = np.stack([map_coordinates(img[..., c], [vv, uu], order=1) for c in range(5)], axis=1)
+    occ = np.abs(zeta_d - I[:, 1]) > params["occ_abs"] + params["occ_rel"] * zeta_d
+    reason[(reason == 0) & occ] = 4
+    reason[(reason == 0) & (np.linalg.norm(I[:, 2:5], axis=1) < 0.5)] = 5
+    e = np.column_stack([src[rows, cols, 0], zeta_d, nb]) - I
+    om = np.array([params["w_int"], params["w_depth"]] + [params["w_normal"]] * 3)
+    chi = np.sqrt((om * e * e).sum(1))
+    delta = params["huber_delta"]
+    rho = np.where(chi <= delta, chi * chi, 2 * delta * chi - delta * delta)
+    return reason == 0, e, rho, reason, p @ Xo[:3, :3].T + Xo[:3, 3]
+
+
+def _residual_case(O, lib, w, params, reasons, stride):
+    s = w.sensors[0]
+    Ro = np.asarray(s.extrinsic, dtype=np.float64).reshape(3, 4)[:, :3]
+    om = np.array([params["w_int"], params["w_depth"]] + [params["w_normal"]] * 3)
+    worst = 0.0
+    for i, j in np.asarray(w.pairs)[:4]:
+        pts, pix = O.frame_points(s, params, w.channels[i], lib=lib)
+        pix = np.asarray(pix, dtype=np.int64)
+        ok, e, rho, reason, pu = _bf_residuals(s, params, w.channels[i], w.channels[j],
+                                               w.poses_init[i], w.poses_init[j], pix)
+        src = w.channels[i].reshape(-1, 5).astype(np.float64)
+        worst = max(worst, float(np.abs(pts[:, :3] - pu).max()),
+                    float(np.abs(pts[:, 3] - src[pix, 0]).max()),
+                    float(np.abs(pts[:, 4:7] - src[pix, 2:5] @ Ro.T).max()))
+        for k in range(0, len(pix), stride):
+            r = O.point_residual(s, params, w.channels[j], w.poses_init[i], w.poses_init[j], pts[k], lib=lib)
+            if r["flag"]:
+                continue
+            reasons[reason[k]] += 1
+            if r["valid"] != bool(ok[k]):
+                return 1.0
+            if r["valid"]:
+                reasons[6] += int(rho[k] < e[k] @ (om * e[k]) - 1e-12)   # on the linear branch of Huber
+                worst = max(worst, float(np.abs(r["e"] - e[k]).max()),
+                            abs(r["rho"] - rho[k]) / max(1.0, abs(rho[k])))
+    return worst
+
+
+def _flipped_normal_columns(w, every=7):
+    """Every `every`-th column of each image with its normal negated: bilinear
+    samples between such a column and its neighbour have |n| < 0.5."""
+    import dataclasses
+    chans = []
+    for c in w.channels:
+        c = c.copy()
+        c[:, ::every, 2:5] *= -1.0
+        chans.append(c)
+    return dataclasses.replace(w, channels=chans)
+
+
+def pin_residual_brute_force(O, lib, room, street, stride=3):
+    """Per-point validity, e and rho of the oracle against `_bf_residuals`, on
+    the RGB-D room (with and without a sensor offset), the LiDAR street, and the
+    room with flipped normal columns and z_min = 2 m, at thresholds that make
+    every rejection rule and the Huber branch fire (tight occlusion bounds,
+    delta below typical chi).  Points whose decision the oracle flags as within
+    its margin are skipped; every other point must agree in validity, and valid
+    points in e and rho.  The source points themselves (p_u, g_u, n_u^o) are
+    checked against the same unprojection."""
+    base = dict(w_depth=0.5, w_normal=0.3, huber_delta=0.05, occ_abs=0.02, occ_rel=0.01)
+    reasons = np.zeros(7, dtype=np.int64)
+    worst = 0.0
+    for w, over in ((room, {}), (street, {}), (_with_offset(room), {}),
+                    (_flipped_normal_columns(room), dict(z_min=2.0))):
+        worst = max(worst, _residual_case(O, lib, w, dict(w.params, **base, **over), reasons, stride))
+    # valid, depth limit, window, not usable, occlusion, target normal, Huber's linear branch
+    assert reasons[0] > 100 and np.all(reasons[1:] > 0), reasons
+    return worst
+
+
 def all_pins(O, lib, room, street):
     """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
     return {
@@ -785,4 +926,5 @@ def all_pins(O, lib, room, street):
         "coarse_to_fine": pin_coarse_to_fine(O, lib),
         "offset_jacobian_fd": pin_offset_jacobian_fd(O, lib, room),
         "offset_gradient_fd": pin_offset_gradient_fd(O, lib, room),
+        "residual_brute_force": pin_residual_brute_force(O, lib, room, street),
     }

@@ -35,6 +35,16 @@ MUTATIONS = {
     "offset_jacobian_drops_target": ("s += (Ji[6 * r + k] + Jj[6 * r + k]) * A[6 * k + c];",
                                      "s += Ji[6 * r + k] * A[6 * k + c];"),
     "offset_map_rotation_transposed": ("A[6 * r + c] = Ro[3 * r + c];", "A[6 * r + c] = Ro[3 * c + r];"),
+    "huber_rho_constant_sign": ("*rho = 2.0 * prm->huber_delta * chi - prm->huber_delta * prm->huber_delta;",
+                                "*rho = 2.0 * prm->huber_delta * chi + prm->huber_delta * prm->huber_delta;"),
+    "occlusion_relative_term_dropped": ("double thr = prm->occ_abs + prm->occ_rel * zd;", "double thr = prm->occ_abs;"),
+    "target_normal_threshold_squared": ("if (nt < 0.5 && ", "if (nt < 0.25 && "),
+    "z_min_ignored": ("if (!(zd > prm->z_min) && ", "if (!(zd > 0.0) && "),
+    "stencil_corner_for_edge_texel": ("{1, -1}, {1, 0}, {1, 1}, {1, 2}, {2, 0}, {2, 1}};",
+                                      "{1, -1}, {1, 0}, {1, 1}, {1, 2}, {2, 0}, {2, 2}};"),
+    "pinhole_window_one_column_short": ("u >= 1.0 && u < (double)(s->width - 2)", "u >= 1.0 && u < (double)(s->width - 3)"),
+    "range_cue_horizontal_only": ("zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1] + pb[2] * pb[2]);",
+                                  "zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1]);"),
 }
 
 
@@ -62,7 +72,8 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("extrinsic_equivalence", lambda: P.pin_extrinsic_equivalence(oracle_lib, lib, room3)),
                     ("jacobian_fd_extrinsic", lambda: P.pin_jacobian_fd_extrinsic(oracle_lib, lib, room3)),
                     ("offset_jacobian_fd", lambda: P.pin_offset_jacobian_fd(oracle_lib, lib, room3)),
-                    ("offset_gradient_fd", lambda: P.pin_offset_gradient_fd(oracle_lib, lib, room3))]:
+                    ("offset_gradient_fd", lambda: P.pin_offset_gradient_fd(oracle_lib, lib, room3)),
+                    ("residual_brute_force", lambda: P.pin_residual_brute_force(oracle_lib, lib, room3, street3))]:
         try:
             err = fn()
         except (AssertionError, ValueError, ArithmeticError, Exception):

@@ -217,3 +217,10 @@ def test_offset_jacobian_matches_finite_differences(oracle_lib, room3):
 
 def test_offset_gradient_is_twice_b_o(oracle_lib, room3):
     assert P.pin_offset_gradient_fd(oracle_lib, oracle_lib.load(), room3) < P.PIN_TOL["offset_gradient_fd"]
+
+
+def test_residuals_match_brute_force(oracle_lib, room3, street3):
+    """Validity, e and rho of every rule (depth limit, window, usable taps,
+    occlusion, target normal, both Huber branches) against a vectorised
+    evaluation from the definitions."""
+    assert P.pin_residual_brute_force(oracle_lib, oracle_lib.load(), room3, street3) < P.PIN_TOL["residual_brute_force"]
