@@ -131,7 +131,11 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out);
 /* Free the problem and its device memory (synchronises its stream). NULL is a no-op. */
 void pba_destroy(pba_problem* p);
 
-/* Message of the last failed call on p (static text when p is NULL). */
+/* Message of the last failed call on p.  With p NULL: the message of the
+ * calling thread's last failed pba_create (which has no problem to hold it;
+ * for example no CUDA device: the library has no CPU path), or "null problem"
+ * when there was none.  The text stays valid until the next failing call on p
+ * (or, for NULL, the thread's next failing pba_create). */
 const char* pba_last_error(const pba_problem* p);
 
 /* Order all further device work on cuda_stream (NULL: the problem's own stream). */

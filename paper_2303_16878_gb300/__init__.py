@@ -73,7 +73,8 @@ class Problem:
         st = self._lib.pba_create(ctypes.byref(cfg), ctypes.c_void_p(self._stream_handle(stream)),
                                   ctypes.byref(self._h))
         if st != 0:
-            raise PbaError(st, "pba_create failed")
+            msg = self._lib.pba_last_error(None)
+            raise PbaError(st, msg.decode() if msg else "pba_create failed")
 
     @staticmethod
     def _stream_handle(stream) -> int:

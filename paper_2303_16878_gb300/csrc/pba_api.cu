@@ -524,27 +524,48 @@ int sync_offsets_to_host(pba_problem* p) {
 
 extern "C" {
 
+// message of the calling thread's last failed pba_create (no problem exists to hold it)
+thread_local std::string t_create_err;
+
+static int create_fail(int code, const std::string& what) {
+    t_create_err = "pba_create: " + what;
+    return code;
+}
+
 const char* pba_last_error(const pba_problem* p) {
-    if (!p) return "null problem";
+    if (!p) return t_create_err.empty() ? "null problem" : t_create_err.c_str();
     return p->err.c_str();
 }
 
 int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
-    if (!cfg || !out) return PBA_EINVAL;
+    if (!cfg || !out) return create_fail(PBA_EINVAL, "null configuration or output pointer");
     *out = nullptr;
-    if (cfg->n_frames < 1 || cfg->n_sensors < 1 || !cfg->sensors) return PBA_EINVAL;
-    if (!(cfg->huber_delta > 0.0)) return PBA_EINVAL;
-    if (cfg->grad_mode != 0 && cfg->grad_mode != 1) return PBA_EINVAL;
-    if (cfg->texel_precision != 0 && cfg->texel_precision != 1) return PBA_EINVAL;
-    if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return PBA_EINVAL;
+    if (cfg->n_frames < 1 || cfg->n_sensors < 1 || !cfg->sensors)
+        return create_fail(PBA_EINVAL, "n_frames and n_sensors must be >= 1 with a sensor array");
+    if (!(cfg->huber_delta > 0.0)) return create_fail(PBA_EINVAL, "huber_delta must be > 0");
+    if (cfg->grad_mode != 0 && cfg->grad_mode != 1) return create_fail(PBA_EINVAL, "grad_mode must be 0 or 1");
+    if (cfg->texel_precision != 0 && cfg->texel_precision != 1)
+        return create_fail(PBA_EINVAL, "texel_precision must be PBA_TEXEL_F32 or PBA_TEXEL_F16");
+    if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return create_fail(PBA_EINVAL, "unknown path");
     if (cfg->solver != PBA_SOLVE_CHOLESKY_F64 && cfg->solver != PBA_SOLVE_MIXED &&
         cfg->solver != PBA_SOLVE_MIXED_STEPS)
-        return PBA_EINVAL;
+        return create_fail(PBA_EINVAL, "unknown solver");
     for (int s = 0; s < cfg->n_sensors; ++s) {
         const pba_sensor& S = cfg->sensors[s];
-        if ((S.model != PBA_PINHOLE && S.model != PBA_SPHERICAL) || S.width < 4 || S.height < 4) return PBA_EINVAL;
-        if (S.fx == 0.0 || S.fy == 0.0) return PBA_EINVAL;
-        if ((long long)S.width * S.height > (1LL << 30)) return PBA_EINVAL;
+        if ((S.model != PBA_PINHOLE && S.model != PBA_SPHERICAL) || S.width < 4 || S.height < 4)
+            return create_fail(PBA_EINVAL, "sensor " + std::to_string(s) + ": unknown model or image below 4 x 4");
+        if (S.fx == 0.0 || S.fy == 0.0) return create_fail(PBA_EINVAL, "sensor " + std::to_string(s) + ": zero focal length");
+        if ((long long)S.width * S.height > (1LL << 30))
+            return create_fail(PBA_EINVAL, "sensor " + std::to_string(s) + ": more than 2^30 pixels");
+    }
+    {
+        int n_dev = 0;
+        const cudaError_t e = cudaGetDeviceCount(&n_dev);
+        if (e != cudaSuccess || n_dev < 1) {
+            const std::string why = e != cudaSuccess ? cudaGetErrorString(e) : "no CUDA device";
+            cudaGetLastError();
+            return create_fail(PBA_ECUDA, "no usable CUDA device (" + why + "); the library has no CPU path");
+        }
     }
     pba_problem* p = new pba_problem();
     p->cfg = *cfg;
@@ -556,7 +577,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
         for (int k = 0; k < p->N; ++k) {
             if (cfg->frame_sensor[k] < 0 || cfg->frame_sensor[k] >= cfg->n_sensors) {
                 delete p;
-                return PBA_EINVAL;
+                return create_fail(PBA_EINVAL, "frame_sensor[" + std::to_string(k) + "] out of range");
             }
             p->frame_sensor[k] = cfg->frame_sensor[k];
         }
@@ -564,8 +585,10 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->cfg.frame_sensor = nullptr;
     cudaGetDevice(&p->device);
     auto bail = [&](int code) {
+        const cudaError_t e = cudaGetLastError();
         pba_destroy(p);
-        return code;
+        return create_fail(code, std::string(code == PBA_ENOMEM ? "device allocation failed" : "CUDA call failed") +
+                                     (e != cudaSuccess ? std::string(" (") + cudaGetErrorString(e) + ")" : ""));
     };
     if (cuda_stream) {
         p->stream = (cudaStream_t)cuda_stream;

@@ -31,9 +31,26 @@ def test_binding_declares_argument_types_without_touching_the_gpu():
     lib = _lib.load()
     for name in _lib.EXPORTS:
         assert getattr(lib, name).argtypes is not None
-    # no-GPU-safe calls: argument validation happens before any CUDA call
-    assert lib.pba_last_error(None) == b"null problem"
+    # no-GPU-safe calls: argument validation happens before any CUDA call, and a
+    # failed create leaves its reason for pba_last_error(NULL) on this thread
     assert lib.pba_create(None, None, None) == _lib.PBA_EINVAL
+    assert lib.pba_last_error(None).startswith(b"pba_create: null configuration")
+
+
+def test_without_a_gpu_creation_fails_loudly():
+    """The library has no CPU path: on a machine without a CUDA device,
+    creating a problem raises with the CUDA runtime's reason."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import synth
+    w = synth.make_rgbd_room(n_frames=2, width=32, height=24, f=24.0)
+    with pytest.raises(pba.PbaError) as err:
+        pba.problem_from_workload(w)
+    assert err.value.code == pba._lib.PBA_ECUDA
+    assert "no usable CUDA device" in str(err.value) and "no CPU path" in str(err.value)
 
 
 def test_struct_layouts_match_the_header():
