@@ -22,6 +22,7 @@ host cores (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import math
 import os
@@ -79,7 +80,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["street", "room"], default="street")
@@ -120,6 +121,29 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            atexit.register(self._end)  # never outlive the bench, whatever ends it
+
+    def _end(self):
+        if self.proc and self.proc.poll() is None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def wait_first(self, timeout_s: float = 10.0) -> bool:
+        """Block until nvidia-smi has written its first row (it takes a moment to
+        start), at most timeout_s; True when a row is there."""
+        if not self.proc:
+            return False
+        deadline = time.time() + timeout_s
+        while time.time() < deadline:
+            if os.path.getsize(self.path) > 0:
+                return True
+            if self.proc.poll() is not None:
+                return False
+            time.sleep(0.05)
+        return False
 
     def mark(self, t0: float, t1: float):
         """The timed region, as time.time() values."""
@@ -128,11 +152,7 @@ class ClockSampler:
     def stop(self, slack: float = 0.5):
         if not self.proc:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+        self._end()
         with open(self.path) as fh:
             rows = parse_clock_lines(fh)
         os.unlink(self.path)
@@ -206,6 +226,9 @@ def run_ours(args, rank, world, device):
     import torch
     import paper_2303_16878_gb300 as pba
 
+    # clock sampling starts before the set-up, so that nvidia-smi is emitting
+    # rows well before the timed region
+    clocks = ClockSampler(device.index if device.index is not None else 0)
     w = make_workload(args.workload)
     # a dedicated stream: the library enqueues on it and the events below are recorded on it
     stream = torch.cuda.Stream(device)
@@ -233,7 +256,7 @@ def run_ours(args, rank, world, device):
         return e0.elapsed_time(e1), p.get_stats()
 
     variants = prob.autotune(2)
-    clocks = ClockSampler(device.index if device.index is not None else 0)
+    clocks.wait_first()
     start(prob)
     for _ in range(args.warmup):
         one_step(prob)
@@ -401,7 +424,7 @@ def oracle_sample(w, seconds, seed=0):
 
 def run_reference(args):
     w = make_workload(args.workload)
-    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = max(0.5, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     vals, secs = [], []
     for k in range(args.warmup + args.steps):
         r = oracle_sample(w, per_step, seed=k)
