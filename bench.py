@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of one Levenberg-Marquardt iteration of photometric bundle
-adjustment (linearise every pair, reduce, assemble, damped FP64 Cholesky
-solve, box-plus update, cost re-evaluation, accept/reject) on one GB300.
+adjustment (damped solve: FP32 Cholesky with FP64 refinement in one
+thread-block-cluster launch; box-plus update; linearisation of every pair at
+the candidate; reduce, assemble, accept/reject) on one GB300.
 
 Default workload: LiDAR spherical-projection BA, 50 frames of 64 x 1024
 (vertical FOV -16.6..+16.6 deg) along a synthetic street, every pair with more
 than 30% overlap, FP16 texels / FP32 residuals / FP64 solve.
 
-Metric: residuals per second (valid pixel-point residuals linearised per
-iteration / device time of the iteration) and ms per iteration.  Every timed
-step restarts from the same initial poses, so all steps do identical work;
-L2 is flushed (256 MiB write) before each step.
+Metric: residuals per second (valid pixel-point residuals linearised over
+the timed iterations / their device time) and ms per iteration.  The timed
+steps are consecutive iterations from the initial poses, after one untimed
+linearisation and the warm-up iterations (the valid-residual count grows a
+little as the poses converge); L2 is flushed (256 MiB write) before each step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
