@@ -295,7 +295,8 @@ def run_ours(args, rank, world, device):
             phases.setdefault(k, []).append(v)
     phase_ms = {k: float(np.mean(v)) for k, v in phases.items()}
 
-    out = dict(value=value, ms_per_step=ms_per_step, n_valid=int(nvalid[-1]), launches=launches, clocks=clk,
+    out = dict(value=value, ms_per_step=ms_per_step, n_valid=int(nvalid[-1]), n_valid_mean=float(np.mean(nvalid)),
+               launches=launches, clocks=clk,
                phase_ms=phase_ms, wall_s=wall, n_points=int(n_points_total), n_pairs=int(len(w.pairs)),
                stats=stats, variants=variants)
 
@@ -445,6 +446,56 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- the JSON line
+
+def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_gbs: float) -> dict:
+    """The GPU arm's JSON line from the measurements in `out` (pure: no device
+    access).  Roofline of the dominant kernel: algorithmic FP32 FLOPs of one
+    full linearisation (per valid residual and per processed point, mean
+    valid count of the timed iterations) over its CUDA-event duration, against
+    the nominal FP32 ALU peak at the sampled maximum SM clock."""
+    ph = out["phase_ms"]
+    lin_ms = ph["linearize"]
+    n_valid = out.get("n_valid_mean", out["n_valid"])
+    flops = n_valid * FLOP_PER_RESIDUAL_FULL + out["n_points"] * FLOP_PER_POINT_SPHERICAL
+    sm_max = (out["clocks"] or {}).get("sm_max_mhz") or 2070.0
+    peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (lin_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": n_frames, "pairs": out["n_pairs"],
+                   "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)",
+                   "parallelism": f"replicas x{world}", "autotuned_variants": list(out["variants"])},
+        # each residual is a 5-vector (g, d, n_x, n_y, n_z)
+        "scalar_residuals_per_s": 5.0 * out["value"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": LINEARIZE_DRAM_BYTES, "kernel": "k_linearize<f16, full>",
+                     "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak_gbs,
+                             "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak_gbs,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                     "ncu_unit_fracs": LINEARIZE_NCU_UNITS,
+                     "binding": "SM instruction issue, then the L1 data pipe of the gathers"},
+        "phase_ms": ph,
+        "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
+        "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
+        "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
+        "gpu_launches": out["launches"] * args.steps,
+        "clocks": out["clocks"],
+    }
+    for k in ("build_pairs", "normals", "adjoint", "e2e"):
+        if k in out:
+            line[k] = out[k]
+    if "plain_ms_per_step" in out:
+        line["plain_ms_per_step"] = out["plain_ms_per_step"]
+        line["speedup_vs_plain"] = out["plain_ms_per_step"] / out["ms_per_step"]
+    return line
+
+
 # ----------------------------------------------------------------------------- main
 
 def main():
@@ -465,48 +516,8 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=device)
     out, w = run_ours(args, rank, world, device)
     if rank == 0:
-        ph = out["phase_ms"]
-        lin_ms = ph["linearize"]
-        n_valid = out["n_valid"]
-        flops = n_valid * FLOP_PER_RESIDUAL_FULL + out["n_points"] * FLOP_PER_POINT_SPHERICAL
-        import torch
-        props = torch.cuda.get_device_properties(device)
-        sm_max = (out["clocks"] or {}).get("sm_max_mhz") or 2070.0
-        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        achieved = flops / (lin_ms / 1e3) / 1e12
-        hbm_peak = measured_hbm_gbs()
-        line = {
-            "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "frames": w.n_frames, "pairs": out["n_pairs"],
-                       "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
-                       "l2": "flushed before every timed step (256 MiB write)",
-                       "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)", "parallelism": f"replicas x{world}",
-                       "autotuned_variants": list(out["variants"])},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": LINEARIZE_DRAM_BYTES, "kernel": "k_linearize<f16, full>",
-                         "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
-                         "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak,
-                                 "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak,
-                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
-                         "ncu_unit_fracs": LINEARIZE_NCU_UNITS,
-                         "binding": "SM instruction issue, then the L1 data pipe of the gathers"},
-            "phase_ms": ph,
-            "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
-            "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
-            "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
-            "gpu_launches": out["launches"] * args.steps,
-            "clocks": out["clocks"],
-        }
-        line["build_pairs"] = out["build_pairs"]
-        line["normals"] = out["normals"]
-        line["adjoint"] = out["adjoint"]
-        if "plain_ms_per_step" in out:
-            line["plain_ms_per_step"] = out["plain_ms_per_step"]
-            line["speedup_vs_plain"] = out["plain_ms_per_step"] / out["ms_per_step"]
-        if "e2e" in out:
-            line["e2e"] = out["e2e"]
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        line = make_line(args, world, out, w.n_frames, sms, measured_hbm_gbs())
         if not args.no_cpu:
             cb = oracle_sample(w, args.cpu_seconds)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

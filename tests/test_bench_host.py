@@ -1,4 +1,5 @@
-"""Host-side logic of bench.py that needs no GPU: the clock-sample summary."""
+"""Host-side logic of bench.py that needs no GPU: the clock-sample summary and
+the JSON line built from a measurement."""
 import os
 import sys
 
@@ -28,3 +29,32 @@ def test_clock_summary_widens_a_short_region():
     s = bench.summarise_clocks(rows, (rows[2]["ts"] - 0.01, rows[2]["ts"] + 0.01), slack=0.5)
     assert s["samples"] == 3 and s["window"].startswith("timed region +-")
     assert bench.summarise_clocks([], (0.0, 1.0)) is None
+
+
+def test_json_line_carries_the_contract_keys_and_its_arithmetic():
+    """The GPU arm's line from a fake measurement: contract keys, the roofline
+    arithmetic (algorithmic FLOPs over the kernel's event time against the
+    nominal ALU peak) and JSON serialisability."""
+    import argparse
+    import json
+    import bench
+    args = argparse.Namespace(steps=100, warmup=3)
+    out = dict(value=1.7e10, ms_per_step=1.3, n_valid=22_000_000, n_valid_mean=21_500_000.0, n_points=68_000_000,
+               n_pairs=1170, launches=10, variants=(1, 2),
+               clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 6, "window": "timed region"},
+               phase_ms={"solve": 0.17, "update": 0.02, "linearize": 1.08, "reduce_assemble": 0.05, "accept": 0.01},
+               solve_update_f64_ms=0.78, plain_ms_per_step=29.0,
+               e2e={"value": 6.8e9, "unit": bench.UNIT, "h2d_bytes_per_step": 65540800, "d2h_bytes_per_step": 4848})
+    line = bench.make_line(args, 1, out, 50, 152, 6693.8)
+    json.dumps(line)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "e2e", "gpu_launches"):
+        assert k in line, k
+    assert line["gpu_launches"] == 1000 and line["scalar_residuals_per_s"] == 5 * 1.7e10
+    r = line["roofline"]
+    flops = 21_500_000.0 * bench.FLOP_PER_RESIDUAL_FULL + 68_000_000 * bench.FLOP_PER_POINT_SPHERICAL
+    assert abs(r["achieved"] - flops / 1.08e-3 / 1e12) < 1e-9 * r["achieved"]
+    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12 and 0 < r["frac"] < 1
+    assert abs(r["hbm"]["frac"] - bench.LINEARIZE_DRAM_BYTES / 1.08e-3 / 1e9 / 6693.8) < 1e-12
+    assert abs(line["speedup_vs_plain"] - 29.0 / 1.3) < 1e-12
