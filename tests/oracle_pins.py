@@ -46,6 +46,7 @@ PIN_TOL = {
     "offset_jacobian_fd": 1e-6,
     "offset_gradient_fd": 1e-4,  # central differences of F at h = 2e-8 (roundoff eps F / h)
     "residual_brute_force": 1e-9,
+    "build_pairs": 0.5,
 }
 
 
@@ -900,6 +901,53 @@ def pin_residual_brute_force(O, lib, room, street, stride=3):
     return worst
 
 
+# ------------------------------------------------------- graph construction
+
+def pin_build_pairs(O, lib, w):
+    """Graph construction (Sec. IV-B) against an independent evaluation: the
+    candidate set from scipy's rotation magnitude of R_i^T R_j and numpy's
+    translation distance (thresholds at the medians, so that each criterion
+    removes pairs), every candidate's ratio against the valid fraction of
+    `_bf_residuals` over all points of i (up to the oracle's margin-flagged
+    points), and the kept set (ratio above the median ratio, or sequential).
+    Returns 0 when all agree, else 1."""
+    from scipy.spatial.transform import Rotation
+    poses = np.asarray(w.poses_init, dtype=np.float64).reshape(-1, 3, 4)
+    n = poses.shape[0]
+    ang, dist = {}, {}
+    for i in range(n):
+        for j in range(i + 1, n):
+            if w.frame_sensor[i] == w.frame_sensor[j]:
+                ang[(i, j)] = Rotation.from_matrix(poses[i][:, :3].T @ poses[j][:, :3]).magnitude()
+                dist[(i, j)] = float(np.linalg.norm(poses[i][:, 3] - poses[j][:, 3]))
+    max_angle, max_dist = float(np.median(list(ang.values()))), float(np.median(list(dist.values())))
+    expect = {ij for ij in ang if (ang[ij] < max_angle and dist[ij] < max_dist) or ij[1] == ij[0] + 1}
+    assert any(ang[ij] >= max_angle and dist[ij] < max_dist for ij in ang)
+    assert any(dist[ij] >= max_dist and ang[ij] < max_angle for ij in ang)
+    # ratios of every candidate by brute force
+    bf = {}
+    for (i, j) in expect:
+        s = w.sensors[w.frame_sensor[i]]
+        _, pix = O.frame_points(s, w.params, w.channels[i], lib=lib)
+        ok = _bf_residuals(s, w.params, w.channels[i], w.channels[j], poses[i], poses[j],
+                           np.asarray(pix, dtype=np.int64))[0]
+        bf[(i, j)] = (float(ok.mean()) if len(ok) else 0.0, len(ok))
+    min_ratio = float(np.median([v[0] for v in bf.values()]))
+    r = O.build_pairs(w.sensors, w.frame_sensor, w.channels, poses, w.params, max_angle, max_dist, min_ratio,
+                      sequential=True, lib=lib)
+    if set(r["candidates"]) != expect:
+        return 1.0
+    kept = {tuple(p) for p in r["pairs"].tolist()}
+    for ij, c in r["candidates"].items():
+        ratio, npts = bf[ij]
+        slack = c["flagged"] / max(npts, 1) + 1e-12
+        if c["n_points"] != npts or abs(c["ratio"] - ratio) > slack:
+            return 1.0
+        if abs(ratio - min_ratio) > slack and (ij in kept) != (ratio > min_ratio or ij[1] == ij[0] + 1):
+            return 1.0
+    return 0.0
+
+
 def all_pins(O, lib, room, street):
     """Every pin's error on library `lib` (room: 3-frame RGB-D, street: 3-frame LiDAR)."""
     return {
@@ -928,3 +976,7 @@ def all_pins(O, lib, room, street):
         "offset_gradient_fd": pin_offset_gradient_fd(O, lib, room),
         "residual_brute_force": pin_residual_brute_force(O, lib, room, street),
     }
+
+
+def graph_pins(O, lib, room8):
+    return {"build_pairs": pin_build_pairs(O, lib, room8)}

@@ -198,3 +198,31 @@ def test_planted_variable_mistake_is_caught(name, oracle_lib, room3, fusion):
             failed.append(pin)
             break
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+GRAPH_MUTATIONS = {
+    "angle_uses_R_i_R_j": ("np.trace(Ri.T @ Rj)", "np.trace(Ri @ Rj)"),
+    "distance_from_a_rotation_column": ("np.linalg.norm(poses[i][:, 3] - poses[j][:, 3])",
+                                        "np.linalg.norm(poses[i][:, 2] - poses[j][:, 2])"),
+    "criteria_joined_by_or": ("(ang < max_angle and dist < max_dist) or is_seq",
+                              "(ang < max_angle or dist < max_dist) or is_seq"),
+    "ratio_over_pixels_not_points": ('ratio = r["count"] / r["n_points"] if r["n_points"] else 0.0',
+                                     'ratio = r["count"] / channels[i][..., 0].size if r["n_points"] else 0.0'),
+    "sequential_edges_ignored": ("is_seq = sequential and j == i + 1", "is_seq = False"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPH_MUTATIONS))
+def test_planted_graph_mistake_is_caught(name, oracle_lib, room8):
+    import types
+    before, after = GRAPH_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mod = types.ModuleType("oracle_mutated")
+    mod.__file__ = PY_SRC
+    exec(compile(src.replace(before, after), PY_SRC, "exec"), mod.__dict__)
+    try:
+        err = P.pin_build_pairs(mod, oracle_lib.load(), room8)
+    except Exception:
+        return
+    assert not err < P.PIN_TOL["build_pairs"], f"no pin caught the planted mistake {name}"

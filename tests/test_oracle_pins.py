@@ -224,3 +224,10 @@ def test_residuals_match_brute_force(oracle_lib, room3, street3):
     occlusion, target normal, both Huber branches) against a vectorised
     evaluation from the definitions."""
     assert P.pin_residual_brute_force(oracle_lib, oracle_lib.load(), room3, street3) < P.PIN_TOL["residual_brute_force"]
+
+
+def test_build_pairs_matches_an_independent_graph(oracle_lib, room8):
+    """Candidates by scipy's rotation magnitude and the translation distance,
+    ratios by the brute-force residual evaluation, kept pairs by the ratio
+    threshold or sequence (Sec. IV-B)."""
+    assert P.pin_build_pairs(oracle_lib, oracle_lib.load(), room8) < P.PIN_TOL["build_pairs"]
