@@ -138,7 +138,8 @@ void pba_destroy(pba_problem* p);
  * (or, for NULL, the thread's next failing pba_create). */
 const char* pba_last_error(const pba_problem* p);
 
-/* Order all further device work on cuda_stream (NULL: the problem's own stream). */
+/* Order all further device work on cuda_stream (NULL: the problem's own stream).
+ * Errors: PBA_EINVAL (p NULL), PBA_ECUDA. */
 int pba_set_stream(pba_problem* p, void* cuda_stream);
 
 /* Upload the five-channel cue images (Sec. IV-A) of frames first..first+count-1
@@ -151,7 +152,8 @@ int pba_upload_frames(pba_problem* p, int first, int count, const float* channel
 
 /* Replace the extrinsic offset X_o (row-major 3x4, host memory) of one
  * sensor (Supp., p_u = R_o pi^-1(u, d) + t_o): the pixel-points of that
- * sensor's uploaded frames are rebuilt; the next iteration relinearises. */
+ * sensor's uploaded frames are rebuilt; the next iteration relinearises.
+ * Errors: PBA_EINVAL (bad sensor index, extrinsic NULL), PBA_ECUDA. */
 int pba_set_extrinsic(pba_problem* p, int sensor, const double* extrinsic);
 
 /* Normal estimation (Sec. IV-A) for the uploaded frames first..first+count-1,
@@ -179,18 +181,25 @@ int pba_estimate_normals(pba_problem* p, int first, int count, float scale, int 
  * Errors: PBA_EINVAL, PBA_ENOTREADY (a frame not uploaded), PBA_ECUDA. */
 int pba_get_channels(pba_problem* p, int first, int count, float* channels, int is_device);
 
-/* Number of valid pixel-points of a frame (after its upload). */
+/* Number of valid pixel-points of a frame (Sec. IV-A: its valid pixels, after
+ * its upload).  Errors: PBA_EINVAL (bad frame, n_points NULL), PBA_ENOTREADY
+ * (frame not uploaded). */
 int pba_frame_points(pba_problem* p, int frame, int32_t* n_points);
 
-/* Set all N poses (N x 12 doubles, host or device). */
+/* Set all N poses X_k (Sec. III; N x 12 doubles in the pose convention above,
+ * host or device memory).  The next iteration linearises at them first.
+ * Errors: PBA_EINVAL (poses NULL), PBA_ECUDA. */
 int pba_set_poses(pba_problem* p, const double* poses, int is_device);
 
-/* Read all N poses into host memory (N x 12 doubles); synchronises. */
+/* Read all N poses into host memory (N x 12 doubles); synchronises.
+ * Errors: PBA_EINVAL (poses NULL), PBA_ECUDA. */
 int pba_get_poses(pba_problem* p, double* poses);
 
 /* Set the directed pairs (source i, target j), m x 2 int32 in host memory,
  * Sec. IV-B.  Both frames must use the same sensor; i == j is allowed.
- * Requires every frame named to have been uploaded. */
+ * Requires every frame named to have been uploaded.  Errors: PBA_EINVAL
+ * (m < 0, pairs NULL with m > 0, a frame out of range, frames of different
+ * sensors), PBA_ENOTREADY (a frame not uploaded), PBA_ENOMEM, PBA_ECUDA. */
 int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m);
 
 /* Graph construction (Sec. IV-B): directed candidate pairs (i, j), i < j,
@@ -211,7 +220,9 @@ int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double mi
 
 /* Linearise all pairs at the current poses: builds H (6N x 6N, gauge not
  * fixed) and b (6N) on the device and returns the total cost F (Eq. total-error-multicue) and
- * the number of valid residuals; synchronises.  Either output may be NULL. */
+ * the number of valid residuals; synchronises.  Either output may be NULL.
+ * Errors: PBA_EINVAL (p NULL), PBA_ENOTREADY (poses or pairs not set),
+ * PBA_ECUDA. */
 int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
 
 /* Adjoint of the total cost F (Eq. total-error-multicue) at the current
@@ -233,18 +244,25 @@ int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
 int pba_cost_gradient(pba_problem* p, double* cost, int64_t* n_valid, double* d_poses, double* d_extrinsic,
                       float* d_channels);
 
-/* Copy the last linearisation's H (6N x 6N row-major) and b (6N) to host
- * memory; either may be NULL.  Frame k owns rows and columns 6k..6k+5. */
+/* Copy the last linearisation's Gauss-Newton system (Sec. IV-C: H = sum of
+ * w J^T Omega J and b = sum of w J^T Omega e over every residual of Eq.
+ * total-error-multicue, J = [J_i J_j] from the Supp. Jacobians) to host
+ * memory: H (6N x 6N row-major) and b (6N); either may be NULL.  Frame k owns
+ * rows and columns 6k..6k+5.  Errors: PBA_EINVAL, PBA_ENOTREADY (no
+ * linearisation yet), PBA_ECUDA. */
 int pba_get_system(pba_problem* p, double* H, double* b);
 
 /* Copy the last linearisation's per-pair results to host memory: pair_H
  * (m x 12 x 12: rows/cols 0-5 frame i, 6-11 frame j), pair_b (m x 12),
- * pair_cost (m), pair_count (m).  Any may be NULL. */
+ * pair_cost (m), pair_count (m).  Any may be NULL.  Errors: PBA_EINVAL,
+ * PBA_ENOTREADY (no linearisation yet), PBA_ECUDA. */
 int pba_get_pair_system(pba_problem* p, double* pair_H, double* pair_b, double* pair_cost,
                         int64_t* pair_count);
 
-/* Enable (1) or disable (0) export of the valid-residual mask by later
- * linearisations (batched path only). */
+/* Enable (1) or disable (0) export of the valid-residual mask (which
+ * pixel-points pass the validity and occlusion rules of Sec. IV-C) by later
+ * linearisations.  Errors: PBA_EINVAL (p NULL, or enabling on the plain
+ * path). */
 int pba_set_mask_export(pba_problem* p, int enable);
 
 /* Copy the valid-residual mask of one pair from the last linearisation with
@@ -253,34 +271,41 @@ int pba_set_mask_export(pba_problem* p, int enable);
  * >= ceil(P_i / 32).  Errors: PBA_EINVAL, PBA_ENOTREADY (no mask exported). */
 int pba_get_mask(pba_problem* p, int pair, uint32_t* bits, int n_words);
 
-/* One damped step from the last linearisation with the given lambda >= 0:
- * solve (H_ff + lambda I) dx_f = -b_f with frame 0 held fixed (gauge),
- * evaluate F at X [+] dx, keep the candidate when F decreased.  Fills stats
- * (may be NULL); synchronises.  Returns PBA_OK even when the step is
- * rejected; stats->status reports PBA_ENOTPD. */
+/* One damped (Levenberg-Marquardt, Sec. IV-C) step from the last
+ * linearisation with the given lambda >= 0: solve (H_ff + lambda I) dx_f =
+ * -b_f with frame 0 held fixed (gauge), evaluate F at X [+] dx, keep the
+ * candidate when F decreased.  Fills stats (may be NULL); synchronises.
+ * Returns PBA_OK even when the step is rejected; stats->status reports
+ * PBA_ENOTPD.  Errors: PBA_EINVAL (lambda < 0 or NaN), PBA_ENOTREADY (poses
+ * or pairs not set, no linearisation), PBA_ECUDA. */
 int pba_solve_step(pba_problem* p, double lambda, pba_iter_stats* stats);
 
-/* Damping used by pba_iterate: lambda >= 0 sets it, lambda < 0 resets it to
- * automatic (1e-4 times the largest diagonal entry of H_ff on the next
- * iteration).  The schedule then divides by 10 on acceptance and multiplies
- * by 10 on rejection, on the device. */
+/* Damping used by pba_iterate (Sec. IV-C, Levenberg-Marquardt): lambda >= 0
+ * sets it, lambda < 0 resets it to automatic (1e-4 times the largest diagonal
+ * entry of H_ff on the next iteration).  The schedule then divides by 10 on
+ * acceptance and multiplies by 10 on rejection, on the device.
+ * Errors: PBA_EINVAL (p NULL), PBA_ECUDA. */
 int pba_set_lambda(pba_problem* p, double lambda);
 
-/* One full Levenberg-Marquardt iteration with the device-side lambda
+/* One full Levenberg-Marquardt iteration (Sec. IV-C) with the device-side lambda
  * schedule: damp and solve the current system, form the candidate poses,
  * linearise fully at the candidate, and accept (the candidate's poses and
  * system become current) or reject (nothing changes).  The first iteration
  * after new poses, frames or pairs first linearises at the current poses.
  * stats->cost is F at the start, stats->new_cost F at the candidate,
  * stats->n_valid the residuals of the candidate's linearisation.  Fills stats
- * (may be NULL) and synchronises. */
+ * (may be NULL) and synchronises.  A rejected or not positive definite step
+ * is an outcome (stats), not an error.  Errors: PBA_EINVAL (p NULL),
+ * PBA_ENOTREADY (poses or pairs not set), PBA_ECUDA. */
 int pba_iterate(pba_problem* p, pba_iter_stats* stats);
 
 /* Enqueue n iterations as replays of one captured CUDA graph without
- * synchronising; pba_get_stats() then reads the last iteration's outcome. */
+ * synchronising; pba_get_stats() then reads the last iteration's outcome.
+ * Errors: as pba_iterate, and PBA_EINVAL for n < 0. */
 int pba_iterate_async(pba_problem* p, int n);
 
-/* Synchronise and read the outcome of the last iteration. */
+/* Synchronise and read the outcome of the last iteration.  Errors:
+ * PBA_EINVAL (p NULL), PBA_ECUDA. */
 int pba_get_stats(pba_problem* p, pba_iter_stats* stats);
 
 /* The current offset X_o of one sensor (row-major 3x4, host memory).
@@ -359,7 +384,8 @@ int pba_build_pyramid(pba_problem* p, int n_levels);
 
 /* The problem of one level (borrowed: owned by p, valid until the pyramid is
  * rebuilt or p destroyed; level 0 returns p).  Every entry point applies to
- * it, e.g. to linearise at a coarse level. */
+ * it, e.g. to linearise at a coarse level.  Errors: PBA_EINVAL (no such
+ * level), PBA_ENOTREADY (stale pyramid). */
 int pba_pyramid_level(pba_problem* p, int level, pba_problem** level_out);
 
 /* Outcome of one level of pba_optimize. */
@@ -383,7 +409,9 @@ typedef struct {
  * PBA_ENOTREADY (stale pyramid, poses or pairs not set), PBA_ECUDA. */
 int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double rel_tol, pba_level_stats* stats);
 
-/* Number of kernel launches one pba_iterate performs (for accounting). */
+/* Number of kernel launches one pba_iterate performs (for accounting; captures
+ * the iteration graph when there is none).  Errors: PBA_EINVAL,
+ * PBA_ENOTREADY (poses or pairs not set), PBA_ECUDA. */
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
 /* Occupancy variants of the batched linearisation kernel: register budgets
@@ -397,7 +425,8 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
  * (each launched repeats + 1 times, the first as warm-up); later iterations
  * use the choice.  Reports the choice (0 .. PBA_N_VARIANTS - 1) in the
  * optional outputs.  Needs frames, poses and pairs; synchronises.  A no-op on
- * the plain path. */
+ * the plain path.  Errors: PBA_EINVAL, PBA_ENOTREADY (poses or pairs not
+ * set), PBA_ECUDA. */
 int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost);
 
 /* Set the variants explicitly (e.g. to reproduce a tuned configuration).
@@ -410,7 +439,7 @@ int pba_set_variants(pba_problem* p, int variant_full, int variant_cost);
  * milliseconds: [0] damping + solve, [1] box-plus + candidate transforms,
  * [2] the linearisation kernel at the candidate, [3] per-pair reduction +
  * assembly + cost, [4] accept / reject (and the swap of the system).  Fills
- * stats (may be NULL); synchronises. */
+ * stats (may be NULL); synchronises.  Errors: as pba_iterate. */
 #define PBA_N_PHASES 5
 int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_stats* stats);
 
