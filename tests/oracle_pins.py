@@ -128,6 +128,21 @@ def pin_boxplus(O, lib):
         X4[:3] = X
         ref = (X4 @ E)[:3]
         err = max(err, float(np.abs(O.boxplus(X, dx, lib=lib) - ref).max()))
+    # |dq| >= 1 has no unit quaternion with imaginary part dq: the reading
+    # normalises (1, dq), the quaternion scipy builds from (dq, 1)
+    for _ in range(20):
+        X = np.zeros((3, 4))
+        X[:, :3] = Rotation.from_rotvec(rng.normal(0, 1, 3)).as_matrix()
+        X[:, 3] = rng.normal(0, 2, 3)
+        q = rng.normal(0, 1, 3)
+        q *= rng.uniform(1.0, 3.0) / np.linalg.norm(q)
+        dx = np.concatenate([rng.normal(0, 0.5, 3), q])
+        E = np.eye(4)
+        E[:3, :3] = Rotation.from_quat([q[0], q[1], q[2], 1.0]).as_matrix()
+        E[:3, 3] = dx[:3]
+        X4 = np.eye(4)
+        X4[:3] = X
+        err = max(err, float(np.abs(O.boxplus(X, dx, lib=lib) - (X4 @ E)[:3]).max()))
     # X [+] 0 = X
     err = max(err, float(np.abs(O.boxplus(X, np.zeros(6), lib=lib) - X).max()))
     return err

@@ -43,6 +43,7 @@ MUTATIONS = {
     "stencil_corner_for_edge_texel": ("{1, -1}, {1, 0}, {1, 1}, {1, 2}, {2, 0}, {2, 1}};",
                                       "{1, -1}, {1, 0}, {1, 1}, {1, 2}, {2, 0}, {2, 2}};"),
     "pinhole_window_one_column_short": ("u >= 1.0 && u < (double)(s->width - 2)", "u >= 1.0 && u < (double)(s->width - 3)"),
+    "boxplus_large_step_not_normalised": ("qw = 1.0 / n; qx /= n; qy /= n; qz /= n;", "qw = 0.0;"),
     "range_cue_horizontal_only": ("zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1] + pb[2] * pb[2]);",
                                   "zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1]);"),
 }
