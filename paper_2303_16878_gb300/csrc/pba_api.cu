@@ -1182,7 +1182,6 @@ int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double mi
         std::vector<int32_t> keep = p->pairs;
         int st = pba_set_pairs(p, cand.data(), mc);
         if (st) return st;
-        int nl = 0;
         CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
         if (p->cfg.path == PBA_PATH_BATCHED) {
             CUDA_TRY(p, cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), p->stream));
