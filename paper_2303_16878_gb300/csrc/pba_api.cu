@@ -1201,7 +1201,6 @@ int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double mi
             }
             CUDA_TRY(p, launch_plain_expand(p->d_plain_acc, p->M, false, p->d_blocks_cand, p->stream));
         }
-        (void)nl;
         std::vector<double> blk((size_t)kBlockStride * mc);
         CUDA_TRY(p, cudaMemcpyAsync(blk.data(), p->d_blocks_cand, sizeof(double) * blk.size(),
                                     cudaMemcpyDeviceToHost, p->stream));
