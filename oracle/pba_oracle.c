@@ -53,6 +53,9 @@
  *   R9  integer pixel coordinates are pixel centres; column = u, row = v.
  *   R10 X [+] Dx = [R R(Dq), R Dt + t], R(Dq) from the unit quaternion
  *       (sqrt(1 - |Dq|^2), Dq) (normalised (1, Dq) when |Dq| >= 1).
+ *   R24 d pbar / d Dx_j = R_o^T [-I | 2 [q]x]: the Supp. derivation of the
+ *       target's perturbation leaves out the rotation R(-Dq) acting on Dt,
+ *       which changes nothing at first order, the order a Jacobian keeps.
  *
  * Decision margins: the oracle flags a point when a validity decision lies
  * within `margin_px` pixels (projections against integers) or `margin_rel`
@@ -435,7 +438,7 @@ int o_point_residual(const o_sensor* s, const o_params* prm, const float* tgt,
             for (int k = 0; k < 3; ++k) acc += M[3 * r + k] * (-2.0 * Spu[3 * k + c]);
             dPi[6 * r + 3 + c] = acc;
         }
-    /* d pbar / d Dx_j = R_o^T [-I | 2 [q]x]   (R3) */
+    /* d pbar / d Dx_j = R_o^T [-I | 2 [q]x]   (R3, R24) */
     double Sq[9];
     skew(q, Sq);
     for (int r = 0; r < 3; ++r)
