@@ -558,6 +558,10 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
         if ((long long)S.width * S.height > (1LL << 30))
             return create_fail(PBA_EINVAL, "sensor " + std::to_string(s) + ": more than 2^30 pixels");
     }
+    if (cfg->frame_sensor)
+        for (int k = 0; k < cfg->n_frames; ++k)
+            if (cfg->frame_sensor[k] < 0 || cfg->frame_sensor[k] >= cfg->n_sensors)
+                return create_fail(PBA_EINVAL, "frame_sensor[" + std::to_string(k) + "] out of range");
     {
         int n_dev = 0;
         const cudaError_t e = cudaGetDeviceCount(&n_dev);
@@ -573,15 +577,8 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     p->sensors.assign(cfg->sensors, cfg->sensors + cfg->n_sensors);
     p->cfg.sensors = nullptr;
     p->frame_sensor.assign(p->N, 0);
-    if (cfg->frame_sensor) {
-        for (int k = 0; k < p->N; ++k) {
-            if (cfg->frame_sensor[k] < 0 || cfg->frame_sensor[k] >= cfg->n_sensors) {
-                delete p;
-                return create_fail(PBA_EINVAL, "frame_sensor[" + std::to_string(k) + "] out of range");
-            }
-            p->frame_sensor[k] = cfg->frame_sensor[k];
-        }
-    }
+    if (cfg->frame_sensor)
+        for (int k = 0; k < p->N; ++k) p->frame_sensor[k] = cfg->frame_sensor[k];  // checked above
     p->cfg.frame_sensor = nullptr;
     cudaGetDevice(&p->device);
     auto bail = [&](int code) {

@@ -59,3 +59,64 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.PbaSensor) == 16 + 8 * 16
     assert ctypes.sizeof(_lib.PbaConfig) == 8 + 8 + 8 + 9 * 8 + 16
     assert ctypes.sizeof(_lib.PbaIterStats) == 4 * 8 + 8 + 8
+
+
+def _config(_lib, sensors, n_frames=2, frame_sensor=None, **over):
+    cfg = _lib.PbaConfig()
+    cfg.n_frames, cfg.n_sensors = n_frames, len(sensors)
+    arr = (_lib.PbaSensor * len(sensors))(*sensors)
+    cfg.sensors = ctypes.cast(arr, ctypes.POINTER(_lib.PbaSensor))
+    keep = [arr]
+    if frame_sensor is not None:
+        fs = (ctypes.c_int32 * len(frame_sensor))(*frame_sensor)
+        cfg.frame_sensor = ctypes.cast(fs, ctypes.POINTER(ctypes.c_int32))
+        keep.append(fs)
+    cfg.w_int = cfg.w_depth = cfg.w_normal = 1.0
+    cfg.huber_delta, cfg.occ_abs, cfg.occ_rel, cfg.z_min = 0.1, 0.1, 0.05, 0.05
+    cfg.range_min, cfg.range_max = 0.0, 1e30
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg, keep
+
+
+def _sensor(_lib, **over):
+    s = _lib.PbaSensor()
+    s.model, s.width, s.height = _lib.PBA_PINHOLE, 64, 48
+    s.fx = s.fy = 48.0
+    s.cx, s.cy = 32.0, 24.0
+    for e, v in enumerate((1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0)):
+        s.extrinsic[e] = v
+    for k, v in over.items():
+        setattr(s, k, v)
+    return s
+
+
+def test_create_rejects_bad_configurations_before_touching_the_gpu():
+    """Every configuration check of pba_create runs before any CUDA call:
+    each bad field gives PBA_EINVAL and names itself in pba_last_error(NULL)."""
+    from paper_2303_16878_gb300 import _lib
+    lib = _lib.load()
+    good = _sensor(_lib)
+    cases = [
+        (dict(n_frames=0), [good], None, b"n_frames"),
+        (dict(huber_delta=0.0), [good], None, b"huber_delta"),
+        (dict(huber_delta=float("nan")), [good], None, b"huber_delta"),
+        (dict(grad_mode=2), [good], None, b"grad_mode"),
+        (dict(texel_precision=5), [good], None, b"texel_precision"),
+        (dict(path=7), [good], None, b"path"),
+        (dict(solver=9), [good], None, b"solver"),
+        ({}, [_sensor(_lib, model=3)], None, b"sensor 0"),
+        ({}, [_sensor(_lib, width=3)], None, b"sensor 0"),
+        ({}, [good, _sensor(_lib, fx=0.0)], None, b"sensor 1: zero focal length"),
+        ({}, [_sensor(_lib, width=1 << 16, height=1 << 15)], None, b"2^30 pixels"),
+        ({}, [good], [0, 1], b"frame_sensor[1] out of range"),
+        ({}, [good, good], [-1, 0], b"frame_sensor[0] out of range"),
+    ]
+    for over, sensors, fs, needle in cases:
+        n_frames = over.pop("n_frames", 2)
+        cfg, keep = _config(_lib, sensors, n_frames=n_frames, frame_sensor=fs, **over)
+        h = ctypes.c_void_p()
+        assert lib.pba_create(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.PBA_EINVAL, needle
+        assert not h.value
+        msg = lib.pba_last_error(None)
+        assert msg.startswith(b"pba_create: ") and needle in msg, (needle, msg)
