@@ -1,5 +1,6 @@
-"""The torch renderer and overlap ratio (used to generate the large
-configurations on the GPU) reproduce the numpy ones bit for bit (CPU)."""
+"""The synthetic inputs (CPU): the torch renderer and overlap ratio (used to
+generate the large configurations on the GPU) reproduce the numpy ones bit for
+bit, and the benchmark street and the RGB-D room follow their stated recipes."""
 import numpy as np
 
 
@@ -38,3 +39,53 @@ def test_torch_overlap_ratios_match_numpy():
     ref = [synth.overlap_ratio(w.channels[0], w.channels[j], s, w.poses_gt[0], w.poses_gt[j], stride=7)
            for j in (1, 2, 3)]
     assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_lidar_street_follows_its_recipe():
+    """The benchmark input is what the design notes state: 50 spherical frames
+    of 64 x 1024 over +-16.6 deg (f_x = -W / 2 pi, c_x = W / 2), ranges in
+    [1, 80] m, unit normals, intensity in [0, 1], intensity and normals exact
+    in binary16, 5 % of returns dropped (measured on the lower rows, which see
+    the ground within range), poses 1 m apart, 10 cm / 0.5 deg initial noise,
+    1170 pairs i < j within 40 m."""
+    import math
+    import numpy as np
+    from scipy.spatial.transform import Rotation
+    from conftest import workload
+    w = workload("street")
+    C = np.stack(w.channels)
+    assert C.shape == (50, 64, 1024, 5) and C.dtype == np.float32
+    d = C[..., 1]
+    assert d[d > 0].min() >= 1.0 and d[d > 0].max() <= 80.0
+    assert np.abs(np.linalg.norm(C[..., 2:5], axis=-1)[d > 0] - 1.0).max() < 1e-3
+    assert C[..., 0].min() >= 0.0 and C[..., 0].max() <= 1.0
+    g16 = C[..., [0, 2, 3, 4]]
+    assert np.array_equal(g16, g16.astype(np.float16).astype(np.float32))
+    assert 0.045 < (d[:, 48:, :] <= 0).mean() < 0.055
+    s = w.sensors[0]
+    assert math.isclose(s.fx, -1024 / (2 * math.pi)) and s.cx == 512.0
+    assert math.isclose(math.degrees((0 - s.cy) / s.fy), 16.6) and math.isclose(math.degrees((63 - s.cy) / s.fy), -16.6)
+    t = w.poses_gt[:, :, 3]
+    steps = np.linalg.norm(np.diff(t, axis=0), axis=1)
+    assert np.all(np.abs(steps - 1.0) < 0.01)
+    assert 0.085 < (w.poses_init[:, :, 3] - t).std() < 0.115
+    rv = np.array([Rotation.from_matrix(w.poses_gt[k][:, :3].T @ w.poses_init[k][:, :3]).as_rotvec()
+                   for k in range(w.n_frames)])
+    assert 0.42 < math.degrees(rv.std()) < 0.58
+    assert len(w.pairs) == 1170 and np.all(w.pairs[:, 0] < w.pairs[:, 1])
+    assert max(np.linalg.norm(t[i] - t[j]) for i, j in w.pairs) <= 40.0
+
+
+def test_rgbd_room_follows_its_recipe():
+    """8 pinhole frames of 160 x 120 (f = 120, c = (80, 60)), depth within
+    0.5-5 m, 18 pairs with j - i <= 3."""
+    import numpy as np
+    from conftest import workload
+    w = workload("room")
+    C = np.stack(w.channels)
+    assert C.shape == (8, 120, 160, 5)
+    d = C[..., 1]
+    assert d[d > 0].min() >= 0.5 and d[d > 0].max() <= 5.0
+    s = w.sensors[0]
+    assert (s.fx, s.fy, s.cx, s.cy) == (120.0, 120.0, 80.0, 60.0)
+    assert len(w.pairs) == 18 and np.all((w.pairs[:, 1] - w.pairs[:, 0] >= 1) & (w.pairs[:, 1] - w.pairs[:, 0] <= 3))
