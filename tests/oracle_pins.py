@@ -47,6 +47,7 @@ PIN_TOL = {
     "offset_gradient_fd": 1e-4,  # central differences of F at h = 2e-8 (roundoff eps F / h)
     "residual_brute_force": 1e-9,
     "build_pairs": 0.5,
+    "relative_jacobian": 1e-12,
 }
 
 
@@ -916,6 +917,41 @@ def pin_residual_brute_force(O, lib, room, street, stride=3):
     return worst
 
 
+# ------------------------------------------ J_j from J_i (relative-pose invariance)
+
+def _skew(v):
+    return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
+
+
+def pin_relative_jacobian(O, lib, w, stride=7):
+    """The residual depends on X_i, X_j only through A = X_j^-1 X_i (Eq.
+    uprime), so a perturbation of X_j acts as a perturbation of X_i mapped by
+    the adjoint of A^-1: J_j = J_i T with R = R_j^T R_i, t = R_j^T (t_i - t_j)
+    and T = [[-R^T, 2 R^T [t]x], [0, -R^T]] in the box-plus chart (dq the
+    quaternion's imaginary part, so rotations enter doubled).  Checked on the
+    oracle's separately computed J_i and J_j over three pairs; returns the
+    largest |J_j - J_i T| relative to max |J_j| of the point."""
+    s = w.sensors[0]
+    worst, used = 0.0, 0
+    for i, j in ((0, 1), (1, 2), (2, 0)):
+        Xi, Xj = w.poses_init[i], w.poses_init[j]
+        R = Xj[:, :3].T @ Xi[:, :3]
+        t = Xj[:, :3].T @ (Xi[:, 3] - Xj[:, 3])
+        T = np.zeros((6, 6))
+        T[:3, :3] = -R.T
+        T[:3, 3:] = 2.0 * R.T @ _skew(t)
+        T[3:, 3:] = -R.T
+        pts, _ = O.frame_points(s, w.params, w.channels[i], lib=lib)
+        for k in range(0, len(pts), stride):
+            r = O.point_residual(s, w.params, w.channels[j], Xi, Xj, pts[k], lib=lib)
+            if not r["valid"]:
+                continue
+            used += 1
+            worst = max(worst, float(np.abs(r["Jj"] - r["Ji"] @ T).max() / max(np.abs(r["Jj"]).max(), 1e-30)))
+    assert used > 100
+    return worst
+
+
 # ------------------------------------------------------- graph construction
 
 def pin_build_pairs(O, lib, w):
@@ -990,6 +1026,8 @@ def all_pins(O, lib, room, street):
         "offset_jacobian_fd": pin_offset_jacobian_fd(O, lib, room),
         "offset_gradient_fd": pin_offset_gradient_fd(O, lib, room),
         "residual_brute_force": pin_residual_brute_force(O, lib, room, street),
+        "relative_jacobian": max(pin_relative_jacobian(O, lib, room), pin_relative_jacobian(O, lib, street),
+                                 pin_relative_jacobian(O, lib, _with_offset(room))),
     }
 
 

@@ -74,7 +74,9 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("jacobian_fd_extrinsic", lambda: P.pin_jacobian_fd_extrinsic(oracle_lib, lib, room3)),
                     ("offset_jacobian_fd", lambda: P.pin_offset_jacobian_fd(oracle_lib, lib, room3)),
                     ("offset_gradient_fd", lambda: P.pin_offset_gradient_fd(oracle_lib, lib, room3)),
-                    ("residual_brute_force", lambda: P.pin_residual_brute_force(oracle_lib, lib, room3, street3))]:
+                    ("residual_brute_force", lambda: P.pin_residual_brute_force(oracle_lib, lib, room3, street3)),
+                    ("relative_jacobian", lambda: max(P.pin_relative_jacobian(oracle_lib, lib, room3),
+                                                      P.pin_relative_jacobian(oracle_lib, lib, street3)))]:
         try:
             err = fn()
         except (AssertionError, ValueError, ArithmeticError, Exception):

@@ -231,3 +231,13 @@ def test_build_pairs_matches_an_independent_graph(oracle_lib, room8):
     ratios by the brute-force residual evaluation, kept pairs by the ratio
     threshold or sequence (Sec. IV-B)."""
     assert P.pin_build_pairs(oracle_lib, oracle_lib.load(), room8) < P.PIN_TOL["build_pairs"]
+
+
+@pytest.mark.parametrize("which", ["room3", "street3", "room3_offset"])
+def test_target_jacobian_is_the_source_jacobian_mapped_by_the_relative_pose(oracle_lib, which, request):
+    """J_j = J_i T (the residual depends on the poses only through X_j^-1 X_i),
+    on the oracle's separately computed J_i and J_j."""
+    w = request.getfixturevalue(which.replace("_offset", ""))
+    if which.endswith("_offset"):
+        w = P._with_offset(w)
+    assert P.pin_relative_jacobian(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["relative_jacobian"]
