@@ -391,9 +391,6 @@ int ready(pba_problem* p) {
     return PBA_OK;
 }
 
-// Optionally re-estimates the normals of frames first..first+count-1 (max_radius > 0),
-// then rebuilds their texels and pixel-points and, when a point count changed, the
-// pair plan.  Synchronises.
 // Texels, pixel-points and central differences of frames first .. first+count-1 on stream s.
 int pack_frames(pba_problem* p, int first, int count, cudaStream_t s) {
     CUDA_TRY(p, launch_pack(p->raw, p->d_frames, p->d_sensors, p->d_frame_iota + first, count,
@@ -420,6 +417,9 @@ int finish_repack(pba_problem* p) {
     return PBA_OK;
 }
 
+// Optionally re-estimates the normals of frames first..first+count-1 (max_radius > 0),
+// then rebuilds their texels and pixel-points and, when a point count changed, the
+// pair plan.  Synchronises.
 int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
     if (max_radius > 0) {
         int max_px = 0;
