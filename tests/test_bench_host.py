@@ -58,3 +58,31 @@ def test_json_line_carries_the_contract_keys_and_its_arithmetic():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12 and 0 < r["frac"] < 1
     assert abs(r["hbm"]["frac"] - bench.LINEARIZE_DRAM_BYTES / 1.08e-3 / 1e9 / 6693.8) < 1e-12
     assert abs(line["speedup_vs_plain"] - 29.0 / 1.3) < 1e-12
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """--impl reference: one line with impl, the metric and unit of the GPU arm,
+    a cpu_baseline describing the run and an e2e object with zero copies; the
+    per-step sample budget keeps 100 + 3 steps near 150 s of oracle work."""
+    import argparse
+    import json
+    import bench
+    calls = []
+
+    def fake_sample(w, seconds, seed=0):
+        calls.append(seconds)
+        return dict(value=5.0e5 + seed, unit=bench.UNIT, cores=1, kind="oracle", sample="fake", seconds=seconds,
+                    pairs=3)
+
+    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
+    monkeypatch.setattr(bench, "make_workload", lambda name: object())
+    args = argparse.Namespace(workload="street", steps=100, warmup=3, cpu_seconds=12.0, gpus=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 100 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert len(calls) == 103 and 0.5 <= calls[0] <= 12.0 and 103 * calls[0] <= 160.0
+    assert abs(line["value"] - (5.0e5 + sum(range(3, 103)) / 100)) < 1e-6
