@@ -11,7 +11,9 @@
  *   - Status: every int-returning call returns PBA_OK (0) or a negative
  *     PBA_E* code and never throws; pba_last_error() gives a message.
  *   - Ownership: input buffers are borrowed for the duration of the call
- *     only (the library copies what it keeps); outputs are caller-allocated.
+ *     only (the library copies what it keeps; the one exception is device
+ *     memory given to pba_set_poses, read by a copy ordered on the problem's
+ *     stream); outputs are caller-allocated.
  *     The problem object owns all device memory it allocates.
  *   - Host / device pointers: arguments documented "host or device" take an
  *     `is_device` flag; 1 means a pointer into the current CUDA device's
@@ -188,7 +190,11 @@ int pba_frame_points(pba_problem* p, int frame, int32_t* n_points);
 
 /* Set all N poses X_k (Sec. III; N x 12 doubles in the pose convention above,
  * host or device memory).  The next iteration linearises at them first.
- * Errors: PBA_EINVAL (poses NULL), PBA_ECUDA. */
+ * Host poses are copied before the call returns; device poses are copied by
+ * work ordered on the problem's stream, without waiting, so they must stay
+ * unchanged until that stream has passed this call (automatic when the
+ * caller works on the same stream).  Errors: PBA_EINVAL (poses NULL),
+ * PBA_ECUDA. */
 int pba_set_poses(pba_problem* p, const double* poses, int is_device);
 
 /* Read all N poses into host memory (N x 12 doubles); synchronises.

@@ -244,11 +244,22 @@ class Problem:
         return n.value
 
     def set_poses(self, poses):
+        """All N poses, (N, 3, 4) or (N, 12): a numpy array, or a torch tensor on
+        the host or a CUDA device.  A contiguous float64 CUDA tensor is read on
+        the device (keep it unchanged until the problem's stream has passed
+        this call); anything else goes through a float64 host copy."""
         if _is_torch(poses):
-            self._check(self._lib.pba_set_poses(self._h, ctypes.c_void_p(poses.data_ptr()), 1 if poses.is_cuda else 0),
-                        "set_poses")
-            return
-        arr = np.ascontiguousarray(poses, dtype=np.float64).reshape(self.n_frames, 12)
+            t = poses.detach()
+            if t.numel() != 12 * self.n_frames:
+                raise ValueError(f"poses must hold {self.n_frames} x 12 values, got shape {tuple(poses.shape)}")
+            if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()):
+                poses = t.cpu().double().numpy()
+            else:
+                self._check(self._lib.pba_set_poses(self._h, ctypes.c_void_p(t.data_ptr()), 1), "set_poses")
+                return
+        arr = np.ascontiguousarray(poses, dtype=np.float64)
+        if arr.size != 12 * self.n_frames:
+            raise ValueError(f"poses must hold {self.n_frames} x 12 values, got shape {arr.shape}")
         self._check(self._lib.pba_set_poses(self._h, arr.ctypes.data_as(ctypes.c_void_p), 0), "set_poses")
 
     def get_poses(self) -> np.ndarray:
