@@ -120,3 +120,44 @@ def test_create_rejects_bad_configurations_before_touching_the_gpu():
         assert not h.value
         msg = lib.pba_last_error(None)
         assert msg.startswith(b"pba_create: ") and needle in msg, (needle, msg)
+
+
+def test_header_compiles_as_c99_and_links(tmp_path):
+    """include/pba.h is plain C: a C99 program includes it, links libpba.so and
+    calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2303_16878_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "pba.h"
+int main(void) {
+    pba_problem* p = NULL;
+    pba_config cfg;
+    memset(&cfg, 0, sizeof cfg);
+    if (pba_create(NULL, NULL, &p) != PBA_EINVAL) return 1;
+    if (strncmp(pba_last_error(NULL), "pba_create: ", 12) != 0) return 2;
+    if (pba_create(&cfg, NULL, &p) != PBA_EINVAL || p != NULL) return 3;
+    if (pba_set_lambda(NULL, 1.0) != PBA_EINVAL) return 4;
+    pba_destroy(NULL);
+    printf("%d %d %s\n", (int)sizeof(pba_sensor), (int)sizeof(pba_config), pba_last_error(NULL));
+    return 0;
+}
+""")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-lpba", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    size_s, size_c, msg = r.stdout.split(" ", 2)
+    assert (int(size_s), int(size_c)) == (16 + 8 * 16, 8 + 8 + 8 + 9 * 8 + 16)
+    assert msg.startswith("pba_create: n_frames")
