@@ -56,14 +56,16 @@ FLOP_PER_POINT_SPHERICAL = 31
 FLOP_PER_RESIDUAL_FULL = 765
 
 
-def measured_hbm_gbs() -> float:
-    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the
-    6.8 TB/s fallback of one earlier GB300 measurement."""
+def measured_hbm(path: str = None):
+    """(GB/s, source): the HBM copy bandwidth measured on the GB300s
+    (MEASURED_PEAKS.json), else the 6.8 TB/s fallback of one earlier GB300
+    measurement."""
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
     try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured: MEASURED_PEAKS.json hbm_gbs"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback: 6.8 TB/s, one earlier GB300 measurement"
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch on this
@@ -448,7 +450,8 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- the JSON line
 
-def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_gbs: float) -> dict:
+def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_gbs: float,
+              hbm_source: str = "measured: MEASURED_PEAKS.json hbm_gbs") -> dict:
     """The GPU arm's JSON line from the measurements in `out` (pure: no device
     access).  Roofline of the dominant kernel: algorithmic FP32 FLOPs of one
     full linearisation (per valid residual and per processed point, mean
@@ -477,7 +480,7 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
                      "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
                      "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak_gbs,
                              "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak_gbs,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                             "peak_source": hbm_source},
                      "ncu_unit_fracs": LINEARIZE_NCU_UNITS,
                      "binding": "SM instruction issue, then the L1 data pipe of the gathers"},
         "phase_ms": ph,
@@ -517,7 +520,7 @@ def main():
     out, w = run_ours(args, rank, world, device)
     if rank == 0:
         sms = torch.cuda.get_device_properties(device).multi_processor_count
-        line = make_line(args, world, out, w.n_frames, sms, measured_hbm_gbs())
+        line = make_line(args, world, out, w.n_frames, sms, *measured_hbm())
         if not args.no_cpu:
             cb = oracle_sample(w, args.cpu_seconds)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -86,3 +86,15 @@ def test_reference_arm_line(monkeypatch, capsys):
                            "d2h_bytes_per_step": 0}
     assert len(calls) == 103 and 0.5 <= calls[0] <= 12.0 and 103 * calls[0] <= 160.0
     assert abs(line["value"] - (5.0e5 + sum(range(3, 103)) / 100)) < 1e-6
+
+
+def test_hbm_peak_comes_from_the_measured_file_or_says_fallback(tmp_path):
+    import json
+    import bench
+    f = tmp_path / "peaks.json"
+    f.write_text(json.dumps({"hbm_gbs": 6693.8, "bf16_tflops": 1900.0}))
+    assert bench.measured_hbm(str(f)) == (6693.8, "measured: MEASURED_PEAKS.json hbm_gbs")
+    gbs, src = bench.measured_hbm(str(tmp_path / "absent.json"))
+    assert gbs == 6800.0 and src.startswith("fallback")
+    f.write_text("{}")
+    assert bench.measured_hbm(str(f))[1].startswith("fallback")
