@@ -98,3 +98,33 @@ def test_hbm_peak_comes_from_the_measured_file_or_says_fallback(tmp_path):
     assert gbs == 6800.0 and src.startswith("fallback")
     f.write_text("{}")
     assert bench.measured_hbm(str(f))[1].startswith("fallback")
+
+
+def test_main_wires_the_measurement_into_one_line(monkeypatch, capsys):
+    """main() on a faked single-GPU run: the measurement of run_ours, the SM
+    count, the HBM peak and the CPU baseline end up in one JSON line."""
+    import json
+    import sys
+    import types
+    import torch
+    import bench
+    out = dict(value=1.7e10, ms_per_step=1.3, n_valid=22_000_000, n_valid_mean=21_500_000.0, n_points=68_000_000,
+               n_pairs=1170, launches=10, variants=(1, 2), clocks=None,
+               phase_ms={"solve": 0.17, "update": 0.02, "linearize": 1.08, "reduce_assemble": 0.05, "accept": 0.01},
+               solve_update_f64_ms=0.78, build_pairs={}, normals={}, adjoint={})
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: types.SimpleNamespace(multi_processor_count=152))
+    monkeypatch.setattr(bench, "run_ours", lambda args, rank, world, device: (out, types.SimpleNamespace(n_frames=50)))
+    monkeypatch.setattr(bench, "oracle_sample", lambda w, seconds, seed=0: dict(
+        value=5.3e5, unit=bench.UNIT, cores=1, kind="oracle", sample="fake", seconds=seconds, pairs=3))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "7", "--warmup", "3"])
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.main()
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["steps"] == 7 and line["gpu_launches"] == 70 and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["value"] == 5.3e5 and line["roofline"]["peak"] > 80.0
+    assert line["roofline"]["hbm"]["peak_source"].startswith(("measured", "fallback"))
