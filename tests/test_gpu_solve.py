@@ -5,7 +5,8 @@ mixed-precision arithmetic (PBA_SOLVE_MIXED_STEPS) and the FP64 Cholesky.
 
 Bars: after one iteration the poses of the mixed solves agree with the FP64
 Cholesky to max(1e-8, 1e-10 kappa) of the step, kappa the condition number of
-the Jacobi-scaled damped system (the refinement stops at |r| <= 1e-10 |b'|),
+the Jacobi-scaled damped system (after its three fixed passes the refinement
+requires |r| <= 1e-10 |b'|, else the step is rejected),
 accept/reject decisions are identical, and a singular damped system is
 rejected by all three.
 """
@@ -61,7 +62,7 @@ def test_cluster_solve_matches_per_step_and_f64(n_frames):
                 stats.append(p.iterate())
             assert all(s["status"] == 0 for s in stats)
             assert len({s["accepted"] for s in stats}) == 1
-            # the refinement stops at |r| <= 1e-10 |b'| for the Jacobi-scaled system
+            # the refined solution satisfies |r| <= 1e-10 |b'| for the Jacobi-scaled system
             # A' = D (H_ff + lambda I) D, so its step is within kappa(A') 1e-10 of the exact one
             A = H[6:, 6:] + stats[2]["lambda_used"] * np.eye(H.shape[0] - 6)
             d = 1.0 / np.sqrt(np.diag(A))
