@@ -74,14 +74,25 @@ def test_reference_arm_line(monkeypatch, capsys):
         return dict(value=5.0e5 + seed, unit=bench.UNIT, cores=1, kind="oracle", sample="fake", seconds=seconds,
                     pairs=3)
 
-    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
-    monkeypatch.setattr(bench, "make_workload", lambda name: object())
+    class FakePool:
+        def __init__(self, name, workers=None):
+            self.n = 4
+
+        def sample(self, seconds, seed=0):
+            return fake_sample(None, seconds, seed)
+
+        def close(self):
+            calls.append("closed")
+
+    monkeypatch.setattr(bench, "OraclePool", FakePool)
     args = argparse.Namespace(workload="street", steps=100, warmup=3, cpu_seconds=12.0, gpus=1)
     bench.run_reference(args)
+    assert calls.pop() == "closed"
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["steps"] == 100 and line["warmup"] == 3 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] == 4
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert len(calls) == 103 and 0.5 <= calls[0] <= 12.0 and 103 * calls[0] <= 160.0
@@ -118,6 +129,18 @@ def test_main_wires_the_measurement_into_one_line(monkeypatch, capsys):
     monkeypatch.setattr(bench, "run_ours", lambda args, rank, world, device: (out, types.SimpleNamespace(n_frames=50)))
     monkeypatch.setattr(bench, "oracle_sample", lambda w, seconds, seed=0: dict(
         value=5.3e5, unit=bench.UNIT, cores=1, kind="oracle", sample="fake", seconds=seconds, pairs=3))
+
+    class FakePool:
+        def __init__(self, name, workers=None):
+            self.n = 16
+
+        def sample(self, seconds, seed=0):
+            return dict(value=8.0e6, unit=bench.UNIT, cores=16, kind="oracle", sample="fake16", seconds=seconds)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(bench, "OraclePool", FakePool)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "7", "--warmup", "3"])
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
@@ -126,5 +149,22 @@ def test_main_wires_the_measurement_into_one_line(monkeypatch, capsys):
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["steps"] == 7 and line["gpu_launches"] == 70 and line["n_gpus"] == 1
-    assert line["cpu_baseline"]["value"] == 5.3e5 and line["roofline"]["peak"] > 80.0
+    assert line["cpu_baseline"]["value"] == 8.0e6 and line["cpu_baseline"]["cores"] == 16
+    assert line["cpu_baseline_one_core"]["value"] == 5.3e5 and line["roofline"]["peak"] > 80.0
     assert line["roofline"]["hbm"]["peak_source"].startswith(("measured", "fallback"))
+
+
+def test_oracle_pool_times_disjoint_slices_concurrently():
+    """Two spawn-started oracle processes on the small RGB-D room: one sample
+    covers more pairs than either slice alone, reports 2 cores, and its rate
+    is the residuals of both over the slower one's time; the processes end on
+    close()."""
+    import bench
+    pool = bench.OraclePool("room", workers=2)
+    try:
+        r = pool.sample(0.3, seed=1)
+    finally:
+        pool.close()
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["pairs"] >= 2
+    assert abs(r["value"] - r["residuals"] / r["seconds"]) < 1e-6 * r["value"]
+    assert all(not p.is_alive() for p in pool.procs)
