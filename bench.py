@@ -99,7 +99,9 @@ def make_workload(name):
     from paper_2303_16878_gb300 import synth
     if name == "room":
         return synth.make_rgbd_room()
-    return synth.make_lidar_street()
+    if name == "street":
+        return synth.make_lidar_street()
+    raise ValueError(f"unknown workload {name!r}")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -458,7 +460,7 @@ class OraclePool:
     seeded pair order concurrently, and the rate is all residuals over the
     slowest worker's time."""
 
-    def __init__(self, workload_name: str, workers: int = None, ready_timeout: float = 900.0):
+    def __init__(self, workload_name: str, workers: int = None, ready_timeout: float = 300.0):
         import multiprocessing as mp
         ctx = mp.get_context("spawn")
         self.n = workers or host_cores()
@@ -469,16 +471,31 @@ class OraclePool:
         for pr in self.procs:
             pr.start()
         try:
-            for _ in range(self.n):
-                self.outbox.get(timeout=ready_timeout)
+            self._collect(ready_timeout)
         except Exception:
             self.close()
             raise
 
+    def _collect(self, timeout: float) -> list:
+        """One message from every worker; raises as soon as a worker has died,
+        or after timeout seconds."""
+        import queue
+        out, deadline = [], time.time() + timeout
+        while len(out) < self.n:
+            try:
+                out.append(self.outbox.get(timeout=1.0))
+            except queue.Empty:
+                dead = [pr.exitcode for pr in self.procs if pr.exitcode is not None]
+                if dead:
+                    raise RuntimeError(f"oracle worker exited with code {dead[0]}")
+                if time.time() > deadline:
+                    raise TimeoutError(f"oracle workers: {len(out)} of {self.n} answered in {timeout:.0f} s")
+        return out
+
     def sample(self, seconds: float, seed: int = 0) -> dict:
         for q in self.inboxes:
             q.put((seconds, seed))
-        rs = [self.outbox.get(timeout=10 * seconds + 300) for _ in range(self.n)]
+        rs = self._collect(3 * seconds + 120)
         res = sum(r["residuals"] for r in rs)
         elapsed = max(r["seconds"] for r in rs)
         pairs = sum(r["pairs"] for r in rs)

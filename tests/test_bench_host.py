@@ -168,3 +168,15 @@ def test_oracle_pool_times_disjoint_slices_concurrently():
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["pairs"] >= 2
     assert abs(r["value"] - r["residuals"] / r["seconds"]) < 1e-6 * r["value"]
     assert all(not p.is_alive() for p in pool.procs)
+
+
+def test_oracle_pool_reports_a_dead_worker_quickly():
+    """A worker that cannot build its workload ends at once; the pool raises
+    within seconds instead of waiting for its timeout."""
+    import time
+    import pytest
+    import bench
+    t0 = time.time()
+    with pytest.raises(RuntimeError):
+        bench.OraclePool("no-such-workload", workers=2, ready_timeout=120.0)
+    assert time.time() - t0 < 60.0
