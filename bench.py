@@ -83,13 +83,15 @@ FP32_LANES_PER_SM = 128
 
 def parse():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["street", "room"], default="street")
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs of the run (N > 1 under torchrun: one replica per rank)")
+    ap.add_argument("--steps", type=int, default=100, help="timed LM iterations")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed LM iterations before them")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours",
+                    help="ours: the GPU library; reference: the FP64 oracle on the host cores")
+    ap.add_argument("--workload", choices=["street", "room"], default="street",
+                    help="street: 50 LiDAR frames of 64 x 1024 (the benchmark); room: 8 RGB-D frames of 160 x 120")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-pair path")
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run from pinned host buffers")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     return ap.parse_args()
@@ -268,7 +270,7 @@ def run_ours(args, rank, world, device):
         one_step(prob)
     launches = prob.iteration_launches()
 
-    # timed region: K identical iterations
+    # timed region: K consecutive iterations
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
