@@ -45,6 +45,9 @@ METRIC = "residuals/sec and ms per GN iteration, batched vs plain GPU path at st
 UNIT = "residuals/s"
 WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, "
             "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64-refined solve")
+WORKLOADS = {"street": WORKLOAD,
+             "room": ("rgbd-room 8 frames 160x120 pinhole (f 120), pairs j - i <= 3, init noise 2 cm / 1 deg, "
+                      "FP16 texels / FP32 residuals / FP64-refined solve")}
 
 # Algorithmic FP32 work of the linearisation kernel, counted from the formulas as
 # implemented (FMA = 2 FLOP; square root, division and atan2 = 1):
@@ -535,7 +538,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: seeded pairs of the workload split over {cores} processes "
                                        f"(one per host core), each process timing at most {per_step:.1f} s of "
@@ -564,7 +567,8 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
         "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames": n_frames, "pairs": out["n_pairs"],
+        "config": {"workload": WORKLOADS[getattr(args, "workload", "street")], "frames": n_frames,
+                   "pairs": out["n_pairs"],
                    "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)",
