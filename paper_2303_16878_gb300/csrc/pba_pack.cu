@@ -1,16 +1,22 @@
-// pba_pack.cu -- per-frame packing (once per upload).
+// pba_pack.cu -- per-frame packing (once per upload), in three passes over
+// all SMs, then the central differences.
 //
 // For every pixel u of a frame (Sec. IV-A five-channel cue image):
-//   - a sampling texel: d (FP32, 0 when the pixel is not valid) and g, n in
-//     FP16 or FP32, so one bilinear tap is one 16- or 32-byte load;
-//   - when the pixel is valid, a pixel-point p_u = R_o pi^-1(u, d) + t_o with
-//     its intensity g_u, normal n_u^o = R_o n_u (Supp., p_u) and pixel index,
-//     written in raster order to a compacted array (block-wide ballot scan).
+//   - pass 1 (k_pack_valid): its validity as a byte, and per tile of 1024
+//     pixels the count of valid ones;
+//   - pass 2 (k_pack_tex): a sampling texel: d (FP32, 0 when the pixel is not
+//     valid), g and n in FP16 or FP32, and the usable flag (the pixel and its
+//     four neighbours valid), so one bilinear tap is one 16- or 32-byte load;
+//   - pass 3 (k_pack_points): when the pixel is valid, a pixel-point
+//     p_u = R_o pi^-1(u, d) + t_o with its intensity g_u, normal
+//     n_u^o = R_o n_u (Supp., p_u) and pixel index, written in raster order at
+//     the offset given by the counts of the frame's earlier tiles;
+//   - k_grad: the central differences of the Supp. at every usable pixel.
 // Unprojection pi^-1 (Sec. III): pinhole p = d K^-1 (u, v, 1)^T; spherical
 // p = d (cos el cos az, cos el sin az, sin el) with az = (u - c_x) / f_x,
 // el = (v - c_y) / f_y.  Validity: range_min <= d <= range_max, d > 0 and
-// |n| > 0.5, evaluated in double so that the decision is exact for the
-// float32 inputs.
+// |n| > 0.5, decided in FP32 exactly as the double evaluation of the float32
+// inputs would decide it (see pixel_valid).
 #include <cfloat>
 
 #include "pba_internal.cuh"
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restri
     }
 }
 
-// Pass 2: the valid pixels of a tile as pixel-points p_u = R_o pi^-1(u, d) + t_o
+// Pass 3: the valid pixels of a tile as pixel-points p_u = R_o pi^-1(u, d) + t_o
 // with g_u, n_u^o = R_o n_u and the pixel index, written in raster order at the
 // tile's offset (the counts of the frame's earlier tiles); the CTA of tile 0
 // also writes the frame's point count.

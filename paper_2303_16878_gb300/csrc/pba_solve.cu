@@ -1,14 +1,21 @@
-#include <algorithm>
-// pba_solve.cu -- FP64 assembly, damped gauge-fixed Cholesky solve, box-plus
-// update and the Levenberg-Marquardt accept / reject, all on the device.
+// pba_solve.cu -- FP64 assembly, the damped gauge-fixed solve in per-tile-step
+// launches, box-plus update and the Levenberg-Marquardt accept / reject, all
+// on the device.
 //
 // The paper minimises Eq. total-error-multicue with Levenberg-Marquardt (Sec. IV-C, srrg2_solver);
 // the normal equations are H = sum w J^T Omega J, b = sum w J^T Omega e over all
 // residuals.  Each step solves (H_ff + lambda I) dx_f = -b_f, where _f drops
 // frame 0 (gauge freedom), and applies X_k <- X_k [+] dx_k (Supp.):
-// X [+] dx = [R R(dq), R dt + t], R(dq) from the unit quaternion (sqrt(1 - |dq|^2), dq).
-// The step is kept when the cost decreased (lambda / 10), otherwise the poses
-// are restored and lambda grows (x 10).  Double precision throughout.
+// X [+] dx = [R R(dq), R dt + t], R(dq) from the unit quaternion (sqrt(1 - |dq|^2), dq),
+// normalised (1, dq) when |dq| >= 1.  The step is kept when the cost decreased
+// (lambda / 10), otherwise the poses are restored and lambda grows (x 10).
+// Assembly, damping, update and accept are FP64.  The tiled Cholesky kernels
+// are templates: FP64 for the FP64 solver, FP32 on the Jacobi-scaled matrix for
+// the mixed-precision solver, whose solution is refined with FP64 residuals
+// (k_refine_*); the one-launch cluster version of the mixed solve is in
+// pba_solve_cluster.cu.
+#include <algorithm>
+
 #include "pba_internal.cuh"
 #include "../../include/pba.h"
 
