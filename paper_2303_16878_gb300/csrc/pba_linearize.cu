@@ -4,8 +4,9 @@
 //                 M = R_o^T R_j^T R_i, a = R_o^T (R_j^T (t_i - t_j) - t_o)  (Supp., pbar_u; Eq. uprime)
 // k_linearize     one persistent launch over a queue of chunks (pair, points);
 //                 per pixel-point: transform, project (Eq. pinhole-projection / spherical-projection), sample the
-//                 five target channels and their image gradients bilinearly from
-//                 the 12-texel central-difference stencil (Supp., image Jacobians),
+//                 five target channels bilinearly at the 4 taps and their image
+//                 gradients (Supp., image Jacobians: the central differences,
+//                 precomputed per pixel at upload, interpolated at the same taps),
 //                 residual e = zeta(pbar) - I_j(u') (Supp., Eq. error-jacobian),
 //                 Huber weight, Jacobian J_i, and accumulation of the 6x6
 //                 H6 = sum w J_i^T Omega J_i, b6 = sum w J_i^T Omega e, cost, count
@@ -88,10 +89,11 @@ constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two
 constexpr int kQItems = 14;  // floats per queued residual: e[5], w, pbar[3], point, r0, c0, a, b
 
 // Stage 2 (a4 gradients + a6 + a7) for one queued residual: the image
-// gradients of the five channels at u' from the 12-texel stencil (central
-// differences of the Supp. interpolated bilinearly, grad_mode 0, or the exact
-// bilinear derivative, grad_mode 1), d pi / d pbar, the 5 x 6 Jacobian J_i and
-// its Huber-weighted accumulation into H6 (upper triangle) and b6.
+// gradients of the five channels at u' (grad_mode 0: the central differences
+// of the Supp., precomputed per pixel, interpolated bilinearly at the 4 taps,
+// which equals the 12-texel stencil term by term; grad_mode 1: the exact
+// bilinear derivative from the 4 texels), d pi / d pbar, the 5 x 6 Jacobian
+// J_i and its Huber-weighted accumulation into H6 (upper triangle) and b6.
 template <int TEXEL>
 __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int model, float fx, float fy, int W,
                                                bool wrap, const float (&M)[9], const float (&om)[5],
