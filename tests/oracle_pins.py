@@ -48,6 +48,8 @@ PIN_TOL = {
     "residual_brute_force": 1e-9,
     "build_pairs": 0.5,
     "relative_jacobian": 1e-12,
+    "hessian_zero_residual": 1e-6,
+    "huber_hessian": 1e-5,
 }
 
 
@@ -952,6 +954,133 @@ def pin_relative_jacobian(O, lib, w, stride=7):
     return worst
 
 
+# ---------------------------------------------- the weights of H (Sec. IV-C)
+
+def affine_plane_workload(shift_px=(2.75, 1.5), depth=2.0, f=40.0):
+    """Two pinhole frames facing a fronto-parallel plane at constant depth,
+    the second translated so that the image moves by a fractional number of
+    pixels.  The intensity is affine in the pixel coordinates (dyadic slope,
+    exact in binary16), so bilinear interpolation is exact at every sub-pixel
+    position and the residual is zero at the true poses: pixel u of frame 0
+    sees the plane point that frame 1 sees at u - shift."""
+    from paper_2303_16878_gb300 import synth
+    W, H = 48, 40
+    s = synth.pinhole_sensor(W, H, f, W / 2.0, H / 2.0)
+    cols = np.arange(W)[None, :].astype(np.float64)
+    rows = np.arange(H)[:, None].astype(np.float64)
+
+    def img(dc, dr):
+        c = np.zeros((H, W, 5), dtype=np.float32)
+        c[..., 0] = 0.25 + 2.0 ** -8 * (cols + dc) + 2.0 ** -9 * (rows + dr)
+        c[..., 1] = depth
+        c[..., 4] = -1.0
+        return c
+    X0 = synth.IDENTITY_3x4.copy()
+    X1 = synth.IDENTITY_3x4.copy()
+    X1[0, 3] = shift_px[0] * depth / f
+    X1[1, 3] = shift_px[1] * depth / f
+    poses = np.stack([X0, X1])
+    params = synth.default_params(w_int=1.0, w_depth=0.5, w_normal=0.3, huber_delta=1e9, occ_abs=0.1,
+                                  occ_rel=0.05)
+    return synth.Workload("affine-plane", [s], np.zeros(2, dtype=np.int32), [img(0.0, 0.0), img(*shift_px)],
+                          poses, poses.copy(), np.array([[0, 1]], dtype=np.int32), params)
+
+
+def pin_hessian_zero_residual(O, lib, h=1e-5):
+    """Where every residual is zero, the Gauss-Newton matrix of the LM normal
+    equations (Sec. IV-C) is the exact Hessian of F / 2: d b / d dx = H, since
+    b = sum w J^T Omega e and the terms with the derivative of J are
+    multiplied by e = 0.  Central differences of the oracle's b under
+    X_k [+] (+-h e_a) on the affine plane (non-unit Omega, both gradient
+    modes; b itself is pinned as dF / d dx / 2 by the cost-gradient pin)
+    must equal column 6 k + a of the oracle's H, for both frames; a weight
+    left out of H or put into it twice (Omega, Huber), or a transposed block,
+    moves H away from them.  Returns the largest difference relative to
+    max |H|."""
+    w = affine_plane_workload()
+    s = w.sensors[0]
+    worst = 0.0
+    for gm in (0, 1):
+        params = dict(w.params, grad_mode=gm)
+        r0 = O.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_gt, w.pairs, params, lib=lib)
+        assert r0["count"] > 800, r0["count"]
+        assert np.abs(r0["b"]).max() < 1e-9 * np.abs(r0["H"]).max()
+        H = r0["H"]
+        for k in (0, 1):
+            for a in range(6):
+                bs, counts = [], []
+                for sg in (1, -1):
+                    d = np.zeros(6)
+                    d[a] = sg * h
+                    poses = w.poses_gt.copy()
+                    poses[k] = O.boxplus(poses[k], d, lib=lib)
+                    r = O.linearize(w.sensors, w.frame_sensor, w.channels, poses, w.pairs, params, lib=lib)
+                    bs.append(r["b"])
+                    counts.append(r["count"])
+                assert counts[0] == counts[1] == r0["count"], "a point changed validity under the step"
+                fd = (bs[0] - bs[1]) / (2 * h)
+                worst = max(worst, float(np.abs(fd - H[:, 6 * k + a]).max() / np.abs(H).max()))
+    return worst
+
+
+def pin_huber_hessian(O, lib, w, n_each=12, h=1e-6, seed=5):
+    """The Huber weight of the LM normal equations (Sec. IV-C; reading R1:
+    w = 1 when chi <= delta, else delta / chi, chi = sqrt(e^T Omega e)): the
+    12 x 12 block of a pair whose source image holds a single valid pixel
+    equals w J^T Omega J, with J = [J_i J_j] from central differences of e
+    under X [+] dx (grad_mode 1) and chi, hence w, from the brute-force
+    residual `_bf_residuals`; neither comes from the oracle's accumulation.
+    Points on both sides of delta are taken (n_each of each).  Returns the
+    largest difference relative to max |H| of the point."""
+    params = dict(w.params, grad_mode=1, w_depth=0.5, w_normal=0.3, huber_delta=0.05)
+    om = np.array([params["w_int"], params["w_depth"]] + [params["w_normal"]] * 3)
+    s = w.sensors[0]
+    rng = np.random.default_rng(seed)
+    worst, used = 0.0, [0, 0]
+    i, j = 0, 1
+    Xi, Xj = w.poses_init[i], w.poses_init[j]
+    pts, pix = O.frame_points(s, params, w.channels[i], lib=lib)
+    for k in rng.permutation(len(pts)):
+        if min(used) >= n_each:
+            break
+        ok, e_bf, _, _, _ = _bf_residuals(s, params, w.channels[i], w.channels[j], Xi, Xj,
+                                          np.array([pix[k]], dtype=np.int64))
+        r = O.point_residual(s, params, w.channels[j], Xi, Xj, pts[k], lib=lib)
+        if not ok[0] or not r["valid"] or r["flag"]:
+            continue
+        chi = float(np.sqrt(om @ (e_bf[0] * e_bf[0])))
+        branch = int(chi > params["huber_delta"])
+        if used[branch] >= n_each:
+            continue
+        J = np.zeros((5, 12))
+        good = True
+        for a in range(6):
+            d = np.zeros(6)
+            d[a] = h
+            ev = [O.point_residual(s, params, w.channels[j], O.boxplus(Xi, sg * d, lib=lib), Xj, pts[k], lib=lib)
+                  for sg in (1, -1)]
+            ev += [O.point_residual(s, params, w.channels[j], Xi, O.boxplus(Xj, sg * d, lib=lib), pts[k], lib=lib)
+                   for sg in (1, -1)]
+            if not all(x["valid"] for x in ev):
+                good = False
+                break
+            J[:, a] = (ev[0]["e"] - ev[1]["e"]) / (2 * h)
+            J[:, 6 + a] = (ev[2]["e"] - ev[3]["e"]) / (2 * h)
+        if not good:
+            continue
+        wt = 1.0 if chi <= params["huber_delta"] else params["huber_delta"] / chi
+        ref = wt * (J.T * om) @ J
+        src1 = np.zeros_like(w.channels[i])
+        row, col = divmod(int(pix[k]), s.width)
+        src1[row, col] = w.channels[i][row, col]
+        pr = O.linearize_pair(s, params, src1, w.channels[j], Xi, Xj, lib=lib)
+        assert pr["count"] == 1
+        worst = max(worst, float(np.abs(pr["H"] - ref).max() / np.abs(ref).max()))
+        used[branch] += 1
+    assert min(used) >= n_each, f"too few points on one side of delta: {used}"
+    return worst
+
+
 # ------------------------------------------------------- graph construction
 
 def pin_build_pairs(O, lib, w):
@@ -1028,6 +1157,8 @@ def all_pins(O, lib, room, street):
         "residual_brute_force": pin_residual_brute_force(O, lib, room, street),
         "relative_jacobian": max(pin_relative_jacobian(O, lib, room), pin_relative_jacobian(O, lib, street),
                                  pin_relative_jacobian(O, lib, _with_offset(room))),
+        "hessian_zero_residual": pin_hessian_zero_residual(O, lib),
+        "huber_hessian": max(pin_huber_hessian(O, lib, room), pin_huber_hessian(O, lib, street)),
     }
 
 

@@ -44,6 +44,11 @@ MUTATIONS = {
                                       "{1, -1}, {1, 0}, {1, 1}, {1, 2}, {2, 0}, {2, 2}};"),
     "pinhole_window_one_column_short": ("u >= 1.0 && u < (double)(s->width - 2)", "u >= 1.0 && u < (double)(s->width - 3)"),
     "boxplus_large_step_not_normalised": ("qw = 1.0 / n; qx /= n; qy /= n; qz /= n;", "qw = 0.0;"),
+    "omega_dropped_from_H": ("for (int r = 0; r < 5; ++r) s_h += J[r][a] * om[r] * J[r][c];",
+                             "for (int r = 0; r < 5; ++r) s_h += J[r][a] * J[r][c];"),
+    "huber_weight_dropped_from_H": ("H12[12 * a + c] += w * s_h;", "H12[12 * a + c] += s_h;"),
+    "huber_weight_squared_in_H": ("H12[12 * a + c] += w * s_h;", "H12[12 * a + c] += w * w * s_h;"),
+    "H_block_rows_and_columns_mixed": ("s_h += J[r][a] * om[r] * J[r][c];", "s_h += J[r][a] * om[r] * J[r][11 - c];"),
     "range_cue_horizontal_only": ("zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1] + pb[2] * pb[2]);",
                                   "zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1]);"),
 }
@@ -76,7 +81,10 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("offset_gradient_fd", lambda: P.pin_offset_gradient_fd(oracle_lib, lib, room3)),
                     ("residual_brute_force", lambda: P.pin_residual_brute_force(oracle_lib, lib, room3, street3)),
                     ("relative_jacobian", lambda: max(P.pin_relative_jacobian(oracle_lib, lib, room3),
-                                                      P.pin_relative_jacobian(oracle_lib, lib, street3)))]:
+                                                      P.pin_relative_jacobian(oracle_lib, lib, street3))),
+                    ("hessian_zero_residual", lambda: P.pin_hessian_zero_residual(oracle_lib, lib)),
+                    ("huber_hessian", lambda: max(P.pin_huber_hessian(oracle_lib, lib, room3),
+                                                  P.pin_huber_hessian(oracle_lib, lib, street3)))]:
         try:
             err = fn()
         except (AssertionError, ValueError, ArithmeticError, Exception):

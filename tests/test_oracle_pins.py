@@ -241,3 +241,17 @@ def test_target_jacobian_is_the_source_jacobian_mapped_by_the_relative_pose(orac
     if which.endswith("_offset"):
         w = P._with_offset(w)
     assert P.pin_relative_jacobian(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["relative_jacobian"]
+
+
+def test_hessian_equals_gauss_newton_matrix_at_zero_residual(oracle_lib):
+    """d b / d dx = H where every residual vanishes (Sec. IV-C normal equations;
+    pins the Omega weighting of H)."""
+    assert P.pin_hessian_zero_residual(oracle_lib, oracle_lib.load()) < P.PIN_TOL["hessian_zero_residual"]
+
+
+@pytest.mark.parametrize("which", ["room3", "street3"])
+def test_huber_weight_of_the_normal_equations(oracle_lib, which, request):
+    """Single-point pair blocks equal w J^T Omega J from finite-difference
+    Jacobians and the brute-force chi, on both sides of delta."""
+    w = request.getfixturevalue(which)
+    assert P.pin_huber_hessian(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["huber_hessian"]
