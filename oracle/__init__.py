@@ -39,7 +39,7 @@ class OParams(ctypes.Structure):
                 ("huber_delta", ctypes.c_double), ("occ_abs", ctypes.c_double), ("occ_rel", ctypes.c_double),
                 ("z_min", ctypes.c_double), ("range_min", ctypes.c_double), ("range_max", ctypes.c_double),
                 ("margin_px", ctypes.c_double), ("margin_rel", ctypes.c_double),
-                ("grad_mode", ctypes.c_int), ("other_branch", ctypes.c_int)]
+                ("grad_mode", ctypes.c_int), ("other_branch", ctypes.c_int), ("texel_f16", ctypes.c_int)]
 
 
 def build(force: bool = False, src: Optional[str] = None, out: Optional[str] = None) -> str:
@@ -79,6 +79,8 @@ def _declare(lib):
     P = ctypes.POINTER
     d, i32, i64, u32 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
     S, Pr = P(OSensor), P(OParams)
+    lib.o_half.argtypes = [ctypes.c_float]
+    lib.o_half.restype = d
     lib.o_project.argtypes = [S, P(d), P(d)]
     lib.o_unproject.argtypes = [S, d, d, d, P(d)]
     lib.o_proj_jacobian.argtypes = [S, P(d), P(d)]
@@ -137,10 +139,19 @@ def _params(p: Dict, margin_px: float = 1e-3, margin_rel: float = 1e-4) -> OPara
     o.margin_rel = float(p.get("margin_rel", margin_rel))
     o.grad_mode = int(p.get("grad_mode", 0))
     o.other_branch = int(p.get("other_branch", 0))
+    # R25: the target's intensity and normals sampled as binary16 values (FP16 texels)
+    o.texel_f16 = int(p.get("texel_f16", 0))
     return o
 
 
 # ---------------------------------------------------------------- primitives
+
+def half_round(x, lib=None) -> np.ndarray:
+    """Each float32 value rounded to the nearest binary16 number (R25), as float64."""
+    lib = lib or _load()
+    x = np.asarray(x, dtype=np.float32)
+    return np.array([lib.o_half(float(v)) for v in x.reshape(-1)]).reshape(x.shape)
+
 
 def project(sensor, p, lib=None) -> np.ndarray:
     lib, p = lib or _load(), _f64(p)

@@ -98,6 +98,7 @@ typedef struct {
     double margin_px, margin_rel;    /* decision margins */
     int grad_mode;                   /* R5 */
     int other_branch;                /* 1: a rejection whose decision lies within its margin is overruled */
+    int texel_f16;                   /* R25: target g and n sampled as binary16 values */
 } o_params;
 
 /* ---------------------------------------------------------------- algebra */
@@ -279,6 +280,31 @@ static const float* texel(const o_sensor* s, const float* ch, int r, int c) {
     return ch + 5 * ((size_t)r * s->width + c);
 }
 
+/*
+ * Reading R25 (FP16 image channels): with half-precision texels the target's
+ * intensity and normal channels are sampled as their binary16 values (depth
+ * stays float32; a pixel's validity is still decided on its float32
+ * channels).  Rounding to the nearest binary16 number, ties to even, from the
+ * format's definition: 11 significant bits, smallest normal exponent -14 (so
+ * below 2^-14 the spacing stays 2^-24), largest finite value 65504.
+ */
+double o_half(float x) {
+    double v = (double)x;
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    (void)frexp(v, &e);        /* |v| = m 2^e, 0.5 <= m < 1 */
+    int q = e - 11;            /* spacing of 11-bit significands in [2^(e-1), 2^e) */
+    if (q < -24) q = -24;      /* subnormal binary16 numbers */
+    double r = ldexp(nearbyint(ldexp(v, -q)), q);  /* exact scaling; nearbyint rounds ties to even */
+    if (fabs(r) > 65504.0) return v > 0.0 ? INFINITY : -INFINITY;
+    return r;
+}
+
+/* channel ci of texel I as the sampled image holds it */
+static double tval(const o_params* prm, const float* I, int ci) {
+    return (prm->texel_f16 && ci != 1) ? o_half(I[ci]) : (double)I[ci];
+}
+
 static double near_int_dist(double x) {
     return fabs(x - floor(x + 0.5));
 }
@@ -320,18 +346,18 @@ static int sample(const o_sensor* s, const o_params* prm, const float* ch, doubl
         const float* Iu = texel(s, ch, r - 1, c);
         const float* Id = texel(s, ch, r + 1, c);
         for (int ci = 0; ci < 5; ++ci) {
-            val[ci] += w[t] * (double)I[ci];
+            val[ci] += w[t] * tval(prm, I, ci);
             if (prm->grad_mode == 0) {
                 /* Supp.: dI/dc = (I_{r,c+1} - I_{r,c-1}) / 2, dI/dr = (I_{r+1,c} - I_{r-1,c}) / 2 */
-                gu[ci] += w[t] * 0.5 * ((double)Ir[ci] - (double)Il[ci]);
-                gv[ci] += w[t] * 0.5 * ((double)Id[ci] - (double)Iu[ci]);
+                gu[ci] += w[t] * 0.5 * (tval(prm, Ir, ci) - tval(prm, Il, ci));
+                gv[ci] += w[t] * 0.5 * (tval(prm, Id, ci) - tval(prm, Iu, ci));
             }
         }
     }
     for (int ci = 0; ci < 5; ++ci) {
         /* slopes of the bilinear interpolant in u and v: |d val / du| + |d val / dv| */
-        double I00 = texel(s, ch, r0, c0)[ci], I01 = texel(s, ch, r0, c0 + 1)[ci];
-        double I10 = texel(s, ch, r0 + 1, c0)[ci], I11 = texel(s, ch, r0 + 1, c0 + 1)[ci];
+        double I00 = tval(prm, texel(s, ch, r0, c0), ci), I01 = tval(prm, texel(s, ch, r0, c0 + 1), ci);
+        double I10 = tval(prm, texel(s, ch, r0 + 1, c0), ci), I11 = tval(prm, texel(s, ch, r0 + 1, c0 + 1), ci);
         double su = (1 - b) * (I01 - I00) + b * (I11 - I10);
         double sv = (1 - a) * (I10 - I00) + a * (I11 - I01);
         slope[ci] = fabs(su) + fabs(sv);

@@ -369,7 +369,7 @@ def _room_scene(seed: int) -> Scene:
 def make_rgbd_room(n_frames: int = 8, width: int = 160, height: int = 120, f: float = 120.0,
                    cx: Optional[float] = None, cy: Optional[float] = None,
                    seed: int = 1, sigma_t: float = 0.02, sigma_r_deg: float = 1.0,
-                   pair_window: int = 3, fp16_exact: bool = True,
+                   pair_window: int = 3, fp16_exact: bool = False,
                    depth_noise: float = 0.0, intensity_noise: float = 0.0,
                    params: Optional[Dict] = None) -> Workload:
     """RGB-D pinhole sequence in a 5 x 5 x 3 m room of six textured planes.
@@ -504,7 +504,7 @@ def make_lidar_street(n_frames: int = 50, width: int = 1024, height: int = 64,
                       vfov_up_deg: float = 16.6, vfov_down_deg: float = -16.6,
                       spacing: float = 1.0, seed: int = 2, sigma_t: float = 0.10,
                       sigma_r_deg: float = 0.5, drop: float = 0.05, min_overlap: float = 0.3,
-                      max_pair_distance: float = 40.0, fp16_exact: bool = True,
+                      max_pair_distance: float = 40.0, fp16_exact: bool = False,
                       params: Optional[Dict] = None) -> Workload:
     """LiDAR spherical-projection sequence along a synthetic street.
 
@@ -585,7 +585,7 @@ def make_plane_shift(width: int = 48, height: int = 40, f: float = 40.0, depth: 
     poses[1] = IDENTITY_3x4
     poses[1, 0, 3] = shift_px[0] * depth / f
     poses[1, 1, 3] = shift_px[1] * depth / f
-    chans = [quantize_fp16(render(scene, sensor, poses[k], 0.1, 100.0)) for k in range(2)]
+    chans = [render(scene, sensor, poses[k], 0.1, 100.0) for k in range(2)]
     return Workload("plane-shift", [sensor], np.zeros(2, dtype=np.int32), chans, poses,
                     poses.copy(), np.array([[0, 1]], dtype=np.int32), default_params())
 
@@ -608,7 +608,8 @@ def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 1
                      lidar_width: int = 512, lidar_height: int = 32, vfov_up_deg: float = 16.6,
                      vfov_down_deg: float = -16.6, cam_offset=(0.10, 0.0, 0.10), seed: int = 7,
                      sigma_t: float = 0.02, sigma_r_deg: float = 1.0, coupled: bool = True,
-                     tilt_deg: float = 0.0, params: Optional[Dict] = None) -> Workload:
+                     tilt_deg: float = 0.0, fp16_exact: bool = False,
+                     params: Optional[Dict] = None) -> Workload:
     """A platform carrying an RGB-D camera and a 3D LiDAR (Sec. V, fusion) in
     the textured room of make_rgbd_room.
 
@@ -644,9 +645,11 @@ def make_fusion_room(n_poses: int = 4, cam_width: int = 160, cam_height: int = 1
         plat[k, :, 3] = [0.4 * math.cos(th), 0.4 * math.sin(th) - 0.3, 1.2 + rng.uniform(0.0, 0.1)]
     chans = []
     for k in range(n_poses):
-        chans.append(quantize_fp16(render(scene, cam, compose(plat[k], Xc), 0.5, 5.0)))
+        chans.append(render(scene, cam, compose(plat[k], Xc), 0.5, 5.0))
     for k in range(n_poses):
-        chans.append(quantize_fp16(render(scene, lidar, plat[k], 0.5, 8.0)))
+        chans.append(render(scene, lidar, plat[k], 0.5, 8.0))
+    if fp16_exact:
+        chans = [quantize_fp16(c) for c in chans]
     init_plat = perturb_poses(plat, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
     poses = np.concatenate([plat, plat])
     init = np.concatenate([init_plat, init_plat])
@@ -959,11 +962,12 @@ def _noisy(ch, seed: int, depth_noise: float, intensity_noise: float):
 def make_rgbd_hall(n_frames: int = 200, width: int = 640, height: int = 480, f: float = 525.0, seed: int = 3,
                    sigma_t: float = 0.02, sigma_r_deg: float = 1.0, depth_noise: float = 1e-3,
                    intensity_noise: float = 0.01, max_angle_deg: float = 30.0, max_dist: float = 1.0,
-                   min_ratio: float = 1.0 / 3.0, device="cuda", params: Optional[Dict] = None) -> Workload:
+                   min_ratio: float = 1.0 / 3.0, device="cuda", fp16_exact: bool = False,
+                   params: Optional[Dict] = None) -> Workload:
     """RGB-D 640 x 480 sequence of n_frames along a smooth closed spline
     through the four rooms of _hall_scene; depth noise sigma = 1 mm z^2,
-    intensity noise sigma = 0.01, then intensity and normals rounded to
-    binary16.  Pairs by the Sec. IV-B rule on the initial poses: rotation
+    intensity noise sigma = 0.01 (with fp16_exact, intensity and normals
+    rounded to binary16 afterwards).  Pairs by the Sec. IV-B rule on the initial poses: rotation
     angle < 30 deg, translation < 1 m, overlap ratio (renderer geometry) >
     1/3, plus consecutive frames (a sequential acquisition, closing the
     loop).  Channels are torch tensors on `device`.  Seeds: scene 1000 + seed,
@@ -981,7 +985,7 @@ def make_rgbd_hall(n_frames: int = 200, width: int = 640, height: int = 480, f: 
     for k in range(n_frames):
         c = render_t(scene, cam, compose(plat[k], Xc), 0.5, 5.0, device=device, rays=rays, st=st)
         c = _noisy(c, 5000 + seed * 977 + k, depth_noise, intensity_noise)
-        chans.append(quantize_fp16_t(c))
+        chans.append(quantize_fp16_t(c) if fp16_exact else c)
     init = perturb_poses(plat, sigma_t, math.radians(sigma_r_deg), 3000 + seed)
     pairs = []
     for i in range(n_frames):
@@ -1008,7 +1012,7 @@ def make_lidar_street_graph(n_frames: int = 500, width: int = 2048, height: int 
                             vfov_down_deg: float = -22.5, spacing: float = 1.0, seed: int = 4,
                             sigma_t: float = 0.10, sigma_r_deg: float = 0.5, drop: float = 0.05,
                             degree=(2, 20), window: int = 40, min_overlap: float = 0.3, device="cuda",
-                            params: Optional[Dict] = None) -> Workload:
+                            fp16_exact: bool = False, params: Optional[Dict] = None) -> Workload:
     """LiDAR 128 x 2048 sequence of n_frames along the synthetic street with an
     uneven overlap graph: frame i is the source of d_i pairs, d_i uniform in
     [2, 20], towards frames j != i within `window` frames whose overlap ratio
@@ -1028,7 +1032,8 @@ def make_lidar_street_graph(n_frames: int = 500, width: int = 2048, height: int 
     for k in range(n_frames):
         c = render_t(scene, sensor, poses[k], 1.0, 80.0, device=device, rays=rays, st=st)
         keep = torch.rand((height, width), generator=g, device=device) >= drop
-        chans.append(quantize_fp16_t(torch.where(keep[..., None], c, torch.zeros_like(c))))
+        c = torch.where(keep[..., None], c, torch.zeros_like(c))
+        chans.append(quantize_fp16_t(c) if fp16_exact else c)
     rng = np.random.default_rng(6000 + seed)
     pairs = []
     for i in range(n_frames):
@@ -1060,7 +1065,7 @@ def make_joint_hall(n_lidar: int = 300, lidar_width: int = 1024, lidar_height: i
                     cam_height: int = 480, f: float = 525.0, rate: int = 2, cam_offset=(0.10, 0.0, 0.10),
                     offset_error_m: float = 0.02, offset_error_deg: float = 0.5, seed: int = 5,
                     sigma_t: float = 0.02, sigma_r_deg: float = 1.0, tilt_deg: float = 10.0, device="cuda",
-                    params: Optional[Dict] = None) -> Workload:
+                    fp16_exact: bool = False, params: Optional[Dict] = None) -> Workload:
     """Joint LiDAR + RGB-D platform in the hall (Sec. V, fusion): n_lidar LiDAR
     frames (128 x 1024, vfov +-45 deg, the platform origin) and rate x n_lidar
     camera frames (640 x 480, `cam_offset` ahead / above, looking forward)
@@ -1087,10 +1092,10 @@ def make_joint_hall(n_lidar: int = 300, lidar_width: int = 1024, lidar_height: i
     plat = _hall_path(n_cam, 2000 + seed, height=1.5, tilt_deg=tilt_deg)
     rays_c = torch.as_tensor(_pixel_rays(cam)[0].reshape(-1, 3), dtype=torch.float64, device=device)
     rays_l = torch.as_tensor(_pixel_rays(lidar)[0].reshape(-1, 3), dtype=torch.float64, device=device)
-    chans = [quantize_fp16_t(render_t(scene, cam, compose(plat[k], Xc), 0.5, 5.0, device, rays_c, st))
-             for k in range(n_cam)]
-    chans += [quantize_fp16_t(render_t(scene, lidar, plat[rate * k], 0.5, 12.0, device, rays_l, st))
-              for k in range(n_lidar)]
+    chans = [render_t(scene, cam, compose(plat[k], Xc), 0.5, 5.0, device, rays_c, st) for k in range(n_cam)]
+    chans += [render_t(scene, lidar, plat[rate * k], 0.5, 12.0, device, rays_l, st) for k in range(n_lidar)]
+    if fp16_exact:
+        chans = [quantize_fp16_t(c) for c in chans]
     rng = np.random.default_rng(4000 + seed)
     ax = rng.normal(size=3)
     d = rng.normal(size=3)
@@ -1126,7 +1131,7 @@ def make_joint_hall(n_lidar: int = 300, lidar_width: int = 1024, lidar_height: i
 
 
 def make_street_batch(n_problems: int = 16, sizes=(50, 400), width: int = 1024, height: int = 64, seed: int = 6,
-                      device="cuda", params: Optional[Dict] = None):
+                      device="cuda", fp16_exact: bool = False, params: Optional[Dict] = None):
     """n_problems independent LiDAR street problems (sizes drawn uniformly in
     `sizes`, seed 3005 + seed) concatenated into one workload: frames of
     problem k follow those of problem k - 1, pairs stay within a problem
@@ -1150,7 +1155,8 @@ def make_street_batch(n_problems: int = 16, sizes=(50, 400), width: int = 1024, 
         for f in range(n):
             c = render_t(scene, sensor, P[f], 1.0, 80.0, device, rays, st)
             keep = torch.rand((height, width), generator=g, device=device) >= 0.05
-            chans.append(quantize_fp16_t(torch.where(keep[..., None], c, torch.zeros_like(c))))
+            c = torch.where(keep[..., None], c, torch.zeros_like(c))
+            chans.append(quantize_fp16_t(c) if fp16_exact else c)
         for i in range(n):
             near = list(range(i + 1, min(n, i + 4)))
             ratios = overlap_ratios_t(chans[base + i], [chans[base + j] for j in near], sensor, P[i], P[near], rays)

@@ -50,6 +50,7 @@ PIN_TOL = {
     "relative_jacobian": 1e-12,
     "hessian_zero_residual": 1e-6,
     "huber_hessian": 1e-5,
+    "half_rounding": 0.5,
 }
 
 
@@ -829,9 +830,15 @@ def _bf_residuals(s, params, src, tgt, Xi, Xj, pix):
     dt = tgt64[..., 1]
     valid_px = (dt > 0) & (dt >= params["range_min"]) & (dt <= params["range_max"]) & (n2 > 0.25)
     img = tgt64
+    if params.get("texel_f16", 0):
+        # R25: sampled intensity and normals are the binary16 values (numpy's IEEE conversion);
+        # validity stays with the float32 channels
+        img = tgt64.copy()
+        for c in (0, 2, 3, 4):
+            img[..., c] = tgt[..., c].astype(np.float16).astype(np.float64)
     if s.model == 1:  # wrap columns: three copies side by side, u shifted into the middle one
         valid_px = np.concatenate([valid_px] * 3, axis=1)
-        img = np.concatenate([tgt64] * 3, axis=1)
+        img = np.concatenate([img] * 3, axis=1)
     usable = np.zeros_like(valid_px)
     usable[1:-1, 1:-1] = (valid_px[1:-1, 1:-1] & valid_px[:-2, 1:-1] & valid_px[2:, 1:-1]
                           & valid_px[1:-1, :-2] & valid_px[1:-1, 2:])
@@ -912,7 +919,8 @@ def pin_residual_brute_force(O, lib, room, street, stride=3):
     reasons = np.zeros(7, dtype=np.int64)
     worst = 0.0
     for w, over in ((room, {}), (street, {}), (_with_offset(room), {}),
-                    (_flipped_normal_columns(room), dict(z_min=2.0))):
+                    (_flipped_normal_columns(room), dict(z_min=2.0)), (room, dict(texel_f16=1)),
+                    (street, dict(texel_f16=1))):
         worst = max(worst, _residual_case(O, lib, w, dict(w.params, **base, **over), reasons, stride))
     # valid, depth limit, window, not usable, occlusion, target normal, Huber's linear branch
     assert reasons[0] > 100 and np.all(reasons[1:] > 0), reasons
@@ -952,6 +960,31 @@ def pin_relative_jacobian(O, lib, w, stride=7):
             worst = max(worst, float(np.abs(r["Jj"] - r["Ji"] @ T).max() / max(np.abs(r["Jj"]).max(), 1e-30)))
     assert used > 100
     return worst
+
+
+# ------------------------------------------- binary16 texel values (R25)
+
+def pin_half_rounding(O, lib, n=20000, seed=9):
+    """The oracle's binary16 rounding against numpy's IEEE conversion to
+    float16 (round to nearest, ties to even): random values over the normal
+    and subnormal ranges, exact midpoints between neighbouring binary16
+    numbers (ties), values around the largest finite number and the overflow
+    threshold, signed zeros.  Returns the number of mismatches."""
+    rng = np.random.default_rng(seed)
+    normal = rng.uniform(-2.0, 2.0, n).astype(np.float32)
+    tiny = (rng.uniform(-1.0, 1.0, n) * 2.0 ** rng.integers(-26, -12, n)).astype(np.float32)
+    h = rng.uniform(-1000.0, 1000.0, n).astype(np.float16)
+    up = np.nextafter(h, np.float16(np.inf))
+    ties = ((h.astype(np.float64) + up.astype(np.float64)) / 2).astype(np.float32)  # exact in float32
+    edge = np.array([65504.0, 65519.0, 65520.0, 65535.0, -65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26,
+                     2.0 ** -14, 0.0, -0.0, 1.0, 0.5, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11], dtype=np.float32)
+    x = np.concatenate([normal, tiny, ties, edge])
+    assert np.count_nonzero(ties.astype(np.float16) == h) > n // 4  # half of the ties go down, to the even one
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).astype(np.float64)
+    got = O.half_round(x, lib=lib)
+    bad = ~((got == ref) | (np.isinf(got) & np.isinf(ref) & (np.sign(got) == np.sign(ref))))
+    return int(np.count_nonzero(bad))
 
 
 # ---------------------------------------------- the weights of H (Sec. IV-C)
@@ -1158,6 +1191,7 @@ def all_pins(O, lib, room, street):
         "relative_jacobian": max(pin_relative_jacobian(O, lib, room), pin_relative_jacobian(O, lib, street),
                                  pin_relative_jacobian(O, lib, _with_offset(room))),
         "hessian_zero_residual": pin_hessian_zero_residual(O, lib),
+        "half_rounding": pin_half_rounding(O, lib),
         "huber_hessian": max(pin_huber_hessian(O, lib, room), pin_huber_hessian(O, lib, street)),
     }
 

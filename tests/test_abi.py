@@ -58,7 +58,7 @@ def test_struct_layouts_match_the_header():
     # sizes implied by include/pba.h on LP64 (4 x int32 + 16 doubles, ...)
     assert ctypes.sizeof(_lib.PbaSensor) == 16 + 8 * 16
     assert ctypes.sizeof(_lib.PbaConfig) == 8 + 8 + 8 + 9 * 8 + 16
-    assert ctypes.sizeof(_lib.PbaIterStats) == 4 * 8 + 8 + 8
+    assert ctypes.sizeof(_lib.PbaIterStats) == 4 * 8 + 8 + 8 + 2 * 8
 
 
 def _config(_lib, sensors, n_frames=2, frame_sensor=None, **over):
@@ -147,7 +147,8 @@ int main(void) {
     if (pba_create(&cfg, NULL, &p) != PBA_EINVAL || p != NULL) return 3;
     if (pba_set_lambda(NULL, 1.0) != PBA_EINVAL) return 4;
     pba_destroy(NULL);
-    printf("%d %d %s\n", (int)sizeof(pba_sensor), (int)sizeof(pba_config), pba_last_error(NULL));
+    printf("%d %d %d %s\n", (int)sizeof(pba_sensor), (int)sizeof(pba_config), (int)sizeof(pba_iter_stats),
+           pba_last_error(NULL));
     return 0;
 }
 """)
@@ -158,6 +159,6 @@ int main(void) {
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
-    size_s, size_c, msg = r.stdout.split(" ", 2)
-    assert (int(size_s), int(size_c)) == (16 + 8 * 16, 8 + 8 + 8 + 9 * 8 + 16)
+    size_s, size_c, size_i, msg = r.stdout.split(" ", 3)
+    assert (int(size_s), int(size_c), int(size_i)) == (16 + 8 * 16, 8 + 8 + 8 + 9 * 8 + 16, 4 * 8 + 8 + 8 + 2 * 8)
     assert msg.startswith("pba_create: n_frames")

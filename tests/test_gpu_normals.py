@@ -131,3 +131,37 @@ def test_estimate_normals_rejects_bad_arguments(room3):
     with pytest.raises(pba.PbaError) as e:
         q.estimate_normals(0, 1)
     assert e.value.code == pba._lib.PBA_ENOTREADY
+
+
+@pytest.mark.parametrize("which,scale,max_radius", [("room3", 6.0, 4), ("street3", 8.0, 4)])
+def test_linearisation_of_estimated_normals_matches_oracle(oracle_lib, which, scale, max_radius, request):
+    """Normal estimation feeding the hot path (Sec. IV-A then Sec. IV-C): the
+    GPU estimates normals from depth, rebuilds FP16 texels and points and
+    linearises; the oracle estimates its own normals in FP64, samples the
+    target's intensity and normals as binary16 values (R25) and linearises.
+    H, b to 1e-4 and the cost to 1e-5 (relative), the count within the
+    pixels whose normal decision lies inside the oracle's margin + 2.  Pixels
+    whose plane is not determined to float32 accuracy (tol > 0.05 in
+    compare_frame) keep different normals on the two sides; their share of
+    the residuals is what separates the two sums."""
+    import paper_2303_16878_gb300 as pba
+    w = request.getfixturevalue(which)
+    p, got = estimate_on_gpu(w, list(range(w.n_frames)), scale, max_radius)
+    cost, count = p.linearize()
+    H, b = p.get_system()
+    chans, near = [], 0
+    for k in range(w.n_frames):
+        s = w.sensors[int(w.frame_sensor[k])]
+        ref = oracle_lib.estimate_normals(s, w.channels[k], scale, max_radius, params=w.params)
+        c = w.channels[k].copy()
+        c[..., 2:5] = ref["normals"].astype(np.float32)
+        chans.append(c)
+        near += int(np.count_nonzero(ref["margin"]))
+    o = oracle_lib.linearize(w.sensors, w.frame_sensor, chans, w.poses_init, w.pairs,
+                             dict(w.params, texel_f16=1))
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))
+    assert abs(count - o["count"]) <= near + 2, (count, o["count"], near)
+    assert rel(H, o["H"]) <= 1e-4, rel(H, o["H"])
+    assert rel(b, o["b"]) <= 1e-4, rel(b, o["b"])
+    assert abs(cost - o["cost"]) <= 1e-5 * o["cost"], (cost, o["cost"])
+    p.close()

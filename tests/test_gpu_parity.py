@@ -18,6 +18,13 @@ TOL_B = 1e-4
 TOL_COST = 1e-5
 
 
+def oprm(params, texel):
+    """The oracle's parameters for a GPU run with texel precision `texel`:
+    FP16 texels sample the target's intensity and normals as binary16 values
+    (reading R25), which the oracle evaluates exactly when asked."""
+    return dict(params, texel_f16=int(texel == 1))
+
+
 def rel(a, b):
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
@@ -51,7 +58,7 @@ def _path(name):
 @pytest.mark.parametrize("which", ["room8", "street3", "room8x"])
 def test_system_matches_oracle(oracle_lib, which, path, texel, grad_mode, request):
     w = request.getfixturevalue(which)
-    params = dict(w.params, grad_mode=grad_mode)
+    params = oprm(dict(w.params, grad_mode=grad_mode), texel if path == "batched" else 0)
     ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, params,
                                want_pairs=True)
     p = make(w, _path(path), texel, params={"grad_mode": grad_mode})
@@ -78,8 +85,8 @@ def test_valid_mask_bit_exact_outside_decision_margin(oracle_lib, which, texel, 
     p.linearize()
     total, disagree = 0, 0
     for q, (i, j) in enumerate(w.pairs.tolist()):
-        r = oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], w.poses_init[i],
-                                      w.poses_init[j])
+        r = oracle_lib.linearize_pair(w.sensors[0], oprm(w.params, texel), w.channels[i], w.channels[j],
+                                      w.poses_init[i], w.poses_init[j])
         assert p.frame_points(i) == r["n_points"]
         m = p.get_mask(q, r["n_points"])
         diff = m ^ r["mask"]
@@ -106,8 +113,8 @@ def test_full_size_lidar_street_sampled_pairs(oracle_lib):
     sample = rng.choice(len(w.pairs), size=8, replace=False)
     for q in sample:
         i, j = w.pairs[q]
-        r = oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], w.poses_init[i],
-                                      w.poses_init[j])
+        r = oracle_lib.linearize_pair(w.sensors[0], oprm(w.params, 1), w.channels[i], w.channels[j],
+                                      w.poses_init[i], w.poses_init[j])
         assert abs(ps["count"][q] - r["count"]) <= 2
         assert abs(ps["cost"][q] - r["cost"]) <= 1e-4 * r["cost"] + 1e-9
         assert rel(ps["H"][q], r["H"]) <= TOL_H
@@ -127,11 +134,12 @@ def test_damped_step_matches_oracle(oracle_lib, room8, solver):
     FP32-factorisation + FP64-refinement solver)."""
     import paper_2303_16878_gb300 as pba
     w = room8
-    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
+    prm = oprm(w.params, 1)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, prm)
     lam = 10.0 * float(np.diag(ref["H"])[6:].max())
     dx, ok = oracle_lib.solve_step(ref["H"], ref["b"], lam)
     cand = oracle_lib.apply_update(w.poses_init, dx)
-    new = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, w.params, want_system=False)
+    new = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, cand, w.pairs, prm, want_system=False)
     assert ok and new["cost"] < ref["cost"]
     p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16, solver=solver)
     p.linearize()
@@ -193,7 +201,7 @@ def test_autotuned_variants_agree(oracle_lib, street3):
     (within float32 reordering) and matches the oracle."""
     import paper_2303_16878_gb300 as pba
     w = street3
-    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, w.params)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, 1))
     p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
     p.linearize()
     H0, b0 = p.get_system()
@@ -261,11 +269,13 @@ def test_plain_and_batched_agree(room8):
 # ------------------------------------------------------------------ edge cases
 
 def test_self_pair_and_empty_frames(oracle_lib):
-    """A self pair (i, i) at equal poses gives zero error; a frame without a
-    single valid pixel yields no residuals and zero blocks; a pair that sees
-    nothing of its target contributes nothing.  In the self pair every point
-    lands exactly on a pixel centre, i.e. on a floor() tie, so its valid set
-    may differ from the oracle's on points the oracle flags."""
+    """A self pair (i, i) at equal poses gives zero error (with FP16 texels the
+    error of sampling the binary16 target values, R25: the oracle's cost); a
+    frame without a single valid pixel yields no residuals and zero blocks; a
+    pair that sees nothing of its target contributes nothing.  In the self
+    pair every point lands exactly on a pixel centre, i.e. on a floor() tie,
+    so its valid set may differ from the oracle's on points the oracle
+    flags."""
     import paper_2303_16878_gb300 as pba
     from paper_2303_16878_gb300 import synth
     base = workload("room", n_frames=3)
@@ -275,9 +285,9 @@ def test_self_pair_and_empty_frames(oracle_lib):
     far[1][:, 3] += np.array([0.0, 0.0, -50.0])  # frame 1 far away: nothing projects into frame 0
     pairs = np.array([[0, 0], [2, 0], [0, 2], [1, 0], [0, 1]], dtype=np.int32)
     w = synth.Workload("edge", base.sensors, base.frame_sensor, chans, base.poses_gt, far, pairs, base.params)
-    refs = [oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], far[i], far[j])
-            for i, j in pairs.tolist()]
     for texel in (0, 1):
+        refs = [oracle_lib.linearize_pair(w.sensors[0], oprm(w.params, texel), w.channels[i], w.channels[j],
+                                          far[i], far[j]) for i, j in pairs.tolist()]
         p = make(w, pba.PBA_PATH_BATCHED, texel)
         assert p.frame_points(2) == 0
         cost, count = p.linearize()
@@ -285,7 +295,11 @@ def test_self_pair_and_empty_frames(oracle_lib):
         for q, r in enumerate(refs):
             flagged = int(sum(bin(int(x)).count("1") for x in r["flags"]))
             assert abs(ps["count"][q] - r["count"]) <= flagged + 2, q
-        assert ps["count"][0] > 0.9 * p.frame_points(0) and ps["cost"][0] < 1e-6
+        assert ps["count"][0] > 0.9 * p.frame_points(0)
+        if texel == 0:
+            assert ps["cost"][0] < 1e-6
+        else:  # e = g - binary16(g), n - binary16(n) at the pixel itself
+            assert 0 < refs[0]["cost"] < 1e-2 and abs(ps["cost"][0] - refs[0]["cost"]) <= 1e-3 * refs[0]["cost"]
         assert np.abs(ps["b"][0]).max() < 1e-3 * np.abs(ps["H"][0]).max() ** 0.5
         assert ps["count"][1] == 0 and ps["count"][2] == 0 and np.all(ps["H"][1] == 0) and np.all(ps["H"][2] == 0)
         for q in (3, 4):
@@ -330,4 +344,66 @@ def test_invalid_arguments_fail_loudly():
     with pytest.raises(pba.PbaError) as e:
         p.set_pairs([[0, 7]])
     assert e.value.code == pba._lib.PBA_EINVAL
+    p.close()
+
+
+def test_nonfinite_inputs_are_counted_in_the_status_word(oracle_lib):
+    """The status word of a linearisation.  A NaN pose: every pair that
+    touches the frame has a non-finite relative pose, yields no residual and
+    is counted; the other pairs equal the oracle's.  NaN intensities at valid
+    pixels of a source frame: those residuals are left out of H, b and F and
+    counted; the rest of the system equals the oracle's with those pixels
+    removed (frame 0 is the target of no pair, so only its points change)."""
+    import paper_2303_16878_gb300 as pba
+    from paper_2303_16878_gb300 import synth
+    w = workload("room", n_frames=4, width=80, height=60, f=60.0)
+    # a NaN pose
+    poses = w.poses_init.copy()
+    poses[3, 0, 3] = np.nan
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    p.set_poses(poses)
+    p.linearize()
+    st = p.solve_step(1.0)
+    touching = [q for q, (i, j) in enumerate(w.pairs.tolist()) if 3 in (i, j)]
+    assert st["nonfinite_pairs"] == len(touching) > 0 and st["n_nonfinite"] == 0 and st["status"] == 0
+    ps = p.get_pair_system()
+    assert np.all(ps["count"][touching] == 0)
+    for q, (i, j) in enumerate(w.pairs.tolist()):
+        if q in touching:
+            continue
+        r = oracle_lib.linearize_pair(w.sensors[0], w.params, w.channels[i], w.channels[j], poses[i], poses[j])
+        assert abs(ps["count"][q] - r["count"]) <= 2 and rel(ps["H"][q], r["H"]) <= TOL_H
+    p.close()
+    # NaN intensities at 60 valid pixels of frame 0
+    rng = np.random.default_rng(4)
+    chans = [c.copy() for c in w.channels]
+    valid = np.flatnonzero(chans[0][..., 1].reshape(-1) > 0)
+    bad = rng.choice(valid, size=60, replace=False)
+    chans[0].reshape(-1, 5)[bad, 0] = np.nan
+    wn = synth.Workload("nan", w.sensors, w.frame_sensor, chans, w.poses_gt, w.poses_init, w.pairs, w.params)
+    removed = [c.copy() for c in w.channels]
+    removed[0].reshape(-1, 5)[bad, 1] = 0.0
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, removed, w.poses_init, w.pairs, w.params)
+    # the points of the NaN pixels that the oracle takes as residuals (with their finite intensity)
+    pts, pix = oracle_lib.frame_points(w.sensors[0], w.params, w.channels[0])
+    at = {int(x): k for k, x in enumerate(pix)}
+    expect, flagged = 0, 0
+    for i, j in w.pairs.tolist():
+        if i != 0:
+            continue
+        for x in bad.tolist():
+            r = oracle_lib.point_residual(w.sensors[0], w.params, w.channels[j], w.poses_init[0], w.poses_init[j],
+                                          pts[at[x]])
+            expect += int(r["valid"])
+            flagged += int(r["flag"])
+    assert expect > 20
+    p = make(wn, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    cost, count = p.linearize()
+    st = p.solve_step(1.0)
+    assert abs(st["n_nonfinite"] - expect) <= flagged and st["nonfinite_pairs"] == 0
+    H, b = p.get_system()
+    assert np.all(np.isfinite(H)) and np.all(np.isfinite(b)) and np.isfinite(cost)
+    assert abs(count - ref["count"]) <= 1e-5 * ref["count"] + 2
+    assert rel(H, ref["H"]) <= TOL_H and rel(b, ref["b"]) <= TOL_B
+    assert abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
     p.close()

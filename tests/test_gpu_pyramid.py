@@ -45,22 +45,24 @@ def test_levels_are_bit_exact(oracle_lib, which, request):
         assert [q.frame_points(k) for k in range(w.n_frames)] == n_ref
 
 
+@pytest.mark.parametrize("texel", [0, 1])
 @pytest.mark.parametrize("which", ["room8", "street3"])
-def test_coarse_level_system_matches_oracle(oracle_lib, which, request):
+def test_coarse_level_system_matches_oracle(oracle_lib, which, texel, request):
     """H and b of the whole level to 1e-4; per pair, the valid masks agree on
     every point outside the oracle's decision margin, and pairs whose masks
     agree fully match the oracle's cost to 1e-5 and its count exactly (a
     point decided the other way inside the margin changes its pair's cost by
     that point's rho: such pairs are left out of the cost comparison).
-    FP32 texels: the coarse images are block means, not binary16 values, so
-    FP16 texels would round them (level 0 inputs are binary16-exact)."""
+    Both texel precisions; with FP16 texels the oracle samples the coarse
+    target's intensity and normals as binary16 values (R25)."""
     w = request.getfixturevalue(which)
-    p = gpu_problem(w, texel=0)
+    p = gpu_problem(w, texel=texel)
     p.build_pyramid(3)
     ref_levels = oracle_lib.pyramid(w, 3)
+    prm = dict(w.params, texel_f16=texel)
     for lv in (1, 2):
         sens, chans = ref_levels[lv]
-        ref = oracle_lib.linearize(sens, w.frame_sensor, chans, w.poses_init, w.pairs, w.params)
+        ref = oracle_lib.linearize(sens, w.frame_sensor, chans, w.poses_init, w.pairs, prm)
         q = p.level(lv)
         q.set_mask_export(True)
         cost, count = q.linearize()
@@ -70,7 +72,7 @@ def test_coarse_level_system_matches_oracle(oracle_lib, which, request):
         total, disagree, compared = 0, 0, 0
         for k, (i, j) in enumerate(w.pairs.tolist()):
             s = sens[int(w.frame_sensor[i])]
-            r = oracle_lib.linearize_pair(s, w.params, chans[i], chans[j], w.poses_init[i], w.poses_init[j])
+            r = oracle_lib.linearize_pair(s, prm, chans[i], chans[j], w.poses_init[i], w.poses_init[j])
             diff = q.get_mask(k, r["n_points"]) ^ r["mask"]
             assert not np.any(diff & ~r["flags"]), f"level {lv} pair {k}: mask differs on unflagged points"
             nd = int(sum(bin(int(x)).count("1") for x in diff))
@@ -98,22 +100,23 @@ def _pose_diff(A, B):
 
 @pytest.mark.parametrize("solver,texel", [(0, 0), (1, 1)])
 def test_coarse_to_fine_matches_oracle(oracle_lib, solver, texel):
-    """Final poses within 1e-4 m / 1e-5 rad of the oracle's; with FP32 texels
-    the first cost of the coarsest level (same initial poses) also to 1e-5.
-    The levels' accept / reject sequences may differ where a step's decrease
-    is within float32 rounding, so only the converged finest level is
-    compared."""
+    """Final poses within 1e-4 m / 1e-5 rad of the oracle's, and the first
+    cost of the coarsest level (same initial poses) to 1e-5 (with FP16
+    texels against the oracle's binary16 sampling, R25).  The levels' accept
+    / reject sequences may differ where a step's decrease is within float32
+    rounding, so only the converged finest level is compared."""
+    import dataclasses
     w = workload("room", n_frames=4, width=160, height=120, f=120.0)
     iters = [10, 5, 10]
-    ref = oracle_lib.coarse_to_fine(w, w.poses_init, 3, iters, 1e-7)
+    wo = dataclasses.replace(w, params=dict(w.params, texel_f16=texel))
+    ref = oracle_lib.coarse_to_fine(wo, w.poses_init, 3, iters, 1e-7)
     p = gpu_problem(w, solver=solver, texel=texel)
     p.build_pyramid(3)
     log = p.optimize(iters, rel_tol=1e-7)
     assert [lv["level"] for lv in log] == [2, 1, 0]
     for lv in log:
         assert lv["iterations"] <= iters[2 - lv["level"]] and lv["cost_last"] <= lv["cost_first"]
-    if texel == 0:
-        assert abs(log[0]["cost_first"] - ref["log"][0]["cost_first"]) <= 1e-5 * ref["log"][0]["cost_first"]
+    assert abs(log[0]["cost_first"] - ref["log"][0]["cost_first"]) <= 1e-5 * ref["log"][0]["cost_first"]
     dt, dr = _pose_diff(p.get_poses(), ref["poses"])
     assert dt <= 1e-4 and dr <= 1e-5, (dt, dr)
 

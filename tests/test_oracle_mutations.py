@@ -13,8 +13,8 @@ MUTATIONS = {
                                     "acc += M[3 * r + k] * (2.0 * Spu[3 * k + c]);"),
     "target_translation_jacobian_sign": ("dPj[6 * r + c] = -RoT[3 * r + c];", "dPj[6 * r + c] = RoT[3 * r + c];"),
     "normal_cue_uses_Rj_not_RjT": ("mat3_vec(RjT, Rn, RjTRn);", "mat3_vec(Rj, Rn, RjTRn);"),
-    "image_gradient_axes_swapped": ("gu[ci] += w[t] * 0.5 * ((double)Ir[ci] - (double)Il[ci]);",
-                                    "gu[ci] += w[t] * 0.5 * ((double)Id[ci] - (double)Iu[ci]);"),
+    "image_gradient_axes_swapped": ("gu[ci] += w[t] * 0.5 * (tval(prm, Ir, ci) - tval(prm, Il, ci));",
+                                    "gu[ci] += w[t] * 0.5 * (tval(prm, Id, ci) - tval(prm, Iu, ci));"),
     "huber_weight_dropped": ("*w = prm->huber_delta / chi;", "*w = 1.0;"),
     "omega_dropped_from_b": ("s_b += J[r][a] * om[r] * e[r];", "s_b += J[r][a] * e[r];"),
     "depth_cue_jacobian_dropped": ("map_i += dz[k] * dPi[6 * k + col];", "map_i += 0.0 * dPi[6 * k + col];"),
@@ -49,6 +49,13 @@ MUTATIONS = {
     "huber_weight_dropped_from_H": ("H12[12 * a + c] += w * s_h;", "H12[12 * a + c] += s_h;"),
     "huber_weight_squared_in_H": ("H12[12 * a + c] += w * s_h;", "H12[12 * a + c] += w * w * s_h;"),
     "H_block_rows_and_columns_mixed": ("s_h += J[r][a] * om[r] * J[r][c];", "s_h += J[r][a] * om[r] * J[r][11 - c];"),
+    "half_rounding_truncates": ("double r = ldexp(nearbyint(ldexp(v, -q)), q);", "double r = ldexp(trunc(ldexp(v, -q)), q);"),
+    "half_ten_significant_bits": ("int q = e - 11;", "int q = e - 10;"),
+    "half_subnormal_spacing": ("if (q < -24) q = -24;", "if (q < -25) q = -25;"),
+    "half_texels_ignored": ("return (prm->texel_f16 && ci != 1) ? o_half(I[ci]) : (double)I[ci];",
+                            "return (double)I[ci];"),
+    "half_texel_depth_rounded": ("return (prm->texel_f16 && ci != 1) ? o_half(I[ci]) : (double)I[ci];",
+                                 "return prm->texel_f16 ? o_half(I[ci]) : (double)I[ci];"),
     "range_cue_horizontal_only": ("zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1] + pb[2] * pb[2]);",
                                   "zd = sqrt(pb[0] * pb[0] + pb[1] * pb[1]);"),
 }
@@ -83,6 +90,7 @@ def test_planted_mistake_is_caught(name, tmp_path, oracle_lib, room3, street3):
                     ("relative_jacobian", lambda: max(P.pin_relative_jacobian(oracle_lib, lib, room3),
                                                       P.pin_relative_jacobian(oracle_lib, lib, street3))),
                     ("hessian_zero_residual", lambda: P.pin_hessian_zero_residual(oracle_lib, lib)),
+                    ("half_rounding", lambda: P.pin_half_rounding(oracle_lib, lib)),
                     ("huber_hessian", lambda: max(P.pin_huber_hessian(oracle_lib, lib, room3),
                                                   P.pin_huber_hessian(oracle_lib, lib, street3)))]:
         try:

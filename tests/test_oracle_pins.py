@@ -255,3 +255,8 @@ def test_huber_weight_of_the_normal_equations(oracle_lib, which, request):
     Jacobians and the brute-force chi, on both sides of delta."""
     w = request.getfixturevalue(which)
     assert P.pin_huber_hessian(oracle_lib, oracle_lib.load(), w) < P.PIN_TOL["huber_hessian"]
+
+
+def test_binary16_rounding_of_texel_values(oracle_lib):
+    """R25's rounding against numpy's IEEE float16 conversion (ties to even, subnormals, overflow)."""
+    assert P.pin_half_rounding(oracle_lib, oracle_lib.load()) < P.PIN_TOL["half_rounding"]

@@ -44,8 +44,8 @@ def test_torch_overlap_ratios_match_numpy():
 def test_lidar_street_follows_its_recipe():
     """The benchmark input is what the design notes state: 50 spherical frames
     of 64 x 1024 over +-16.6 deg (f_x = -W / 2 pi, c_x = W / 2), ranges in
-    [1, 80] m, unit normals, intensity in [0, 1], intensity and normals exact
-    in binary16, 5 % of returns dropped (measured on the lower rows, which see
+    [1, 80] m, unit normals, intensity in [0, 1], full float32 channels (not
+    narrowed to binary16), 5 % of returns dropped (measured on the lower rows, which see
     the ground within range), poses 1 m apart, 10 cm / 0.5 deg initial noise,
     1170 pairs i < j within 40 m."""
     import math
@@ -59,8 +59,8 @@ def test_lidar_street_follows_its_recipe():
     assert d[d > 0].min() >= 1.0 and d[d > 0].max() <= 80.0
     assert np.abs(np.linalg.norm(C[..., 2:5], axis=-1)[d > 0] - 1.0).max() < 1e-3
     assert C[..., 0].min() >= 0.0 and C[..., 0].max() <= 1.0
-    g16 = C[..., [0, 2, 3, 4]]
-    assert np.array_equal(g16, g16.astype(np.float16).astype(np.float32))
+    g16 = C[..., [0, 2, 3, 4]][d > 0]
+    assert np.mean(g16 != g16.astype(np.float16).astype(np.float32)) > 0.5
     assert 0.045 < (d[:, 48:, :] <= 0).mean() < 0.055
     s = w.sensors[0]
     assert math.isclose(s.fx, -1024 / (2 * math.pi)) and s.cx == 512.0
