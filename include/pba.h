@@ -122,6 +122,13 @@ typedef struct {
     int64_t n_valid;    /* residuals (valid pixel-points over all pairs) linearised */
     int32_t accepted;   /* 1 when new_cost < cost and the poses were updated */
     int32_t status;     /* PBA_OK, or PBA_ENOTPD when the Cholesky met a non-positive pivot */
+    /* status word of the same linearisation as n_valid (batched path; 0 on the
+     * plain path): residuals left out of H, b and F because their value was
+     * not finite (a NaN or infinite intensity or normal), and pairs whose
+     * relative pose X_j^-1 X_i was not finite (a NaN or infinite pose; such a
+     * pair yields no residual) */
+    int64_t n_nonfinite;
+    int64_t nonfinite_pairs;
 } pba_iter_stats;
 
 /* Create a problem on the current CUDA device.  cuda_stream is a
@@ -224,6 +231,19 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m);
 int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double min_ratio, int sequential,
                     int32_t* pairs_out, float* ratio_out, int cap, int32_t* m_out);
 
+/* The gradient of F in the box-plus chart of the Supp. (X [+] dx =
+ * [R R(dq), R dt + t], dx = [dt, dq]) from matrix gradients: for each of n
+ * 3x4 transforms X_k (row-major [R | t]) and G_k = dF/dX_k (as
+ * pba_cost_gradient returns them), g_k = dF/d dx_k at dx = 0:
+ *   g_k[0..2] = R^T G_t,  g_k[3..5] = 2 (W_zy - W_yz, W_xz - W_zx, W_yx - W_xy),
+ *   W = R^T G_R  (R(dq) = I + 2 [dq]x to first order).
+ * X, G: n x 12 doubles, g: n x 6 doubles, device buffers of the problem's
+ * device (caller-owned; G may be the d_poses of pba_cost_gradient, X the
+ * poses it was evaluated at).  Enqueued on the problem's stream;
+ * synchronises.  Errors: PBA_EINVAL (p NULL, n < 0, a NULL buffer with
+ * n > 0), PBA_ECUDA. */
+int pba_tangent_gradient(pba_problem* p, const double* X, const double* G, int n, double* g);
+
 /* Linearise all pairs at the current poses: builds H (6N x 6N, gauge not
  * fixed) and b (6N) on the device and returns the total cost F (Eq. total-error-multicue) and
  * the number of valid residuals; synchronises.  Either output may be NULL.
@@ -237,8 +257,8 @@ int pba_linearize(pba_problem* p, double* cost, int64_t* n_valid);
  * occlusion, Huber branch) held fixed:
  *   d_poses     N x 12 doubles: dF/dX_k, the derivative with respect to the
  *               entries of each 3x4 pose [R_k | t_k] (F evaluated with the
- *               paper's formulas for any 3x4 matrices; the se(3) gradient in
- *               the box-plus chart is [R^T g_t, 2 vex-type pairs of R^T G_R]);
+ *               paper's formulas for any 3x4 matrices; pba_tangent_gradient
+ *               turns it into the gradient in the box-plus chart);
  *   d_extrinsic S x 12 doubles: dF/dX_o per sensor, likewise;
  *   d_channels  one float per channel of every uploaded pixel (the layout of
  *               pba_upload_frames, frames back to back): dF/d(g, d, n) through

@@ -28,7 +28,8 @@ def _is_torch(x) -> bool:
 
 def _stats(s: _lib.PbaIterStats) -> Dict:
     return dict(cost=s.cost, new_cost=s.new_cost, lambda_used=s.lambda_used, lambda_next=s.lambda_next,
-                n_valid=int(s.n_valid), accepted=bool(s.accepted), status=int(s.status))
+                n_valid=int(s.n_valid), accepted=bool(s.accepted), status=int(s.status),
+                n_nonfinite=int(s.n_nonfinite), nonfinite_pairs=int(s.nonfinite_pairs))
 
 
 class Problem:
@@ -306,6 +307,23 @@ class Problem:
         self._check(self._lib.pba_cost_gradient(self._h, ctypes.byref(cost), ctypes.byref(n), ptr(dP), ptr(dE),
                                                 ptr(dI)), "cost_gradient")
         return cost.value, n.value, dP, dE, dI
+
+    def tangent_gradient(self, X, G):
+        """dF/d dx in the box-plus chart (pba_tangent_gradient) from matrix
+        gradients G = dF/dX at the 3x4 transforms X: CUDA tensors (..., 3, 4)
+        -> float64 CUDA tensor (..., 6)."""
+        import torch
+        Xc = torch.as_tensor(X, dtype=torch.float64).contiguous()
+        Gc = torch.as_tensor(G, dtype=torch.float64, device=Xc.device).contiguous()
+        if Xc.shape != Gc.shape or Xc.shape[-2:] != (3, 4) or not Xc.is_cuda:
+            raise ValueError("tangent_gradient: X and G must be CUDA tensors of equal shape (..., 3, 4)")
+        n = Xc.numel() // 12
+        g = torch.empty(Xc.shape[:-2] + (6,), dtype=torch.float64, device=Xc.device)
+        torch.cuda.current_stream(Xc.device).synchronize()  # X, G written on torch's stream; the library uses its own
+        self._check(self._lib.pba_tangent_gradient(self._h, ctypes.c_void_p(Xc.data_ptr()),
+                                                   ctypes.c_void_p(Gc.data_ptr()), int(n),
+                                                   ctypes.c_void_p(g.data_ptr())), "tangent_gradient")
+        return g
 
     def get_system(self):
         n6 = 6 * self.n_frames

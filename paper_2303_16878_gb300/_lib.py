@@ -43,7 +43,7 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
-           "pba_set_extrinsic", "pba_cost_gradient", "pba_estimate_normals", "pba_get_channels",
+           "pba_set_extrinsic", "pba_cost_gradient", "pba_tangent_gradient", "pba_estimate_normals", "pba_get_channels",
            "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
            "pba_set_variants", "pba_refine_extrinsic",
            "pba_get_extrinsic", "pba_set_offset_free"]
@@ -73,7 +73,7 @@ class PbaConfig(ctypes.Structure):
 class PbaIterStats(ctypes.Structure):
     _fields_ = [("cost", ctypes.c_double), ("new_cost", ctypes.c_double), ("lambda_used", ctypes.c_double),
                 ("lambda_next", ctypes.c_double), ("n_valid", ctypes.c_int64), ("accepted", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("n_nonfinite", ctypes.c_int64), ("nonfinite_pairs", ctypes.c_int64)]
 
 
 class PbaLevelStats(ctypes.Structure):
@@ -140,6 +140,7 @@ def load(build_if_missing: bool = True):
             "pba_pyramid_level": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
             "pba_optimize": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_double, P(PbaLevelStats)], ctypes.c_int),
             "pba_cost_gradient": ([vp, P(d), P(i64), vp, vp, vp], ctypes.c_int),
+            "pba_tangent_gradient": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
             "pba_linearize_pairs_noalloc": ([P(PbaSensor), P(PbaConfig), vp, ctypes.c_int, vp, vp, ctypes.c_int, vp,
                                              vp], ctypes.c_int),
         }

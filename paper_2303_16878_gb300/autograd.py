@@ -49,14 +49,8 @@ def photometric_cost(problem, poses, extrinsics, channels):
     return PhotometricCost.apply(poses, extrinsics, channels, problem)
 
 
-def tangent_gradient(poses, dposes):
-    """dF/d dx_k in the box-plus chart X [+] dx = [R R(dq), R dt + t] from the
-    matrix gradient G = dF/dX: dt part R^T G_t; dq part 2 (W_zy - W_yz,
-    W_xz - W_zx, W_yx - W_xy) with W = R^T G_R (R(dq) ~ I + 2 [dq]x)."""
-    R = poses[..., :3]
-    GR, Gt = dposes[..., :3], dposes[..., 3]
-    gt = torch.einsum("...ji,...j->...i", R, Gt)
-    Wm = torch.einsum("...ji,...jk->...ik", R, GR)
-    gq = 2.0 * torch.stack([Wm[..., 2, 1] - Wm[..., 1, 2], Wm[..., 0, 2] - Wm[..., 2, 0],
-                            Wm[..., 1, 0] - Wm[..., 0, 1]], dim=-1)
-    return torch.cat([gt, gq], dim=-1)
+def tangent_gradient(problem, poses, dposes):
+    """dF/d dx_k in the box-plus chart of the Supp. from the matrix gradient
+    dF/dX_k at the poses X_k: the library's pba_tangent_gradient on the
+    device ((N, 3, 4), (N, 3, 4) -> (N, 6))."""
+    return problem.tangent_gradient(poses, dposes)

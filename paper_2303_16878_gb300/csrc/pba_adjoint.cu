@@ -425,6 +425,43 @@ cudaError_t launch_adjoint(int texel_precision, const int4* chunks, int n_chunks
     return cudaGetLastError();
 }
 
+namespace {
+
+// dF/d dx in the box-plus chart of Supp. (X [+] dx = [R R(dq), R dt + t], R(dq)
+// from the unit quaternion with imaginary part dq, so R(dq) = I + 2 [dq]x to
+// first order) from the matrix gradient G = dF/dX of a 3x4 transform X:
+// d/d dt = R^T G_t and, with W = R^T G_R, d/d dq = 2 (W_zy - W_yz, W_xz - W_zx,
+// W_yx - W_xy) (the derivative of tr(G_R^T R 2 [dq]x)).  One thread per transform.
+__global__ void k_tangent(const double* __restrict__ X, const double* __restrict__ G, int n, double* __restrict__ g) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double* x = X + 12 * k;
+    const double* d = G + 12 * k;
+    double W[9];
+    for (int r = 0; r < 3; ++r) {
+        // (R^T G_t)_r and row r of R^T G_R: sums over the rows a of R and G
+        double t = 0.0;
+        for (int a = 0; a < 3; ++a) t += x[4 * a + r] * d[4 * a + 3];
+        g[6 * k + r] = t;
+        for (int c = 0; c < 3; ++c) {
+            double w = 0.0;
+            for (int a = 0; a < 3; ++a) w += x[4 * a + r] * d[4 * a + c];
+            W[3 * r + c] = w;
+        }
+    }
+    g[6 * k + 3] = 2.0 * (W[7] - W[5]);
+    g[6 * k + 4] = 2.0 * (W[2] - W[6]);
+    g[6 * k + 5] = 2.0 * (W[3] - W[1]);
+}
+
+}  // namespace
+
+cudaError_t launch_tangent(const double* X, const double* G, int n, double* g, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_tangent<<<(n + 127) / 128, 128, 0, s>>>(X, G, n, g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_reduce(const float* partials, const PairStatic* ps, const int2* pf, const double* poses,
                                   const double* pair_Xo, int m, double* pair_out, const AsmTask* tasks, int n_tasks,
                                   const AsmContrib* contrib, const int* frame_sensor, int n_sensors,

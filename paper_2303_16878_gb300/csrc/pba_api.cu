@@ -377,6 +377,8 @@ int read_stats(pba_problem* p, pba_iter_stats* stats) {
         stats->lambda_used = st.lambda_used;
         stats->lambda_next = st.lambda;
         stats->n_valid = st.iter_n_valid;
+        stats->n_nonfinite = st.iter_nf_res;
+        stats->nonfinite_pairs = st.iter_nf_pairs;
         stats->accepted = st.accepted;
         stats->status = st.status;
     }
@@ -1256,6 +1258,15 @@ int pba_cost_gradient(pba_problem* p, double* cost, int64_t* n_valid, double* d_
     CUDA_TRY(p, cudaStreamSynchronize(s));
     if (cost) *cost = tot[0];
     if (n_valid) *n_valid = (int64_t)tot[1];
+    return PBA_OK;
+}
+
+int pba_tangent_gradient(pba_problem* p, const double* X, const double* G, int n, double* g) {
+    if (!p || n < 0 || (n > 0 && (!X || !G || !g))) return fail(p, PBA_EINVAL, "tangent_gradient: bad arguments");
+    if (n == 0) return PBA_OK;
+    cudaSetDevice(p->device);
+    CUDA_TRY(p, launch_tangent(X, G, n, g, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     return PBA_OK;
 }
 

@@ -12,8 +12,9 @@
 //             a = R_o^T (R_j^T (t_i - t_j) - t_o)   (Supp., pbar_u)
 //   chunk list int4 {pair, first point, count, 0}: the persistent launch's work queue
 //   partials  FP32 per chunk (one warp's work item): 21 (H6 upper) + 6 (b6) + cost + count
-//             (+3 pad) = 32 floats
-//   pair blocks FP64 per pair: H12 (144) + b12 (12) + cost + count (+2 pad) = 160 doubles
+//             + residuals left out as not finite (+2 pad) = 32 floats
+//   pair blocks FP64 per pair: H12 (144) + b12 (12) + cost + count + residuals left out as
+//             not finite + 1 when the pair's relative pose is not finite = 160 doubles
 //   H (6N x 6N) and b (6N) FP64 dense; A = H_ff + lambda I padded to a multiple of 32
 #pragma once
 
@@ -24,7 +25,7 @@
 namespace pba {
 
 constexpr int kPartialStride = 32;   // floats per chunk partial
-constexpr int kNumAcc = 29;          // 21 + 6 + cost + count
+constexpr int kNumAcc = 30;          // 21 + 6 + cost + count + non-finite residuals
 constexpr int kBlockStride = 160;    // doubles per pair block
 constexpr int kTile = 32;            // Cholesky tile
 constexpr double kRefineTol = 1e-10; // |r| <= kRefineTol |b'| ends the mixed-precision refinement
@@ -102,6 +103,10 @@ struct LmState {
     int pad;
     double iter_cost;       // F at the poses the last iteration started from
     long long iter_n_valid; // residuals linearised by the last iteration
+    // status word: residuals left out because their value is not finite, and pairs
+    // whose relative pose is not finite (current system, candidate, last iteration's)
+    long long nf_res, nf_res_new, iter_nf_res;
+    long long nf_pairs, nf_pairs_new, iter_nf_pairs;
 };
 
 // Assembly task: one 6x6 block of H (diagonal when a == b).
@@ -250,6 +255,8 @@ cudaError_t launch_adjoint(int texel_precision, const int4* chunks, int n_chunks
                            const PairPose* pp, const float4* pts_pg, const float4* pts_n, const int* pts_pix,
                            const void* texels, const SensorDev* sensors, const int* frame_sensor,
                            const LinParams& prm, float* partials, float* d_img, int grid, cudaStream_t s);
+// dF/d dx in the box-plus chart from dF/dX for n transforms (n x 12 -> n x 6).
+cudaError_t launch_tangent(const double* X, const double* G, int n, double* g, cudaStream_t s);
 cudaError_t launch_adjoint_reduce(const float* partials, const PairStatic* ps, const int2* pf, const double* poses,
                                   const double* pair_Xo, int m, double* pair_out, const AsmTask* tasks, int n_tasks,
                                   const AsmContrib* contrib, const int* frame_sensor, int n_sensors,

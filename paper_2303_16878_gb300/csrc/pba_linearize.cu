@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         const float umin = wrap ? -3.4e38f : 1.f;
         const float vmax = (float)(Hh - 2);
 
-        float Hacc[21], bacc[6], cost = 0.f, cnt = 0.f;
+        float Hacc[21], bacc[6], cost = 0.f, cnt = 0.f, nonfin = 0.f;
         if (FULL) {
 #pragma unroll
             for (int k = 0; k < 21; ++k) Hacc[k] = 0.f;
@@ -333,17 +333,24 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                         float chi2 = 0.f;
 #pragma unroll
                         for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
-                        float rho;
-                        if (chi2 <= prm.huber_delta2) {
-                            w = 1.f;
-                            rho = chi2;
+                        if (!(chi2 < INFINITY)) {
+                            // a NaN or infinite input value (intensity, normal): the residual is
+                            // left out of H, b and F and counted in the status word
+                            valid = false;
+                            nonfin += 1.f;
                         } else {
-                            const float chi = sqrtf(chi2);
-                            w = prm.huber_delta / chi;
-                            rho = fmaf(2.f * prm.huber_delta, chi, -prm.huber_delta2);
+                            float rho;
+                            if (chi2 <= prm.huber_delta2) {
+                                w = 1.f;
+                                rho = chi2;
+                            } else {
+                                const float chi = sqrtf(chi2);
+                                w = prm.huber_delta / chi;
+                                rho = fmaf(2.f * prm.huber_delta, chi, -prm.huber_delta2);
+                            }
+                            cost += rho;
+                            cnt += 1.f;
                         }
-                        cost += rho;
-                        cnt += 1.f;
                     }
                 }
             }
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         }
 #pragma unroll
         for (int j = 27; j < kNumAcc; ++j) {
-            float x = j == 27 ? cost : cnt;
+            float x = j == 27 ? cost : (j == 28 ? cnt : nonfin);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             if (lane == j) mine = x;
@@ -437,6 +444,14 @@ __global__ void __launch_bounds__(32 * kPairSlices) k_pair_reduce(const float* _
     __shared__ double H6[36], T[36], HT[36], R[9], tv[3];
     const PairStatic P = ps[p];
     const int k0 = full ? 0 : 27;
+    double* out = blocks + (long long)p * kBlockStride;
+    if (t == 64) {
+        // status word: 1 when the pair's relative pose is not finite (a NaN or infinite pose)
+        const int2 ij = pf[p];
+        bool bad = false;
+        for (int e = 0; e < 12; ++e) bad = bad || !isfinite(poses[12 * ij.x + e]) || !isfinite(poses[12 * ij.y + e]);
+        out[159] = bad ? 1.0 : 0.0;
+    }
     // thread (slice, j) sums accumulator j over its contiguous slice of the pair's
     // chunks in chunk order (4 loads in flight), then the slices are added in order
     {
@@ -464,11 +479,11 @@ __global__ void __launch_bounds__(32 * kPairSlices) k_pair_reduce(const float* _
         acc[t] = s;
     }
     __syncthreads();
-    double* out = blocks + (long long)p * kBlockStride;
     if (!full) {
         if (t == 0) {
             out[156] = acc[27];
             out[157] = acc[28];
+            out[158] = acc[29];
         }
         return;
     }
@@ -535,6 +550,7 @@ __global__ void __launch_bounds__(32 * kPairSlices) k_pair_reduce(const float* _
     if (t == 0) {
         out[156] = acc[27];
         out[157] = acc[28];
+        out[158] = acc[29];
     }
 }
 

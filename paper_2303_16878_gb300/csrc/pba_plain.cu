@@ -263,6 +263,8 @@ __global__ void k_plain_expand(const float* __restrict__ acc, int m, bool full, 
     if (t == 0) {
         out[156] = (double)a[90];
         out[157] = (double)a[91];
+        out[158] = 0.0;  // the plain path keeps no status word
+        out[159] = 0.0;
     }
 }
 

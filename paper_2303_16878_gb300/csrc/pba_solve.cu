@@ -82,7 +82,15 @@ __global__ void __launch_bounds__(64) k_assemble(const AsmTask* __restrict__ tas
 __global__ void k_total_cost(const double* __restrict__ blocks, int m, LmState* st, bool candidate) {
     __shared__ double sc[256];
     __shared__ double sn[256];
+    __shared__ long long snf[256], snp[256];
     double c = 0.0, n = 0.0;
+    long long nf = 0, np = 0;  // status word: non-finite residuals and pairs (exact integer sums)
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        nf += (long long)blocks[(long long)p * kBlockStride + 158];
+        np += (long long)blocks[(long long)p * kBlockStride + 159];
+    }
+    snf[threadIdx.x] = nf;
+    snp[threadIdx.x] = np;
     // strided per thread (loads 4 at a time, added in the same order), then a tree
     for (int p0 = threadIdx.x; p0 < m; p0 += 4 * blockDim.x) {
         double vc[4], vn[4];
@@ -106,6 +114,8 @@ __global__ void k_total_cost(const double* __restrict__ blocks, int m, LmState* 
         if (threadIdx.x < o) {
             sc[threadIdx.x] += sc[threadIdx.x + o];
             sn[threadIdx.x] += sn[threadIdx.x + o];
+            snf[threadIdx.x] += snf[threadIdx.x + o];
+            snp[threadIdx.x] += snp[threadIdx.x + o];
         }
         __syncthreads();
     }
@@ -113,9 +123,13 @@ __global__ void k_total_cost(const double* __restrict__ blocks, int m, LmState* 
         if (candidate) {
             st->new_cost = sc[0];
             st->n_valid_new = (long long)sn[0];
+            st->nf_res_new = snf[0];
+            st->nf_pairs_new = snp[0];
         } else {
             st->cost = sc[0];
             st->n_valid = (long long)sn[0];
+            st->nf_res = snf[0];
+            st->nf_pairs = snp[0];
         }
     }
 }
@@ -592,9 +606,13 @@ __global__ void k_accept(LmState* st, double* __restrict__ poses, const double* 
         st->lambda = ok ? st->lambda_used * 0.1 : st->lambda_used * 10.0;
         st->iter_cost = st->cost;
         st->iter_n_valid = speculative ? st->n_valid_new : st->n_valid;
+        st->iter_nf_res = speculative ? st->nf_res_new : st->nf_res;
+        st->iter_nf_pairs = speculative ? st->nf_pairs_new : st->nf_pairs;
         if (ok && speculative) {
             st->cost = st->new_cost;
             st->n_valid = st->n_valid_new;
+            st->nf_res = st->nf_res_new;
+            st->nf_pairs = st->nf_pairs_new;
         }
     }
     __syncthreads();
