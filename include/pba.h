@@ -42,7 +42,7 @@ extern "C" {
 #define PBA_ENOMEM (-2)     /* device or host allocation failed */
 #define PBA_ECUDA (-3)      /* a CUDA call failed; the message names it */
 #define PBA_ENOTPD (-4)     /* damped system not positive definite; the step was rejected */
-#define PBA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+/* (-5 is not used: no kernel of the library waits on another) */
 #define PBA_ENOTREADY (-6)  /* a required input (frames, poses, pairs) was not set */
 #define PBA_ETOOBIG (-7)    /* a size exceeds the fixed maximum of pba_linearize_pairs_noalloc */
 
@@ -64,12 +64,19 @@ extern "C" {
  * with FP64 residuals until |r| <= 1e-10 |b| (else the step is rejected and
  * lambda grows), which suits GB300's FP64 rate of ~1/64 of FP32.  MIXED runs
  * as one launch of a thread-block cluster holding the FP32 factor in shared
- * memory when the system fits (up to about 800 unknowns), else as one launch per
- * tile step; MIXED_STEPS always takes the per-step launches (same arithmetic,
- * kept for comparison). */
+ * memory when the system fits (up to about 800 unknowns); larger systems,
+ * unless a sensor offset is a variable, take the block-sparse solve of SPARSE;
+ * otherwise one launch per tile step.  MIXED_STEPS always takes the per-step
+ * launches (same arithmetic, kept for comparison).  SPARSE (same arithmetic)
+ * gathers the system in pose variables block by block from the pair blocks,
+ * orders each independent component of the pose graph for a small envelope
+ * (natural or reverse Cuthill-McKee order), factorises in tile-envelope
+ * storage and refines, one thread-block cluster per component in one launch;
+ * with a sensor offset as a variable it takes the per-step launches. */
 #define PBA_SOLVE_CHOLESKY_F64 0
 #define PBA_SOLVE_MIXED 1
 #define PBA_SOLVE_MIXED_STEPS 2
+#define PBA_SOLVE_SPARSE 3
 
 /* image-gradient modes (Supp., image Jacobians) */
 #define PBA_GRAD_CENTRAL 0  /* central differences at pixels, bilinearly interpolated (paper) */
@@ -110,7 +117,7 @@ typedef struct {
     int32_t grad_mode;          /* PBA_GRAD_CENTRAL or PBA_GRAD_BILINEAR */
     int32_t texel_precision;    /* PBA_TEXEL_F32 or PBA_TEXEL_F16 (batched path only) */
     int32_t path;               /* PBA_PATH_BATCHED or PBA_PATH_PLAIN */
-    int32_t solver;             /* PBA_SOLVE_CHOLESKY_F64, PBA_SOLVE_MIXED or PBA_SOLVE_MIXED_STEPS */
+    int32_t solver;             /* PBA_SOLVE_CHOLESKY_F64, _MIXED, _MIXED_STEPS or _SPARSE */
 } pba_config;
 
 /* Outcome of one Levenberg-Marquardt iteration. */
@@ -446,14 +453,36 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
  * summation order. */
 #define PBA_N_VARIANTS 3
 
-/* Pick, by timing them on this problem, the fastest occupancy variant of the
- * batched linearisation kernel for the full pass and for the cost-only pass
- * (each launched repeats + 1 times, the first as warm-up); later iterations
- * use the choice.  Reports the choice (0 .. PBA_N_VARIANTS - 1) in the
- * optional outputs.  Needs frames, poses and pairs; synchronises.  A no-op on
- * the plain path.  Errors: PBA_EINVAL, PBA_ENOTREADY (poses or pairs not
- * set), PBA_ECUDA. */
+/* Tune the batched linearisation on this problem by timing it (each setting
+ * launched repeats + 1 times, the first as warm-up): for the full pass every
+ * work-item size (512, 1024, 2048 points per warp item) x size of the short
+ * items that end the queue (128, 256) x occupancy variant, then for the
+ * cost-only pass the occupancy variants at the chosen work items; later
+ * iterations use the choice (pba_get_tuning reports it).  The result is
+ * cached for the life of the process per configuration (device, texel
+ * precision, gradient mode, pairs, point counts, sensors): tuning the same
+ * configuration again applies it without timing.  Rebuilds the pair plan
+ * when the work items change.  Reports the variants (0 .. PBA_N_VARIANTS - 1)
+ * in the optional outputs.  Needs frames, poses and pairs; synchronises.  A
+ * no-op on the plain path.  Errors: PBA_EINVAL, PBA_ENOTREADY (poses or pairs
+ * not set), PBA_ECUDA. */
 int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost);
+
+/* The settings the last pba_autotune chose (or the defaults): occupancy
+ * variants of the full and the cost-only pass, the work-item size (points per
+ * warp work item: 512, 1024 or 2048) and the size of the short items at the
+ * end of the queue (128 or 256), whether they came from the process's cache
+ * of tuned configurations (same device, texel precision, gradient mode,
+ * pairs, point counts and sensors: no timing was done), and the mean time of
+ * one full and one cost-only pass with them (0 before any tuning).
+ * Errors: PBA_EINVAL (a NULL argument). */
+typedef struct {
+    int32_t variant_full, variant_cost;
+    int32_t chunk, chunk_tail;
+    int32_t from_cache, pad;
+    float ms_full, ms_cost;
+} pba_tuning;
+int pba_get_tuning(pba_problem* p, pba_tuning* out);
 
 /* Set the variants explicitly (e.g. to reproduce a tuned configuration).
  * Errors: PBA_EINVAL (a variant outside [0, PBA_N_VARIANTS)). */
@@ -479,9 +508,10 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
  * PBA_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
  * the library holds until the process exits.
  *
- * It linearises m directed pairs (i, j) of frames that share one sensor,
- * exactly as pba_linearize does on the plain path (same residual, Jacobians,
- * robust weights and validity rules as set by cfg; cfg->texel_precision,
+ * It linearises m directed pairs (i, j) of frames that share one sensor with
+ * the residual, Jacobians, robust weights and validity rules of pba_linearize
+ * on the plain path, and agrees with it within the parity tolerances (not bit
+ * for bit: sums are formed in another order; cfg->texel_precision,
  * cfg->path and cfg->n_frames / sensors / frame_sensor are ignored), and
  * writes per pair PBA_NOALLOC_PAIR_STRIDE doubles to pair_out: H12 (144,
  * rows/cols 0-5 frame i, 6-11 frame j), b12 (12), cost, count, 2 zeros --
@@ -498,9 +528,9 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
  * has more than 2^30 pixels; PBA_EINVAL for null pointers or a bad sensor /
  * configuration; PBA_ECUDA when a launch fails.
  *
- * Sharing: the first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream capture.
- * Every call reuses the same array and clears the accumulators it uses, so
+ * Sharing: every call looks up the array's device address on the current
+ * device (a host-side query); make the first call on a device before any
+ * stream capture.  Every call reuses the same array and clears the accumulators it uses, so
  * the array keeps the previous call's contents until then; calls whose device
  * work overlaps (other streams or threads) race on it and must be serialised
  * by the caller. */

@@ -249,6 +249,35 @@ def linearize_pair(sensor, params: Dict, src: np.ndarray, tgt: np.ndarray, Xi, X
                 mask=mask[:nw].copy(), flags=flags[:nw].copy())
 
 
+def accounted_pair(s, params, src, tgt, Xi, Xj, other_mask, r, lib=None):
+    """The oracle's sums of one pair (r = linearize_pair's result) with every
+    point that another implementation decided the other way (other_mask: its
+    valid-point bit words) moved to that side: the point's contribution (from
+    the oracle, or from the oracle's other-branch evaluation when the oracle
+    rejected it) is removed or added.  Returns (H, b, cost, count, n_flipped,
+    n_unexplained); n_unexplained counts points decided the other way with no
+    other-branch evaluation (outside every decision margin)."""
+    H, b, cost, count = r["H"].copy(), r["b"].copy(), r["cost"], r["count"]
+    n = r["n_points"]
+    diff = np.unpackbits((other_mask ^ r["mask"]).view(np.uint8), bitorder="little")[:n]
+    ok_o = np.unpackbits(r["mask"].view(np.uint8), bitorder="little")[:n]
+    idx = np.nonzero(diff)[0]
+    unexplained = 0
+    if idx.size:
+        pts, _ = frame_points(s, params, src, lib=lib)
+        for k in idx.tolist():
+            c = point_contribution(s, params, tgt, Xi, Xj, pts[k], lib=lib, other_branch=not ok_o[k])
+            if c is None:
+                unexplained += 1
+                continue
+            sign = -1.0 if ok_o[k] else 1.0
+            H += sign * c[0]
+            b += sign * c[1]
+            cost += sign * c[2]
+            count += int(sign)
+    return H, b, cost, count, int(idx.size), unexplained
+
+
 def offset_map(extrinsic) -> np.ndarray:
     """A_o (6 x 6): the offset perturbation d acts like A_o d on both poses (R23)."""
     lib = _load()

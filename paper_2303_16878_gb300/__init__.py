@@ -15,10 +15,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PBA_PATH_BATCHED, PBA_PATH_PLAIN, PBA_PINHOLE, PBA_SOLVE_CHOLESKY_F64, PBA_SOLVE_MIXED,
-                   PBA_SOLVE_MIXED_STEPS, PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32, PbaError)
+                   PBA_SOLVE_MIXED_STEPS, PBA_SOLVE_SPARSE, PBA_SPHERICAL, PBA_TEXEL_F16, PBA_TEXEL_F32,
+                   PbaError)
 
 __all__ = ["Problem", "PbaError", "PBA_PATH_BATCHED", "PBA_PATH_PLAIN", "PBA_TEXEL_F16", "PBA_TEXEL_F32",
            "PBA_PINHOLE", "PBA_SPHERICAL", "PBA_SOLVE_CHOLESKY_F64", "PBA_SOLVE_MIXED", "PBA_SOLVE_MIXED_STEPS",
+           "PBA_SOLVE_SPARSE",
            "problem_from_workload"]
 
 
@@ -383,6 +385,15 @@ class Problem:
         a, b = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._lib.pba_autotune(self._h, int(repeats), ctypes.byref(a), ctypes.byref(b)), "autotune")
         return a.value, b.value
+
+    def tuning(self) -> Dict:
+        """The settings of the linearisation (pba_get_tuning): occupancy variants,
+        work-item sizes, whether they came from the process's tuning cache, and
+        the tuned pass times in ms."""
+        t = _lib.PbaTuning()
+        self._check(self._lib.pba_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        return dict(variant_full=t.variant_full, variant_cost=t.variant_cost, chunk=t.chunk,
+                    chunk_tail=t.chunk_tail, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost)
 
     def set_variants(self, variant_full: int, variant_cost: int):
         """Occupancy variants of the linearisation kernel (0 .. PBA_N_VARIANTS - 1)."""

@@ -17,7 +17,6 @@ PBA_EINVAL = -1
 PBA_ENOMEM = -2
 PBA_ECUDA = -3
 PBA_ENOTPD = -4
-PBA_ETIMEOUT = -5
 PBA_ENOTREADY = -6
 PBA_ETOOBIG = -7
 PBA_NOALLOC_MAX_PAIRS = 4096
@@ -32,9 +31,10 @@ PBA_TEXEL_F16 = 1
 PBA_SOLVE_CHOLESKY_F64 = 0
 PBA_SOLVE_MIXED = 1
 PBA_SOLVE_MIXED_STEPS = 2
+PBA_SOLVE_SPARSE = 3
 
 ERROR_NAMES = {PBA_EINVAL: "PBA_EINVAL", PBA_ENOMEM: "PBA_ENOMEM", PBA_ECUDA: "PBA_ECUDA",
-               PBA_ENOTPD: "PBA_ENOTPD", PBA_ETIMEOUT: "PBA_ETIMEOUT", PBA_ENOTREADY: "PBA_ENOTREADY",
+               PBA_ENOTPD: "PBA_ENOTPD", PBA_ENOTREADY: "PBA_ENOTREADY",
                PBA_ETOOBIG: "PBA_ETOOBIG"}
 
 # every exported symbol of include/pba.h
@@ -42,7 +42,7 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_frame_points", "pba_set_poses", "pba_get_poses", "pba_set_pairs", "pba_linearize",
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
            "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
-           "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_build_pairs",
+           "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_get_tuning", "pba_build_pairs",
            "pba_set_extrinsic", "pba_cost_gradient", "pba_tangent_gradient", "pba_estimate_normals", "pba_get_channels",
            "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
            "pba_set_variants", "pba_refine_extrinsic",
@@ -74,6 +74,12 @@ class PbaIterStats(ctypes.Structure):
     _fields_ = [("cost", ctypes.c_double), ("new_cost", ctypes.c_double), ("lambda_used", ctypes.c_double),
                 ("lambda_next", ctypes.c_double), ("n_valid", ctypes.c_int64), ("accepted", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("n_nonfinite", ctypes.c_int64), ("nonfinite_pairs", ctypes.c_int64)]
+
+
+class PbaTuning(ctypes.Structure):
+    _fields_ = [("variant_full", ctypes.c_int32), ("variant_cost", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("chunk_tail", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ms_full", ctypes.c_float), ("ms_cost", ctypes.c_float)]
 
 
 class PbaLevelStats(ctypes.Structure):
@@ -126,6 +132,7 @@ def load(build_if_missing: bool = True):
             "pba_iteration_launches": ([vp, P(i32)], ctypes.c_int),
             "pba_iterate_timed": ([vp, P(ctypes.c_float), ctypes.c_int, P(PbaIterStats)], ctypes.c_int),
             "pba_autotune": ([vp, ctypes.c_int, P(i32), P(i32)], ctypes.c_int),
+            "pba_get_tuning": ([vp, P(PbaTuning)], ctypes.c_int),
             "pba_build_pairs": ([vp, d, d, d, ctypes.c_int, vp, vp, ctypes.c_int, P(i32)], ctypes.c_int),
             "pba_set_extrinsic": ([vp, ctypes.c_int, vp], ctypes.c_int),
             "pba_estimate_normals": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int], ctypes.c_int),

@@ -78,28 +78,32 @@ __global__ void __launch_bounds__(kAdjThreads)
             const float qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
             const float qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));
             const float qz = fmaf(M[6], p.x, fmaf(M[7], p.y, fmaf(M[8], p.z, av[2])));
-            float u, v, zeta_d, rxy2 = 0.f;
+            float v, zeta_d, fa, rxy2 = 0.f;
+            int c0;
             bool ok;
             if (model == 0) {
                 ok = qz > prm.z_min;
                 const float iz = 1.f / qz;
-                u = fmaf(fx * qx, iz, cx);
+                const float u = fmaf(fx * qx, iz, cx);
                 v = fmaf(fy * qy, iz, cy);
                 zeta_d = qz;
+                ok = ok && u >= umin && u < umax;
+                const float fu = floorf(u);
+                c0 = (int)fu;
+                fa = u - fu;
             } else {
                 rxy2 = fmaf(qx, qx, qy * qy);
                 zeta_d = sqrtf(fmaf(qz, qz, rxy2));
                 ok = zeta_d > prm.z_min;
-                u = fmaf(fx, atan2_poly(qy, qx), cx);
-                v = fmaf(fy, atan2_poly(qz, sqrtf(rxy2)), cy);
+                spherical_project(qx, qy, qz, rsqrtf(rxy2), fx, fy, cx, cy, P.fxh, P.fxp, c0, fa, v);
             }
-            ok = ok && v >= 1.f && v < vmax && u >= umin && u < umax;
+            ok = ok && v >= 1.f && v < vmax;
             if (!ok) continue;
-            const float fu = floorf(u), fv = floorf(v);
+            const float fv = floorf(v);
             const int r0 = (int)fv;
-            const float fa = u - fu, fb = v - fv;
+            const float fb = v - fv;
             int cm1, cc, cp1, cp2;
-            stencil_cols((int)fu, W, wrap, cm1, cc, cp1, cp2);
+            stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
             const int rr0 = r0 * W, rp1 = rr0 + W;
             const Texel A = load_texel<TEXEL>(tex_j, rr0 + cc), B = load_texel<TEXEL>(tex_j, rr0 + cp1);
             const Texel C = load_texel<TEXEL>(tex_j, rp1 + cc), D = load_texel<TEXEL>(tex_j, rp1 + cp1);

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -18,8 +19,12 @@ using namespace pba;
 
 namespace {
 
-constexpr int kChunk = 1024;     // points per work item (one warp) of the persistent launch
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kChunk = 1024;     // default points per work item (one warp) of the persistent launch
 constexpr int kChunkTail = 256;  // ... in the last stretch of the queue, so that the warps finish closer together
+// the work-item sizes pba_autotune tries
+constexpr int kTuneChunks[3] = {512, 1024, 2048};
+constexpr int kTuneTails[2] = {128, 256};
 
 }  // namespace
 
@@ -106,6 +111,9 @@ struct pba_problem {
     bool linearized = false;
     int grid_full = 0, grid_cost = 0;
     int variant_full = 0, variant_cost = 0;  // occupancy variants chosen by pba_autotune
+    int chunk = kChunk, chunk_tail = kChunkTail;  // work-item sizes (pba_autotune)
+    float tune_ms_full = 0.f, tune_ms_cost = 0.f;
+    int tune_from_cache = 0;
     LinParams prm{};
 
     cudaGraph_t graph = nullptr;
@@ -145,6 +153,12 @@ struct pba_problem {
     int* d_free_frames = nullptr;
     int n_free_frames = 0;
 
+    // block-sparse solve (pba_solve_sparse.cu): used when `sparse`; its device plan
+    // and work buffers (sp_mem: every allocation of the plan, freed together)
+    bool sparse = false;
+    SpPlanDev sp{};
+    std::vector<void*> sp_mem;
+
     // coarser pyramid levels 1.. (Sec. IV-A), each a problem of its own on the same stream
     std::vector<pba_problem*> levels;
     bool pyramid_stale = true;
@@ -171,7 +185,10 @@ void dfree(T*& ptr) {
     ptr = nullptr;
 }
 
+void free_sparse(pba_problem* p);
+
 void free_pair_buffers(pba_problem* p) {
+    free_sparse(p);
     dfree(p->d_ps);
     dfree(p->d_pp);
     dfree(p->d_pf);
@@ -198,6 +215,13 @@ void free_pair_buffers(pba_problem* p) {
     p->M = 0;
     p->n_chunks = 0;
     p->n_tasks = 0;
+}
+
+void free_sparse(pba_problem* p) {
+    for (void* ptr : p->sp_mem) cudaFree(ptr);
+    p->sp_mem.clear();
+    p->sp = SpPlanDev{};
+    p->sparse = false;
 }
 
 void drop_graph(pba_problem* p) {
@@ -250,9 +274,13 @@ int enqueue_linearize(pba_problem* p, cudaStream_t s, int* nl, cudaEvent_t* ev =
         CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, poses, p->d_pair_Xo, p->M, true, blocks, s));
         *nl += 2;
     }
-    CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, blocks, p->N, H, b, s));
+    // the block-sparse solve gathers its system from the pair blocks: no dense H
+    if (!p->sparse) {
+        CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, blocks, p->N, H, b, s));
+        ++*nl;
+    }
     CUDA_TRY(p, launch_total_cost(blocks, p->M, p->d_state, at_cand, s));
-    *nl += 2;
+    ++*nl;
     if (ev) CUDA_TRY(p, cudaEventRecord(ev[4], s));
     return PBA_OK;
 }
@@ -270,7 +298,10 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
     const double* bs = p->d_b;
     int nf = p->N, npad = p->n_pad;
     const int S = (int)p->sensors.size();
-    if (p->n_vars >= 0 && p->offsets_free) {
+    if (p->sparse) {
+        // gathered in pose variables from the pair blocks, damped, factorised and refined
+        CUDA_TRY(p, launch_sparse_solve(p->sp, p->d_blocks, p->d_state, lambda, 3, p->d_rhs, s, nl));
+    } else if (p->n_vars >= 0 && p->offsets_free) {
         // offset blocks from the current pair blocks (J_o = (J_i + J_j) A_o), then S^T H S
         CUDA_TRY(p, launch_offset_system(p->d_blocks, p->d_pair_Xo, p->M, p->d_pext, p->d_f_start, p->d_f_items,
                                          p->d_s_start, p->d_s_items, p->d_frame_sensor, p->d_sensor_var, p->N, S,
@@ -291,10 +322,12 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
         nf = p->n_vars + 1;
         npad = p->n_pad_vars;
     }
-    CUDA_TRY(p, launch_lm_prepare(Hs, nf, p->d_state, lambda, s));
     int nc = 0;
     CsGeom cg{};
-    if (p->cfg.solver == PBA_SOLVE_MIXED && solve_cluster_plan(npad, &cg)) {
+    if (!p->sparse) CUDA_TRY(p, launch_lm_prepare(Hs, nf, p->d_state, lambda, s));
+    if (p->sparse) {
+        // solved above
+    } else if (p->cfg.solver == PBA_SOLVE_MIXED && solve_cluster_plan(npad, &cg)) {
         CUDA_TRY(p, launch_solve_cluster(Hs, bs, nf, cg, p->d_state, 3, p->d_rhs, p->mixed.A32, p->mixed.D32, s));
         *nl += 2;
     } else if (p->cfg.solver != PBA_SOLVE_CHOLESKY_F64) {
@@ -351,8 +384,9 @@ int enqueue_step(pba_problem* p, double lambda, cudaStream_t s, int* nl, cudaEve
         CUDA_TRY(p, launch_total_cost(p->d_blocks_cand, p->M, p->d_state, true, s));
         ++*nl;
     }
-    CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, speculative, p->d_H, p->d_H_cand, p->d_b,
-                              p->d_b_cand, p->d_blocks, p->d_blocks_cand, p->M, s));
+    CUDA_TRY(p, launch_accept(p->d_state, p->d_poses, p->d_cand, p->N, speculative,
+                              p->sparse ? nullptr : p->d_H, p->d_H_cand, p->d_b, p->d_b_cand, p->d_blocks,
+                              p->d_blocks_cand, p->M, s));
     *nl += speculative ? 2 : 1;
     if (p->offsets_free) {  // the accepted (or kept) offsets become current again everywhere
         CUDA_TRY(p, launch_offset_accept(p->d_state, p->d_extr, p->d_extr_cand, S, s));
@@ -441,7 +475,17 @@ int repack(pba_problem* p, int first, int count, float scale, int max_radius) {
 // offsets: device CSR of the blocks of each variable (frames f < N, offsets
 // N + s), the frame and sensor maps used by the box-plus, Hr / br, and the list
 // of frames re-packed when an offset moves.  Drops the iteration graph.
+int plan_sparse(pba_problem* p);
+
+int rebuild_vars_mapping(pba_problem* p);
+
+// The variables of the solve changed: rebuild their mapping, then the sparse plan.
 int rebuild_vars(pba_problem* p) {
+    const int st = rebuild_vars_mapping(p);
+    return st ? st : plan_sparse(p);
+}
+
+int rebuild_vars_mapping(pba_problem* p) {
     drop_graph(p);
     p->pyramid_stale = true;
     const int S = (int)p->sensors.size();
@@ -511,6 +555,85 @@ int rebuild_vars(pba_problem* p) {
     return PBA_OK;
 }
 
+// Whether the block-sparse solve runs, and its plan: for PBA_SOLVE_SPARSE, and for
+// PBA_SOLVE_MIXED when the system is too large for the one-launch cluster solve;
+// not while a sensor offset is a variable (its dense coupling rows take the
+// per-step launches).  The plan follows the pairs and the frames' variables.
+int plan_sparse(pba_problem* p) {
+    free_sparse(p);
+    if (p->M <= 0 || p->offsets_free) return PBA_OK;
+    if (p->cfg.solver != PBA_SOLVE_SPARSE) {
+        CsGeom cg{};
+        const int npad = p->n_vars >= 0 ? p->n_pad_vars : p->n_pad;
+        if (p->cfg.solver != PBA_SOLVE_MIXED || solve_cluster_plan(npad, &cg)) return PBA_OK;
+    }
+    std::vector<int> fv(p->N);
+    int nv;
+    if (p->n_fv_user >= 0) {
+        fv.assign(p->fv_user.begin(), p->fv_user.end());
+        nv = p->n_fv_user;
+    } else {
+        for (int k = 0; k < p->N; ++k) fv[k] = k - 1;
+        nv = p->N - 1;
+    }
+    const int cmax = sparse_cluster_max();
+    SpPlanHost h;
+    if (cmax < 1 || !sparse_plan(nv, fv, p->pairs, cmax, &h)) return PBA_OK;  // the dense solves remain
+    bool ok = true;
+    auto up = [&](const void* src, size_t bytes) -> void* {
+        void* d = nullptr;
+        if (!ok || cudaMalloc(&d, bytes ? bytes : 16) != cudaSuccess) {
+            ok = false;
+            return nullptr;
+        }
+        p->sp_mem.push_back(d);
+        if (src && bytes && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+        return d;
+    };
+    SpPlanDev& d = p->sp;
+    d.nv = h.nv;
+    d.n_rows = h.n_rows;
+    d.nblk = (int)h.blk.size();
+    d.n_comp = (int)h.comp_rows.size();
+    d.C = h.C;
+    d.n_tiles = h.n_tiles;
+    d.var_of_pos = (const int*)up(h.var_of_pos.data(), sizeof(int) * h.var_of_pos.size());
+    d.scal_of_pos = (const int*)up(h.scal_of_pos.data(), sizeof(int) * h.scal_of_pos.size());
+    d.pos_of_scalar = (const int*)up(h.pos_of_scalar.data(), sizeof(int) * h.pos_of_scalar.size());
+    d.diag_blk = (const int*)up(h.diag_blk.data(), sizeof(int) * h.diag_blk.size());
+    d.blk = (const int2*)up(h.blk.data(), sizeof(int2) * h.blk.size());
+    d.blk_start = (const int*)up(h.blk_start.data(), sizeof(int) * h.blk_start.size());
+    d.blk_contrib = (const int4*)up(h.blk_contrib.data(), sizeof(int4) * h.blk_contrib.size());
+    d.b_start = (const int*)up(h.b_start.data(), sizeof(int) * h.b_start.size());
+    d.b_contrib = (const int2*)up(h.b_contrib.data(), sizeof(int2) * h.b_contrib.size());
+    d.row_start = (const int*)up(h.row_start.data(), sizeof(int) * h.row_start.size());
+    d.row_items = (const int2*)up(h.row_items.data(), sizeof(int2) * h.row_items.size());
+    d.tile_first = (const int*)up(h.tile_first.data(), sizeof(int) * h.tile_first.size());
+    d.tile_off = (const long long*)up(h.tile_off.data(), sizeof(long long) * h.tile_off.size());
+    d.comp_rows = (const int2*)up(h.comp_rows.data(), sizeof(int2) * h.comp_rows.size());
+    const size_t ns = (size_t)h.n_rows * kTile;
+    d.Hv = (double*)up(nullptr, sizeof(double) * 36 * h.blk.size());
+    d.bvec = (double*)up(nullptr, sizeof(double) * 6 * (size_t)h.nv);
+    d.dsc = (double*)up(nullptr, sizeof(double) * ns);
+    d.dsc32 = (float*)up(nullptr, sizeof(float) * ns);
+    d.bsc = (double*)up(nullptr, sizeof(double) * ns);
+    d.x = (double*)up(nullptr, sizeof(double) * ns);
+    d.r64 = (double*)up(nullptr, sizeof(double) * ns);
+    d.L = (float*)up(nullptr, sizeof(float) * kTile * kTile * (size_t)h.n_tiles);
+    d.Dinv = (float*)up(nullptr, sizeof(float) * kTile * ns);
+    d.rv = (float*)up(nullptr, sizeof(float) * ns);
+    d.yv = (float*)up(nullptr, sizeof(float) * ns);
+    d.zv = (float*)up(nullptr, sizeof(float) * ns);
+    d.acc = (float*)up(nullptr, sizeof(float) * ns);
+    d.nrm = (double*)up(nullptr, sizeof(double) * 2 * (size_t)d.n_comp * d.C);
+    if (!ok) {
+        free_sparse(p);
+        return fail(p, PBA_ENOMEM, "sparse solve: device allocation failed");
+    }
+    p->sparse = true;
+    return PBA_OK;
+}
+
 // The host copies of the offsets follow the device ones (refined by the solve).
 int sync_offsets_to_host(pba_problem* p) {
     const int S = (int)p->sensors.size();
@@ -550,7 +673,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
         return create_fail(PBA_EINVAL, "texel_precision must be PBA_TEXEL_F32 or PBA_TEXEL_F16");
     if (cfg->path != PBA_PATH_BATCHED && cfg->path != PBA_PATH_PLAIN) return create_fail(PBA_EINVAL, "unknown path");
     if (cfg->solver != PBA_SOLVE_CHOLESKY_F64 && cfg->solver != PBA_SOLVE_MIXED &&
-        cfg->solver != PBA_SOLVE_MIXED_STEPS)
+        cfg->solver != PBA_SOLVE_MIXED_STEPS && cfg->solver != PBA_SOLVE_SPARSE)
         return create_fail(PBA_EINVAL, "unknown solver");
     for (int s = 0; s < cfg->n_sensors; ++s) {
         const pba_sensor& S = cfg->sensors[s];
@@ -658,6 +781,7 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     if (!ok) return bail(PBA_ENOMEM);
     // cluster limits of the one-launch mixed solve, queried here (outside any stream capture)
     if (cfg->solver == PBA_SOLVE_MIXED) solve_cluster_init();
+    if (cfg->solver == PBA_SOLVE_MIXED || cfg->solver == PBA_SOLVE_SPARSE) sparse_cluster_max();
 
     std::vector<FrameInfo> fi(p->N);
     for (int k = 0; k < p->N; ++k) {
@@ -753,6 +877,7 @@ void pba_destroy(pba_problem* p) {
     dfree(p->d_Hfo);
     dfree(p->d_Hoo);
     dfree(p->d_bo);
+    free_sparse(p);
     free_pair_buffers(p);
     dfree(p->raw);
     dfree(p->tex);
@@ -1014,6 +1139,8 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
         P.height = S.height;
         P.n_points = p->n_points[i];
         P.fx = (float)S.fx;
+        P.fxh = (float)(S.fx * (0.5 * kPi));
+        P.fxp = (float)(S.fx * kPi);
         P.fy = (float)S.fy;
         P.cx = (float)S.cx;
         P.cy = (float)S.cy;
@@ -1035,13 +1162,13 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     long long total_pts = 0;
     for (int q = 0; q < m; ++q) total_pts += ps[q].n_points;
     const long long resident = (long long)std::max(p->grid_full, 1) * 8;
-    const long long tail_start = total_pts - std::min(total_pts / 4, resident * kChunk);
+    const long long tail_start = total_pts - std::min(total_pts / 4, resident * p->chunk);
     long long done_pts = 0;
     for (int oi = 0; oi < m; ++oi) {
         const int q = order[oi];
         ps[q].chunk_begin = (int)chunks.size();
         for (int s = 0; s < ps[q].n_points;) {
-            const int size = done_pts + s >= tail_start ? kChunkTail : kChunk;
+            const int size = done_pts + s >= tail_start ? p->chunk_tail : p->chunk;
             const int n = std::min(size, ps[q].n_points - s);
             chunks.push_back(make_int4(q, s, n, 0));
             s += n;
@@ -1139,7 +1266,7 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     CUDA_TRY(p, cudaMemset(p->d_b, 0, sizeof(double) * n6));
     CUDA_TRY(p, cudaMemset(p->d_H_cand, 0, sizeof(double) * (size_t)n6 * n6));
     CUDA_TRY(p, cudaMemset(p->d_b_cand, 0, sizeof(double) * n6));
-    return PBA_OK;
+    return plan_sparse(p);
 }
 
 int pba_build_pairs(pba_problem* p, double max_angle, double max_dist, double min_ratio, int sequential,
@@ -1291,6 +1418,10 @@ int pba_get_system(pba_problem* p, double* H, double* b) {
     if (!p->linearized) return fail(p, PBA_ENOTREADY, "get_system: no linearisation");
     cudaSetDevice(p->device);
     const int n6 = 6 * p->N;
+    // the block-sparse solve keeps no dense system: assemble it from the pair blocks now
+    if (p->sparse && p->M > 0)
+        CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, p->d_blocks, p->N, p->d_H, p->d_b,
+                                    p->stream));
     if (H) CUDA_TRY(p, cudaMemcpyAsync(H, p->d_H, sizeof(double) * (size_t)n6 * n6, cudaMemcpyDeviceToHost, p->stream));
     if (b) CUDA_TRY(p, cudaMemcpyAsync(b, p->d_b, sizeof(double) * n6, cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
@@ -1424,6 +1555,68 @@ int pba_iterate_timed(pba_problem* p, float* phase_ms, int n_phases, pba_iter_st
     return st;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Tuned settings per configuration, for the life of the process.
+struct TuneEntry {
+    int variant_full, variant_cost, chunk, chunk_tail;
+    float ms_full, ms_cost;
+};
+std::mutex g_tune_mutex;
+std::map<std::string, TuneEntry> g_tune_cache;
+
+// What a tuning depends on: device, texel precision, gradient mode, the pairs
+// (count, points and sensor models) and the frames' sizes.
+std::string tune_key(const pba_problem* p) {
+    long long pts = 0, h = 1469598103934665603LL;
+    for (int q = 0; q < p->M; ++q) {
+        const int i = p->pairs[2 * q], j = p->pairs[2 * q + 1];
+        pts += p->n_points[i];
+        const pba_sensor& S = p->sensors[p->frame_sensor[i]];
+        for (long long v : {(long long)i, (long long)j, (long long)S.model, (long long)S.width, (long long)S.height})
+            h = (h ^ v) * 1099511628211LL;
+    }
+    char buf[160];
+    snprintf(buf, sizeof buf, "d%d t%d g%d m%d p%lld h%llx", p->device, p->cfg.texel_precision, p->cfg.grad_mode, p->M,
+             pts, (unsigned long long)h);
+    return buf;
+}
+
+// Rebuild the chunk queue (and everything pba_set_pairs plans) for new work-item sizes.
+int set_chunking(pba_problem* p, int chunk, int tail) {
+    if (p->chunk == chunk && p->chunk_tail == tail) return PBA_OK;
+    p->chunk = chunk;
+    p->chunk_tail = tail;
+    std::vector<int32_t> keep = p->pairs;
+    return pba_set_pairs(p, keep.data(), (int)(keep.size() / 2));
+}
+
+// Mean time of `repeats` launches of one linearisation pass (after one untimed launch).
+int time_pass(pba_problem* p, bool full, int variant, int repeats, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+    const int grid = linearize_grid(p->cfg.texel_precision, full, variant);
+    float total = 0.f;
+    for (int r = 0; r <= repeats; ++r) {
+        CUDA_TRY(p, cudaMemsetAsync(p->d_queue, 0, sizeof(int), p->stream));
+        CUDA_TRY(p, cudaEventRecord(e0, p->stream));
+        CUDA_TRY(p, launch_linearize(full, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks, p->d_queue,
+                                     p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials, nullptr,
+                                     grid, variant, p->stream));
+        CUDA_TRY(p, cudaEventRecord(e1, p->stream));
+        CUDA_TRY(p, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(p, cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) total += ms;
+    }
+    *ms_out = total / repeats;
+    return PBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* variant_cost) {
     int st = ready(p);
     if (st) return st;
@@ -1433,44 +1626,80 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
         if (variant_cost) *variant_cost = 0;
         return PBA_OK;
     }
-    cudaEvent_t e0, e1;
-    CUDA_TRY(p, cudaEventCreate(&e0));
-    CUDA_TRY(p, cudaEventCreate(&e1));
-    CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
-    int best[2] = {0, 0};
-    for (int full = 1; full >= 0; --full) {
-        float best_ms = 3.4e38f;
-        for (int v = 0; v < PBA_N_VARIANTS; ++v) {
-            const int grid = linearize_grid(p->cfg.texel_precision, full != 0, v);
-            float total = 0.f;
-            for (int r = 0; r <= repeats; ++r) {  // r = 0 is a warm-up
-                CUDA_TRY(p, cudaMemsetAsync(p->d_queue, 0, sizeof(int), p->stream));
-                CUDA_TRY(p, cudaEventRecord(e0, p->stream));
-                CUDA_TRY(p, launch_linearize(full != 0, false, p->cfg.texel_precision, p->d_chunks, p->n_chunks,
-                                             p->d_queue, p->d_ps, p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm,
-                                             p->d_partials, nullptr, grid, v, p->stream));
-                CUDA_TRY(p, cudaEventRecord(e1, p->stream));
-                CUDA_TRY(p, cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CUDA_TRY(p, cudaEventElapsedTime(&ms, e0, e1));
-                if (r > 0) total += ms;
-            }
-            if (total < best_ms) {
-                best_ms = total;
-                best[full] = v;
-            }
+    if ((st = ensure_points(p))) return st;
+    const std::string key = tune_key(p);
+    TuneEntry best{0, 0, kChunk, kChunkTail, 3.4e38f, 3.4e38f};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->variant_full = best[1];
-    p->variant_cost = best[0];
+    if (!cached) {
+        cudaEvent_t e0, e1;
+        CUDA_TRY(p, cudaEventCreate(&e0));
+        CUDA_TRY(p, cudaEventCreate(&e1));
+        // the full pass over work-item size x tail size x occupancy variant
+        for (int c : kTuneChunks)
+            for (int t : kTuneTails) {
+                if ((st = set_chunking(p, c, t))) return st;
+                CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
+                for (int v = 0; v < PBA_N_VARIANTS; ++v) {
+                    float ms = 0.f;
+                    if ((st = time_pass(p, true, v, repeats, e0, e1, &ms))) return st;
+                    if (ms < best.ms_full) {
+                        best.ms_full = ms;
+                        best.variant_full = v;
+                        best.chunk = c;
+                        best.chunk_tail = t;
+                    }
+                }
+            }
+        // the cost-only pass at the chosen work items
+        if ((st = set_chunking(p, best.chunk, best.chunk_tail))) return st;
+        CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
+        for (int v = 0; v < PBA_N_VARIANTS; ++v) {
+            float ms = 0.f;
+            if ((st = time_pass(p, false, v, repeats, e0, e1, &ms))) return st;
+            if (ms < best.ms_cost) {
+                best.ms_cost = ms;
+                best.variant_cost = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    } else if ((st = set_chunking(p, best.chunk, best.chunk_tail))) {
+        return st;
+    }
+    p->variant_full = best.variant_full;
+    p->variant_cost = best.variant_cost;
+    p->tune_ms_full = best.ms_full;
+    p->tune_ms_cost = best.ms_cost;
+    p->tune_from_cache = cached ? 1 : 0;
     p->grid_full = linearize_grid(p->cfg.texel_precision, true, p->variant_full);
     p->grid_cost = linearize_grid(p->cfg.texel_precision, false, p->variant_cost);
     drop_graph(p);
     p->linearized = false;
     if (variant_full) *variant_full = p->variant_full;
     if (variant_cost) *variant_cost = p->variant_cost;
+    return PBA_OK;
+}
+
+int pba_get_tuning(pba_problem* p, pba_tuning* out) {
+    if (!p || !out) return PBA_EINVAL;
+    out->variant_full = p->variant_full;
+    out->variant_cost = p->variant_cost;
+    out->chunk = p->chunk;
+    out->chunk_tail = p->chunk_tail;
+    out->from_cache = p->tune_from_cache;
+    out->pad = 0;
+    out->ms_full = p->tune_ms_full;
+    out->ms_cost = p->tune_ms_cost;
     return PBA_OK;
 }
 

@@ -9,29 +9,58 @@ namespace pba {
 
 // ------------------------------------------------------------ arctangent
 
-// atan2(y, x) for the spherical projection: reduce to t = min(|x|,|y|) /
-// max(|x|,|y|) in [0, 1], approximate atan(t) = t P(t^2) with a degree-8
-// polynomial fitted by least squares (gen_atan_poly.py prints the
-// coefficients and its float32 error, max 3e-7 rad), then reflect into the
-// octant.  atan2(0, 0) = 0.
-__device__ __forceinline__ float atan2_poly(float y, float x) {
+// atan(t) for t in [0, 1] as t + t s Q(s), s = t^2, Q of degree 7
+// (gen_atan_poly.py fits Q towards the minimax error in float64 and prints
+// the float32 error of this evaluation: below 8e-8 rad, about 1.3 ulp of
+// pi / 4; the leading term t is added last, with one rounding).
+__device__ __forceinline__ float atan_unit(float t) {
+    const float s = t * t;
+    float q = 0.0026222029700875282f;
+    q = fmaf(q, s, -0.015132364816963673f);
+    q = fmaf(q, s, 0.04112157225608826f);
+    q = fmaf(q, s, -0.07366681098937988f);
+    q = fmaf(q, s, 0.10573919862508774f);
+    q = fmaf(q, s, -0.1418597251176834f);
+    q = fmaf(q, s, 0.1999039649963379f);
+    q = fmaf(q, s, -0.33332985639572144f);
+    return fmaf(t * s, q, t);
+}
+
+// Spherical projection (Eq. spherical-projection) of pbar = (x, y, z):
+// u = cx + fx atan2(y, x), v = cy + fy atan2(z, sqrt(x^2 + y^2)), returned as
+// the column c0 = floor(u), its bilinear weight a = u - c0, and v.
+// The azimuth is written sgn(y) (B + sigma r) with r = atan(t) in [0, pi/4],
+// t = min(|x|, |y|) / max(|x|, |y|) (a reciprocal refined by one Newton
+// step), B in {0, pi/2, pi} and sigma = +-1 by octant, so u = U + s with
+// U = cx + sgn(y) fx B (fxh = fx pi / 2 and fxp = fx pi are per-pair
+// constants; for the spherical intrinsics fx = -W / 2 pi, cx = W / 2 every U
+// is an exact integer) and s = sgn(y) sigma fx r, |s| <= |fx| pi / 4.  The
+// floor and the fraction are taken of s (float32 spacing at most W / 2^26)
+// rather than of u, whose float32 spacing near W is 16 times coarser.
+// The elevation is atan(|z| / rxy) with irxy = 1 / rxy given, or
+// pi/2 - atan(rxy / |z|) above 45 degrees; NaN or infinite inputs give a v
+// that fails every bound.
+__device__ __forceinline__ void spherical_project(float x, float y, float z, float irxy, float fx, float fy,
+                                                  float cx, float cy, float fxh, float fxp, int& c0, float& a,
+                                                  float& v) {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
-    const float s = t * t;
-    float p = 0.002932762f;
-    p = fmaf(p, s, -0.01641319f);
-    p = fmaf(p, s, 0.043278243f);
-    p = fmaf(p, s, -0.075569004f);
-    p = fmaf(p, s, 0.10667487f);
-    p = fmaf(p, s, -0.14211106f);
-    p = fmaf(p, s, 0.19993694f);
-    p = fmaf(p, s, -0.33333138f);
-    p = fmaf(p, s, 1.0f);
-    float r = t * p;
-    if (ay > ax) r = 1.57079637f - r;
-    if (x < 0.f) r = 3.14159274f - r;
-    return y < 0.f ? -r : r;
+    const float rc = __fdividef(1.f, mx);
+    const float t0 = mn * rc;
+    const float t = mx > 0.f ? fmaf(fmaf(-t0, mx, mn), rc, t0) : 0.f;
+    const float r = atan_unit(t);
+    const bool swap = ay > ax, neg_x = x < 0.f;
+    const float sg = y < 0.f ? -1.f : 1.f;
+    const float U = fmaf(sg, swap ? fxh : (neg_x ? fxp : 0.f), cx);
+    const float s = (swap != neg_x ? -sg : sg) * (fx * r);
+    const float Ui = floorf(U);
+    const float w = (U - Ui) + s;
+    const float fw = floorf(w);
+    c0 = (int)(Ui + fw);
+    a = w - fw;
+    const float te = fabsf(z) * irxy;
+    const float el = te <= 1.f ? atan_unit(te) : 1.57079637f - atan_unit(__fdividef(1.f, te));
+    v = fmaf(fy, z < 0.f ? -el : el, cy);
 }
 
 // ------------------------------------------------------------ texel access

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace pba {
 
 constexpr int kPartialStride = 32;   // floats per chunk partial
@@ -29,6 +31,30 @@ constexpr int kNumAcc = 30;          // 21 + 6 + cost + count + non-finite resid
 constexpr int kBlockStride = 160;    // doubles per pair block
 constexpr int kTile = 32;            // Cholesky tile
 constexpr double kRefineTol = 1e-10; // |r| <= kRefineTol |b'| ends the mixed-precision refinement
+
+// The float32 range limits that decide d >= range_min and d <= range_max for
+// every float32 depth d exactly as the double comparisons do: range_min
+// rounded up and range_max rounded down to float32 (a limit above the float
+// range stays at 3e38).
+inline void float_range_limits(double range_min, double range_max, float* rmin, float* rmax) {
+    float lo = (float)range_min;
+    if ((double)lo < range_min) lo = nextafterf(lo, 3.0e38f);
+    float hi = range_max > 3.0e38 ? 3.0e38f : (float)range_max;
+    if ((double)hi > range_max) hi = nextafterf(hi, -3.0e38f);
+    *rmin = lo;
+    *rmax = hi;
+}
+
+// Pixel validity of the plain paths (Sec. IV-A): range_min <= d <= range_max
+// (limits from float_range_limits), d > 0 and |n|^2 > 0.25, the last summed in
+// FP32 unless it lies within 1e-6 of the threshold, where the double sum
+// decides (as the double evaluation of the float inputs would).
+__device__ __forceinline__ bool plain_pixel_valid(const float* c, float rmin, float rmax) {
+    if (!(c[1] > 0.f && c[1] >= rmin && c[1] <= rmax)) return false;
+    const float n2 = fmaf(c[4], c[4], fmaf(c[3], c[3], c[2] * c[2]));
+    if (fabsf(n2 - 0.25f) > 1e-6f) return n2 > 0.25f;
+    return (double)c[2] * c[2] + (double)c[3] * c[3] + (double)c[4] * c[4] > 0.25;
+}
 
 struct FrameInfo {
     int width, height, sensor, model;
@@ -55,6 +81,7 @@ struct PairStatic {
     long long mask_offset;   // in 32-bit words
     long long src_px_offset; // raw buffer of the source (plain path)
     int src_width, src_height;
+    float fxh, fxp;          // spherical: f_x pi / 2 and f_x pi (offsets of the column, spherical_project)
 };
 
 // Pose-dependent per-pair constants (FP32), rebuilt on the device each iteration.
@@ -234,6 +261,68 @@ bool solve_cluster_plan(int n_pad, CsGeom* g);
 cudaError_t launch_solve_cluster(const double* H, const double* b, int n_frames, const CsGeom& g, LmState* st,
                                  int refinements, double* dx, float* gL, float* gD, cudaStream_t s);
 
+// Block-sparse damped solve for large pose graphs (pba_solve_sparse.cu).  Positions
+// are the pose variables in the solve's order (components contiguous, each
+// ordered for a small envelope); unknown s = 6 position + r within a
+// component's tile rows (components start on a tile row; padding unknowns get
+// an identity row).  Lower blocks have row position >= column position.
+struct SpPlanHost {
+    int nv = 0, n_rows = 0, C = 1;
+    long long n_tiles = 0;
+    std::vector<int> var_of_pos, scal_of_pos, pos_of_scalar, diag_blk;
+    std::vector<int2> blk;                 // lower blocks (row position, column position)
+    std::vector<int> blk_start;            // contributions of each block ...
+    std::vector<int4> blk_contrib;         // ... (pair, row role, column role, 0)
+    std::vector<int> b_start;              // b contributions of each position ...
+    std::vector<int2> b_contrib;           // ... (pair, role)
+    std::vector<int> row_start;            // blocks of each position's block row ...
+    std::vector<int2> row_items;           // ... (block, 1 when used transposed)
+    std::vector<int> tile_first;           // per tile row I: F(I), the first stored tile column
+    std::vector<long long> tile_off;       // per tile row: index of its tile (I, F(I))
+    std::vector<int2> comp_rows;           // per component: (first tile row, tile rows)
+};
+struct SpPlanDev {
+    int nv, n_rows, nblk, n_comp, C;
+    long long n_tiles;
+    const int* var_of_pos;
+    const int* scal_of_pos;
+    const int* pos_of_scalar;
+    const int* diag_blk;
+    const int2* blk;
+    const int* blk_start;
+    const int4* blk_contrib;
+    const int* b_start;
+    const int2* b_contrib;
+    const int* row_start;
+    const int2* row_items;
+    const int* tile_first;
+    const long long* tile_off;
+    const int2* comp_rows;
+    // work buffers
+    double* Hv;    // nblk x 36: the blocks of H_ff (without damping)
+    double* bvec;  // nv x 6: b of each position
+    double* dsc;   // n_rows x 32: D
+    float* dsc32;
+    double* bsc;   // b' = -D b
+    double* x;     // refined solution of the scaled system
+    double* r64;   // its FP64 residual
+    float* L;      // n_tiles x 32 x 32: A', then its factor (row-major tiles)
+    float* Dinv;   // n_rows x 32 x 32: inverses of the diagonal tiles
+    float* rv;     // FP32 right-hand side of the triangular solves (n_rows x 32)
+    float* yv;
+    float* zv;
+    float* acc;    // backward-solve accumulators
+    double* nrm;   // 2 per CTA: |b'|^2 and |r|^2 partials
+};
+// Host plan: variable graph, components, ordering, blocks, envelope; cluster size
+// chosen from cmax (the largest cluster the device runs).  False when nothing to solve.
+bool sparse_plan(int n_vars, const std::vector<int>& frame_var, const std::vector<int32_t>& pairs, int cmax,
+                 SpPlanHost* out);
+int sparse_cluster_max();
+// Gather, damp, scale, factorise and refine; dx in variable order (6 per variable).
+cudaError_t launch_sparse_solve(const SpPlanDev& pl, const double* blocks, LmState* st, double explicit_lambda,
+                                int refinements, double* dx, cudaStream_t s, int* n_launches);
+
 cudaError_t launch_boxplus(const double* poses, const double* dx_ff, int n_frames, const int* frame_var,
                            const LmState* st, double* cand, cudaStream_t s);
 // Hr = S^T H S, br = S^T b in pose variables (leading fixed dummy block).
@@ -242,7 +331,8 @@ cudaError_t launch_reduce_vars(const double* H, const double* b, int n_frames, c
 
 // Keep the candidate when the cost decreased.  speculative: the candidate was
 // linearised in full, so on acceptance its system (H_cand, b_cand, blocks_cand,
-// cost, count) replaces the current one as well as the poses.
+// cost, count) replaces the current one as well as the poses (H nullptr: only
+// the pair blocks, when no dense system is kept).
 cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_frames, bool speculative,
                           double* H, const double* H_cand, double* b, const double* b_cand, double* blocks,
                           const double* blocks_cand, int m, cudaStream_t s);

@@ -272,15 +272,19 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
                 qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));
                 qz = fmaf(M[6], p.x, fmaf(M[7], p.y, fmaf(M[8], p.z, av[2])));
-                // a3: projection and bounds
-                float u, v, zeta_d;
+                // a3: projection (the column as floor and fraction) and bounds
+                float v, zeta_d;
                 bool ok;
                 if (model == 0) {
                     ok = qz > prm.z_min;
                     const float iz = __fdividef(1.f, qz);
-                    u = fmaf(fx * qx, iz, cx);
+                    const float u = fmaf(fx * qx, iz, cx);
                     v = fmaf(fy * qy, iz, cy);
                     zeta_d = qz;
+                    ok = ok && u >= umin && u < umax;
+                    const float fu = floorf(u);
+                    c0 = (int)fu;
+                    fa = u - fu;
                 } else {
                     // square roots through the hardware reciprocal square root
                     // (~1e-7 relative); a zero radius gives NaN and fails the tests
@@ -288,15 +292,12 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                     const float r2 = fmaf(qz, qz, rxy2);
                     zeta_d = r2 * rsqrtf(r2);
                     ok = zeta_d > prm.z_min;
-                    u = fmaf(fx, atan2_poly(qy, qx), cx);
-                    v = fmaf(fy, atan2_poly(qz, rxy2 * rsqrtf(rxy2)), cy);
+                    spherical_project(qx, qy, qz, rsqrtf(rxy2), fx, fy, cx, cy, P.fxh, P.fxp, c0, fa, v);
                 }
-                ok = ok && v >= 1.f && v < vmax && u >= umin && u < umax;
+                ok = ok && v >= 1.f && v < vmax;
                 if (ok) {
-                    const float fu = floorf(u), fv = floorf(v);
-                    c0 = (int)fu;
+                    const float fv = floorf(v);
                     r0 = (int)fv;
-                    fa = u - fu;
                     fb = v - fv;
                     int cm1, cc, cp1, cp2;
                     stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
@@ -518,7 +519,9 @@ __global__ void __launch_bounds__(32 * kPairSlices) k_pair_reduce(const float* _
         } else if (r >= 3 && c >= 3) {
             val = -R[3 * (c - 3) + (r - 3)];
         }
-        T[t] = val;
+        // a pair whose relative pose is not finite has no residual (H6 = 0, b6 = 0):
+        // its blocks stay 0 instead of 0 x NaN
+        T[t] = isfinite(val) ? val : 0.0;
     }
     __syncthreads();
     if (t < 36) {

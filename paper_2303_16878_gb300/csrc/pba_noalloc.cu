@@ -10,22 +10,22 @@
 //
 // The scratch: `g_noalloc_scratch` below, PBA_NOALLOC_SCRATCH_BYTES per GPU
 // that loads the library, held until the process exits.  It holds, per pair,
-// the FP32 accumulators of the plain linearisation (92 sums), the pair's
-// static data and its FP32 transform.  Host code never dereferences the
-// symbol: on the first call on a device (with that device current) the host
-// looks up its device address with cudaGetSymbolAddress and passes that
-// pointer to the kernels.  Every call reuses the same array: each call zeroes
-// the accumulators it uses before the kernels run, and calls whose device
-// work overlaps (several streams, several threads) race on it.
+// the FP32 accumulators of the plain linearisation (78 + 12 sums), an FP64
+// cost and an exact integer count, the pair's static data and its FP32
+// transform.  Host code never dereferences the symbol: on every call the host
+// looks up its device address on the current device with cudaGetSymbolAddress
+// and passes that pointer to the kernels.  Every call reuses the same array:
+// each call zeroes the accumulators it uses before the kernels run, and calls
+// whose device work overlaps (several streams, several threads) race on it.
 //
 // The kernel is a variant of the plain path's k_plain (pba_plain.cu): one
 // thread per source pixel, FP32 cue images read directly, the full 5 x 12
 // Jacobian [J_i J_j] from the Supp. derivatives, block reduction and FP32
-// atomics into the pair's accumulator; here every pair runs in one launch
-// (blockIdx.y = pair).  The results match pba_get_pair_system of a problem on
-// the same inputs within the parity tolerances.
-#include <mutex>
-
+// atomics into the pair's accumulator (the cost in FP64, the count as an
+// integer); here every pair runs in one launch (blockIdx.y = pair).  The
+// results match pba_get_pair_system of a plain-path problem on the same inputs
+// within the parity tolerances (not bit for bit: the pair transform is formed
+// in another order and the atomics sum in no fixed order).
 #include "../../include/pba.h"
 #include "pba_internal.cuh"
 
@@ -43,7 +43,9 @@ struct NaPair {
 };
 
 struct NaScratch {
-    float acc[PBA_NOALLOC_MAX_PAIRS][kNaStride];
+    float acc[PBA_NOALLOC_MAX_PAIRS][kNaStride];  // 78 + 12 FP32 sums (H upper, b)
+    double cost[PBA_NOALLOC_MAX_PAIRS];           // FP64 sum of the blocks' FP32 partial costs
+    unsigned long long count[PBA_NOALLOC_MAX_PAIRS];  // valid residuals, exact
     NaPair pairs[PBA_NOALLOC_MAX_PAIRS];
 };
 
@@ -59,7 +61,8 @@ struct NaSensor {
 
 __device__ __forceinline__ bool na_valid(const float* c, float rmin, float rmax) {
     const float n2 = c[2] * c[2] + c[3] * c[3] + c[4] * c[4];
-    return c[1] > 0.f && c[1] >= rmin && c[1] <= rmax && n2 > 0.25f;
+    (void)n2;
+    return plain_pixel_valid(c, rmin, rmax);
 }
 
 // Per pair: zero the accumulator and build the FP32 transform
@@ -74,6 +77,8 @@ __global__ void k_na_setup(NaScratch* S, const double* __restrict__ poses, const
     if (q >= m) return;
     for (int k = threadIdx.x; k < kNaStride; k += blockDim.x) S->acc[q][k] = 0.f;
     if (threadIdx.x != 0) return;
+    S->cost[q] = 0.0;
+    S->count[q] = 0ull;
     const double* Xo = xo.v;
     const int i = pairs[2 * q], j = pairs[2 * q + 1];
     if (i < 0 || j < 0 || i >= n_frames || j >= n_frames) {
@@ -300,7 +305,9 @@ __global__ void __launch_bounds__(kNaThreads)
     if (threadIdx.x < kNaAcc) {
         float x = 0.f;
         for (int w8 = 0; w8 < kNaThreads / 32; ++w8) x += s_red[w8][threadIdx.x];
-        atomicAdd(&S->acc[q][threadIdx.x], x);
+        if (threadIdx.x < 90) atomicAdd(&S->acc[q][threadIdx.x], x);
+        else if (threadIdx.x == 90) atomicAdd(&S->cost[q], (double)x);
+        else atomicAdd(&S->count[q], (unsigned long long)x);  // a block's count: an integer <= 256, exact in FP32
     }
 }
 
@@ -316,15 +323,12 @@ __global__ void k_na_expand(const NaScratch* S, double* __restrict__ out) {
     }
     if (t < 12) o[144 + t] = (double)a[78 + t];
     if (t == 0) {
-        o[156] = (double)a[90];
-        o[157] = (double)a[91];
+        o[156] = S->cost[q];
+        o[157] = (double)S->count[q];
         o[158] = 0.0;
         o[159] = 0.0;
     }
 }
-
-std::mutex g_lock;
-NaScratch* g_scratch_ptr[64] = {};
 
 }  // namespace
 }  // namespace pba
@@ -343,17 +347,11 @@ extern "C" int pba_linearize_pairs_noalloc(const pba_sensor* sensor, const pba_c
     if (m == 0) return PBA_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PBA_ECUDA;
-    NaScratch* S = nullptr;
-    {
-        // once per device, with that device current: the device address of the static array
-        std::lock_guard<std::mutex> g(g_lock);
-        if (!g_scratch_ptr[dev]) {
-            void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PBA_ECUDA;
-            g_scratch_ptr[dev] = reinterpret_cast<NaScratch*>(ptr);
-        }
-        S = g_scratch_ptr[dev];
-    }
+    // the device address of the static array on the current device, looked up on
+    // every call (a host-side query; it stays right after a device reset)
+    void* sym = nullptr;
+    if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) return PBA_ECUDA;
+    NaScratch* S = reinterpret_cast<NaScratch*>(sym);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     LinParams prm{};
     prm.w_int = (float)cfg->w_int;
@@ -379,8 +377,8 @@ extern "C" int pba_linearize_pairs_noalloc(const pba_sensor* sensor, const pba_c
     }
     Xo12 xo;
     for (int k = 0; k < 12; ++k) xo.v[k] = sensor->extrinsic[k];
-    const float rmin = (float)cfg->range_min;
-    const float rmax = cfg->range_max > 3.0e38 ? 3.0e38f : (float)cfg->range_max;
+    float rmin, rmax;
+    float_range_limits(cfg->range_min, cfg->range_max, &rmin, &rmax);
     const long long npx = (long long)sensor->width * sensor->height;
     // 1. zero this call's accumulators and build the pair transforms
     k_na_setup<<<m, 128, 0, s>>>(S, poses, pairs, m, n_frames, xo);

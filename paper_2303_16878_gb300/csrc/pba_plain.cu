@@ -21,7 +21,8 @@ constexpr int kPlainStride = 96;
 
 __device__ __forceinline__ bool valid_px(const float* c, float rmin, float rmax) {
     const float n2 = c[2] * c[2] + c[3] * c[3] + c[4] * c[4];
-    return c[1] > 0.f && c[1] >= rmin && c[1] <= rmax && n2 > 0.25f;
+    (void)n2;
+    return plain_pixel_valid(c, rmin, rmax);
 }
 
 template <bool FULL>
@@ -275,8 +276,8 @@ cudaError_t launch_plain(bool full, int pair, const PairStatic* ps, const PairPo
                          double range_max, float* acc, int width, int height, cudaStream_t s) {
     const int npx = width * height;
     const int grid = (npx + kPlainThreads - 1) / kPlainThreads;
-    const float rmin = (float)range_min;
-    const float rmax = range_max > 3.0e38 ? 3.0e38f : (float)range_max;
+    float rmin, rmax;
+    float_range_limits(range_min, range_max, &rmin, &rmax);
     if (full)
         k_plain<true><<<grid, kPlainThreads, 0, s>>>(pair, ps, pp, raw, sensors, src_sensor, prm, rmin, rmax, acc);
     else

@@ -740,7 +740,8 @@ cudaError_t launch_accept(LmState* st, double* poses, const double* cand, int n_
                           const double* blocks_cand, int m, cudaStream_t s) {
     k_accept<<<1, 256, 0, s>>>(st, poses, cand, n_frames, speculative);
     if (speculative) {
-        const long long n6 = 6LL * n_frames;
+        // H == nullptr: no dense system is kept (block-sparse solve), only the pair blocks move
+        const long long n6 = H ? 6LL * n_frames : 0;
         const long long nblk = (long long)kBlockStride * m;
         long long most = n6 * n6 > nblk ? n6 * n6 : nblk;
         int grid = (int)((most + 255) / 256);

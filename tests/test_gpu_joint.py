@@ -6,8 +6,9 @@ then a batch of 16 independent LiDAR problems of 50-400 frames linearised in
 one launch.
 
 Bars: 50 seeded pairs of each configuration against the oracle as in
-test_gpu_large.py (masks outside the decision margin, H12 / b12 1e-4, cost
-1e-5 with the points decided the other way accounted for, at most 1e-5 of
+test_gpu_large.py (masks outside the decision margin; the sampled
+sub-system's H, b 1e-4 and cost 1e-5, each pair's H12 / b12 1e-3 and cost
+1e-4, with the points decided the other way accounted for; at most 1e-5 of
 the residuals (+2) decided the other way); the joint
 refinement lowers the cost and brings the offset to within 1 cm / 0.25 deg
 of the true one; batch problems share no block of H.

