@@ -1,25 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of one Levenberg-Marquardt iteration of photometric bundle
-adjustment (damped solve: FP32 Cholesky with FP64 refinement in one
-thread-block-cluster launch; box-plus update; linearisation of every pair at
-the candidate; reduce, assemble, accept/reject) on one GB300.
+adjustment (damped solve, box-plus update, linearisation of every pair at
+the candidate, reduce, accept/reject) on one GB300.
 
-Default workload: LiDAR spherical-projection BA, 50 frames of 64 x 1024
-(vertical FOV -16.6..+16.6 deg) along a synthetic street, every pair with more
-than 30% overlap, FP16 texels / FP32 residuals / FP64 solve.
+Default workload: the largest single-GPU configuration, the joint LiDAR +
+RGB-D problem: 300 LiDAR frames of 128 x 1024 (vfov +-45 deg) and 600 RGB-D
+frames of 640 x 480 on one hand-held platform in a multi-room hall, camera
+and LiDAR frames of one instant sharing a pose variable (599 variables), the
+camera offset given with a 2 cm / 0.5 deg error (held at its given value by
+the LM step; its refinement uses the adjoint gradient, timed as `adjoint`).
+The other configurations are reported under `configs` (LiDAR 128 x 2048 with
+500 frames, the batch of 16 independent LiDAR problems, the 50-frame LiDAR
+street) and can be made the main line with --workload.
 
 Metric: residuals per second (valid pixel-point residuals linearised over
 the timed iterations / their device time) and ms per iteration.  The timed
 steps are consecutive iterations from the initial poses, after one untimed
-linearisation and the warm-up iterations (the valid-residual count grows a
-little as the poses converge); L2 is flushed (256 MiB write) before each step.
+linearisation and the warm-up iterations; L2 is flushed (256 MiB write)
+before each step.  FP16 texels, FP32 residuals and Jacobians, FP64 pair
+reduction and an FP64-accurate solve (block-sparse FP32 factorisation with
+FP64 refinement for the large pose graphs).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 Under torchrun (N > 1) every rank runs an independent replica of the problem
 on its own GPU (the path has no exchange step); value = all ranks' residuals /
 the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
-host cores (rank 0 only).
+host cores (rank 0 only) on a bounded seeded sample of the workload's pairs.
 """
 from __future__ import annotations
 
@@ -43,20 +50,40 @@ if ROOT not in sys.path:
 
 METRIC = "residuals/sec and ms per GN iteration, batched vs plain GPU path at stated error"
 UNIT = "residuals/s"
-WORKLOAD = ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, "
-            "init noise 10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64-refined solve")
-WORKLOADS = {"street": WORKLOAD,
-             "room": ("rgbd-room 8 frames 160x120 pinhole (f 120), pairs j - i <= 3, init noise 2 cm / 1 deg, "
-                      "FP16 texels / FP32 residuals / FP64-refined solve")}
+WORKLOADS = {
+    "joint": ("joint LiDAR + RGB-D: 300 LiDAR frames 128x1024 (vfov +-45 deg) + 600 RGB-D frames 640x480 "
+              "(f 525) in a multi-room hall, camera and LiDAR of one instant tied (599 pose variables), camera "
+              "offset with a 2 cm / 0.5 deg error, init noise 2 cm / 1 deg, FP16 texels / FP32 residuals / "
+              "FP64-refined block-sparse solve"),
+    "street_graph": ("lidar-street-graph 500 frames 128x2048 spherical (vfov +-22.5 deg), each frame the source of "
+                     "2-20 pairs with >30% overlap, 5% missing returns, init noise 10 cm / 0.5 deg, FP16 texels / "
+                     "FP32 residuals / FP64-refined block-sparse solve"),
+    "batch": ("street-batch: 16 independent LiDAR problems of 50-400 frames 64x1024 in one problem (16 "
+              "components of the pose graph), pairs j - i <= 3 with >30% overlap, FP16 texels / FP32 residuals "
+              "/ FP64-refined block-sparse solve, one cluster per problem"),
+    "hall": ("rgbd-hall 200 frames 640x480 pinhole (f 525) along a closed path through four rooms, depth noise "
+             "1 mm z^2, intensity noise 0.01, pairs by the Sec. IV-B rule, FP16 texels / FP32 residuals / "
+             "FP64-refined solve"),
+    "street": ("lidar-street 50 frames 64x1024 spherical (vfov +-16.6 deg), pairs with >30% overlap, init noise "
+               "10 cm / 0.5 deg, 5% missing returns, FP16 texels / FP32 residuals / FP64-refined solve"),
+    "room": ("rgbd-room 8 frames 160x120 pinhole (f 120), pairs j - i <= 3, init noise 2 cm / 1 deg, "
+             "FP16 texels / FP32 residuals / FP64-refined solve"),
+}
+DEFAULT_WORKLOAD = "joint"
+EXTRA_WORKLOADS = ("street_graph", "batch", "street")
+# graph-construction thresholds per workload (Sec. IV-B): angle, translation, overlap ratio
+BUILD_PAIRS = {"street": (30.0, 40.0, 0.3), "room": (30.0, 1.0, 1.0 / 3.0)}
 
 # Algorithmic FP32 work of the linearisation kernel, counted from the formulas as
-# implemented (FMA = 2 FLOP; square root, division and atan2 = 1):
-# per processed point, transform 18 + spherical projection 13 = 31;
+# implemented (FMA = 2 FLOP; square root, division and arctangent = 1):
+# per processed point, transform 18 + projection 13 (spherical) or 7 (pinhole);
 # per valid residual, taps and interpolation 51, residual / Huber / normal
-# rotation 40, image gradients 118, d pi / d pbar 23, five Jacobian rows and
-# their 6 x 6 accumulation 533 = 765.
-FLOP_PER_POINT_SPHERICAL = 31
-FLOP_PER_RESIDUAL_FULL = 765
+# rotation 40, image gradients 118, d pi / d pbar 23 (spherical) or 9 (pinhole),
+# five Jacobian rows and their 6 x 6 accumulation 533.
+FLOP_PER_POINT = {0: 25, 1: 31}
+FLOP_PER_RESIDUAL = {0: 751, 1: 765}
+FLOP_PER_POINT_SPHERICAL = FLOP_PER_POINT[1]
+FLOP_PER_RESIDUAL_FULL = FLOP_PER_RESIDUAL[1]
 
 
 def measured_hbm(path: str = None):
@@ -71,13 +98,11 @@ def measured_hbm(path: str = None):
         return 6800.0, "fallback: 6.8 TB/s, one earlier GB300 measurement"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch on this
-# workload (ncu --set full capture of k_linearize<1, 1, 0, 3>, one launch after the autotuner's);
-# to be retaken whenever the kernel changes
-LINEARIZE_DRAM_BYTES = (370.882048 + 11.2384) * 1e6
-# the same capture's unit utilisations (fraction of each unit's peak over the launch):
-# SM issue, the L1 data pipe (the gathers), L2, DRAM
-LINEARIZE_NCU_UNITS = {"sm_issue": 0.727, "l1_data_pipe": 0.575, "l2": 0.216, "dram": 0.041}
+# dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch and the
+# unit utilisations (SM issue, L1 data pipe, L2, DRAM) from ncu captures of the
+# current kernel (profiles/), keyed by (workload, occupancy variant, work-item
+# size, tail item size); settings without an entry report null
+LINEARIZE_NCU = {}
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
 NORMAL_MAX_RADIUS = 5
@@ -91,22 +116,45 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3, help="untimed LM iterations before them")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours",
                     help="ours: the GPU library; reference: the FP64 oracle on the host cores")
-    ap.add_argument("--workload", choices=["street", "room"], default="street",
-                    help="street: 50 LiDAR frames of 64 x 1024 (the benchmark); room: 8 RGB-D frames of 160 x 120")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
+                    help="the configuration of the main line (default: the largest single-GPU one)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other configurations (`configs`)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-pair path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run from pinned host buffers")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
+    ap.add_argument("--error-pairs", type=int, default=50, help="pairs of the stated-error comparison")
     return ap.parse_args()
 
 
 def make_workload(name):
+    """The synthetic workload `name` (large ones render on the GPU when one is
+    present, else on the CPU)."""
     from paper_2303_16878_gb300 import synth
+    dev = "cuda"
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            dev = "cpu"
+    except ImportError:
+        dev = "cpu"
     if name == "room":
         return synth.make_rgbd_room()
     if name == "street":
         return synth.make_lidar_street()
+    if name == "hall":
+        return synth.make_rgbd_hall(device=dev)
+    if name == "street_graph":
+        return synth.make_lidar_street_graph(device=dev)
+    if name == "joint":
+        return synth.make_joint_hall(device=dev)
+    if name == "batch":
+        return synth.make_street_batch(device=dev)[0]
     raise ValueError(f"unknown workload {name!r}")
+
+
+def _host(ch):
+    return ch.detach().cpu().numpy() if hasattr(ch, "detach") else np.asarray(ch)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -233,6 +281,82 @@ def reduce_over_ranks(seconds_or_ms: float, units: float, world: int, device=Non
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def _model_split(w, prob, pair_counts=None):
+    """Processed points and (with pair_counts) valid residuals per camera model
+    (0 pinhole, 1 spherical) over the pair list."""
+    pts = {0: 0, 1: 0}
+    res = {0: 0, 1: 0}
+    for q, (i, _) in enumerate(np.asarray(w.pairs).tolist()):
+        m = int(w.sensors[int(w.frame_sensor[i])].model)
+        pts[m] += prob.frame_points(int(i))
+        if pair_counts is not None:
+            res[m] += int(pair_counts[q])
+    return pts, res
+
+
+def time_iterations(prob, init, stream, flush, steps, warmup):
+    """K consecutive LM iterations (graph replays) from the initial poses, each
+    bracketed by CUDA events on the library's stream with L2 flushed before."""
+    import torch
+
+    def one_step():
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.iterate_async(1)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), prob.get_stats()
+
+    prob.set_poses(init)
+    prob.set_lambda(None)
+    prob.linearize()
+    for _ in range(warmup):
+        one_step()
+    ms, nvalid = [], []
+    for _ in range(steps):
+        t, st = one_step()
+        ms.append(t)
+        nvalid.append(st["n_valid"])
+    return ms, nvalid
+
+
+def phase_times(prob, init, flush, steps):
+    """Per-phase device times (events between the phases on the launch stream)."""
+    prob.set_poses(init)
+    prob.set_lambda(None)
+    prob.linearize()
+    phases = {}
+    for _ in range(steps):
+        flush.zero_()
+        _, ph = prob.iterate_timed()
+        for k, v in ph.items():
+            phases.setdefault(k, []).append(v)
+    return {k: float(np.mean(v)) for k, v in phases.items()}
+
+
+def run_config(name, w, stream, flush, steps, warmup, device):
+    """A configuration other than the main one: value, ms per step and the phase
+    split, from `steps` timed iterations."""
+    import paper_2303_16878_gb300 as pba
+    t0 = time.time()
+    prob = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
+                                     solver=pba.PBA_SOLVE_MIXED)
+    init = np.ascontiguousarray(w.poses_init.reshape(-1, 12))
+    variants = prob.autotune(1)
+    tuning = prob.tuning()
+    ms, nvalid = time_iterations(prob, init, stream, flush, steps, warmup)
+    ph = phase_times(prob, init, flush, max(3, steps // 2))
+    pts, _ = _model_split(w, prob)
+    prob.close()
+    return {"workload": WORKLOADS[name], "frames": int(w.n_frames), "pairs": int(len(w.pairs)),
+            "pose_variables": int(w.n_vars) if getattr(w, "frame_var", None) is not None else int(w.n_frames - 1),
+            "steps": steps, "value": float(sum(nvalid) / (sum(ms) / 1e3)), "unit": UNIT,
+            "ms_per_step": float(np.mean(ms)), "residuals_per_iteration": float(np.mean(nvalid)),
+            "points_per_iteration": int(pts[0] + pts[1]), "phase_ms": ph, "autotuned": tuning,
+            "wall_s": time.time() - t0}
+
+
 def run_ours(args, rank, world, device):
     import torch
     import paper_2303_16878_gb300 as pba
@@ -248,30 +372,19 @@ def run_ours(args, rank, world, device):
                                      solver=pba.PBA_SOLVE_MIXED)
     init = np.ascontiguousarray(w.poses_init.reshape(-1, 12))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    n_points_total = sum(prob.frame_points(int(i)) for i, _ in w.pairs)
-
-    def start(p):
-        # every run starts from the initial poses with automatic damping; the
-        # first linearisation is not part of any timed iteration
-        p.set_poses(init)
-        p.set_lambda(None)
-        p.linearize()
-
-    def one_step(p):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        p.iterate_async(1)
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), p.get_stats()
 
     variants = prob.autotune(2)
+    tuning = prob.tuning()
     clocks.wait_first()
-    start(prob)
-    for _ in range(args.warmup):
-        one_step(prob)
-    launches = prob.iteration_launches()
+    # the per-pair system and valid masks at the initial poses, for the stated-error
+    # comparison on a seeded sample of pairs (the CPU leg recomputes them)
+    prob.set_poses(init)
+    prob.set_mask_export(True)
+    prob.linearize()
+    pair_sys0 = prob.get_pair_system()
+    err_pairs = sample_pairs(w, args.error_pairs)
+    masks0 = {q: prob.get_mask(q, prob.frame_points(int(w.pairs[q][0]))) for q in err_pairs}
+    prob.set_mask_export(False)
 
     # timed region: K consecutive iterations
     if world > 1:
@@ -279,38 +392,30 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     epoch0 = time.time()
     wall0 = time.perf_counter()
-    ms, nvalid, stats = [], [], None
-    for _ in range(args.steps):
-        t, stats = one_step(prob)
-        ms.append(t)
-        nvalid.append(stats["n_valid"])
+    ms, nvalid = time_iterations(prob, init, stream, flush, args.steps, args.warmup)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks.mark(epoch0, time.time())
     clk = clocks.stop()
+    launches = prob.iteration_launches()
+    last_counts = prob.get_pair_system()["count"]
     if world > 1:
         torch.distributed.barrier()
     total_ms, res_all = reduce_over_ranks(float(sum(ms)), float(sum(nvalid)), world, device)
     value = res_all / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
-
-    # per-phase device times (same stream, same flush), for the roofline
-    phases = {}
-    start(prob)
-    for _ in range(args.steps):
-        flush.zero_()
-        _, ph = prob.iterate_timed()
-        for k, v in ph.items():
-            phases.setdefault(k, []).append(v)
-    phase_ms = {k: float(np.mean(v)) for k, v in phases.items()}
+    pts, res_split = _model_split(w, prob, last_counts)
+    phase_ms = phase_times(prob, init, flush, args.steps)
 
     out = dict(value=value, ms_per_step=ms_per_step, n_valid=int(nvalid[-1]), n_valid_mean=float(np.mean(nvalid)),
-               launches=launches, clocks=clk,
-               phase_ms=phase_ms, wall_s=wall, n_points=int(n_points_total), n_pairs=int(len(w.pairs)),
-               stats=stats, variants=variants)
+               launches=launches, clocks=clk, phase_ms=phase_ms, wall_s=wall, n_points=int(pts[0] + pts[1]),
+               points_by_model=pts, residual_share_by_model={m: res_split[m] / max(1, sum(res_split.values()))
+                                                             for m in res_split},
+               n_pairs=int(len(w.pairs)), variants=variants, tuning=tuning, workload=args.workload,
+               pose_variables=int(w.n_vars) if getattr(w, "frame_var", None) is not None else int(w.n_frames - 1))
 
     # adjoint of the total cost (pose / extrinsic / image gradients), events on the same stream
-    start(prob)
+    prob.set_poses(init)
     adj = {}
     for images in (False, True):
         ts = []
@@ -325,12 +430,14 @@ def run_ours(args, rank, world, device):
         adj["with_image_gradient_ms" if images else "poses_extrinsic_ms"] = float(np.median(ts))
     out["adjoint"] = adj
 
-    # graph construction (Sec. IV-B) over every same-sensor candidate within 30 deg / 40 m
+    # graph construction (Sec. IV-B) over the same-sensor candidates within the thresholds
+    ang, dist, ratio = BUILD_PAIRS.get(args.workload, (30.0, 1.0, 1.0 / 3.0))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gp, _ = prob.build_pairs(math.radians(30.0), 40.0, 0.3, True)
+    gp, _ = prob.build_pairs(math.radians(ang), dist, ratio, True)
     out["build_pairs"] = {"ms": 1e3 * (time.perf_counter() - t0), "pairs_kept": int(len(gp)),
-                          "criteria": "angle < 30 deg, translation < 40 m, valid ratio > 0.3, sequential edges"}
+                          "criteria": f"angle < {ang:g} deg, translation < {dist:g} m, valid ratio > {ratio:.3g}, "
+                                      "sequential edges"}
 
     # normal estimation (Sec. IV-A) of every frame from its depth, then the rebuild of
     # texels and pixel-points; the problem's later use (e2e) uploads the frames again
@@ -347,48 +454,28 @@ def run_ours(args, rank, world, device):
         nwall.append(1e3 * (time.perf_counter() - t0))
         nts.append(e0.elapsed_time(e1))
     out["normals"] = {"device_ms": float(np.median(nts)), "call_ms": float(np.median(nwall)),
-                      "frames": int(w.n_frames), "scale": NORMAL_SCALE, "max_radius": NORMAL_MAX_RADIUS,
-                      "points_after": int(sum(prob.frame_points(k) for k in range(w.n_frames)))}
+                      "frames": int(w.n_frames), "scale": NORMAL_SCALE, "max_radius": NORMAL_MAX_RADIUS}
 
-    # the same iteration with the FP64 Cholesky solver (phase times only)
-    f64 = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
-                                    solver=pba.PBA_SOLVE_CHOLESKY_F64)
-    f64.autotune(1)
-    f64_solve = []
-    start(f64)
-    for _ in range(max(3, args.steps // 2)):
-        flush.zero_()
-        _, ph = f64.iterate_timed()
-        f64_solve.append(ph["solve"])
-    f64.close()
-    out["solve_update_f64_ms"] = float(np.mean(f64_solve))
-
-    # plain per-pair path on the same workload
-    if not args.no_plain:
-        plain = pba.problem_from_workload(w, path=pba.PBA_PATH_PLAIN, texel=pba.PBA_TEXEL_F32, stream=stream,
-                                          solver=pba.PBA_SOLVE_MIXED)
-        start(plain)
-        for _ in range(max(1, args.warmup)):
-            one_step(plain)
-        pms = []
-        for _ in range(max(3, args.steps // 2)):
-            t, _ = one_step(plain)
-            pms.append(t)
-        plain.close()
-        out["plain_ms_per_step"] = float(np.mean(pms))
-
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers: every frame, the poses
+    # and the iteration's outcome cross the bus in each step
     if not args.no_e2e:
-        chans = torch.from_numpy(w.channels_array()).pin_memory()
+        groups, k = [], 0
+        while k < w.n_frames:
+            j = k
+            while j + 1 < w.n_frames and w.channels[j + 1].shape == w.channels[k].shape:
+                j += 1
+            groups.append((k, torch.from_numpy(np.stack([_host(c) for c in w.channels[k:j + 1]])).pin_memory()))
+            k = j + 1
         poses_h = torch.from_numpy(init.copy()).pin_memory()
         out_h = torch.empty_like(poses_h).pin_memory()
-        h2d = chans.numel() * 4 + poses_h.numel() * 8
+        h2d = sum(g.numel() * 4 for _, g in groups) + poses_h.numel() * 8
         d2h = out_h.numel() * 8 + 48
         walls, ev = [], 0
         for k in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            prob.upload_frames(0, chans)
+            for first, g in groups:
+                prob.upload_frames(first, g)
             prob.set_poses(poses_h)
             prob.set_lambda(None)
             prob.iterate_async(1)
@@ -398,42 +485,90 @@ def run_ours(args, rank, world, device):
             if k >= args.warmup:
                 walls.append(t1 - t0)
                 ev += st["n_valid"]
+        del groups
         wall_max, ev_all = reduce_over_ranks(sum(walls), float(ev), world, device)
-        e2e_local = ev_all / wall_max
-        out["e2e"] = {"value": e2e_local, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": 1e3 * sum(walls) / len(walls)}
+        out["e2e"] = {"value": ev_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(walls) / len(walls)}
     prob.close()
+
+    # the same iteration with the FP64 Cholesky solver (phase times only)
+    f64 = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, stream=stream,
+                                    solver=pba.PBA_SOLVE_CHOLESKY_F64)
+    f64.autotune(1)
+    out["solve_f64_cholesky_ms"] = phase_times(f64, init, flush, 3)["solve"]
+    f64.close()
+
+    # plain per-pair path on the same workload
+    if not args.no_plain:
+        plain = pba.problem_from_workload(w, path=pba.PBA_PATH_PLAIN, texel=pba.PBA_TEXEL_F32, stream=stream,
+                                          solver=pba.PBA_SOLVE_MIXED)
+        pms, _ = time_iterations(plain, init, stream, flush, 3, 1)
+        plain.close()
+        out["plain_ms_per_step"] = float(np.mean(pms))
+    out["pair_system_at_init"] = pair_sys0
+    out["error_masks"] = masks0
+
+    # the other configurations, fewer steps each
+    if not args.no_extra:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        configs = {}
+        for name in EXTRA_WORKLOADS:
+            if name == args.workload:
+                continue
+            wx = make_workload(name)
+            configs[name] = run_config(name, wx, stream, flush, max(3, min(args.steps, 20)), args.warmup, device)
+            del wx
+            torch.cuda.empty_cache()
+        out["configs"] = configs
     return out, w
 
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(w, seconds, seed=0, part=(0, 1)):
+def oracle_sample(w, seconds, seed=0, part=(0, 1), pairs=None, want_blocks=False, masks=None):
     """Time the FP64 oracle's LM iteration work (full linearisation + cost
     re-evaluation) on a seeded sample of pairs of the same workload, one core.
     part = (k, n): only every n-th pair of the seeded order from the k-th on
-    (the slice of worker k of n)."""
+    (the slice of worker k of n).  pairs: the pair indices to take instead (in
+    that order).  The oracle evaluates the GPU arm's precision reading (FP16
+    texels: binary16 target samples).  want_blocks: also return each pair's
+    12 x 12 block, 12-vector, cost, count and points decided the other way,
+    with the GPU's other-way decisions (masks: its valid-point bit words per
+    pair) accounted for (outside the timing)."""
     import oracle
     oracle.build()
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(len(w.pairs))[part[0]::part[1]]
-    s = w.sensors[0]
-    done_res, elapsed, used = 0, 0.0, 0
-    for q in order:
-        i, j = w.pairs[q]
+    params = dict(w.params, texel_f16=1)
+    if pairs is None:
+        rng = np.random.default_rng(seed)
+        pairs = rng.permutation(len(w.pairs))[part[0]::part[1]]
+    done_res, elapsed, used, blocks = 0, 0.0, 0, {}
+    for q in pairs:
+        i, j = (int(x) for x in w.pairs[q])
+        s = w.sensors[int(w.frame_sensor[i])]
+        src, tgt = _host(w.channels[i]), _host(w.channels[j])
         t0 = time.perf_counter()
-        r = oracle.linearize_pair(s, w.params, w.channels[i], w.channels[j], w.poses_init[i], w.poses_init[j])
-        oracle.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs[q:q + 1], w.params,
-                         want_system=False)
+        r = oracle.linearize_pair(s, params, src, tgt, w.poses_init[i], w.poses_init[j])
+        oracle.linearize_pair(s, params, src, tgt, w.poses_init[i], w.poses_init[j])  # the cost pass at the candidate
         elapsed += time.perf_counter() - t0
         done_res += r["count"]
         used += 1
+        if want_blocks:
+            if masks is not None and int(q) in masks:
+                H, b, c, n, nf, _ = oracle.accounted_pair(s, params, src, tgt, w.poses_init[i], w.poses_init[j],
+                                                          masks[int(q)], r)
+            else:
+                H, b, c, n, nf = r["H"], r["b"], r["cost"], r["count"], 0
+            blocks[int(q)] = (H, b, c, n, nf)
         if elapsed >= seconds:
             break
-    return dict(value=done_res / elapsed, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{used} of {len(w.pairs)} pairs (seeded), full linearisation + cost re-evaluation, "
-                       f"{done_res} residuals in {elapsed:.1f} s, single-threaded FP64 C",
-                seconds=elapsed, pairs=used, residuals=done_res)
+    out = dict(value=done_res / max(elapsed, 1e-9), unit=UNIT, cores=1, kind="oracle",
+               sample=f"{used} of {len(w.pairs)} pairs (seeded), full linearisation + cost re-evaluation, "
+                      f"{done_res} residuals in {elapsed:.1f} s, single-threaded FP64 C",
+               seconds=elapsed, pairs=used, residuals=done_res)
+    if want_blocks:
+        out["blocks"] = blocks
+    return out
 
 
 def host_cores() -> int:
@@ -443,10 +578,41 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def _oracle_worker(workload_name, k, n, inbox, outbox):
-    """Worker k of n: builds the workload once, then times its slice of the
-    seeded pair order for every (seconds, seed) it receives (None ends it)."""
-    w = make_workload(workload_name)
+def sample_pairs(w, n_pairs, seed=0):
+    """A seeded sample of pair indices (the stated-error and CPU-baseline sample)."""
+    return [int(q) for q in np.random.default_rng(seed).permutation(len(w.pairs))[:n_pairs]]
+
+
+def sample_slices(w, n_workers, n_pairs, seed=0, masks=None):
+    """A seeded sample of n_pairs pairs split over n_workers: per worker a small
+    workload holding only the frames of its pairs (host arrays), the indices
+    of its pairs in the full list and their GPU masks (when given)."""
+    from paper_2303_16878_gb300 import synth
+    order = sample_pairs(w, n_pairs, seed)
+    out = []
+    for k in range(n_workers):
+        mine = order[k::n_workers]
+        frames = sorted({int(x) for q in mine for x in w.pairs[q]})
+        remap = {f: n for n, f in enumerate(frames)}
+        pairs = np.array([[remap[int(w.pairs[q][0])], remap[int(w.pairs[q][1])]] for q in mine],
+                         dtype=np.int32).reshape(-1, 2)
+        sub = synth.Workload(w.name + "-sample", w.sensors, np.asarray(w.frame_sensor)[frames],
+                             [_host(w.channels[f]) for f in frames], w.poses_gt[frames], w.poses_init[frames],
+                             pairs, dict(w.params))
+        ids = [int(q) for q in mine]
+        out.append((sub, ids, {n: masks[q] for n, q in enumerate(ids) if masks and q in masks}))
+    return out
+
+
+def _oracle_worker(source, k, n, inbox, outbox):
+    """Worker k of n: builds its workload (a name: the whole workload, timing
+    slice k of a seeded pair order; a (workload, pair ids) slice: its sampled
+    pairs) once, then times it for every (seconds, seed, want_blocks) it
+    receives (None ends it)."""
+    if isinstance(source, str):
+        w, ids, masks = make_workload(source), None, None
+    else:
+        w, ids, masks = source
     import oracle
     oracle.build()
     outbox.put(("ready", k))
@@ -454,24 +620,32 @@ def _oracle_worker(workload_name, k, n, inbox, outbox):
         task = inbox.get()
         if task is None:
             return
-        seconds, seed = task
-        outbox.put(oracle_sample(w, seconds, seed=seed, part=(k, n)))
+        seconds, seed, want_blocks = task
+        if ids is None:
+            outbox.put(oracle_sample(w, seconds, seed=seed, part=(k, n)))
+        else:
+            r = oracle_sample(w, seconds, pairs=np.arange(len(w.pairs)), want_blocks=want_blocks, masks=masks)
+            if want_blocks:
+                r["blocks"] = {ids[q]: v for q, v in r["blocks"].items()}
+            outbox.put(r)
 
 
 class OraclePool:
     """The oracle on every host core: n processes started with spawn (safe after
-    CUDA initialisation), each holding the workload.  A sample sends the same
-    (seconds, seed) to all of them at once; they time disjoint slices of one
-    seeded pair order concurrently, and the rate is all residuals over the
-    slowest worker's time."""
+    CUDA initialisation).  `source` is a workload name (each process builds it
+    and times a disjoint slice of one seeded pair order) or a list of
+    (workload, pair ids) slices, one per process (sample_slices).  A sample
+    sends the same task to all of them at once; the rate is all residuals
+    over the slowest worker's time."""
 
-    def __init__(self, workload_name: str, workers: int = None, ready_timeout: float = 300.0):
+    def __init__(self, source, workers: int = None, ready_timeout: float = 300.0):
         import multiprocessing as mp
         ctx = mp.get_context("spawn")
-        self.n = workers or host_cores()
+        self.n = len(source) if not isinstance(source, str) else (workers or host_cores())
+        srcs = [source] * self.n if isinstance(source, str) else list(source)
         self.outbox = ctx.Queue()
         self.inboxes = [ctx.Queue() for _ in range(self.n)]
-        self.procs = [ctx.Process(target=_oracle_worker, args=(workload_name, k, self.n, self.inboxes[k], self.outbox),
+        self.procs = [ctx.Process(target=_oracle_worker, args=(srcs[k], k, self.n, self.inboxes[k], self.outbox),
                                   daemon=True) for k in range(self.n)]
         for pr in self.procs:
             pr.start()
@@ -497,17 +671,20 @@ class OraclePool:
                     raise TimeoutError(f"oracle workers: {len(out)} of {self.n} answered in {timeout:.0f} s")
         return out
 
-    def sample(self, seconds: float, seed: int = 0) -> dict:
+    def sample(self, seconds: float, seed: int = 0, want_blocks: bool = False) -> dict:
         for q in self.inboxes:
-            q.put((seconds, seed))
-        rs = self._collect(3 * seconds + 120)
+            q.put((seconds, seed, want_blocks))
+        rs = self._collect(3 * seconds + 300)
         res = sum(r["residuals"] for r in rs)
         elapsed = max(r["seconds"] for r in rs)
         pairs = sum(r["pairs"] for r in rs)
-        return dict(value=res / elapsed, unit=UNIT, cores=self.n, kind="oracle",
-                    sample=f"{pairs} pairs (seeded, split over {self.n} processes), full linearisation + cost "
-                           f"re-evaluation, {res} residuals in {elapsed:.1f} s, FP64 C, one process per host core",
-                    seconds=elapsed, pairs=pairs, residuals=res)
+        out = dict(value=res / max(elapsed, 1e-9), unit=UNIT, cores=self.n, kind="oracle",
+                   sample=f"{pairs} pairs (seeded, split over {self.n} processes), full linearisation + cost "
+                          f"re-evaluation, {res} residuals in {elapsed:.1f} s, FP64 C, one process per host core",
+                   seconds=elapsed, pairs=pairs, residuals=res)
+        if want_blocks:
+            out["blocks"] = {q: v for r in rs for q, v in r.get("blocks", {}).items()}
+        return out
 
     def close(self):
         for q in self.inboxes:
@@ -521,9 +698,72 @@ class OraclePool:
                 pr.terminate()
 
 
+def stated_error(pair_sys, blocks):
+    """Errors of the GPU's per-pair blocks (at the initial poses) against the
+    oracle's for the sampled pairs, the points the two decided the other way
+    (inside the oracle's decision margins) accounted for: the sampled
+    sub-system's relative Frobenius errors of H and b and the relative cost
+    error (the bars of the iteration's system), each pair's largest, the count
+    difference and the share of residuals decided the other way."""
+    eh, eb, ec, dn = [], [], [], []
+    dH2 = H2 = db2 = b2 = dc = cs = 0.0
+    flipped = res = 0
+    rel = lambda a, r: float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-300))
+    for q, (H, b, c, n, nf) in blocks.items():
+        eh.append(rel(pair_sys["H"][q], H))
+        eb.append(rel(pair_sys["b"][q], b))
+        ec.append(abs(float(pair_sys["cost"][q]) - c) / max(abs(c), 1e-300))
+        dn.append(abs(int(pair_sys["count"][q]) - int(n)))
+        dH2 += float(np.sum((pair_sys["H"][q] - H) ** 2))
+        H2 += float(np.sum(H ** 2))
+        db2 += float(np.sum((pair_sys["b"][q] - b) ** 2))
+        b2 += float(np.sum(b ** 2))
+        dc += abs(float(pair_sys["cost"][q]) - c)
+        cs += c
+        flipped += int(nf)
+        res += int(n)
+    if not eh:
+        return None
+    return {"pairs": len(eh), "residuals": res, "H_rel": (dH2 / H2) ** 0.5, "b_rel": (db2 / b2) ** 0.5,
+            "cost_rel": dc / cs, "bars": {"H": 1e-4, "b": 1e-4, "cost": 1e-5},
+            "per_pair_max": {"H_rel": max(eh), "b_rel": max(eb), "cost_rel": max(ec), "count_diff": max(dn)},
+            "decided_other_way": flipped / max(res, 1),
+            "reference": "FP64 oracle per pair at the initial poses, target intensity and normals sampled as "
+                         "binary16 values (the FP16 texels' reading), points decided the other way inside its "
+                         "decision margins accounted for"}
+
+
+def cpu_legs(args, w, pair_sys=None, masks=None):
+    """cpu_baseline (all host cores, a seeded sample of the workload's pairs
+    split over one process per core), cpu_baseline_one_core and, with the
+    GPU's pair system and masks, the stated error on the sampled pairs."""
+    n = host_cores()
+    one = oracle_sample(w, args.cpu_seconds)
+    try:
+        pool = OraclePool(sample_slices(w, n, max(args.error_pairs, 3 * n), masks=masks))
+        try:
+            cb = pool.sample(args.cpu_seconds, want_blocks=pair_sys is not None)
+        finally:
+            pool.close()
+    except Exception as e:  # the single-process figure still stands
+        cb = dict(one, sample=one["sample"] + f" (parallel run failed: {type(e).__name__})")
+    out = {"cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+           "cpu_baseline_one_core": {k: one[k] for k in ("value", "unit", "cores", "kind", "sample")}}
+    out["cpu_baseline"]["sample"] += " (a seeded sample of the workload's pairs; per-residual rate)"
+    if pair_sys is not None and cb.get("blocks"):
+        out["error"] = stated_error(pair_sys, cb["blocks"])
+    return out
+
+
 def run_reference(args):
     per_step = max(0.5, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
-    pool = OraclePool(args.workload)
+    big = args.workload not in ("room", "street")
+    if big:
+        w = make_workload(args.workload)
+        n = host_cores()
+        pool = OraclePool(sample_slices(w, n, max(50, 3 * n)))
+    else:
+        pool = OraclePool(args.workload)
     cores = pool.n
     vals, secs = [], []
     try:
@@ -553,45 +793,59 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
               hbm_source: str = "measured: MEASURED_PEAKS.json hbm_gbs") -> dict:
     """The GPU arm's JSON line from the measurements in `out` (pure: no device
     access).  Roofline of the dominant kernel: algorithmic FP32 FLOPs of one
-    full linearisation (per valid residual and per processed point, mean
-    valid count of the timed iterations) over its CUDA-event duration, against
-    the nominal FP32 ALU peak at the sampled maximum SM clock."""
+    full linearisation (per valid residual and per processed point, by camera
+    model, mean valid count of the timed iterations) over its CUDA-event
+    duration, against the nominal FP32 ALU peak at the sampled maximum SM
+    clock.  DRAM traffic and unit utilisations come from the ncu capture of
+    the kernel variant the run kept, when one exists for this workload."""
+    workload = out.get("workload", getattr(args, "workload", "street"))
     ph = out["phase_ms"]
     lin_ms = ph["linearize"]
     n_valid = out.get("n_valid_mean", out["n_valid"])
-    flops = n_valid * FLOP_PER_RESIDUAL_FULL + out["n_points"] * FLOP_PER_POINT_SPHERICAL
+    pts = out.get("points_by_model") or {1: out["n_points"], 0: 0}
+    share = out.get("residual_share_by_model") or {1: 1.0, 0: 0.0}
+    flops = sum(n_valid * share[m] * FLOP_PER_RESIDUAL[m] + pts[m] * FLOP_PER_POINT[m] for m in (0, 1))
     sm_max = (out["clocks"] or {}).get("sm_max_mhz") or 2070.0
     peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (lin_ms / 1e3) / 1e12
+    tun = out.get("tuning") or {}
+    ncu = LINEARIZE_NCU.get((workload, int(out["variants"][0]), int(tun.get("chunk", 1024)),
+                             int(tun.get("chunk_tail", 256))))
+    traffic = ncu["dram_bytes"] if ncu else None
     line = {
         "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[getattr(args, "workload", "street")], "frames": n_frames,
-                   "pairs": out["n_pairs"],
+        "config": {"workload": WORKLOADS[workload], "frames": n_frames, "pairs": out["n_pairs"],
+                   "pose_variables": out.get("pose_variables"),
                    "points_per_iteration": out["n_points"], "residuals_per_iteration": n_valid,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "steps": "consecutive LM iterations from the initial poses (one untimed linearisation first)",
-                   "parallelism": f"replicas x{world}", "autotuned_variants": list(out["variants"])},
+                   "parallelism": f"replicas x{world}",
+                   "autotuned": out.get("tuning") or {"variant_full": int(out["variants"][0]),
+                                                      "variant_cost": int(out["variants"][1])}},
         # each residual is a 5-vector (g, d, n_x, n_y, n_z)
         "scalar_residuals_per_s": 5.0 * out["value"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": LINEARIZE_DRAM_BYTES, "kernel": "k_linearize<f16, full>",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_linearize<f16, full>",
                      "kernel_ms": lin_ms, "peak_source": "nominal: SMs x 128 FP32 lanes x 2 x max SM clock",
-                     "hbm": {"traffic_bytes": LINEARIZE_DRAM_BYTES, "peak_gbs": hbm_peak_gbs,
-                             "frac": LINEARIZE_DRAM_BYTES / (lin_ms / 1e3) / 1e9 / hbm_peak_gbs,
+                     "hbm": {"traffic_bytes": traffic, "peak_gbs": hbm_peak_gbs,
+                             "frac": (traffic / (lin_ms / 1e3) / 1e9 / hbm_peak_gbs) if traffic else None,
                              "peak_source": hbm_source},
-                     "ncu_unit_fracs": LINEARIZE_NCU_UNITS,
-                     "binding": "SM instruction issue, then the L1 data pipe of the gathers"},
+                     "ncu_unit_fracs": ncu["units"] if ncu else None,
+                     "binding": "SM instruction issue (FP32 ALU roof); the gather roofs (L1 data pipe, L2, "
+                                "DRAM) from ncu: below the 60% target"},
         "phase_ms": ph,
-        "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|), one thread-block-cluster launch",
-        "solve_f64_cholesky_ms": out["solve_update_f64_ms"],
+        "solver": "FP32 Jacobi-scaled Cholesky + FP64 iterative refinement (|r| <= 1e-10 |b|): block-sparse "
+                  "envelope factorisation, one thread-block cluster per component of the pose graph, above "
+                  "~800 unknowns; one dense cluster launch below",
+        "solve_f64_cholesky_ms": out.get("solve_f64_cholesky_ms", out.get("solve_update_f64_ms")),
         "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
         "gpu_launches": out["launches"] * args.steps,
         "clocks": out["clocks"],
     }
-    for k in ("build_pairs", "normals", "adjoint", "e2e"):
-        if k in out:
+    for k in ("build_pairs", "normals", "adjoint", "e2e", "configs", "error"):
+        if k in out and out[k] is not None:
             line[k] = out[k]
     if "plain_ms_per_step" in out:
         line["plain_ms_per_step"] = out["plain_ms_per_step"]
@@ -620,19 +874,12 @@ def main():
     out, w = run_ours(args, rank, world, device)
     if rank == 0:
         sms = torch.cuda.get_device_properties(device).multi_processor_count
-        line = make_line(args, world, out, w.n_frames, sms, *measured_hbm())
         if not args.no_cpu and world == 1:
-            one = oracle_sample(w, args.cpu_seconds)
-            try:
-                pool = OraclePool(args.workload)
-                try:
-                    cb = pool.sample(args.cpu_seconds)
-                finally:
-                    pool.close()
-            except Exception as e:  # the single-process figure still stands
-                cb = dict(one, sample=one["sample"] + f" (parallel run failed: {type(e).__name__})")
-            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-            line["cpu_baseline_one_core"] = {k: one[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            out.update(cpu_legs(args, w, out.get("pair_system_at_init"), out.get("error_masks")))
+        line = make_line(args, world, out, w.n_frames, sms, *measured_hbm())
+        for k in ("cpu_baseline", "cpu_baseline_one_core"):
+            if k in out:
+                line[k] = out[k]
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

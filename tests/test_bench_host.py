@@ -33,12 +33,13 @@ def test_clock_summary_widens_a_short_region():
 
 def test_json_line_carries_the_contract_keys_and_its_arithmetic():
     """The GPU arm's line from a fake measurement: contract keys, the roofline
-    arithmetic (algorithmic FLOPs over the kernel's event time against the
-    nominal ALU peak) and JSON serialisability."""
+    arithmetic (algorithmic FLOPs by camera model over the kernel's event time
+    against the nominal ALU peak; DRAM traffic from the ncu table of the kept
+    variant, null without an entry) and JSON serialisability."""
     import argparse
     import json
     import bench
-    args = argparse.Namespace(steps=100, warmup=3)
+    args = argparse.Namespace(steps=100, warmup=3, workload="street")
     out = dict(value=1.7e10, ms_per_step=1.3, n_valid=22_000_000, n_valid_mean=21_500_000.0, n_points=68_000_000,
                n_pairs=1170, launches=10, variants=(1, 2),
                clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 6, "window": "timed region"},
@@ -56,8 +57,21 @@ def test_json_line_carries_the_contract_keys_and_its_arithmetic():
     assert abs(r["achieved"] - flops / 1.08e-3 / 1e12) < 1e-9 * r["achieved"]
     assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12 and 0 < r["frac"] < 1
-    assert abs(r["hbm"]["frac"] - bench.LINEARIZE_DRAM_BYTES / 1.08e-3 / 1e9 / 6693.8) < 1e-12
     assert abs(line["speedup_vs_plain"] - 29.0 / 1.3) < 1e-12
+    # traffic: null without a capture of the kept variant, the capture's bytes with one
+    assert r["traffic"] is None and r["hbm"]["frac"] is None
+    bench.LINEARIZE_NCU[("street", 1, 1024, 256)] = {"dram_bytes": 4.0e8, "units": {"sm_issue": 0.7}}
+    try:
+        r = bench.make_line(args, 1, out, 50, 152, 6693.8)["roofline"]
+    finally:
+        bench.LINEARIZE_NCU.pop(("street", 1, 1024, 256))
+    assert r["traffic"] == 4.0e8 and abs(r["hbm"]["frac"] - 4.0e8 / 1.08e-3 / 1e9 / 6693.8) < 1e-12
+    # a mixed pinhole / spherical workload counts each model's points and residuals
+    out2 = dict(out, points_by_model={0: 10_000_000, 1: 5_000_000}, residual_share_by_model={0: 0.75, 1: 0.25})
+    r2 = bench.make_line(args, 1, out2, 50, 152, 6693.8)["roofline"]
+    f2 = (21_500_000.0 * (0.75 * bench.FLOP_PER_RESIDUAL[0] + 0.25 * bench.FLOP_PER_RESIDUAL[1])
+          + 10_000_000 * bench.FLOP_PER_POINT[0] + 5_000_000 * bench.FLOP_PER_POINT[1])
+    assert abs(r2["achieved"] - f2 / 1.08e-3 / 1e12) < 1e-9 * r2["achieved"]
 
 
 def test_reference_arm_line(monkeypatch, capsys):
@@ -134,14 +148,15 @@ def test_main_wires_the_measurement_into_one_line(monkeypatch, capsys):
         def __init__(self, name, workers=None):
             self.n = 16
 
-        def sample(self, seconds, seed=0):
+        def sample(self, seconds, seed=0, want_blocks=False):
             return dict(value=8.0e6, unit=bench.UNIT, cores=16, kind="oracle", sample="fake16", seconds=seconds)
 
         def close(self):
             pass
 
     monkeypatch.setattr(bench, "OraclePool", FakePool)
-    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "7", "--warmup", "3"])
+    monkeypatch.setattr(bench, "sample_slices", lambda w, n, k, masks=None: [])
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "7", "--warmup", "3", "--workload", "street"])
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
     bench.main()
@@ -180,3 +195,40 @@ def test_oracle_pool_reports_a_dead_worker_quickly():
     with pytest.raises(RuntimeError):
         bench.OraclePool("no-such-workload", workers=2, ready_timeout=120.0)
     assert time.time() - t0 < 60.0
+
+
+def test_stated_error_is_the_sampled_subsystem_error():
+    """stated_error: the stacked blocks' relative Frobenius errors, each pair's
+    largest, the count difference and the share decided the other way."""
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(3)
+    H = rng.normal(size=(3, 12, 12))
+    b = rng.normal(size=(3, 12))
+    ps = {"H": H + 1e-6 * rng.normal(size=H.shape), "b": b.copy(), "cost": np.array([1.0, 2.0, 3.0]),
+          "count": np.array([10, 20, 31])}
+    blocks = {0: (H[0], b[0], 1.0, 10, 0), 1: (H[1], b[1], 2.0, 20, 1), 2: (H[2], b[2], 3.3, 30, 2)}
+    e = bench.stated_error(ps, blocks)
+    dH = np.sqrt(sum(np.sum((ps["H"][q] - H[q]) ** 2) for q in range(3)) / np.sum(H ** 2))
+    assert abs(e["H_rel"] - dH) < 1e-15 and e["b_rel"] == 0.0
+    assert abs(e["cost_rel"] - 0.3 / 6.3) < 1e-12 and e["per_pair_max"]["count_diff"] == 1
+    assert e["decided_other_way"] == 3 / 60 and e["pairs"] == 3
+
+
+def test_sample_slices_keep_only_their_frames():
+    """The CPU legs' slices: disjoint seeded pairs, each slice's frames
+    renumbered, the same channels and poses as the full workload."""
+    import numpy as np
+    import bench
+    from conftest import workload
+    w = workload("room")
+    sl = bench.sample_slices(w, 3, 9, masks={q: np.array([q], dtype=np.uint32) for q in range(len(w.pairs))})
+    ids = [q for _, qs, _ in sl for q in qs]
+    assert len(ids) == 9 and len(set(ids)) == 9
+    for sub, qs, masks in sl:
+        assert sorted(masks) == list(range(len(qs)))
+        for n, q in enumerate(qs):
+            i, j = w.pairs[q]
+            si, sj = sub.pairs[n]
+            assert np.array_equal(sub.channels[si], w.channels[i]) and np.array_equal(sub.channels[sj], w.channels[j])
+            assert np.array_equal(sub.poses_init[si], w.poses_init[i]) and masks[n][0] == q
