@@ -102,7 +102,11 @@ def measured_hbm(path: str = None):
 # unit utilisations (SM issue, L1 data pipe, L2, DRAM) from ncu captures of the
 # current kernel (profiles/), keyed by (workload, occupancy variant, work-item
 # size, tail item size); settings without an entry report null
-LINEARIZE_NCU = {}
+LINEARIZE_NCU = {
+    # profiles/k_linearize_lidar_street_50x64x1024.md (ncu --set full, one launch at the initial poses)
+    ("street", 1, 2048, 256): {"dram_bytes": 446.6e6 + 8.8e6,
+                               "units": {"sm_issue": 0.697, "l1_data_pipe": 0.583, "l2": 0.221, "dram": 0.056}},
+}
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
 NORMAL_MAX_RADIUS = 5
@@ -124,6 +128,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     ap.add_argument("--error-pairs", type=int, default=50, help="pairs of the stated-error comparison")
+    ap.add_argument("--tuning", default=None, metavar="VF,VC,CHUNK,TAIL",
+                    help="apply this linearisation tuning (variants of the full and cost-only pass, work-item and "
+                         "tail item size) to the main workload instead of autotuning it (pins the launch "
+                         "configuration of a profile)")
     return ap.parse_args()
 
 
@@ -373,8 +381,14 @@ def run_ours(args, rank, world, device):
     init = np.ascontiguousarray(w.poses_init.reshape(-1, 12))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
-    variants = prob.autotune(2)
-    tuning = prob.tuning()
+    if args.tuning:
+        vf, vc, chunk, tail = (int(x) for x in args.tuning.split(","))
+        prob.set_tuning(dict(variant_full=vf, variant_cost=vc, chunk=chunk, chunk_tail=tail))
+        variants = (vf, vc)
+        tuning = dict(prob.tuning(), given=True)
+    else:
+        variants = prob.autotune(2)
+        tuning = prob.tuning()
     clocks.wait_first()
     # the per-pair system and valid masks at the initial poses, for the stated-error
     # comparison on a seeded sample of pairs (the CPU leg recomputes them)
@@ -459,36 +473,61 @@ def run_ours(args, rank, world, device):
     # end to end through the C ABI from pinned host buffers: every frame, the poses
     # and the iteration's outcome cross the bus in each step
     if not args.no_e2e:
-        groups, k = [], 0
-        while k < w.n_frames:
-            j = k
-            while j + 1 < w.n_frames and w.channels[j + 1].shape == w.channels[k].shape:
-                j += 1
-            groups.append((k, torch.from_numpy(np.stack([_host(c) for c in w.channels[k:j + 1]])).pin_memory()))
-            k = j + 1
+        # every frame back to back in frame order, in page-locked host memory
+        flat = torch.from_numpy(np.concatenate([_host(c).reshape(-1) for c in w.channels])).pin_memory()
         poses_h = torch.from_numpy(init.copy()).pin_memory()
         out_h = torch.empty_like(poses_h).pin_memory()
-        h2d = sum(g.numel() * 4 for _, g in groups) + poses_h.numel() * 8
+        h2d = flat.numel() * 4 + poses_h.numel() * 8
         d2h = out_h.numel() * 8 + 48
-        walls, ev = [], 0
-        for k in range(args.warmup + args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for first, g in groups:
-                prob.upload_frames(first, g)
+
+        def e2e_steps(n, one):
+            walls, ev = [], 0
+            for k in range(n):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = one()
+                prob._check(prob._lib.pba_get_poses(prob._h, out_h.data_ptr()), "get_poses")
+                walls.append(time.perf_counter() - t0)
+                ev += st["n_valid"]
+            return walls, ev
+
+        def overlapped():
+            # pba_iterate_frames: each pair is linearised as soon as its frames have
+            # arrived, while later frames are still being copied; then the damped
+            # step and the cost at the candidate
+            prob.set_lambda(None)
+            return prob.iterate_frames(flat, poses_h)
+
+        def sequential():
+            # the same inputs through pba_upload_frames (each run of same-size frames,
+            # synchronising), pba_set_poses and pba_iterate
+            off = 0
+            k = 0
+            while k < w.n_frames:
+                j = k
+                while j + 1 < w.n_frames and w.channels[j + 1].shape == w.channels[k].shape:
+                    j += 1
+                shape = (j - k + 1,) + tuple(w.channels[k].shape)
+                n = int(np.prod(shape))
+                prob.upload_frames(k, flat[off:off + n].view(shape))
+                off += n
+                k = j + 1
             prob.set_poses(poses_h)
             prob.set_lambda(None)
-            prob.iterate_async(1)
-            st = prob.get_stats()
-            prob._check(prob._lib.pba_get_poses(prob._h, out_h.data_ptr()), "get_poses")
-            t1 = time.perf_counter()
-            if k >= args.warmup:
-                walls.append(t1 - t0)
-                ev += st["n_valid"]
-        del groups
+            return prob.iterate()
+
+        e2e_steps(args.warmup, overlapped)
+        walls, ev = e2e_steps(args.steps, overlapped)
         wall_max, ev_all = reduce_over_ranks(sum(walls), float(ev), world, device)
+        e2e_steps(1, sequential)
+        seq, _ = e2e_steps(3, sequential)
         out["e2e"] = {"value": ev_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(walls) / len(walls)}
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(walls) / len(walls),
+                      "call": "pba_iterate_frames (pinned host frames and poses) + pba_get_poses",
+                      "sequential_ms_per_step": 1e3 * float(np.mean(seq)),
+                      "sequential_call": "pba_upload_frames per image size + pba_set_poses + pba_iterate + "
+                                         "pba_get_poses"}
+        del flat
     prob.close()
 
     # the same iteration with the FP64 Cholesky solver (phase times only)

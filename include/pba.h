@@ -332,6 +332,30 @@ int pba_set_lambda(pba_problem* p, double lambda);
  * PBA_ENOTREADY (poses or pairs not set), PBA_ECUDA. */
 int pba_iterate(pba_problem* p, pba_iter_stats* stats);
 
+/* One Levenberg-Marquardt iteration (Sec. IV-C) on new images of all N
+ * frames: sets the poses (host memory, N x 12; NULL keeps the current ones),
+ * uploads channels, linearises at the poses, damps and solves, and evaluates
+ * F at the candidate (the system there is not formed: the next iteration
+ * linearises afresh) before accepting or rejecting it.  channels holds every
+ * frame back to back in frame order, each height x width x 5 float32 of its
+ * sensor as in pba_upload_frames (the layout pba_get_channels writes for
+ * frames 0 .. N-1), in host memory; page-locked memory lets the copies overlap
+ * the computation.  Once every frame has been uploaded before, the frames are
+ * copied in lanes of whole frames in frame order, each lane packed as soon as
+ * it has arrived, and the work items of each pair are linearised as soon as
+ * both its frames are packed, while later lanes are still in flight.  That
+ * linearisation uses the pair plan of the previous point counts; when a
+ * frame's count has changed, the plan is rebuilt and the pass redone before
+ * the step (the same result, without the overlap).  Before every frame has
+ * been uploaded: pba_upload_frames of each run of same-size frames, then the
+ * iteration.  The result equals pba_upload_frames, pba_linearize and one
+ * damped step with the device-side lambda schedule.  channels must stay
+ * unchanged until the call returns.  Fills stats (may be NULL; n_valid is the
+ * residual count of the linearisation at the given poses); synchronises.  Errors: PBA_EINVAL (p or
+ * channels NULL), PBA_ENOTREADY (pairs not set, or poses neither given nor
+ * set), PBA_ECUDA. */
+int pba_iterate_frames(pba_problem* p, const float* channels, const double* poses, pba_iter_stats* stats);
+
 /* Enqueue n iterations as replays of one captured CUDA graph without
  * synchronising; pba_get_stats() then reads the last iteration's outcome.
  * Errors: as pba_iterate, and PBA_EINVAL for n < 0. */
@@ -448,10 +472,10 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
 /* Occupancy variants of the batched linearisation kernel: register budgets
- * for 2, 3 or 4 (full pass) and 3, 4 or 5 (cost-only pass) blocks of 256
- * threads per SM, variants 0, 1, 2.  The results agree up to float32
+ * for 4, 6, 7 or 8 (full pass) and 6, 7, 9 or 10 (cost-only pass) blocks of
+ * 128 threads per SM, variants 0 .. 3.  The results agree up to float32
  * summation order. */
-#define PBA_N_VARIANTS 3
+#define PBA_N_VARIANTS 4
 
 /* Tune the batched linearisation on this problem by timing it (each setting
  * launched repeats + 1 times, the first as warm-up): for the full pass every
@@ -487,6 +511,15 @@ int pba_get_tuning(pba_problem* p, pba_tuning* out);
 /* Set the variants explicitly (e.g. to reproduce a tuned configuration).
  * Errors: PBA_EINVAL (a variant outside [0, PBA_N_VARIANTS)). */
 int pba_set_variants(pba_problem* p, int variant_full, int variant_cost);
+
+/* Apply a tuning given by the caller (e.g. one pba_get_tuning reported in an
+ * earlier process) without timing anything: its variants, work-item size and
+ * tail item size; from_cache, ms_full and ms_cost are ignored (reported as 0
+ * afterwards).  Rebuilds the pair plan when the work items change.  On the
+ * plain path only the values are recorded.  Errors: PBA_EINVAL (tuning NULL, a
+ * variant outside [0, PBA_N_VARIANTS), chunk not a multiple of 32 in
+ * [32, 8192], chunk_tail not a multiple of 32 in [32, chunk]), PBA_ECUDA. */
+int pba_set_tuning(pba_problem* p, const pba_tuning* tuning);
 
 /* Instrumentation: one iteration like pba_iterate, enqueued launch by launch
  * (not as a graph) with CUDA events recorded on the problem's stream between

@@ -363,6 +363,37 @@ class Problem:
         self._check(self._lib.pba_iterate(self._h, ctypes.byref(s)), "iterate")
         return _stats(s)
 
+    def iterate_frames(self, channels, poses=None) -> Dict:
+        """pba_iterate_frames: one LM iteration on new images of every frame.
+        channels: host float32 holding all frames back to back in frame order
+        (each H x W x 5 of its sensor), a numpy array or a CPU torch tensor
+        (page-locked, e.g. .pin_memory(), for the copies to overlap the
+        linearisation); poses: (N, 3, 4) / (N, 12) host values or None."""
+        total = 5 * sum(self._sizes[int(self._fs[k])][0] * self._sizes[int(self._fs[k])][1]
+                        for k in range(self.n_frames))
+        if _is_torch(channels):
+            if channels.is_cuda or str(channels.dtype) != "torch.float32" or not channels.is_contiguous():
+                raise ValueError("channels must be a contiguous float32 host tensor")
+            n, ptr, keep = channels.numel(), channels.data_ptr(), channels
+        else:
+            keep = np.ascontiguousarray(channels, dtype=np.float32)
+            n, ptr = keep.size, keep.ctypes.data
+        if n != total:
+            raise ValueError(f"channels must hold {total} floats (every frame, H x W x 5), got {n}")
+        pp = None
+        if poses is not None:
+            if _is_torch(poses):
+                poses = poses.detach().cpu().numpy()
+            pp = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
+            if pp.size != 12 * self.n_frames:
+                raise ValueError(f"poses must hold {self.n_frames} x 12 values")
+        s = _lib.PbaIterStats()
+        self._check(self._lib.pba_iterate_frames(self._h, ctypes.c_void_p(ptr),
+                                                 None if pp is None else pp.ctypes.data_as(ctypes.c_void_p),
+                                                 ctypes.byref(s)), "iterate_frames")
+        del keep
+        return _stats(s)
+
     def iterate_async(self, n: int = 1):
         self._check(self._lib.pba_iterate_async(self._h, int(n)), "iterate_async")
 
@@ -394,6 +425,14 @@ class Problem:
         self._check(self._lib.pba_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
         return dict(variant_full=t.variant_full, variant_cost=t.variant_cost, chunk=t.chunk,
                     chunk_tail=t.chunk_tail, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost)
+
+    def set_tuning(self, tuning: Dict):
+        """Apply a tuning as tuning() reports it (variant_full, variant_cost,
+        chunk, chunk_tail; other keys ignored) without timing anything."""
+        t = _lib.PbaTuning()
+        t.variant_full, t.variant_cost = int(tuning["variant_full"]), int(tuning["variant_cost"])
+        t.chunk, t.chunk_tail = int(tuning["chunk"]), int(tuning["chunk_tail"])
+        self._check(self._lib.pba_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
 
     def set_variants(self, variant_full: int, variant_cost: int):
         """Occupancy variants of the linearisation kernel (0 .. PBA_N_VARIANTS - 1)."""

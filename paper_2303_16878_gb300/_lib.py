@@ -41,13 +41,14 @@ ERROR_NAMES = {PBA_EINVAL: "PBA_EINVAL", PBA_ENOMEM: "PBA_ENOMEM", PBA_ECUDA: "P
 EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba_upload_frames",
            "pba_frame_points", "pba_set_poses", "pba_get_poses", "pba_set_pairs", "pba_linearize",
            "pba_get_system", "pba_get_pair_system", "pba_set_mask_export", "pba_get_mask", "pba_solve_step",
-           "pba_set_lambda", "pba_iterate", "pba_iterate_async", "pba_get_stats", "pba_iteration_launches",
+           "pba_set_lambda", "pba_iterate", "pba_iterate_frames", "pba_iterate_async", "pba_get_stats",
+           "pba_iteration_launches",
            "pba_iterate_timed", "pba_linearize_pairs_noalloc", "pba_autotune", "pba_get_tuning", "pba_build_pairs",
            "pba_set_extrinsic", "pba_cost_gradient", "pba_tangent_gradient", "pba_estimate_normals", "pba_get_channels",
            "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
-           "pba_set_variants", "pba_refine_extrinsic",
+           "pba_set_variants", "pba_set_tuning", "pba_refine_extrinsic",
            "pba_get_extrinsic", "pba_set_offset_free"]
-PBA_N_VARIANTS = 3
+PBA_N_VARIANTS = 4
 PBA_MAX_LEVELS = 8
 PBA_NORMALS_MAX_RADIUS = 32
 PBA_N_PHASES = 5
@@ -140,6 +141,8 @@ def load(build_if_missing: bool = True):
             "pba_build_pyramid": ([vp, ctypes.c_int], ctypes.c_int),
             "pba_set_variables": ([vp, P(ctypes.c_int32), ctypes.c_int], ctypes.c_int),
             "pba_set_variants": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "pba_set_tuning": ([vp, P(PbaTuning)], ctypes.c_int),
+            "pba_iterate_frames": ([vp, vp, vp, P(PbaIterStats)], ctypes.c_int),
             "pba_get_extrinsic": ([vp, ctypes.c_int, vp], ctypes.c_int),
             "pba_set_offset_free": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "pba_refine_extrinsic": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, P(ctypes.c_double),

@@ -42,6 +42,22 @@ struct pba_problem {
     static constexpr int kCopyLanes = 4;
     cudaStream_t copy_streams[kCopyLanes - 1] = {};
     cudaEvent_t copy_events[kCopyLanes] = {};
+    // pba_iterate_frames: the frames arrive in lanes of whole frames (copied in
+    // order on lane_copy, packed on lane_pack); the work items of the pairs whose
+    // frames have all arrived with lane l form segment l of d_chunks_ready, whose
+    // linearisation (alternately on the problem's stream and lane_lin) waits for
+    // that lane only
+    static constexpr int kFrameLanes = 8;
+    cudaStream_t lane_copy = nullptr, lane_pack = nullptr, lane_lin = nullptr;
+    cudaEvent_t lane_start = nullptr, lane_lin_start = nullptr, lane_lin_done = nullptr;
+    cudaEvent_t lane_copied[kFrameLanes] = {}, lane_ready[kFrameLanes] = {};
+    int4* d_chunks_ready = nullptr;
+    int n_chunks_ready_alloc = 0;
+    std::vector<int> ready_first;  // lane boundaries (frames) d_chunks_ready was ordered for
+    std::vector<int> ready_seg;    // segment boundaries in d_chunks_ready
+    long long plan_serial = 0, ready_serial = -1;
+    int* d_seg_queue = nullptr;    // one work-queue counter per segment
+    int* h_counts = nullptr;       // pinned: point counts read back after the overlapped pass
     std::string err;
 
     // frames
@@ -215,6 +231,7 @@ void free_pair_buffers(pba_problem* p) {
     p->M = 0;
     p->n_chunks = 0;
     p->n_tasks = 0;
+    ++p->plan_serial;  // any order of the work items built for the previous plan is stale
 }
 
 void free_sparse(pba_problem* p) {
@@ -916,6 +933,17 @@ void pba_destroy(pba_problem* p) {
         if (c) cudaStreamDestroy(c);
     for (cudaEvent_t& e : p->copy_events)
         if (e) cudaEventDestroy(e);
+    dfree(p->d_chunks_ready);
+    dfree(p->d_seg_queue);
+    if (p->h_counts) cudaFreeHost(p->h_counts);
+    for (cudaStream_t c : {p->lane_copy, p->lane_pack, p->lane_lin})
+        if (c) cudaStreamDestroy(c);
+    for (cudaEvent_t e : {p->lane_start, p->lane_lin_start, p->lane_lin_done})
+        if (e) cudaEventDestroy(e);
+    for (int l = 0; l < p->kFrameLanes; ++l) {
+        if (p->lane_copied[l]) cudaEventDestroy(p->lane_copied[l]);
+        if (p->lane_ready[l]) cudaEventDestroy(p->lane_ready[l]);
+    }
     if (p->own_stream) cudaStreamDestroy(p->own_stream);
     delete p;
 }
@@ -1161,7 +1189,7 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
     // with a whole long item while the others idle
     long long total_pts = 0;
     for (int q = 0; q < m; ++q) total_pts += ps[q].n_points;
-    const long long resident = (long long)std::max(p->grid_full, 1) * 8;
+    const long long resident = (long long)std::max(p->grid_full, 1) * (kLinThreads / 32);
     const long long tail_start = total_pts - std::min(total_pts / 4, resident * p->chunk);
     long long done_pts = 0;
     for (int oi = 0; oi < m; ++oi) {
@@ -1170,7 +1198,7 @@ int pba_set_pairs(pba_problem* p, const int32_t* pairs, int m) {
         for (int s = 0; s < ps[q].n_points;) {
             const int size = done_pts + s >= tail_start ? p->chunk_tail : p->chunk;
             const int n = std::min(size, ps[q].n_points - s);
-            chunks.push_back(make_int4(q, s, n, 0));
+            chunks.push_back(make_int4(q, s, n, (int)chunks.size()));  // pair, first point, count, slot
             s += n;
         }
         done_pts += ps[q].n_points;
@@ -1486,6 +1514,154 @@ int pba_set_lambda(pba_problem* p, double lambda) {
     CUDA_TRY(p, cudaMemcpyAsync(&p->d_state->lambda, &v, sizeof v, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     return PBA_OK;
+}
+
+// The plan's work items ordered by the lane in which the last of their pair's
+// two frames arrives (lanes: frame ranges [first[l], first[l + 1])), within a
+// lane the long items first; cached for the plan and lane boundaries.
+static int build_ready_order(pba_problem* p, const std::vector<int>& first) {
+    if (p->ready_serial == p->plan_serial && p->ready_first == first) return PBA_OK;
+    const int L = (int)first.size() - 1;
+    std::vector<int4> items(p->n_chunks);
+    CUDA_TRY(p, cudaMemcpyAsync(items.data(), p->d_chunks, sizeof(int4) * items.size(), cudaMemcpyDeviceToHost,
+                                p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    std::vector<int> lane_of(p->N);
+    for (int l = 0; l < L; ++l)
+        for (int k = first[l]; k < first[l + 1]; ++k) lane_of[k] = l;
+    std::vector<int> key(items.size());
+    std::vector<int> seg(L + 1, 0);
+    for (size_t c = 0; c < items.size(); ++c) {
+        const int q = items[c].x;
+        key[c] = std::max(lane_of[p->pairs[2 * q]], lane_of[p->pairs[2 * q + 1]]);
+        ++seg[key[c] + 1];
+    }
+    for (int l = 0; l < L; ++l) seg[l + 1] += seg[l];
+    std::vector<int4> ordered(items.size());
+    std::vector<int> fill(seg.begin(), seg.end() - 1);
+    for (size_t c = 0; c < items.size(); ++c) ordered[fill[key[c]]++] = items[c];
+    for (int l = 0; l < L; ++l)  // the short items end each segment, as they end the plan
+        std::stable_sort(ordered.begin() + seg[l], ordered.begin() + seg[l + 1],
+                         [](const int4& a, const int4& b) { return a.z > b.z; });
+    if (p->n_chunks_ready_alloc < p->n_chunks) {
+        dfree(p->d_chunks_ready);
+        p->n_chunks_ready_alloc = 0;
+        CUDA_TRY(p, cudaMalloc((void**)&p->d_chunks_ready, sizeof(int4) * (size_t)p->n_chunks));
+        p->n_chunks_ready_alloc = p->n_chunks;
+    }
+    CUDA_TRY(p, cudaMemcpy(p->d_chunks_ready, ordered.data(), sizeof(int4) * ordered.size(), cudaMemcpyHostToDevice));
+    p->ready_first = first;
+    p->ready_seg = seg;
+    p->ready_serial = p->plan_serial;
+    return PBA_OK;
+}
+
+int pba_iterate_frames(pba_problem* p, const float* channels, const double* poses, pba_iter_stats* stats) {
+    if (!p) return PBA_EINVAL;
+    if (!channels) return fail(p, PBA_EINVAL, "iterate_frames: channels is NULL");
+    cudaSetDevice(p->device);
+    int st;
+    if (poses && (st = pba_set_poses(p, poses, 0))) return st;
+    if ((st = ready(p))) return st;
+    bool overlap = p->cfg.path == PBA_PATH_BATCHED && p->points_known && p->n_chunks > 0;
+    for (int k = 0; k < p->N && overlap; ++k) overlap = p->uploaded[k] != 0;
+    int nl = 0;
+    if (!overlap) {
+        // frames not uploaded before (no plan to start from): the upload of each run
+        // of same-size frames, then the linearisation
+        for (int k = 0; k < p->N;) {
+            const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+            int j = k + 1;
+            while (j < p->N && p->sensors[p->frame_sensor[j]].width == S.width &&
+                   p->sensors[p->frame_sensor[j]].height == S.height)
+                ++j;
+            if ((st = pba_upload_frames(p, k, j - k, channels + 5 * p->px_off[k], 0))) return st;
+            k = j;
+        }
+        if ((st = ready(p))) return st;
+        if ((st = enqueue_linearize(p, p->stream, &nl))) return st;
+    } else {
+        if (!p->lane_copy) {
+            for (cudaStream_t* c : {&p->lane_copy, &p->lane_pack, &p->lane_lin})
+                CUDA_TRY(p, cudaStreamCreateWithFlags(c, cudaStreamNonBlocking));
+            for (cudaEvent_t* e : {&p->lane_start, &p->lane_lin_start, &p->lane_lin_done})
+                CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            for (int l = 0; l < p->kFrameLanes; ++l) {
+                CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_copied[l], cudaEventDisableTiming));
+                CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_ready[l], cudaEventDisableTiming));
+            }
+            CUDA_TRY(p, cudaMalloc((void**)&p->d_seg_queue, sizeof(int) * p->kFrameLanes));
+            CUDA_TRY(p, cudaMallocHost((void**)&p->h_counts, sizeof(int) * (size_t)p->N));
+        }
+        // lanes of whole frames, about equal in bytes
+        std::vector<int> first(1, 0);
+        for (int l = 1; l < p->kFrameLanes; ++l) {
+            const long long target = p->total_px * l / p->kFrameLanes;
+            int k = first.back() + 1;
+            while (k < p->N && p->px_off[k] < target) ++k;
+            if (k < p->N) first.push_back(k);
+        }
+        first.push_back(p->N);
+        const int L = (int)first.size() - 1;
+        if ((st = build_ready_order(p, first))) return st;
+        // the copies start once earlier work on the frames' buffers is done; each
+        // lane is packed as soon as it has arrived
+        CUDA_TRY(p, cudaEventRecord(p->lane_start, p->stream));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->lane_copy, p->lane_start, 0));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->lane_pack, p->lane_start, 0));
+        for (int l = 0; l < L; ++l) {
+            const long long a = p->px_off[first[l]];
+            const long long b = first[l + 1] < p->N ? p->px_off[first[l + 1]] : p->total_px;
+            CUDA_TRY(p, cudaMemcpyAsync(p->raw + 5 * a, channels + 5 * a, sizeof(float) * 5 * (size_t)(b - a),
+                                        cudaMemcpyHostToDevice, p->lane_copy));
+            CUDA_TRY(p, cudaEventRecord(p->lane_copied[l], p->lane_copy));
+            CUDA_TRY(p, cudaStreamWaitEvent(p->lane_pack, p->lane_copied[l], 0));
+            if ((st = pack_frames(p, first[l], first[l + 1] - first[l], p->lane_pack))) return st;
+            CUDA_TRY(p, cudaEventRecord(p->lane_ready[l], p->lane_pack));
+        }
+        p->pyramid_stale = true;
+        p->linearized = false;
+        p->mask_valid = false;
+        // segment l of the linearisation waits for lane l; consecutive segments run
+        // on two streams, so one's last work items overlap the next one's first
+        CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
+        CUDA_TRY(p, cudaMemsetAsync(p->d_seg_queue, 0, sizeof(int) * L, p->stream));
+        CUDA_TRY(p, cudaEventRecord(p->lane_lin_start, p->stream));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->lane_lin, p->lane_lin_start, 0));
+        for (int l = 0; l < L; ++l) {
+            cudaStream_t s = (l & 1) ? p->lane_lin : p->stream;
+            CUDA_TRY(p, cudaStreamWaitEvent(s, p->lane_ready[l], 0));
+            CUDA_TRY(p, launch_linearize(true, false, p->cfg.texel_precision, p->d_chunks_ready + p->ready_seg[l],
+                                         p->ready_seg[l + 1] - p->ready_seg[l], p->d_seg_queue + l, p->d_ps, p->d_pp, p->pts_pg,
+                                         p->pts_n, p->tex, p->prm, p->d_partials, nullptr, p->grid_full,
+                                         p->variant_full, s));
+            ++nl;
+        }
+        CUDA_TRY(p, cudaEventRecord(p->lane_lin_done, p->lane_lin));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->lane_lin_done, 0));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->lane_ready[L - 1], 0));
+        // the point counts the plan was built for must still hold
+        CUDA_TRY(p, cudaMemcpyAsync(p->h_counts, p->d_npoints, sizeof(int) * (size_t)p->N, cudaMemcpyDeviceToHost,
+                                    p->stream));
+        CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+        if (std::equal(p->n_points.begin(), p->n_points.end(), p->h_counts)) {
+            CUDA_TRY(p, launch_pair_reduce(p->d_partials, p->d_ps, p->d_pf, p->d_poses, p->d_pair_Xo, p->M, true,
+                                           p->d_blocks, p->stream));
+            if (!p->sparse)
+                CUDA_TRY(p, launch_assemble(p->d_tasks, p->n_tasks, p->d_contrib, p->d_blocks, p->N, p->d_H, p->d_b,
+                                            p->stream));
+            CUDA_TRY(p, launch_total_cost(p->d_blocks, p->M, p->d_state, false, p->stream));
+        } else {
+            // a frame's count changed: the pair plan is rebuilt and the pass redone
+            if ((st = finish_repack(p))) return st;
+            if ((st = enqueue_linearize(p, p->stream, &nl))) return st;
+        }
+    }
+    // the damped step and the cost at the candidate (the system there is not formed)
+    p->linearized = true;
+    if ((st = enqueue_step(p, -1.0, p->stream, &nl))) return st;
+    p->linearized = false;
+    return read_stats(p, stats);
 }
 
 int pba_iterate(pba_problem* p, pba_iter_stats* stats) {
@@ -2075,6 +2251,25 @@ int pba_set_variants(pba_problem* p, int variant_full, int variant_cost) {
     p->grid_cost = linearize_grid(p->cfg.texel_precision, false, variant_cost);
     drop_graph(p);
     return PBA_OK;
+}
+
+int pba_set_tuning(pba_problem* p, const pba_tuning* t) {
+    if (!p) return PBA_EINVAL;
+    if (!t) return fail(p, PBA_EINVAL, "set_tuning: tuning is NULL");
+    if (t->chunk < 32 || t->chunk > 8192 || t->chunk % 32 || t->chunk_tail < 32 || t->chunk_tail > t->chunk ||
+        t->chunk_tail % 32)
+        return fail(p, PBA_EINVAL, "set_tuning: chunk must be a multiple of 32 in [32, 8192], chunk_tail one in [32, chunk]");
+    int st = pba_set_variants(p, t->variant_full, t->variant_cost);
+    if (st) return st;
+    p->tune_ms_full = p->tune_ms_cost = 0.f;
+    p->tune_from_cache = 0;
+    if (p->cfg.path != PBA_PATH_BATCHED || p->M <= 0) {
+        p->chunk = t->chunk;
+        p->chunk_tail = t->chunk_tail;
+        return PBA_OK;
+    }
+    p->linearized = false;
+    return set_chunking(p, t->chunk, t->chunk_tail);
 }
 
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches) {

@@ -194,12 +194,20 @@ cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorD
 cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const double* pair_Xo, int m,
                              PairPose* out, cudaStream_t s);
 
+// chunks: work items (pair, first point, point count, partial-sum slot), taken
+// in array order from *queue (counting up to n_chunks); item k writes its sums
+// to slot chunks[k].w of partials, so a launch may take a permuted subset.
 cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const int4* chunks, int n_chunks,
                              int* queue, const PairStatic* ps, const PairPose* pp, const float4* pts_pg,
                              const float4* pts_n, const void* texels, const LinParams& prm,
                              float* partials, uint32_t* mask_bits, int grid, int variant, cudaStream_t s);
 
-// Persistent grid (SMs x resident blocks) of a linearisation variant (0 or 1, see launch_linearize).
+// Threads of a block of the batched linearisation kernel (warps of one block
+// share nothing but their queue regions).
+constexpr int kLinThreads = 128;
+
+// Persistent grid (SMs x resident blocks) of a linearisation occupancy variant
+// (0 .. PBA_N_VARIANTS - 1, see launch_linearize).
 int linearize_grid(int texel_precision, bool full, int variant);
 
 cudaError_t launch_pair_reduce(const float* partials, const PairStatic* ps, const int2* pair_frames,

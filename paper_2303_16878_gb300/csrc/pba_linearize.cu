@@ -38,7 +38,6 @@ namespace pba {
 
 namespace {
 
-constexpr int kLinThreads = 256;
 constexpr int kLinWarps = kLinThreads / 32;
 
 // ------------------------------------------------------------ pair poses
@@ -149,13 +148,24 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
     const float4 p = __ldg(pg + k);
     const float4 n = __ldg(pn + k);
     // d pi / d pbar (2 x 3) and d zeta^d / d pbar (hardware reciprocal and
-    // reciprocal square root: ~1e-7 relative, far below the FP32 Jacobian's use)
-    float P0[3], P1[3], dz[3];
+    // reciprocal square root: ~1e-7 relative, far below the FP32 Jacobian's use),
+    // taken to the i-frame at once: h_c = M^T g_c with g_c = d zeta_c / d pbar -
+    // grad I_c d pi / d pbar is linear in those rows, A0 = M^T (d pi / d pbar)_0,
+    // A1 = M^T (d pi / d pbar)_1, Az = M^T d zeta^d / d pbar.  The model is the same
+    // for the whole warp (one pair per work item), and each branch keeps only the
+    // nonzero terms of its model's derivatives.
+    float A0[3], A1[3], Az[3];
     if (model == 0) {
+        // pinhole: (d pi / d pbar)_0 = (fx / z, 0, -fx x / z^2), _1 = (0, fy / z, -fy y / z^2), d zeta^d = e_z
         const float iz = __fdividef(1.f, qz);
-        P0[0] = fx * iz; P0[1] = 0.f; P0[2] = -fx * qx * iz * iz;
-        P1[0] = 0.f; P1[1] = fy * iz; P1[2] = -fy * qy * iz * iz;
-        dz[0] = 0.f; dz[1] = 0.f; dz[2] = 1.f;
+        const float p00 = fx * iz, p02 = -fx * qx * iz * iz;
+        const float p11 = fy * iz, p12 = -fy * qy * iz * iz;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            A0[j] = fmaf(M[j], p00, M[6 + j] * p02);
+            A1[j] = fmaf(M[3 + j], p11, M[6 + j] * p12);
+            Az[j] = M[6 + j];
+        }
     } else {
         const float rxy2 = fmaf(qx, qx, qy * qy);
         const float irxy = rsqrtf(rxy2);
@@ -163,19 +173,18 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
         const float rxy = rxy2 * irxy;
         const float inv_r = rsqrtf(fmaf(qz, qz, rxy2));
         const float ir2 = inv_r * inv_r;
-        P0[0] = -fx * qy * irxy2; P0[1] = fx * qx * irxy2; P0[2] = 0.f;
+        // spherical: (d pi / d pbar)_0 = fx (-y, x, 0) / rxy^2, _1 = fy (-z x / (r^2 rxy), -z y / (r^2 rxy), rxy / r^2),
+        // d zeta^d = pbar / r
+        const float p00 = -fx * qy * irxy2, p01 = fx * qx * irxy2;
         const float k1 = -fy * qz * ir2 * irxy;
-        P1[0] = k1 * qx; P1[1] = k1 * qy; P1[2] = fy * rxy * ir2;
-        dz[0] = qx * inv_r; dz[1] = qy * inv_r; dz[2] = qz * inv_r;
-    }
-    // h_c = M^T g_c with g_c = d zeta_c / d pbar - grad I_c d pi / d pbar is linear
-    // in the rows of d pi / d pbar: take them (and d zeta^d / d pbar) to the i-frame once
-    float A0[3], A1[3], Az[3];
+        const float p10 = k1 * qx, p11 = k1 * qy, p12 = fy * rxy * ir2;
+        const float d0 = qx * inv_r, d1 = qy * inv_r, d2 = qz * inv_r;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        A0[j] = fmaf(M[j], P0[0], fmaf(M[3 + j], P0[1], M[6 + j] * P0[2]));
-        A1[j] = fmaf(M[j], P1[0], fmaf(M[3 + j], P1[1], M[6 + j] * P1[2]));
-        Az[j] = fmaf(M[j], dz[0], fmaf(M[3 + j], dz[1], M[6 + j] * dz[2]));
+        for (int j = 0; j < 3; ++j) {
+            A0[j] = fmaf(M[j], p00, M[3 + j] * p01);
+            A1[j] = fmaf(M[j], p10, fmaf(M[3 + j], p11, M[6 + j] * p12));
+            Az[j] = fmaf(M[j], d0, fmaf(M[3 + j], d1, M[6 + j] * d2));
+        }
     }
     const float4 p2 = make_float4(2.f * p.x, 2.f * p.y, 2.f * p.z, 0.f);
     const float n2x = 2.f * n.x, n2y = 2.f * n.y, n2z = 2.f * n.z;
@@ -427,7 +436,10 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             if (lane == j) mine = x;
         }
-        if (lane < kNumAcc && (FULL || lane >= 27)) partials[(long long)ci * kPartialStride + lane] = mine;
+        // the item's partial-sum slot (its index in the plan's own order, whatever
+        // order this launch takes the items in)
+        const int slot = __ldg(reinterpret_cast<const int*>(chunks + ci) + 3);
+        if (lane < kNumAcc && (FULL || lane >= 27)) partials[(long long)slot * kPartialStride + lane] = mine;
     }
 }
 
@@ -571,17 +583,22 @@ static void* lin_kernel() {
     return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK, MINB>);
 }
 
-// Occupancy variants (blocks of 256 threads per SM the register budget aims
-// at): full pass 2, 3 or 4, cost-only pass 3, 4 or 5 for variants 0, 1, 2.
-// Fewer registers per thread trade spills for warps to hide gather latency.
+// Occupancy variants (blocks of 128 threads per SM the register budget aims
+// at): full pass 4, 6, 7 or 8 (128, 80, 72 or 64 registers: 16 to 32 warps per
+// SM), cost-only pass 6, 7, 9 or 10 (72 to 48 registers: 28 to 40 warps) for
+// variants 0 .. 3.  Fewer registers per thread trade spills for warps to hide
+// gather latency; the block size only sets the occupancy steps (the warps of a
+// block share nothing but their queue regions).
 template <int TEXEL, bool FULL, bool MASK>
 static void* pick_minb(int variant) {
     if (FULL) {
-        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 4>();
-        return variant ? lin_kernel<TEXEL, FULL, MASK, 3>() : lin_kernel<TEXEL, FULL, MASK, 2>();
+        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 8>();
+        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 7>();
+        return variant ? lin_kernel<TEXEL, FULL, MASK, 6>() : lin_kernel<TEXEL, FULL, MASK, 4>();
     }
-    if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 5>();
-    return variant ? lin_kernel<TEXEL, FULL, MASK, 4>() : lin_kernel<TEXEL, FULL, MASK, 3>();
+    if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 10>();
+    if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 9>();
+    return variant ? lin_kernel<TEXEL, FULL, MASK, 7>() : lin_kernel<TEXEL, FULL, MASK, 6>();
 }
 
 static void* pick(int texel_precision, bool full, bool mask, int variant) {

@@ -245,6 +245,31 @@ def test_autotuner_reports_its_tuple_and_caches_it(oracle_lib, street3):
     b.close()
 
 
+def test_given_tuning_is_applied_without_timing(oracle_lib, street3):
+    """pba_set_tuning applies a tuple as pba_get_tuning reports it (here one
+    the autotuner never tries: 640-point items, 96-point tail) without timing;
+    the system with it matches the oracle; tuples outside the documented
+    ranges are refused and leave the tuning as it was."""
+    import paper_2303_16878_gb300 as pba
+    w = street3
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, 1))
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    given = dict(variant_full=pba._lib.PBA_N_VARIANTS - 1, variant_cost=1, chunk=640, chunk_tail=96)
+    p.set_tuning(given)
+    t = p.tuning()
+    assert {k: t[k] for k in given} == given and not t["from_cache"] and t["ms_full"] == 0
+    cost, _ = p.linearize()
+    H, b = p.get_system()
+    assert rel(H, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
+    for bad in (dict(given, chunk=650), dict(given, chunk_tail=1024), dict(given, chunk_tail=0),
+                dict(given, chunk=16384), dict(given, variant_cost=pba._lib.PBA_N_VARIANTS)):
+        with pytest.raises(pba.PbaError):
+            p.set_tuning(bad)
+        assert {k: p.tuning()[k] for k in given} == given
+    assert p.iterate()["status"] == 0
+    p.close()
+
+
 def test_mixed_and_f64_solvers_agree_on_the_lidar_street():
     """One LM iteration on the full 50-frame street: the mixed solver's step
     equals the FP64 Cholesky step to the refinement tolerance."""
