@@ -106,6 +106,8 @@ LINEARIZE_NCU = {
     # profiles/k_linearize_lidar_street_50x64x1024.md (ncu --set full, one launch at the initial poses)
     ("street", 1, 2048, 256): {"dram_bytes": 446.6e6 + 8.8e6,
                                "units": {"sm_issue": 0.697, "l1_data_pipe": 0.583, "l2": 0.221, "dram": 0.056}},
+    # profiles/k_linearize_joint_hall_900.md (DRAM bytes only: one pass on the full workload)
+    ("joint", 1, 1024, 128): {"dram_bytes": 45.86e9 + 0.24e9, "units": None},
 }
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
@@ -523,6 +525,8 @@ def run_ours(args, rank, world, device):
         seq, _ = e2e_steps(3, sequential)
         out["e2e"] = {"value": ev_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(walls) / len(walls),
+                      # the host-to-device rate over the shared host link varies between steps
+                      "median_ms_per_step": 1e3 * float(np.median(walls)), "min_ms_per_step": 1e3 * min(walls),
                       "call": "pba_iterate_frames (pinned host frames and poses) + pba_get_poses",
                       "sequential_ms_per_step": 1e3 * float(np.mean(seq)),
                       "sequential_call": "pba_upload_frames per image size + pba_set_poses + pba_iterate + "

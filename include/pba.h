@@ -481,7 +481,10 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
  * launched repeats + 1 times, the first as warm-up): for the full pass every
  * work-item size (512, 1024, 2048 points per warp item) x size of the short
  * items that end the queue (128, 256) x occupancy variant, then for the
- * cost-only pass the occupancy variants at the chosen work items; later
+ * cost-only pass the occupancy variants at the chosen work items; settings
+ * within 2 % of the fastest count as equal, and the first of them in that
+ * order (work-item size, then tail size, then variant, each ascending) is
+ * kept, so that timing noise does not change the choice between runs.  Later
  * iterations use the choice (pba_get_tuning reports it).  The result is
  * cached for the life of the process per configuration (device, texel
  * precision, gradient mode, pairs, point counts, sensors): tuning the same

@@ -25,6 +25,7 @@ constexpr int kChunkTail = 256;  // ... in the last stretch of the queue, so tha
 // the work-item sizes pba_autotune tries
 constexpr int kTuneChunks[3] = {512, 1024, 2048};
 constexpr int kTuneTails[2] = {128, 256};
+constexpr float kTuneTie = 0.02f;  // relative time difference the autotuner treats as a tie
 
 }  // namespace
 
@@ -43,13 +44,13 @@ struct pba_problem {
     cudaStream_t copy_streams[kCopyLanes - 1] = {};
     cudaEvent_t copy_events[kCopyLanes] = {};
     // pba_iterate_frames: the frames arrive in lanes of whole frames (copied in
-    // order on lane_copy, packed on lane_pack); the work items of the pairs whose
-    // frames have all arrived with lane l form segment l of d_chunks_ready, whose
-    // linearisation (alternately on the problem's stream and lane_lin) waits for
-    // that lane only
+    // order on lane_copy, packed on lane_pack, a stream of the greatest
+    // priority); the work items of the pairs whose frames have all arrived with
+    // lane l form segment l of d_chunks_ready, whose linearisation (on the
+    // problem's stream) waits for that lane only
     static constexpr int kFrameLanes = 8;
-    cudaStream_t lane_copy = nullptr, lane_pack = nullptr, lane_lin = nullptr;
-    cudaEvent_t lane_start = nullptr, lane_lin_start = nullptr, lane_lin_done = nullptr;
+    cudaStream_t lane_copy = nullptr, lane_pack = nullptr;
+    cudaEvent_t lane_start = nullptr;
     cudaEvent_t lane_copied[kFrameLanes] = {}, lane_ready[kFrameLanes] = {};
     int4* d_chunks_ready = nullptr;
     int n_chunks_ready_alloc = 0;
@@ -936,10 +937,9 @@ void pba_destroy(pba_problem* p) {
     dfree(p->d_chunks_ready);
     dfree(p->d_seg_queue);
     if (p->h_counts) cudaFreeHost(p->h_counts);
-    for (cudaStream_t c : {p->lane_copy, p->lane_pack, p->lane_lin})
+    for (cudaStream_t c : {p->lane_copy, p->lane_pack})
         if (c) cudaStreamDestroy(c);
-    for (cudaEvent_t e : {p->lane_start, p->lane_lin_start, p->lane_lin_done})
-        if (e) cudaEventDestroy(e);
+    if (p->lane_start) cudaEventDestroy(p->lane_start);
     for (int l = 0; l < p->kFrameLanes; ++l) {
         if (p->lane_copied[l]) cudaEventDestroy(p->lane_copied[l]);
         if (p->lane_ready[l]) cudaEventDestroy(p->lane_ready[l]);
@@ -1582,10 +1582,11 @@ int pba_iterate_frames(pba_problem* p, const float* channels, const double* pose
         if ((st = enqueue_linearize(p, p->stream, &nl))) return st;
     } else {
         if (!p->lane_copy) {
-            for (cudaStream_t* c : {&p->lane_copy, &p->lane_pack, &p->lane_lin})
-                CUDA_TRY(p, cudaStreamCreateWithFlags(c, cudaStreamNonBlocking));
-            for (cudaEvent_t* e : {&p->lane_start, &p->lane_lin_start, &p->lane_lin_done})
-                CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            int least = 0, greatest = 0;
+            CUDA_TRY(p, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            CUDA_TRY(p, cudaStreamCreateWithFlags(&p->lane_copy, cudaStreamNonBlocking));
+            CUDA_TRY(p, cudaStreamCreateWithPriority(&p->lane_pack, cudaStreamNonBlocking, greatest));
+            CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_start, cudaEventDisableTiming));
             for (int l = 0; l < p->kFrameLanes; ++l) {
                 CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_copied[l], cudaEventDisableTiming));
                 CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_ready[l], cudaEventDisableTiming));
@@ -1622,24 +1623,19 @@ int pba_iterate_frames(pba_problem* p, const float* channels, const double* pose
         p->pyramid_stale = true;
         p->linearized = false;
         p->mask_valid = false;
-        // segment l of the linearisation waits for lane l; consecutive segments run
-        // on two streams, so one's last work items overlap the next one's first
+        // segment l of the linearisation waits for lane l (the copies run ahead of
+        // it on the copy engine; the packing, on a stream of greater priority,
+        // takes the SMs as a segment drains)
         CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
         CUDA_TRY(p, cudaMemsetAsync(p->d_seg_queue, 0, sizeof(int) * L, p->stream));
-        CUDA_TRY(p, cudaEventRecord(p->lane_lin_start, p->stream));
-        CUDA_TRY(p, cudaStreamWaitEvent(p->lane_lin, p->lane_lin_start, 0));
         for (int l = 0; l < L; ++l) {
-            cudaStream_t s = (l & 1) ? p->lane_lin : p->stream;
-            CUDA_TRY(p, cudaStreamWaitEvent(s, p->lane_ready[l], 0));
+            CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->lane_ready[l], 0));
             CUDA_TRY(p, launch_linearize(true, false, p->cfg.texel_precision, p->d_chunks_ready + p->ready_seg[l],
-                                         p->ready_seg[l + 1] - p->ready_seg[l], p->d_seg_queue + l, p->d_ps, p->d_pp, p->pts_pg,
-                                         p->pts_n, p->tex, p->prm, p->d_partials, nullptr, p->grid_full,
-                                         p->variant_full, s));
+                                         p->ready_seg[l + 1] - p->ready_seg[l], p->d_seg_queue + l, p->d_ps,
+                                         p->d_pp, p->pts_pg, p->pts_n, p->tex, p->prm, p->d_partials, nullptr,
+                                         p->grid_full, p->variant_full, p->stream));
             ++nl;
         }
-        CUDA_TRY(p, cudaEventRecord(p->lane_lin_done, p->lane_lin));
-        CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->lane_lin_done, 0));
-        CUDA_TRY(p, cudaStreamWaitEvent(p->stream, p->lane_ready[L - 1], 0));
         // the point counts the plan was built for must still hold
         CUDA_TRY(p, cudaMemcpyAsync(p->h_counts, p->d_npoints, sizeof(int) * (size_t)p->N, cudaMemcpyDeviceToHost,
                                     p->stream));
@@ -1818,7 +1814,11 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
         cudaEvent_t e0, e1;
         CUDA_TRY(p, cudaEventCreate(&e0));
         CUDA_TRY(p, cudaEventCreate(&e1));
-        // the full pass over work-item size x tail size x occupancy variant
+        // the full pass over work-item size x tail size x occupancy variant; settings
+        // within kTuneTie of the fastest count as equal and the first of them in
+        // this order is kept, so that timing noise does not flip the choice
+        struct Timed { int chunk, tail, variant; float ms; };
+        std::vector<Timed> full;
         for (int c : kTuneChunks)
             for (int t : kTuneTails) {
                 if ((st = set_chunking(p, c, t))) return st;
@@ -1826,25 +1826,32 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
                 for (int v = 0; v < PBA_N_VARIANTS; ++v) {
                     float ms = 0.f;
                     if ((st = time_pass(p, true, v, repeats, e0, e1, &ms))) return st;
-                    if (ms < best.ms_full) {
-                        best.ms_full = ms;
-                        best.variant_full = v;
-                        best.chunk = c;
-                        best.chunk_tail = t;
-                    }
+                    full.push_back({c, t, v, ms});
                 }
+            }
+        float fastest = 3.4e38f;
+        for (const Timed& x : full) fastest = std::min(fastest, x.ms);
+        for (const Timed& x : full)
+            if (x.ms <= fastest * (1.f + kTuneTie)) {
+                best.ms_full = x.ms;
+                best.variant_full = x.variant;
+                best.chunk = x.chunk;
+                best.chunk_tail = x.tail;
+                break;
             }
         // the cost-only pass at the chosen work items
         if ((st = set_chunking(p, best.chunk, best.chunk_tail))) return st;
         CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
-        for (int v = 0; v < PBA_N_VARIANTS; ++v) {
-            float ms = 0.f;
-            if ((st = time_pass(p, false, v, repeats, e0, e1, &ms))) return st;
-            if (ms < best.ms_cost) {
-                best.ms_cost = ms;
+        float cost_ms[PBA_N_VARIANTS];
+        for (int v = 0; v < PBA_N_VARIANTS; ++v)
+            if ((st = time_pass(p, false, v, repeats, e0, e1, &cost_ms[v]))) return st;
+        const float cost_fastest = *std::min_element(cost_ms, cost_ms + PBA_N_VARIANTS);
+        for (int v = 0; v < PBA_N_VARIANTS; ++v)
+            if (cost_ms[v] <= cost_fastest * (1.f + kTuneTie)) {
+                best.ms_cost = cost_ms[v];
                 best.variant_cost = v;
+                break;
             }
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mutex);
