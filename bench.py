@@ -108,6 +108,7 @@ LINEARIZE_NCU = {
                                "units": {"sm_issue": 0.697, "l1_data_pipe": 0.583, "l2": 0.221, "dram": 0.056}},
     # profiles/k_linearize_joint_hall_900.md (DRAM bytes only: one pass on the full workload)
     ("joint", 1, 1024, 128): {"dram_bytes": 45.86e9 + 0.24e9, "units": None},
+    ("joint", 1, 512, 128): {"dram_bytes": 40.77e9 + 0.43e9, "units": None},
 }
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
