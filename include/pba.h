@@ -471,17 +471,22 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
  * PBA_ENOTREADY (poses or pairs not set), PBA_ECUDA. */
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
-/* Occupancy variants of the batched linearisation kernel: register budgets
- * for 4, 6, 7 or 8 (full pass) and 6, 7, 9 or 10 (cost-only pass) blocks of
- * 128 threads per SM, variants 0 .. 3.  The results agree up to float32
+/* Variants of the batched linearisation kernel: register budgets for 4, 6, 7
+ * or 8 (full pass) and 6, 7, 9 or 10 (cost-only pass) blocks of 128 threads
+ * per SM, variants 0 .. 3; variants 4 .. 7 have the same budgets and read each
+ * 32-point step's bilinear taps from a 4 x 48-pixel tile of the target's
+ * texels that one TMA tensor copy staged in shared memory (FP16 texels and
+ * frames of at least 48 x 4 pixels; otherwise, and for the linearisation with
+ * mask export, they run as variants 0 .. 3).  The results agree up to float32
  * summation order. */
-#define PBA_N_VARIANTS 4
+#define PBA_N_VARIANTS 8
 
 /* Tune the batched linearisation on this problem by timing it (each setting
  * launched repeats + 1 times, the first as warm-up): for the full pass every
  * work-item size (512, 1024, 2048 points per warp item) x size of the short
- * items that end the queue (128, 256) x occupancy variant, then for the
- * cost-only pass the occupancy variants at the chosen work items; settings
+ * items that end the queue (128, 256) x variant (0 .. PBA_N_VARIANTS - 1; the
+ * staged variants 4 .. 7 only where tiles are staged), then for the cost-only
+ * pass the variants at the chosen work items; settings
  * within 2 % of the fastest count as equal, and the first of them in that
  * order (work-item size, then tail size, then variant, each ascending) is
  * kept, so that timing noise does not change the choice between runs.  Later
@@ -500,13 +505,15 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
  * warp work item: 512, 1024 or 2048) and the size of the short items at the
  * end of the queue (128 or 256), whether they came from the process's cache
  * of tuned configurations (same device, texel precision, gradient mode,
- * pairs, point counts and sensors: no timing was done), and the mean time of
- * one full and one cost-only pass with them (0 before any tuning).
+ * pairs, point counts and sensors: no timing was done), whether a staged
+ * tile's wait ran past its limit since the problem was created (tile_err: 1;
+ * the taps are then read directly, the results stay exact), and the mean time
+ * of one full and one cost-only pass with them (0 before any tuning).
  * Errors: PBA_EINVAL (a NULL argument). */
 typedef struct {
     int32_t variant_full, variant_cost;
     int32_t chunk, chunk_tail;
-    int32_t from_cache, pad;
+    int32_t from_cache, tile_err;
     float ms_full, ms_cost;
 } pba_tuning;
 int pba_get_tuning(pba_problem* p, pba_tuning* out);

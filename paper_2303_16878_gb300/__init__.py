@@ -418,13 +418,15 @@ class Problem:
         return a.value, b.value
 
     def tuning(self) -> Dict:
-        """The settings of the linearisation (pba_get_tuning): occupancy variants,
-        work-item sizes, whether they came from the process's tuning cache, and
-        the tuned pass times in ms."""
+        """The settings of the linearisation (pba_get_tuning): variants (occupancy
+        budget, staged taps from 4 on), work-item sizes, whether they came from
+        the process's tuning cache, the tuned pass times in ms and the staged
+        tiles' timeout flag."""
         t = _lib.PbaTuning()
         self._check(self._lib.pba_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
         return dict(variant_full=t.variant_full, variant_cost=t.variant_cost, chunk=t.chunk,
-                    chunk_tail=t.chunk_tail, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost)
+                    chunk_tail=t.chunk_tail, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost,
+                    tile_err=int(t.tile_err))
 
     def set_tuning(self, tuning: Dict):
         """Apply a tuning as tuning() reports it (variant_full, variant_cost,

@@ -48,7 +48,7 @@ EXPORTS = ["pba_create", "pba_destroy", "pba_last_error", "pba_set_stream", "pba
            "pba_build_pyramid", "pba_pyramid_level", "pba_optimize", "pba_set_variables",
            "pba_set_variants", "pba_set_tuning", "pba_refine_extrinsic",
            "pba_get_extrinsic", "pba_set_offset_free"]
-PBA_N_VARIANTS = 4
+PBA_N_VARIANTS = 8
 PBA_MAX_LEVELS = 8
 PBA_NORMALS_MAX_RADIUS = 32
 PBA_N_PHASES = 5
@@ -79,7 +79,7 @@ class PbaIterStats(ctypes.Structure):
 
 class PbaTuning(ctypes.Structure):
     _fields_ = [("variant_full", ctypes.c_int32), ("variant_cost", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("chunk_tail", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("chunk_tail", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("tile_err", ctypes.c_int32),
                 ("ms_full", ctypes.c_float), ("ms_cost", ctypes.c_float)]
 
 

@@ -14,6 +14,7 @@
 
 #include "../../include/pba.h"
 #include "pba_internal.cuh"
+#include "pba_tma.cuh"
 
 using namespace pba;
 
@@ -59,6 +60,11 @@ struct pba_problem {
     long long plan_serial = 0, ready_serial = -1;
     int* d_seg_queue = nullptr;    // one work-queue counter per segment
     int* h_counts = nullptr;       // pinned: point counts read back after the overlapped pass
+    // staged linearisation variants (FP16 texels, frames at least one tile in size):
+    // one TMA tensor map per frame and the flag a tile wait raises when it runs out
+    bool stage_ok = false;
+    CUtensorMap* d_tmaps = nullptr;
+    int* d_tile_err = nullptr;
     std::string err;
 
     // frames
@@ -680,6 +686,51 @@ const char* pba_last_error(const pba_problem* p) {
     return p->err.c_str();
 }
 
+// The TMA tensor maps of the staged linearisation: frame k's FP16 texels as a
+// 3-D tensor (4 words, width, height; strides 16 B and 16 B x width) with a
+// box of one tile (4 words x kTileCols x kTileRows), zero fill outside.  Staging
+// is left off for FP32 texels and when a frame is smaller than a tile.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int build_tile_maps(pba_problem* p) {
+    p->stage_ok = false;
+    p->prm.tmaps = nullptr;
+    p->prm.tile_err = nullptr;
+    if (p->cfg.texel_precision != PBA_TEXEL_F16) return PBA_OK;
+    for (const pba_sensor& S : p->sensors)
+        if (S.width < kTileCols || S.height < kTileRows) return PBA_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return fail(p, PBA_ECUDA, "create: the driver has no cuTensorMapEncodeTiled");
+    const EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    std::vector<CUtensorMap> maps(p->N);
+    for (int k = 0; k < p->N; ++k) {
+        const pba_sensor& S = p->sensors[p->frame_sensor[k]];
+        const cuuint64_t dims[3] = {4, (cuuint64_t)S.width, (cuuint64_t)S.height};
+        const cuuint64_t strides[2] = {16, 16ull * (cuuint64_t)S.width};
+        const cuuint32_t box[3] = {4, (cuuint32_t)kTileCols, (cuuint32_t)kTileRows};
+        const cuuint32_t elem[3] = {1, 1, 1};
+        void* base = reinterpret_cast<char*>(p->tex) + 16ll * p->px_off[k];
+        if (encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, base, dims, strides, box, elem,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(p, PBA_ECUDA, "create: cuTensorMapEncodeTiled refused a frame's texels");
+    }
+    CUDA_TRY(p, cudaMalloc((void**)&p->d_tmaps, sizeof(CUtensorMap) * (size_t)p->N));
+    CUDA_TRY(p, cudaMalloc((void**)&p->d_tile_err, sizeof(int)));
+    CUDA_TRY(p, cudaMemcpy(p->d_tmaps, maps.data(), sizeof(CUtensorMap) * (size_t)p->N, cudaMemcpyHostToDevice));
+    CUDA_TRY(p, cudaMemset(p->d_tile_err, 0, sizeof(int)));
+    p->prm.tmaps = p->d_tmaps;
+    p->prm.tile_err = p->d_tile_err;
+    p->stage_ok = true;
+    return PBA_OK;
+}
+
 int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
     if (!cfg || !out) return create_fail(PBA_EINVAL, "null configuration or output pointer");
     *out = nullptr;
@@ -870,6 +921,11 @@ int pba_create(const pba_config* cfg, void* cuda_stream, pba_problem** out) {
         if (cudaMemcpy(p->d_frame_iota, iota.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(PBA_ECUDA);
     }
+    if (int st = build_tile_maps(p)) {
+        const std::string what = p->err;
+        pba_destroy(p);
+        return create_fail(st, what);
+    }
     p->grid_full = linearize_grid(cfg->texel_precision, true, 0);
     p->grid_cost = linearize_grid(cfg->texel_precision, false, 0);
     *out = p;
@@ -936,6 +992,8 @@ void pba_destroy(pba_problem* p) {
         if (e) cudaEventDestroy(e);
     dfree(p->d_chunks_ready);
     dfree(p->d_seg_queue);
+    dfree(p->d_tmaps);
+    dfree(p->d_tile_err);
     if (p->h_counts) cudaFreeHost(p->h_counts);
     for (cudaStream_t c : {p->lane_copy, p->lane_pack})
         if (c) cudaStreamDestroy(c);
@@ -1819,11 +1877,12 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
         // this order is kept, so that timing noise does not flip the choice
         struct Timed { int chunk, tail, variant; float ms; };
         std::vector<Timed> full;
+        const int n_var = p->stage_ok ? PBA_N_VARIANTS : PBA_N_VARIANTS / 2;  // staged ones need tiles
         for (int c : kTuneChunks)
             for (int t : kTuneTails) {
                 if ((st = set_chunking(p, c, t))) return st;
                 CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
-                for (int v = 0; v < PBA_N_VARIANTS; ++v) {
+                for (int v = 0; v < n_var; ++v) {
                     float ms = 0.f;
                     if ((st = time_pass(p, true, v, repeats, e0, e1, &ms))) return st;
                     full.push_back({c, t, v, ms});
@@ -1843,10 +1902,10 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
         if ((st = set_chunking(p, best.chunk, best.chunk_tail))) return st;
         CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
         float cost_ms[PBA_N_VARIANTS];
-        for (int v = 0; v < PBA_N_VARIANTS; ++v)
+        for (int v = 0; v < n_var; ++v)
             if ((st = time_pass(p, false, v, repeats, e0, e1, &cost_ms[v]))) return st;
-        const float cost_fastest = *std::min_element(cost_ms, cost_ms + PBA_N_VARIANTS);
-        for (int v = 0; v < PBA_N_VARIANTS; ++v)
+        const float cost_fastest = *std::min_element(cost_ms, cost_ms + n_var);
+        for (int v = 0; v < n_var; ++v)
             if (cost_ms[v] <= cost_fastest * (1.f + kTuneTie)) {
                 best.ms_cost = cost_ms[v];
                 best.variant_cost = v;
@@ -1859,8 +1918,9 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     } else if ((st = set_chunking(p, best.chunk, best.chunk_tail))) {
         return st;
     }
-    p->variant_full = best.variant_full;
-    p->variant_cost = best.variant_cost;
+    // (staged variants only where this problem stages tiles)
+    p->variant_full = p->stage_ok ? best.variant_full : (best.variant_full & 3);
+    p->variant_cost = p->stage_ok ? best.variant_cost : (best.variant_cost & 3);
     p->tune_ms_full = best.ms_full;
     p->tune_ms_cost = best.ms_cost;
     p->tune_from_cache = cached ? 1 : 0;
@@ -1880,7 +1940,8 @@ int pba_get_tuning(pba_problem* p, pba_tuning* out) {
     out->chunk = p->chunk;
     out->chunk_tail = p->chunk_tail;
     out->from_cache = p->tune_from_cache;
-    out->pad = 0;
+    out->tile_err = 0;
+    if (p->d_tile_err) CUDA_TRY(p, cudaMemcpy(&out->tile_err, p->d_tile_err, sizeof(int), cudaMemcpyDeviceToHost));
     out->ms_full = p->tune_ms_full;
     out->ms_cost = p->tune_ms_cost;
     return PBA_OK;
@@ -2252,6 +2313,10 @@ int pba_set_variants(pba_problem* p, int variant_full, int variant_cost) {
     if (variant_full < 0 || variant_full >= PBA_N_VARIANTS || variant_cost < 0 || variant_cost >= PBA_N_VARIANTS)
         return fail(p, PBA_EINVAL, "set_variants: variant outside [0, PBA_N_VARIANTS)");
     cudaSetDevice(p->device);
+    if (!p->stage_ok) {  // no staged tiles here: variants 4 .. 7 run as 0 .. 3
+        variant_full &= 3;
+        variant_cost &= 3;
+    }
     p->variant_full = variant_full;
     p->variant_cost = variant_cost;
     p->grid_full = linearize_grid(p->cfg.texel_precision, true, variant_full);

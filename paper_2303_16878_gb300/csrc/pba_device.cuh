@@ -70,20 +70,26 @@ struct Texel {
     bool usable;
 };
 
+// An FP16 texel (Tex16 as 4 words) in FP32.
+__device__ __forceinline__ Texel texel_of(const uint4 v) {
+    Texel t;
+    t.d = __uint_as_float(v.x);
+    __half2 a = *reinterpret_cast<const __half2*>(&v.y);
+    __half2 b = *reinterpret_cast<const __half2*>(&v.z);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    t.g = fa.x;
+    t.nx = fa.y;
+    t.ny = fb.x;
+    t.nz = fb.y;
+    t.usable = v.w != 0u;
+    return t;
+}
+
 template <int TEXEL>
 __device__ __forceinline__ Texel load_texel(const void* __restrict__ base, int idx) {
     Texel t;
     if (TEXEL == 1) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + idx);
-        t.d = __uint_as_float(v.x);
-        __half2 a = *reinterpret_cast<const __half2*>(&v.y);
-        __half2 b = *reinterpret_cast<const __half2*>(&v.z);
-        const float2 fa = __half22float2(a), fb = __half22float2(b);
-        t.g = fa.x;
-        t.nx = fa.y;
-        t.ny = fb.x;
-        t.nz = fb.y;
-        t.usable = v.w != 0u;
+        t = texel_of(__ldg(reinterpret_cast<const uint4*>(base) + idx));
     } else {
         const float4* p = reinterpret_cast<const float4*>(base) + 2 * idx;
         const float4 v0 = __ldg(p);

@@ -18,6 +18,7 @@
 //   H (6N x 6N) and b (6N) FP64 dense; A = H_ff + lambda I padded to a multiple of 32
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -114,6 +115,11 @@ struct LinParams {
     // (d/du, d/dv) of (g, d, n_x, n_y, n_z), 12 floats (3 float4, the last two 0);
     // zero where the pixel is not usable
     const float4* gtex;
+    // FP16 texels: one TMA tensor map per frame (its texels as 4 words x width x
+    // height), read by the staged kernel variants; tile_err is raised when a tile
+    // wait ran out
+    const CUtensorMap* tmaps;
+    int* tile_err;
 };
 
 // Device-side Levenberg-Marquardt state of one problem.

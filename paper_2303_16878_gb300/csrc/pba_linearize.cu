@@ -33,6 +33,7 @@
 // rows c = 2 + k, 2 n^o x m_k in the rotation part (m_k = row k of M).
 #include "pba_device.cuh"
 #include "pba_internal.cuh"
+#include "pba_tma.cuh"
 
 namespace pba {
 
@@ -221,18 +222,34 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
 // 12-texel stencil), sampled values, residual, occlusion test, Huber weight and
 // cost.  Valid residuals are compacted into the warp's queue; stage 2 runs on
 // full warps of them.
-template <int TEXEL, bool FULL, bool MASK, int MINB>
+//
+// STAGE (FP16 texels): the four taps of each 32-point step are read from a
+// kTileRows x kTileCols tile of the target's texels in shared memory, fetched
+// by one lane with one TMA tensor copy (the step's taps span a few rows and
+// columns: consecutive points of a source row land on neighbouring target
+// pixels); a step whose taps do not fit the tile, or straddle the wrap seam of
+// a spherical image, reads them from global memory as the unstaged kernel does.
+template <int TEXEL, bool FULL, bool MASK, int MINB, bool STAGE>
 __global__ void __launch_bounds__(kLinThreads, MINB)
     k_linearize(const int4* __restrict__ chunks, int n_chunks, int* __restrict__ queue,
                 const PairStatic* __restrict__ ps, const PairPose* __restrict__ pp,
                 const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
                 const void* __restrict__ tex, const LinParams prm, float* __restrict__ partials,
                 uint32_t* __restrict__ mask_bits) {
+    static_assert(!STAGE || TEXEL == 1, "tiles are staged for FP16 texels only");
     __shared__ __align__(16) float s_q[FULL ? kLinWarps : 1][kQItems][kQueue];
+    __shared__ __align__(128) uint4 s_tile[STAGE ? kLinWarps : 1][STAGE ? kTileRows * kTileCols : 1];
+    __shared__ __align__(8) uint64_t s_bar[kLinWarps];
     static_assert(27 * 32 <= kQItems * kQueue, "the reduction table must fit the queue region");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float om[5] = {prm.w_int, prm.w_depth, prm.w_normal, prm.w_normal, prm.w_normal};
     float(*Q)[kQueue] = s_q[FULL ? warp : 0];
+    unsigned tile_phase = 0;      // parity of the warp's mbarrier for the next tile
+    bool tile_ok = STAGE;         // false once a tile wait ran out (taps read directly)
+    if (STAGE) {
+        if (lane == 0) tma_mbar_init(&s_bar[warp], 1);
+        __syncwarp();
+    }
 
     for (;;) {
         int ci = 0;
@@ -276,14 +293,16 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
             int r0 = 0, c0 = 0;
             const float4 p = p_next;
             if (k + 32 < end) p_next = __ldg(pts_pg + pt_off + k + 32);
+            float zeta_d = 0.f;
+            bool ok = false;
+            int cp1 = 0;
             if (k < end) {
                 // a2: pbar = M p_u + a
                 qx = fmaf(M[0], p.x, fmaf(M[1], p.y, fmaf(M[2], p.z, av[0])));
                 qy = fmaf(M[3], p.x, fmaf(M[4], p.y, fmaf(M[5], p.z, av[1])));
                 qz = fmaf(M[6], p.x, fmaf(M[7], p.y, fmaf(M[8], p.z, av[2])));
                 // a3: projection (the column as floor and fraction) and bounds
-                float v, zeta_d;
-                bool ok;
+                float v;
                 if (model == 0) {
                     ok = qz > prm.z_min;
                     const float iz = __fdividef(1.f, qz);
@@ -308,59 +327,99 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                     const float fv = floorf(v);
                     r0 = (int)fv;
                     fb = v - fv;
-                    int cm1, cc, cp1, cp2;
+                    int cm1, cc, cp2;
                     stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
                     c0 = cc;
-                    // a4: the four bilinear taps; their usable flags decide the 12-texel stencil
+                }
+            }
+            // staged taps: the warp's tile around this step's taps, one TMA copy
+            bool staged = false;
+            int t_r = 0, t_c = 0;
+            if (STAGE && tile_ok) {
+                const int rl = __reduce_min_sync(0xffffffffu, ok ? r0 : 0x7fffffff);
+                const int rh = __reduce_max_sync(0xffffffffu, ok ? r0 + 1 : -1);
+                const int cl = __reduce_min_sync(0xffffffffu, ok ? c0 : 0x7fffffff);
+                const int chh = __reduce_max_sync(0xffffffffu, ok ? c0 + 1 : -1);
+                const bool seam = __any_sync(0xffffffffu, ok && cp1 != c0 + 1);
+                staged = rh >= 0 && !seam && rh - rl < kTileRows && chh - cl < kTileCols;
+                if (staged) {
+                    t_r = rl;
+                    t_c = cl;
+                    __syncwarp();  // every lane's reads of the previous tile are done
+                    if (lane == 0)
+                        tma_load_tile(s_tile[warp], &s_bar[warp], prm.tmaps + P.tgt, t_c, t_r);
+                    if (!tma_wait(&s_bar[warp], tile_phase)) {
+                        // the copy did not complete within the limit: raise the flag and read
+                        // the taps directly from now on (the tile is not read again)
+                        if (lane == 0) atomicExch(prm.tile_err, 1);
+                        tile_ok = false;
+                        staged = false;
+                    }
+                    tile_phase ^= 1u;
+                }
+            }
+            if (ok) {
+                // a4: the four bilinear taps; their usable flags decide the 12-texel stencil
+                Texel A, B, C, D;
+                if (STAGE && staged) {
+                    const uint4* T = s_tile[warp];
+                    const int i0 = (r0 - t_r) * kTileCols + (c0 - t_c);
+                    A = texel_of(T[i0]);
+                    B = texel_of(T[i0 + 1]);
+                    C = texel_of(T[i0 + kTileCols]);
+                    D = texel_of(T[i0 + kTileCols + 1]);
+                } else {
                     const int rr0 = r0 * W, rp1 = rr0 + W;
-                    const Texel A = load_texel<TEXEL>(tex_j, rr0 + cc), B = load_texel<TEXEL>(tex_j, rr0 + cp1);
-                    const Texel C = load_texel<TEXEL>(tex_j, rp1 + cc), D = load_texel<TEXEL>(tex_j, rp1 + cp1);
-                    ok = A.usable && B.usable && C.usable && D.usable;
-                    const float wA = (1.f - fa) * (1.f - fb), wB = fa * (1.f - fb), wC = (1.f - fa) * fb, wD = fa * fb;
-                    float xa[5], xb[5], xc[5], xd[5], s[5];
-                    channels(A, xa);
-                    channels(B, xb);
-                    channels(C, xc);
-                    channels(D, xd);
+                    A = load_texel<TEXEL>(tex_j, rr0 + c0);
+                    B = load_texel<TEXEL>(tex_j, rr0 + cp1);
+                    C = load_texel<TEXEL>(tex_j, rp1 + c0);
+                    D = load_texel<TEXEL>(tex_j, rp1 + cp1);
+                }
+                ok = A.usable && B.usable && C.usable && D.usable;
+                const float wA = (1.f - fa) * (1.f - fb), wB = fa * (1.f - fb), wC = (1.f - fa) * fb, wD = fa * fb;
+                float xa[5], xb[5], xc[5], xd[5], s[5];
+                channels(A, xa);
+                channels(B, xb);
+                channels(C, xc);
+                channels(D, xd);
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) s[c] = fmaf(wA, xa[c], fmaf(wB, xb[c], fmaf(wC, xc[c], wD * xd[c])));
-                    // a5: residual, occlusion test, Huber
-                    const float e_d = zeta_d - s[1];
-                    ok = ok && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
-                    const float nt2 = fmaf(s[2], s[2], fmaf(s[3], s[3], s[4] * s[4]));
-                    ok = ok && nt2 >= 0.25f;
-                    if (ok) {
-                        valid = true;
-                        const float4 n = __ldg(pts_n + pt_off + k);
-                        const float nbx = fmaf(M[0], n.x, fmaf(M[1], n.y, M[2] * n.z));
-                        const float nby = fmaf(M[3], n.x, fmaf(M[4], n.y, M[5] * n.z));
-                        const float nbz = fmaf(M[6], n.x, fmaf(M[7], n.y, M[8] * n.z));
-                        e[0] = p.w - s[0];
-                        e[1] = e_d;
-                        e[2] = nbx - s[2];
-                        e[3] = nby - s[3];
-                        e[4] = nbz - s[4];
-                        float chi2 = 0.f;
+                for (int c = 0; c < 5; ++c) s[c] = fmaf(wA, xa[c], fmaf(wB, xb[c], fmaf(wC, xc[c], wD * xd[c])));
+                // a5: residual, occlusion test, Huber
+                const float e_d = zeta_d - s[1];
+                ok = ok && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
+                const float nt2 = fmaf(s[2], s[2], fmaf(s[3], s[3], s[4] * s[4]));
+                ok = ok && nt2 >= 0.25f;
+                if (ok) {
+                    valid = true;
+                    const float4 n = __ldg(pts_n + pt_off + k);
+                    const float nbx = fmaf(M[0], n.x, fmaf(M[1], n.y, M[2] * n.z));
+                    const float nby = fmaf(M[3], n.x, fmaf(M[4], n.y, M[5] * n.z));
+                    const float nbz = fmaf(M[6], n.x, fmaf(M[7], n.y, M[8] * n.z));
+                    e[0] = p.w - s[0];
+                    e[1] = e_d;
+                    e[2] = nbx - s[2];
+                    e[3] = nby - s[3];
+                    e[4] = nbz - s[4];
+                    float chi2 = 0.f;
 #pragma unroll
-                        for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
-                        if (!(chi2 < INFINITY)) {
-                            // a NaN or infinite input value (intensity, normal): the residual is
-                            // left out of H, b and F and counted in the status word
-                            valid = false;
-                            nonfin += 1.f;
+                    for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
+                    if (!(chi2 < INFINITY)) {
+                        // a NaN or infinite input value (intensity, normal): the residual is
+                        // left out of H, b and F and counted in the status word
+                        valid = false;
+                        nonfin += 1.f;
+                    } else {
+                        float rho;
+                        if (chi2 <= prm.huber_delta2) {
+                            w = 1.f;
+                            rho = chi2;
                         } else {
-                            float rho;
-                            if (chi2 <= prm.huber_delta2) {
-                                w = 1.f;
-                                rho = chi2;
-                            } else {
-                                const float chi = sqrtf(chi2);
-                                w = prm.huber_delta / chi;
-                                rho = fmaf(2.f * prm.huber_delta, chi, -prm.huber_delta2);
-                            }
-                            cost += rho;
-                            cnt += 1.f;
+                            const float chi = sqrtf(chi2);
+                            w = prm.huber_delta / chi;
+                            rho = fmaf(2.f * prm.huber_delta, chi, -prm.huber_delta2);
                         }
+                        cost += rho;
+                        cnt += 1.f;
                     }
                 }
             }
@@ -578,36 +637,43 @@ cudaError_t launch_pair_pose(const double* poses, const int2* pair_frames, const
     return cudaGetLastError();
 }
 
-template <int TEXEL, bool FULL, bool MASK, int MINB>
+template <int TEXEL, bool FULL, bool MASK, int MINB, bool STAGE>
 static void* lin_kernel() {
-    return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK, MINB>);
+    return reinterpret_cast<void*>(&k_linearize<TEXEL, FULL, MASK, MINB, STAGE>);
 }
 
 // Occupancy variants (blocks of 128 threads per SM the register budget aims
 // at): full pass 4, 6, 7 or 8 (128, 80, 72 or 64 registers: 16 to 32 warps per
 // SM), cost-only pass 6, 7, 9 or 10 (72 to 48 registers: 28 to 40 warps) for
-// variants 0 .. 3.  Fewer registers per thread trade spills for warps to hide
+// variants 0 .. 3; variants 4 .. 7 are the same budgets with the taps read from
+// TMA-staged tiles (FP16 texels without mask export; otherwise they run as
+// variants 0 .. 3).  Fewer registers per thread trade spills for warps to hide
 // gather latency; the block size only sets the occupancy steps (the warps of a
-// block share nothing but their queue regions).
-template <int TEXEL, bool FULL, bool MASK>
+// block share nothing but their queue and tile regions).
+template <int TEXEL, bool FULL, bool MASK, bool STAGE>
 static void* pick_minb(int variant) {
-    if (FULL) {
-        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 8>();
-        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 7>();
-        return variant ? lin_kernel<TEXEL, FULL, MASK, 6>() : lin_kernel<TEXEL, FULL, MASK, 4>();
+    if constexpr (FULL) {
+        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 8, STAGE>();
+        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 7, STAGE>();
+        return variant ? lin_kernel<TEXEL, FULL, MASK, 6, STAGE>() : lin_kernel<TEXEL, FULL, MASK, 4, STAGE>();
+    } else {
+        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 10, STAGE>();
+        if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 9, STAGE>();
+        return variant ? lin_kernel<TEXEL, FULL, MASK, 7, STAGE>() : lin_kernel<TEXEL, FULL, MASK, 6, STAGE>();
     }
-    if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 10>();
-    if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 9>();
-    return variant ? lin_kernel<TEXEL, FULL, MASK, 7>() : lin_kernel<TEXEL, FULL, MASK, 6>();
 }
 
 static void* pick(int texel_precision, bool full, bool mask, int variant) {
+    const bool stage = variant >= 4;
+    variant &= 3;
     if (texel_precision == 1) {
-        if (full) return mask ? pick_minb<1, true, true>(variant) : pick_minb<1, true, false>(variant);
-        return mask ? pick_minb<1, false, true>(variant) : pick_minb<1, false, false>(variant);
+        if (stage && !mask)
+            return full ? pick_minb<1, true, false, true>(variant) : pick_minb<1, false, false, true>(variant);
+        if (full) return mask ? pick_minb<1, true, true, false>(variant) : pick_minb<1, true, false, false>(variant);
+        return mask ? pick_minb<1, false, true, false>(variant) : pick_minb<1, false, false, false>(variant);
     }
-    if (full) return mask ? pick_minb<0, true, true>(variant) : pick_minb<0, true, false>(variant);
-    return mask ? pick_minb<0, false, true>(variant) : pick_minb<0, false, false>(variant);
+    if (full) return mask ? pick_minb<0, true, true, false>(variant) : pick_minb<0, true, false, false>(variant);
+    return mask ? pick_minb<0, false, true, false>(variant) : pick_minb<0, false, false, false>(variant);
 }
 
 int linearize_grid(int texel_precision, bool full, int variant) {
@@ -625,8 +691,10 @@ cudaError_t launch_linearize(bool full, bool mask, int texel_precision, const in
                              const void* texels, const LinParams& prm, float* partials, uint32_t* mask_bits,
                              int grid, int variant, cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    const int warps = (n_chunks + 0);
+    const int warps = n_chunks;  // one work item per warp at a time
     if (grid * (kLinThreads / 32) > warps) grid = (warps + kLinThreads / 32 - 1) / (kLinThreads / 32);
+    // staged variants need the frames' tensor maps
+    if (!prm.tmaps) variant &= 3;
     void* fn = pick(texel_precision, full, mask, variant);
     LinParams prm_copy = prm;
     void* args[] = {(void*)&chunks, (void*)&n_chunks, (void*)&queue, (void*)&ps, (void*)&pp, (void*)&pts_pg,

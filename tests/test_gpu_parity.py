@@ -221,6 +221,51 @@ def test_autotuned_variants_agree(oracle_lib, street3):
     p.close()
 
 
+@pytest.mark.parametrize("which", ["room8", "street3"])
+def test_staged_tiles_give_the_same_system(oracle_lib, which, request):
+    """Variants 4 .. 7 read each step's bilinear taps from a TMA-staged tile of
+    the target's FP16 texels (steps whose taps do not fit the tile, or straddle
+    the spherical wrap seam, read them directly): the same texel values, so the
+    system, cost and count equal those of variants 0 .. 3 bit for bit, for the
+    full and the cost-only pass, and match the oracle; no tile wait runs out."""
+    import paper_2303_16878_gb300 as pba
+    w = request.getfixturevalue(which)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, 1))
+    p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
+    for v in range(pba._lib.PBA_N_VARIANTS // 2):
+        out = []
+        for vv in (v, v + pba._lib.PBA_N_VARIANTS // 2):
+            p.set_variants(vv, vv)
+            assert p.tuning()["variant_full"] == vv
+            cost, count = p.linearize()
+            H, b = p.get_system()
+            sys_ = p.get_pair_system()
+            st = p.solve_step(1e-3)  # the cost-only pass at the candidate
+            p.set_poses(w.poses_init)
+            p.set_lambda(None)
+            it = p.iterate()  # the graph's speculative full pass at the candidate
+            p.set_poses(w.poses_init)
+            out.append((cost, count, H, b, sys_["H"], st["new_cost"], it["n_valid"], it["new_cost"]))
+        a, c = out
+        assert a[0] == c[0] and a[1] == c[1] and a[5] == c[5] and a[6] == c[6] and a[7] == c[7]
+        assert np.array_equal(a[2], c[2]) and np.array_equal(a[3], c[3]) and np.array_equal(a[4], c[4])
+        assert rel(c[2], ref["H"]) <= TOL_H and abs(c[0] - ref["cost"]) <= TOL_COST * ref["cost"]
+    assert p.tuning()["tile_err"] == 0
+    p.close()
+
+
+def test_staged_variants_fall_back_without_tiles(room8):
+    """FP32 texels have no staged tiles: variants 4 .. 7 run (and are reported)
+    as 0 .. 3."""
+    import paper_2303_16878_gb300 as pba
+    p = make(room8, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F32)
+    p.set_variants(6, 5)
+    t = p.tuning()
+    assert (t["variant_full"], t["variant_cost"]) == (2, 1)
+    p.linearize()
+    p.close()
+
+
 def test_autotuner_reports_its_tuple_and_caches_it(oracle_lib, street3):
     """pba_autotune searches work-item size x tail size x occupancy variant;
     the chosen tuple is reported, the system with it matches the oracle, and
