@@ -104,11 +104,10 @@ def measured_hbm(path: str = None):
 # size, tail item size); settings without an entry report null
 LINEARIZE_NCU = {
     # profiles/k_linearize_lidar_street_50x64x1024.md (ncu --set full, one launch at the initial poses)
-    ("street", 1, 2048, 256): {"dram_bytes": 446.6e6 + 8.8e6,
-                               "units": {"sm_issue": 0.697, "l1_data_pipe": 0.583, "l2": 0.221, "dram": 0.056}},
+    ("street", 1, 1024, 128): {"dram_bytes": 372.6e6 + 12.2e6,
+                               "units": {"sm_issue": 0.650, "l1_data_pipe": 0.599, "l2": 0.225, "dram": 0.047}},
     # profiles/k_linearize_joint_hall_900.md (DRAM bytes only: one pass on the full workload)
-    ("joint", 1, 1024, 128): {"dram_bytes": 45.86e9 + 0.24e9, "units": None},
-    ("joint", 1, 512, 128): {"dram_bytes": 40.77e9 + 0.43e9, "units": None},
+    ("joint", 1, 512, 128): {"dram_bytes": 40.76e9 + 0.53e9, "units": None},
 }
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0

@@ -472,7 +472,7 @@ int pba_optimize(pba_problem* p, int n_levels, const int32_t* max_iters, double 
 int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
 /* Variants of the batched linearisation kernel: register budgets for 4, 6, 7
- * or 8 (full pass) and 6, 7, 9 or 10 (cost-only pass) blocks of 128 threads
+ * or 5 (full pass) and 6, 7, 9 or 10 (cost-only pass) blocks of 128 threads
  * per SM, variants 0 .. 3; variants 4 .. 7 have the same budgets and read each
  * 32-point step's bilinear taps from a 4 x 48-pixel tile of the target's
  * texels that one TMA tensor copy staged in shared memory (FP16 texels and

@@ -104,6 +104,57 @@ __device__ __forceinline__ Texel load_texel(const void* __restrict__ base, int i
     return t;
 }
 
+// A bilinear tap as loaded.  FP16 texels keep their words until a channel other
+// than the FP32 depth is needed, so the binary16 conversions are only done for
+// points whose taps are usable and that pass the occlusion test.
+template <int TEXEL>
+struct Tap;
+template <>
+struct Tap<1> {
+    uint4 v;
+    __device__ __forceinline__ bool usable() const { return v.w != 0u; }
+    __device__ __forceinline__ float depth() const { return __uint_as_float(v.x); }
+    __device__ __forceinline__ void rest(float& g, float& nx, float& ny, float& nz) const {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
+        g = a.x;
+        nx = a.y;
+        ny = b.x;
+        nz = b.y;
+    }
+    // (g, n_x), (n_y, n_z)
+    __device__ __forceinline__ void rest2(float2& gnx, float2& nynz) const {
+        gnx = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        nynz = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
+    }
+};
+template <>
+struct Tap<0> {
+    Texel t;
+    __device__ __forceinline__ bool usable() const { return t.usable; }
+    __device__ __forceinline__ float depth() const { return t.d; }
+    __device__ __forceinline__ void rest(float& g, float& nx, float& ny, float& nz) const {
+        g = t.g;
+        nx = t.nx;
+        ny = t.ny;
+        nz = t.nz;
+    }
+    __device__ __forceinline__ void rest2(float2& gnx, float2& nynz) const {
+        gnx = make_float2(t.g, t.nx);
+        nynz = make_float2(t.ny, t.nz);
+    }
+};
+
+template <int TEXEL>
+__device__ __forceinline__ Tap<TEXEL> load_tap(const void* __restrict__ base, int idx) {
+    Tap<TEXEL> a;
+    if constexpr (TEXEL == 1)
+        a.v = __ldg(reinterpret_cast<const uint4*>(base) + idx);
+    else
+        a.t = load_texel<0>(base, idx);
+    return a;
+}
+
 __device__ __forceinline__ void channels(const Texel& t, float (&x)[5]) {
     x[0] = t.g;
     x[1] = t.d;

@@ -68,21 +68,77 @@ __global__ void k_pair_pose(const double* __restrict__ poses, const int2* __rest
     out[p] = o;
 }
 
-// H6 (upper triangle, row-major 21) += s * J J^T ; b6 += s * J e
-__device__ __forceinline__ void accum_row(float (&H)[21], float (&bb)[6], const float (&J)[6], float sw, float e) {
-    float t[6];
+// One lane's 21 + 6 sums of H6 = sum s J J^T (upper triangle) and b6 = sum s J e.
+// Where both factors of two sums sit in the same register pairs, the pair is
+// updated by one packed FP32 instruction of sm_100-class SMs (FFMA2 / FMUL2: two
+// single-precision operations, each rounded as fmaf / a * b would be, so every
+// sum gets exactly the operations of the scalar version):
+//   d: (H00, H11), (H22, H33), (H44, H55)  = (t0, t1) * (J0, J1), ...
+//   o: (H02, H13), (H04, H15), (H24, H35)  = (t0, t1) * (J2, J3), (t0, t1) * (J4, J5), (t2, t3) * (J4, J5)
+//   b: (b0, b1), (b2, b3), (b4, b5)         = (t0, t1) * (e, e), ...
+// with t = s J; the other nine sums are scalar FMAs (pairing them would need
+// swapped copies of J, which cost as many moves as they save).
+struct Acc6 {
+    float2 d[3], o[3], b[3];
+    float h01, h03, h05, h12, h14, h23, h25, h34, h45;
+};
+
+__device__ __forceinline__ void acc_zero(Acc6& A) {
 #pragma unroll
-    for (int a = 0; a < 6; ++a) t[a] = sw * J[a];
-    int k = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-#pragma unroll
-        for (int c = a; c < 6; ++c) {
-            H[k] = fmaf(t[a], J[c], H[k]);
-            ++k;
-        }
-        bb[a] = fmaf(t[a], e, bb[a]);
+    for (int i = 0; i < 3; ++i) A.d[i] = A.o[i] = A.b[i] = make_float2(0.f, 0.f);
+    A.h01 = A.h03 = A.h05 = A.h12 = A.h14 = A.h23 = A.h25 = A.h34 = A.h45 = 0.f;
+}
+
+// Sum k of H6 in upper-triangle row-major order (the partials' layout), k < 21.
+__device__ __forceinline__ float acc_h(const Acc6& A, int k) {
+    switch (k) {
+        case 0: return A.d[0].x;   // H00
+        case 1: return A.h01;
+        case 2: return A.o[0].x;   // H02
+        case 3: return A.h03;
+        case 4: return A.o[1].x;   // H04
+        case 5: return A.h05;
+        case 6: return A.d[0].y;   // H11
+        case 7: return A.h12;
+        case 8: return A.o[0].y;   // H13
+        case 9: return A.h14;
+        case 10: return A.o[1].y;  // H15
+        case 11: return A.d[1].x;  // H22
+        case 12: return A.h23;
+        case 13: return A.o[2].x;  // H24
+        case 14: return A.h25;
+        case 15: return A.d[1].y;  // H33
+        case 16: return A.h34;
+        case 17: return A.o[2].y;  // H35
+        case 18: return A.d[2].x;  // H44
+        case 19: return A.h45;
+        default: return A.d[2].y;  // H55
     }
+}
+
+// H6 += s J J^T ; b6 += s J e for one residual row.
+__device__ __forceinline__ void accum_row(Acc6& A, const float (&J)[6], float sw, float e) {
+    const float2 j01 = make_float2(J[0], J[1]), j23 = make_float2(J[2], J[3]), j45 = make_float2(J[4], J[5]);
+    const float2 s2 = make_float2(sw, sw), e2 = make_float2(e, e);
+    const float2 t01 = __fmul2_rn(s2, j01), t23 = __fmul2_rn(s2, j23), t45 = __fmul2_rn(s2, j45);
+    A.d[0] = __ffma2_rn(t01, j01, A.d[0]);
+    A.d[1] = __ffma2_rn(t23, j23, A.d[1]);
+    A.d[2] = __ffma2_rn(t45, j45, A.d[2]);
+    A.o[0] = __ffma2_rn(t01, j23, A.o[0]);
+    A.o[1] = __ffma2_rn(t01, j45, A.o[1]);
+    A.o[2] = __ffma2_rn(t23, j45, A.o[2]);
+    A.h01 = fmaf(t01.x, J[1], A.h01);
+    A.h03 = fmaf(t01.x, J[3], A.h03);
+    A.h05 = fmaf(t01.x, J[5], A.h05);
+    A.h12 = fmaf(t01.y, J[2], A.h12);
+    A.h14 = fmaf(t01.y, J[4], A.h14);
+    A.h23 = fmaf(t23.x, J[3], A.h23);
+    A.h25 = fmaf(t23.x, J[5], A.h25);
+    A.h34 = fmaf(t23.y, J[4], A.h34);
+    A.h45 = fmaf(t45.x, J[5], A.h45);
+    A.b[0] = __ffma2_rn(t01, e2, A.b[0]);
+    A.b[1] = __ffma2_rn(t23, e2, A.b[1]);
+    A.b[2] = __ffma2_rn(t45, e2, A.b[2]);
 }
 
 constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two >= 63)
@@ -99,8 +155,7 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
                                                bool wrap, const float (&M)[9], const float (&om)[5],
                                                const float4* __restrict__ pg, const float4* __restrict__ pn,
                                                const void* __restrict__ tex, const float4* __restrict__ gtex,
-                                               long long tex_off, int grad_mode, float (&Hacc)[21],
-                                               float (&bacc)[6]) {
+                                               long long tex_off, int grad_mode, Acc6& acc) {
     float e[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) e[c] = Q[c][slot];
@@ -212,7 +267,7 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
             J[4] += fmaf(n2z, mx, -n2x * mz);
             J[5] += fmaf(n2x, my, -n2y * mx);
         }
-        accum_row(Hacc, bacc, J, w * om[c], e[c]);
+        accum_row(acc, J, w * om[c], e[c]);
     }
 }
 
@@ -274,13 +329,9 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         const float umin = wrap ? -3.4e38f : 1.f;
         const float vmax = (float)(Hh - 2);
 
-        float Hacc[21], bacc[6], cost = 0.f, cnt = 0.f, nonfin = 0.f;
-        if (FULL) {
-#pragma unroll
-            for (int k = 0; k < 21; ++k) Hacc[k] = 0.f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) bacc[k] = 0.f;
-        }
+        Acc6 acc;
+        float cost = 0.f, cnt = 0.f, nonfin = 0.f;
+        if (FULL) acc_zero(acc);
         int head = 0, tail = 0;  // warp-uniform queue counters
         const int end = first + count;
         // the point of the next iteration is loaded one iteration ahead (its
@@ -360,35 +411,52 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
             }
             if (ok) {
                 // a4: the four bilinear taps; their usable flags decide the 12-texel stencil
-                Texel A, B, C, D;
-                if (STAGE && staged) {
-                    const uint4* T = s_tile[warp];
-                    const int i0 = (r0 - t_r) * kTileCols + (c0 - t_c);
-                    A = texel_of(T[i0]);
-                    B = texel_of(T[i0 + 1]);
-                    C = texel_of(T[i0 + kTileCols]);
-                    D = texel_of(T[i0 + kTileCols + 1]);
-                } else {
-                    const int rr0 = r0 * W, rp1 = rr0 + W;
-                    A = load_texel<TEXEL>(tex_j, rr0 + c0);
-                    B = load_texel<TEXEL>(tex_j, rr0 + cp1);
-                    C = load_texel<TEXEL>(tex_j, rp1 + c0);
-                    D = load_texel<TEXEL>(tex_j, rp1 + cp1);
+                Tap<TEXEL> A, B, C, D;
+                if constexpr (STAGE) {
+                    if (staged) {
+                        const uint4* T = s_tile[warp];
+                        const int i0 = (r0 - t_r) * kTileCols + (c0 - t_c);
+                        A.v = T[i0];
+                        B.v = T[i0 + 1];
+                        C.v = T[i0 + kTileCols];
+                        D.v = T[i0 + kTileCols + 1];
+                    }
                 }
-                ok = A.usable && B.usable && C.usable && D.usable;
+                if (!(STAGE && staged)) {
+                    const int rr0 = r0 * W, rp1 = rr0 + W;
+                    A = load_tap<TEXEL>(tex_j, rr0 + c0);
+                    B = load_tap<TEXEL>(tex_j, rr0 + cp1);
+                    C = load_tap<TEXEL>(tex_j, rp1 + c0);
+                    D = load_tap<TEXEL>(tex_j, rp1 + cp1);
+                }
+                // a5: the depth channel first (FP32 in every texel) and the occlusion
+                // test; the other channels are only converted and interpolated for the
+                // points that pass
                 const float wA = (1.f - fa) * (1.f - fb), wB = fa * (1.f - fb), wC = (1.f - fa) * fb, wD = fa * fb;
-                float xa[5], xb[5], xc[5], xd[5], s[5];
-                channels(A, xa);
-                channels(B, xb);
-                channels(C, xc);
-                channels(D, xd);
-#pragma unroll
-                for (int c = 0; c < 5; ++c) s[c] = fmaf(wA, xa[c], fmaf(wB, xb[c], fmaf(wC, xc[c], wD * xd[c])));
-                // a5: residual, occlusion test, Huber
+                float s[5];
+                s[1] = fmaf(wA, A.depth(), fmaf(wB, B.depth(), fmaf(wC, C.depth(), wD * D.depth())));
                 const float e_d = zeta_d - s[1];
-                ok = ok && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
-                const float nt2 = fmaf(s[2], s[2], fmaf(s[3], s[3], s[4] * s[4]));
-                ok = ok && nt2 >= 0.25f;
+                ok = A.usable() && B.usable() && C.usable() && D.usable() &&
+                     fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
+                if (ok) {
+                    // (g, n_x) and (n_y, n_z) of the four taps as register pairs, interpolated
+                    // with packed FMAs (each rounded as fmaf, in the same order)
+                    float2 a0, a1, b0, b1, c0p, c1p, d0, d1;
+                    A.rest2(a0, a1);
+                    B.rest2(b0, b1);
+                    C.rest2(c0p, c1p);
+                    D.rest2(d0, d1);
+                    const float2 wA2 = make_float2(wA, wA), wB2 = make_float2(wB, wB);
+                    const float2 wC2 = make_float2(wC, wC), wD2 = make_float2(wD, wD);
+                    const float2 i0 = __ffma2_rn(wA2, a0, __ffma2_rn(wB2, b0, __ffma2_rn(wC2, c0p, __fmul2_rn(wD2, d0))));
+                    const float2 i1 = __ffma2_rn(wA2, a1, __ffma2_rn(wB2, b1, __ffma2_rn(wC2, c1p, __fmul2_rn(wD2, d1))));
+                    s[0] = i0.x;
+                    s[2] = i0.y;
+                    s[3] = i1.x;
+                    s[4] = i1.y;
+                    const float nt2 = fmaf(s[2], s[2], fmaf(s[3], s[3], s[4] * s[4]));
+                    ok = nt2 >= 0.25f;
+                }
                 if (ok) {
                     valid = true;
                     const float4 n = __ldg(pts_n + pt_off + k);
@@ -447,8 +515,7 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 __syncwarp();
                 if (tail - head >= 32) {
                     jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
-                                          pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, Hacc,
-                                          bacc);
+                                          pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, acc);
                     head += 32;
                     __syncwarp();
                 }
@@ -457,8 +524,7 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         if (FULL && tail > head) {
             if (lane < tail - head)
                 jacobian_stage<TEXEL>(Q, (head + lane) & (kQueue - 1), model, fx, fy, W, wrap, M, om,
-                                      pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, Hacc,
-                                          bacc);
+                                      pts_pg + pt_off, pts_n + pt_off, tex, prm.gtex, tex_off, prm.grad_mode, acc);
             __syncwarp();
         }
 
@@ -469,7 +535,12 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
         if (FULL) {
             float* tab = &Q[0][0];  // 27 x 32 floats <= kQItems x kQueue
 #pragma unroll
-            for (int j = 0; j < 27; ++j) tab[j * 32 + lane] = j < 21 ? Hacc[j] : bacc[j - 21];
+            for (int j = 0; j < 21; ++j) tab[j * 32 + lane] = acc_h(acc, j);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                tab[(21 + 2 * j) * 32 + lane] = acc.b[j].x;
+                tab[(22 + 2 * j) * 32 + lane] = acc.b[j].y;
+            }
             __syncwarp();
             if (lane < 27) {
                 // rows start on bank 0: lane j reads its row from float4 (q + j) mod 8 on,
@@ -643,7 +714,7 @@ static void* lin_kernel() {
 }
 
 // Occupancy variants (blocks of 128 threads per SM the register budget aims
-// at): full pass 4, 6, 7 or 8 (128, 80, 72 or 64 registers: 16 to 32 warps per
+// at): full pass 4, 6, 7 or 5 (128, 80, 72 or 96 registers: 16 to 28 warps per
 // SM), cost-only pass 6, 7, 9 or 10 (72 to 48 registers: 28 to 40 warps) for
 // variants 0 .. 3; variants 4 .. 7 are the same budgets with the taps read from
 // TMA-staged tiles (FP16 texels without mask export; otherwise they run as
@@ -653,7 +724,7 @@ static void* lin_kernel() {
 template <int TEXEL, bool FULL, bool MASK, bool STAGE>
 static void* pick_minb(int variant) {
     if constexpr (FULL) {
-        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 8, STAGE>();
+        if (variant == 3) return lin_kernel<TEXEL, FULL, MASK, 5, STAGE>();
         if (variant == 2) return lin_kernel<TEXEL, FULL, MASK, 7, STAGE>();
         return variant ? lin_kernel<TEXEL, FULL, MASK, 6, STAGE>() : lin_kernel<TEXEL, FULL, MASK, 4, STAGE>();
     } else {

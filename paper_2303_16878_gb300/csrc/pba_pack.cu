@@ -1,16 +1,16 @@
-// pba_pack.cu -- per-frame packing (once per upload), in three passes over
-// all SMs, then the central differences.
+// pba_pack.cu -- per-frame packing (once per upload), in two passes over all
+// SMs, then the central differences.
 //
 // For every pixel u of a frame (Sec. IV-A five-channel cue image):
 //   - pass 1 (k_pack_valid): its validity as a byte, and per tile of 1024
 //     pixels the count of valid ones;
-//   - pass 2 (k_pack_tex): a sampling texel: d (FP32, 0 when the pixel is not
-//     valid), g and n in FP16 or FP32, and the usable flag (the pixel and its
-//     four neighbours valid), so one bilinear tap is one 16- or 32-byte load;
-//   - pass 3 (k_pack_points): when the pixel is valid, a pixel-point
-//     p_u = R_o pi^-1(u, d) + t_o with its intensity g_u, normal
-//     n_u^o = R_o n_u (Supp., p_u) and pixel index, written in raster order at
-//     the offset given by the counts of the frame's earlier tiles;
+//   - pass 2 (k_pack_points), from one read of the pixel's channels: a
+//     sampling texel: d (FP32, 0 when the pixel is not valid), g and n in FP16
+//     or FP32, and the usable flag (the pixel and its four neighbours valid),
+//     so one bilinear tap is one 16- or 32-byte load; and, when the pixel is
+//     valid, a pixel-point p_u = R_o pi^-1(u, d) + t_o with its intensity g_u,
+//     normal n_u^o = R_o n_u (Supp., p_u) and pixel index, written in raster
+//     order at the offset given by the counts of the frame's earlier tiles;
 //   - k_grad: the central differences of the Supp. at every usable pixel.
 // Unprojection pi^-1 (Sec. III): pinhole p = d K^-1 (u, v, 1)^T; spherical
 // p = d (cos el cos az, cos el sin az, sin el) with az = (u - c_x) / f_x,
@@ -76,20 +76,12 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_valid(const float* __rest
     if (threadIdx.x == 0) tile_counts[(long long)f * max_tiles + tile] = count;
 }
 
-// Pass 2: the sampling texel of every pixel, with its usable flag (the pixel
-// and its four neighbours are valid, i.e. the central differences of the Supp.
-// are defined there; columns wrap for the spherical model).
+// The sampling texel of a pixel, with its usable flag (the pixel and its four
+// neighbours are valid, i.e. the central differences of the Supp. are defined
+// there; columns wrap for the spherical model).
 template <int TEXEL>
-__global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restrict__ raw,
-                                                           const FrameInfo* __restrict__ frames,
-                                                           const int* __restrict__ frame_ids,
-                                                           const unsigned char* __restrict__ valid_px, void* texels) {
-    const FrameInfo fr = frames[frame_ids[blockIdx.y]];
-    const int npx = fr.width * fr.height;
-    const int px = blockIdx.x * kPackThreads + threadIdx.x;
-    if (px >= npx) return;
-    const unsigned char* vf = valid_px + fr.px_offset;
-    const bool valid = vf[px] != 0;
+__device__ __forceinline__ void write_texel(const FrameInfo& fr, const unsigned char* __restrict__ vf, int px,
+                                            bool valid, const float (&c)[5], void* texels) {
     bool usable = valid;
     if (usable) {
         const int col = px % fr.width, row = px / fr.width;
@@ -99,10 +91,6 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restri
         usable = row > 0 && row < fr.height - 1 && cl >= 0 && cr >= 0 && vf[px - fr.width] && vf[px + fr.width] &&
                  vf[row * fr.width + cl] && vf[row * fr.width + cr];
     }
-    const float* src = raw + (fr.px_offset + px) * 5;
-    float c[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) c[q] = src[q];
     const long long t = fr.px_offset + px;
     if (TEXEL == 1) {
         Tex16 tx;
@@ -118,16 +106,19 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_tex(const float* __restri
     }
 }
 
-// Pass 3: the valid pixels of a tile as pixel-points p_u = R_o pi^-1(u, d) + t_o
-// with g_u, n_u^o = R_o n_u and the pixel index, written in raster order at the
-// tile's offset (the counts of the frame's earlier tiles); the CTA of tile 0
-// also writes the frame's point count.
+// Pass 2: every pixel's texel (write_texel) and the tile's valid pixels as
+// pixel-points p_u = R_o pi^-1(u, d) + t_o with g_u, n_u^o = R_o n_u and the
+// pixel index, written in raster order at the tile's offset (the counts of the
+// frame's earlier tiles), from one read of the pixel's channels; the CTA of tile
+// 0 also writes the frame's point count.
+template <int TEXEL>
 __global__ void __launch_bounds__(kPackThreads) k_pack_points(const float* __restrict__ raw,
                                                               const FrameInfo* __restrict__ frames,
                                                               const SensorDev* __restrict__ sensors,
                                                               const int* __restrict__ frame_ids,
                                                               const unsigned char* __restrict__ valid_px,
                                                               const int* __restrict__ tile_counts, int max_tiles,
+                                                              void* __restrict__ texels,
                                                               float4* __restrict__ pts_pg, float4* __restrict__ pts_n,
                                                               int* __restrict__ pts_pix, int* __restrict__ n_points) {
     __shared__ int s_warp[kPackThreads / 32];
@@ -162,10 +153,11 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_points(const float* __res
         const int px = tile * kPackTile + k * kPackThreads + threadIdx.x;
         const bool valid = px < npx && valid_px[fr.px_offset + px] != 0;
         float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) {
+        if (px < npx) {
             const float* src = raw + (fr.px_offset + px) * 5;
 #pragma unroll
             for (int q = 0; q < 5; ++q) c[q] = src[q];
+            write_texel<TEXEL>(fr, valid_px + fr.px_offset, px, valid, c, texels);
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, valid);
         if (lane == 0) s_warp[warp] = __popc(ballot);
@@ -262,15 +254,17 @@ cudaError_t launch_pack(const float* raw, const FrameInfo* frames, const SensorD
     const int max_tiles = pack_tiles(max_px);
     for (int f0 = 0; f0 < n; f0 += 65535) {  // grid.y limit
         const int nf = n - f0 < 65535 ? n - f0 : 65535;
-        const dim3 grid(max_tiles, nf), grid_px((max_px + kPackThreads - 1) / kPackThreads, nf);
+        const dim3 grid(max_tiles, nf);
         k_pack_valid<<<grid, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, tile_counts, max_tiles,
                                                    rmin, rmax);
         if (texel_precision == 1)
-            k_pack_tex<1><<<grid_px, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, texels);
+            k_pack_points<1><<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, valid_px,
+                                                           tile_counts, max_tiles, texels, pts_pg, pts_n, pts_pix,
+                                                           n_points);
         else
-            k_pack_tex<0><<<grid_px, kPackThreads, 0, s>>>(raw, frames, frame_ids + f0, valid_px, texels);
-        k_pack_points<<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, valid_px, tile_counts,
-                                                    max_tiles, pts_pg, pts_n, pts_pix, n_points);
+            k_pack_points<0><<<grid, kPackThreads, 0, s>>>(raw, frames, sensors, frame_ids + f0, valid_px,
+                                                           tile_counts, max_tiles, texels, pts_pg, pts_n, pts_pix,
+                                                           n_points);
     }
     if (gtex && max_px > 0) {
         for (int f0 = 0; f0 < n; f0 += 65535) {
