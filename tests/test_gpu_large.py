@@ -15,7 +15,8 @@ cost to 1e-5 (relative Frobenius), each pair's H12 and b12 to 1e-3 and cost
 to 1e-4 (float32 pixel-points at depth discontinuities; see the helper); at
 most 1e-5 of the sample's residuals (+2) decided the other way; for the
 whole system: exact symmetry and the gauge null space; one LM iteration
-runs.  The
+runs.  The TMA-staged kernel variant gives the unstaged variant's per-pair
+systems bit for bit at full size.  The
 generators render on the GPU (torch), so these tests need one; the inputs
 are the same seeded scenes on any device.
 """
@@ -100,4 +101,27 @@ def test_hall_adjoint_on_a_four_frame_subset(oracle_lib):
     gt = autograd.tangent_gradient(p, X, dposes.reshape(-1, 3, 4)).reshape(-1).cpu().numpy()
     assert rel(gt, 2.0 * ref["b"]) <= 1e-4
     assert abs(cost - ref["cost"]) <= 1e-5 * ref["cost"]
+    p.close()
+
+
+@pytest.mark.parametrize("name", ["hall", "street_graph"])
+def test_staged_tiles_at_full_size(name):
+    """The TMA-staged variant of the kernel (taps of each 32-point step from a
+    shared-memory tile) on the full-size configurations, whose steps straddle
+    tile edges, image borders and (LiDAR 128 x 2048) the wrap seam: the per-pair
+    systems, costs and counts equal the unstaged variant's bit for bit, and no
+    tile wait ran out."""
+    import paper_2303_16878_gb300 as pba
+    w = big(name)
+    p = pba.problem_from_workload(w, path=pba.PBA_PATH_BATCHED, texel=pba.PBA_TEXEL_F16, solver=pba.PBA_SOLVE_MIXED)
+    out = []
+    for v in (1, 1 + pba._lib.PBA_N_VARIANTS // 2):
+        p.set_variants(v, v)
+        cost, count = p.linearize()
+        out.append((cost, count, p.get_pair_system()))
+    (c0, n0, s0), (c1, n1, s1) = out
+    assert c0 == c1 and n0 == n1
+    for key in ("H", "b", "cost", "count"):
+        assert np.array_equal(s0[key], s1[key]), key
+    assert p.tuning()["tile_err"] == 0
     p.close()
