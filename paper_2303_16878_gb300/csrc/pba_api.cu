@@ -1639,19 +1639,21 @@ int pba_iterate_frames(pba_problem* p, const float* channels, const double* pose
         if ((st = ready(p))) return st;
         if ((st = enqueue_linearize(p, p->stream, &nl))) return st;
     } else {
-        if (!p->lane_copy) {
+        // streams, events and buffers of the lanes, created on first use (each one
+        // that is still missing, so that a failed earlier attempt is completed)
+        if (!p->lane_pack) {
             int least = 0, greatest = 0;
             CUDA_TRY(p, cudaDeviceGetStreamPriorityRange(&least, &greatest));
-            CUDA_TRY(p, cudaStreamCreateWithFlags(&p->lane_copy, cudaStreamNonBlocking));
             CUDA_TRY(p, cudaStreamCreateWithPriority(&p->lane_pack, cudaStreamNonBlocking, greatest));
-            CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_start, cudaEventDisableTiming));
-            for (int l = 0; l < p->kFrameLanes; ++l) {
-                CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_copied[l], cudaEventDisableTiming));
-                CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_ready[l], cudaEventDisableTiming));
-            }
-            CUDA_TRY(p, cudaMalloc((void**)&p->d_seg_queue, sizeof(int) * p->kFrameLanes));
-            CUDA_TRY(p, cudaMallocHost((void**)&p->h_counts, sizeof(int) * (size_t)p->N));
         }
+        if (!p->lane_copy) CUDA_TRY(p, cudaStreamCreateWithFlags(&p->lane_copy, cudaStreamNonBlocking));
+        if (!p->lane_start) CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_start, cudaEventDisableTiming));
+        for (int l = 0; l < p->kFrameLanes; ++l) {
+            if (!p->lane_copied[l]) CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_copied[l], cudaEventDisableTiming));
+            if (!p->lane_ready[l]) CUDA_TRY(p, cudaEventCreateWithFlags(&p->lane_ready[l], cudaEventDisableTiming));
+        }
+        if (!p->d_seg_queue) CUDA_TRY(p, cudaMalloc((void**)&p->d_seg_queue, sizeof(int) * p->kFrameLanes));
+        if (!p->h_counts) CUDA_TRY(p, cudaMallocHost((void**)&p->h_counts, sizeof(int) * (size_t)p->N));
         // lanes of whole frames, about equal in bytes
         std::vector<int> first(1, 0);
         for (int l = 1; l < p->kFrameLanes; ++l) {
