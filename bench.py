@@ -21,7 +21,13 @@ before each step.  FP16 texels, FP32 residuals and Jacobians, FP64 pair
 reduction and an FP64-accurate solve (block-sparse FP32 factorisation with
 FP64 refinement for the large pose graphs).
 
+End to end (`e2e`): each step hands all frames (4.47 GB) and the poses to
+pba_iterate_frames from pinned host memory (the copies overlapped with the
+linearisation of the pairs whose frames have arrived) and reads the poses
+back; mean, median and minimum step times are reported.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                  [--tuning VF,VC,CHUNK,TAIL]
 
 Under torchrun (N > 1) every rank runs an independent replica of the problem
 on its own GPU (the path has no exchange step); value = all ranks' residuals /
