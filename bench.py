@@ -27,7 +27,7 @@ linearisation of the pairs whose frames have arrived) and reads the poses
 back; mean, median and minimum step times are reported.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                  [--tuning VF,VC,CHUNK,TAIL]
+                  [--tuning VF,VC,CHUNK,TAIL[,RED]]
 
 Under torchrun (N > 1) every rank runs an independent replica of the problem
 on its own GPU (the path has no exchange step); value = all ranks' residuals /
@@ -107,13 +107,10 @@ def measured_hbm(path: str = None):
 # dram__bytes_read.sum + dram__bytes_write.sum of one full k_linearize launch and the
 # unit utilisations (SM issue, L1 data pipe, L2, DRAM) from ncu captures of the
 # current kernel (profiles/), keyed by (workload, occupancy variant, work-item
-# size, tail item size); settings without an entry report null
+# size, tail item size, reduction scheme); settings without an entry report null
 LINEARIZE_NCU = {
-    # profiles/k_linearize_lidar_street_50x64x1024.md (ncu --set full, one launch at the initial poses)
-    ("street", 1, 1024, 128): {"dram_bytes": 372.6e6 + 12.2e6,
-                               "units": {"sm_issue": 0.650, "l1_data_pipe": 0.599, "l2": 0.225, "dram": 0.047}},
-    # profiles/k_linearize_joint_hall_900.md (DRAM bytes only: one pass on the full workload)
-    ("joint", 1, 512, 128): {"dram_bytes": 40.76e9 + 0.53e9, "units": None},
+    # keyed by (workload, variant, work-item size, tail item size, reduction scheme);
+    # entries are retaken whenever k_linearize changes
 }
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0
@@ -136,10 +133,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     ap.add_argument("--error-pairs", type=int, default=50, help="pairs of the stated-error comparison")
-    ap.add_argument("--tuning", default=None, metavar="VF,VC,CHUNK,TAIL",
+    ap.add_argument("--tuning", default=None, metavar="VF,VC,CHUNK,TAIL[,RED]",
                     help="apply this linearisation tuning (variants of the full and cost-only pass, work-item and "
-                         "tail item size) to the main workload instead of autotuning it (pins the launch "
-                         "configuration of a profile)")
+                         "tail item size, reduction scheme: 0 table, 1 shuffle butterfly, default 0) to the main "
+                         "workload instead of autotuning it (pins the launch configuration of a profile)")
     return ap.parse_args()
 
 
@@ -310,6 +307,26 @@ def _model_split(w, prob, pair_counts=None):
     return pts, res
 
 
+def measure_fp64_rate(stream, n: int = 4096, reps: int = 5) -> float:
+    """FP64 rate of this GPU in TFLOP/s: the best of `reps` cuBLAS DGEMMs
+    (torch.matmul of two n x n float64 matrices, 2 n^3 FLOP) by CUDA events.
+    A measuring stick for the solve, which runs none of it."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    best = float("inf")
+    with torch.cuda.stream(stream):
+        for r in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.matmul(a, b)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= 2:
+                best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
 def time_iterations(prob, init, stream, flush, steps, warmup):
     """K consecutive LM iterations (graph replays) from the initial poses, each
     bracketed by CUDA events on the library's stream with L2 flushed before."""
@@ -390,8 +407,10 @@ def run_ours(args, rank, world, device):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
     if args.tuning:
-        vf, vc, chunk, tail = (int(x) for x in args.tuning.split(","))
-        prob.set_tuning(dict(variant_full=vf, variant_cost=vc, chunk=chunk, chunk_tail=tail))
+        vals = [int(x) for x in args.tuning.split(",")]
+        vf, vc, chunk, tail = vals[:4]
+        red = vals[4] if len(vals) > 4 else 0
+        prob.set_tuning(dict(variant_full=vf, variant_cost=vc, chunk=chunk, chunk_tail=tail, reduction=red))
         variants = (vf, vc)
         tuning = dict(prob.tuning(), given=True)
     else:
@@ -546,6 +565,7 @@ def run_ours(args, rank, world, device):
     f64.autotune(1)
     out["solve_f64_cholesky_ms"] = phase_times(f64, init, flush, 3)["solve"]
     f64.close()
+    out["fp64_dgemm_tflops"] = measure_fp64_rate(stream)
 
     # plain per-pair path on the same workload
     if not args.no_plain:
@@ -838,6 +858,20 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- the JSON line
 
+def solve_roof(solve_ms, pose_variables, fp64_tflops):
+    """The solve against the measured FP64 rate: the work of a dense FP64
+    Cholesky of the same system (n^3 / 3 FLOP, n = 6 x pose variables) and its
+    time at that rate, beside the block-sparse solve's own time."""
+    if not solve_ms or not pose_variables or not fp64_tflops:
+        return None
+    n = 6 * int(pose_variables)
+    gflop = n ** 3 / 3.0 / 1e9
+    return {"unknowns": n, "solve_ms": solve_ms, "fp64_dgemm_tflops_measured": fp64_tflops,
+            "dense_cholesky_gflop": gflop, "dense_cholesky_ms_at_measured_fp64": gflop / fp64_tflops,
+            "bound": "latency: a chain of dependent tile pivots with one cluster barrier each (block-sparse "
+                     "envelope factorisation in FP32 plus 3 FP64 refinement passes), not FP64 throughput"}
+
+
 def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_gbs: float,
               hbm_source: str = "measured: MEASURED_PEAKS.json hbm_gbs") -> dict:
     """The GPU arm's JSON line from the measurements in `out` (pure: no device
@@ -859,7 +893,7 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
     achieved = flops / (lin_ms / 1e3) / 1e12
     tun = out.get("tuning") or {}
     ncu = LINEARIZE_NCU.get((workload, int(out["variants"][0]), int(tun.get("chunk", 1024)),
-                             int(tun.get("chunk_tail", 256))))
+                             int(tun.get("chunk_tail", 256)), int(tun.get("reduction", 0))))
     traffic = ncu["dram_bytes"] if ncu else None
     line = {
         "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -889,6 +923,7 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
                   "envelope factorisation, one thread-block cluster per component of the pose graph, above "
                   "~800 unknowns; one dense cluster launch below",
         "solve_f64_cholesky_ms": out.get("solve_f64_cholesky_ms", out.get("solve_update_f64_ms")),
+        "solve_roof": solve_roof(ph.get("solve"), out.get("pose_variables"), out.get("fp64_dgemm_tflops")),
         "lm_step": "speculative: linearise in full at the candidate; its system becomes current on acceptance",
         "gpu_launches": out["launches"] * args.steps,
         "clocks": out["clocks"],

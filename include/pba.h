@@ -483,12 +483,15 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
 
 /* Tune the batched linearisation on this problem by timing it (each setting
  * launched repeats + 1 times, the first as warm-up): for the full pass every
- * work-item size (512, 1024, 2048 points per warp item) x size of the short
- * items that end the queue (128, 256) x variant (0 .. PBA_N_VARIANTS - 1; the
- * staged variants 4 .. 7 only where tiles are staged), then for the cost-only
+ * work-item size (512, 1024, 2048 points per warp item, i.e. 16, 32 or 64
+ * points per lane) x size of the short items that end the queue (128, 256) x
+ * variant (0 .. PBA_N_VARIANTS - 1; the staged variants 4 .. 7 only where
+ * tiles are staged) x reduction scheme of a work item's sums (0, 1: see
+ * pba_tuning), then for the cost-only
  * pass the variants at the chosen work items; settings
  * within 2 % of the fastest count as equal, and the first of them in that
- * order (work-item size, then tail size, then variant, each ascending) is
+ * order (work-item size, then tail size and variant, each ascending, then
+ * reduction 1 before 0) is
  * kept, so that timing noise does not change the choice between runs.  Later
  * iterations use the choice (pba_get_tuning reports it).  The result is
  * cached for the life of the process per configuration (device, texel
@@ -503,7 +506,12 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
 /* The settings the last pba_autotune chose (or the defaults): occupancy
  * variants of the full and the cost-only pass, the work-item size (points per
  * warp work item: 512, 1024 or 2048) and the size of the short items at the
- * end of the queue (128 or 256), whether they came from the process's cache
+ * end of the queue (128 or 256), the reduction of each work item's 30 FP32
+ * sums into its partial (0: each lane writes its sums as one column of a
+ * transposed table in the warp's shared memory and lane j adds row j; 1: a
+ * butterfly of warp shuffles in which every level halves the values a lane
+ * holds, lane j ending with sum j; the two differ only in float32 summation
+ * order), whether they came from the process's cache
  * of tuned configurations (same device, texel precision, gradient mode,
  * pairs, point counts and sensors: no timing was done), whether a staged
  * tile's wait ran past its limit since the problem was created (tile_err: 1;
@@ -515,6 +523,7 @@ typedef struct {
     int32_t chunk, chunk_tail;
     int32_t from_cache, tile_err;
     float ms_full, ms_cost;
+    int32_t reduction;
 } pba_tuning;
 int pba_get_tuning(pba_problem* p, pba_tuning* out);
 
@@ -523,12 +532,13 @@ int pba_get_tuning(pba_problem* p, pba_tuning* out);
 int pba_set_variants(pba_problem* p, int variant_full, int variant_cost);
 
 /* Apply a tuning given by the caller (e.g. one pba_get_tuning reported in an
- * earlier process) without timing anything: its variants, work-item size and
- * tail item size; from_cache, ms_full and ms_cost are ignored (reported as 0
+ * earlier process) without timing anything: its variants, work-item size,
+ * tail item size and reduction scheme; from_cache, ms_full and ms_cost are ignored (reported as 0
  * afterwards).  Rebuilds the pair plan when the work items change.  On the
  * plain path only the values are recorded.  Errors: PBA_EINVAL (tuning NULL, a
  * variant outside [0, PBA_N_VARIANTS), chunk not a multiple of 32 in
- * [32, 8192], chunk_tail not a multiple of 32 in [32, chunk]), PBA_ECUDA. */
+ * [32, 8192], chunk_tail not a multiple of 32 in [32, chunk], reduction not
+ * 0 or 1), PBA_ECUDA. */
 int pba_set_tuning(pba_problem* p, const pba_tuning* tuning);
 
 /* Instrumentation: one iteration like pba_iterate, enqueued launch by launch

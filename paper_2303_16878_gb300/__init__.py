@@ -419,21 +419,24 @@ class Problem:
 
     def tuning(self) -> Dict:
         """The settings of the linearisation (pba_get_tuning): variants (occupancy
-        budget, staged taps from 4 on), work-item sizes, whether they came from
+        budget, staged taps from 4 on), work-item sizes, the reduction scheme of
+        the work items' sums (0 shared-memory table, 1 shuffle butterfly), whether they came from
         the process's tuning cache, the tuned pass times in ms and the staged
         tiles' timeout flag."""
         t = _lib.PbaTuning()
         self._check(self._lib.pba_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
         return dict(variant_full=t.variant_full, variant_cost=t.variant_cost, chunk=t.chunk,
-                    chunk_tail=t.chunk_tail, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost,
+                    chunk_tail=t.chunk_tail, reduction=t.reduction, from_cache=bool(t.from_cache), ms_full=t.ms_full, ms_cost=t.ms_cost,
                     tile_err=int(t.tile_err))
 
     def set_tuning(self, tuning: Dict):
         """Apply a tuning as tuning() reports it (variant_full, variant_cost,
-        chunk, chunk_tail; other keys ignored) without timing anything."""
+        chunk, chunk_tail, reduction (0 when absent); other keys ignored)
+        without timing anything."""
         t = _lib.PbaTuning()
         t.variant_full, t.variant_cost = int(tuning["variant_full"]), int(tuning["variant_cost"])
         t.chunk, t.chunk_tail = int(tuning["chunk"]), int(tuning["chunk_tail"])
+        t.reduction = int(tuning.get("reduction", 0))
         self._check(self._lib.pba_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
 
     def set_variants(self, variant_full: int, variant_cost: int):

@@ -80,7 +80,7 @@ class PbaIterStats(ctypes.Structure):
 class PbaTuning(ctypes.Structure):
     _fields_ = [("variant_full", ctypes.c_int32), ("variant_cost", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("chunk_tail", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("tile_err", ctypes.c_int32),
-                ("ms_full", ctypes.c_float), ("ms_cost", ctypes.c_float)]
+                ("ms_full", ctypes.c_float), ("ms_cost", ctypes.c_float), ("reduction", ctypes.c_int32)]
 
 
 class PbaLevelStats(ctypes.Structure):

@@ -26,6 +26,10 @@ constexpr int kChunkTail = 256;  // ... in the last stretch of the queue, so tha
 // the work-item sizes pba_autotune tries
 constexpr int kTuneChunks[3] = {512, 1024, 2048};
 constexpr int kTuneTails[2] = {128, 256};
+constexpr int kNumReductions = 2;  // reduction schemes of a work item's sums (LinParams::reduction)
+// the order pba_autotune tries them in (the butterfly first: it measured a
+// fraction of a per cent faster, within the tie margin, on every workload)
+constexpr int kTuneReductions[kNumReductions] = {1, 0};
 constexpr float kTuneTie = 0.02f;  // relative time difference the autotuner treats as a tie
 
 }  // namespace
@@ -1793,7 +1797,7 @@ namespace {
 
 // Tuned settings per configuration, for the life of the process.
 struct TuneEntry {
-    int variant_full, variant_cost, chunk, chunk_tail;
+    int variant_full, variant_cost, chunk, chunk_tail, reduction;
     float ms_full, ms_cost;
 };
 std::mutex g_tune_mutex;
@@ -1860,7 +1864,7 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     }
     if ((st = ensure_points(p))) return st;
     const std::string key = tune_key(p);
-    TuneEntry best{0, 0, kChunk, kChunkTail, 3.4e38f, 3.4e38f};
+    TuneEntry best{0, 0, kChunk, kChunkTail, 0, 3.4e38f, 3.4e38f};
     bool cached = false;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1874,21 +1878,26 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
         cudaEvent_t e0, e1;
         CUDA_TRY(p, cudaEventCreate(&e0));
         CUDA_TRY(p, cudaEventCreate(&e1));
-        // the full pass over work-item size x tail size x occupancy variant; settings
-        // within kTuneTie of the fastest count as equal and the first of them in
-        // this order is kept, so that timing noise does not flip the choice
-        struct Timed { int chunk, tail, variant; float ms; };
+        // the full pass over work-item size x tail size x occupancy variant x
+        // reduction scheme; settings within kTuneTie of the fastest count as equal
+        // and the first of them in this order is kept, so that timing noise does
+        // not flip the choice
+        struct Timed { int chunk, tail, variant, reduction; float ms; };
         std::vector<Timed> full;
         const int n_var = p->stage_ok ? PBA_N_VARIANTS : PBA_N_VARIANTS / 2;  // staged ones need tiles
         for (int c : kTuneChunks)
             for (int t : kTuneTails) {
                 if ((st = set_chunking(p, c, t))) return st;
                 CUDA_TRY(p, launch_pair_pose(p->d_poses, p->d_pf, p->d_pair_Xo, p->M, p->d_pp, p->stream));
-                for (int v = 0; v < n_var; ++v) {
-                    float ms = 0.f;
-                    if ((st = time_pass(p, true, v, repeats, e0, e1, &ms))) return st;
-                    full.push_back({c, t, v, ms});
-                }
+                for (int v = 0; v < n_var; ++v)
+                    for (int red : kTuneReductions) {
+                        float ms = 0.f;
+                        p->prm.reduction = red;
+                        st = time_pass(p, true, v, repeats, e0, e1, &ms);
+                        p->prm.reduction = 0;
+                        if (st) return st;
+                        full.push_back({c, t, v, red, ms});
+                    }
             }
         float fastest = 3.4e38f;
         for (const Timed& x : full) fastest = std::min(fastest, x.ms);
@@ -1898,6 +1907,7 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
                 best.variant_full = x.variant;
                 best.chunk = x.chunk;
                 best.chunk_tail = x.tail;
+                best.reduction = x.reduction;
                 break;
             }
         // the cost-only pass at the chosen work items
@@ -1923,6 +1933,7 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
     // (staged variants only where this problem stages tiles)
     p->variant_full = p->stage_ok ? best.variant_full : (best.variant_full & 3);
     p->variant_cost = p->stage_ok ? best.variant_cost : (best.variant_cost & 3);
+    p->prm.reduction = best.reduction;
     p->tune_ms_full = best.ms_full;
     p->tune_ms_cost = best.ms_cost;
     p->tune_from_cache = cached ? 1 : 0;
@@ -1941,6 +1952,7 @@ int pba_get_tuning(pba_problem* p, pba_tuning* out) {
     out->variant_cost = p->variant_cost;
     out->chunk = p->chunk;
     out->chunk_tail = p->chunk_tail;
+    out->reduction = p->prm.reduction;
     out->from_cache = p->tune_from_cache;
     out->tile_err = 0;
     if (p->d_tile_err) CUDA_TRY(p, cudaMemcpy(&out->tile_err, p->d_tile_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -2333,8 +2345,15 @@ int pba_set_tuning(pba_problem* p, const pba_tuning* t) {
     if (t->chunk < 32 || t->chunk > 8192 || t->chunk % 32 || t->chunk_tail < 32 || t->chunk_tail > t->chunk ||
         t->chunk_tail % 32)
         return fail(p, PBA_EINVAL, "set_tuning: chunk must be a multiple of 32 in [32, 8192], chunk_tail one in [32, chunk]");
+    if (t->reduction < 0 || t->reduction >= kNumReductions)
+        return fail(p, PBA_EINVAL, "set_tuning: reduction must be 0 (shared-memory table) or 1 (shuffle butterfly)");
+    const int old_reduction = p->prm.reduction;
+    p->prm.reduction = t->reduction;  // (pba_set_variants drops the iteration graph)
     int st = pba_set_variants(p, t->variant_full, t->variant_cost);
-    if (st) return st;
+    if (st) {
+        p->prm.reduction = old_reduction;
+        return st;
+    }
     p->tune_ms_full = p->tune_ms_cost = 0.f;
     p->tune_from_cache = 0;
     if (p->cfg.path != PBA_PATH_BATCHED || p->M <= 0) {

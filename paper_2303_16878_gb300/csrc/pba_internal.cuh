@@ -120,6 +120,9 @@ struct LinParams {
     // wait ran out
     const CUtensorMap* tmaps;
     int* tile_err;
+    // reduction of a work item's 30 sums: 0 a transposed table in shared
+    // memory (+ shuffles for the last three), 1 a butterfly of shuffles
+    int reduction;
 };
 
 // Device-side Levenberg-Marquardt state of one problem.

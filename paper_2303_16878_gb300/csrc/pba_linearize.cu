@@ -141,6 +141,24 @@ __device__ __forceinline__ void accum_row(Acc6& A, const float (&J)[6], float sw
     A.b[2] = __ffma2_rn(t45, e2, A.b[2]);
 }
 
+// Sum of value l over the warp's 32 lanes, returned in lane l (a reduce-scatter:
+// at the level of offset o each lane keeps the half of its o-value window that
+// its bit o selects and adds the partner's copy of that half, so after the
+// levels 16, 8, 4, 2, 1 value 0 of lane l holds the full sum of value l).
+__device__ __forceinline__ float butterfly_sum(float (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
 constexpr int kQueue = 64;   // slots of a warp's residual queue (a power of two >= 63)
 constexpr int kQItems = 14;  // floats per queued residual: e[5], w, pbar[3], point, r0, c0, a, b
 
@@ -528,43 +546,63 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
             __syncwarp();
         }
 
-        // a7: warp reduction, one FP32 partial per work item (lane t writes sum t).
-        // H6 and b6 go through the warp's queue region, empty at this point: lane l
-        // writes its 27 sums as column l of a 27 x 32 table, lane j < 27 adds row j.
+        // a7: warp reduction, one FP32 partial per work item (lane t writes sum t),
+        // by one of two schemes (LinParams::reduction, chosen by the autotuner):
+        // 0: H6 and b6 go through the warp's queue region, empty at this point:
+        //    lane l writes its 27 sums as column l of a 27 x 32 table, lane j < 27
+        //    adds row j; cost, count and the status count by shuffles;
+        // 1: all 30 sums by a butterfly of shuffles that halves the values each
+        //    lane holds at every level (lane l ends with the warp's sum l).
         float mine = 0.f;
-        if (FULL) {
-            float* tab = &Q[0][0];  // 27 x 32 floats <= kQItems x kQueue
+        if (FULL && prm.reduction == 1) {
+            float v[32];
 #pragma unroll
-            for (int j = 0; j < 21; ++j) tab[j * 32 + lane] = acc_h(acc, j);
+            for (int j = 0; j < 21; ++j) v[j] = acc_h(acc, j);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                tab[(21 + 2 * j) * 32 + lane] = acc.b[j].x;
-                tab[(22 + 2 * j) * 32 + lane] = acc.b[j].y;
+                v[21 + 2 * j] = acc.b[j].x;
+                v[22 + 2 * j] = acc.b[j].y;
             }
-            __syncwarp();
-            if (lane < 27) {
-                // rows start on bank 0: lane j reads its row from float4 (q + j) mod 8 on,
-                // so that the 8 lanes of a quarter-warp hit 8 different bank quads
-                const float4* row = reinterpret_cast<const float4*>(tab + lane * 32);
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            v[27] = cost;
+            v[28] = cnt;
+            v[29] = nonfin;
+            v[30] = v[31] = 0.f;
+            mine = butterfly_sum(v, lane);
+        } else {
+            if (FULL) {
+                float* tab = &Q[0][0];  // 27 x 32 floats <= kQItems x kQueue
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 v = row[(q + lane) & 7];
-                    s0 += v.x;
-                    s1 += v.y;
-                    s2 += v.z;
-                    s3 += v.w;
+                for (int j = 0; j < 21; ++j) tab[j * 32 + lane] = acc_h(acc, j);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    tab[(21 + 2 * j) * 32 + lane] = acc.b[j].x;
+                    tab[(22 + 2 * j) * 32 + lane] = acc.b[j].y;
                 }
-                mine = (s0 + s1) + (s2 + s3);
+                __syncwarp();
+                if (lane < 27) {
+                    // rows start on bank 0: lane j reads its row from float4 (q + j) mod 8 on,
+                    // so that the 8 lanes of a quarter-warp hit 8 different bank quads
+                    const float4* row = reinterpret_cast<const float4*>(tab + lane * 32);
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 v = row[(q + lane) & 7];
+                        s0 += v.x;
+                        s1 += v.y;
+                        s2 += v.z;
+                        s3 += v.w;
+                    }
+                    mine = (s0 + s1) + (s2 + s3);
+                }
+                __syncwarp();  // the next work item's queue writes come after these reads
             }
-            __syncwarp();  // the next work item's queue writes come after these reads
-        }
 #pragma unroll
-        for (int j = 27; j < kNumAcc; ++j) {
-            float x = j == 27 ? cost : (j == 28 ? cnt : nonfin);
+            for (int j = 27; j < kNumAcc; ++j) {
+                float x = j == 27 ? cost : (j == 28 ? cnt : nonfin);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == j) mine = x;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == j) mine = x;
+            }
         }
         // the item's partial-sum slot (its index in the plan's own order, whatever
         // order this launch takes the items in)

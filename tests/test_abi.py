@@ -59,6 +59,8 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.PbaSensor) == 16 + 8 * 16
     assert ctypes.sizeof(_lib.PbaConfig) == 8 + 8 + 8 + 9 * 8 + 16
     assert ctypes.sizeof(_lib.PbaIterStats) == 4 * 8 + 8 + 8 + 2 * 8
+    assert ctypes.sizeof(_lib.PbaTuning) == 6 * 4 + 2 * 4 + 4
+    assert _lib.PbaTuning.reduction.offset == 32
 
 
 def _config(_lib, sensors, n_frames=2, frame_sensor=None, **over):
@@ -135,6 +137,7 @@ def test_header_compiles_as_c99_and_links(tmp_path):
     lib = build.build()
     src = tmp_path / "abi.c"
     src.write_text(r"""
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 #include "pba.h"
@@ -147,6 +150,7 @@ int main(void) {
     if (pba_create(&cfg, NULL, &p) != PBA_EINVAL || p != NULL) return 3;
     if (pba_set_lambda(NULL, 1.0) != PBA_EINVAL) return 4;
     pba_destroy(NULL);
+    if (sizeof(pba_tuning) != 36 || offsetof(pba_tuning, reduction) != 32) return 5;
     printf("%d %d %d %s\n", (int)sizeof(pba_sensor), (int)sizeof(pba_config), (int)sizeof(pba_iter_stats),
            pba_last_error(NULL));
     return 0;

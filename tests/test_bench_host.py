@@ -60,11 +60,11 @@ def test_json_line_carries_the_contract_keys_and_its_arithmetic():
     assert abs(line["speedup_vs_plain"] - 29.0 / 1.3) < 1e-12
     # traffic: null without a capture of the kept variant, the capture's bytes with one
     assert r["traffic"] is None and r["hbm"]["frac"] is None
-    bench.LINEARIZE_NCU[("street", 1, 1024, 256)] = {"dram_bytes": 4.0e8, "units": {"sm_issue": 0.7}}
+    bench.LINEARIZE_NCU[("street", 1, 1024, 256, 0)] = {"dram_bytes": 4.0e8, "units": {"sm_issue": 0.7}}
     try:
         r = bench.make_line(args, 1, out, 50, 152, 6693.8)["roofline"]
     finally:
-        bench.LINEARIZE_NCU.pop(("street", 1, 1024, 256))
+        bench.LINEARIZE_NCU.pop(("street", 1, 1024, 256, 0))
     assert r["traffic"] == 4.0e8 and abs(r["hbm"]["frac"] - 4.0e8 / 1.08e-3 / 1e9 / 6693.8) < 1e-12
     # a mixed pinhole / spherical workload counts each model's points and residuals
     out2 = dict(out, points_by_model={0: 10_000_000, 1: 5_000_000}, residual_share_by_model={0: 0.75, 1: 0.25})

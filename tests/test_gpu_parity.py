@@ -278,14 +278,15 @@ def test_autotuner_reports_its_tuple_and_caches_it(oracle_lib, street3):
     a.autotune(1)
     ta = a.tuning()
     assert ta["chunk"] in (512, 1024, 2048) and ta["chunk_tail"] in (128, 256) and ta["ms_full"] > 0
+    assert ta["reduction"] in (0, 1)
     cost, _ = a.linearize()
     H, _ = a.get_system()
     assert rel(H, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
     b = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
     b.autotune(1)
     tb = b.tuning()
-    assert tb["from_cache"] and (tb["chunk"], tb["chunk_tail"], tb["variant_full"]) == \
-        (ta["chunk"], ta["chunk_tail"], ta["variant_full"])
+    assert tb["from_cache"] and (tb["chunk"], tb["chunk_tail"], tb["variant_full"], tb["reduction"]) == \
+        (ta["chunk"], ta["chunk_tail"], ta["variant_full"], ta["reduction"])
     a.close()
     b.close()
 
@@ -299,7 +300,7 @@ def test_given_tuning_is_applied_without_timing(oracle_lib, street3):
     w = street3
     ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, 1))
     p = make(w, pba.PBA_PATH_BATCHED, pba.PBA_TEXEL_F16)
-    given = dict(variant_full=pba._lib.PBA_N_VARIANTS - 1, variant_cost=1, chunk=640, chunk_tail=96)
+    given = dict(variant_full=pba._lib.PBA_N_VARIANTS - 1, variant_cost=1, chunk=640, chunk_tail=96, reduction=1)
     p.set_tuning(given)
     t = p.tuning()
     assert {k: t[k] for k in given} == given and not t["from_cache"] and t["ms_full"] == 0
@@ -307,11 +308,44 @@ def test_given_tuning_is_applied_without_timing(oracle_lib, street3):
     H, b = p.get_system()
     assert rel(H, ref["H"]) <= TOL_H and abs(cost - ref["cost"]) <= TOL_COST * ref["cost"]
     for bad in (dict(given, chunk=650), dict(given, chunk_tail=1024), dict(given, chunk_tail=0),
-                dict(given, chunk=16384), dict(given, variant_cost=pba._lib.PBA_N_VARIANTS)):
+                dict(given, chunk=16384), dict(given, variant_cost=pba._lib.PBA_N_VARIANTS),
+                dict(given, reduction=2), dict(given, reduction=-1)):
         with pytest.raises(pba.PbaError):
             p.set_tuning(bad)
         assert {k: p.tuning()[k] for k in given} == given
     assert p.iterate()["status"] == 0
+    p.close()
+
+
+@pytest.mark.parametrize("texel", [1, 0])
+@pytest.mark.parametrize("which", ["room8", "street3"])
+def test_reduction_schemes_agree(oracle_lib, which, texel, request):
+    """The two reductions of a work item's 30 sums (0: transposed table in
+    shared memory, 1: shuffle butterfly) give the same counts exactly and the
+    same system and cost up to float32 summation order, both within the
+    oracle's bars, at every occupancy variant and at short work items (many
+    partial sums per pair); the iteration graph follows a changed scheme."""
+    import paper_2303_16878_gb300 as pba
+    w = request.getfixturevalue(which)
+    ref = oracle_lib.linearize(w.sensors, w.frame_sensor, w.channels, w.poses_init, w.pairs, oprm(w.params, texel))
+    p = make(w, pba.PBA_PATH_BATCHED, texel)
+    for v in range(pba._lib.PBA_N_VARIANTS // 2):
+        out = []
+        for red in (0, 1):
+            p.set_tuning(dict(variant_full=v, variant_cost=v, chunk=256, chunk_tail=64, reduction=red))
+            assert p.tuning()["reduction"] == red
+            cost, count = p.linearize()
+            H, b = p.get_system()
+            p.set_lambda(None)
+            it = p.iterate()
+            p.set_poses(w.poses_init)
+            out.append((cost, count, H, b, it["n_valid"]))
+        (c0, n0, H0, b0, i0), (c1, n1, H1, b1, i1) = out
+        assert n0 == n1 and i0 == i1 and abs(n0 - ref["count"]) <= 1e-5 * ref["count"] + 2
+        assert abs(c0 - c1) <= 1e-6 * abs(c0) and rel(H1, H0) <= 1e-5 and rel(b1, b0) <= 1e-5
+        for H, b, c in ((H0, b0, c0), (H1, b1, c1)):
+            assert rel(H, ref["H"]) <= TOL_H and rel(b, ref["b"]) <= TOL_B
+            assert abs(c - ref["cost"]) <= TOL_COST * ref["cost"]
     p.close()
 
 
