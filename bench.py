@@ -10,8 +10,9 @@ and LiDAR frames of one instant sharing a pose variable (599 variables), the
 camera offset given with a 2 cm / 0.5 deg error (held at its given value by
 the LM step; its refinement uses the adjoint gradient, timed as `adjoint`).
 The other configurations are reported under `configs` (LiDAR 128 x 2048 with
-500 frames, the batch of 16 independent LiDAR problems, the 50-frame LiDAR
-street) and can be made the main line with --workload.
+500 frames, RGB-D 640 x 480 with 200 frames, the batch of 16 independent
+LiDAR problems, the 50-frame LiDAR street) and can be made the main line
+with --workload.
 
 Metric: residuals per second (valid pixel-point residuals linearised over
 the timed iterations / their device time) and ms per iteration.  The timed
@@ -76,7 +77,7 @@ WORKLOADS = {
              "FP16 texels / FP32 residuals / FP64-refined solve"),
 }
 DEFAULT_WORKLOAD = "joint"
-EXTRA_WORKLOADS = ("street_graph", "batch", "street")
+EXTRA_WORKLOADS = ("street_graph", "hall", "batch", "street")
 # graph-construction thresholds per workload (Sec. IV-B): angle, translation, overlap ratio
 BUILD_PAIRS = {"street": (30.0, 40.0, 0.3), "room": (30.0, 1.0, 1.0 / 3.0)}
 
