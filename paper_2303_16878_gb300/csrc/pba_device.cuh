@@ -59,7 +59,9 @@ __device__ __forceinline__ void spherical_project(float x, float y, float z, flo
     c0 = (int)(Ui + fw);
     a = w - fw;
     const float te = fabsf(z) * irxy;
-    const float el = te <= 1.f ? atan_unit(te) : 1.57079637f - atan_unit(__fdividef(1.f, te));
+    const bool steep = te > 1.f;
+    const float re = atan_unit(steep ? __fdividef(1.f, te) : te);
+    const float el = steep ? 1.57079637f - re : re;
     v = fmaf(fy, z < 0.f ? -el : el, cy);
 }
 
