@@ -111,10 +111,10 @@ def measured_hbm(path: str = None):
 # size, tail item size, reduction scheme); settings without an entry report null
 LINEARIZE_NCU = {
     # profiles/k_linearize_lidar_street_50x64x1024.md (ncu --set full, one launch at the initial poses)
-    ("street", 1, 1024, 128, 1): {"dram_bytes": 374.5e6 + 14.2e6,
-                                  "units": {"sm_issue": 0.651, "l1_data_pipe": 0.592, "l2": 0.227, "dram": 0.047}},
+    ("street", 1, 1024, 128, 1): {"dram_bytes": 374.3e6 + 13.7e6,
+                                  "units": {"sm_issue": 0.662, "l1_data_pipe": 0.602, "l2": 0.235, "dram": 0.048}},
     # profiles/k_linearize_joint_hall_900.md (DRAM bytes only: one pass on the full workload)
-    ("joint", 1, 512, 128, 1): {"dram_bytes": 40.91e9 + 0.67e9, "units": None},
+    ("joint", 1, 512, 128, 1): {"dram_bytes": 40.90e9 + 0.67e9, "units": None},
 }
 # normal estimation: neighbourhood radius clamp(NORMAL_SCALE / range, 1.5, NORMAL_MAX_RADIUS) pixels
 NORMAL_SCALE = 8.0

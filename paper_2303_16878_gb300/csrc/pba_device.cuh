@@ -147,6 +147,14 @@ struct Tap<0> {
     }
 };
 
+// All four taps usable (FP16 texels: the flags are 1 or 0, so one AND of the words).
+__device__ __forceinline__ bool all_usable(const Tap<1>& A, const Tap<1>& B, const Tap<1>& C, const Tap<1>& D) {
+    return (A.v.w & B.v.w & C.v.w & D.v.w) != 0u;
+}
+__device__ __forceinline__ bool all_usable(const Tap<0>& A, const Tap<0>& B, const Tap<0>& C, const Tap<0>& D) {
+    return A.t.usable && B.t.usable && C.t.usable && D.t.usable;
+}
+
 template <int TEXEL>
 __device__ __forceinline__ Tap<TEXEL> load_tap(const void* __restrict__ base, int idx) {
     Tap<TEXEL> a;

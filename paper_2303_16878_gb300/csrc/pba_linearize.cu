@@ -184,8 +184,8 @@ __device__ __forceinline__ void jacobian_stage(float (*Q)[kQueue], int slot, int
     const int c0 = __float_as_int(Q[11][slot]);
     const float a = Q[12][slot], b = Q[13][slot];
 
-    int cm1, cc, cp1, cp2;
-    stencil_cols(c0, W, wrap, cm1, cc, cp1, cp2);
+    // c0 was wrapped into [0, W) by stage 1
+    const int cc = c0, cp1 = wrap && c0 == W - 1 ? 0 : c0 + 1;
     const int rr0 = r0 * W, rp1 = rr0 + W;
     float gu[5], gv[5];
     if (grad_mode == 0) {
@@ -454,8 +454,7 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                 float s[5];
                 s[1] = fmaf(wA, A.depth(), fmaf(wB, B.depth(), fmaf(wC, C.depth(), wD * D.depth())));
                 const float e_d = zeta_d - s[1];
-                ok = A.usable() && B.usable() && C.usable() && D.usable() &&
-                     fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
+                ok = all_usable(A, B, C, D) && fabsf(e_d) <= fmaf(prm.occ_rel, zeta_d, prm.occ_abs);
                 if (ok) {
                     // (g, n_x) and (n_y, n_z) of the four taps as register pairs, interpolated
                     // with packed FMAs (each rounded as fmaf, in the same order)
@@ -486,9 +485,9 @@ __global__ void __launch_bounds__(kLinThreads, MINB)
                     e[2] = nbx - s[2];
                     e[3] = nby - s[3];
                     e[4] = nbz - s[4];
-                    float chi2 = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) chi2 = fmaf(om[c] * e[c], e[c], chi2);
+                    // chi^2 = e^T Omega e with the three normal rows sharing their weight
+                    const float en = fmaf(e[2], e[2], fmaf(e[3], e[3], e[4] * e[4]));
+                    const float chi2 = fmaf(om[0] * e[0], e[0], fmaf(om[1] * e[1], e[1], om[2] * en));
                     if (!(chi2 < INFINITY)) {
                         // a NaN or infinite input value (intensity, normal): the residual is
                         // left out of H, b and F and counted in the status word
