@@ -11,8 +11,9 @@
 //                 Huber weight, Jacobian J_i, and accumulation of the 6x6
 //                 H6 = sum w J_i^T Omega J_i, b6 = sum w J_i^T Omega e, cost, count
 //                 in FP32 registers; a transposed table in the warp's shared
-//                 memory (and shuffles for cost and count) gives one FP32 partial
-//                 per work item (no global atomics on residuals).
+//                 memory (and shuffles for cost and count) or a shuffle
+//                 butterfly, whichever the autotuner keeps, gives one FP32
+//                 partial per work item (no global atomics on residuals).
 // k_pair_reduce   FP64 sum of a pair's chunk partials in a fixed order, then the
 //                 pair's full 12x12 block from J_j = J_i T (see below).
 //
