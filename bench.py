@@ -22,6 +22,12 @@ before each step.  FP16 texels, FP32 residuals and Jacobians, FP64 pair
 reduction and an FP64-accurate solve (block-sparse FP32 factorisation with
 FP64 refinement for the large pose graphs).
 
+Per pyramid level (`pyramid`, the paper's runtime measure: time per complete
+iteration at each level against its pixel count): levels of half and a
+quarter of the resolution built on the device, each autotuned and timed
+like the main line with fewer steps, then the wall time of the
+coarse-to-fine optimisation (10 / 5 / 2 iterations, coarsest first).
+
 End to end (`e2e`): each step hands all frames (4.47 GB) and the poses to
 pba_iterate_frames from pinned host memory (the copies overlapped with the
 linearisation of the pairs whose frames have arrived) and reads the poses
@@ -372,6 +378,38 @@ def phase_times(prob, init, flush, steps):
     return {k: float(np.mean(v)) for k, v in phases.items()}
 
 
+def pyramid_leg(prob, w, init, stream, flush, steps, warmup, n_levels=3, schedule=(10, 5, 2)):
+    """Per pyramid level (level 0 = the frames as given, each further level half
+    the resolution): pixels, processed points, valid residuals and device ms
+    per LM iteration (events on the launch stream, L2 flushed, each level
+    autotuned); then the wall time of the coarse-to-fine optimisation with
+    `schedule` iterations (coarsest first) from the initial poses."""
+    import torch
+    prob.build_pyramid(n_levels)
+    levels = []
+    for lv in range(n_levels):
+        q = prob.level(lv)
+        pixels = int(sum(q._sizes[int(k)][0] * q._sizes[int(k)][1] for k in q._fs))
+        if lv > 0:
+            q.autotune(1)
+        ms, nvalid = time_iterations(q, init, stream, flush, steps, warmup)
+        pts = sum(q.frame_points(int(i)) for i, _ in np.asarray(w.pairs).tolist())
+        levels.append({"level": lv, "pixels": pixels, "points_per_iteration": int(pts),
+                       "residuals_per_iteration": float(np.mean(nvalid)), "ms_per_iteration": float(np.mean(ms)),
+                       "residuals_per_s": float(sum(nvalid) / (sum(ms) / 1e3))})
+    prob.set_poses(init)
+    prob.set_lambda(None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = prob.optimize(schedule)
+    torch.cuda.synchronize()
+    wall_ms = 1e3 * (time.perf_counter() - t0)
+    return {"levels": levels, "schedule": list(schedule), "optimize_ms": wall_ms,
+            "optimize_levels": [{"level": int(x["level"]), "iterations": int(x["iterations"]),
+                                 "accepted": int(x["accepted"]), "cost_first": float(x["cost_first"]),
+                                 "cost_last": float(x["cost_last"])} for x in st]}
+
+
 def run_config(name, w, stream, flush, steps, warmup, device):
     """A configuration other than the main one: value, ms per step and the phase
     split, from `steps` timed iterations."""
@@ -458,6 +496,12 @@ def run_ours(args, rank, world, device):
                                                              for m in res_split},
                n_pairs=int(len(w.pairs)), variants=variants, tuning=tuning, workload=args.workload,
                pose_variables=int(w.n_vars) if getattr(w, "frame_var", None) is not None else int(w.n_frames - 1))
+
+    # time per iteration at each pyramid level (the paper's runtime measure: one
+    # complete iteration per level against the level's pixel count), then the
+    # coarse-to-fine schedule of 10 / 5 / 2 iterations from the initial poses
+    if not args.no_extra:
+        out["pyramid"] = pyramid_leg(prob, w, init, stream, flush, min(args.steps, 20), args.warmup)
 
     # adjoint of the total cost (pose / extrinsic / image gradients), events on the same stream
     prob.set_poses(init)
@@ -932,7 +976,7 @@ def make_line(args, world: int, out: dict, n_frames: int, n_sms: int, hbm_peak_g
         "gpu_launches": out["launches"] * args.steps,
         "clocks": out["clocks"],
     }
-    for k in ("build_pairs", "normals", "adjoint", "e2e", "configs", "error"):
+    for k in ("build_pairs", "normals", "adjoint", "pyramid", "e2e", "configs", "error"):
         if k in out and out[k] is not None:
             line[k] = out[k]
     if "plain_ms_per_step" in out:
