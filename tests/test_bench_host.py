@@ -232,3 +232,65 @@ def test_sample_slices_keep_only_their_frames():
             si, sj = sub.pairs[n]
             assert np.array_equal(sub.channels[si], w.channels[i]) and np.array_equal(sub.channels[sj], w.channels[j])
             assert np.array_equal(sub.poses_init[si], w.poses_init[i]) and masks[n][0] == q
+
+
+def test_pyramid_leg_reports_every_level_and_the_schedule(monkeypatch):
+    """The per-level timing leg on a stand-in for the problem: one entry per
+    level with its pixel count (sensor sizes halved per level), points,
+    residuals and times, coarse levels tuned, and the schedule's per-level
+    outcome."""
+    import types
+    import bench
+
+    calls = []
+
+    class Level:
+        def __init__(self, lv):
+            self.lv = lv
+            self._sizes = [(480 >> lv, 640 >> lv), (128 >> lv, 1024 >> lv)]
+            self._fs = [0, 0, 1]
+
+        def autotune(self, repeats):
+            calls.append(("autotune", self.lv))
+
+        def frame_points(self, i):
+            return 1000 >> (2 * self.lv)
+
+    class Prob:
+        def __init__(self):
+            self.levels = {lv: Level(lv) for lv in range(3)}
+
+        def build_pyramid(self, n):
+            calls.append(("build", n))
+
+        def level(self, lv):
+            return self.levels[lv]
+
+        def set_poses(self, p):
+            pass
+
+        def set_lambda(self, x):
+            pass
+
+        def optimize(self, schedule):
+            return [dict(level=2 - k, iterations=n, accepted=n - 1, status=0, cost_first=10.0 - k, cost_last=9.0 - k)
+                    for k, n in enumerate(schedule)]
+
+    def fake_time(q, init, stream, flush, steps, warmup):
+        return [2.0 / (1 + q.lv)] * steps, [100.0 / (1 + q.lv)] * steps
+
+    monkeypatch.setattr(bench, "time_iterations", fake_time)
+    torch_stub = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
+    monkeypatch.setitem(__import__("sys").modules, "torch", torch_stub)
+    import numpy as np
+    w = types.SimpleNamespace(pairs=np.array([[0, 1], [1, 2], [2, 0]]))
+    out = bench.pyramid_leg(Prob(), w, None, None, None, 4, 1)
+    assert calls[0] == ("build", 3) and ("autotune", 1) in calls and ("autotune", 2) in calls
+    assert ("autotune", 0) not in calls
+    px = [lv["pixels"] for lv in out["levels"]]
+    assert px == [2 * 480 * 640 + 128 * 1024, 2 * 240 * 320 + 64 * 512, 2 * 120 * 160 + 32 * 256]
+    assert [lv["points_per_iteration"] for lv in out["levels"]] == [3000, 3 * 250, 3 * 62]
+    assert out["levels"][1]["ms_per_iteration"] == 1.0 and out["levels"][1]["residuals_per_iteration"] == 50.0
+    assert abs(out["levels"][0]["residuals_per_s"] - 100.0 / 2e-3) < 1e-6
+    assert out["schedule"] == [10, 5, 2] and [x["level"] for x in out["optimize_levels"]] == [2, 1, 0]
+    assert out["optimize_levels"][0]["iterations"] == 10 and out["optimize_ms"] >= 0.0
