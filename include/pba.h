@@ -487,12 +487,11 @@ int pba_iteration_launches(pba_problem* p, int32_t* n_launches);
  * points per lane) x size of the short items that end the queue (128, 256) x
  * variant (0 .. PBA_N_VARIANTS - 1; the staged variants 4 .. 7 only where
  * tiles are staged) x reduction scheme of a work item's sums (0, 1: see
- * pba_tuning), then for the cost-only
- * pass the variants at the chosen work items; settings
- * within 2 % of the fastest count as equal, and the first of them in that
- * order (work-item size, then tail size and variant, each ascending, then
- * reduction 1 before 0) is
- * kept, so that timing noise does not change the choice between runs.  Later
+ * pba_tuning), then for the cost-only pass the variants at the chosen work
+ * items; settings within 2 % of the fastest count as equal, and the first of
+ * them in that order (work-item size, then tail size and variant, each
+ * ascending, then reduction 1 before 0) is kept, so that timing noise does
+ * not change the choice between runs.  Later
  * iterations use the choice (pba_get_tuning reports it).  The result is
  * cached for the life of the process per configuration (device, texel
  * precision, gradient mode, pairs, point counts, sensors): tuning the same
@@ -511,8 +510,8 @@ int pba_autotune(pba_problem* p, int repeats, int32_t* variant_full, int32_t* va
  * transposed table in the warp's shared memory and lane j adds row j; 1: a
  * butterfly of warp shuffles in which every level halves the values a lane
  * holds, lane j ending with sum j; the two differ only in float32 summation
- * order), whether they came from the process's cache
- * of tuned configurations (same device, texel precision, gradient mode,
+ * order), whether they came from the process's cache of tuned
+ * configurations (same device, texel precision, gradient mode,
  * pairs, point counts and sensors: no timing was done), whether a staged
  * tile's wait ran past its limit since the problem was created (tile_err: 1;
  * the taps are then read directly, the results stay exact), and the mean time
@@ -533,8 +532,8 @@ int pba_set_variants(pba_problem* p, int variant_full, int variant_cost);
 
 /* Apply a tuning given by the caller (e.g. one pba_get_tuning reported in an
  * earlier process) without timing anything: its variants, work-item size,
- * tail item size and reduction scheme; from_cache, ms_full and ms_cost are ignored (reported as 0
- * afterwards).  Rebuilds the pair plan when the work items change.  On the
+ * tail item size and reduction scheme; from_cache, ms_full and ms_cost are
+ * ignored (reported as 0 afterwards).  Rebuilds the pair plan when the work items change.  On the
  * plain path only the values are recorded.  Errors: PBA_EINVAL (tuning NULL, a
  * variant outside [0, PBA_N_VARIANTS), chunk not a multiple of 32 in
  * [32, 8192], chunk_tail not a multiple of 32 in [32, chunk], reduction not
