@@ -35,7 +35,7 @@ constexpr int kAdjStride = 48;     // floats per work-item partial
 constexpr int kAdjPairStride = 40; // doubles per pair: dR_i dt_i dR_j dt_j (24), dR_o dt_o (12), cost, count
 
 template <int TEXEL>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, 2)
     k_adjoint(const int4* __restrict__ chunks, int n_chunks, int* __restrict__ queue, const PairStatic* __restrict__ ps,
               const PairPose* __restrict__ pp, const float4* __restrict__ pts_pg, const float4* __restrict__ pts_n,
               const int* __restrict__ pts_pix, const void* __restrict__ tex, const SensorDev* __restrict__ sensors,
