@@ -16,7 +16,11 @@
 // derivative of F, whatever grad_mode the linearisation uses), and per work
 // item the sums  P1 = sum g_p p_u^T,  g_a = sum g_p,  N1 = sum g_n n^o^T,
 // Q = sum pbar g_p^T,  Nn = sum nbar g_n^T  (39 floats) plus cost and count.
-// Image gradients go straight to the caller's buffer with atomics.
+// Image gradients go straight to the caller's buffer with atomics.  The launch
+// is persistent (warps take work items from a counter) with 256-thread blocks
+// held to 128 registers so that two blocks share an SM: at the 156 registers
+// the compiler takes otherwise, one block (8 warps) per SM left the gathers'
+// latency unhidden.
 // k_adjoint_pairs turns a pair's FP64 sums into
 //   dF/dR_i = R_j R_o G_M,  dF/dt_i = R_j R_o g_a = -dF/dt_j,
 //   dF/dR_j = R_i G_M^T R_o^T + (t_i - t_j) g_a^T R_o^T,        G_M = P1 + N1,
