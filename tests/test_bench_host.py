@@ -294,3 +294,16 @@ def test_pyramid_leg_reports_every_level_and_the_schedule(monkeypatch):
     assert abs(out["levels"][0]["residuals_per_s"] - 100.0 / 2e-3) < 1e-6
     assert out["schedule"] == [10, 5, 2] and [x["level"] for x in out["optimize_levels"]] == [2, 1, 0]
     assert out["optimize_levels"][0]["iterations"] == 10 and out["optimize_ms"] >= 0.0
+
+
+def test_solve_roof_is_the_dense_cholesky_work_at_the_measured_rate():
+    """The solve's roof object: n = 6 x pose variables unknowns, n^3 / 3 FLOP of a
+    dense Cholesky, its time at the measured FP64 rate, and null without a rate."""
+    import bench
+    r = bench.solve_roof(2.85, 599, 1.1)
+    n = 6 * 599
+    assert r["unknowns"] == n and r["solve_ms"] == 2.85 and r["fp64_dgemm_tflops_measured"] == 1.1
+    assert abs(r["dense_cholesky_gflop"] - n ** 3 / 3e9) < 1e-9
+    assert abs(r["dense_cholesky_ms_at_measured_fp64"] - n ** 3 / 3e9 / 1.1) < 1e-9
+    assert "latency" in r["bound"]
+    assert bench.solve_roof(2.85, 599, None) is None and bench.solve_roof(None, 599, 1.1) is None
